@@ -1,0 +1,640 @@
+/*
+ * gsvr_oracle.c -- FP64 brute-force CPU oracle for the analytic-PSF slice
+ * forward model over anisotropic 3D Gaussians, its gradient, the Adam step
+ * and the pixel sampler.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline / reference arm of bench.py load this library.  It shares no
+ * code, header, table or helper with the CUDA path, and the product path never
+ * calls it.
+ *
+ * What it computes (paper sections / equations):
+ *  - Gaussian primitive (Sec. 3.2, Eq. 2 numerator): mean mu, covariance
+ *    Sigma = R S S^T R^T with S = diag(exp(ls)) (log-space scales, Nomenclature
+ *    table) and R from the normalised quaternion q = (w, x, y, z); amplitude c.
+ *  - Acquisition (Eq. 1, Eq. 3): pixel u of slice i sits at x = R_i u + t_i
+ *    (u = (u_x, u_y, 0) in slice millimetres), and its value is the volume
+ *    convolved with the slice PSF N(0, R_i Sigma_PSF R_i^T) evaluated at x.
+ *  - Closed form (Eq. 4, Eq. 5 numerator): for each Gaussian,
+ *    Sigma_obs = Sigma_j + R_i Sigma_PSF R_i^T and the pixel receives
+ *    c_j * f * exp(-1/2 v^T Sigma_obs^-1 v), v = x - mu_j, where f is the
+ *    exact-convolution normalisation sqrt(det Sigma_j / det Sigma_obs)
+ *    (norm_mode 0) or 1 (norm_mode 1, the literal substitution of Eq. 5).
+ *    EVERY (pixel, Gaussian) pair is summed; nothing is culled.
+ *  - Motion (Sec. 3.4): per slice a 6-DoF motion (r, tau), r axis-angle.  The
+ *    slice frame is R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau.
+ *  - Loss: L = sum_p w_p (I_hat_p - I_p)^2 (mean squared error, w_p = 1/|sample|).
+ *  - Gradient of L with respect to mu, ls, q, c and (r, tau), written out in
+ *    the 3D form (derivative of the expressions above, pair by pair).
+ *  - Adam (the optimiser of the Optimization Details appendix, decoupled
+ *    weight decay 0), per parameter group learning rate.
+ *
+ * Parameter vector layout (component-major SoA), N Gaussians, M slices:
+ *   [0,N) mu_x  [N,2N) mu_y  [2N,3N) mu_z  [3N..6N) ls_0..2
+ *   [6N..10N) q_w q_x q_y q_z   [10N,11N) c   [11N + 6i + k] pose of slice i
+ *   (k = 0..2 axis-angle r, 3..5 translation tau).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t n_slices, H, W, pad_;
+    double dx, dy, thickness;
+    double R[9];      /* row-major; columns are the slice x, y and normal axes in world */
+    double origin[3]; /* world position of the stack centre */
+    double fwhm[3];   /* PSF full width at half maximum along slice x, y, normal */
+} or_stack;
+
+typedef struct {
+    double R0[9], c0[3]; /* nominal frame of the slice */
+    double var[3];       /* diagonal of Sigma_PSF in slice coordinates */
+    double dx, dy;
+    int32_t H, W;
+    int64_t pix_base;    /* first global pixel index of this slice */
+} or_slice;
+
+/* ---------------------------------------------------------------- 3x3 utils */
+static void mat_mul(const double *A, const double *B, double *C) {
+    double T[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * k + c];
+            T[3 * r + c] = s;
+        }
+    memcpy(C, T, sizeof T);
+}
+static void mat_mul_bt(const double *A, const double *B, double *C) { /* A B^T */
+    double T[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * c + k];
+            T[3 * r + c] = s;
+        }
+    memcpy(C, T, sizeof T);
+}
+static void mat_mul_at(const double *A, const double *B, double *C) { /* A^T B */
+    double T[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * k + r] * B[3 * k + c];
+            T[3 * r + c] = s;
+        }
+    memcpy(C, T, sizeof T);
+}
+static void mat_vec(const double *A, const double *v, double *o) {
+    double t[3];
+    for (int r = 0; r < 3; ++r) t[r] = A[3 * r] * v[0] + A[3 * r + 1] * v[1] + A[3 * r + 2] * v[2];
+    memcpy(o, t, sizeof t);
+}
+static double det3(const double *A) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+/* inverse by the adjugate; returns the determinant */
+static double inv3(const double *A, double *Ai) {
+    double d = det3(A);
+    double id = 1.0 / d;
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) * id;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) * id;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return d;
+}
+static void skew(const double *v, double *K) {
+    K[0] = 0.0;   K[1] = -v[2]; K[2] = v[1];
+    K[3] = v[2];  K[4] = 0.0;   K[5] = -v[0];
+    K[6] = -v[1]; K[7] = v[0];  K[8] = 0.0;
+}
+
+/* --------------------------------------------------------------- rotations */
+/* Rotation matrix of the unit quaternion q/|q|, q = (w, x, y, z). */
+void oracle_quat_to_rot(const double *q_in, double *R) {
+    double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Rodrigues: exp of the skew matrix of the axis-angle vector r,
+ * R = I + A K + B K^2 with A = sin(th)/th, B = (1 - cos th)/th^2. */
+static void rod_coeffs(double th, double *A, double *B, double *dA, double *dB) {
+    /* dA = A'(th)/th, dB = B'(th)/th (so that d/dr_k of A is dA * r_k) */
+    if (th < 1e-3) {
+        double t2 = th * th;
+        *A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+        *B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        *dA = -1.0 / 3.0 + t2 / 30.0 - t2 * t2 / 840.0;
+        *dB = -1.0 / 12.0 + t2 / 180.0 - t2 * t2 / 6720.0;
+    } else {
+        double s = sin(th), c = cos(th);
+        *A = s / th;
+        *B = (1.0 - c) / (th * th);
+        *dA = (th * c - s) / (th * th * th);
+        *dB = (th * s - 2.0 * (1.0 - c)) / (th * th * th * th);
+    }
+}
+void oracle_rodrigues(const double *r, double *R) {
+    double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double A, B, dA, dB, K[9], K2[9];
+    rod_coeffs(th, &A, &B, &dA, &dB);
+    skew(r, K);
+    mat_mul(K, K, K2);
+    for (int e = 0; e < 9; ++e) R[e] = (e % 4 == 0 ? 1.0 : 0.0) + A * K[e] + B * K2[e];
+}
+/* dR/dr_k by the product rule on R = I + A(th) K + B(th) K^2. */
+static void rodrigues_jac(const double *r, double J[3][9]) {
+    double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double A, B, dA, dB, K[9], K2[9];
+    rod_coeffs(th, &A, &B, &dA, &dB);
+    skew(r, K);
+    mat_mul(K, K, K2);
+    for (int k = 0; k < 3; ++k) {
+        double ek[3] = {0, 0, 0}, E[9], EK[9], KE[9];
+        ek[k] = 1.0;
+        skew(ek, E);
+        mat_mul(E, K, EK);
+        mat_mul(K, E, KE);
+        for (int e = 0; e < 9; ++e)
+            J[k][e] = dA * r[k] * K[e] + A * E[e] + dB * r[k] * K2[e] + B * (EK[e] + KE[e]);
+    }
+}
+
+/* ------------------------------------------------------------ slice frames */
+/* Stacks -> slices.  Slice k of a stack of n slices is centred at
+ * origin + (k - (n-1)/2) * thickness * normal (contiguous slices, no gap);
+ * its nominal rotation is the stack rotation; Sigma_PSF = diag((fwhm/2.355)^2).
+ * Returns the number of slices; fills out (may be NULL to count). */
+int64_t oracle_build_slices(int n_stacks, const or_stack *st, or_slice *out, int64_t *n_pixels) {
+    int64_t m = 0, pix = 0;
+    for (int s = 0; s < n_stacks; ++s) {
+        for (int k = 0; k < st[s].n_slices; ++k) {
+            if (out) {
+                or_slice *o = &out[m];
+                memcpy(o->R0, st[s].R, sizeof o->R0);
+                double off = ((double)k - 0.5 * (st[s].n_slices - 1)) * st[s].thickness;
+                for (int a = 0; a < 3; ++a) o->c0[a] = st[s].origin[a] + off * st[s].R[3 * a + 2];
+                for (int a = 0; a < 3; ++a) {
+                    double sg = st[s].fwhm[a] / 2.355;
+                    o->var[a] = sg * sg;
+                }
+                o->dx = st[s].dx;
+                o->dy = st[s].dy;
+                o->H = st[s].H;
+                o->W = st[s].W;
+                o->pix_base = pix;
+            }
+            pix += (int64_t)st[s].H * st[s].W;
+            ++m;
+        }
+    }
+    if (n_pixels) *n_pixels = pix;
+    return m;
+}
+
+typedef struct {
+    double R[9], t[3];  /* world-from-slice rotation and slice centre */
+    double Spsf[9];     /* R Sigma_PSF R^T */
+    double rod[9];      /* Rod(r) */
+} or_frame;
+
+static void slice_frame(const or_slice *s, const double *pose, or_frame *f) {
+    oracle_rodrigues(pose, f->rod);
+    mat_mul(f->rod, s->R0, f->R);
+    mat_vec(f->rod, s->c0, f->t);
+    for (int a = 0; a < 3; ++a) f->t[a] += pose[3 + a];
+    double D[9] = {s->var[0], 0, 0, 0, s->var[1], 0, 0, 0, s->var[2]}, T[9];
+    mat_mul(f->R, D, T);
+    mat_mul_bt(T, f->R, f->Spsf);
+}
+
+/* Exported for the geometry pins: world frame (R_i, t_i) of every slice. */
+int oracle_slice_frames(int n_stacks, const or_stack *st, const double *pose, double *R_out, double *t_out) {
+    int64_t npx;
+    int64_t M = oracle_build_slices(n_stacks, st, NULL, &npx);
+    or_slice *sl = (or_slice *)malloc(sizeof(or_slice) * (size_t)(M ? M : 1));
+    oracle_build_slices(n_stacks, st, sl, &npx);
+    for (int64_t i = 0; i < M; ++i) {
+        or_frame f;
+        slice_frame(&sl[i], pose + 6 * i, &f);
+        memcpy(R_out + 9 * i, f.R, sizeof f.R);
+        memcpy(t_out + 3 * i, f.t, sizeof f.t);
+    }
+    free(sl);
+    return (int)M;
+}
+
+/* Decode a global pixel index into (slice, row, col) and its slice-local mm
+ * coordinate u = ((col - (W-1)/2) dx, (row - (H-1)/2) dy, 0). */
+static int64_t find_slice(const or_slice *sl, int64_t M, int64_t p) {
+    int64_t lo = 0, hi = M - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (sl[mid].pix_base <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+static void pixel_local(const or_slice *s, int64_t p, double *u) {
+    int64_t loc = p - s->pix_base;
+    int64_t row = loc / s->W, col = loc % s->W;
+    u[0] = ((double)col - 0.5 * (s->W - 1)) * s->dx;
+    u[1] = ((double)row - 0.5 * (s->H - 1)) * s->dy;
+    u[2] = 0.0;
+}
+
+/* ---------------------------------------------------------------- Gaussians */
+typedef struct {
+    double mu[3], Rj[9], s2[3], Sig[9], det, c, qn[4], qnorm;
+} or_gauss;
+
+static void gauss_setup(int64_t N, const double *th, int64_t j, or_gauss *g) {
+    for (int a = 0; a < 3; ++a) g->mu[a] = th[a * N + j];
+    double q[4];
+    for (int a = 0; a < 4; ++a) q[a] = th[(6 + a) * N + j];
+    g->qnorm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int a = 0; a < 4; ++a) g->qn[a] = q[a] / g->qnorm;
+    oracle_quat_to_rot(q, g->Rj);
+    double lsum = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double ls = th[(3 + a) * N + j];
+        g->s2[a] = exp(2.0 * ls);
+        lsum += ls;
+    }
+    double D[9] = {g->s2[0], 0, 0, 0, g->s2[1], 0, 0, 0, g->s2[2]}, T[9];
+    mat_mul(g->Rj, D, T);
+    mat_mul_bt(T, g->Rj, g->Sig);
+    g->det = exp(2.0 * lsum);
+    g->c = th[10 * N + j];
+}
+
+/* Gaussian covariance for the pins: Sigma (9 per Gaussian, row-major). */
+void oracle_gauss_cov(int64_t N, const double *theta, double *Sig_out) {
+    for (int64_t j = 0; j < N; ++j) {
+        or_gauss g;
+        gauss_setup(N, theta, j, &g);
+        memcpy(Sig_out + 9 * j, g.Sig, sizeof g.Sig);
+    }
+}
+
+/* One pair: value g = f * exp(-1/2 v^T P v) and the pieces the gradient needs. */
+typedef struct {
+    double P[9], v[3], Pv[3], e, f, g;
+} or_pair;
+
+static void eval_pair(const or_gauss *gj, const or_frame *fr, const double *x, int norm_mode, or_pair *pr) {
+    double So[9];
+    for (int e = 0; e < 9; ++e) So[e] = gj->Sig[e] + fr->Spsf[e];
+    double dso = inv3(So, pr->P);
+    for (int a = 0; a < 3; ++a) pr->v[a] = x[a] - gj->mu[a];
+    mat_vec(pr->P, pr->v, pr->Pv);
+    double d2 = pr->v[0] * pr->Pv[0] + pr->v[1] * pr->Pv[1] + pr->v[2] * pr->Pv[2];
+    pr->e = exp(-0.5 * d2);
+    pr->f = norm_mode == 0 ? sqrt(gj->det / dso) : 1.0;
+    pr->g = pr->f * pr->e;
+}
+
+typedef struct {
+    int64_t M, npx;
+    or_slice *sl;
+    or_frame *fr;
+    or_gauss *g;
+} or_model;
+
+static int model_setup(int n_stacks, const or_stack *st, int64_t N, const double *theta, or_model *m) {
+    m->M = oracle_build_slices(n_stacks, st, NULL, &m->npx);
+    m->sl = (or_slice *)malloc(sizeof(or_slice) * (size_t)(m->M ? m->M : 1));
+    m->fr = (or_frame *)malloc(sizeof(or_frame) * (size_t)(m->M ? m->M : 1));
+    m->g = (or_gauss *)malloc(sizeof(or_gauss) * (size_t)(N ? N : 1));
+    if (!m->sl || !m->fr || !m->g) return -1;
+    oracle_build_slices(n_stacks, st, m->sl, &m->npx);
+    for (int64_t i = 0; i < m->M; ++i) slice_frame(&m->sl[i], theta + 11 * N + 6 * i, &m->fr[i]);
+    for (int64_t j = 0; j < N; ++j) gauss_setup(N, theta, j, &m->g[j]);
+    return 0;
+}
+static void model_free(or_model *m) {
+    free(m->sl);
+    free(m->fr);
+    free(m->g);
+}
+
+static void pixel_world(const or_model *m, int64_t p, int64_t *slice, double *u, double *x) {
+    int64_t i = find_slice(m->sl, m->M, p);
+    pixel_local(&m->sl[i], p, u);
+    mat_vec(m->fr[i].R, u, x);
+    for (int a = 0; a < 3; ++a) x[a] += m->fr[i].t[a];
+    *slice = i;
+}
+
+/* Forward: pred[p] = sum over ALL Gaussians; loss = sum_p w_pix (pred - I)^2. */
+int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
+                   const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, double *pred,
+                   double *loss) {
+    or_model m;
+    if (model_setup(n_stacks, st, N, theta, &m)) return -1;
+    double L = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : L)
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t i;
+        double u[3], x[3];
+        pixel_world(&m, pix[p], &i, u, x);
+        double s = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            or_pair pr;
+            eval_pair(&m.g[j], &m.fr[i], x, norm_mode, &pr);
+            s += m.g[j].c * pr.g;
+        }
+        pred[p] = s;
+        if (I_obs) {
+            double r = s - I_obs[p];
+            L += w_pix * r * r;
+        }
+    }
+    if (loss) *loss = L;
+    model_free(&m);
+    return 0;
+}
+
+/* Chain of a symmetric covariance gradient G (dL = tr(G dSigma)) through
+ * Sigma = R diag(s^2) R^T, s = exp(ls), R = R(q/|q|): d ls (3) and d q (4). */
+static void cov_chain(const or_gauss *g, const double *G, double *dls, double *dq) {
+    double RtG[9], RtGR[9];
+    mat_mul_at(g->Rj, G, RtG);
+    mat_mul(RtG, g->Rj, RtGR);
+    for (int k = 0; k < 3; ++k) dls[k] = 2.0 * g->s2[k] * RtGR[4 * k];
+    /* dL/dR = 2 G R D */
+    double D[9] = {g->s2[0], 0, 0, 0, g->s2[1], 0, 0, 0, g->s2[2]}, GR[9], GRD[9];
+    mat_mul(G, g->Rj, GR);
+    mat_mul(GR, D, GRD);
+    for (int e = 0; e < 9; ++e) GRD[e] *= 2.0;
+    double w = g->qn[0], x = g->qn[1], y = g->qn[2], z = g->qn[3];
+    /* partial derivatives of R(w,x,y,z) (unit-quaternion formula) */
+    const double dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    const double dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const double dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    const double dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    double gq[4] = {0, 0, 0, 0};
+    for (int e = 0; e < 9; ++e) {
+        gq[0] += GRD[e] * dRw[e];
+        gq[1] += GRD[e] * dRx[e];
+        gq[2] += GRD[e] * dRy[e];
+        gq[3] += GRD[e] * dRz[e];
+    }
+    /* through the normalisation q_hat = q / |q| */
+    double dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    dq[0] = (gq[0] - w * dot) / g->qnorm;
+    dq[1] = (gq[1] - x * dot) / g->qnorm;
+    dq[2] = (gq[2] - y * dot) / g->qnorm;
+    dq[3] = (gq[3] - z * dot) / g->qnorm;
+}
+
+/* Chain of the slice-frame gradients (dL/dR_i, dL/dt_i) through
+ * R_i = Rod(r) R0, t_i = Rod(r) c0 + tau: d r (3), d tau (3). */
+static void pose_chain(const or_slice *s, const double *pose, const double *GR, const double *Gt, double *out6) {
+    double J[3][9], G[9];
+    rodrigues_jac(pose, J);
+    /* dL/dRod = GR R0^T + Gt c0^T */
+    mat_mul_bt(GR, s->R0, G);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[3 * a + b] += Gt[a] * s->c0[b];
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        for (int e = 0; e < 9; ++e) acc += G[e] * J[k][e];
+        out6[k] = acc;
+    }
+    for (int a = 0; a < 3; ++a) out6[3 + a] = Gt[a];
+}
+
+/*
+ * Forward + backward.  grad (11N + 6M) receives dL/dtheta.  absgrad, when not
+ * NULL, receives for every entry the sum over pairs of |that pair's
+ * contribution| (a condition-aware scale for comparing float32 sums).
+ * Only Gaussians with sel[j] != 0 get gradients (sel NULL = all); pose
+ * gradients always include every pair of the selected Gaussians.
+ */
+int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
+                            const int64_t *pix, const double *I_obs, double w_pix, int norm_mode,
+                            const uint8_t *sel, double *pred, double *loss, double *grad, double *absgrad) {
+    or_model m;
+    if (model_setup(n_stacks, st, N, theta, &m)) return -1;
+    const int64_t M = m.M;
+    double *rbar = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *px = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
+    double *pu = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
+    int64_t *psl = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
+    double L = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : L)
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t i;
+        pixel_world(&m, pix[p], &i, &pu[3 * p], &px[3 * p]);
+        psl[p] = i;
+        double s = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            or_pair pr;
+            eval_pair(&m.g[j], &m.fr[i], &px[3 * p], norm_mode, &pr);
+            s += m.g[j].c * pr.g;
+        }
+        if (pred) pred[p] = s;
+        double r = s - I_obs[p];
+        L += w_pix * r * r;
+        rbar[p] = 2.0 * w_pix * r;
+    }
+    if (loss) *loss = L;
+    memset(grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
+    if (absgrad) memset(absgrad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
+
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    /* per-thread slice accumulators: dL/dR_i (9), dL/dt_i (3), |.| of the pose entries (6) */
+    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 18, sizeof(double));
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 18;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < N; ++j) {
+            if (sel && !sel[j]) continue;
+            const or_gauss *gj = &m.g[j];
+            double gmu[3] = {0, 0, 0}, GS[9] = {0}, gc = 0.0, glogdet = 0.0;
+            double amu[3] = {0, 0, 0}, als[3] = {0, 0, 0}, aq[4] = {0, 0, 0, 0}, ac = 0.0;
+            for (int64_t p = 0; p < P; ++p) {
+                int64_t i = psl[p];
+                or_pair pr;
+                eval_pair(gj, &m.fr[i], &px[3 * p], norm_mode, &pr);
+                double a = rbar[p] * gj->c * pr.g;
+                double dc = rbar[p] * pr.g;
+                gc += dc;
+                /* d/dSigma_obs of exp(-1/2 v^T P v) is 1/2 P v v^T P; the exact
+                 * normalisation adds d/dSigma_obs of -1/2 log det Sigma_obs = -1/2 P. */
+                const double pk = norm_mode == 0 ? 1.0 : 0.0;
+                double Go[9];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c)
+                        Go[3 * r + c] = 0.5 * a * (pr.Pv[r] * pr.Pv[c] - pk * pr.P[3 * r + c]);
+                for (int e = 0; e < 9; ++e) GS[e] += Go[e];
+                for (int k = 0; k < 3; ++k) gmu[k] += a * pr.Pv[k];
+                if (norm_mode == 0) glogdet += 0.5 * a; /* d(1/2 log det Sigma_j) */
+                /* slice-frame contributions: x = R u + t, Sigma_obs contains R Sigma_PSF R^T */
+                double dx[3] = {-a * pr.Pv[0], -a * pr.Pv[1], -a * pr.Pv[2]};
+                double GR[9], D[9] = {0}, RD[9], GoRD[9];
+                D[0] = m.sl[i].var[0]; D[4] = m.sl[i].var[1]; D[8] = m.sl[i].var[2];
+                mat_mul(m.fr[i].R, D, RD);
+                mat_mul(Go, RD, GoRD);
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c)
+                        GR[3 * r + c] = dx[r] * pu[3 * p + c] + 2.0 * GoRD[3 * r + c];
+                double *acc = my + 18 * i;
+                for (int e = 0; e < 9; ++e) acc[e] += GR[e];
+                for (int k = 0; k < 3; ++k) acc[9 + k] += dx[k];
+                if (absgrad) {
+                    double d6[6], dls[3], dq[4];
+                    pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, dx, d6);
+                    for (int k = 0; k < 6; ++k) acc[12 + k] += fabs(d6[k]);
+                    cov_chain(gj, Go, dls, dq);
+                    for (int k = 0; k < 3; ++k) {
+                        double v = dls[k] + (norm_mode == 0 ? a : 0.0);
+                        als[k] += fabs(v);
+                        amu[k] += fabs(a * pr.Pv[k]);
+                    }
+                    for (int k = 0; k < 4; ++k) aq[k] += fabs(dq[k]);
+                    ac += fabs(dc);
+                }
+            }
+            double dls[3], dq[4];
+            cov_chain(gj, GS, dls, dq);
+            for (int k = 0; k < 3; ++k) {
+                grad[k * N + j] = gmu[k];
+                grad[(3 + k) * N + j] = dls[k] + 2.0 * glogdet; /* log det Sigma_j = 2 sum ls */
+            }
+            for (int k = 0; k < 4; ++k) grad[(6 + k) * N + j] = dq[k];
+            grad[10 * N + j] = gc;
+            if (absgrad) {
+                for (int k = 0; k < 3; ++k) {
+                    absgrad[k * N + j] = amu[k];
+                    absgrad[(3 + k) * N + j] = als[k];
+                }
+                for (int k = 0; k < 4; ++k) absgrad[(6 + k) * N + j] = aq[k];
+                absgrad[10 * N + j] = ac;
+            }
+        }
+    }
+    for (int64_t i = 0; i < M; ++i) {
+        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0};
+        for (int t = 0; t < nthreads; ++t) {
+            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 18;
+            for (int e = 0; e < 9; ++e) GR[e] += acc[e];
+            for (int k = 0; k < 3; ++k) Gt[k] += acc[9 + k];
+            for (int k = 0; k < 6; ++k) ab[k] += acc[12 + k];
+        }
+        double d6[6];
+        pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, Gt, d6);
+        for (int k = 0; k < 6; ++k) {
+            grad[11 * N + 6 * i + k] = d6[k];
+            if (absgrad) absgrad[11 * N + 6 * i + k] = ab[k];
+        }
+    }
+    free(pacc);
+    free(rbar);
+    free(px);
+    free(pu);
+    free(psl);
+    model_free(&m);
+    return 0;
+}
+
+/*
+ * Adam (Kingma & Ba), bias-corrected, decoupled weight decay 0, one step t >= 1,
+ * in place on theta, m, v.  Learning rate per group: lr[0] mu, lr[1] ls,
+ * lr[2] q, lr[3] c, lr[4] pose rotation r, lr[5] pose translation tau.
+ * Slices with frozen[i] != 0 keep their pose (and its moments) unchanged.
+ */
+void oracle_adam(int64_t N, int64_t M, double *theta, const double *grad, double *m, double *v,
+                 const double *lr, double beta1, double beta2, double eps, int64_t t, const uint8_t *frozen) {
+    int64_t n = 11 * N + 6 * M;
+    double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t e = 0; e < n; ++e) {
+        double rate;
+        if (e < 3 * N) rate = lr[0];
+        else if (e < 6 * N) rate = lr[1];
+        else if (e < 10 * N) rate = lr[2];
+        else if (e < 11 * N) rate = lr[3];
+        else {
+            int64_t i = (e - 11 * N) / 6, k = (e - 11 * N) % 6;
+            if (frozen && frozen[i]) continue;
+            rate = k < 3 ? lr[4] : lr[5];
+        }
+        m[e] = beta1 * m[e] + (1.0 - beta1) * grad[e];
+        v[e] = beta2 * v[e] + (1.0 - beta2) * grad[e] * grad[e];
+        double mh = m[e] / bc1, vh = v[e] / bc2;
+        theta[e] -= rate * mh / (sqrt(vh) + eps);
+    }
+}
+
+/*
+ * Pixel sampler: n_s of n mask pixels, uniformly without replacement, as the
+ * first n_s values of a keyed random permutation of [0, n).
+ *  - SplitMix64 (Steele, Lea & Flood 2014), used as a counter-based generator:
+ *    out(seed, ctr) = mix(seed + (ctr + 1) * 0x9E3779B97F4A7C15).
+ *  - A bijection f on k-bit integers (2^k >= n) made of 4 rounds of
+ *    x ^= key_r; x *= odd_r; x ^= x >> h (all mod 2^k, each step invertible),
+ *    with round keys out(seed, 4 * step + r).
+ *  - Cycle walking: y = f(x) until y < n (a permutation of [0, n)).
+ */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t ctr) {
+    uint64_t z = seed + (ctr + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+int oracle_sample_positions(int64_t n, int64_t n_s, uint64_t seed, uint64_t step, int64_t *out) {
+    if (n_s > n || n <= 0) return -1;
+    int k = 1;
+    while ((1LL << k) < n) ++k;
+    uint64_t mask = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
+    int h = (k + 1) / 2;
+    uint64_t xk[4], mul[4];
+    for (int r = 0; r < 4; ++r) {
+        uint64_t key = oracle_splitmix64(seed, 4ULL * step + (uint64_t)r);
+        xk[r] = key & mask;
+        mul[r] = (key >> 32) | 1ULL;
+    }
+    for (int64_t t = 0; t < n_s; ++t) {
+        uint64_t x = (uint64_t)t;
+        do {
+            for (int r = 0; r < 4; ++r) {
+                x = (x ^ xk[r]) & mask;
+                x = (x * mul[r]) & mask;
+                x ^= x >> h;
+            }
+        } while (x >= (uint64_t)n);
+        out[t] = (int64_t)x;
+    }
+    return 0;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,183 @@
+"""ctypes wrapper over the FP64 brute-force CPU oracle (``gsvr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference arm of ``bench.py`` import this module.  It does not
+import the CUDA package and the CUDA package does not import it.
+
+Inputs are plain numpy arrays and stack dictionaries as produced by the seeded
+input generators: ``{"n_slices", "H", "W", "dx", "dy", "thickness", "R" (3x3,
+columns = slice x, y, normal axes in world), "origin" (3), "fwhm" (3)}``.
+The parameter vector is the component-major layout documented in
+``gsvr_oracle.c`` (11 N Gaussian entries, then 6 per slice).
+
+Every function computes the plain definition (Eq. 1, 3, 4 and the numerator of
+Eq. 5 with the exact-convolution normalisation) by summing every
+(pixel, Gaussian) pair in float64; see the C file for the passages followed.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrStack(C.Structure):
+    _fields_ = [("n_slices", C.c_int32), ("H", C.c_int32), ("W", C.c_int32), ("pad_", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("thickness", C.c_double),
+                ("R", C.c_double * 9), ("origin", C.c_double * 3), ("fwhm", C.c_double * 3)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+        d, i64, vp = C.c_double, C.c_int64, C.c_void_p
+        _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp]
+        _lib.oracle_forward_backward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp, vp,
+                                                 vp, vp]
+        _lib.oracle_adam.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, d, d, i64, vp]
+        _lib.oracle_adam.restype = None
+        _lib.oracle_build_slices.argtypes = [C.c_int, vp, vp, vp]
+        _lib.oracle_build_slices.restype = i64
+        _lib.oracle_slice_frames.argtypes = [C.c_int, vp, vp, vp, vp]
+        _lib.oracle_quat_to_rot.argtypes = [vp, vp]
+        _lib.oracle_quat_to_rot.restype = None
+        _lib.oracle_rodrigues.argtypes = [vp, vp]
+        _lib.oracle_rodrigues.restype = None
+        _lib.oracle_gauss_cov.argtypes = [i64, vp, vp]
+        _lib.oracle_gauss_cov.restype = None
+        _lib.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+        _lib.oracle_splitmix64.restype = C.c_uint64
+        _lib.oracle_sample_positions.argtypes = [i64, i64, C.c_uint64, C.c_uint64, vp]
+        _lib.oracle_num_threads.restype = C.c_int
+    return _lib
+
+
+def _stacks(stacks):
+    arr = (OrStack * max(1, len(stacks)))()
+    for k, s in enumerate(stacks):
+        a = arr[k]
+        a.n_slices, a.H, a.W = int(s["n_slices"]), int(s["H"]), int(s["W"])
+        a.dx, a.dy, a.thickness = float(s["dx"]), float(s["dy"]), float(s["thickness"])
+        R = np.asarray(s["R"], dtype=np.float64).reshape(9)
+        for e in range(9):
+            a.R[e] = R[e]
+        for e in range(3):
+            a.origin[e] = float(s["origin"][e])
+            a.fwhm[e] = float(s["fwhm"][e])
+    return arr
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def num_slices(stacks):
+    return int(sum(int(s["n_slices"]) for s in stacks))
+
+
+def num_pixels(stacks):
+    return int(sum(int(s["n_slices"]) * int(s["H"]) * int(s["W"]) for s in stacks))
+
+
+def num_threads():
+    return int(lib().oracle_num_threads())
+
+
+def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0):
+    """Predictions for the listed global pixels and the MSE loss (float64)."""
+    st = _stacks(stacks)
+    th = _f64(theta)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    I = _f64(I_obs) if I_obs is not None else None
+    pred = np.zeros(len(pix), np.float64)
+    loss = np.zeros(1, np.float64)
+    rc = lib().oracle_forward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
+                              float(w_pix), int(norm_mode), _p(pred), _p(loss))
+    if rc != 0:
+        raise RuntimeError("oracle_forward failed")
+    return pred, float(loss[0])
+
+
+def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True):
+    """(pred, loss, grad, absgrad) in float64; grad has the parameter-vector layout."""
+    st = _stacks(stacks)
+    th = _f64(theta)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    I = _f64(I_obs)
+    M = num_slices(stacks)
+    n = 11 * int(N) + 6 * M
+    pred = np.zeros(len(pix), np.float64)
+    loss = np.zeros(1, np.float64)
+    grad = np.zeros(n, np.float64)
+    absg = np.zeros(n, np.float64) if want_abs else None
+    s = np.ascontiguousarray(sel, dtype=np.uint8) if sel is not None else None
+    rc = lib().oracle_forward_backward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
+                                       float(w_pix), int(norm_mode), _p(s), _p(pred), _p(loss), _p(grad),
+                                       _p(absg))
+    if rc != 0:
+        raise RuntimeError("oracle_forward_backward failed")
+    return pred, float(loss[0]), grad, absg
+
+
+def adam(N, M, theta, grad, m, v, lr, beta1, beta2, eps, t, frozen=None):
+    """One Adam step in float64; returns new (theta, m, v)."""
+    th, mm, vv = _f64(theta).copy(), _f64(m).copy(), _f64(v).copy()
+    g = _f64(grad)
+    lr = _f64(lr)
+    fz = np.ascontiguousarray(frozen, dtype=np.uint8) if frozen is not None else None
+    lib().oracle_adam(int(N), int(M), _p(th), _p(g), _p(mm), _p(vv), _p(lr), float(beta1), float(beta2),
+                      float(eps), int(t), _p(fz))
+    return th, mm, vv
+
+
+def slice_frames(stacks, theta_pose):
+    """World rotation R_i (M,3,3) and centre t_i (M,3) of every slice."""
+    st = _stacks(stacks)
+    M = num_slices(stacks)
+    pose = _f64(theta_pose).reshape(M * 6)
+    R = np.zeros((M, 9), np.float64)
+    t = np.zeros((M, 3), np.float64)
+    lib().oracle_slice_frames(len(stacks), C.addressof(st), _p(pose), _p(R), _p(t))
+    return R.reshape(M, 3, 3), t
+
+
+def quat_to_rot(q):
+    q = _f64(q)
+    R = np.zeros(9, np.float64)
+    lib().oracle_quat_to_rot(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def rodrigues(r):
+    r = _f64(r)
+    R = np.zeros(9, np.float64)
+    lib().oracle_rodrigues(_p(r), _p(R))
+    return R.reshape(3, 3)
+
+
+def gauss_cov(theta, N):
+    th = _f64(theta)
+    S = np.zeros((int(N), 9), np.float64)
+    lib().oracle_gauss_cov(int(N), _p(th), _p(S))
+    return S.reshape(int(N), 3, 3)
+
+
+def splitmix64(seed, ctr):
+    return int(lib().oracle_splitmix64(C.c_uint64(seed), C.c_uint64(ctr)))
+
+
+def sample_positions(n, n_s, seed, step):
+    out = np.zeros(int(n_s), np.int64)
+    rc = lib().oracle_sample_positions(int(n), int(n_s), C.c_uint64(seed), C.c_uint64(step), _p(out))
+    if rc != 0:
+        raise ValueError("bad sample size")
+    return out

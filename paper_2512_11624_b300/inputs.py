@@ -1,0 +1,299 @@
+"""Seeded synthetic input generators shared by the CUDA path's tests/benchmark and
+the oracle's tests.
+
+This module holds none of the method's arithmetic (no Gaussian evaluation, no
+covariance addition, no gradient): it only draws parameters, builds stack
+descriptions and simulates observations from an analytic phantom, on the CPU
+with numpy.  It imports nothing else from this package, so importing it never
+loads the CUDA library.
+
+Workloads (shapes follow the paper's acquisitions: three orthogonal thick-slice
+stacks, brain-sized field of view, motion of a few degrees / millimetres;
+Sec. 4 "Data"):
+
+- ``tiny``   2,000 Gaussians, 1 stack of 8 x 32 x 32 px (1 x 1 x 3 mm).
+- ``fetal``  ~200k Gaussians on a 0.8 mm grid inside a brain-like phantom,
+             3 orthogonal stacks of 40 x 192 x 192 px (1 x 1 x 3.5 mm),
+             per-slice motion U(+-5 deg) / U(+-3 mm), Rician noise 2 %.
+- ``random_case`` small random geometries for edge-case parity tests.
+
+Stack dictionaries: ``n_slices, H, W, dx, dy, thickness`` (mm), ``R`` (3x3,
+columns = slice x axis, slice y axis, slice normal in world coordinates),
+``origin`` (3, world position of the stack centre), ``fwhm`` (3, PSF FWHM along
+slice x, y and normal; in-plane 1.2 x pixel size, through-plane = thickness).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+FWHM_TO_SIGMA = 1.0 / 2.355
+
+
+def stack(n_slices, H, W, dx, dy, thickness, R=None, origin=(0.0, 0.0, 0.0)):
+    R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+    return {"n_slices": int(n_slices), "H": int(H), "W": int(W), "dx": float(dx), "dy": float(dy),
+            "thickness": float(thickness), "R": R.astype(np.float64),
+            "origin": np.asarray(origin, np.float64),
+            "fwhm": np.array([1.2 * dx, 1.2 * dy, thickness], np.float64)}
+
+
+# Orthogonal stack orientations: columns = (slice x, slice y, normal).
+AXIAL = np.eye(3)
+CORONAL = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])   # normal = world y
+SAGITTAL = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])   # normal = world x
+
+
+def n_slices_total(stacks):
+    return int(sum(s["n_slices"] for s in stacks))
+
+
+def n_pixels_total(stacks):
+    return int(sum(s["n_slices"] * s["H"] * s["W"] for s in stacks))
+
+
+def random_gaussians(rng, N, lo=-16.0, hi=16.0, s_lo=0.5, s_hi=2.0):
+    """Means U(lo, hi)^3, per-axis scales log-uniform [s_lo, s_hi], unit quaternions
+    (normalised 4-D normal), amplitudes U(0, 1).  Returns the 11 N SoA vector."""
+    mu = rng.uniform(lo, hi, size=(3, N))
+    ls = rng.uniform(np.log(s_lo), np.log(s_hi), size=(3, N))
+    q = rng.normal(size=(4, N))
+    q /= np.linalg.norm(q, axis=0, keepdims=True)
+    c = rng.uniform(0.0, 1.0, size=(1, N))
+    return np.concatenate([mu, ls, q, c], axis=0).reshape(-1)
+
+
+def random_motion(rng, M, max_deg, max_mm):
+    """Per-slice motion (axis-angle r, translation tau): axis uniform on S^2,
+    angle U(-max_deg, max_deg), tau ~ U(-max_mm, max_mm)^3.  Shape (M, 6)."""
+    ax = rng.normal(size=(M, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    ang = np.deg2rad(rng.uniform(-max_deg, max_deg, size=(M, 1)))
+    tau = rng.uniform(-max_mm, max_mm, size=(M, 3))
+    return np.concatenate([ax * ang, tau], axis=1)
+
+
+def smooth_observations(rng, stacks, noise=0.01):
+    """A smooth field over (slice, row, col) plus Gaussian noise, for the tiny and
+    random cases (any values give a nonzero loss and gradient)."""
+    out = []
+    k0 = 0
+    for s in stacks:
+        n, H, W = s["n_slices"], s["H"], s["W"]
+        k = np.arange(n)[:, None, None] + k0
+        a = np.arange(H)[None, :, None]
+        b = np.arange(W)[None, None, :]
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        img = (0.45 + 0.2 * np.sin(0.31 * b + ph[0]) * np.cos(0.23 * a + ph[1])
+               + 0.1 * np.sin(0.7 * k + ph[2]))
+        out.append(img.reshape(-1))
+        k0 += n
+    I = np.concatenate(out)
+    return (I + rng.normal(0.0, noise, size=I.shape)).astype(np.float32)
+
+
+def tiny(seed=0):
+    """The tiny plain case: 2,000 Gaussians, 1 axial stack of 8 x 32 x 32 px at
+    1 x 1 mm, 3 mm thick (slice centres z = (k - 3.5) * 3), identity poses."""
+    rng = np.random.default_rng(seed)
+    N = 2000
+    theta_g = random_gaussians(rng, N)
+    stacks = [stack(8, 32, 32, 1.0, 1.0, 3.0)]
+    M = n_slices_total(stacks)
+    pose = np.zeros((M, 6))
+    I = smooth_observations(rng, stacks)
+    mask = np.ones(n_pixels_total(stacks), np.uint8)
+    theta = np.concatenate([theta_g, pose.reshape(-1)]).astype(np.float32)
+    return {"name": "tiny", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
+            "n_sample": int(mask.sum())}
+
+
+def random_case(seed, N, sizes, n_stacks=1, motion_deg=6.0, motion_mm=4.0, extent=None, s_lo=0.5, s_hi=2.0,
+                thickness=3.0, dx=1.0):
+    """Small random geometry: n_stacks stacks with random orientations (first
+    axial), each of the given (n_slices, H, W); random Gaussians spread over the
+    field of view; random per-slice motion; smooth observations."""
+    rng = np.random.default_rng(seed)
+    stacks = []
+    for k in range(n_stacks):
+        n, H, W = sizes[k % len(sizes)]
+        R = np.eye(3) if k == 0 else Rotation.random(random_state=int(rng.integers(1 << 31))).as_matrix()
+        origin = rng.uniform(-1.5, 1.5, 3)
+        stacks.append(stack(n, H, W, dx, dx, thickness, R, origin))
+    if extent is None:
+        extent = 0.45 * min(min(s["H"], s["W"]) * s["dx"] for s in stacks)
+    theta_g = random_gaussians(rng, N, -extent, extent, s_lo, s_hi)
+    M = n_slices_total(stacks)
+    pose = random_motion(rng, M, motion_deg, motion_mm)
+    I = smooth_observations(rng, stacks)
+    mask = np.ones(n_pixels_total(stacks), np.uint8)
+    theta = np.concatenate([theta_g, pose.reshape(-1)]).astype(np.float32)
+    return {"name": "random", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
+            "n_sample": int(mask.sum())}
+
+
+# --------------------------------------------------------------------------- phantom
+class BrainPhantom:
+    """Brain-like analytic phantom, intensities in [0, 1] (T2-like):
+    background 0, CSF shell 0.95 between the outer ellipsoid and the cortex,
+    folded cortex band 0.45 (2.5 mm thick), white matter 0.65, deep grey matter
+    0.55, two ventricles 0.95.  Edges are logistic with a 0.3 mm width.
+    Semi-axes (35, 28, 25) mm times ``scale``."""
+
+    def __init__(self, seed=0, scale=1.0):
+        rng = np.random.default_rng(seed + 7919)
+        self.axes = np.array([35.0, 28.0, 25.0]) * scale
+        self.scale = scale
+        self.ka = rng.integers(2, 7, size=8).astype(np.float64)
+        self.kb = rng.integers(1, 6, size=8).astype(np.float64)
+        self.ph = rng.uniform(0, 2 * np.pi, size=8)
+        self.width = 0.3
+        self.L = float(np.mean(self.axes))
+
+    @staticmethod
+    def _sig(z):
+        return 0.5 * (1.0 + np.tanh(0.5 * z))
+
+    def _ell(self, x, centre, axes):
+        p = (x - np.asarray(centre)) / np.asarray(axes)
+        rho = np.sqrt((p * p).sum(-1))
+        return self._sig((1.0 - rho) * float(np.min(axes)) / self.width)
+
+    def __call__(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        p = x / self.axes
+        rho = np.sqrt((p * p).sum(-1)) + 1e-12
+        th = np.arccos(np.clip(p[..., 2] / rho, -1.0, 1.0))
+        phi = np.arctan2(p[..., 1], p[..., 0])
+        fold = np.ones_like(rho)
+        for a, b, c in zip(self.ka, self.kb, self.ph):
+            fold += 0.03 * np.sin(a * th + c) * np.cos(b * phi)
+        rc_out = 0.93 * fold
+        rc_in = rc_out - 2.5 / self.L
+        k = self.L / self.width
+        m_out = self._sig((1.0 - rho) * k)
+        m_cx = self._sig((rc_out - rho) * k)
+        m_wm = self._sig((rc_in - rho) * k)
+        s = self.scale
+        m_gm = self._ell(x, (0.0, 0.0, -2.0 * s), (12.0 * s, 8.0 * s, 6.0 * s))
+        m_v = np.maximum(self._ell(x, (6.0 * s, 2.0 * s, 4.0 * s), (3.5 * s, 9.0 * s, 4.0 * s)),
+                         self._ell(x, (-6.0 * s, 2.0 * s, 4.0 * s), (3.5 * s, 9.0 * s, 4.0 * s)))
+        inner = 0.65 * (1 - m_gm) + 0.55 * m_gm
+        inner = inner * (1 - m_v) + 0.95 * m_v
+        cx = 0.45 * (1 - m_wm) + inner * m_wm
+        brain = 0.95 * (1 - m_cx) + cx * m_cx
+        return m_out * brain
+
+    def inside(self, x, dilate=0.0):
+        p = np.asarray(x) / (self.axes + dilate)
+        return (p * p).sum(-1) <= 1.0
+
+
+def _slice_frames_sim(stacks, motion):
+    """Simulator-side slice frames (its own geometry, written with scipy's
+    Rotation): R_i = Rot(r_i) R_stack, centre = Rot(r_i) c0_i + tau_i."""
+    Rs, ts = [], []
+    i = 0
+    for s in stacks:
+        n = s["n_slices"]
+        for k in range(n):
+            c0 = s["origin"] + (k - 0.5 * (n - 1)) * s["thickness"] * s["R"][:, 2]
+            Q = Rotation.from_rotvec(motion[i, :3]).as_matrix()
+            Rs.append(Q @ s["R"])
+            ts.append(Q @ c0 + motion[i, 3:])
+            i += 1
+    return np.array(Rs), np.array(ts)
+
+
+def _pixel_grid(s):
+    a = (np.arange(s["H"]) - 0.5 * (s["H"] - 1)) * s["dy"]
+    b = (np.arange(s["W"]) - 0.5 * (s["W"] - 1)) * s["dx"]
+    return a, b
+
+
+def simulate_phantom_stacks(phantom, stacks, motion, mask_dilate_mm=15.0, noise_frac=0.02, seed=0,
+                            nodes=(3, 3, 5)):
+    """Observed slices: the phantom integrated over each pixel's PSF (separable
+    Gauss-Hermite quadrature along the slice axes) at the moved pixel position,
+    then Rician noise sqrt((I + n1)^2 + n2^2), n ~ N(0, (noise_frac * max)^2).
+    Only pixels inside the nominal-geometry mask (phantom dilated by
+    mask_dilate_mm) are simulated; the others read 0.  Returns (I, mask)."""
+    rng = np.random.default_rng(seed + 104729)
+    Rm, tm = _slice_frames_sim(stacks, motion)
+    Rn, tn = _slice_frames_sim(stacks, np.zeros_like(motion))
+    gh = [np.polynomial.hermite_e.hermegauss(n) for n in nodes]
+    offs, wts = [], []
+    for i0, w0 in zip(*gh[0]):
+        for i1, w1 in zip(*gh[1]):
+            for i2, w2 in zip(*gh[2]):
+                offs.append((i0, i1, i2))
+                wts.append(w0 * w1 * w2)
+    offs = np.array(offs)
+    wts = np.array(wts) / np.sum(wts)
+    I_all, mask_all = [], []
+    i = 0
+    for s in stacks:
+        a, b = _pixel_grid(s)
+        A, B = np.meshgrid(a, b, indexing="ij")
+        u = np.stack([B.reshape(-1), A.reshape(-1), np.zeros(A.size)], axis=1)
+        sig = s["fwhm"] * FWHM_TO_SIGMA
+        for k in range(s["n_slices"]):
+            xn = u @ Rn[i].T + tn[i]
+            msk = phantom.inside(xn, mask_dilate_mm)
+            img = np.zeros(u.shape[0])
+            idx = np.nonzero(msk)[0]
+            for c0 in range(0, idx.size, 8192):
+                sel = idx[c0:c0 + 8192]
+                ul = u[sel][:, None, :] + offs[None, :, :] * sig[None, None, :]
+                xw = ul @ Rm[i].T + tm[i]
+                img[sel] = (phantom(xw) * wts[None, :]).sum(-1)
+            I_all.append(img)
+            mask_all.append(msk)
+            i += 1
+    I = np.concatenate(I_all)
+    mask = np.concatenate(mask_all).astype(np.uint8)
+    sd = noise_frac * max(1e-6, float(I.max()))
+    n1 = rng.normal(0.0, sd, I.shape)
+    n2 = rng.normal(0.0, sd, I.shape)
+    I = np.sqrt((I + n1) ** 2 + n2 ** 2) * mask
+    return I.astype(np.float32), mask
+
+
+def grid_gaussians(phantom, h=0.8, s=0.8):
+    """Gaussians on an h-mm grid inside the phantom's outer ellipsoid, isotropic
+    scale s, identity quaternion, amplitude phantom(mu) h^3 / ((2 pi)^(3/2) s^3)
+    (so that their sum approximates the phantom)."""
+    ext = phantom.axes
+    axes = [np.arange(-e + 0.5 * h, e, h) for e in ext]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
+    P = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], 1)
+    P = P[phantom.inside(P)]
+    N = P.shape[0]
+    c = phantom(P) * h ** 3 / ((2 * np.pi) ** 1.5 * s ** 3)
+    ls = np.full((3, N), np.log(s))
+    q = np.zeros((4, N))
+    q[0] = 1.0
+    return np.concatenate([P.T, ls, q, c[None, :]], axis=0).reshape(-1), N
+
+
+def fetal(seed=0, with_truth=False):
+    """The fetal-scale plain case: ~200k Gaussians on a 0.8 mm grid inside the
+    brain phantom; axial / coronal / sagittal stacks of 40 x 192 x 192 px at
+    1 x 1 x 3.5 mm centred on the origin; per-slice motion U(+-5 deg) axis
+    uniform on the sphere, U(+-3 mm); Rician noise 2 %; pixel mask = brain
+    dilated by 15 mm; 2^18 pixels sampled per iteration.  Poses start at 0
+    (the unknown motion is what the optimisation recovers)."""
+    rng = np.random.default_rng(seed)
+    ph = BrainPhantom(seed)
+    stacks = [stack(40, 192, 192, 1.0, 1.0, 3.5, R) for R in (AXIAL, CORONAL, SAGITTAL)]
+    M = n_slices_total(stacks)
+    motion = random_motion(rng, M, 5.0, 3.0)
+    I, mask = simulate_phantom_stacks(ph, stacks, motion, seed=seed)
+    theta_g, N = grid_gaussians(ph)
+    theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
+    out = {"name": "fetal", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
+           "n_sample": 1 << 18}
+    if with_truth:
+        out["motion"] = motion
+        out["phantom"] = ph
+    return out
