@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: one optimisation step of the analytic-PSF Gaussian slice model.
+
+A step = sample 2^18 masked pixels on the device, forward (Gaussian and slice
+preprocessing, Mahalanobis cut, (tile, record) keys, radix sort, tile
+evaluation with the fused MSE loss), backward (tile adjoint, gradient
+epilogue) and the fused Adam update, on the fetal-scale synthetic workload
+(~200k Gaussians, 3 orthogonal stacks of 40 x 192 x 192 px at 1 x 1 x 3.5 mm).
+
+Prints one JSON line.  `value` counts (pixel, Gaussian) pairs inside the
+1e-7 cut (the pairs the method needs) per second of whole-step device time;
+`px_per_s` counts sampled slice pixels.  `e2e` is the same metric through the
+host-buffer C-ABI call (gsvr_step_host: parameters and pixel list uploaded
+from pinned memory, gradient and loss read back every step).
+
+--impl reference times the FP64 brute-force CPU oracle on bounded pixel
+samples of the same workload (the oracle is this project's reference program).
+Multi-GPU (torchrun): every rank reconstructs its own subject (weak scaling,
+no data-path collective); rank 0 prints the aggregate.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Gaussian-pixel pairs/s & slice px/s; sec to fixed PSNR vs plain, 1 B300"
+UNIT = "pairs/s"
+# Issue slots per evaluated pair in the tile kernels (FP32 + MUFU instructions of the
+# centred 2D conic form): forward 8 + 1, backward 16 + 1.
+ISSUE_PER_PAIR = {"fwd_eval": 9.0, "bwd_eval": 17.0}
+THREAD_INSTR_PER_CLK_PER_SM = 128.0  # 4 schedulers x 32 lanes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fetal", choices=["fetal", "tiny"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    from paper_2512_11624_b300 import inputs
+    if name == "fetal":
+        case = inputs.fetal(seed)
+        desc = ("fetal: %d Gaussians (0.8 mm grid in a brain phantom), 3 orthogonal stacks of 40 x 192 x 192 px "
+                "at 1 x 1 x 3.5 mm, motion U(+-5 deg)/U(+-3 mm), 2^18 sampled px/step, Adam" % case["N"])
+    else:
+        case = inputs.tiny(seed)
+        desc = "tiny: 2000 Gaussians, 1 stack of 8 x 32 x 32 px, all pixels, Adam"
+    return case, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_id=None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id is not None:
+            cmd += ["-i", str(gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2512_11624_b300", "csrc", "gsvr_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel, workload_name):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha()
+    for line in open(path):
+        p = line.split()
+        if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload_name and p[2] == sha:
+            return float(p[3])
+    return None
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if __import__("torch").cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_sample(case, pix, n_sample_total):
+    """FP64 oracle fwd+bwd (every Gaussian, gradients of all parameters) on the
+    listed pixels; returns (seconds, useful pairs in them, threads)."""
+    from oracle import oracle
+    th = case["theta"].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.forward_backward(case["stacks"], th, case["N"], pix, case["I"].astype(np.float64)[pix],
+                            1.0 / n_sample_total, want_abs=False)
+    dt = time.perf_counter() - t0
+    useful = oracle.count_pairs(case["stacks"], th, case["N"], pix)
+    return dt, useful, oracle.num_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    case, desc = workload(args.workload, 0)
+    from oracle import oracle
+    rng = np.random.default_rng(0)
+    masked = np.nonzero(case["mask"])[0]
+    n_s = min(case["n_sample"], masked.size)
+    # per-step pixel count so that warmup + steps fit in ~150 s
+    probe = rng.choice(masked, 8, replace=False)
+    t_probe, _, _ = cpu_oracle_sample(case, probe, n_s)
+    per_px = max(t_probe / 8, 1e-6)
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    n_px = int(max(2, min(4096, budget / per_px)))
+    times, useful = [], 0
+    for k in range(args.warmup + args.steps):
+        pix = rng.choice(masked, n_px, replace=False)
+        dt, u, cores = cpu_oracle_sample(case, pix, n_s)
+        if k >= args.warmup:
+            times.append(dt)
+            useful += u
+    tot = sum(times)
+    value = useful / tot
+    px_s = n_px * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
+            "px_per_s": px_s,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d random masked pixels per step x every Gaussian, fwd+bwd, float64" % n_px},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    from paper_2512_11624_b300 import gsvr
+    torch.cuda.set_device(local)
+    dev = local
+    stream = torch.cuda.Stream(device=dev)
+    th_, tw_ = (int(v) for v in args.tile.split("x"))
+    case, desc = workload(args.workload, rank)
+    n_s = min(case["n_sample"], int(case["mask"].sum()))
+    sampled = args.workload == "fetal"
+
+    # capacities from one probe forward, then a fixed-capacity context (no host sync per step)
+    probe = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=th_, tile_w=tw_)
+    if sampled:
+        gsvr.gsvr_sample_pixels(probe.ctx, n_s, 0)
+    probe.forward()
+    st0 = probe.stats()
+    probe.close()
+    ctx = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=th_, tile_w=tw_, fixed_capacity=1,
+                       cap_records=int(st0["n_records"] * 1.5) + 4096, cap_keys=int(st0["n_keys"] * 1.5) + 4096,
+                       timing=1, seed=1234 + rank)
+    M = ctx.M
+    gsvr.gsvr_set_frozen(ctx.ctx, np.array([1 if i == M // 6 else 0 for i in range(M)], np.uint8))
+
+    def step(k):
+        if sampled:
+            gsvr.gsvr_sample_pixels(ctx.ctx, n_s, k)
+        gsvr.gsvr_forward(ctx.ctx)
+        gsvr.gsvr_backward(ctx.ctx)
+        gsvr.gsvr_adam_step(ctx.ctx, k + 1)
+
+    for k in range(args.warmup):
+        step(k)
+    gsvr.gsvr_sync_status(ctx.ctx)
+    gsvr.gsvr_timing_reset(ctx.ctx)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    gsvr.gsvr_sync_status(ctx.ctx)
+    kt = gsvr.gsvr_get_kernel_times(ctx.ctx)
+    ms_max = reduce_max(ms, ws)
+
+    # pairs inside the cut: counted on 3 further steps' samples (outside the timed region)
+    u_sum = e_sum = 0
+    for k in range(3):
+        if sampled:
+            gsvr.gsvr_sample_pixels(ctx.ctx, n_s, args.warmup + args.steps + k)
+        gsvr.gsvr_forward(ctx.ctx)
+        u, e = gsvr.gsvr_count_pairs(ctx.ctx)
+        u_sum += u
+        e_sum += e
+    useful_frac = u_sum / max(e_sum, 1)
+    eval_per_step = kt["pairs_evaluated"] / args.steps
+    useful_per_step = useful_frac * eval_per_step
+    useful_total = reduce_sum(useful_per_step * args.steps, ws)
+    px_total = reduce_sum(float(n_s) * args.steps, ws)
+    value = useful_total / (ms_max / 1e3)
+
+    # roofline of the dominant tile kernel (FP32/MUFU issue bound)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0
+    dom = max(("fwd_eval", "bwd_eval"), key=lambda s: kt["ms"][s])
+    avg_ms = kt["ms"][dom] / max(kt["calls"][dom], 1)
+    pairs_per_launch = eval_per_step
+    achieved = pairs_per_launch / (avg_ms / 1e3) / 1e9
+    peak = n_sm * f_mhz * 1e6 * THREAD_INSTR_PER_CLK_PER_SM / ISSUE_PER_PAIR[dom] / 1e9
+    traffic = profiled_traffic({"fwd_eval": "k_forward", "bwd_eval": "k_backward"}[dom], args.workload)
+    roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_forward", "bwd_eval": "k_backward"}[dom],
+                "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_basis": "%d SMs x %.0f MHz (median sampled) x 128 issue slots/clk / %.0f slots per pair" %
+                              (n_sm, f_mhz, ISSUE_PER_PAIR[dom])}
+
+    # end to end through the host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        rng = np.random.default_rng(99 + rank)
+        masked = np.nonzero(case["mask"])[0].astype(np.int32)
+        ke = max(3, min(args.steps, 20))
+        lists = [np.sort(rng.choice(masked, n_s, replace=False)).astype(np.int32) for _ in range(ke + 2)]
+        theta_h = torch.from_numpy(case["theta"].astype(np.float32)).pin_memory()
+        grad_h = torch.empty_like(theta_h).pin_memory()
+        loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+        idx_h = [torch.from_numpy(l).pin_memory() for l in lists]
+        for k in range(2):
+            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[k], grad_h, loss_h)
+        gsvr.gsvr_timing_reset(ctx.ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ke):
+            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[2 + k], grad_h, loss_h)
+        dt = time.perf_counter() - t0
+        kt2 = gsvr.gsvr_get_kernel_times(ctx.ctx)
+        dt = reduce_max(dt, ws)
+        e2e_useful = reduce_sum(useful_frac * kt2["pairs_evaluated"], ws)
+        e2e = {"value": e2e_useful / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(theta_h.numel() * 4 + n_s * 4),
+               "d2h_bytes_per_step": int(grad_h.numel() * 4 + 8), "steps": ke}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = gsvr.gsvr_get_sample(ctx.ctx)
+        rng = np.random.default_rng(7)
+        pix = rng.choice(sample, 16, replace=False)
+        t1, _, _ = cpu_oracle_sample(case, pix, n_s)
+        n_px = int(max(16, min(8192, 16 * args.cpu_seconds / max(t1, 1e-3))))
+        pix = rng.choice(sample, min(n_px, sample.size), replace=False)
+        t_cpu, u_cpu, cores = cpu_oracle_sample(case, pix, n_s)
+        cpu = {"value": u_cpu / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "px_per_s": len(pix) / t_cpu,
+               "sample": "%d sampled pixels of one step x all %d Gaussians, fwd+bwd (all gradients), float64, "
+                         "%.1f s" % (len(pix), case["N"], t_cpu)}
+
+    if rank == 0:
+        stats = ctx.stats()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": desc, "tile": args.tile, "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (records + keys + tile records ~%.0f MB per step)" %
+                                 ((stats["n_records"] * 44 + stats["n_keys"] * 108) / 1e6)},
+                "px_per_s": px_total / (ms_max / 1e3),
+                "evaluated_pairs_per_s": eval_per_step * args.steps * ws / (ms_max / 1e3),
+                "useful_fraction": useful_frac,
+                "stage_ms_per_step": {k: v / args.steps for k, v in kt["ms"].items()},
+                "records_per_step": stats["n_records"], "keys_per_step": stats["n_keys"],
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": kt["kernel_launches"], "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * gsvr.h -- C ABI of libgsvr.so: the analytic-PSF slice forward model over
+ * anisotropic 3D Gaussians, its adjoint and the Adam step, on one B300 GPU.
+ *
+ * Method (paper "Fast and Explicit: Slice-to-Volume Reconstruction via 3D
+ * Gaussian Primitives with Analytic PSF Modeling"):
+ *  - Sec. 3.1, Eq. 1 / Eq. 3: a slice pixel u of slice i is the volume
+ *    convolved with the slice-oriented PSF, read at x = T_i(u) = R_i u + t_i.
+ *  - Sec. 3.2: the volume is a sum of N Gaussians, 11 parameters each
+ *    (mean mu, log-space scales ls, quaternion q = (w,x,y,z), amplitude c),
+ *    Sigma_j = R(q) diag(exp(2 ls)) R(q)^T.
+ *  - Sec. 3.3, Eq. 4: Sigma_obs = Sigma_j + R_i Sigma_PSF R_i^T, Sigma_PSF
+ *    diagonal in slice coordinates; Eq. 5 (numerator): the pixel receives
+ *    c_j f exp(-1/2 v^T Sigma_obs^-1 v), v = x - mu_j, with
+ *    f = sqrt(det Sigma_j / det Sigma_obs) (the exact convolution of a
+ *    unit-mass PSF; GSVR_NORM_EXACT) or f = 1 (GSVR_NORM_LITERAL).
+ *  - Sec. 3.4: per slice a rigid motion (axis-angle r, translation tau) that
+ *    moves the slice and rotates its PSF: R_i = Rod(r) R0_i,
+ *    t_i = Rod(r) c0_i + tau, (R0_i, c0_i) the slice's nominal frame.
+ *  - Loss: L = sum_p w_p (I_hat_p - I_p)^2, w_p = 1 / |sampled pixels|.
+ *  - Optimisation Details (appendix): Adam, per-group learning rates
+ *    (mu, s: 2.5e-2; q, c: 1e-2; rotation 2.5e-3; translation 1e-1).
+ *
+ * Conventions shared by every call:
+ *  - Units: millimetres and radians.  float32 data unless stated.
+ *  - Every call is asynchronous on the context's CUDA stream unless it says
+ *    it synchronises; pointers passed in are only read during the call (data
+ *    is copied), so the caller may reuse them when the call returns (host
+ *    pointers) or after the stream reaches the call (device pointers).
+ *  - `mem` arguments say where a pointer lives: GSVR_MEM_HOST (pageable or
+ *    pinned host memory) or GSVR_MEM_DEVICE (memory of the context's device).
+ *  - Every call returns a gsvr_status.  Argument errors return immediately
+ *    with GSVR_ERR_INVALID_ARG and change nothing.  Errors found on the device
+ *    (capacity overflow in fixed-capacity mode, non-finite values, a wait
+ *    that ran out) are latched in a device status word and returned by
+ *    gsvr_sync_status().  gsvr_last_error() describes the last failure.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Parameter vector theta (component-major structure of arrays), N Gaussians,
+ * M slices (slices ordered stack by stack, slice index k within a stack):
+ *   [0,N) mu_x [N,2N) mu_y [2N,3N) mu_z [3N,6N) ls_0..2 [6N,10N) q_w,q_x,q_y,q_z
+ *   [10N,11N) c   then 6 floats per slice i at 11N + 6i: r_0..2, tau_0..2.
+ * Pixels: global index = (first pixel of slice i) + row * W + col, slices in
+ * the order above; pixel (row, col) sits at slice-local
+ * u = ((col - (W-1)/2) dx, (row - (H-1)/2) dy, 0).
+ */
+#ifndef GSVR_H
+#define GSVR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSVR_ABI_VERSION 1
+
+typedef struct gsvr_ctx gsvr_ctx; /* opaque; owns all of its device buffers */
+
+typedef enum gsvr_status {
+    GSVR_OK = 0,
+    GSVR_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or value */
+    GSVR_ERR_CUDA = 2,        /* a CUDA runtime call failed (see gsvr_last_error) */
+    GSVR_ERR_CAPACITY = 3,    /* fixed-capacity buffers overflowed; results of that call are invalid */
+    GSVR_ERR_NONFINITE = 4,   /* a parameter, observation or the loss is not finite */
+    GSVR_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    GSVR_ERR_STATE = 6,       /* call out of order (e.g. backward before forward) */
+    GSVR_ERR_NOMEM = 7        /* device allocation failed */
+} gsvr_status;
+
+enum { GSVR_MEM_HOST = 0, GSVR_MEM_DEVICE = 1 };
+enum { GSVR_NORM_EXACT = 0, GSVR_NORM_LITERAL = 1 };
+
+/* One stack of parallel, contiguous slices (no gap), Sec. 3.1 / Sec. 4.
+ * Slice k (0-based) of n is centred at origin + (k - (n-1)/2) * thickness * n_hat,
+ * n_hat = third column of R.  Sigma_PSF = diag((fwhm / 2.355)^2) in slice axes. */
+typedef struct gsvr_stack_desc {
+    int32_t n_slices, H, W, reserved;
+    float dx, dy, thickness;  /* pixel spacing along slice x (columns), y (rows); slice thickness */
+    float R[9];               /* row-major 3x3; columns = slice x, slice y, slice normal in world */
+    float origin[3];          /* world position of the stack centre */
+    float fwhm[3];            /* PSF full width at half maximum along slice x, y, normal */
+} gsvr_stack_desc;
+
+typedef struct gsvr_config {
+    float cutoff_rel;       /* drop a (pixel, Gaussian) pair when exp(-1/2 v^T Sigma_obs^-1 v) < cutoff_rel;
+                               0 -> 1e-7 (truncated mass below 1e-7 of the amplitude) */
+    int32_t tile_h, tile_w; /* pixel tile shape used for binning; 0 -> 16 x 16; each in [4, 32] */
+    int32_t norm_mode;      /* GSVR_NORM_EXACT (default) or GSVR_NORM_LITERAL */
+    int32_t fixed_capacity; /* 0: the library grows its buffers as needed (reads two counts back
+                               per forward, synchronising the stream); 1: buffers keep the
+                               capacities below, nothing synchronises, overflow -> GSVR_ERR_CAPACITY */
+    int32_t timing;         /* 1: record CUDA events around each stage (see gsvr_get_kernel_times) */
+    int64_t cap_records;    /* initial / fixed capacity of (slice, Gaussian) records; 0 -> auto */
+    int64_t cap_keys;       /* initial / fixed capacity of (tile, record) keys; 0 -> auto */
+    uint64_t seed;          /* seed of the device pixel sampler */
+} gsvr_config;
+
+typedef struct gsvr_adam_cfg {
+    float lr_mu, lr_ls, lr_q, lr_c, lr_rot, lr_trans; /* per-group learning rates */
+    float beta1, beta2, eps;                          /* 0 -> 0.9, 0.999, 1e-8 */
+    int32_t reserved;
+} gsvr_adam_cfg;
+
+/* Device views of context-owned buffers (valid until the next gsvr_set_* call that
+ * resizes them, or gsvr_destroy).  The caller may read and write them on the
+ * context's stream. */
+typedef struct gsvr_views {
+    float *theta;    /* 11N + 6M parameter vector */
+    float *grad;     /* dL/dtheta, same layout (written by gsvr_backward) */
+    float *adam_m;   /* Adam first moments, same layout */
+    float *adam_v;   /* Adam second moments, same layout */
+    float *pred;     /* I_hat per global pixel; only the sampled pixels are written */
+    float *rbar;     /* dL/dI_hat per global pixel; only the sampled pixels are written */
+    double *loss;    /* scalar loss of the last forward */
+    int64_t n_gauss, n_slices, n_pixels, n_params;
+} gsvr_views;
+
+/* Counters of the last forward (synchronises the stream). */
+typedef struct gsvr_stats {
+    int64_t n_sampled;       /* pixels in the current sample */
+    int64_t n_records;       /* (slice, Gaussian) pairs that survived the Mahalanobis cut */
+    int64_t n_keys;          /* (tile, record) keys sorted */
+    int64_t pairs_evaluated; /* (pixel, Gaussian) pairs the evaluation kernels visit, each pass */
+    int64_t n_tiles;         /* pixel tiles in all slices */
+    int64_t tile_px_max;     /* pixels per tile (tile_h * tile_w) */
+    int64_t cap_records, cap_keys;
+} gsvr_stats;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `cfg` may be NULL for
+ * defaults.  *out receives the context.  Synchronous. */
+gsvr_status gsvr_create(gsvr_ctx **out, int device, void *cuda_stream, const gsvr_config *cfg);
+
+/* Release every buffer of the context (synchronises its stream first). */
+gsvr_status gsvr_destroy(gsvr_ctx *ctx);
+
+/* Acquisition geometry (Sec. 3.1, Sec. 4): n_stacks stack descriptions in host
+ * memory.  Defines M (slices) and the pixel count; invalidates observations,
+ * poses and the sample.  Synchronous. */
+gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_desc *stacks);
+
+/* Observed slice intensities I (float32, one per global pixel) and the pixel
+ * mask (uint8, nonzero = usable), both `mem`.  mask may be NULL (all usable).
+ * Requires gsvr_set_stacks.  Makes the sample "every masked pixel". */
+gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *mask, int32_t mem);
+
+/* The N Gaussians (Sec. 3.2): theta_g = the first 11N entries of the
+ * parameter vector, `mem`.  Resets the Adam moments of the Gaussians. */
+gsvr_status gsvr_set_gaussians(gsvr_ctx *ctx, int64_t N, const float *theta_g, int32_t mem);
+
+/* The M slice motions (Sec. 3.4): pose[6i + 0..2] = axis-angle r,
+ * pose[6i + 3..5] = translation tau, `mem`.  Resets the pose Adam moments. */
+gsvr_status gsvr_set_poses(gsvr_ctx *ctx, const float *pose, int32_t mem);
+
+/* Mark slices whose pose the optimiser must not move (gauge fixing: a joint
+ * rigid motion of volume and slices leaves L unchanged).  frozen: M bytes,
+ * host memory; NULL clears. */
+gsvr_status gsvr_set_frozen(gsvr_ctx *ctx, const uint8_t *frozen);
+
+/* Sample = the listed global pixels (int32, `mem`, any order; duplicates count
+ * once; unmasked pixels are dropped).  n < 0: every masked pixel.
+ * w_p = 1 / (number of distinct usable pixels listed). */
+gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, int32_t mem);
+
+/* Sample n masked pixels uniformly without replacement on the device: the
+ * first n values of a keyed random permutation of the masked pixels (SplitMix64
+ * round keys from (seed, step), a 4-round multiply/xor-shift bijection on
+ * ceil(log2(#masked)) bits, cycle walking).  n must not exceed #masked. */
+gsvr_status gsvr_sample_pixels(gsvr_ctx *ctx, int64_t n, uint64_t step);
+
+/* Forward pass (Eq. 4, Eq. 5 numerator with the normalisation of norm_mode,
+ * MSE loss) over the current sample: per-Gaussian and per-slice preprocessing,
+ * Mahalanobis cut of every (slice, Gaussian) pair at cutoff_rel, (tile, record)
+ * key emission and radix sort, fused tile evaluation.  Writes pred, rbar and
+ * loss (see gsvr_views).  In growing mode this synchronises twice to size
+ * buffers. */
+gsvr_status gsvr_forward(gsvr_ctx *ctx);
+
+/* Adjoint of the last forward: dL/dtheta for every Gaussian parameter and
+ * every slice pose, recomputing each pair from the sorted tile lists (nothing
+ * per pair is stored by the forward).  Requires a forward since the last
+ * change of parameters, sample or observations. */
+gsvr_status gsvr_backward(gsvr_ctx *ctx);
+
+/* One Adam step (bias-corrected, no weight decay) on theta with the last
+ * gradient; `step` is the 1-based step count used for bias correction. */
+gsvr_status gsvr_adam_step(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step);
+
+/* End to end from host buffers: copy theta (11N + 6M floats, host) and the
+ * pixel sample (n int32 global indices, host; n < 0 = every masked pixel) to
+ * the device, run forward and backward, copy dL/dtheta (host, 11N + 6M floats)
+ * and the loss (host double) back.  Synchronises.  grad_out or loss_out may be
+ * NULL. */
+gsvr_status gsvr_step_host(gsvr_ctx *ctx, const float *theta, const int32_t *idx, int64_t n, float *grad_out,
+                           double *loss_out);
+
+/* Copy the current sample (global pixel indices, in the library's tile order)
+ * to host memory `out` of `cap` int32 entries; *n_out receives the sample size
+ * (entries beyond cap are not written).  Synchronises. */
+gsvr_status gsvr_get_sample(gsvr_ctx *ctx, int32_t *out, int64_t cap, int64_t *n_out);
+
+gsvr_status gsvr_get_views(gsvr_ctx *ctx, gsvr_views *out);
+gsvr_status gsvr_get_stats(gsvr_ctx *ctx, gsvr_stats *out);
+
+/* Stages timed when gsvr_config.timing = 1. */
+enum {
+    GSVR_STAGE_SAMPLE = 0,   /* device pixel sampler and tile ranges */
+    GSVR_STAGE_PREP = 1,     /* Gaussian covariances and slice frames */
+    GSVR_STAGE_BIN = 2,      /* Mahalanobis cut, records, keys, radix sort, tile ranges, gather */
+    GSVR_STAGE_FWD_EVAL = 3, /* forward tile evaluation kernel */
+    GSVR_STAGE_BWD_EVAL = 4, /* backward tile evaluation kernel */
+    GSVR_STAGE_GRAD = 5,     /* per-Gaussian and per-slice gradient epilogue */
+    GSVR_STAGE_ADAM = 6,     /* fused Adam */
+    GSVR_N_STAGES = 8
+};
+
+typedef struct gsvr_kernel_times {
+    double ms[GSVR_N_STAGES];     /* device time per stage since gsvr_timing_reset (CUDA events
+                                     on the context stream) */
+    int64_t calls[GSVR_N_STAGES]; /* executions of each stage */
+    int64_t pairs_evaluated;      /* pixel x record pairs the forward visited since the reset */
+    int64_t kernel_launches;      /* kernels this library launched since the reset (all contexts) */
+} gsvr_kernel_times;
+
+/* Clear the stage timers and counters. */
+gsvr_status gsvr_timing_reset(gsvr_ctx *ctx);
+
+/* Read the stage timers (synchronises). */
+gsvr_status gsvr_get_kernel_times(gsvr_ctx *ctx, gsvr_kernel_times *out);
+
+/* Diagnostic pass over the current forward's tile lists (synchronises):
+ * *useful = (pixel, Gaussian) pairs with exp(-1/2 v^T Sigma_obs^-1 v) >= cutoff_rel,
+ * *evaluated = pairs the evaluation kernels visit.  Requires a current forward. */
+gsvr_status gsvr_count_pairs(gsvr_ctx *ctx, int64_t *useful, int64_t *evaluated);
+
+/* Synchronise the stream; return and clear the device status word
+ * (GSVR_OK, GSVR_ERR_CAPACITY, GSVR_ERR_NONFINITE or GSVR_ERR_TIMEOUT). */
+gsvr_status gsvr_sync_status(gsvr_ctx *ctx);
+
+/* Text of the last error of this context (static storage owned by ctx);
+ * ctx NULL gives the last error of gsvr_create. */
+const char *gsvr_last_error(gsvr_ctx *ctx);
+
+/* ABI version (GSVR_ABI_VERSION of the built library). */
+int32_t gsvr_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSVR_H */

@@ -367,6 +367,28 @@ int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *th
     return 0;
 }
 
+/* Number of (listed pixel, Gaussian) pairs with exp(-1/2 v^T Sigma_obs^-1 v) >= cutoff
+ * (the pairs a per-pair truncation at `cutoff` keeps; Eq. 4 / Eq. 5 exponent). */
+int64_t oracle_count_pairs(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
+                           const int64_t *pix, double cutoff) {
+    or_model m;
+    if (model_setup(n_stacks, st, N, theta, &m)) return -1;
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : total)
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t i;
+        double u[3], x[3];
+        pixel_world(&m, pix[p], &i, u, x);
+        for (int64_t j = 0; j < N; ++j) {
+            or_pair pr;
+            eval_pair(&m.g[j], &m.fr[i], x, 0, &pr);
+            total += pr.e >= cutoff ? 1 : 0;
+        }
+    }
+    model_free(&m);
+    return total;
+}
+
 /* Chain of a symmetric covariance gradient G (dL = tr(G dSigma)) through
  * Sigma = R diag(s^2) R^T, s = exp(ls), R = R(q/|q|): d ls (3) and d q (4). */
 static void cov_chain(const or_gauss *g, const double *G, double *dls, double *dq) {

@@ -54,6 +54,8 @@ def lib():
         _lib.oracle_splitmix64.restype = C.c_uint64
         _lib.oracle_sample_positions.argtypes = [i64, i64, C.c_uint64, C.c_uint64, vp]
         _lib.oracle_num_threads.restype = C.c_int
+        _lib.oracle_count_pairs.argtypes = [C.c_int, vp, i64, vp, i64, vp, d]
+        _lib.oracle_count_pairs.restype = i64
     return _lib
 
 
@@ -126,6 +128,17 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None,
     if rc != 0:
         raise RuntimeError("oracle_forward_backward failed")
     return pred, float(loss[0]), grad, absg
+
+
+def count_pairs(stacks, theta, N, pix, cutoff=1e-7):
+    """Pairs (listed pixel, Gaussian) whose exponent factor is at least `cutoff`."""
+    st = _stacks(stacks)
+    th = _f64(theta)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    n = lib().oracle_count_pairs(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), float(cutoff))
+    if n < 0:
+        raise RuntimeError("oracle_count_pairs failed")
+    return int(n)
 
 
 def adam(N, M, theta, grad, m, v, lr, beta1, beta2, eps, t, frozen=None):

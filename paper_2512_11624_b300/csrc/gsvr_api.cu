@@ -1,0 +1,1018 @@
+// gsvr_api.cu -- the C ABI of libgsvr.so (declared in include/gsvr.h): context,
+// device store (structure-of-arrays parameters, slice frames, pixel tiles),
+// buffer management and the per-call orchestration of the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gsvr_launch.cuh"
+
+using namespace gsvr;
+
+namespace {
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // Make room for `want` elements; contents are not kept.
+    cudaError_t ensure(size_t want) {
+        if (want <= n && p) return cudaSuccess;
+        release();
+        size_t bytes = std::max<size_t>(want, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = std::max<size_t>(want, 1);
+        return cudaSuccess;
+    }
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct gsvr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    gsvr_config cfg{};
+    std::string err;
+    float rc2 = 0.f;
+    int tile_w = 16, tile_h = 16;
+
+    // geometry
+    int n_stacks = 0, M = 0, n_tiles = 0, sort_bits = 1;
+    int64_t P = 0;
+    std::vector<SliceDev> h_slices;
+    std::vector<SliceStatic> h_static;
+    DBuf<SliceDev> d_slices;
+    DBuf<SliceStatic> d_static;
+    DBuf<int> d_tile_slice, d_pix_tile, d_pix_tpos, d_tile_sorted_pix;
+    std::vector<int> h_tile_sorted_pix;
+
+    // observations
+    DBuf<float> d_I;
+    DBuf<uint8_t> d_mask;
+    DBuf<int> d_mask_tpos, d_mask_pix_sorted;
+    int n_mask = 0;
+
+    // parameters
+    int64_t N = 0;
+    DBuf<float> d_theta, d_grad, d_m, d_v;
+    DBuf<float4> d_gpre;
+    DBuf<uint8_t> d_frozen;
+    bool any_frozen = false;
+
+    // sample
+    DBuf<int> d_flags, d_flag_pos, d_sampled, d_tile_px_start, d_tile_px_end, d_idx;
+
+    // binning
+    DBuf<int> d_rec_cnt, d_rec_off, d_rec_nkeys, d_key_off, d_key_rec, d_tile_rec_start, d_tile_rec_end;
+    DBuf<Rec> d_rec, d_trec;
+    DBuf<int2> d_rec_tiles;
+    DBuf<uint32_t> d_keys, d_keys_sorted, d_vals_sorted, d_keys_alt, d_vals_alt;
+    DBuf<int> d_hist, d_scan_bsum;
+    DBuf<float4> d_mom;
+    int cap_rec = 0, cap_keys = 0;
+    int last_n_rec = 0, last_n_keys = 0;
+
+    // outputs
+    DBuf<float> d_pred, d_rbar;
+    DBuf<double> d_tile_loss, d_loss, d_pose_acc;
+    DBuf<unsigned> d_status;
+    DBuf<Counters> d_counters;
+
+    bool have_stacks = false, have_obs = false, have_gauss = false, have_sample = false, fwd_valid = false;
+
+    // stage timing (cfg.timing)
+    struct Mark {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Mark> marks;
+    cudaEvent_t open_ev[GSVR_N_STAGES] = {};
+    double ms[GSVR_N_STAGES] = {};
+    int64_t calls[GSVR_N_STAGES] = {};
+    long long launches_at_reset = 0;
+    DBuf<unsigned long long> d_pairs_total, d_useful;
+
+    ~gsvr_ctx() {
+        for (auto &m : marks) {
+            cudaEventDestroy(m.a);
+            cudaEventDestroy(m.b);
+        }
+        for (auto e : ev_pool) cudaEventDestroy(e);
+        for (auto e : open_ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+gsvr_status fail(gsvr_ctx *c, gsvr_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) {                                                                          \
+            cudaGetLastError();                                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? GSVR_ERR_NOMEM : GSVR_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+        }                                                                                                 \
+    } while (0)
+
+bool finite_all(const float *v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
+// out(seed, ctr) = mix(seed + (ctr + 1) * golden gamma).
+uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
+    uint64_t z = seed + (ctr + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+size_t scan_scratch_blocks(gsvr_ctx *ctx) {
+    size_t n = std::max<size_t>({(size_t)ctx->N + 1, (size_t)ctx->P + 1, (size_t)ctx->cap_rec + 1,
+                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_keys) + 1});
+    return (n + kScanTile - 1) / kScanTile + 2;
+}
+
+cudaError_t ensure_scan_scratch(gsvr_ctx *ctx) { return ctx->d_scan_bsum.ensure(scan_scratch_blocks(ctx) + 1); }
+
+ScanScratch scan_scratch(gsvr_ctx *ctx) { return ScanScratch{ctx->d_scan_bsum.p, (int)ctx->d_scan_bsum.n - 1}; }
+
+gsvr_status ensure_rec_capacity(gsvr_ctx *ctx, int64_t want) {
+    if (want <= ctx->cap_rec && ctx->d_rec.p) return GSVR_OK;
+    if (want > (int64_t)INT32_MAX - 16) return fail(ctx, GSVR_ERR_CAPACITY, "record count exceeds int32 range");
+    const int cap = (int)std::min<int64_t>((int64_t)INT32_MAX - 16, std::max<int64_t>(want, 1024));
+    CK(ctx->d_rec.ensure(cap));
+    CK(ctx->d_rec_tiles.ensure(cap));
+    CK(ctx->d_rec_nkeys.ensure(cap));
+    CK(ctx->d_key_off.ensure((size_t)cap + 1));
+    ctx->cap_rec = cap;
+    CK(ensure_scan_scratch(ctx));
+    return GSVR_OK;
+}
+
+gsvr_status ensure_key_capacity(gsvr_ctx *ctx, int64_t want) {
+    if (want <= ctx->cap_keys && ctx->d_keys.p) return GSVR_OK;
+    if (want > (int64_t)INT32_MAX - 16) return fail(ctx, GSVR_ERR_CAPACITY, "key count exceeds int32 range");
+    const int cap = (int)std::min<int64_t>((int64_t)INT32_MAX - 16, std::max<int64_t>(want, 4096));
+    CK(ctx->d_keys.ensure(cap));
+    CK(ctx->d_key_rec.ensure(cap));
+    CK(ctx->d_keys_sorted.ensure(cap));
+    CK(ctx->d_vals_sorted.ensure(cap));
+    CK(ctx->d_keys_alt.ensure(cap));
+    CK(ctx->d_vals_alt.ensure(cap));
+    CK(ctx->d_trec.ensure(cap));
+    CK(ctx->d_mom.ensure((size_t)cap * 2));
+    CK(ctx->d_hist.ensure((size_t)256 * sort_blocks(cap) + 1));
+    ctx->cap_keys = cap;
+    CK(ensure_scan_scratch(ctx));
+    return GSVR_OK;
+}
+
+// Tile ranges of the current sample (sampled pixels are in tile order).
+gsvr_status finish_sample(gsvr_ctx *ctx) {
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(ctx->d_tile_px_start.p, 0, sizeof(int) * ctx->n_tiles, st));
+    CK(cudaMemsetAsync(ctx->d_tile_px_end.p, 0, sizeof(int) * ctx->n_tiles, st));
+    launch_tile_px_ranges(ctx->d_sampled.p, &ctx->d_counters.p->n_sampled, (int)ctx->P, ctx->d_pix_tile.p,
+                          ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, st);
+    CK(cudaGetLastError());
+    ctx->have_sample = true;
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status sample_all(gsvr_ctx *ctx) {
+    cudaStream_t st = ctx->stream;
+    if (ctx->n_mask > 0)
+        CK(cudaMemcpyAsync(ctx->d_sampled.p, ctx->d_mask_pix_sorted.p, sizeof(int) * ctx->n_mask,
+                           cudaMemcpyDeviceToDevice, st));
+    launch_set_count(&ctx->d_counters.p->n_sampled, ctx->n_mask, st);
+    CK(cudaGetLastError());
+    return finish_sample(ctx);
+}
+
+// Compact flagged tile-order positions into the sample.
+gsvr_status compact_flags(gsvr_ctx *ctx) {
+    cudaStream_t st = ctx->stream;
+    CK(scan_exclusive(ctx->d_flags.p, ctx->d_flag_pos.p, nullptr, (int)ctx->P, (int)ctx->P,
+                      &ctx->d_counters.p->n_sampled, scan_scratch(ctx), st));
+    launch_compact(ctx->d_flags.p, ctx->d_flag_pos.p, ctx->d_tile_sorted_pix.p, (int)ctx->P, ctx->d_sampled.p, st);
+    CK(cudaGetLastError());
+    return finish_sample(ctx);
+}
+
+gsvr_status check_ctx(gsvr_ctx *ctx) { return ctx ? GSVR_OK : GSVR_ERR_INVALID_ARG; }
+
+cudaEvent_t pooled_event(gsvr_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void fold_marks(gsvr_ctx *ctx) {
+    for (auto &m : ctx->marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+            ctx->ms[m.stage] += t;
+            ctx->calls[m.stage] += 1;
+        }
+        cudaGetLastError();
+        ctx->ev_pool.push_back(m.a);
+        ctx->ev_pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+}
+
+// Stage timers: CUDA events on the context stream around each stage.
+void stage_begin(gsvr_ctx *ctx, int stage) {
+    if (!ctx->cfg.timing) return;
+    cudaEvent_t e = pooled_event(ctx);
+    if (!e) return;
+    cudaEventRecord(e, ctx->stream);
+    if (ctx->open_ev[stage]) ctx->ev_pool.push_back(ctx->open_ev[stage]);
+    ctx->open_ev[stage] = e;
+}
+void stage_end(gsvr_ctx *ctx, int stage) {
+    if (!ctx->cfg.timing || !ctx->open_ev[stage]) return;
+    cudaEvent_t e = pooled_event(ctx);
+    if (!e) return;
+    cudaEventRecord(e, ctx->stream);
+    ctx->marks.push_back({stage, ctx->open_ev[stage], e});
+    ctx->open_ev[stage] = nullptr;
+    if (ctx->marks.size() > 65536) {
+        cudaStreamSynchronize(ctx->stream);
+        fold_marks(ctx);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gsvr_abi_version(void) { return GSVR_ABI_VERSION; }
+
+const char *gsvr_last_error(gsvr_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+gsvr_status gsvr_create(gsvr_ctx **out, int device, void *cuda_stream, const gsvr_config *cfg) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return GSVR_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "no such CUDA device";
+        return GSVR_ERR_INVALID_ARG;
+    }
+    gsvr_config c{};
+    if (cfg) c = *cfg;
+    if (c.cutoff_rel == 0.f) c.cutoff_rel = 1e-7f;
+    if (c.tile_w == 0) c.tile_w = 16;
+    if (c.tile_h == 0) c.tile_h = 16;
+    if (!(c.cutoff_rel > 0.f && c.cutoff_rel < 1.f) || (c.timing != 0 && c.timing != 1) || c.tile_w < 4 || c.tile_w > 32 || c.tile_h < 4 ||
+        c.tile_h > 32 || (c.norm_mode != GSVR_NORM_EXACT && c.norm_mode != GSVR_NORM_LITERAL) ||
+        c.cap_records < 0 || c.cap_keys < 0 || (c.fixed_capacity && (c.cap_records <= 0 || c.cap_keys <= 0))) {
+        g_create_error = "invalid gsvr_config";
+        return GSVR_ERR_INVALID_ARG;
+    }
+    gsvr_ctx *ctx = new (std::nothrow) gsvr_ctx();
+    if (!ctx) return GSVR_ERR_NOMEM;
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    ctx->cfg = c;
+    ctx->tile_w = c.tile_w;
+    ctx->tile_h = c.tile_h;
+    ctx->rc2 = (float)(2.0 * std::log(1.0 / (double)c.cutoff_rel));
+    DeviceGuard g(device);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = ctx->d_status.ensure(1);
+    if (e == cudaSuccess) e = ctx->d_counters.ensure(1);
+    if (e == cudaSuccess) e = ctx->d_loss.ensure(1);
+    if (e == cudaSuccess) e = ctx->d_pairs_total.ensure(1);
+    if (e == cudaSuccess) e = ctx->d_useful.ensure(1);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_pairs_total.p, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status.p, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_counters.p, 0, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_loss.p, 0, sizeof(double));
+    if (e != cudaSuccess) {
+        g_create_error = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        delete ctx;
+        return GSVR_ERR_NOMEM;
+    }
+    *out = ctx;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_destroy(gsvr_ctx *ctx) {
+    if (!ctx) return GSVR_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+        delete ctx;
+    }
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_desc *stacks) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (n_stacks <= 0 || !stacks) return fail(ctx, GSVR_ERR_INVALID_ARG, "need at least one stack");
+    DeviceGuard g(ctx->device);
+    const int tw = ctx->tile_w, th = ctx->tile_h;
+    std::vector<SliceDev> sl;
+    std::vector<SliceStatic> ss;
+    int64_t P = 0, T = 0;
+    for (int s = 0; s < n_stacks; ++s) {
+        const gsvr_stack_desc &d = stacks[s];
+        if (d.n_slices <= 0 || d.H <= 0 || d.W <= 0 || d.H > 65536 || d.W > 65536 || !(d.dx > 0.f) ||
+            !(d.dy > 0.f) || !(d.thickness > 0.f) || !finite_all(d.R, 9) || !finite_all(d.origin, 3) ||
+            !finite_all(d.fwhm, 3) || d.fwhm[0] < 0.f || d.fwhm[1] < 0.f || d.fwhm[2] < 0.f)
+            return fail(ctx, GSVR_ERR_INVALID_ARG, "invalid stack description " + std::to_string(s));
+        const int tx = (d.W + tw - 1) / tw, ty = (d.H + th - 1) / th;
+        for (int k = 0; k < d.n_slices; ++k) {
+            SliceDev v{};
+            SliceStatic st{};
+            const double off = ((double)k - 0.5 * (d.n_slices - 1)) * (double)d.thickness;
+            for (int e = 0; e < 9; ++e) st.R0[e] = d.R[e];
+            for (int a = 0; a < 3; ++a) st.c0[a] = (double)d.origin[a] + off * (double)d.R[3 * a + 2];
+            for (int a = 0; a < 3; ++a) {
+                const double sg = (double)d.fwhm[a] / 2.355;
+                v.var[a] = (float)(sg * sg);
+            }
+            v.dx = d.dx;
+            v.dy = d.dy;
+            v.cx0 = 0.5f * (float)(d.W - 1);
+            v.cy0 = 0.5f * (float)(d.H - 1);
+            v.H = d.H;
+            v.W = d.W;
+            v.tiles_x = tx;
+            v.tiles_y = ty;
+            v.tile_base = (int)T;
+            v.pix_base = (int)P;
+            v.stack = s;
+            for (int e = 0; e < 9; ++e) v.R[e] = st.R0[e];
+            for (int a = 0; a < 3; ++a) v.t[a] = st.c0[a];
+            P += (int64_t)d.H * d.W;
+            T += (int64_t)tx * ty;
+            if (P >= (int64_t)INT32_MAX / 2 || T >= (int64_t)INT32_MAX / 2)
+                return fail(ctx, GSVR_ERR_INVALID_ARG, "too many pixels or tiles");
+            sl.push_back(v);
+            ss.push_back(st);
+        }
+    }
+    const int M = (int)sl.size();
+    // static pixel / tile maps: tile order = slice, tile row, tile col, row-major inside the tile
+    std::vector<int> tile_slice((size_t)T), pix_tile((size_t)P), tsp((size_t)P), tpos((size_t)P);
+    int64_t o = 0;
+    for (int i = 0; i < M; ++i) {
+        const SliceDev &v = sl[i];
+        for (int ty = 0; ty < v.tiles_y; ++ty)
+            for (int tx = 0; tx < v.tiles_x; ++tx) {
+                const int t = v.tile_base + ty * v.tiles_x + tx;
+                tile_slice[t] = i;
+                for (int a = ty * th; a < std::min(v.H, (ty + 1) * th); ++a)
+                    for (int b = tx * tw; b < std::min(v.W, (tx + 1) * tw); ++b) {
+                        const int p = v.pix_base + a * v.W + b;
+                        pix_tile[p] = t;
+                        tsp[o] = p;
+                        tpos[p] = (int)o;
+                        ++o;
+                    }
+            }
+    }
+    ctx->have_stacks = ctx->have_obs = ctx->have_sample = ctx->fwd_valid = false;
+    ctx->n_stacks = n_stacks;
+    ctx->M = M;
+    ctx->P = P;
+    ctx->n_tiles = (int)T;
+    int bits = 1;
+    while ((1LL << bits) < T) ++bits;
+    ctx->sort_bits = bits;
+    ctx->h_slices = sl;
+    ctx->h_static = ss;
+    ctx->h_tile_sorted_pix = tsp;
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    CK(ctx->d_slices.ensure(M));
+    CK(ctx->d_static.ensure(M));
+    CK(ctx->d_tile_slice.ensure(T));
+    CK(ctx->d_pix_tile.ensure(P));
+    CK(ctx->d_pix_tpos.ensure(P));
+    CK(ctx->d_tile_sorted_pix.ensure(P));
+    CK(cudaMemcpy(ctx->d_slices.p, sl.data(), sizeof(SliceDev) * M, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_static.p, ss.data(), sizeof(SliceStatic) * M, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tile_slice.p, tile_slice.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_pix_tile.p, pix_tile.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_pix_tpos.p, tpos.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tile_sorted_pix.p, tsp.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(ctx->d_I.ensure(P));
+    CK(ctx->d_mask.ensure(P));
+    CK(ctx->d_flags.ensure(P));
+    CK(ctx->d_flag_pos.ensure(P + 1));
+    CK(ctx->d_sampled.ensure(P));
+    CK(ctx->d_pred.ensure(P));
+    CK(ctx->d_rbar.ensure(P));
+    CK(ctx->d_tile_px_start.ensure(T));
+    CK(ctx->d_tile_px_end.ensure(T));
+    CK(ctx->d_tile_rec_start.ensure(T));
+    CK(ctx->d_tile_rec_end.ensure(T));
+    CK(ctx->d_tile_loss.ensure(T));
+    CK(ctx->d_pose_acc.ensure((size_t)M * 12));
+    CK(ctx->d_frozen.ensure(M));
+    CK(cudaMemset(ctx->d_frozen.p, 0, M));
+    CK(cudaMemset(ctx->d_pred.p, 0, sizeof(float) * P));
+    CK(cudaMemset(ctx->d_rbar.p, 0, sizeof(float) * P));
+    ctx->any_frozen = false;
+    CK(ensure_scan_scratch(ctx));
+    // parameters sized for a different M are dropped
+    if (ctx->have_gauss && ctx->d_theta.n != (size_t)(11 * ctx->N + 6 * M)) ctx->have_gauss = false;
+    ctx->have_stacks = true;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *mask, int32_t mem) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks first");
+    if (!I || (mem != GSVR_MEM_HOST && mem != GSVR_MEM_DEVICE))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad observation pointer or mem kind");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int64_t P = ctx->P;
+    const cudaMemcpyKind kind = mem == GSVR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(ctx->d_I.p, I, sizeof(float) * P, kind, st));
+    std::vector<uint8_t> hm((size_t)P, 1);
+    if (mask) {
+        if (mem == GSVR_MEM_HOST) memcpy(hm.data(), mask, (size_t)P);
+        else CK(cudaMemcpyAsync(hm.data(), mask, (size_t)P, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (auto &v : hm) v = v ? 1 : 0;
+    CK(cudaMemcpy(ctx->d_mask.p, hm.data(), (size_t)P, cudaMemcpyHostToDevice));
+    std::vector<int> mtp, mps;
+    mtp.reserve((size_t)P);
+    for (int64_t t = 0; t < P; ++t) {
+        const int p = ctx->h_tile_sorted_pix[(size_t)t];
+        if (hm[(size_t)p]) {
+            mtp.push_back((int)t);
+            mps.push_back(p);
+        }
+    }
+    ctx->n_mask = (int)mtp.size();
+    CK(ctx->d_mask_tpos.ensure(mtp.size()));
+    CK(ctx->d_mask_pix_sorted.ensure(mps.size()));
+    if (!mtp.empty()) {
+        CK(cudaMemcpy(ctx->d_mask_tpos.p, mtp.data(), sizeof(int) * mtp.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_mask_pix_sorted.p, mps.data(), sizeof(int) * mps.size(), cudaMemcpyHostToDevice));
+    }
+    ctx->have_obs = true;
+    return sample_all(ctx);
+}
+
+gsvr_status gsvr_set_gaussians(gsvr_ctx *ctx, int64_t N, const float *theta_g, int32_t mem) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks first");
+    if (N < 0 || N > (1LL << 26) || (N > 0 && !theta_g) || (mem != GSVR_MEM_HOST && mem != GSVR_MEM_DEVICE))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad Gaussian count, pointer or mem kind");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int M = ctx->M;
+    const size_t np = (size_t)(11 * N + 6 * M);
+    std::vector<float> pose((size_t)6 * M, 0.f);
+    const bool keep_pose = ctx->have_gauss && ctx->d_theta.p && ctx->d_theta.n >= (size_t)(11 * ctx->N + 6 * M);
+    std::vector<float> mv_pose((size_t)12 * M, 0.f);
+    if (keep_pose && M > 0) {
+        CK(cudaMemcpyAsync(pose.data(), ctx->d_theta.p + 11 * ctx->N, sizeof(float) * 6 * M, cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaMemcpyAsync(mv_pose.data(), ctx->d_m.p + 11 * ctx->N, sizeof(float) * 6 * M, cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaMemcpyAsync(mv_pose.data() + 6 * M, ctx->d_v.p + 11 * ctx->N, sizeof(float) * 6 * M,
+                           cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (ctx->d_theta.n != np || !ctx->d_theta.p) {
+        ctx->d_theta.release();
+        ctx->d_grad.release();
+        ctx->d_m.release();
+        ctx->d_v.release();
+    }
+    CK(ctx->d_theta.ensure(np));
+    CK(ctx->d_grad.ensure(np));
+    CK(ctx->d_m.ensure(np));
+    CK(ctx->d_v.ensure(np));
+    CK(ctx->d_gpre.ensure((size_t)2 * N));
+    CK(ctx->d_rec_cnt.ensure((size_t)N + 1));
+    CK(ctx->d_rec_off.ensure((size_t)N + 1));
+    ctx->N = N;
+    if (N > 0)
+        CK(cudaMemcpyAsync(ctx->d_theta.p, theta_g, sizeof(float) * 11 * N,
+                           mem == GSVR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    if (M > 0) {
+        CK(cudaMemcpyAsync(ctx->d_theta.p + 11 * N, pose.data(), sizeof(float) * 6 * M, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_m.p + 11 * N, mv_pose.data(), sizeof(float) * 6 * M, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_v.p + 11 * N, mv_pose.data() + 6 * M, sizeof(float) * 6 * M,
+                           cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(ctx->d_grad.p, 0, sizeof(float) * np, st));
+    if (N > 0) {
+        CK(cudaMemsetAsync(ctx->d_m.p, 0, sizeof(float) * 11 * N, st));
+        CK(cudaMemsetAsync(ctx->d_v.p, 0, sizeof(float) * 11 * N, st));
+    }
+    // initial capacities
+    if (ctx->cfg.fixed_capacity) {
+        gsvr_status s = ensure_rec_capacity(ctx, ctx->cfg.cap_records);
+        if (s) return s;
+        s = ensure_key_capacity(ctx, ctx->cfg.cap_keys);
+        if (s) return s;
+    } else {
+        const int64_t want_r = ctx->cfg.cap_records > 0 ? ctx->cfg.cap_records : std::max<int64_t>(4096, 8 * N);
+        const int64_t want_k = ctx->cfg.cap_keys > 0 ? ctx->cfg.cap_keys : 4 * want_r;
+        gsvr_status s = ensure_rec_capacity(ctx, std::max<int64_t>(ctx->cap_rec, want_r));
+        if (s) return s;
+        s = ensure_key_capacity(ctx, std::max<int64_t>(ctx->cap_keys, want_k));
+        if (s) return s;
+    }
+    CK(ensure_scan_scratch(ctx));
+    ctx->have_gauss = true;
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_poses(gsvr_ctx *ctx, const float *pose, int32_t mem) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
+    if (!pose || (mem != GSVR_MEM_HOST && mem != GSVR_MEM_DEVICE))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad pose pointer or mem kind");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int M = ctx->M;
+    if (M > 0) {
+        CK(cudaMemcpyAsync(ctx->d_theta.p + 11 * ctx->N, pose, sizeof(float) * 6 * M,
+                           mem == GSVR_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(ctx->d_m.p + 11 * ctx->N, 0, sizeof(float) * 6 * M, st));
+        CK(cudaMemsetAsync(ctx->d_v.p + 11 * ctx->N, 0, sizeof(float) * 6 * M, st));
+    }
+    if (mem == GSVR_MEM_HOST) CK(cudaStreamSynchronize(st));
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_frozen(gsvr_ctx *ctx, const uint8_t *frozen) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks first");
+    DeviceGuard g(ctx->device);
+    std::vector<uint8_t> f((size_t)ctx->M, 0);
+    bool any = false;
+    if (frozen)
+        for (int i = 0; i < ctx->M; ++i) {
+            f[i] = frozen[i] ? 1 : 0;
+            any = any || f[i];
+        }
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_frozen.p, f.data(), (size_t)ctx->M, cudaMemcpyHostToDevice));
+    ctx->any_frozen = any;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, int32_t mem) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_observations first");
+    if (n < 0) {
+        DeviceGuard g(ctx->device);
+        return sample_all(ctx);
+    }
+    if ((n > 0 && !idx) || n > (int64_t)INT32_MAX / 2 || (mem != GSVR_MEM_HOST && mem != GSVR_MEM_DEVICE))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad sample pointer, size or mem kind");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int32_t *didx = idx;
+    if (mem == GSVR_MEM_HOST && n > 0) {
+        for (int64_t k = 0; k < n; ++k)
+            if (idx[k] < 0 || idx[k] >= ctx->P) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range");
+        CK(ctx->d_idx.ensure((size_t)n));
+        CK(cudaMemcpyAsync(ctx->d_idx.p, idx, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        didx = ctx->d_idx.p;
+    }
+    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
+    launch_flags_from_list(didx, (int)n, (int)ctx->P, ctx->d_mask.p, ctx->d_pix_tpos.p, ctx->d_flags.p,
+                           ctx->d_status.p, st);
+    CK(cudaGetLastError());
+    return compact_flags(ctx);
+}
+
+gsvr_status gsvr_sample_pixels(gsvr_ctx *ctx, int64_t n, uint64_t step) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_observations first");
+    if (n < 0 || n > ctx->n_mask) return fail(ctx, GSVR_ERR_INVALID_ARG, "sample larger than the masked pixels");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    SamplerKeys sk{};
+    int k = 1;
+    while ((1LL << k) < ctx->n_mask) ++k;
+    sk.k = k;
+    sk.h = (k + 1) / 2;
+    const uint64_t msk = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
+    for (int r = 0; r < 4; ++r) {
+        const uint64_t key = splitmix64_at(ctx->cfg.seed, 4ULL * step + (uint64_t)r);
+        sk.xk[r] = key & msk;
+        sk.mul[r] = (key >> 32) | 1ULL;
+    }
+    stage_begin(ctx, GSVR_STAGE_SAMPLE);
+    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
+    launch_sample_flags(ctx->n_mask, (int)n, sk, ctx->d_mask_tpos.p, ctx->d_flags.p, st);
+    CK(cudaGetLastError());
+    gsvr_status s = compact_flags(ctx);
+    stage_end(ctx, GSVR_STAGE_SAMPLE);
+    return s;
+}
+
+gsvr_status gsvr_forward(gsvr_ctx *ctx) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss || !ctx->have_obs || !ctx->have_sample)
+        return fail(ctx, GSVR_ERR_STATE, "set stacks, observations and Gaussians before gsvr_forward");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int N = (int)ctx->N, M = ctx->M;
+    Counters *cnt = ctx->d_counters.p;
+    const bool grow = !ctx->cfg.fixed_capacity;
+    stage_begin(ctx, GSVR_STAGE_PREP);
+    CK(cudaMemsetAsync(&cnt->pairs, 0, sizeof(unsigned long long), st));
+    launch_gauss_prep(ctx->d_theta.p, N, ctx->d_gpre.p, ctx->d_status.p, st);
+    launch_pose_prep(ctx->d_theta.p + 11LL * N, ctx->d_static.p, ctx->d_slices.p, M, ctx->d_status.p, st);
+    stage_end(ctx, GSVR_STAGE_PREP);
+    stage_begin(ctx, GSVR_STAGE_BIN);
+
+    BinArgs b{};
+    b.theta = ctx->d_theta.p;
+    b.gpre = ctx->d_gpre.p;
+    b.slices = ctx->d_slices.p;
+    b.N = N;
+    b.M = M;
+    b.rc2 = ctx->rc2;
+    b.norm_mode = ctx->cfg.norm_mode;
+    b.tile_w = ctx->tile_w;
+    b.tile_h = ctx->tile_h;
+    b.tile_px_start = ctx->d_tile_px_start.p;
+    b.tile_px_end = ctx->d_tile_px_end.p;
+    b.rec_cnt = ctx->d_rec_cnt.p;
+    b.status = ctx->d_status.p;
+    launch_rec_count(b, st);
+    CK(cudaGetLastError());
+    CK(scan_exclusive(ctx->d_rec_cnt.p, ctx->d_rec_off.p, nullptr, N, N, &cnt->n_rec, scan_scratch(ctx), st));
+    int n_rec_max = ctx->cap_rec;
+    if (grow) {
+        int n_rec = 0;
+        CK(cudaMemcpyAsync(&n_rec, &cnt->n_rec, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (n_rec > ctx->cap_rec) {
+            gsvr_status s = ensure_rec_capacity(ctx, (int64_t)n_rec + n_rec / 4 + 1024);
+            if (s) return s;
+        }
+        n_rec_max = n_rec;
+        ctx->last_n_rec = n_rec;
+    }
+    b.rec_off = ctx->d_rec_off.p;
+    b.rec = ctx->d_rec.p;
+    b.rec_tiles = ctx->d_rec_tiles.p;
+    b.rec_nkeys = ctx->d_rec_nkeys.p;
+    b.cap_rec = ctx->cap_rec;
+    launch_rec_emit(b, st);
+    CK(cudaGetLastError());
+    CK(scan_exclusive(ctx->d_rec_nkeys.p, ctx->d_key_off.p, &cnt->n_rec, 0, std::max(n_rec_max, 0), &cnt->n_keys,
+                      scan_scratch(ctx), st));
+    int n_keys_max = ctx->cap_keys;
+    if (grow) {
+        int n_keys = 0;
+        CK(cudaMemcpyAsync(&n_keys, &cnt->n_keys, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (n_keys > ctx->cap_keys) {
+            gsvr_status s = ensure_key_capacity(ctx, (int64_t)n_keys + n_keys / 4 + 4096);
+            if (s) return s;
+        }
+        n_keys_max = n_keys;
+        ctx->last_n_keys = n_keys;
+    }
+    KeyArgs k{};
+    k.rec = ctx->d_rec.p;
+    k.rec_tiles = ctx->d_rec_tiles.p;
+    k.key_off = ctx->d_key_off.p;
+    k.slices = ctx->d_slices.p;
+    k.tile_px_start = ctx->d_tile_px_start.p;
+    k.tile_px_end = ctx->d_tile_px_end.p;
+    k.n_rec = &cnt->n_rec;
+    k.cap_rec = ctx->cap_rec;
+    k.cap_keys = ctx->cap_keys;
+    k.keys = ctx->d_keys.p;
+    k.key_rec = ctx->d_key_rec.p;
+    k.status = ctx->d_status.p;
+    launch_key_emit(k, n_rec_max, st);
+    CK(cudaGetLastError());
+    SortScratch ss{ctx->d_keys_alt.p, ctx->d_vals_alt.p, ctx->d_hist.p, scan_scratch(ctx)};
+    if (n_keys_max > 0)
+        CK(radix_sort_pairs(ctx->d_keys.p, nullptr, ctx->d_keys_sorted.p, ctx->d_vals_sorted.p, &cnt->n_keys,
+                            n_keys_max, ctx->sort_bits, ss, st));
+    CK(cudaMemsetAsync(ctx->d_tile_rec_start.p, 0, sizeof(int) * ctx->n_tiles, st));
+    CK(cudaMemsetAsync(ctx->d_tile_rec_end.p, 0, sizeof(int) * ctx->n_tiles, st));
+    launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->d_tile_rec_start.p,
+                           ctx->d_tile_rec_end.p, st);
+    launch_gather(ctx->d_rec.p, ctx->d_vals_sorted.p, ctx->d_key_rec.p, &cnt->n_keys, n_keys_max, ctx->d_trec.p, st);
+    stage_end(ctx, GSVR_STAGE_BIN);
+    EvalArgs e{};
+    e.trec = ctx->d_trec.p;
+    e.tile_rec_start = ctx->d_tile_rec_start.p;
+    e.tile_rec_end = ctx->d_tile_rec_end.p;
+    e.tile_px_start = ctx->d_tile_px_start.p;
+    e.tile_px_end = ctx->d_tile_px_end.p;
+    e.tile_slice = ctx->d_tile_slice.p;
+    e.slices = ctx->d_slices.p;
+    e.sampled = ctx->d_sampled.p;
+    e.n_sampled = &cnt->n_sampled;
+    e.I_obs = ctx->d_I.p;
+    e.pred = ctx->d_pred.p;
+    e.rbar = ctx->d_rbar.p;
+    e.tile_loss = ctx->d_tile_loss.p;
+    e.mom = ctx->d_mom.p;
+    e.counters = cnt;
+    e.pairs_total = ctx->d_pairs_total.p;
+    e.n_tiles = ctx->n_tiles;
+    e.status = ctx->d_status.p;
+    stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
+    launch_forward(e, ctx->tile_w * ctx->tile_h, st);
+    stage_end(ctx, GSVR_STAGE_FWD_EVAL);
+    launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_loss.p, ctx->d_status.p, st);
+    CK(cudaGetLastError());
+    ctx->fwd_valid = true;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_backward(gsvr_ctx *ctx) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->fwd_valid) return fail(ctx, GSVR_ERR_STATE, "gsvr_backward needs a current gsvr_forward");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int N = (int)ctx->N, M = ctx->M;
+    Counters *cnt = ctx->d_counters.p;
+    EvalArgs e{};
+    e.trec = ctx->d_trec.p;
+    e.tile_rec_start = ctx->d_tile_rec_start.p;
+    e.tile_rec_end = ctx->d_tile_rec_end.p;
+    e.tile_px_start = ctx->d_tile_px_start.p;
+    e.tile_px_end = ctx->d_tile_px_end.p;
+    e.tile_slice = ctx->d_tile_slice.p;
+    e.slices = ctx->d_slices.p;
+    e.sampled = ctx->d_sampled.p;
+    e.n_sampled = &cnt->n_sampled;
+    e.I_obs = ctx->d_I.p;
+    e.pred = ctx->d_pred.p;
+    e.rbar = ctx->d_rbar.p;
+    e.tile_loss = ctx->d_tile_loss.p;
+    e.mom = ctx->d_mom.p;
+    e.counters = cnt;
+    e.n_tiles = ctx->n_tiles;
+    e.status = ctx->d_status.p;
+    stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
+    launch_backward(e, st);
+    stage_end(ctx, GSVR_STAGE_BWD_EVAL);
+    stage_begin(ctx, GSVR_STAGE_GRAD);
+    CK(cudaMemsetAsync(ctx->d_pose_acc.p, 0, sizeof(double) * 12 * M, st));
+    GradArgs a{};
+    a.theta = ctx->d_theta.p;
+    a.gpre = ctx->d_gpre.p;
+    a.slices = ctx->d_slices.p;
+    a.rec = ctx->d_rec.p;
+    a.rec_off = ctx->d_rec_off.p;
+    a.key_off = ctx->d_key_off.p;
+    a.mom = ctx->d_mom.p;
+    a.N = N;
+    a.M = M;
+    a.rc2 = ctx->rc2;
+    a.norm_mode = ctx->cfg.norm_mode;
+    a.grad = ctx->d_grad.p;
+    a.pose_acc = ctx->d_pose_acc.p;
+    a.use_smem = (size_t)M * 12 * sizeof(float) <= 48 * 1024 ? 1 : 0;
+    a.cap_rec = ctx->cap_rec;
+    a.cap_keys = ctx->cap_keys;
+    launch_gauss_grad(a, st);
+    launch_pose_grad(ctx->d_pose_acc.p, ctx->d_static.p, ctx->d_theta.p + 11LL * N, ctx->d_grad.p + 11LL * N, M, st);
+    stage_end(ctx, GSVR_STAGE_GRAD);
+    CK(cudaGetLastError());
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_adam_step(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
+    if (!cfg || step < 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "adam config NULL or step < 1");
+    DeviceGuard g(ctx->device);
+    const float b1 = cfg->beta1 == 0.f ? 0.9f : cfg->beta1;
+    const float b2 = cfg->beta2 == 0.f ? 0.999f : cfg->beta2;
+    const float eps = cfg->eps == 0.f ? 1e-8f : cfg->eps;
+    if (!(b1 > 0.f && b1 < 1.f && b2 > 0.f && b2 < 1.f && eps > 0.f))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad Adam betas or eps");
+    const float lr[6] = {cfg->lr_mu, cfg->lr_ls, cfg->lr_q, cfg->lr_c, cfg->lr_rot, cfg->lr_trans};
+    const double bc1 = 1.0 - std::pow((double)b1, (double)step);
+    const double bc2 = 1.0 - std::pow((double)b2, (double)step);
+    stage_begin(ctx, GSVR_STAGE_ADAM);
+    launch_adam(ctx->d_theta.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, (int)ctx->N, ctx->M, lr, b1, b2, eps, bc1,
+                bc2, ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
+    stage_end(ctx, GSVR_STAGE_ADAM);
+    CK(cudaGetLastError());
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_sync_status(gsvr_ctx *ctx) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    unsigned s = 0;
+    CK(cudaMemcpyAsync(&s, ctx->d_status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (s) CK(cudaMemsetAsync(ctx->d_status.p, 0, sizeof(unsigned), ctx->stream));
+    if (s & ST_CAPACITY) return fail(ctx, GSVR_ERR_CAPACITY, "record or key capacity exceeded");
+    if (s & ST_NONFINITE) return fail(ctx, GSVR_ERR_NONFINITE, "non-finite parameter, pose or loss");
+    if (s & ST_TIMEOUT) return fail(ctx, GSVR_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (s & ST_INDEX) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range in a device sample");
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_step_host(gsvr_ctx *ctx, const float *theta, const int32_t *idx, int64_t n, float *grad_out,
+                           double *loss_out) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss || !ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "context not initialised");
+    if (!theta) return fail(ctx, GSVR_ERR_INVALID_ARG, "theta is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t np = (size_t)(11 * ctx->N + 6 * ctx->M);
+    CK(cudaMemcpyAsync(ctx->d_theta.p, theta, sizeof(float) * np, cudaMemcpyHostToDevice, st));
+    gsvr_status s = gsvr_set_pixel_sample(ctx, idx, n, GSVR_MEM_HOST);
+    if (s) return s;
+    s = gsvr_forward(ctx);
+    if (s) return s;
+    s = gsvr_backward(ctx);
+    if (s) return s;
+    if (grad_out) CK(cudaMemcpyAsync(grad_out, ctx->d_grad.p, sizeof(float) * np, cudaMemcpyDeviceToHost, st));
+    if (loss_out) CK(cudaMemcpyAsync(loss_out, ctx->d_loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return gsvr_sync_status(ctx);
+}
+
+gsvr_status gsvr_timing_reset(gsvr_ctx *ctx) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    fold_marks(ctx);
+    for (int k = 0; k < GSVR_N_STAGES; ++k) {
+        ctx->ms[k] = 0.0;
+        ctx->calls[k] = 0;
+    }
+    CK(cudaMemset(ctx->d_pairs_total.p, 0, sizeof(unsigned long long)));
+    ctx->launches_at_reset = launch_count();
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_kernel_times(gsvr_ctx *ctx, gsvr_kernel_times *out) {
+    if (check_ctx(ctx) || !out) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    fold_marks(ctx);
+    unsigned long long pt = 0;
+    CK(cudaMemcpy(&pt, ctx->d_pairs_total.p, sizeof(pt), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < GSVR_N_STAGES; ++k) {
+        out->ms[k] = ctx->ms[k];
+        out->calls[k] = ctx->calls[k];
+    }
+    out->pairs_evaluated = (int64_t)pt;
+    out->kernel_launches = launch_count() - ctx->launches_at_reset;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_count_pairs(gsvr_ctx *ctx, int64_t *useful, int64_t *evaluated) {
+    if (check_ctx(ctx) || !useful || !evaluated) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->fwd_valid) return fail(ctx, GSVR_ERR_STATE, "gsvr_count_pairs needs a current gsvr_forward");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    Counters *cnt = ctx->d_counters.p;
+    CK(cudaMemsetAsync(ctx->d_useful.p, 0, sizeof(unsigned long long), st));
+    EvalArgs e{};
+    e.trec = ctx->d_trec.p;
+    e.tile_rec_start = ctx->d_tile_rec_start.p;
+    e.tile_rec_end = ctx->d_tile_rec_end.p;
+    e.tile_px_start = ctx->d_tile_px_start.p;
+    e.tile_px_end = ctx->d_tile_px_end.p;
+    e.tile_slice = ctx->d_tile_slice.p;
+    e.slices = ctx->d_slices.p;
+    e.sampled = ctx->d_sampled.p;
+    e.n_sampled = &cnt->n_sampled;
+    e.counters = cnt;
+    e.useful = ctx->d_useful.p;
+    e.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
+    e.n_tiles = ctx->n_tiles;
+    e.status = ctx->d_status.p;
+    launch_count_pairs(e, ctx->tile_w * ctx->tile_h, st);
+    CK(cudaGetLastError());
+    unsigned long long u = 0;
+    Counters c{};
+    CK(cudaMemcpyAsync(&u, ctx->d_useful.p, sizeof(u), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *useful = (int64_t)u;
+    *evaluated = (int64_t)c.pairs;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_sample(gsvr_ctx *ctx, int32_t *out, int64_t cap, int64_t *n_out) {
+    if (check_ctx(ctx) || !n_out || cap < 0 || (cap > 0 && !out)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_sample) return fail(ctx, GSVR_ERR_STATE, "no sample");
+    DeviceGuard g(ctx->device);
+    Counters c{};
+    CK(cudaMemcpyAsync(&c, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n_out = c.n_sampled;
+    const int64_t n = std::min<int64_t>(cap, c.n_sampled);
+    if (n > 0) CK(cudaMemcpy(out, ctx->d_sampled.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_views(gsvr_ctx *ctx, gsvr_views *out) {
+    if (check_ctx(ctx) || !out) return GSVR_ERR_INVALID_ARG;
+    out->theta = ctx->d_theta.p;
+    out->grad = ctx->d_grad.p;
+    out->adam_m = ctx->d_m.p;
+    out->adam_v = ctx->d_v.p;
+    out->pred = ctx->d_pred.p;
+    out->rbar = ctx->d_rbar.p;
+    out->loss = ctx->d_loss.p;
+    out->n_gauss = ctx->N;
+    out->n_slices = ctx->M;
+    out->n_pixels = ctx->P;
+    out->n_params = 11 * ctx->N + 6 * ctx->M;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_stats(gsvr_ctx *ctx, gsvr_stats *out) {
+    if (check_ctx(ctx) || !out) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    Counters c{};
+    CK(cudaMemcpyAsync(&c, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->n_sampled = c.n_sampled;
+    out->n_records = c.n_rec;
+    out->n_keys = c.n_keys;
+    out->pairs_evaluated = (int64_t)c.pairs;
+    out->n_tiles = ctx->n_tiles;
+    out->tile_px_max = (int64_t)ctx->tile_w * ctx->tile_h;
+    out->cap_records = ctx->cap_rec;
+    out->cap_keys = ctx->cap_keys;
+    return GSVR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// gsvr_internal.cuh -- device data layout, PTX helpers and launcher declarations
+// shared by the libgsvr.so translation units.  Nothing here is visible through
+// the C ABI (include/gsvr.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsvr.h"
+
+namespace gsvr {
+
+constexpr int kThreads = 128;     // threads of the tile kernels
+constexpr int kChunk = 256;       // records staged per shared-memory buffer in the forward
+constexpr int kMaxTilePx = 1024;  // largest tile (32 x 32 pixels)
+constexpr int kScanTile = 4096;   // items per block of the scans
+constexpr int kSortThreads = 256; // 8 warps
+constexpr int kSortItems = 16;    // keys per thread per radix pass (4096 per block)
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Device status word bits (latched; read by gsvr_sync_status).
+enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
+
+// Per-slice frame and geometry.  R, t are rewritten from the pose every
+// forward (Sec. 3.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau); the rest is
+// fixed by the stack description.
+struct SliceDev {
+    double R[9];    // world-from-slice rotation, row-major
+    double t[3];    // world position of the slice centre
+    float var[3];   // Sigma_PSF diagonal (slice axes), mm^2
+    float dx, dy;   // pixel spacing (mm)
+    float cx0, cy0; // (W-1)/2, (H-1)/2
+    int H, W;
+    int tiles_x, tiles_y;
+    int tile_base;  // global id of the slice's first tile
+    int pix_base;   // global index of the slice's first pixel
+    int stack;
+    int pad_;
+};
+
+struct SliceStatic {
+    double R0[9];   // nominal rotation (the stack's)
+    double c0[3];   // nominal centre
+};
+
+// Device-side counts of the current forward.
+struct Counters {
+    int n_sampled;
+    int n_rec;
+    int n_keys;
+    int pad_;
+    unsigned long long pairs;  // pixel x record pairs visited by one evaluation pass
+};
+
+// A (slice, Gaussian) record: the 3D Gaussian conditioned on the slice plane
+// (an exact identity: restricting exp(-1/2 v^T K^-1 v) to z = 0 gives a 2D
+// Gaussian), in slice-centred pixel units, exponent pre-scaled by -1/2 log2(e):
+//   f4[0] = (cb, ca, A, C2)   f4[1] = (B, w, j, i-or-key)
+// value at pixel (b, a) = w * exp2(A db^2 + C2 db da + B da^2), db = b - cb, da = a - ca.
+struct __align__(16) Rec {
+    float4 a, b;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------ launcher API
+struct ScanScratch {
+    int *bsum;   // >= blocks + 1 ints
+    int cap_blocks;
+};
+// Exclusive scan of n int32 (n from *d_n when d_n != null, else n_static;
+// n_max bounds the grid).  out[n] = total; *total_out = total when non-null.
+cudaError_t scan_exclusive(const int *in, int *out, const int *d_n, int n_static, int n_max, int *total_out,
+                           const ScanScratch &s, cudaStream_t st);
+int scan_blocks(int n_max);
+
+struct SortScratch {
+    uint32_t *keys_alt, *vals_alt;  // ping-pong buffers (n_max each)
+    int *hist;                      // 256 * blocks + 1
+    ScanScratch scan;
+};
+int sort_blocks(int n_max);
+// Stable LSD radix sort of n u32 keys (only the low `bits` bits are used) with
+// u32 values; vals_in == null means values are the identity 0..n-1.  Result in
+// keys_out / vals_out.
+cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
+                             uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
+                             cudaStream_t st);
+
+}  // namespace gsvr

@@ -1,0 +1,977 @@
+// gsvr_kernels.cu -- the compute path of libgsvr.so (sm_103a).
+//
+// Per forward:
+//   gauss_prep   Sigma_j = R(q) diag(exp(2 ls)) R(q)^T            (Sec. 3.2)
+//   pose_prep    R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau          (Sec. 3.4)
+//   rec_count / rec_emit
+//                every (slice i, Gaussian j): m = R_i^T (mu_j - t_i),
+//                K = R_i^T Sigma_j R_i + Sigma_PSF (= R_i^T Sigma_obs R_i, Eq. 4);
+//                keep if m_z^2 / K_zz <= r_c^2 (Mahalanobis cut); the pair's
+//                restriction to the slice plane is the exact 2D Gaussian
+//                w exp(-1/2 (u - c)^T P2 (u - c)) with P2 = Schur complement
+//                inverse, c = m_xy - K_xz m_z / K_zz,
+//                w = c_j sqrt(det Sigma_j / det K) exp(-1/2 m_z^2 / K_zz)  (Eq. 5 numerator)
+//   key_emit     one key per (non-empty tile, record) in the record's bounding box
+//   radix sort   keys by tile id (stable: within a tile records stay in Gaussian order)
+//   gather       tile-ordered copy of the records
+//   forward      per tile: records staged through shared memory by the TMA bulk
+//                engine (double-buffered, mbarrier-completed), thread per pixel,
+//                fused residual and loss
+// Per backward:
+//   backward     per tile: thread per record, pixels broadcast from shared
+//                memory; 6 first/second moments of r_bar * e per (tile, record)
+//   gauss_grad   thread per Gaussian: sums its records' moments, chains them to
+//                mu, Sigma_j -> (ls, q), c; slice-frame gradients reduced in
+//                shared memory, then one float64 atomic per (block, slice, entry)
+//   pose_grad    (R_i, t_i) gradients -> (r, tau) through the exponential map
+//   adam         fused, per-group learning rates
+#include <math.h>
+
+#include <atomic>
+
+#include "gsvr_launch.cuh"
+
+namespace gsvr {
+
+namespace {
+
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -1/2 log2(e)
+constexpr uint64_t kWaitLimitNs = 1000000000ull;            // 1 s bound on any mbarrier wait
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z);
+    R[1] = 2.f * (x * y - w * z);
+    R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);
+    R[4] = 1.f - 2.f * (x * x + z * z);
+    R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);
+    R[7] = 2.f * (y * z + w * x);
+    R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ void rodrigues_d(const double r[3], double R[9]) {
+    const double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const double th = sqrt(th2);
+    double A, B;
+    if (th < 1e-4) {
+        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+    }
+    const double K[9] = {0.0, -r[2], r[1], r[2], 0.0, -r[0], -r[1], r[0], 0.0};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double k2 = K[3 * a] * K[b] + K[3 * a + 1] * K[3 + b] + K[3 * a + 2] * K[6 + b];
+            R[3 * a + b] = (a == b ? 1.0 : 0.0) + A * K[3 * a + b] + B * k2;
+        }
+}
+
+// Everything the record and its gradient need about one (slice, Gaussian) pair.
+struct RecGeom {
+    double d[3];      // mu - t (world)
+    double mz;        // slice-normal coordinate of the mean
+    double cxm, cym;  // conditional centre in slice mm
+    float R[9];       // slice rotation (float)
+    float Kxx, Kyy, Kzz, Kxy, Kxz, Kyz;
+    float qz;         // m_z^2 / K_zz
+    float M2xx, M2yy, M2xy, det2;
+    float P2xx, P2yy, P2xy;
+    float w0;         // w / c_j
+};
+
+// Cheap float32 rejection before the float64 geometry: |m_z| against the cut
+// with a relative margin (the exact test follows in rec_geom).
+__device__ __forceinline__ bool slab_candidate(const float4 g0, const float4 g1, const float mu[3],
+                                               const SliceDev &S, float rc2) {
+    const float nx = (float)S.R[2], ny = (float)S.R[5], nz = (float)S.R[8];
+    const float mz = nx * (mu[0] - (float)S.t[0]) + ny * (mu[1] - (float)S.t[1]) + nz * (mu[2] - (float)S.t[2]);
+    // n^T Sigma n
+    const float sx = g0.x * nx + g0.w * ny + g1.x * nz;
+    const float sy = g0.w * nx + g0.y * ny + g1.y * nz;
+    const float sz = g1.x * nx + g1.y * ny + g0.z * nz;
+    const float kzz = nx * sx + ny * sy + nz * sz + S.var[2];
+    return mz * mz <= (rc2 * 1.001f + 1e-3f) * kzz + 1e-3f;
+}
+
+__device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const float mu[3], const SliceDev &S,
+                                         float rc2, int norm_mode, RecGeom &G) {
+    for (int a = 0; a < 3; ++a) G.d[a] = (double)mu[a] - S.t[a];
+    const double m0 = S.R[0] * G.d[0] + S.R[3] * G.d[1] + S.R[6] * G.d[2];
+    const double m1 = S.R[1] * G.d[0] + S.R[4] * G.d[1] + S.R[7] * G.d[2];
+    const double m2 = S.R[2] * G.d[0] + S.R[5] * G.d[1] + S.R[8] * G.d[2];
+    for (int e = 0; e < 9; ++e) G.R[e] = (float)S.R[e];
+    const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
+    float T[9];  // Sigma R
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            T[3 * a + b] = Sg[3 * a] * G.R[b] + Sg[3 * a + 1] * G.R[3 + b] + Sg[3 * a + 2] * G.R[6 + b];
+    auto K = [&](int a, int b) { return G.R[a] * T[b] + G.R[3 + a] * T[3 + b] + G.R[6 + a] * T[6 + b]; };
+    G.Kxx = K(0, 0) + S.var[0];
+    G.Kyy = K(1, 1) + S.var[1];
+    G.Kzz = K(2, 2) + S.var[2];
+    G.Kxy = K(0, 1);
+    G.Kxz = K(0, 2);
+    G.Kyz = K(1, 2);
+    G.mz = m2;
+    G.qz = (float)(m2 * m2 / (double)G.Kzz);
+    if (!(G.qz <= rc2)) return false;
+    const float ik = 1.0f / G.Kzz;
+    G.M2xx = G.Kxx - G.Kxz * G.Kxz * ik;
+    G.M2yy = G.Kyy - G.Kyz * G.Kyz * ik;
+    G.M2xy = G.Kxy - G.Kxz * G.Kyz * ik;
+    G.det2 = G.M2xx * G.M2yy - G.M2xy * G.M2xy;
+    const float idet = 1.0f / G.det2;
+    G.P2xx = G.M2yy * idet;
+    G.P2yy = G.M2xx * idet;
+    G.P2xy = -G.M2xy * idet;
+    G.cxm = m0 - (double)(G.Kxz * ik) * m2;
+    G.cym = m1 - (double)(G.Kyz * ik) * m2;
+    if (norm_mode == GSVR_NORM_EXACT)
+        G.w0 = expf(g1.z - 0.5f * G.qz) * rsqrtf(G.Kzz * G.det2);
+    else
+        G.w0 = expf(-0.5f * G.qz);
+    return true;
+}
+
+// Tile bounding box of the record's ellipse {q <= r_c^2} on the slice.
+__device__ __forceinline__ bool rec_bbox(const RecGeom &G, const SliceDev &S, float rc2, int tw, int th,
+                                         float &cb, float &ca, int &tx0, int &tx1, int &ty0, int &ty1) {
+    const float rho2 = fmaxf(rc2 - G.qz, 0.0f);
+    const float hx = sqrtf(rho2 * G.M2xx) / S.dx;
+    const float hy = sqrtf(rho2 * G.M2yy) / S.dy;
+    cb = (float)(G.cxm / (double)S.dx);
+    ca = (float)(G.cym / (double)S.dy);
+    const float blo = fminf(fmaxf(cb + S.cx0 - hx, -1.0f), (float)S.W);
+    const float bhi = fminf(fmaxf(cb + S.cx0 + hx, -1.0f), (float)S.W);
+    const float alo = fminf(fmaxf(ca + S.cy0 - hy, -1.0f), (float)S.H);
+    const float ahi = fminf(fmaxf(ca + S.cy0 + hy, -1.0f), (float)S.H);
+    const int b0 = max(0, (int)ceilf(blo)), b1 = min(S.W - 1, (int)floorf(bhi));
+    const int a0 = max(0, (int)ceilf(alo)), a1 = min(S.H - 1, (int)floorf(ahi));
+    if (!(G.det2 > 0.0f) || b0 > b1 || a0 > a1) return false;
+    tx0 = b0 / tw;
+    tx1 = b1 / tw;
+    ty0 = a0 / th;
+    ty1 = a1 / th;
+    return true;
+}
+
+__device__ __forceinline__ int count_live_tiles(const SliceDev &S, int tx0, int tx1, int ty0, int ty1,
+                                                const int *tps, const int *tpe) {
+    int n = 0;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const int t = S.tile_base + ty * S.tiles_x + tx;
+            n += (tpe[t] > tps[t]) ? 1 : 0;
+        }
+    return n;
+}
+
+// ------------------------------------------------------------- preprocessing
+__global__ void k_gauss_prep(const float *__restrict__ th, int N, float4 *__restrict__ gpre, unsigned *status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    float p[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) p[k] = th[(size_t)k * N + j];
+    bool fin = true;
+#pragma unroll
+    for (int k = 0; k < 11; ++k) fin = fin && isfinite(p[k]);
+    const float qn2 = p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9];
+    if (!fin || !(qn2 > 0.0f)) atomicOr(status, ST_NONFINITE);
+    const float iq = rsqrtf(qn2);
+    float R[9];
+    quat_rot(p[6] * iq, p[7] * iq, p[8] * iq, p[9] * iq, R);
+    const float s0 = expf(2.f * p[3]), s1 = expf(2.f * p[4]), s2 = expf(2.f * p[5]);
+    auto S = [&](int a, int b) { return R[3 * a] * s0 * R[3 * b] + R[3 * a + 1] * s1 * R[3 * b + 1] + R[3 * a + 2] * s2 * R[3 * b + 2]; };
+    gpre[2 * j] = make_float4(S(0, 0), S(1, 1), S(2, 2), S(0, 1));
+    gpre[2 * j + 1] = make_float4(S(0, 2), S(1, 2), p[3] + p[4] + p[5], p[10]);
+}
+
+__global__ void k_pose_prep(const float *__restrict__ pose, const SliceStatic *__restrict__ ss,
+                            SliceDev *__restrict__ sd, int M, unsigned *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double r[3], tau[3];
+    bool fin = true;
+    for (int k = 0; k < 3; ++k) {
+        r[k] = pose[6 * i + k];
+        tau[k] = pose[6 * i + 3 + k];
+        fin = fin && isfinite(r[k]) && isfinite(tau[k]);
+    }
+    if (!fin) atomicOr(status, ST_NONFINITE);
+    double Q[9];
+    rodrigues_d(r, Q);
+    const SliceStatic s = ss[i];
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b)
+            sd[i].R[3 * a + b] = Q[3 * a] * s.R0[b] + Q[3 * a + 1] * s.R0[3 + b] + Q[3 * a + 2] * s.R0[6 + b];
+        sd[i].t[a] = Q[3 * a] * s.c0[0] + Q[3 * a + 1] * s.c0[1] + Q[3 * a + 2] * s.c0[2] + tau[a];
+    }
+}
+
+// ---------------------------------------------------------------- sampling
+__global__ void k_sample_flags(int n_mask, int n_s, SamplerKeys sk, const int *__restrict__ mask_tpos,
+                               int *__restrict__ flags) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_s) return;
+    const unsigned long long msk = (sk.k >= 64) ? ~0ull : ((1ull << sk.k) - 1ull);
+    unsigned long long x = (unsigned long long)t;
+    // cycle walking terminates within 2^k steps (f permutes [0, 2^k))
+    for (unsigned long long it = 0; it <= msk; ++it) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            x = (x ^ sk.xk[r]) & msk;
+            x = (x * sk.mul[r]) & msk;
+            x ^= x >> sk.h;
+        }
+        if (x < (unsigned long long)n_mask) break;
+    }
+    if (x < (unsigned long long)n_mask) flags[mask_tpos[x]] = 1;
+}
+
+__global__ void k_flags_from_list(const int *__restrict__ idx, int n, int n_pix, const uint8_t *__restrict__ mask,
+                                  const int *__restrict__ pix_tpos, int *__restrict__ flags, unsigned *status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int p = idx[k];
+    if (p < 0 || p >= n_pix) {
+        atomicOr(status, ST_INDEX);
+        return;
+    }
+    if (mask[p]) flags[pix_tpos[p]] = 1;
+}
+
+__global__ void k_compact(const int *__restrict__ flags, const int *__restrict__ pos,
+                          const int *__restrict__ tile_sorted_pix, int n_pix, int *__restrict__ sampled) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pix) return;
+    if (flags[t]) sampled[pos[t]] = tile_sorted_pix[t];
+}
+
+__global__ void k_tile_px_ranges(const int *__restrict__ sampled, const int *n_sampled, int cap,
+                                 const int *__restrict__ pix_tile, int *start, int *end) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = min(*n_sampled, cap);
+    if (s >= n) return;
+    const int t = pix_tile[sampled[s]];
+    if (s == 0 || pix_tile[sampled[s - 1]] != t) start[t] = s;
+    if (s == n - 1 || pix_tile[sampled[s + 1]] != t) end[t] = s + 1;
+}
+
+__global__ void k_set_count(int *dst, int v) { *dst = v; }
+
+// ------------------------------------------------------------------ binning
+constexpr int kSliceChunk = 32;
+
+template <bool EMIT>
+__global__ void __launch_bounds__(128) k_records(BinArgs a) {
+    __shared__ SliceDev ssl[kSliceChunk];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = j < a.N;
+    float mu[3] = {0.f, 0.f, 0.f};
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+    if (live) {
+        mu[0] = a.theta[j];
+        mu[1] = a.theta[a.N + j];
+        mu[2] = a.theta[2 * a.N + j];
+        g0 = a.gpre[2 * j];
+        g1 = a.gpre[2 * j + 1];
+    }
+    int n = 0;
+    const int base = EMIT && live ? a.rec_off[j] : 0;
+    for (int i0 = 0; i0 < a.M; i0 += kSliceChunk) {
+        __syncthreads();
+        const int nc = min(kSliceChunk, a.M - i0);
+        {
+            const int words = nc * (int)(sizeof(SliceDev) / 4);
+            const int *src = reinterpret_cast<const int *>(a.slices + i0);
+            int *dst = reinterpret_cast<int *>(ssl);
+            for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+        }
+        __syncthreads();
+        if (!live) continue;
+        for (int ii = 0; ii < nc; ++ii) {
+            const SliceDev &S = ssl[ii];
+            if (!slab_candidate(g0, g1, mu, S, a.rc2)) continue;
+            RecGeom G;
+            if (!rec_geom(g0, g1, mu, S, a.rc2, a.norm_mode, G)) continue;
+            float cb, ca;
+            int tx0, tx1, ty0, ty1;
+            if (!rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, cb, ca, tx0, tx1, ty0, ty1)) continue;
+            const int nk = count_live_tiles(S, tx0, tx1, ty0, ty1, a.tile_px_start, a.tile_px_end);
+            if (nk == 0) continue;
+            if (EMIT) {
+                const int r = base + n;
+                if (r < a.cap_rec) {
+                    const float L = kNegHalfLog2e;
+                    Rec R;
+                    R.a = make_float4(cb, ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
+                    R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz,
+                                      __int_as_float(i0 + ii));
+                    a.rec[r] = R;
+                    a.rec_tiles[r] = make_int2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+                    a.rec_nkeys[r] = nk;
+                } else {
+                    atomicOr(a.status, ST_CAPACITY);
+                }
+            }
+            ++n;
+        }
+    }
+    if (!EMIT && live) a.rec_cnt[j] = n;
+}
+
+__global__ void k_key_emit(KeyArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_rec = min(*a.n_rec, a.cap_rec);
+    if (r >= n_rec) return;
+    const int i = __float_as_int(a.rec[r].b.w);
+    const SliceDev &S = a.slices[i];
+    const int2 tb = a.rec_tiles[r];
+    const int tx0 = tb.x & 0xffff, tx1 = tb.x >> 16, ty0 = tb.y & 0xffff, ty1 = tb.y >> 16;
+    int k = a.key_off[r];
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const int t = S.tile_base + ty * S.tiles_x + tx;
+            if (a.tile_px_end[t] > a.tile_px_start[t]) {
+                if (k < a.cap_keys) {
+                    a.keys[k] = (uint32_t)t;
+                    a.key_rec[k] = r;
+                } else {
+                    atomicOr(a.status, ST_CAPACITY);
+                }
+                ++k;
+            }
+        }
+}
+
+__global__ void k_tile_rec_ranges(const uint32_t *__restrict__ keys, const int *n_keys, int cap, int *start,
+                                  int *end) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = min(*n_keys, cap);
+    if (s >= n) return;
+    const uint32_t t = keys[s];
+    if (s == 0 || keys[s - 1] != t) start[t] = s;
+    if (s == n - 1 || keys[s + 1] != t) end[t] = s + 1;
+}
+
+__global__ void k_gather(const Rec *__restrict__ rec, const uint32_t *__restrict__ vals,
+                         const int *__restrict__ key_rec, const int *n_keys, int cap, Rec *__restrict__ trec) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = min(*n_keys, cap);
+    if (s >= n) return;
+    const uint32_t k = vals[s];
+    Rec R = rec[key_rec[k]];
+    R.b.w = __int_as_float((int)k);
+    trec[s] = R;
+}
+
+// ----------------------------------------------------------------- forward
+// One CTA per tile, thread per pixel (PX pixels per thread).  The tile's
+// records stream through two shared-memory buffers filled by 1-D bulk copies
+// (cp.async.bulk, completion on an mbarrier); every thread reads each record
+// as a broadcast.  Pixel value = sum_r w_r exp2(q_r(pixel)).
+template <int PX, bool COUNT>
+__global__ void __launch_bounds__(kThreads) k_forward(EvalArgs a) {
+    __shared__ __align__(128) Rec buf[2][kChunk];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double red[kThreads / 32];
+    const int t = blockIdx.x;
+    const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+    if (ps >= pe) {
+        if (threadIdx.x == 0 && !COUNT) a.tile_loss[t] = 0.0;
+        return;
+    }
+    const int rs = a.tile_rec_start[t], re = a.tile_rec_end[t];
+    const int nrec = re - rs;
+    const SliceDev &S = a.slices[a.tile_slice[t]];
+    const float cx0 = S.cx0, cy0 = S.cy0;
+    const int W = S.W, pbase = S.pix_base;
+    float pb[PX], pa[PX], acc[PX];
+    int pix[PX];
+    unsigned long long useful = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        const int s = ps + threadIdx.x + k * kThreads;
+        acc[k] = 0.f;
+        if (s < pe) {
+            const int p = a.sampled[s];
+            const int loc = p - pbase;
+            const int row = loc / W;
+            pix[k] = p;
+            pb[k] = (float)(loc - row * W) - cx0;
+            pa[k] = (float)row - cy0;
+        } else {
+            pix[k] = -1;
+            pb[k] = 0.f;
+            pa[k] = 0.f;
+        }
+    }
+    if (nrec > 0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        const int nch = (nrec + kChunk - 1) / kChunk;
+        const Rec *src = a.trec + rs;
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)min(kChunk, nrec) * (uint32_t)sizeof(Rec);
+            mbar_arrive_expect_tx(&bar[0], bytes);
+            bulk_g2s(&buf[0][0], src, bytes, &bar[0]);
+        }
+        bool ok = true;
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            if (threadIdx.x == 0 && c + 1 < nch) {
+                const int off = (c + 1) * kChunk;
+                const uint32_t bytes = (uint32_t)min(kChunk, nrec - off) * (uint32_t)sizeof(Rec);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar[b ^ 1], bytes);
+                bulk_g2s(&buf[b ^ 1][0], src + off, bytes, &bar[b ^ 1]);
+            }
+            if (!mbar_wait_bounded(&bar[b], (uint32_t)((c >> 1) & 1), kWaitLimitNs)) {
+                atomicOr(a.status, ST_TIMEOUT);
+                ok = false;
+            }
+            const int nin = min(kChunk, nrec - c * kChunk);
+            float part[PX];
+#pragma unroll
+            for (int k = 0; k < PX; ++k) part[k] = 0.f;
+            if (ok && !COUNT) {
+#pragma unroll 4
+                for (int r = 0; r < nin; ++r) {
+                    const float4 r0 = buf[b][r].a;
+                    const float4 r1 = buf[b][r].b;
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        const float dx = pb[k] - r0.x;
+                        const float dy = pa[k] - r0.y;
+                        const float u = fmaf(r0.z, dx, r0.w * dy);
+                        const float q = fmaf(u, dx, r1.x * dy * dy);
+                        part[k] = fmaf(r1.y, ex2_approx(q), part[k]);
+                    }
+                }
+            }
+            if (ok && COUNT) {
+                // pairs whose full exponent (slice-plane part + normal part, log2 units)
+                // is inside the cut
+                for (int r = 0; r < nin; ++r) {
+                    const float4 r0 = buf[b][r].a;
+                    const float4 r1 = buf[b][r].b;
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        const float dx = pb[k] - r0.x;
+                        const float dy = pa[k] - r0.y;
+                        const float u = fmaf(r0.z, dx, r0.w * dy);
+                        const float q = fmaf(u, dx, r1.x * dy * dy);
+                        useful += (pix[k] >= 0 && q + r1.z >= a.qcut) ? 1ull : 0ull;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PX; ++k) acc[k] += part[k];
+            // the barrier also frees buffer b for the copy issued next iteration
+            if (!__syncthreads_and(ok)) {
+                // bounded second waits for copies that may still be in flight, then leave
+                if (threadIdx.x == 0) {
+                    mbar_wait_bounded(&bar[b], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+                    if (c + 1 < nch) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((c + 1) >> 1) & 1), kWaitLimitNs);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0 && !COUNT) a.tile_loss[t] = 0.0;
+                return;
+            }
+        }
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) useful += __shfl_down_sync(0xffffffffu, useful, o);
+        if ((threadIdx.x & 31) == 0 && useful) atomicAdd(a.useful, useful);
+        return;
+    }
+    const int ns = *a.n_sampled;
+    const float wp = 1.0f / (float)max(ns, 1);
+    double l = 0.0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        if (pix[k] >= 0) {
+            const float r = acc[k] - a.I_obs[pix[k]];
+            a.pred[pix[k]] = acc[k];
+            a.rbar[pix[k]] = 2.0f * wp * r;
+            l += (double)(wp * r * r);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+        a.tile_loss[t] = s;
+        const unsigned long long np = (unsigned long long)(pe - ps) * (unsigned long long)nrec;
+        atomicAdd(&a.counters->pairs, np);
+        if (a.pairs_total) atomicAdd(a.pairs_total, np);
+    }
+}
+
+// ---------------------------------------------------------------- backward
+// One CTA per tile, thread per record (two records per thread at a time);
+// the tile's pixels (b, a, r_bar) are broadcast from shared memory.  For each
+// (tile, record) the 6 moments sum_p g, g db, g da, g db^2, g db da, g da^2 with
+// g = r_bar_p exp2(q(p)) are written to the record's key slot (no atomics).
+__global__ void __launch_bounds__(kThreads) k_backward(EvalArgs a) {
+    __shared__ float4 spx[kMaxTilePx];
+    const int t = blockIdx.x;
+    const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+    const int rs = a.tile_rec_start[t], re = a.tile_rec_end[t];
+    if (ps >= pe || rs >= re) return;
+    const SliceDev &S = a.slices[a.tile_slice[t]];
+    const int npx = pe - ps;
+    for (int s = threadIdx.x; s < npx; s += kThreads) {
+        const int p = a.sampled[ps + s];
+        const int loc = p - S.pix_base;
+        const int row = loc / S.W;
+        spx[s] = make_float4((float)(loc - row * S.W) - S.cx0, (float)row - S.cy0, a.rbar[p], 0.f);
+    }
+    __syncthreads();
+    for (int r0 = rs + threadIdx.x; r0 < re; r0 += 2 * kThreads) {
+        const int r1 = r0 + kThreads;
+        const bool v1 = r1 < re;
+        const Rec A = a.trec[r0];
+        const Rec B = v1 ? a.trec[r1] : A;
+        float m0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, m1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int i = 0; i < npx; ++i) {
+            const float4 P = spx[i];
+            {
+                const float dx = P.x - A.a.x, dy = P.y - A.a.y;
+                const float u = fmaf(A.a.z, dx, A.a.w * dy);
+                const float q = fmaf(u, dx, A.b.x * dy * dy);
+                const float g = P.z * ex2_approx(q);
+                const float gx = g * dx, gy = g * dy;
+                m0[0] += g;
+                m0[1] += gx;
+                m0[2] += gy;
+                m0[3] = fmaf(gx, dx, m0[3]);
+                m0[4] = fmaf(gx, dy, m0[4]);
+                m0[5] = fmaf(gy, dy, m0[5]);
+            }
+            {
+                const float dx = P.x - B.a.x, dy = P.y - B.a.y;
+                const float u = fmaf(B.a.z, dx, B.a.w * dy);
+                const float q = fmaf(u, dx, B.b.x * dy * dy);
+                const float g = P.z * ex2_approx(q);
+                const float gx = g * dx, gy = g * dy;
+                m1[0] += g;
+                m1[1] += gx;
+                m1[2] += gy;
+                m1[3] = fmaf(gx, dx, m1[3]);
+                m1[4] = fmaf(gx, dy, m1[4]);
+                m1[5] = fmaf(gy, dy, m1[5]);
+            }
+        }
+        const int k0 = __float_as_int(A.b.w);
+        a.mom[2 * k0] = make_float4(m0[0], m0[1], m0[2], m0[3]);
+        a.mom[2 * k0 + 1] = make_float4(m0[4], m0[5], 0.f, 0.f);
+        if (v1) {
+            const int k1 = __float_as_int(B.b.w);
+            a.mom[2 * k1] = make_float4(m1[0], m1[1], m1[2], m1[3]);
+            a.mom[2 * k1 + 1] = make_float4(m1[4], m1[5], 0.f, 0.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, int n, double *loss,
+                                                      unsigned *status) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += 1024) s += tile_loss[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 32; ++w) tot += red[w];
+        *loss = tot;
+        if (!isfinite(tot)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// ------------------------------------------------------------- gradients
+// dL/d(record) -> dL/d(m, K) -> Gaussian (mu, Sigma_j, c, log det) and slice
+// frame (R_i, t_i).  Moments arrive in slice-centred pixel units about the
+// record centre; all of this is float32 except the frame offsets.
+__global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
+    extern __shared__ float pacc[];  // M x 12 (when use_smem)
+    if (a.use_smem) {
+        for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) pacc[e] = 0.f;
+        __syncthreads();
+    }
+    const int N = a.N;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) {
+        const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
+        const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
+        const float cj = g1.w;
+        const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
+        float gmu[3] = {0.f, 0.f, 0.f};
+        float GS[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float gc = 0.f, glog = 0.f;
+        const int r_end = min(a.rec_off[j + 1], a.cap_rec);
+        for (int r = a.rec_off[j]; r < r_end; ++r) {
+            float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
+            const int k_end = min(a.key_off[r + 1], a.cap_keys);
+            for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
+                const float4 u = a.mom[2 * k], v = a.mom[2 * k + 1];
+                S0 += u.x;
+                Sx += u.y;
+                Sy += u.z;
+                Sxx += u.w;
+                Sxy += v.x;
+                Syy += v.y;
+            }
+            if (S0 == 0.f && Sx == 0.f && Sy == 0.f && Sxx == 0.f && Sxy == 0.f && Syy == 0.f) continue;
+            const int i = __float_as_int(a.rec[r].b.w);
+            const SliceDev &SL = a.slices[i];
+            RecGeom G;
+            if (!rec_geom(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) continue;
+            // moments to slice millimetres
+            const float dx = SL.dx, dy = SL.dy;
+            Sx *= dx;
+            Sy *= dy;
+            Sxx *= dx * dx;
+            Sxy *= dx * dy;
+            Syy *= dy * dy;
+            const float w = cj * G.w0;
+            const float Gw = S0 * w;  // dL/d log w
+            gc += S0 * G.w0;
+            // centre: dL/dc = w P2 S1
+            const float Gcx = w * (G.P2xx * Sx + G.P2xy * Sy);
+            const float Gcy = w * (G.P2xy * Sx + G.P2yy * Sy);
+            // conic: dL/dP2 = -1/2 w S2 -> dL/dM2 = 1/2 w P2 S2 P2
+            const float T00 = G.P2xx * Sxx + G.P2xy * Sxy, T01 = G.P2xx * Sxy + G.P2xy * Syy;
+            const float T10 = G.P2xy * Sxx + G.P2yy * Sxy, T11 = G.P2xy * Sxy + G.P2yy * Syy;
+            const float GMxx = 0.5f * w * (T00 * G.P2xx + T01 * G.P2xy);
+            const float GMxy = 0.5f * w * (T00 * G.P2xy + T01 * G.P2yy);
+            const float GMyy = 0.5f * w * (T10 * G.P2xy + T11 * G.P2yy);
+            const float ik = 1.0f / G.Kzz, kx = G.Kxz, ky = G.Kyz;
+            const float mz = (float)G.mz;
+            // M2 = K_xy - k k^T / K_zz
+            const float Mk0 = GMxx * kx + GMxy * ky, Mk1 = GMxy * kx + GMyy * ky;
+            float Gkx = -2.f * Mk0 * ik, Gky = -2.f * Mk1 * ik;
+            float Gkap = (kx * Mk0 + ky * Mk1) * ik * ik;
+            // centre c = m_xy - k m_z / K_zz
+            const float kGc = kx * Gcx + ky * Gcy;
+            float Gmz = -kGc * ik;
+            Gkx -= Gcx * mz * ik;
+            Gky -= Gcy * mz * ik;
+            Gkap += kGc * mz * ik * ik;
+            // z weight exp(-1/2 m_z^2 / K_zz)
+            Gmz -= Gw * mz * ik;
+            Gkap += 0.5f * Gw * mz * mz * ik * ik;
+            float GK[9] = {GMxx, GMxy, 0.5f * Gkx, GMxy, GMyy, 0.5f * Gky, 0.5f * Gkx, 0.5f * Gky, Gkap};
+            if (a.norm_mode == GSVR_NORM_EXACT) {
+                // -1/2 log det K -> -1/2 Gw K^-1 ; 1/2 log det Sigma_j = sum ls -> d ls_k += Gw
+                const float c00 = G.Kyy * G.Kzz - G.Kyz * G.Kyz, c01 = G.Kxz * G.Kyz - G.Kxy * G.Kzz;
+                const float c02 = G.Kxy * G.Kyz - G.Kxz * G.Kyy, c11 = G.Kxx * G.Kzz - G.Kxz * G.Kxz;
+                const float c12 = G.Kxy * G.Kxz - G.Kxx * G.Kyz, c22 = G.Kxx * G.Kyy - G.Kxy * G.Kxy;
+                const float idK = 1.0f / (G.Kxx * c00 + G.Kxy * c01 + G.Kxz * c02);
+                const float h = -0.5f * Gw * idK;
+                GK[0] += h * c00;
+                GK[1] += h * c01;
+                GK[2] += h * c02;
+                GK[3] += h * c01;
+                GK[4] += h * c11;
+                GK[5] += h * c12;
+                GK[6] += h * c02;
+                GK[7] += h * c12;
+                GK[8] += h * c22;
+                glog += Gw;
+            }
+            const float Gm[3] = {Gcx, Gcy, Gmz};
+            const float *R = G.R;
+            // mu: R Gm ; Sigma_j: R GK R^T
+            float RGm[3];
+            for (int p = 0; p < 3; ++p) RGm[p] = R[3 * p] * Gm[0] + R[3 * p + 1] * Gm[1] + R[3 * p + 2] * Gm[2];
+            for (int p = 0; p < 3; ++p) gmu[p] += RGm[p];
+            float RG[9];
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                    RG[3 * p + q] = R[3 * p] * GK[q] + R[3 * p + 1] * GK[3 + q] + R[3 * p + 2] * GK[6 + q];
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                    GS[3 * p + q] += RG[3 * p] * R[3 * q] + RG[3 * p + 1] * R[3 * q + 1] + RG[3 * p + 2] * R[3 * q + 2];
+            // slice frame: t -> -R Gm ; R -> d Gm^T + 2 Sigma_j R GK
+            float GR[12];
+            for (int p = 0; p < 3; ++p) {
+                const float dp = (float)G.d[p];
+                for (int q = 0; q < 3; ++q) {
+                    float s = Sg[3 * p] * RG[q] + Sg[3 * p + 1] * RG[3 + q] + Sg[3 * p + 2] * RG[6 + q];
+                    GR[3 * p + q] = dp * Gm[q] + 2.f * s;
+                }
+                GR[9 + p] = -RGm[p];
+            }
+            if (a.use_smem) {
+                for (int e = 0; e < 12; ++e) atomicAdd(&pacc[12 * i + e], GR[e]);
+            } else {
+                for (int e = 0; e < 12; ++e) atomicAdd(&a.pose_acc[12 * i + e], (double)GR[e]);
+            }
+        }
+        // Sigma_j = Rj diag(s^2) Rj^T -> ls, q (through q / |q|)
+        const float qw = a.theta[6 * N + j], qx = a.theta[7 * N + j], qy = a.theta[8 * N + j], qz = a.theta[9 * N + j];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
+        float Rj[9];
+        quat_rot(w, x, y, z, Rj);
+        const float s2[3] = {expf(2.f * a.theta[3 * N + j]), expf(2.f * a.theta[4 * N + j]),
+                             expf(2.f * a.theta[5 * N + j])};
+        float GRj[9];  // GS Rj
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q)
+                GRj[3 * p + q] = GS[3 * p] * Rj[q] + GS[3 * p + 1] * Rj[3 + q] + GS[3 * p + 2] * Rj[6 + q];
+        float dls[3];
+        for (int k = 0; k < 3; ++k) {
+            const float d = Rj[k] * GRj[k] + Rj[3 + k] * GRj[3 + k] + Rj[6 + k] * GRj[6 + k];
+            dls[k] = 2.f * s2[k] * d + glog;
+        }
+        float GRD[9];  // dL/dRj = 2 GS Rj D
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) GRD[3 * p + q] = 2.f * GRj[3 * p + q] * s2[q];
+        const float dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+        const float dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+        const float dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+        const float dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+        float gq[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = 0; e < 9; ++e) {
+            gq[0] += GRD[e] * dRw[e];
+            gq[1] += GRD[e] * dRx[e];
+            gq[2] += GRD[e] * dRy[e];
+            gq[3] += GRD[e] * dRz[e];
+        }
+        const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+        float *g = a.grad;
+        g[j] = gmu[0];
+        g[N + j] = gmu[1];
+        g[2 * N + j] = gmu[2];
+        g[3 * N + j] = dls[0];
+        g[4 * N + j] = dls[1];
+        g[5 * N + j] = dls[2];
+        g[6 * N + j] = (gq[0] - w * dot) / qn;
+        g[7 * N + j] = (gq[1] - x * dot) / qn;
+        g[8 * N + j] = (gq[2] - y * dot) / qn;
+        g[9 * N + j] = (gq[3] - z * dot) / qn;
+        g[10 * N + j] = gc;
+    }
+    if (a.use_smem) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) {
+            const float v = pacc[e];
+            if (v != 0.f) atomicAdd(&a.pose_acc[e], (double)v);
+        }
+    }
+}
+
+// (R_i, t_i) gradients -> (r, tau): dL/dRod = G_R R0^T + G_t c0^T, and
+// dRod/dr_k from the exponential-map derivative of Gallego & Yezzi (2015):
+// dR/dr_k = ((r_k [r]x + [r x (I - R) e_k]x) / |r|^2) R, with the first-order
+// series [e_k]x + (E_k K + K E_k)/2 near r = 0.
+__global__ void k_pose_grad(const double *__restrict__ acc, const SliceStatic *__restrict__ ss,
+                            const float *__restrict__ pose, float *__restrict__ gpose, int M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double *A = acc + 12 * i;
+    const SliceStatic s = ss[i];
+    double G[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            G[3 * a + b] = A[3 * a] * s.R0[3 * b] + A[3 * a + 1] * s.R0[3 * b + 1] + A[3 * a + 2] * s.R0[3 * b + 2] +
+                           A[9 + a] * s.c0[b];
+    const double r[3] = {pose[6 * i], pose[6 * i + 1], pose[6 * i + 2]};
+    const double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    double Rr[9];
+    rodrigues_d(r, Rr);
+    const double K[9] = {0.0, -r[2], r[1], r[2], 0.0, -r[0], -r[1], r[0], 0.0};
+    for (int k = 0; k < 3; ++k) {
+        double D[9];
+        const double e[3] = {k == 0 ? 1.0 : 0.0, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0};
+        const double E[9] = {0.0, -e[2], e[1], e[2], 0.0, -e[0], -e[1], e[0], 0.0};
+        if (th2 < 1e-14) {
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double ek = 0.0, ke = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        ek += E[3 * a + c] * K[3 * c + b];
+                        ke += K[3 * a + c] * E[3 * c + b];
+                    }
+                    D[3 * a + b] = E[3 * a + b] + 0.5 * (ek + ke);
+                }
+        } else {
+            double v[3];  // (I - R) e_k
+            for (int a = 0; a < 3; ++a) v[a] = e[a] - Rr[3 * a + k];
+            const double c[3] = {r[1] * v[2] - r[2] * v[1], r[2] * v[0] - r[0] * v[2], r[0] * v[1] - r[1] * v[0]};
+            const double S[9] = {0.0, -c[2], c[1], c[2], 0.0, -c[0], -c[1], c[0], 0.0};
+            double Bm[9];
+            for (int e2 = 0; e2 < 9; ++e2) Bm[e2] = (r[k] * K[e2] + S[e2]) / th2;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    D[3 * a + b] = Bm[3 * a] * Rr[b] + Bm[3 * a + 1] * Rr[3 + b] + Bm[3 * a + 2] * Rr[6 + b];
+        }
+        double g = 0.0;
+        for (int e2 = 0; e2 < 9; ++e2) g += G[e2] * D[e2];
+        gpose[6 * i + k] = (float)g;
+        gpose[6 * i + 3 + k] = (float)A[9 + k];
+    }
+}
+
+__global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int N, int M, float lr0, float lr1, float lr2, float lr3, float lr4,
+                       float lr5, float b1, float b2, float eps, float ibc1, float ibc2,
+                       const uint8_t *__restrict__ frozen) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = 11LL * N + 6LL * M;
+    if (e >= n) return;
+    float lr;
+    if (e < 3LL * N) lr = lr0;
+    else if (e < 6LL * N) lr = lr1;
+    else if (e < 10LL * N) lr = lr2;
+    else if (e < 11LL * N) lr = lr3;
+    else {
+        const int64_t o = e - 11LL * N;
+        if (frozen && frozen[o / 6]) return;
+        lr = (o % 6) < 3 ? lr4 : lr5;
+    }
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    th[e] -= lr * (mi * ibc1) / (sqrtf(vi * ibc2) + eps);
+}
+
+inline int cdiv(int64_t a, int b) { return (int)((a + b - 1) / b); }
+
+std::atomic<long long> g_launches{0};
+inline void counted(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace
+
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ launchers
+void launch_gauss_prep(const float *theta, int N, float4 *gpre, unsigned *status, cudaStream_t st) {
+    if (N <= 0) return;
+    k_gauss_prep<<<cdiv(N, 256), 256, 0, st>>>(theta, N, gpre, status);
+    counted();
+}
+void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, int M, unsigned *status,
+                      cudaStream_t st) {
+    if (M <= 0) return;
+    k_pose_prep<<<cdiv(M, 128), 128, 0, st>>>(pose, ss, sd, M, status);
+    counted();
+}
+void launch_rec_count(const BinArgs &a, cudaStream_t st) {
+    if (a.N <= 0) return;
+    k_records<false><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    counted();
+}
+void launch_rec_emit(const BinArgs &a, cudaStream_t st) {
+    if (a.N <= 0) return;
+    k_records<true><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    counted();
+}
+void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st) {
+    if (n_rec_max <= 0) return;
+    k_key_emit<<<cdiv(n_rec_max, 256), 256, 0, st>>>(a);
+    counted();
+}
+void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int *start, int *end,
+                            cudaStream_t st) {
+    if (cap_keys <= 0) return;
+    k_tile_rec_ranges<<<cdiv(cap_keys, 256), 256, 0, st>>>(keys, n_keys, cap_keys, start, end);
+    counted();
+}
+void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, const int *n_keys, int cap_keys,
+                   Rec *trec, cudaStream_t st) {
+    if (cap_keys <= 0) return;
+    k_gather<<<cdiv(cap_keys, 256), 256, 0, st>>>(rec, vals, key_rec, n_keys, cap_keys, trec);
+    counted();
+}
+template <bool COUNT>
+static void forward_variant(const EvalArgs &a, int tile_px, cudaStream_t st) {
+    if (a.n_tiles <= 0) return;
+    if (tile_px <= kThreads) k_forward<1, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
+    else if (tile_px <= 2 * kThreads) k_forward<2, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
+    else if (tile_px <= 4 * kThreads) k_forward<4, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
+    else k_forward<8, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
+    counted();
+}
+void launch_forward(const EvalArgs &a, int tile_px, cudaStream_t st) { forward_variant<false>(a, tile_px, st); }
+void launch_count_pairs(const EvalArgs &a, int tile_px, cudaStream_t st) { forward_variant<true>(a, tile_px, st); }
+void launch_backward(const EvalArgs &a, cudaStream_t st) {
+    if (a.n_tiles <= 0) return;
+    k_backward<<<a.n_tiles, kThreads, 0, st>>>(a);
+    counted();
+}
+void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st) {
+    k_loss_reduce<<<1, 1024, 0, st>>>(tile_loss, n_tiles, loss, status);
+    counted();
+}
+void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
+    if (a.N <= 0) return;
+    const size_t smem = a.use_smem ? (size_t)a.M * 12 * sizeof(float) : 0;
+    k_gauss_grad<<<cdiv(a.N, 128), 128, smem, st>>>(a);
+    counted();
+}
+void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
+                      cudaStream_t st) {
+    if (M <= 0) return;
+    k_pose_grad<<<cdiv(M, 64), 64, 0, st>>>(pose_acc, ss, pose, grad_pose, M);
+    counted();
+}
+void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
+                 float b2, float eps, double bc1, double bc2, const uint8_t *frozen, cudaStream_t st) {
+    const int64_t n = 11LL * N + 6LL * M;
+    if (n <= 0) return;
+    k_adam<<<cdiv(n, 256), 256, 0, st>>>(theta, grad, m, v, N, M, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], b1, b2,
+                                         eps, (float)(1.0 / bc1), (float)(1.0 / bc2), frozen);
+    counted();
+}
+void launch_sample_flags(int n_mask, int n_s, const SamplerKeys &sk, const int *mask_tpos, int *flags,
+                         cudaStream_t st) {
+    if (n_s <= 0) return;
+    k_sample_flags<<<cdiv(n_s, 256), 256, 0, st>>>(n_mask, n_s, sk, mask_tpos, flags);
+    counted();
+}
+void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mask, const int *pix_tpos,
+                            int *flags, unsigned *status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_flags_from_list<<<cdiv(n, 256), 256, 0, st>>>(idx, n, n_pix, mask, pix_tpos, flags, status);
+    counted();
+}
+void launch_compact(const int *flags, const int *pos, const int *tile_sorted_pix, int n_pix, int *sampled,
+                    cudaStream_t st) {
+    if (n_pix <= 0) return;
+    k_compact<<<cdiv(n_pix, 256), 256, 0, st>>>(flags, pos, tile_sorted_pix, n_pix, sampled);
+    counted();
+}
+void launch_tile_px_ranges(const int *sampled, const int *n_sampled, int cap, const int *pix_tile, int *start,
+                           int *end, cudaStream_t st) {
+    if (cap <= 0) return;
+    k_tile_px_ranges<<<cdiv(cap, 256), 256, 0, st>>>(sampled, n_sampled, cap, pix_tile, start, end);
+    counted();
+}
+void launch_set_count(int *dst, int v, cudaStream_t st) {
+    k_set_count<<<1, 1, 0, st>>>(dst, v);
+    counted();
+}
+void note_launches(int n) { counted(n); }
+
+}  // namespace gsvr

@@ -1,0 +1,112 @@
+// gsvr_launch.cuh -- argument blocks and host launchers of the libgsvr kernels.
+#pragma once
+#include "gsvr_internal.cuh"
+
+namespace gsvr {
+
+struct BinArgs {
+    const float *theta;        // 11N + 6M
+    const float4 *gpre;        // 2 per Gaussian: (Sxx, Syy, Szz, Sxy), (Sxz, Syz, sum ls, c)
+    const SliceDev *slices;
+    int N, M;
+    float rc2;                 // squared Mahalanobis cut: 2 ln(1 / cutoff_rel)
+    int norm_mode;
+    int tile_w, tile_h;
+    const int *tile_px_start, *tile_px_end;
+    int *rec_cnt;              // per Gaussian (count pass)
+    const int *rec_off;        // per Gaussian (emit pass), N + 1
+    Rec *rec;                  // emit pass
+    int2 *rec_tiles;           // packed tile bounding box per record
+    int *rec_nkeys;            // keys per record
+    int cap_rec;
+    unsigned *status;
+};
+
+struct KeyArgs {
+    const Rec *rec;
+    const int2 *rec_tiles;
+    const int *key_off;        // n_rec + 1
+    const SliceDev *slices;
+    const int *tile_px_start, *tile_px_end;
+    const int *n_rec;          // device count
+    int cap_rec, cap_keys;
+    uint32_t *keys;
+    int *key_rec;
+    unsigned *status;
+};
+
+struct EvalArgs {
+    const Rec *trec;           // records in sorted (tile, Gaussian) order, slot b.w = emit index
+    const int *tile_rec_start, *tile_rec_end;
+    const int *tile_px_start, *tile_px_end;
+    const int *tile_slice;
+    const SliceDev *slices;
+    const int *sampled;        // global pixel index, tile order
+    const int *n_sampled;
+    const float *I_obs;        // per global pixel
+    float *pred, *rbar;        // per global pixel
+    double *tile_loss;         // per tile
+    float4 *mom;               // 2 per key (backward)
+    Counters *counters;
+    unsigned long long *pairs_total;  // running sum of visited pairs (timing)
+    unsigned long long *useful;       // count mode: pairs inside the cut
+    float qcut;                       // count mode: log2(cutoff_rel)
+    int n_tiles;
+    unsigned *status;
+};
+
+struct GradArgs {
+    const float *theta;
+    const float4 *gpre;
+    const SliceDev *slices;
+    const Rec *rec;            // j-major records, slot b.w = slice index
+    const int *rec_off;        // N + 1
+    const int *key_off;        // n_rec + 1
+    const float4 *mom;         // 2 per key in emit order
+    int N, M;
+    float rc2;
+    int norm_mode;
+    float *grad;               // 11N + 6M
+    double *pose_acc;          // M x 12: dL/dR_i (9), dL/dt_i (3)
+    int use_smem;
+    int cap_rec, cap_keys;     // reads stay inside the buffers even after an overflow
+};
+
+void launch_gauss_prep(const float *theta, int N, float4 *gpre, unsigned *status, cudaStream_t st);
+void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, int M, unsigned *status,
+                      cudaStream_t st);
+void launch_rec_count(const BinArgs &a, cudaStream_t st);
+void launch_rec_emit(const BinArgs &a, cudaStream_t st);
+void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st);
+void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int *start, int *end,
+                            cudaStream_t st);
+void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, const int *n_keys, int cap_keys,
+                   Rec *trec, cudaStream_t st);
+void launch_forward(const EvalArgs &a, int tile_px, cudaStream_t st);
+void launch_count_pairs(const EvalArgs &a, int tile_px, cudaStream_t st);
+long long launch_count();  // kernels launched by this library so far
+void note_launches(int n); // count kernels launched from other translation units
+void launch_backward(const EvalArgs &a, cudaStream_t st);
+void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st);
+void launch_gauss_grad(const GradArgs &a, cudaStream_t st);
+void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
+                      cudaStream_t st);
+void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
+                 float b2, float eps, double bc1, double bc2, const uint8_t *frozen, cudaStream_t st);
+
+// Sampler: round keys and multipliers of the 4-round bijection on k bits.
+struct SamplerKeys {
+    unsigned long long xk[4], mul[4];
+    int k, h;
+};
+void launch_sample_flags(int n_mask, int n_s, const SamplerKeys &sk, const int *mask_tpos, int *flags,
+                         cudaStream_t st);
+void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mask, const int *pix_tpos,
+                            int *flags, unsigned *status, cudaStream_t st);
+void launch_compact(const int *flags, const int *pos, const int *tile_sorted_pix, int n_pix, int *sampled,
+                    cudaStream_t st);
+void launch_tile_px_ranges(const int *sampled, const int *n_sampled, int cap, const int *pix_tile, int *start,
+                           int *end, cudaStream_t st);
+void launch_set_count(int *dst, int v, cudaStream_t st);
+
+}  // namespace gsvr

@@ -1,0 +1,365 @@
+"""ctypes binding of libgsvr.so, with the names of the C ABI (include/gsvr.h).
+
+Argument marshalling only: every step of the forward model, the adjoint and
+the optimiser runs in the library's CUDA kernels.  Importing this module loads
+the library and raises ImportError when it is missing -- there is no fallback.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); the binding passes the pointer and the matching GSVR_MEM_* kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsvr.so")
+
+GSVR_OK = 0
+STATUS_NAMES = {0: "GSVR_OK", 1: "GSVR_ERR_INVALID_ARG", 2: "GSVR_ERR_CUDA", 3: "GSVR_ERR_CAPACITY",
+                4: "GSVR_ERR_NONFINITE", 5: "GSVR_ERR_TIMEOUT", 6: "GSVR_ERR_STATE", 7: "GSVR_ERR_NOMEM"}
+GSVR_MEM_HOST, GSVR_MEM_DEVICE = 0, 1
+GSVR_NORM_EXACT, GSVR_NORM_LITERAL = 0, 1
+
+EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy", "gsvr_set_stacks",
+           "gsvr_set_observations", "gsvr_set_gaussians", "gsvr_set_poses", "gsvr_set_frozen",
+           "gsvr_set_pixel_sample", "gsvr_sample_pixels", "gsvr_forward", "gsvr_backward", "gsvr_adam_step",
+           "gsvr_step_host", "gsvr_get_sample", "gsvr_get_views", "gsvr_get_stats", "gsvr_sync_status",
+           "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs"]
+STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
+
+
+class GsvrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class StackDesc(C.Structure):
+    _fields_ = [("n_slices", C.c_int32), ("H", C.c_int32), ("W", C.c_int32), ("reserved", C.c_int32),
+                ("dx", C.c_float), ("dy", C.c_float), ("thickness", C.c_float), ("R", C.c_float * 9),
+                ("origin", C.c_float * 3), ("fwhm", C.c_float * 3)]
+
+
+class Config(C.Structure):
+    _fields_ = [("cutoff_rel", C.c_float), ("tile_h", C.c_int32), ("tile_w", C.c_int32), ("norm_mode", C.c_int32),
+                ("fixed_capacity", C.c_int32), ("timing", C.c_int32), ("cap_records", C.c_int64),
+                ("cap_keys", C.c_int64), ("seed", C.c_uint64)]
+
+
+class AdamCfg(C.Structure):
+    _fields_ = [("lr_mu", C.c_float), ("lr_ls", C.c_float), ("lr_q", C.c_float), ("lr_c", C.c_float),
+                ("lr_rot", C.c_float), ("lr_trans", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("reserved", C.c_int32)]
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("calls", C.c_int64 * 8), ("pairs_evaluated", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+class Views(C.Structure):
+    _fields_ = [("theta", C.c_void_p), ("grad", C.c_void_p), ("adam_m", C.c_void_p), ("adam_v", C.c_void_p),
+                ("pred", C.c_void_p), ("rbar", C.c_void_p), ("loss", C.c_void_p), ("n_gauss", C.c_int64),
+                ("n_slices", C.c_int64), ("n_pixels", C.c_int64), ("n_params", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_sampled", C.c_int64), ("n_records", C.c_int64), ("n_keys", C.c_int64),
+                ("pairs_evaluated", C.c_int64), ("n_tiles", C.c_int64), ("tile_px_max", C.c_int64),
+                ("cap_records", C.c_int64), ("cap_keys", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgsvr.so is not built (run __graft_entry__.build() or "
+                          "python paper_2512_11624_b300/csrc/build.py); there is no fallback")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "gsvr_abi_version": ([], i32),
+        "gsvr_last_error": ([vp], C.c_char_p),
+        "gsvr_create": ([C.POINTER(vp), C.c_int, vp, C.POINTER(Config)], C.c_int),
+        "gsvr_destroy": ([vp], C.c_int),
+        "gsvr_set_stacks": ([vp, i32, C.POINTER(StackDesc)], C.c_int),
+        "gsvr_set_observations": ([vp, vp, vp, i32], C.c_int),
+        "gsvr_set_gaussians": ([vp, i64, vp, i32], C.c_int),
+        "gsvr_set_poses": ([vp, vp, i32], C.c_int),
+        "gsvr_set_frozen": ([vp, vp], C.c_int),
+        "gsvr_set_pixel_sample": ([vp, vp, i64, i32], C.c_int),
+        "gsvr_sample_pixels": ([vp, i64, u64], C.c_int),
+        "gsvr_forward": ([vp], C.c_int),
+        "gsvr_backward": ([vp], C.c_int),
+        "gsvr_adam_step": ([vp, C.POINTER(AdamCfg), i64], C.c_int),
+        "gsvr_step_host": ([vp, vp, vp, i64, vp, vp], C.c_int),
+        "gsvr_get_sample": ([vp, vp, i64, C.POINTER(i64)], C.c_int),
+        "gsvr_get_views": ([vp, C.POINTER(Views)], C.c_int),
+        "gsvr_get_stats": ([vp, C.POINTER(Stats)], C.c_int),
+        "gsvr_sync_status": ([vp], C.c_int),
+        "gsvr_timing_reset": ([vp], C.c_int),
+        "gsvr_get_kernel_times": ([vp, C.POINTER(KernelTimes)], C.c_int),
+        "gsvr_count_pairs": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(ctx, status):
+    if status != GSVR_OK:
+        raise GsvrError(status, gsvr_last_error(ctx))
+    return status
+
+
+def _ptr(a):
+    """(pointer, mem kind, keep-alive) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, GSVR_MEM_HOST, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, GSVR_MEM_HOST, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        a = a.contiguous()
+        return a.data_ptr(), (GSVR_MEM_DEVICE if a.is_cuda else GSVR_MEM_HOST), a
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _typed(a, np_dtype, torch_dtype_name):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np_dtype)
+    import torch
+    dt = getattr(torch, torch_dtype_name)
+    return a.to(dt).contiguous() if a.dtype != dt else a.contiguous()
+
+
+# ------------------------------------------------------------------ C ABI names
+def gsvr_abi_version():
+    return int(lib.gsvr_abi_version())
+
+
+def gsvr_last_error(ctx=None):
+    s = lib.gsvr_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def gsvr_create(device=0, stream=None, cutoff_rel=1e-7, tile_h=16, tile_w=16, norm_mode=GSVR_NORM_EXACT,
+                fixed_capacity=0, cap_records=0, cap_keys=0, seed=0, timing=0):
+    cfg = Config(cutoff_rel, tile_h, tile_w, norm_mode, fixed_capacity, timing, cap_records, cap_keys, seed)
+    out = C.c_void_p()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    _check(None, lib.gsvr_create(C.byref(out), int(device), C.c_void_p(int(stream)), C.byref(cfg)))
+    return out
+
+
+def gsvr_destroy(ctx):
+    return _check(ctx, lib.gsvr_destroy(ctx))
+
+
+def stack_descs(stacks):
+    arr = (StackDesc * len(stacks))()
+    for k, s in enumerate(stacks):
+        d = arr[k]
+        d.n_slices, d.H, d.W = int(s["n_slices"]), int(s["H"]), int(s["W"])
+        d.dx, d.dy, d.thickness = float(s["dx"]), float(s["dy"]), float(s["thickness"])
+        R = np.asarray(s["R"], np.float64).reshape(9)
+        for e in range(9):
+            d.R[e] = float(R[e])
+        for e in range(3):
+            d.origin[e] = float(s["origin"][e])
+            d.fwhm[e] = float(s["fwhm"][e])
+    return arr
+
+
+def gsvr_set_stacks(ctx, stacks):
+    arr = stack_descs(stacks)
+    return _check(ctx, lib.gsvr_set_stacks(ctx, len(stacks), arr))
+
+
+def gsvr_set_observations(ctx, I, mask=None):
+    I = _typed(I, np.float32, "float32")
+    pI, mem, kI = _ptr(I)
+    pm = None
+    if mask is not None:
+        mask = _typed(mask, np.uint8, "uint8")
+        pm, mem_m, km = _ptr(mask)
+        if mem_m != mem:
+            raise ValueError("I and mask must live in the same memory")
+    return _check(ctx, lib.gsvr_set_observations(ctx, pI, pm, mem))
+
+
+def gsvr_set_gaussians(ctx, N, theta_g):
+    t = _typed(theta_g, np.float32, "float32")
+    p, mem, k = _ptr(t)
+    return _check(ctx, lib.gsvr_set_gaussians(ctx, int(N), p, mem))
+
+
+def gsvr_set_poses(ctx, pose):
+    t = _typed(pose, np.float32, "float32")
+    p, mem, k = _ptr(t)
+    return _check(ctx, lib.gsvr_set_poses(ctx, p, mem))
+
+
+def gsvr_set_frozen(ctx, frozen=None):
+    if frozen is None:
+        return _check(ctx, lib.gsvr_set_frozen(ctx, None))
+    f = np.ascontiguousarray(frozen, dtype=np.uint8)
+    return _check(ctx, lib.gsvr_set_frozen(ctx, f.ctypes.data))
+
+
+def gsvr_set_pixel_sample(ctx, idx=None):
+    if idx is None:
+        return _check(ctx, lib.gsvr_set_pixel_sample(ctx, None, -1, GSVR_MEM_HOST))
+    t = _typed(idx, np.int32, "int32")
+    p, mem, k = _ptr(t)
+    n = int(t.shape[0]) if hasattr(t, "shape") else len(t)
+    return _check(ctx, lib.gsvr_set_pixel_sample(ctx, p, n, mem))
+
+
+def gsvr_sample_pixels(ctx, n, step):
+    return _check(ctx, lib.gsvr_sample_pixels(ctx, int(n), C.c_uint64(int(step))))
+
+
+def gsvr_forward(ctx):
+    return _check(ctx, lib.gsvr_forward(ctx))
+
+
+def gsvr_backward(ctx):
+    return _check(ctx, lib.gsvr_backward(ctx))
+
+
+PAPER_LR = dict(lr_mu=2.5e-2, lr_ls=2.5e-2, lr_q=1e-2, lr_c=1e-2, lr_rot=2.5e-3, lr_trans=1e-1)
+
+
+def gsvr_adam_step(ctx, step, lr=None, beta1=0.9, beta2=0.999, eps=1e-8):
+    lr = dict(PAPER_LR, **(lr or {}))
+    cfg = AdamCfg(lr["lr_mu"], lr["lr_ls"], lr["lr_q"], lr["lr_c"], lr["lr_rot"], lr["lr_trans"], beta1, beta2,
+                  eps, 0)
+    return _check(ctx, lib.gsvr_adam_step(ctx, C.byref(cfg), int(step)))
+
+
+def gsvr_step_host(ctx, theta, idx, grad_out=None, loss_out=None):
+    """theta, idx, grad_out, loss_out: host arrays (numpy or pinned CPU tensors)."""
+    pt, mt, kt = _ptr(theta)
+    if idx is None:
+        pi, n, ki = None, -1, None
+    else:
+        pi, mi, ki = _ptr(idx)
+        n = int(idx.shape[0])
+    pg, _, kg = _ptr(grad_out)
+    pl, _, kl = _ptr(loss_out)
+    return _check(ctx, lib.gsvr_step_host(ctx, pt, pi, n, pg, pl))
+
+
+def gsvr_get_sample(ctx):
+    n = C.c_int64()
+    _check(ctx, lib.gsvr_get_sample(ctx, None, 0, C.byref(n)))
+    out = np.zeros(max(int(n.value), 1), np.int32)
+    _check(ctx, lib.gsvr_get_sample(ctx, out.ctypes.data, out.size, C.byref(n)))
+    return out[:int(n.value)]
+
+
+def gsvr_get_views(ctx):
+    v = Views()
+    _check(ctx, lib.gsvr_get_views(ctx, C.byref(v)))
+    return v
+
+
+def gsvr_get_stats(ctx):
+    s = Stats()
+    _check(ctx, lib.gsvr_get_stats(ctx, C.byref(s)))
+    return {f: int(getattr(s, f)) for f, _ in Stats._fields_}
+
+
+def gsvr_sync_status(ctx):
+    return _check(ctx, lib.gsvr_sync_status(ctx))
+
+
+def gsvr_timing_reset(ctx):
+    return _check(ctx, lib.gsvr_timing_reset(ctx))
+
+
+def gsvr_get_kernel_times(ctx):
+    t = KernelTimes()
+    _check(ctx, lib.gsvr_get_kernel_times(ctx, C.byref(t)))
+    return {"ms": {STAGES[k]: float(t.ms[k]) for k in range(7)},
+            "calls": {STAGES[k]: int(t.calls[k]) for k in range(7)},
+            "pairs_evaluated": int(t.pairs_evaluated), "kernel_launches": int(t.kernel_launches)}
+
+
+def gsvr_count_pairs(ctx):
+    u, e = C.c_int64(), C.c_int64()
+    _check(ctx, lib.gsvr_count_pairs(ctx, C.byref(u), C.byref(e)))
+    return int(u.value), int(e.value)
+
+
+# --------------------------------------------------------------- torch views
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def device_view(ptr, n, dtype="float32", device=0):
+    """Zero-copy torch view of a context-owned device buffer."""
+    import torch
+    ts = {"float32": "<f4", "float64": "<f8"}[dtype]
+    return torch.as_tensor(_CudaArray(ptr, (int(n),), ts), device="cuda:%d" % device)
+
+
+class Context:
+    """Owning wrapper: one gsvr context set up from a case dictionary
+    (``stacks``, ``N``, ``theta``, ``I``, ``mask``) as made by the input generators."""
+
+    def __init__(self, case, device=0, stream=None, **cfg):
+        self.device = device
+        self.ctx = gsvr_create(device, stream, **cfg)
+        self.N = int(case["N"])
+        self.stacks = case["stacks"]
+        gsvr_set_stacks(self.ctx, self.stacks)
+        gsvr_set_observations(self.ctx, np.asarray(case["I"], np.float32), np.asarray(case["mask"], np.uint8))
+        th = np.asarray(case["theta"], np.float32)
+        gsvr_set_gaussians(self.ctx, self.N, th[:11 * self.N])
+        self.M = int(sum(s["n_slices"] for s in self.stacks))
+        gsvr_set_poses(self.ctx, th[11 * self.N:11 * self.N + 6 * self.M])
+        v = gsvr_get_views(self.ctx)
+        self.n_params = int(v.n_params)
+        self.n_pixels = int(v.n_pixels)
+        self.theta = device_view(v.theta, v.n_params, device=device)
+        self.grad = device_view(v.grad, v.n_params, device=device)
+        self.pred = device_view(v.pred, v.n_pixels, device=device)
+        self.rbar = device_view(v.rbar, v.n_pixels, device=device)
+        self.loss_t = device_view(v.loss, 1, "float64", device=device)
+
+    def forward(self):
+        gsvr_forward(self.ctx)
+
+    def backward(self):
+        gsvr_backward(self.ctx)
+
+    def loss(self):
+        gsvr_sync_status(self.ctx)
+        return float(self.loss_t.item())
+
+    def stats(self):
+        return gsvr_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            gsvr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

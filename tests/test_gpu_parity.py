@@ -1,0 +1,306 @@
+"""CUDA path (through the C ABI) against the FP64 brute-force oracle.
+
+Forward values within 1e-5 relative (floored at 1e-3 of the case maximum),
+gradients within 1e-4 relative plus a float32 rounding floor proportional to
+the sum of term magnitudes (see gpu_util).  Cases span several tiles, ragged
+slice sizes, oblique stacks with motion, both normalisations, tile shapes,
+sample lists with duplicates and masked pixels, empty inputs, and the full
+fetal-scale workload on sampled pixels.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_11624_b300 import inputs
+from tests.gpu_util import describe_grad, forward_ok, grad_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11624_b300 import gsvr
+    return gsvr
+
+
+def run_gpu(G, case, sample=None, **cfg):
+    ctx = G.Context(case, **cfg)
+    if sample is not None:
+        G.gsvr_set_pixel_sample(ctx.ctx, np.asarray(sample, np.int32))
+    ctx.forward()
+    ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    out = dict(pred=ctx.pred.cpu().numpy().astype(np.float64), grad=ctx.grad.cpu().numpy().astype(np.float64),
+               loss=ctx.loss(), stats=ctx.stats(), sample=G.gsvr_get_sample(ctx.ctx))
+    ctx.close()
+    return out
+
+
+def oracle_all(oracle, case, pix, norm_mode=0):
+    th = case["theta"].astype(np.float64)
+    w = 1.0 / max(len(pix), 1)
+    return oracle.forward_backward(case["stacks"], th, case["N"], pix, case["I"].astype(np.float64)[pix], w,
+                                   norm_mode=norm_mode)
+
+
+def compare(case, gpu, ref, pix, label=""):
+    pred_ref, loss_ref, g_ref, a_ref = ref
+    ok, worst = forward_ok(gpu["pred"][pix], pred_ref)
+    assert ok.all(), "%s forward: %d bad, worst %.3g" % (label, (~ok).sum(), worst)
+    assert abs(gpu["loss"] - loss_ref) <= 1e-5 * abs(loss_ref) + 1e-12, (gpu["loss"], loss_ref)
+    M = inputs.n_slices_total(case["stacks"])
+    gok, gworst, plain = grad_ok(gpu["grad"], g_ref, a_ref)
+    print("%s: fwd worst %.3g, grad worst %.3g (plain 1e-4 pass %.4f) %s" %
+          (label, worst, gworst, plain, describe_grad(gpu["grad"], g_ref, a_ref, case["N"], M)))
+    assert gok.all(), "%s gradient: %d bad; %s" % (label, (~gok).sum(),
+                                                  describe_grad(gpu["grad"], g_ref, a_ref, case["N"], M))
+
+
+def test_tiny_forward_backward(G, oracle):
+    case = inputs.tiny(0)
+    gpu = run_gpu(G, case)
+    pix = np.arange(inputs.n_pixels_total(case["stacks"]))
+    assert gpu["stats"]["n_sampled"] == len(pix)
+    compare(case, gpu, oracle_all(oracle, case, pix), pix, "tiny")
+
+
+@pytest.mark.parametrize("seed,N,sizes,n_stacks,tile", [
+    (1, 1, [(3, 9, 11)], 1, (16, 16)),
+    (2, 2, [(2, 7, 13)], 2, (8, 8)),
+    (3, 17, [(3, 20, 33), (2, 17, 9)], 2, (16, 16)),
+    (4, 300, [(4, 37, 29), (3, 31, 40)], 3, (16, 16)),
+    (5, 300, [(3, 40, 40)], 2, (32, 8)),
+    (6, 150, [(5, 24, 48)], 2, (4, 32)),
+    (7, 400, [(2, 70, 66)], 2, (32, 32)),
+])
+def test_random_cases(G, oracle, seed, N, sizes, n_stacks, tile):
+    case = inputs.random_case(seed, N, sizes, n_stacks=n_stacks, motion_deg=10.0, motion_mm=3.0)
+    gpu = run_gpu(G, case, tile_h=tile[0], tile_w=tile[1])
+    pix = np.arange(inputs.n_pixels_total(case["stacks"]))
+    compare(case, gpu, oracle_all(oracle, case, pix), pix, "random%d" % seed)
+
+
+def test_literal_normalisation(G, oracle):
+    case = inputs.random_case(11, 200, [(3, 30, 30)], n_stacks=2)
+    gpu = run_gpu(G, case, norm_mode=G.GSVR_NORM_LITERAL)
+    pix = np.arange(inputs.n_pixels_total(case["stacks"]))
+    compare(case, gpu, oracle_all(oracle, case, pix, norm_mode=1), pix, "literal")
+
+
+def test_sample_list_duplicates_and_mask(G, oracle):
+    case = inputs.random_case(12, 250, [(3, 33, 35)], n_stacks=2)
+    P = inputs.n_pixels_total(case["stacks"])
+    rng = np.random.default_rng(12)
+    case["mask"] = (rng.uniform(size=P) < 0.8).astype(np.uint8)
+    lst = rng.choice(P, size=P // 2, replace=True)  # duplicates and unmasked pixels
+    gpu = run_gpu(G, case, sample=lst)
+    pix = np.unique(lst[case["mask"][lst] > 0])
+    assert np.array_equal(np.sort(gpu["sample"]), pix)
+    compare(case, gpu, oracle_all(oracle, case, pix), pix, "sample")
+
+
+def test_device_sampler_matches_definition(G, oracle):
+    case = inputs.random_case(13, 50, [(4, 30, 50)], n_stacks=2)
+    P = inputs.n_pixels_total(case["stacks"])
+    rng = np.random.default_rng(13)
+    case["mask"] = (rng.uniform(size=P) < 0.6).astype(np.uint8)
+    ctx = G.Context(case, seed=777)
+    # masked pixels in the library's tile order, rebuilt here from the geometry
+    order = []
+    for s in case["stacks"]:
+        pass
+    masked_tile_order = tile_order(case["stacks"], 16, 16)
+    masked_tile_order = masked_tile_order[case["mask"][masked_tile_order] > 0]
+    n_mask = masked_tile_order.size
+    for step, n in [(0, 1), (1, 100), (5, n_mask // 2), (9, n_mask)]:
+        G.gsvr_sample_pixels(ctx.ctx, n, step)
+        got = np.sort(G.gsvr_get_sample(ctx.ctx))
+        pos = oracle.sample_positions(n_mask, n, 777, step)
+        want = np.sort(masked_tile_order[pos])
+        assert np.array_equal(got, want), (step, n)
+    ctx.close()
+
+
+def tile_order(stacks, th, tw):
+    out = []
+    base = 0
+    for s in stacks:
+        H, W = s["H"], s["W"]
+        for k in range(s["n_slices"]):
+            for ty in range((H + th - 1) // th):
+                for tx in range((W + tw - 1) // tw):
+                    for a in range(ty * th, min(H, (ty + 1) * th)):
+                        for b in range(tx * tw, min(W, (tx + 1) * tw)):
+                            out.append(base + a * W + b)
+            base += H * W
+    return np.array(out, np.int64)
+
+
+def test_forward_is_deterministic(G):
+    case = inputs.random_case(14, 600, [(4, 48, 48)], n_stacks=3)
+    ctx = G.Context(case)
+    ctx.forward()
+    p1 = ctx.pred.clone()
+    l1 = ctx.loss()
+    ctx.forward()
+    p2 = ctx.pred.clone()
+    assert bool((p1 == p2).all()) and l1 == ctx.loss()
+    ctx.close()
+
+
+def test_empty_inputs(G, oracle):
+    case = inputs.random_case(15, 40, [(2, 12, 12)], n_stacks=1)
+    # no pixels in the sample
+    gpu = run_gpu(G, case, sample=np.zeros(0, np.int32))
+    assert gpu["loss"] == 0.0 and gpu["stats"]["n_sampled"] == 0
+    assert np.all(gpu["grad"] == 0.0)
+    # no Gaussians
+    c0 = dict(case)
+    c0["N"] = 0
+    M = inputs.n_slices_total(case["stacks"])
+    c0["theta"] = case["theta"][11 * 40:]
+    gpu = run_gpu(G, c0)
+    pix = np.arange(inputs.n_pixels_total(case["stacks"]))
+    assert np.all(gpu["pred"][pix] == 0.0)
+    ref = oracle_all(oracle, c0, pix)
+    assert abs(gpu["loss"] - ref[1]) <= 1e-6 * ref[1]
+    ok, _, _ = grad_ok(gpu["grad"], ref[2], ref[3])
+    assert ok.all() and gpu["grad"].size == 6 * M
+    # every Gaussian far outside the field of view
+    cf = dict(case)
+    th = case["theta"].copy()
+    th[:3 * 40] += 500.0
+    cf["theta"] = th
+    gpu = run_gpu(G, cf)
+    assert gpu["stats"]["n_records"] == 0 and np.all(gpu["pred"][pix] == 0.0)
+
+
+def test_gaussians_on_tile_borders(G, oracle):
+    """Means placed exactly on tile boundaries and pixel centres of an axial stack."""
+    case = inputs.random_case(16, 64, [(2, 32, 32)], n_stacks=1, motion_deg=0.0, motion_mm=0.0)
+    N = 64
+    th = case["theta"].copy()
+    rng = np.random.default_rng(16)
+    s = case["stacks"][0]
+    cols = rng.choice([0, 7.5, 8, 15.5, 16, 23.5, 31], size=N)
+    rows = rng.choice([0, 7.5, 8, 15.5, 16, 31], size=N)
+    th[0:N] = (cols - 15.5) * s["dx"] + s["origin"][0]
+    th[N:2 * N] = (rows - 15.5) * s["dy"] + s["origin"][1]
+    case["theta"] = th
+    gpu = run_gpu(G, case, tile_h=8, tile_w=8)
+    pix = np.arange(inputs.n_pixels_total(case["stacks"]))
+    compare(case, gpu, oracle_all(oracle, case, pix), pix, "borders")
+
+
+def test_adam_matches_oracle(G, oracle):
+    case = inputs.random_case(17, 120, [(3, 24, 24)], n_stacks=2)
+    N = case["N"]
+    M = inputs.n_slices_total(case["stacks"])
+    ctx = G.Context(case)
+    G.gsvr_set_frozen(ctx.ctx, np.array([1] + [0] * (M - 1), np.uint8))
+    lr = np.array([2.5e-2, 2.5e-2, 1e-2, 1e-2, 2.5e-3, 1e-1])
+    th = case["theta"].astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for t in range(1, 4):
+        ctx.forward()
+        ctx.backward()
+        g = ctx.grad.cpu().numpy().astype(np.float64)
+        th_gpu0 = ctx.theta.cpu().numpy().astype(np.float64)
+        G.gsvr_adam_step(ctx.ctx, t)
+        G.gsvr_sync_status(ctx.ctx)
+        th_ref, m, v = oracle.adam(N, M, th_gpu0, g, m, v, lr, 0.9, 0.999, 1e-8, t,
+                                   frozen=np.array([1] + [0] * (M - 1), np.uint8))
+        th_gpu = ctx.theta.cpu().numpy().astype(np.float64)
+        step = np.abs(th_ref - th_gpu0)
+        err = np.abs(th_gpu - th_ref)
+        assert np.all(err <= 1e-6 * np.abs(th_ref) + 1e-5 * step + 1e-7), (t, err.max())
+        assert np.array_equal(th_gpu[11 * N:11 * N + 6], th_gpu0[11 * N:11 * N + 6])
+    ctx.close()
+
+
+def test_fixed_capacity_overflow_then_grow(G):
+    case = inputs.random_case(18, 300, [(3, 40, 40)], n_stacks=2)
+    ctx = G.Context(case, fixed_capacity=1, cap_records=64, cap_keys=64)
+    ctx.forward()
+    with pytest.raises(G.GsvrError) as ei:
+        G.gsvr_sync_status(ctx.ctx)
+    assert ei.value.status == 3
+    ctx.close()
+    ctx = G.Context(case, cap_records=64, cap_keys=64)  # growing mode starts small
+    ctx.forward()
+    ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    st = ctx.stats()
+    assert st["cap_records"] >= st["n_records"] > 64 and st["cap_keys"] >= st["n_keys"] > 64
+    ctx.close()
+
+
+def test_nonfinite_and_invalid_arguments(G):
+    case = inputs.random_case(19, 20, [(2, 16, 16)], n_stacks=1)
+    ctx = G.Context(case)
+    th = ctx.theta.clone()
+    ctx.theta[5] = float("nan")
+    ctx.forward()
+    with pytest.raises(G.GsvrError) as ei:
+        G.gsvr_sync_status(ctx.ctx)
+    assert ei.value.status == 4
+    ctx.theta.copy_(th)
+    ctx.forward()
+    G.gsvr_sync_status(ctx.ctx)
+    with pytest.raises(G.GsvrError) as ei:
+        G.gsvr_sample_pixels(ctx.ctx, 10 ** 9, 0)
+    assert ei.value.status == 1
+    with pytest.raises(G.GsvrError) as ei:
+        G.gsvr_set_pixel_sample(ctx.ctx, np.array([-1, 3], np.int32))
+    assert ei.value.status == 1
+    with pytest.raises(G.GsvrError):
+        G.gsvr_set_stacks(ctx.ctx, [dict(case["stacks"][0], n_slices=0)])
+    ctx.close()
+    c2 = G.gsvr_create(0)
+    with pytest.raises(G.GsvrError) as ei:
+        G.gsvr_forward(c2)
+    assert ei.value.status == 6
+    G.gsvr_destroy(c2)
+
+
+def test_step_host_matches_device_path(G):
+    case = inputs.random_case(20, 300, [(3, 30, 30)], n_stacks=2)
+    ctx = G.Context(case)
+    P = inputs.n_pixels_total(case["stacks"])
+    idx = np.random.default_rng(20).choice(P, P // 3, replace=False).astype(np.int32)
+    theta = case["theta"].astype(np.float32)
+    grad = np.zeros_like(theta)
+    loss = np.zeros(1, np.float64)
+    G.gsvr_step_host(ctx.ctx, theta, idx, grad, loss)
+    G.gsvr_set_pixel_sample(ctx.ctx, idx)
+    ctx.forward()
+    ctx.backward()
+    g2 = ctx.grad.cpu().numpy()
+    assert abs(loss[0] - ctx.loss()) <= 1e-12 * abs(loss[0])
+    assert np.array_equal(grad[:11 * 300], g2[:11 * 300])
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_fetal_scale_sampled_pixels(G, oracle):
+    """Full fetal-scale workload (200k Gaussians, 3 x 40 x 192^2 px, 2^18 sampled
+    pixels, the bench's launch configuration); 48 sampled pixels checked one by
+    one against the brute-force oracle over all Gaussians."""
+    case = inputs.fetal(0)
+    ctx = G.Context(case)
+    G.gsvr_sample_pixels(ctx.ctx, case["n_sample"], 3)
+    ctx.forward()
+    G.gsvr_sync_status(ctx.ctx)
+    sample = G.gsvr_get_sample(ctx.ctx)
+    assert sample.size == case["n_sample"]
+    rng = np.random.default_rng(0)
+    pix = rng.choice(sample, 48, replace=False)
+    pred = ctx.pred.cpu().numpy()[pix].astype(np.float64)
+    ref, _ = oracle.forward(case["stacks"], case["theta"].astype(np.float64), case["N"], pix)
+    ok, worst = forward_ok(pred, ref, floor=1e-3)
+    print("fetal sampled forward worst %.3g" % worst, ctx.stats())
+    assert ok.all(), worst
+    ctx.close()
