@@ -443,12 +443,17 @@ static void pose_chain(const or_slice *s, const double *pose, const double *GR, 
  * Forward + backward.  grad (11N + 6M) receives dL/dtheta.  absgrad, when not
  * NULL, receives for every entry the sum over pairs of |that pair's
  * contribution| (a condition-aware scale for comparing float32 sums).
+ * When cutoff > 0 and trunc_pred / trunc_grad are not NULL they receive the
+ * same sums restricted to the pairs with exp(-1/2 v^T Sigma_obs^-1 v) < cutoff,
+ * i.e. the most a per-pair truncation at `cutoff` can change each output.
  * Only Gaussians with sel[j] != 0 get gradients (sel NULL = all); pose
  * gradients always include every pair of the selected Gaussians.
  */
 int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
                             const int64_t *pix, const double *I_obs, double w_pix, int norm_mode,
-                            const uint8_t *sel, double *pred, double *loss, double *grad, double *absgrad) {
+                            const uint8_t *sel, double *pred, double *loss, double *grad, double *absgrad,
+                            double cutoff, double *trunc_pred, double *trunc_grad) {
+    const int want_trunc = cutoff > 0.0 && trunc_grad != NULL && absgrad != NULL;
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
     const int64_t M = m.M;
@@ -462,13 +467,15 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
         int64_t i;
         pixel_world(&m, pix[p], &i, &pu[3 * p], &px[3 * p]);
         psl[p] = i;
-        double s = 0.0;
+        double s = 0.0, tr = 0.0;
         for (int64_t j = 0; j < N; ++j) {
             or_pair pr;
             eval_pair(&m.g[j], &m.fr[i], &px[3 * p], norm_mode, &pr);
             s += m.g[j].c * pr.g;
+            if (pr.e < cutoff) tr += fabs(m.g[j].c * pr.g);
         }
         if (pred) pred[p] = s;
+        if (trunc_pred) trunc_pred[p] = tr;
         double r = s - I_obs[p];
         L += w_pix * r * r;
         rbar[p] = 2.0 * w_pix * r;
@@ -476,13 +483,15 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
     if (loss) *loss = L;
     memset(grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
     if (absgrad) memset(absgrad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
+    if (want_trunc) memset(trunc_grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
 
     int nthreads = 1;
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
 #endif
-    /* per-thread slice accumulators: dL/dR_i (9), dL/dt_i (3), |.| of the pose entries (6) */
-    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 18, sizeof(double));
+    /* per-thread slice accumulators: dL/dR_i (9), dL/dt_i (3), |.| of the pose entries (6),
+     * |.| of the truncated pairs' pose entries (6) */
+    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 24, sizeof(double));
 
 #pragma omp parallel
     {
@@ -490,13 +499,14 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 18;
+        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 24;
 #pragma omp for schedule(dynamic, 4)
         for (int64_t j = 0; j < N; ++j) {
             if (sel && !sel[j]) continue;
             const or_gauss *gj = &m.g[j];
             double gmu[3] = {0, 0, 0}, GS[9] = {0}, gc = 0.0, glogdet = 0.0;
             double amu[3] = {0, 0, 0}, als[3] = {0, 0, 0}, aq[4] = {0, 0, 0, 0}, ac = 0.0;
+            double tmu[3] = {0, 0, 0}, tls[3] = {0, 0, 0}, tq[4] = {0, 0, 0, 0}, tc = 0.0;
             for (int64_t p = 0; p < P; ++p) {
                 int64_t i = psl[p];
                 or_pair pr;
@@ -523,7 +533,8 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
                 for (int r = 0; r < 3; ++r)
                     for (int c = 0; c < 3; ++c)
                         GR[3 * r + c] = dx[r] * pu[3 * p + c] + 2.0 * GoRD[3 * r + c];
-                double *acc = my + 18 * i;
+                double *acc = my + 24 * i;
+                const int cut = pr.e < cutoff;
                 for (int e = 0; e < 9; ++e) acc[e] += GR[e];
                 for (int k = 0; k < 3; ++k) acc[9 + k] += dx[k];
                 if (absgrad) {
@@ -535,9 +546,20 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
                         double v = dls[k] + (norm_mode == 0 ? a : 0.0);
                         als[k] += fabs(v);
                         amu[k] += fabs(a * pr.Pv[k]);
+                        if (cut) {
+                            tls[k] += fabs(v);
+                            tmu[k] += fabs(a * pr.Pv[k]);
+                        }
                     }
-                    for (int k = 0; k < 4; ++k) aq[k] += fabs(dq[k]);
+                    for (int k = 0; k < 4; ++k) {
+                        aq[k] += fabs(dq[k]);
+                        if (cut) tq[k] += fabs(dq[k]);
+                    }
                     ac += fabs(dc);
+                    if (cut) {
+                        tc += fabs(dc);
+                        for (int k = 0; k < 6; ++k) acc[18 + k] += fabs(d6[k]);
+                    }
                 }
             }
             double dls[3], dq[4];
@@ -556,21 +578,31 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
                 for (int k = 0; k < 4; ++k) absgrad[(6 + k) * N + j] = aq[k];
                 absgrad[10 * N + j] = ac;
             }
+            if (want_trunc) {
+                for (int k = 0; k < 3; ++k) {
+                    trunc_grad[k * N + j] = tmu[k];
+                    trunc_grad[(3 + k) * N + j] = tls[k];
+                }
+                for (int k = 0; k < 4; ++k) trunc_grad[(6 + k) * N + j] = tq[k];
+                trunc_grad[10 * N + j] = tc;
+            }
         }
     }
     for (int64_t i = 0; i < M; ++i) {
-        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0};
+        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0}, tb[6] = {0};
         for (int t = 0; t < nthreads; ++t) {
-            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 18;
+            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 24;
             for (int e = 0; e < 9; ++e) GR[e] += acc[e];
             for (int k = 0; k < 3; ++k) Gt[k] += acc[9 + k];
             for (int k = 0; k < 6; ++k) ab[k] += acc[12 + k];
+            for (int k = 0; k < 6; ++k) tb[k] += acc[18 + k];
         }
         double d6[6];
         pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, Gt, d6);
         for (int k = 0; k < 6; ++k) {
             grad[11 * N + 6 * i + k] = d6[k];
             if (absgrad) absgrad[11 * N + 6 * i + k] = ab[k];
+            if (want_trunc) trunc_grad[11 * N + 6 * i + k] = tb[k];
         }
     }
     free(pacc);

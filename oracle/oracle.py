@@ -38,7 +38,7 @@ def lib():
         d, i64, vp = C.c_double, C.c_int64, C.c_void_p
         _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp]
         _lib.oracle_forward_backward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp, vp,
-                                                 vp, vp]
+                                                 vp, vp, d, vp, vp]
         _lib.oracle_adam.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, d, d, i64, vp]
         _lib.oracle_adam.restype = None
         _lib.oracle_build_slices.argtypes = [C.c_int, vp, vp, vp]
@@ -109,8 +109,10 @@ def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0):
     return pred, float(loss[0])
 
 
-def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True):
-    """(pred, loss, grad, absgrad) in float64; grad has the parameter-vector layout."""
+def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True, cutoff=None):
+    """(pred, loss, grad, absgrad) in float64; grad has the parameter-vector layout.
+    With `cutoff`, returns (pred, loss, grad, absgrad, trunc_pred, trunc_grad): the
+    sums of |pair contributions| over the pairs below the cutoff, per output."""
     st = _stacks(stacks)
     th = _f64(theta)
     pix = np.ascontiguousarray(pix, dtype=np.int64)
@@ -122,11 +124,17 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None,
     grad = np.zeros(n, np.float64)
     absg = np.zeros(n, np.float64) if want_abs else None
     s = np.ascontiguousarray(sel, dtype=np.uint8) if sel is not None else None
+    tp = np.zeros(len(pix), np.float64) if cutoff else None
+    tg = np.zeros(n, np.float64) if cutoff else None
+    if cutoff and absg is None:
+        absg = np.zeros(n, np.float64)
     rc = lib().oracle_forward_backward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
                                        float(w_pix), int(norm_mode), _p(s), _p(pred), _p(loss), _p(grad),
-                                       _p(absg))
+                                       _p(absg), float(cutoff or 0.0), _p(tp), _p(tg))
     if rc != 0:
         raise RuntimeError("oracle_forward_backward failed")
+    if cutoff:
+        return pred, float(loss[0]), grad, absg, tp, tg
     return pred, float(loss[0]), grad, absg
 
 

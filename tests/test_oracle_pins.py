@@ -397,3 +397,20 @@ def test_sampler_subset_uniform(oracle):
     # each element is drawn with probability k/n = 0.1 per step: mean 40, sd ~6
     assert abs(counts.mean() - 40.0) < 1e-9
     assert counts.std() < 9.0 and counts.min() > 10 and counts.max() < 75
+
+
+def test_truncation_sums(oracle):
+    """Sums over pairs below a cutoff: 0 for a cutoff below every pair factor, equal
+    to the full sums of |terms| for a cutoff above every factor (factor <= 1)."""
+    case = inputs.random_case(21, 15, [(2, 7, 8)], n_stacks=2, extent=5.0)
+    N, st = case["N"], case["stacks"]
+    th = case["theta"].astype(np.float64)
+    pix = np.arange(inputs.n_pixels_total(st))
+    I = case["I"].astype(np.float64)
+    r0 = oracle.forward_backward(st, th, N, pix, I, 1.0 / len(pix), cutoff=1e-300)
+    assert np.all(r0[4] == 0.0) and np.all(r0[5] == 0.0)
+    r1 = oracle.forward_backward(st, th, N, pix, I, 1.0 / len(pix), cutoff=1.5)
+    assert np.allclose(r1[5], r1[3], rtol=1e-12, atol=0)
+    assert np.allclose(r1[4], np.abs(r1[0]), rtol=1e-12)  # positive amplitudes
+    r2 = oracle.forward_backward(st, th, N, pix, I, 1.0 / len(pix), cutoff=1e-3)
+    assert np.all(r2[5] <= r2[3] * (1 + 1e-12)) and np.all(r2[4] <= np.abs(r2[0]) * (1 + 1e-12))
