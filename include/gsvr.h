@@ -242,6 +242,40 @@ gsvr_status gsvr_sync_status(gsvr_ctx *ctx);
  * ctx NULL gives the last error of gsvr_create. */
 const char *gsvr_last_error(gsvr_ctx *ctx);
 
+/* Forward pass without any device allocation (this entry point has no
+ * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
+ * code running inside a host framework or plug-in whose device memory is owned
+ * by someone else, or under a budget or in a region where allocating is not
+ * allowed).  It needs no context and allocates nothing: every intermediate
+ * buffer lives in one file-scope device array of 32 MiB that each GPU loading
+ * this library holds until the process exits.  It runs the same kernels as
+ * gsvr_forward with 16 x 16 pixel tiles and fixed capacities.
+ *   device      CUDA device to run on (made current for the call).
+ *   cuda_stream cudaStream_t to issue the work on (NULL = legacy default stream).
+ *   stacks      n_stacks descriptions (host), as for gsvr_set_stacks.
+ *   theta       11N + 6M float32 parameters (device), the layout above.
+ *   I           observed intensity per global pixel (device float32).
+ *   idx, n_idx  sampled global pixel indices (device int32, duplicates count
+ *               once); n_idx = -1 samples every pixel (idx may be NULL).
+ *   cutoff_rel, norm_mode  as in gsvr_config (0 -> 1e-7).
+ *   pred        per global pixel (device float32); only sampled pixels written.
+ *   loss        the MSE loss (device double).
+ *   msg, msg_len optional host buffer receiving an error description.
+ * Limits: problems whose tile maps, sample lists, records and keys do not fit
+ * in 32 MiB (roughly up to ~10^5 pixels and ~10^5 (slice, Gaussian) records)
+ * are rejected with GSVR_ERR_INVALID_ARG before any work, or return
+ * GSVR_ERR_CAPACITY when the records or keys found on the device overflow.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture on that
+ * device.  Every call shares the array and leaves its contents behind (each
+ * call clears what must start at zero), so calls that overlap on the GPU --
+ * on different streams or threads -- race and must not be issued.  The call
+ * synchronises `cuda_stream` before it returns (to report device status). */
+gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32_t n_stacks, const gsvr_stack_desc *stacks,
+                                 int64_t N, const float *theta, const float *I, const int32_t *idx, int64_t n_idx,
+                                 float cutoff_rel, int32_t norm_mode, float *pred, double *loss, char *msg,
+                                 int32_t msg_len);
+
 /* ABI version (GSVR_ABI_VERSION of the built library). */
 int32_t gsvr_abi_version(void);
 

@@ -27,7 +27,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_set_observations", "gsvr_set_gaussians", "gsvr_set_poses", "gsvr_set_frozen",
            "gsvr_set_pixel_sample", "gsvr_sample_pixels", "gsvr_forward", "gsvr_backward", "gsvr_adam_step",
            "gsvr_step_host", "gsvr_get_sample", "gsvr_get_views", "gsvr_get_stats", "gsvr_sync_status",
-           "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs"]
+           "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -101,6 +101,8 @@ def _load():
         "gsvr_timing_reset": ([vp], C.c_int),
         "gsvr_get_kernel_times": ([vp, C.POINTER(KernelTimes)], C.c_int),
         "gsvr_count_pairs": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "gsvr_forward_noalloc": ([C.c_int, vp, i32, C.POINTER(StackDesc), i64, vp, vp, vp, i64, C.c_float, i32, vp,
+                                  vp, C.c_char_p, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -300,6 +302,27 @@ def gsvr_count_pairs(ctx):
     u, e = C.c_int64(), C.c_int64()
     _check(ctx, lib.gsvr_count_pairs(ctx, C.byref(u), C.byref(e)))
     return int(u.value), int(e.value)
+
+
+def gsvr_forward_noalloc(stacks, N, theta, I, idx, pred, loss, device=0, stream=None, cutoff_rel=1e-7,
+                         norm_mode=GSVR_NORM_EXACT):
+    """Context-free forward that allocates no device memory (for callers that
+    cannot call cudaMalloc); all arrays are CUDA tensors: theta (11N + 6M float32),
+    I and pred (one float32 per global pixel), idx (int32 sampled pixels, or None
+    for every pixel), loss (one float64).  Synchronises the stream."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    arr = stack_descs(stacks)
+    buf = C.create_string_buffer(256)
+    pi = idx.data_ptr() if idx is not None else None
+    n = int(idx.numel()) if idx is not None else -1
+    st = lib.gsvr_forward_noalloc(int(device), C.c_void_p(int(stream)), len(stacks), arr, int(N),
+                                  theta.data_ptr() if N > 0 else None, I.data_ptr(), pi, n, float(cutoff_rel),
+                                  int(norm_mode), pred.data_ptr(), loss.data_ptr(), buf, 256)
+    if st != GSVR_OK:
+        raise GsvrError(st, buf.value.decode())
+    return st
 
 
 # --------------------------------------------------------------- torch views
