@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fetal", choices=["fetal", "tiny"])
+    ap.add_argument("--stacks", type=int, default=0, help="keep only the first n stacks (profiling captures)")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,10 +56,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, seed):
+def workload(name, seed, n_stacks=0):
     from paper_2512_11624_b300 import inputs
     if name == "fetal":
         case = inputs.fetal(seed)
+        if n_stacks:
+            case = inputs.first_stacks(case, n_stacks)
         desc = ("fetal: %d Gaussians (0.8 mm grid in a brain phantom), 3 orthogonal stacks of 40 x 192 x 192 px "
                 "at 1 x 1 x 3.5 mm, motion U(+-5 deg)/U(+-3 mm), 2^18 sampled px/step, Adam" % case["N"])
     else:
@@ -222,7 +225,7 @@ def main():
     dev = local
     stream = torch.cuda.Stream(device=dev)
     th_, tw_ = (int(v) for v in args.tile.split("x"))
-    case, desc = workload(args.workload, rank)
+    case, desc = workload(args.workload, rank, args.stacks)
     n_s = min(case["n_sample"], int(case["mask"].sum()))
     sampled = args.workload == "fetal"
 
@@ -300,8 +303,8 @@ def main():
     pairs_per_launch = eval_per_step
     achieved = pairs_per_launch / (avg_ms / 1e3) / 1e9
     peak = n_sm * f_mhz * 1e6 * THREAD_INSTR_PER_CLK_PER_SM / ISSUE_PER_PAIR[dom] / 1e9
-    traffic = profiled_traffic({"fwd_eval": "k_forward", "bwd_eval": "k_backward"}[dom], args.workload)
-    roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_forward", "bwd_eval": "k_backward"}[dom],
+    traffic = profiled_traffic({"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom], args.workload)
+    roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "peak_basis": "%d SMs x %.0f MHz (median sampled) x 128 issue slots/clk / %.0f slots per pair" %

@@ -242,6 +242,13 @@ gsvr_status gsvr_sync_status(gsvr_ctx *ctx);
  * ctx NULL gives the last error of gsvr_create. */
 const char *gsvr_last_error(gsvr_ctx *ctx);
 
+/* Measurement helper (not part of the method): float32 FFMA and MUFU ex2.approx
+ * throughput of the whole device in instructions per second (best of three
+ * launches of independent dependency chains filling every SM) and the SM count;
+ * the roofline denominators of the ALU-bound tile kernels.  Synchronous;
+ * allocates a 1 KB buffer. */
+gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex2_per_s, double *sm_count);
+
 /* Forward pass without any device allocation (this entry point has no
  * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
  * code running inside a host framework or plug-in whose device memory is owned

@@ -88,7 +88,9 @@ struct gsvr_ctx {
     DBuf<uint32_t> d_keys, d_keys_sorted, d_vals_sorted, d_keys_alt, d_vals_alt;
     DBuf<int> d_hist, d_scan_bsum;
     DBuf<float4> d_mom;
-    int cap_rec = 0, cap_keys = 0;
+    DBuf<int> d_item_cnt, d_item_first, d_item_tile;
+    DBuf<float> d_part;
+    int cap_rec = 0, cap_keys = 0, cap_items = 0, grid_items = 0;
     int last_n_rec = 0, last_n_keys = 0;
 
     // outputs
@@ -177,6 +179,8 @@ cudaError_t ensure_scan_scratch(gsvr_ctx *ctx) { return ctx->d_scan_bsum.ensure(
 
 ScanScratch scan_scratch(gsvr_ctx *ctx) { return ScanScratch{ctx->d_scan_bsum.p, (int)ctx->d_scan_bsum.n - 1}; }
 
+gsvr_status ensure_item_capacity(gsvr_ctx *ctx);
+
 gsvr_status ensure_rec_capacity(gsvr_ctx *ctx, int64_t want) {
     if (want <= ctx->cap_rec && ctx->d_rec.p) return GSVR_OK;
     if (want > (int64_t)INT32_MAX - 16) return fail(ctx, GSVR_ERR_CAPACITY, "record count exceeds int32 range");
@@ -205,7 +209,50 @@ gsvr_status ensure_key_capacity(gsvr_ctx *ctx, int64_t want) {
     CK(ctx->d_hist.ensure((size_t)256 * sort_blocks(cap) + 1));
     ctx->cap_keys = cap;
     CK(ensure_scan_scratch(ctx));
+    return ensure_item_capacity(ctx);
+}
+
+// Work items (<= kItemRecs records of one tile): at most one per tile plus one
+// per kItemRecs keys.
+gsvr_status ensure_item_capacity(gsvr_ctx *ctx) {
+    const int64_t want = (int64_t)ctx->n_tiles + ctx->cap_keys / kItemRecs + 2;
+    CK(ctx->d_item_cnt.ensure((size_t)ctx->n_tiles + 1));
+    CK(ctx->d_item_first.ensure((size_t)ctx->n_tiles + 1));
+    if (want > ctx->cap_items || !ctx->d_item_tile.p || ctx->d_part.n < (size_t)want * ctx->tile_w * ctx->tile_h) {
+        CK(ctx->d_item_tile.ensure((size_t)want));
+        CK(ctx->d_part.ensure((size_t)want * ctx->tile_w * ctx->tile_h));
+        ctx->cap_items = (int)want;
+    }
     return GSVR_OK;
+}
+
+EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
+    EvalArgs e{};
+    e.trec = ctx->d_trec.p;
+    e.tile_rec_start = ctx->d_tile_rec_start.p;
+    e.tile_rec_end = ctx->d_tile_rec_end.p;
+    e.tile_px_start = ctx->d_tile_px_start.p;
+    e.tile_px_end = ctx->d_tile_px_end.p;
+    e.tile_slice = ctx->d_tile_slice.p;
+    e.slices = ctx->d_slices.p;
+    e.sampled = ctx->d_sampled.p;
+    e.n_sampled = &ctx->d_counters.p->n_sampled;
+    e.I_obs = ctx->d_I.p;
+    e.pred = ctx->d_pred.p;
+    e.rbar = ctx->d_rbar.p;
+    e.tile_loss = ctx->d_tile_loss.p;
+    e.mom = ctx->d_mom.p;
+    e.counters = ctx->d_counters.p;
+    e.pairs_total = ctx->d_pairs_total.p;
+    e.item_tile = ctx->d_item_tile.p;
+    e.item_first = ctx->d_item_first.p;
+    e.n_items = &ctx->d_counters.p->n_items;
+    e.part = ctx->d_part.p;
+    e.cap_items = std::min(grid_items, ctx->cap_items);
+    e.tile_px = ctx->tile_w * ctx->tile_h;
+    e.n_tiles = ctx->n_tiles;
+    e.status = ctx->d_status.p;
+    return e;
 }
 
 // Tile ranges of the current sample (sampled pixels are in tile order).
@@ -766,28 +813,21 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->d_tile_rec_start.p,
                            ctx->d_tile_rec_end.p, st);
     launch_gather(ctx->d_rec.p, ctx->d_vals_sorted.p, ctx->d_key_rec.p, &cnt->n_keys, n_keys_max, ctx->d_trec.p, st);
+    {
+        gsvr_status si = ensure_item_capacity(ctx);
+        if (si) return si;
+    }
+    launch_items(ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_tile_rec_start.p, ctx->d_tile_rec_end.p,
+                 ctx->n_tiles, ctx->d_item_cnt.p, nullptr, nullptr, 0, 0, st);
+    CK(scan_exclusive(ctx->d_item_cnt.p, ctx->d_item_first.p, nullptr, ctx->n_tiles, ctx->n_tiles, &cnt->n_items,
+                      scan_scratch(ctx), st));
+    launch_items(nullptr, nullptr, nullptr, nullptr, ctx->n_tiles, nullptr, ctx->d_item_first.p, ctx->d_item_tile.p,
+                 ctx->cap_items, 1, st);
     stage_end(ctx, GSVR_STAGE_BIN);
-    EvalArgs e{};
-    e.trec = ctx->d_trec.p;
-    e.tile_rec_start = ctx->d_tile_rec_start.p;
-    e.tile_rec_end = ctx->d_tile_rec_end.p;
-    e.tile_px_start = ctx->d_tile_px_start.p;
-    e.tile_px_end = ctx->d_tile_px_end.p;
-    e.tile_slice = ctx->d_tile_slice.p;
-    e.slices = ctx->d_slices.p;
-    e.sampled = ctx->d_sampled.p;
-    e.n_sampled = &cnt->n_sampled;
-    e.I_obs = ctx->d_I.p;
-    e.pred = ctx->d_pred.p;
-    e.rbar = ctx->d_rbar.p;
-    e.tile_loss = ctx->d_tile_loss.p;
-    e.mom = ctx->d_mom.p;
-    e.counters = cnt;
-    e.pairs_total = ctx->d_pairs_total.p;
-    e.n_tiles = ctx->n_tiles;
-    e.status = ctx->d_status.p;
+    ctx->grid_items = ctx->n_tiles + n_keys_max / kItemRecs + 2;
+    EvalArgs e = eval_args(ctx, ctx->grid_items);
     stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
-    launch_forward(e, ctx->tile_w * ctx->tile_h, st);
+    launch_forward(e, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
     launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_loss.p, ctx->d_status.p, st);
     CK(cudaGetLastError());
@@ -802,24 +842,7 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->N, M = ctx->M;
     Counters *cnt = ctx->d_counters.p;
-    EvalArgs e{};
-    e.trec = ctx->d_trec.p;
-    e.tile_rec_start = ctx->d_tile_rec_start.p;
-    e.tile_rec_end = ctx->d_tile_rec_end.p;
-    e.tile_px_start = ctx->d_tile_px_start.p;
-    e.tile_px_end = ctx->d_tile_px_end.p;
-    e.tile_slice = ctx->d_tile_slice.p;
-    e.slices = ctx->d_slices.p;
-    e.sampled = ctx->d_sampled.p;
-    e.n_sampled = &cnt->n_sampled;
-    e.I_obs = ctx->d_I.p;
-    e.pred = ctx->d_pred.p;
-    e.rbar = ctx->d_rbar.p;
-    e.tile_loss = ctx->d_tile_loss.p;
-    e.mom = ctx->d_mom.p;
-    e.counters = cnt;
-    e.n_tiles = ctx->n_tiles;
-    e.status = ctx->d_status.p;
+    EvalArgs e = eval_args(ctx, ctx->grid_items);
     stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
     launch_backward(e, st);
     stage_end(ctx, GSVR_STAGE_BWD_EVAL);
@@ -942,22 +965,10 @@ gsvr_status gsvr_count_pairs(gsvr_ctx *ctx, int64_t *useful, int64_t *evaluated)
     cudaStream_t st = ctx->stream;
     Counters *cnt = ctx->d_counters.p;
     CK(cudaMemsetAsync(ctx->d_useful.p, 0, sizeof(unsigned long long), st));
-    EvalArgs e{};
-    e.trec = ctx->d_trec.p;
-    e.tile_rec_start = ctx->d_tile_rec_start.p;
-    e.tile_rec_end = ctx->d_tile_rec_end.p;
-    e.tile_px_start = ctx->d_tile_px_start.p;
-    e.tile_px_end = ctx->d_tile_px_end.p;
-    e.tile_slice = ctx->d_tile_slice.p;
-    e.slices = ctx->d_slices.p;
-    e.sampled = ctx->d_sampled.p;
-    e.n_sampled = &cnt->n_sampled;
-    e.counters = cnt;
+    EvalArgs e = eval_args(ctx, ctx->grid_items);
     e.useful = ctx->d_useful.p;
     e.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
-    e.n_tiles = ctx->n_tiles;
-    e.status = ctx->d_status.p;
-    launch_count_pairs(e, ctx->tile_w * ctx->tile_h, st);
+    launch_count_pairs(e, st);
     CK(cudaGetLastError());
     unsigned long long u = 0;
     Counters c{};

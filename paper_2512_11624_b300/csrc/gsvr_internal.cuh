@@ -10,7 +10,7 @@
 namespace gsvr {
 
 constexpr int kThreads = 128;     // threads of the tile kernels
-constexpr int kChunk = 256;       // records staged per shared-memory buffer in the forward
+constexpr int kItemRecs = 2 * kThreads;  // records per evaluation work item (one tile)
 constexpr int kMaxTilePx = 1024;  // largest tile (32 x 32 pixels)
 constexpr int kScanTile = 4096;   // items per block of the scans
 constexpr int kSortThreads = 256; // 8 warps
@@ -47,7 +47,7 @@ struct Counters {
     int n_sampled;
     int n_rec;
     int n_keys;
-    int pad_;
+    int n_items;
     unsigned long long pairs;  // pixel x record pairs visited by one evaluation pass
 };
 

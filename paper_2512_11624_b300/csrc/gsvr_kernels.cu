@@ -370,122 +370,96 @@ __global__ void k_gather(const Rec *__restrict__ rec, const uint32_t *__restrict
     trec[s] = R;
 }
 
+// ------------------------------------------------------------- work items
+// The sorted (tile, record) list is cut into work items of at most kItemRecs
+// records of one tile (a tile with pixels and no records gets one empty item),
+// so the evaluation grids are balanced however unevenly records fall on tiles.
+__global__ void k_item_count(const int *__restrict__ tps, const int *__restrict__ tpe,
+                             const int *__restrict__ trs, const int *__restrict__ tre, int n_tiles,
+                             int *__restrict__ cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const int npx = tpe[t] - tps[t], nrec = tre[t] - trs[t];
+    cnt[t] = npx > 0 ? max(1, (nrec + kItemRecs - 1) / kItemRecs) : 0;
+}
+
+__global__ void k_item_fill(const int *__restrict__ first, int n_tiles, int *__restrict__ item_tile, int cap) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const int e = min(first[t + 1], cap);
+    for (int i = first[t]; i < e; ++i) item_tile[i] = t;
+}
+
 // ----------------------------------------------------------------- forward
-// One CTA per tile, thread per pixel (PX pixels per thread).  The tile's
-// records stream through two shared-memory buffers filled by 1-D bulk copies
-// (cp.async.bulk, completion on an mbarrier); every thread reads each record
-// as a broadcast.  Pixel value = sum_r w_r exp2(q_r(pixel)).
-template <int PX, bool COUNT>
-__global__ void __launch_bounds__(kThreads) k_forward(EvalArgs a) {
-    __shared__ __align__(128) Rec buf[2][kChunk];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ double red[kThreads / 32];
-    const int t = blockIdx.x;
+// One CTA per work item, one thread per tile pixel.  The item's records (at most
+// kItemRecs x 32 bytes) are brought into shared memory by one 1-D bulk copy
+// (cp.async.bulk, completion on an mbarrier); every thread reads each record as
+// a broadcast and accumulates sum_r w_r exp2(q_r(pixel)).  The per-item sums go
+// to part[item][pixel]; k_fwd_reduce adds a tile's items in item order, so the
+// forward is bitwise reproducible.  COUNT: count the pairs inside the cut instead.
+template <bool COUNT>
+__global__ void __launch_bounds__(kMaxTilePx) k_fwd_items(EvalArgs a) {
+    __shared__ __align__(128) Rec buf[kItemRecs];
+    __shared__ __align__(8) uint64_t bar;
+    const int i = blockIdx.x;
+    if (i >= min(*a.n_items, a.cap_items)) return;
+    const int t = a.item_tile[i];
+    const int c = i - a.item_first[t];
     const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-    if (ps >= pe) {
-        if (threadIdx.x == 0 && !COUNT) a.tile_loss[t] = 0.0;
-        return;
-    }
-    const int rs = a.tile_rec_start[t], re = a.tile_rec_end[t];
-    const int nrec = re - rs;
+    const int rs = a.tile_rec_start[t] + c * kItemRecs;
+    const int nrec = max(0, min(kItemRecs, a.tile_rec_end[t] - rs));
     const SliceDev &S = a.slices[a.tile_slice[t]];
-    const float cx0 = S.cx0, cy0 = S.cy0;
-    const int W = S.W, pbase = S.pix_base;
-    float pb[PX], pa[PX], acc[PX];
-    int pix[PX];
-    unsigned long long useful = 0;
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const int s = ps + threadIdx.x + k * kThreads;
-        acc[k] = 0.f;
-        if (s < pe) {
-            const int p = a.sampled[s];
-            const int loc = p - pbase;
-            const int row = loc / W;
-            pix[k] = p;
-            pb[k] = (float)(loc - row * W) - cx0;
-            pa[k] = (float)row - cy0;
-        } else {
-            pix[k] = -1;
-            pb[k] = 0.f;
-            pa[k] = 0.f;
-        }
+    const int slot = threadIdx.x;
+    const int s = ps + slot;
+    const bool valid = s < pe;
+    float pb = 0.f, pa = 0.f;
+    if (valid) {
+        const int loc = a.sampled[s] - S.pix_base;
+        const int row = loc / S.W;
+        pb = (float)(loc - row * S.W) - S.cx0;
+        pa = (float)row - S.cy0;
     }
+    float acc = 0.f;
+    unsigned long long useful = 0;
     if (nrec > 0) {
         if (threadIdx.x == 0) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
+            mbar_init(&bar, 1);
             fence_mbar_init();
         }
         __syncthreads();
-        const int nch = (nrec + kChunk - 1) / kChunk;
-        const Rec *src = a.trec + rs;
         if (threadIdx.x == 0) {
-            const uint32_t bytes = (uint32_t)min(kChunk, nrec) * (uint32_t)sizeof(Rec);
-            mbar_arrive_expect_tx(&bar[0], bytes);
-            bulk_g2s(&buf[0][0], src, bytes, &bar[0]);
+            const uint32_t bytes = (uint32_t)nrec * (uint32_t)sizeof(Rec);
+            mbar_arrive_expect_tx(&bar, bytes);
+            bulk_g2s(&buf[0], a.trec + rs, bytes, &bar);
         }
-        bool ok = true;
-        for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            if (threadIdx.x == 0 && c + 1 < nch) {
-                const int off = (c + 1) * kChunk;
-                const uint32_t bytes = (uint32_t)min(kChunk, nrec - off) * (uint32_t)sizeof(Rec);
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar[b ^ 1], bytes);
-                bulk_g2s(&buf[b ^ 1][0], src + off, bytes, &bar[b ^ 1]);
+        const bool ok = mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
+        if (!ok) atomicOr(a.status, ST_TIMEOUT);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
+            __syncthreads();
+            return;
+        }
+        if (!COUNT) {
+#pragma unroll 8
+            for (int r = 0; r < nrec; ++r) {
+                const float4 r0 = buf[r].a;
+                const float4 r1 = buf[r].b;
+                const float dx = pb - r0.x;
+                const float dy = pa - r0.y;
+                const float u = fmaf(r0.z, dx, r0.w * dy);
+                const float q = fmaf(u, dx, r1.x * dy * dy);
+                acc = fmaf(r1.y, ex2_approx(q), acc);
             }
-            if (!mbar_wait_bounded(&bar[b], (uint32_t)((c >> 1) & 1), kWaitLimitNs)) {
-                atomicOr(a.status, ST_TIMEOUT);
-                ok = false;
-            }
-            const int nin = min(kChunk, nrec - c * kChunk);
-            float part[PX];
-#pragma unroll
-            for (int k = 0; k < PX; ++k) part[k] = 0.f;
-            if (ok && !COUNT) {
-#pragma unroll 4
-                for (int r = 0; r < nin; ++r) {
-                    const float4 r0 = buf[b][r].a;
-                    const float4 r1 = buf[b][r].b;
-#pragma unroll
-                    for (int k = 0; k < PX; ++k) {
-                        const float dx = pb[k] - r0.x;
-                        const float dy = pa[k] - r0.y;
-                        const float u = fmaf(r0.z, dx, r0.w * dy);
-                        const float q = fmaf(u, dx, r1.x * dy * dy);
-                        part[k] = fmaf(r1.y, ex2_approx(q), part[k]);
-                    }
-                }
-            }
-            if (ok && COUNT) {
-                // pairs whose full exponent (slice-plane part + normal part, log2 units)
-                // is inside the cut
-                for (int r = 0; r < nin; ++r) {
-                    const float4 r0 = buf[b][r].a;
-                    const float4 r1 = buf[b][r].b;
-#pragma unroll
-                    for (int k = 0; k < PX; ++k) {
-                        const float dx = pb[k] - r0.x;
-                        const float dy = pa[k] - r0.y;
-                        const float u = fmaf(r0.z, dx, r0.w * dy);
-                        const float q = fmaf(u, dx, r1.x * dy * dy);
-                        useful += (pix[k] >= 0 && q + r1.z >= a.qcut) ? 1ull : 0ull;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < PX; ++k) acc[k] += part[k];
-            // the barrier also frees buffer b for the copy issued next iteration
-            if (!__syncthreads_and(ok)) {
-                // bounded second waits for copies that may still be in flight, then leave
-                if (threadIdx.x == 0) {
-                    mbar_wait_bounded(&bar[b], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
-                    if (c + 1 < nch) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((c + 1) >> 1) & 1), kWaitLimitNs);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0 && !COUNT) a.tile_loss[t] = 0.0;
-                return;
+        } else {
+            for (int r = 0; r < nrec; ++r) {
+                const float4 r0 = buf[r].a;
+                const float4 r1 = buf[r].b;
+                const float dx = pb - r0.x;
+                const float dy = pa - r0.y;
+                const float u = fmaf(r0.z, dx, r0.w * dy);
+                const float q = fmaf(u, dx, r1.x * dy * dy);
+                // full exponent (slice-plane part + normal part, log2 units) inside the cut
+                useful += (valid && q + r1.z >= a.qcut) ? 1ull : 0ull;
             }
         }
     }
@@ -495,42 +469,61 @@ __global__ void __launch_bounds__(kThreads) k_forward(EvalArgs a) {
         if ((threadIdx.x & 31) == 0 && useful) atomicAdd(a.useful, useful);
         return;
     }
-    const int ns = *a.n_sampled;
-    const float wp = 1.0f / (float)max(ns, 1);
+    if (valid) a.part[(size_t)i * a.tile_px + slot] = acc;
+}
+
+// Per tile: add the items' partial sums in order, then residual, dL/dI_hat and loss.
+__global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
+    __shared__ double red[kMaxTilePx / 32];
+    const int t = blockIdx.x;
+    const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+    if (ps >= pe) {
+        if (threadIdx.x == 0) a.tile_loss[t] = 0.0;
+        return;
+    }
+    const int slot = threadIdx.x;
+    const int s = ps + slot;
     double l = 0.0;
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        if (pix[k] >= 0) {
-            const float r = acc[k] - a.I_obs[pix[k]];
-            a.pred[pix[k]] = acc[k];
-            a.rbar[pix[k]] = 2.0f * wp * r;
-            l += (double)(wp * r * r);
-        }
+    if (s < pe) {
+        float acc = 0.f;
+        const int i1 = min(a.item_first[t + 1], a.cap_items);
+        for (int i = a.item_first[t]; i < i1; ++i) acc += a.part[(size_t)i * a.tile_px + slot];
+        const int p = a.sampled[s];
+        const float wp = 1.0f / (float)max(*a.n_sampled, 1);
+        const float r = acc - a.I_obs[p];
+        a.pred[p] = acc;
+        a.rbar[p] = 2.0f * wp * r;
+        l = (double)(wp * r * r);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-        a.tile_loss[t] = s;
-        const unsigned long long np = (unsigned long long)(pe - ps) * (unsigned long long)nrec;
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        a.tile_loss[t] = sum;
+        const unsigned long long np =
+            (unsigned long long)(pe - ps) * (unsigned long long)(a.tile_rec_end[t] - a.tile_rec_start[t]);
         atomicAdd(&a.counters->pairs, np);
         if (a.pairs_total) atomicAdd(a.pairs_total, np);
     }
 }
 
 // ---------------------------------------------------------------- backward
-// One CTA per tile, thread per record (two records per thread at a time);
-// the tile's pixels (b, a, r_bar) are broadcast from shared memory.  For each
+// One CTA per work item, thread per record (two records per thread); the
+// tile's pixels (b, a, r_bar) are broadcast from shared memory.  For each
 // (tile, record) the 6 moments sum_p g, g db, g da, g db^2, g db da, g da^2 with
 // g = r_bar_p exp2(q(p)) are written to the record's key slot (no atomics).
-__global__ void __launch_bounds__(kThreads) k_backward(EvalArgs a) {
-    __shared__ float4 spx[kMaxTilePx];
-    const int t = blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
+    extern __shared__ float4 spx[];  // tile_px entries
+    const int i = blockIdx.x;
+    if (i >= min(*a.n_items, a.cap_items)) return;
+    const int t = a.item_tile[i];
+    const int c = i - a.item_first[t];
     const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-    const int rs = a.tile_rec_start[t], re = a.tile_rec_end[t];
+    const int rs = a.tile_rec_start[t] + c * kItemRecs;
+    const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
     if (ps >= pe || rs >= re) return;
     const SliceDev &S = a.slices[a.tile_slice[t]];
     const int npx = pe - ps;
@@ -541,50 +534,50 @@ __global__ void __launch_bounds__(kThreads) k_backward(EvalArgs a) {
         spx[s] = make_float4((float)(loc - row * S.W) - S.cx0, (float)row - S.cy0, a.rbar[p], 0.f);
     }
     __syncthreads();
-    for (int r0 = rs + threadIdx.x; r0 < re; r0 += 2 * kThreads) {
-        const int r1 = r0 + kThreads;
-        const bool v1 = r1 < re;
-        const Rec A = a.trec[r0];
-        const Rec B = v1 ? a.trec[r1] : A;
-        float m0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, m1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int r0 = rs + threadIdx.x;
+    if (r0 >= re) return;
+    const int r1 = r0 + kThreads;
+    const bool v1 = r1 < re;
+    const Rec A = a.trec[r0];
+    const Rec B = v1 ? a.trec[r1] : A;
+    float m0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, m1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
-        for (int i = 0; i < npx; ++i) {
-            const float4 P = spx[i];
-            {
-                const float dx = P.x - A.a.x, dy = P.y - A.a.y;
-                const float u = fmaf(A.a.z, dx, A.a.w * dy);
-                const float q = fmaf(u, dx, A.b.x * dy * dy);
-                const float g = P.z * ex2_approx(q);
-                const float gx = g * dx, gy = g * dy;
-                m0[0] += g;
-                m0[1] += gx;
-                m0[2] += gy;
-                m0[3] = fmaf(gx, dx, m0[3]);
-                m0[4] = fmaf(gx, dy, m0[4]);
-                m0[5] = fmaf(gy, dy, m0[5]);
-            }
-            {
-                const float dx = P.x - B.a.x, dy = P.y - B.a.y;
-                const float u = fmaf(B.a.z, dx, B.a.w * dy);
-                const float q = fmaf(u, dx, B.b.x * dy * dy);
-                const float g = P.z * ex2_approx(q);
-                const float gx = g * dx, gy = g * dy;
-                m1[0] += g;
-                m1[1] += gx;
-                m1[2] += gy;
-                m1[3] = fmaf(gx, dx, m1[3]);
-                m1[4] = fmaf(gx, dy, m1[4]);
-                m1[5] = fmaf(gy, dy, m1[5]);
-            }
+    for (int k = 0; k < npx; ++k) {
+        const float4 P = spx[k];
+        {
+            const float dx = P.x - A.a.x, dy = P.y - A.a.y;
+            const float u = fmaf(A.a.z, dx, A.a.w * dy);
+            const float q = fmaf(u, dx, A.b.x * dy * dy);
+            const float g = P.z * ex2_approx(q);
+            const float gx = g * dx, gy = g * dy;
+            m0[0] += g;
+            m0[1] += gx;
+            m0[2] += gy;
+            m0[3] = fmaf(gx, dx, m0[3]);
+            m0[4] = fmaf(gx, dy, m0[4]);
+            m0[5] = fmaf(gy, dy, m0[5]);
         }
-        const int k0 = __float_as_int(A.b.w);
-        a.mom[2 * k0] = make_float4(m0[0], m0[1], m0[2], m0[3]);
-        a.mom[2 * k0 + 1] = make_float4(m0[4], m0[5], 0.f, 0.f);
-        if (v1) {
-            const int k1 = __float_as_int(B.b.w);
-            a.mom[2 * k1] = make_float4(m1[0], m1[1], m1[2], m1[3]);
-            a.mom[2 * k1 + 1] = make_float4(m1[4], m1[5], 0.f, 0.f);
+        {
+            const float dx = P.x - B.a.x, dy = P.y - B.a.y;
+            const float u = fmaf(B.a.z, dx, B.a.w * dy);
+            const float q = fmaf(u, dx, B.b.x * dy * dy);
+            const float g = P.z * ex2_approx(q);
+            const float gx = g * dx, gy = g * dy;
+            m1[0] += g;
+            m1[1] += gx;
+            m1[2] += gy;
+            m1[3] = fmaf(gx, dx, m1[3]);
+            m1[4] = fmaf(gx, dy, m1[4]);
+            m1[5] = fmaf(gy, dy, m1[5]);
         }
+    }
+    const int k0 = __float_as_int(A.b.w);
+    a.mom[2 * k0] = make_float4(m0[0], m0[1], m0[2], m0[3]);
+    a.mom[2 * k0 + 1] = make_float4(m0[4], m0[5], 0.f, 0.f);
+    if (v1) {
+        const int k1 = __float_as_int(B.b.w);
+        a.mom[2 * k1] = make_float4(m1[0], m1[1], m1[2], m1[3]);
+        a.mom[2 * k1 + 1] = make_float4(m1[4], m1[5], 0.f, 0.f);
     }
 }
 
@@ -904,20 +897,32 @@ void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, con
     k_gather<<<cdiv(cap_keys, 256), 256, 0, st>>>(rec, vals, key_rec, n_keys, cap_keys, trec);
     counted();
 }
-template <bool COUNT>
-static void forward_variant(const EvalArgs &a, int tile_px, cudaStream_t st) {
-    if (a.n_tiles <= 0) return;
-    if (tile_px <= kThreads) k_forward<1, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
-    else if (tile_px <= 2 * kThreads) k_forward<2, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
-    else if (tile_px <= 4 * kThreads) k_forward<4, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
-    else k_forward<8, COUNT><<<a.n_tiles, kThreads, 0, st>>>(a);
+static inline int round_warp(int n) { return (n + 31) / 32 * 32; }
+void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre, int n_tiles, int *cnt,
+                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    if (phase == 0) k_item_count<<<cdiv(n_tiles, 256), 256, 0, st>>>(tps, tpe, trs, tre, n_tiles, cnt);
+    else k_item_fill<<<cdiv(n_tiles, 256), 256, 0, st>>>(first, n_tiles, item_tile, cap_items);
     counted();
 }
-void launch_forward(const EvalArgs &a, int tile_px, cudaStream_t st) { forward_variant<false>(a, tile_px, st); }
-void launch_count_pairs(const EvalArgs &a, int tile_px, cudaStream_t st) { forward_variant<true>(a, tile_px, st); }
-void launch_backward(const EvalArgs &a, cudaStream_t st) {
+void launch_forward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return;
-    k_backward<<<a.n_tiles, kThreads, 0, st>>>(a);
+    const int nt = round_warp(a.tile_px);
+    if (a.cap_items > 0) {
+        k_fwd_items<false><<<a.cap_items, nt, 0, st>>>(a);
+        counted();
+    }
+    k_fwd_reduce<<<a.n_tiles, nt, 0, st>>>(a);
+    counted();
+}
+void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
+    if (a.n_tiles <= 0 || a.cap_items <= 0) return;
+    k_fwd_items<true><<<a.cap_items, round_warp(a.tile_px), 0, st>>>(a);
+    counted();
+}
+void launch_backward(const EvalArgs &a, cudaStream_t st) {
+    if (a.n_tiles <= 0 || a.cap_items <= 0) return;
+    k_bwd_items<<<a.cap_items, kThreads, (size_t)a.tile_px * sizeof(float4), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st) {

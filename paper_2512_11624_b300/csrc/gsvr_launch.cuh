@@ -51,6 +51,12 @@ struct EvalArgs {
     unsigned long long *pairs_total;  // running sum of visited pairs (timing)
     unsigned long long *useful;       // count mode: pairs inside the cut
     float qcut;                       // count mode: log2(cutoff_rel)
+    const int *item_tile;             // tile of each work item
+    const int *item_first;            // first item of each tile (n_tiles + 1)
+    const int *n_items;               // device count
+    float *part;                      // per-item partial pixel sums (cap_items x tile_px)
+    int cap_items;
+    int tile_px;                      // tile_w * tile_h
     int n_tiles;
     unsigned *status;
 };
@@ -82,8 +88,11 @@ void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_key
                             cudaStream_t st);
 void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, const int *n_keys, int cap_keys,
                    Rec *trec, cudaStream_t st);
-void launch_forward(const EvalArgs &a, int tile_px, cudaStream_t st);
-void launch_count_pairs(const EvalArgs &a, int tile_px, cudaStream_t st);
+// phase 0: items per tile into cnt; phase 1: item -> tile from the scanned offsets `first`
+void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre, int n_tiles, int *cnt,
+                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st);
+void launch_forward(const EvalArgs &a, cudaStream_t st);
+void launch_count_pairs(const EvalArgs &a, cudaStream_t st);
 long long launch_count();  // kernels launched by this library so far
 void note_launches(int n); // count kernels launched from other translation units
 void launch_backward(const EvalArgs &a, cudaStream_t st);

@@ -210,8 +210,8 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     // per record: Rec + tile box + key count + key offset; per key: key, key_rec, sorted key and
     // value, two ping-pong words, tile-ordered record, backward moments (unused here), histogram share
     const size_t per_rec = sizeof(Rec) + sizeof(int2) + 2 * sizeof(int);
-    const size_t per_key = 6 * sizeof(uint32_t) + sizeof(Rec) + 1;
-    const size_t slack = 64 * 256 + 4096 * sizeof(int);
+    const size_t per_key = 6 * sizeof(uint32_t) + sizeof(Rec) + 1 + (kTile * kTile * sizeof(float)) / kItemRecs + 1;
+    const size_t slack = 64 * 256 + 4096 * sizeof(int) + (size_t)(2 * T + 8) * (sizeof(int) + kTile * kTile * sizeof(float));
     if (fixed + slack + per_rec + kKeysPerRecord * per_key >= kScratchBytes) {
         set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch");
         return GSVR_ERR_INVALID_ARG;
@@ -231,6 +231,11 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     uint32_t *d_va = cv.take<uint32_t>(cap_keys);
     Rec *d_trec = cv.take<Rec>(cap_keys);
     int *d_hist = cv.take<int>((size_t)256 * sort_blocks(cap_keys) + 1);
+    const int cap_items = (int)(T + cap_keys / kItemRecs + 2);
+    int *d_item_cnt = cv.take<int>(T + 1);
+    int *d_item_first = cv.take<int>(T + 1);
+    int *d_item_tile = cv.take<int>(cap_items);
+    float *d_part = cv.take<float>((size_t)cap_items * kTile * kTile);
     const size_t scan_n = std::max<size_t>({(size_t)N + 1, (size_t)P + 1, (size_t)cap_rec + 1,
                                             (size_t)256 * (size_t)sort_blocks(cap_keys) + 1});
     const int bsum_blocks = (int)((scan_n + kScanTile - 1) / kScanTile + 2);
@@ -325,6 +330,9 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     NA_CK(radix_sort_pairs(d_keys, nullptr, d_ks, d_vs, &d_cnt->n_keys, cap_keys, bits, sort_s, st));
     launch_tile_rec_ranges(d_ks, &d_cnt->n_keys, cap_keys, d_trs, d_tre, st);
     launch_gather(d_rec, d_vs, d_key_rec, &d_cnt->n_keys, cap_keys, d_trec, st);
+    launch_items(d_tps, d_tpe, d_trs, d_tre, (int)T, d_item_cnt, nullptr, nullptr, 0, 0, st);
+    NA_CK(scan_exclusive(d_item_cnt, d_item_first, nullptr, (int)T, (int)T, &d_cnt->n_items, scs, st));
+    launch_items(nullptr, nullptr, nullptr, nullptr, (int)T, nullptr, d_item_first, d_item_tile, cap_items, 1, st);
     EvalArgs e{};
     e.trec = d_trec;
     e.tile_rec_start = d_trs;
@@ -340,9 +348,15 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     e.rbar = d_rbar;
     e.tile_loss = d_tile_loss;
     e.counters = d_cnt;
+    e.item_tile = d_item_tile;
+    e.item_first = d_item_first;
+    e.n_items = &d_cnt->n_items;
+    e.part = d_part;
+    e.cap_items = cap_items;
+    e.tile_px = kTile * kTile;
     e.n_tiles = (int)T;
     e.status = d_status;
-    launch_forward(e, kTile * kTile, st);
+    launch_forward(e, st);
     launch_loss_reduce(d_tile_loss, (int)T, loss, d_status, st);
     NA_CK(cudaGetLastError());
     unsigned stt = 0;

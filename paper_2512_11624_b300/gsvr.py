@@ -27,7 +27,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_set_observations", "gsvr_set_gaussians", "gsvr_set_poses", "gsvr_set_frozen",
            "gsvr_set_pixel_sample", "gsvr_sample_pixels", "gsvr_forward", "gsvr_backward", "gsvr_adam_step",
            "gsvr_step_host", "gsvr_get_sample", "gsvr_get_views", "gsvr_get_stats", "gsvr_sync_status",
-           "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc"]
+           "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
+           "gsvr_alu_peaks"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -101,6 +102,8 @@ def _load():
         "gsvr_timing_reset": ([vp], C.c_int),
         "gsvr_get_kernel_times": ([vp, C.POINTER(KernelTimes)], C.c_int),
         "gsvr_count_pairs": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "gsvr_alu_peaks": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
+                           C.c_int),
         "gsvr_forward_noalloc": ([C.c_int, vp, i32, C.POINTER(StackDesc), i64, vp, vp, vp, i64, C.c_float, i32, vp,
                                   vp, C.c_char_p, i32], C.c_int),
     }
@@ -302,6 +305,13 @@ def gsvr_count_pairs(ctx):
     u, e = C.c_int64(), C.c_int64()
     _check(ctx, lib.gsvr_count_pairs(ctx, C.byref(u), C.byref(e)))
     return int(u.value), int(e.value)
+
+
+def gsvr_alu_peaks(device=0):
+    """(FFMA instructions/s, ex2.approx instructions/s, SM count) measured on `device`."""
+    f, e, n = C.c_double(), C.c_double(), C.c_double()
+    _check(None, lib.gsvr_alu_peaks(int(device), C.byref(f), C.byref(e), C.byref(n)))
+    return f.value, e.value, int(n.value)
 
 
 def gsvr_forward_noalloc(stacks, N, theta, I, idx, pred, loss, device=0, stream=None, cutoff_rel=1e-7,

@@ -297,3 +297,20 @@ def fetal(seed=0, with_truth=False):
         out["motion"] = motion
         out["phantom"] = ph
     return out
+
+
+def first_stacks(case, n):
+    """The same case restricted to its first n stacks (observations, mask, poses
+    cut accordingly); the pixel sample shrinks with the pixel count."""
+    stacks = case["stacks"][:n]
+    P = n_pixels_total(stacks)
+    M = n_slices_total(stacks)
+    N = case["N"]
+    out = dict(case)
+    out["stacks"] = stacks
+    out["I"] = case["I"][:P]
+    out["mask"] = case["mask"][:P]
+    out["theta"] = np.concatenate([case["theta"][:11 * N], case["theta"][11 * N:11 * N + 6 * M]])
+    frac = P / n_pixels_total(case["stacks"])
+    out["n_sample"] = min(int(out["mask"].sum()), int(case["n_sample"] * frac))
+    return out
