@@ -448,8 +448,6 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
             v.tile_base = (int)T;
             v.pix_base = (int)P;
             v.stack = s;
-            for (int e = 0; e < 9; ++e) v.R[e] = st.R0[e];
-            for (int a = 0; a < 3; ++a) v.t[a] = st.c0[a];
             P += (int64_t)d.H * d.W;
             T += (int64_t)tx * ty;
             if (P >= (int64_t)INT32_MAX / 2 || T >= (int64_t)INT32_MAX / 2)

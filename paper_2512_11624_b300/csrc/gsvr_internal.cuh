@@ -20,21 +20,29 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // Device status word bits (latched; read by gsvr_sync_status).
 enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
 
-// Per-slice frame and geometry.  R, t are rewritten from the pose every
-// forward (Sec. 3.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau); the rest is
-// fixed by the stack description.
+// Per-slice frame and geometry.  The frame fields are rewritten from the pose
+// every forward (Sec. 3.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau, computed in
+// float64 per slice and stored as float32, plus float32 (hi, lo) pairs for the
+// three projections that fix the record centres); the rest is fixed by the
+// stack description.
 struct SliceDev {
-    double R[9];    // world-from-slice rotation, row-major
-    double t[3];    // world position of the slice centre
-    float var[3];   // Sigma_PSF diagonal (slice axes), mm^2
-    float dx, dy;   // pixel spacing (mm)
-    float cx0, cy0; // (W-1)/2, (H-1)/2
+    float R[9];               // world-from-slice rotation, row-major (columns = slice axes)
+    float t[3];               // world position of the slice centre
+    float ux_h[3], ux_l[3];   // slice x axis / dx  (pixels per mm), hi + lo
+    float uy_h[3], uy_l[3];   // slice y axis / dy
+    float nz_h[3], nz_l[3];   // slice normal (mm per mm)
+    float ox_h, ox_l;         // (x axis . t) / dx
+    float oy_h, oy_l;         // (y axis . t) / dy
+    float oz_h, oz_l;         // normal . t
+    float var[3];             // Sigma_PSF diagonal (slice axes), mm^2
+    float dx, dy;             // pixel spacing (mm)
+    float cx0, cy0;           // (W-1)/2, (H-1)/2
     int H, W;
     int tiles_x, tiles_y;
-    int tile_base;  // global id of the slice's first tile
-    int pix_base;   // global index of the slice's first pixel
+    int tile_base;            // global id of the slice's first tile
+    int pix_base;             // global index of the slice's first pixel
     int stack;
-    int pad_;
+    int pad_[3];
 };
 
 struct SliceStatic {

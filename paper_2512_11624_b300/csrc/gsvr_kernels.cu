@@ -70,26 +70,49 @@ __device__ __forceinline__ void rodrigues_d(const double r[3], double R[9]) {
         }
 }
 
-// Everything the record and its gradient need about one (slice, Gaussian) pair.
+// Double-single arithmetic (a value carried as an unevaluated float32 sum
+// hi + lo): TwoSum (Knuth) and the FMA-based exact product.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// u . x - o with u, o given as (hi, lo) pairs and x exact float32; result to
+// ~2^-44 relative of the terms, returned rounded to float32 (hi) plus remainder (lo).
+__device__ __forceinline__ float ds_dot_sub(const float uh[3], const float ul[3], const float x[3], float oh,
+                                            float ol, float &lo) {
+    const float p0 = __fmul_rn(uh[0], x[0]), p1 = __fmul_rn(uh[1], x[1]), p2 = __fmul_rn(uh[2], x[2]);
+    const float e0 = fmaf(uh[0], x[0], -p0), e1 = fmaf(uh[1], x[1], -p1), e2 = fmaf(uh[2], x[2], -p2);
+    float s, t1, t2, t3;
+    two_sum(p0, p1, s, t1);
+    two_sum(s, p2, s, t2);
+    two_sum(s, -oh, s, t3);
+    const float small = ((e0 + e1) + e2) + ((t1 + t2) + t3) + (ul[0] * x[0] + ul[1] * x[1] + ul[2] * x[2]) - ol;
+    float hi;
+    two_sum(s, small, hi, lo);
+    return hi;
+}
+
+// Everything the record and its gradient need about one (slice, Gaussian) pair
+// (float32; the mean's slice coordinates in double-single).
 struct RecGeom {
-    double d[3];      // mu - t (world)
-    double mz;        // slice-normal coordinate of the mean
-    double cxm, cym;  // conditional centre in slice mm
-    float R[9];       // slice rotation (float)
+    float R[9];       // slice rotation
+    float d[3];       // mu - t (world)
+    float mz;         // slice-normal coordinate of the mean
     float Kxx, Kyy, Kzz, Kxy, Kxz, Kyz;
     float qz;         // m_z^2 / K_zz
     float M2xx, M2yy, M2xy, det2;
     float P2xx, P2yy, P2xy;
     float w0;         // w / c_j
+    float cb, ca;     // conditional centre, slice-centred pixel units (centre pass only)
 };
 
-// Cheap float32 rejection before the float64 geometry: |m_z| against the cut
-// with a relative margin (the exact test follows in rec_geom).
+// Cheap float32 rejection before the exact test: |m_z| against the cut with a
+// relative margin (the exact test follows in rec_geom).
 __device__ __forceinline__ bool slab_candidate(const float4 g0, const float4 g1, const float mu[3],
                                                const SliceDev &S, float rc2) {
-    const float nx = (float)S.R[2], ny = (float)S.R[5], nz = (float)S.R[8];
-    const float mz = nx * (mu[0] - (float)S.t[0]) + ny * (mu[1] - (float)S.t[1]) + nz * (mu[2] - (float)S.t[2]);
-    // n^T Sigma n
+    const float nx = S.nz_h[0], ny = S.nz_h[1], nz = S.nz_h[2];
+    const float mz = nx * mu[0] + ny * mu[1] + nz * mu[2] - S.oz_h;
     const float sx = g0.x * nx + g0.w * ny + g1.x * nz;
     const float sy = g0.w * nx + g0.y * ny + g1.y * nz;
     const float sz = g1.x * nx + g1.y * ny + g0.z * nz;
@@ -97,13 +120,14 @@ __device__ __forceinline__ bool slab_candidate(const float4 g0, const float4 g1,
     return mz * mz <= (rc2 * 1.001f + 1e-3f) * kzz + 1e-3f;
 }
 
+template <bool CENTRE>
 __device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const float mu[3], const SliceDev &S,
                                          float rc2, int norm_mode, RecGeom &G) {
-    for (int a = 0; a < 3; ++a) G.d[a] = (double)mu[a] - S.t[a];
-    const double m0 = S.R[0] * G.d[0] + S.R[3] * G.d[1] + S.R[6] * G.d[2];
-    const double m1 = S.R[1] * G.d[0] + S.R[4] * G.d[1] + S.R[7] * G.d[2];
-    const double m2 = S.R[2] * G.d[0] + S.R[5] * G.d[1] + S.R[8] * G.d[2];
-    for (int e = 0; e < 9; ++e) G.R[e] = (float)S.R[e];
+    float zlo;
+    const float zhi = ds_dot_sub(S.nz_h, S.nz_l, mu, S.oz_h, S.oz_l, zlo);
+    G.mz = zhi + zlo;
+    for (int e = 0; e < 9; ++e) G.R[e] = S.R[e];
+    for (int a = 0; a < 3; ++a) G.d[a] = mu[a] - S.t[a];
     const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
     float T[9];  // Sigma R
     for (int a = 0; a < 3; ++a)
@@ -116,8 +140,7 @@ __device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const
     G.Kxy = K(0, 1);
     G.Kxz = K(0, 2);
     G.Kyz = K(1, 2);
-    G.mz = m2;
-    G.qz = (float)(m2 * m2 / (double)G.Kzz);
+    G.qz = G.mz * G.mz / G.Kzz;
     if (!(G.qz <= rc2)) return false;
     const float ik = 1.0f / G.Kzz;
     G.M2xx = G.Kxx - G.Kxz * G.Kxz * ik;
@@ -128,27 +151,31 @@ __device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const
     G.P2xx = G.M2yy * idet;
     G.P2yy = G.M2xx * idet;
     G.P2xy = -G.M2xy * idet;
-    G.cxm = m0 - (double)(G.Kxz * ik) * m2;
-    G.cym = m1 - (double)(G.Kyz * ik) * m2;
     if (norm_mode == GSVR_NORM_EXACT)
         G.w0 = expf(g1.z - 0.5f * G.qz) * rsqrtf(G.Kzz * G.det2);
     else
         G.w0 = expf(-0.5f * G.qz);
+    if (CENTRE) {
+        // centre = m_xy - K_xz,yz m_z / K_zz, in pixels: (u . mu - o) - (K_xz / K_zz) m_z / dx
+        float xlo, ylo;
+        const float xhi = ds_dot_sub(S.ux_h, S.ux_l, mu, S.ox_h, S.ox_l, xlo);
+        const float yhi = ds_dot_sub(S.uy_h, S.uy_l, mu, S.oy_h, S.oy_l, ylo);
+        G.cb = (xhi - G.Kxz * ik * G.mz / S.dx) + xlo;
+        G.ca = (yhi - G.Kyz * ik * G.mz / S.dy) + ylo;
+    }
     return true;
 }
 
 // Tile bounding box of the record's ellipse {q <= r_c^2} on the slice.
-__device__ __forceinline__ bool rec_bbox(const RecGeom &G, const SliceDev &S, float rc2, int tw, int th,
-                                         float &cb, float &ca, int &tx0, int &tx1, int &ty0, int &ty1) {
+__device__ __forceinline__ bool rec_bbox(const RecGeom &G, const SliceDev &S, float rc2, int tw, int th, int &tx0,
+                                         int &tx1, int &ty0, int &ty1) {
     const float rho2 = fmaxf(rc2 - G.qz, 0.0f);
     const float hx = sqrtf(rho2 * G.M2xx) / S.dx;
     const float hy = sqrtf(rho2 * G.M2yy) / S.dy;
-    cb = (float)(G.cxm / (double)S.dx);
-    ca = (float)(G.cym / (double)S.dy);
-    const float blo = fminf(fmaxf(cb + S.cx0 - hx, -1.0f), (float)S.W);
-    const float bhi = fminf(fmaxf(cb + S.cx0 + hx, -1.0f), (float)S.W);
-    const float alo = fminf(fmaxf(ca + S.cy0 - hy, -1.0f), (float)S.H);
-    const float ahi = fminf(fmaxf(ca + S.cy0 + hy, -1.0f), (float)S.H);
+    const float blo = fminf(fmaxf(G.cb + S.cx0 - hx, -1.0f), (float)S.W);
+    const float bhi = fminf(fmaxf(G.cb + S.cx0 + hx, -1.0f), (float)S.W);
+    const float alo = fminf(fmaxf(G.ca + S.cy0 - hy, -1.0f), (float)S.H);
+    const float ahi = fminf(fmaxf(G.ca + S.cy0 + hy, -1.0f), (float)S.H);
     const int b0 = max(0, (int)ceilf(blo)), b1 = min(S.W - 1, (int)floorf(bhi));
     const int a0 = max(0, (int)ceilf(alo)), a1 = min(S.H - 1, (int)floorf(ahi));
     if (!(G.det2 > 0.0f) || b0 > b1 || a0 > a1) return false;
@@ -191,6 +218,11 @@ __global__ void k_gauss_prep(const float *__restrict__ th, int N, float4 *__rest
     gpre[2 * j + 1] = make_float4(S(0, 2), S(1, 2), p[3] + p[4] + p[5], p[10]);
 }
 
+__device__ __forceinline__ void split_pair(double v, float &h, float &l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
 __global__ void k_pose_prep(const float *__restrict__ pose, const SliceStatic *__restrict__ ss,
                             SliceDev *__restrict__ sd, int M, unsigned *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,14 +235,26 @@ __global__ void k_pose_prep(const float *__restrict__ pose, const SliceStatic *_
         fin = fin && isfinite(r[k]) && isfinite(tau[k]);
     }
     if (!fin) atomicOr(status, ST_NONFINITE);
-    double Q[9];
+    double Q[9], R[9], t[3];
     rodrigues_d(r, Q);
     const SliceStatic s = ss[i];
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b)
-            sd[i].R[3 * a + b] = Q[3 * a] * s.R0[b] + Q[3 * a + 1] * s.R0[3 + b] + Q[3 * a + 2] * s.R0[6 + b];
-        sd[i].t[a] = Q[3 * a] * s.c0[0] + Q[3 * a + 1] * s.c0[1] + Q[3 * a + 2] * s.c0[2] + tau[a];
+            R[3 * a + b] = Q[3 * a] * s.R0[b] + Q[3 * a + 1] * s.R0[3 + b] + Q[3 * a + 2] * s.R0[6 + b];
+        t[a] = Q[3 * a] * s.c0[0] + Q[3 * a + 1] * s.c0[1] + Q[3 * a + 2] * s.c0[2] + tau[a];
     }
+    SliceDev &o = sd[i];
+    const double dx = o.dx, dy = o.dy;
+    for (int e = 0; e < 9; ++e) o.R[e] = (float)R[e];
+    for (int a = 0; a < 3; ++a) {
+        o.t[a] = (float)t[a];
+        split_pair(R[3 * a] / dx, o.ux_h[a], o.ux_l[a]);
+        split_pair(R[3 * a + 1] / dy, o.uy_h[a], o.uy_l[a]);
+        split_pair(R[3 * a + 2], o.nz_h[a], o.nz_l[a]);
+    }
+    split_pair((R[0] * t[0] + R[3] * t[1] + R[6] * t[2]) / dx, o.ox_h, o.ox_l);
+    split_pair((R[1] * t[0] + R[4] * t[1] + R[7] * t[2]) / dy, o.oy_h, o.oy_l);
+    split_pair(R[2] * t[0] + R[5] * t[1] + R[8] * t[2], o.oz_h, o.oz_l);
 }
 
 // ---------------------------------------------------------------- sampling
@@ -298,10 +342,9 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
             const SliceDev &S = ssl[ii];
             if (!slab_candidate(g0, g1, mu, S, a.rc2)) continue;
             RecGeom G;
-            if (!rec_geom(g0, g1, mu, S, a.rc2, a.norm_mode, G)) continue;
-            float cb, ca;
+            if (!rec_geom<true>(g0, g1, mu, S, a.rc2, a.norm_mode, G)) continue;
             int tx0, tx1, ty0, ty1;
-            if (!rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, cb, ca, tx0, tx1, ty0, ty1)) continue;
+            if (!rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, tx0, tx1, ty0, ty1)) continue;
             const int nk = count_live_tiles(S, tx0, tx1, ty0, ty1, a.tile_px_start, a.tile_px_end);
             if (nk == 0) continue;
             if (EMIT) {
@@ -309,7 +352,7 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
                 if (r < a.cap_rec) {
                     const float L = kNegHalfLog2e;
                     Rec R;
-                    R.a = make_float4(cb, ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
+                    R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
                     R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz,
                                       __int_as_float(i0 + ii));
                     a.rec[r] = R;
@@ -635,7 +678,7 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
             const int i = __float_as_int(a.rec[r].b.w);
             const SliceDev &SL = a.slices[i];
             RecGeom G;
-            if (!rec_geom(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) continue;
+            if (!rec_geom<false>(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) continue;
             // moments to slice millimetres
             const float dx = SL.dx, dy = SL.dy;
             Sx *= dx;
@@ -656,7 +699,7 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
             const float GMxy = 0.5f * w * (T00 * G.P2xy + T01 * G.P2yy);
             const float GMyy = 0.5f * w * (T10 * G.P2xy + T11 * G.P2yy);
             const float ik = 1.0f / G.Kzz, kx = G.Kxz, ky = G.Kyz;
-            const float mz = (float)G.mz;
+            const float mz = G.mz;
             // M2 = K_xy - k k^T / K_zz
             const float Mk0 = GMxx * kx + GMxy * ky, Mk1 = GMxy * kx + GMyy * ky;
             float Gkx = -2.f * Mk0 * ik, Gky = -2.f * Mk1 * ik;
@@ -705,7 +748,7 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
             // slice frame: t -> -R Gm ; R -> d Gm^T + 2 Sigma_j R GK
             float GR[12];
             for (int p = 0; p < 3; ++p) {
-                const float dp = (float)G.d[p];
+                const float dp = G.d[p];
                 for (int q = 0; q < 3; ++q) {
                     float s = Sg[3 * p] * RG[q] + Sg[3 * p + 1] * RG[3 + q] + Sg[3 * p + 2] * RG[6 + q];
                     GR[3 * p + q] = dp * Gm[q] + 2.f * s;
