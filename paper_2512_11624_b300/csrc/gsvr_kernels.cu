@@ -27,6 +27,7 @@
 //   adam         fused, per-group learning rates
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "gsvr_launch.cuh"
@@ -644,124 +645,146 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, i
 // ------------------------------------------------------------- gradients
 // dL/d(record) -> dL/d(m, K) -> Gaussian (mu, Sigma_j, c, log det) and slice
 // frame (R_i, t_i).  Moments arrive in slice-centred pixel units about the
-// record centre; all of this is float32 except the frame offsets.
-__global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
+// record centre.  A half-warp owns one Gaussian and each of its lanes one of
+// the Gaussian's records (records are stored Gaussian-major), so the lanes of
+// a half-warp touch distinct slices when they add their slice-frame terms into
+// the block's shared-memory accumulators; the 11 Gaussian partials are then
+// reduced with half-warp shuffles.
+__device__ __forceinline__ void record_chain(const GradArgs &a, int r, const float4 g0, const float4 g1,
+                                             const float mu[3], const float Sg[9], float gmu[3], float GS[6],
+                                             float &gc, float &glog, float *pacc) {
+    float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
+    const int k_end = min(a.key_off[r + 1], a.cap_keys);
+    for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
+        const float4 u = a.mom[2 * k], v = a.mom[2 * k + 1];
+        S0 += u.x;
+        Sx += u.y;
+        Sy += u.z;
+        Sxx += u.w;
+        Sxy += v.x;
+        Syy += v.y;
+    }
+    if (S0 == 0.f && Sx == 0.f && Sy == 0.f && Sxx == 0.f && Sxy == 0.f && Syy == 0.f) return;
+    const int i = __float_as_int(a.rec[r].b.w);
+    const SliceDev &SL = a.slices[i];
+    RecGeom G;
+    if (!rec_geom<false>(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) return;
+    const float dx = SL.dx, dy = SL.dy;
+    Sx *= dx;
+    Sy *= dy;
+    Sxx *= dx * dx;
+    Sxy *= dx * dy;
+    Syy *= dy * dy;
+    const float w = g1.w * G.w0;
+    const float Gw = S0 * w;  // dL/d log w
+    gc += S0 * G.w0;
+    // centre: dL/dc = w P2 S1
+    const float Gcx = w * (G.P2xx * Sx + G.P2xy * Sy);
+    const float Gcy = w * (G.P2xy * Sx + G.P2yy * Sy);
+    // conic: dL/dP2 = -1/2 w S2 -> dL/dM2 = 1/2 w P2 S2 P2
+    const float T00 = G.P2xx * Sxx + G.P2xy * Sxy, T01 = G.P2xx * Sxy + G.P2xy * Syy;
+    const float T10 = G.P2xy * Sxx + G.P2yy * Sxy, T11 = G.P2xy * Sxy + G.P2yy * Syy;
+    const float GMxx = 0.5f * w * (T00 * G.P2xx + T01 * G.P2xy);
+    const float GMxy = 0.5f * w * (T00 * G.P2xy + T01 * G.P2yy);
+    const float GMyy = 0.5f * w * (T10 * G.P2xy + T11 * G.P2yy);
+    const float ik = 1.0f / G.Kzz, kx = G.Kxz, ky = G.Kyz;
+    const float mz = G.mz;
+    // M2 = K_xy - k k^T / K_zz
+    const float Mk0 = GMxx * kx + GMxy * ky, Mk1 = GMxy * kx + GMyy * ky;
+    float Gkx = -2.f * Mk0 * ik, Gky = -2.f * Mk1 * ik;
+    float Gkap = (kx * Mk0 + ky * Mk1) * ik * ik;
+    // centre c = m_xy - k m_z / K_zz
+    const float kGc = kx * Gcx + ky * Gcy;
+    float Gmz = -kGc * ik;
+    Gkx -= Gcx * mz * ik;
+    Gky -= Gcy * mz * ik;
+    Gkap += kGc * mz * ik * ik;
+    // normal weight exp(-1/2 m_z^2 / K_zz)
+    Gmz -= Gw * mz * ik;
+    Gkap += 0.5f * Gw * mz * mz * ik * ik;
+    float GK[9] = {GMxx, GMxy, 0.5f * Gkx, GMxy, GMyy, 0.5f * Gky, 0.5f * Gkx, 0.5f * Gky, Gkap};
+    if (a.norm_mode == GSVR_NORM_EXACT) {
+        // -1/2 log det K -> -1/2 Gw K^-1 ; 1/2 log det Sigma_j = sum ls -> d ls_k += Gw
+        const float c00 = G.Kyy * G.Kzz - G.Kyz * G.Kyz, c01 = G.Kxz * G.Kyz - G.Kxy * G.Kzz;
+        const float c02 = G.Kxy * G.Kyz - G.Kxz * G.Kyy, c11 = G.Kxx * G.Kzz - G.Kxz * G.Kxz;
+        const float c12 = G.Kxy * G.Kxz - G.Kxx * G.Kyz, c22 = G.Kxx * G.Kyy - G.Kxy * G.Kxy;
+        const float idK = 1.0f / (G.Kxx * c00 + G.Kxy * c01 + G.Kxz * c02);
+        const float h = -0.5f * Gw * idK;
+        GK[0] += h * c00;
+        GK[1] += h * c01;
+        GK[2] += h * c02;
+        GK[3] += h * c01;
+        GK[4] += h * c11;
+        GK[5] += h * c12;
+        GK[6] += h * c02;
+        GK[7] += h * c12;
+        GK[8] += h * c22;
+        glog += Gw;
+    }
+    const float Gm[3] = {Gcx, Gcy, Gmz};
+    const float *R = G.R;
+    float RGm[3];
+    for (int p = 0; p < 3; ++p) RGm[p] = R[3 * p] * Gm[0] + R[3 * p + 1] * Gm[1] + R[3 * p + 2] * Gm[2];
+    for (int p = 0; p < 3; ++p) gmu[p] += RGm[p];
+    float RG[9];  // R GK
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+            RG[3 * p + q] = R[3 * p] * GK[q] + R[3 * p + 1] * GK[3 + q] + R[3 * p + 2] * GK[6 + q];
+    // Sigma_j: R GK R^T (symmetric; xx yy zz xy xz yz)
+    auto RGR = [&](int p, int q) { return RG[3 * p] * R[3 * q] + RG[3 * p + 1] * R[3 * q + 1] + RG[3 * p + 2] * R[3 * q + 2]; };
+    GS[0] += RGR(0, 0);
+    GS[1] += RGR(1, 1);
+    GS[2] += RGR(2, 2);
+    GS[3] += RGR(0, 1);
+    GS[4] += RGR(0, 2);
+    GS[5] += RGR(1, 2);
+    // slice frame: t -> -R Gm ; R -> d Gm^T + 2 Sigma_j R GK
+    float GR[12];
+    for (int p = 0; p < 3; ++p) {
+        for (int q = 0; q < 3; ++q) {
+            const float sm = Sg[3 * p] * RG[q] + Sg[3 * p + 1] * RG[3 + q] + Sg[3 * p + 2] * RG[6 + q];
+            GR[3 * p + q] = G.d[p] * Gm[q] + 2.f * sm;
+        }
+        GR[9 + p] = -RGm[p];
+    }
+    if (a.use_smem) {
+        for (int e = 0; e < 12; ++e) atomicAdd(&pacc[12 * i + e], GR[e]);
+    } else {
+        for (int e = 0; e < 12; ++e) atomicAdd(&a.pose_acc[12 * i + e], (double)GR[e]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
     extern __shared__ float pacc[];  // M x 12 (when use_smem)
     if (a.use_smem) {
         for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) pacc[e] = 0.f;
         __syncthreads();
     }
     const int N = a.N;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < N) {
+    const int lane = threadIdx.x & 31, hl = lane & 15;
+    const int per_block = blockDim.x >> 4;
+    // grid-stride over groups of Gaussians; the block flushes its slice-frame sums once
+    for (int jb = blockIdx.x * per_block; jb < N; jb += gridDim.x * per_block) {
+    const int j = jb + (threadIdx.x >> 4);
+    const bool valid = j < N;
+    float gmu[3] = {0.f, 0.f, 0.f}, GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gc = 0.f, glog = 0.f;
+    if (valid) {
         const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
         const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
-        const float cj = g1.w;
         const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
-        float gmu[3] = {0.f, 0.f, 0.f};
-        float GS[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float gc = 0.f, glog = 0.f;
         const int r_end = min(a.rec_off[j + 1], a.cap_rec);
-        for (int r = a.rec_off[j]; r < r_end; ++r) {
-            float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
-            const int k_end = min(a.key_off[r + 1], a.cap_keys);
-            for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
-                const float4 u = a.mom[2 * k], v = a.mom[2 * k + 1];
-                S0 += u.x;
-                Sx += u.y;
-                Sy += u.z;
-                Sxx += u.w;
-                Sxy += v.x;
-                Syy += v.y;
-            }
-            if (S0 == 0.f && Sx == 0.f && Sy == 0.f && Sxx == 0.f && Sxy == 0.f && Syy == 0.f) continue;
-            const int i = __float_as_int(a.rec[r].b.w);
-            const SliceDev &SL = a.slices[i];
-            RecGeom G;
-            if (!rec_geom<false>(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) continue;
-            // moments to slice millimetres
-            const float dx = SL.dx, dy = SL.dy;
-            Sx *= dx;
-            Sy *= dy;
-            Sxx *= dx * dx;
-            Sxy *= dx * dy;
-            Syy *= dy * dy;
-            const float w = cj * G.w0;
-            const float Gw = S0 * w;  // dL/d log w
-            gc += S0 * G.w0;
-            // centre: dL/dc = w P2 S1
-            const float Gcx = w * (G.P2xx * Sx + G.P2xy * Sy);
-            const float Gcy = w * (G.P2xy * Sx + G.P2yy * Sy);
-            // conic: dL/dP2 = -1/2 w S2 -> dL/dM2 = 1/2 w P2 S2 P2
-            const float T00 = G.P2xx * Sxx + G.P2xy * Sxy, T01 = G.P2xx * Sxy + G.P2xy * Syy;
-            const float T10 = G.P2xy * Sxx + G.P2yy * Sxy, T11 = G.P2xy * Sxy + G.P2yy * Syy;
-            const float GMxx = 0.5f * w * (T00 * G.P2xx + T01 * G.P2xy);
-            const float GMxy = 0.5f * w * (T00 * G.P2xy + T01 * G.P2yy);
-            const float GMyy = 0.5f * w * (T10 * G.P2xy + T11 * G.P2yy);
-            const float ik = 1.0f / G.Kzz, kx = G.Kxz, ky = G.Kyz;
-            const float mz = G.mz;
-            // M2 = K_xy - k k^T / K_zz
-            const float Mk0 = GMxx * kx + GMxy * ky, Mk1 = GMxy * kx + GMyy * ky;
-            float Gkx = -2.f * Mk0 * ik, Gky = -2.f * Mk1 * ik;
-            float Gkap = (kx * Mk0 + ky * Mk1) * ik * ik;
-            // centre c = m_xy - k m_z / K_zz
-            const float kGc = kx * Gcx + ky * Gcy;
-            float Gmz = -kGc * ik;
-            Gkx -= Gcx * mz * ik;
-            Gky -= Gcy * mz * ik;
-            Gkap += kGc * mz * ik * ik;
-            // z weight exp(-1/2 m_z^2 / K_zz)
-            Gmz -= Gw * mz * ik;
-            Gkap += 0.5f * Gw * mz * mz * ik * ik;
-            float GK[9] = {GMxx, GMxy, 0.5f * Gkx, GMxy, GMyy, 0.5f * Gky, 0.5f * Gkx, 0.5f * Gky, Gkap};
-            if (a.norm_mode == GSVR_NORM_EXACT) {
-                // -1/2 log det K -> -1/2 Gw K^-1 ; 1/2 log det Sigma_j = sum ls -> d ls_k += Gw
-                const float c00 = G.Kyy * G.Kzz - G.Kyz * G.Kyz, c01 = G.Kxz * G.Kyz - G.Kxy * G.Kzz;
-                const float c02 = G.Kxy * G.Kyz - G.Kxz * G.Kyy, c11 = G.Kxx * G.Kzz - G.Kxz * G.Kxz;
-                const float c12 = G.Kxy * G.Kxz - G.Kxx * G.Kyz, c22 = G.Kxx * G.Kyy - G.Kxy * G.Kxy;
-                const float idK = 1.0f / (G.Kxx * c00 + G.Kxy * c01 + G.Kxz * c02);
-                const float h = -0.5f * Gw * idK;
-                GK[0] += h * c00;
-                GK[1] += h * c01;
-                GK[2] += h * c02;
-                GK[3] += h * c01;
-                GK[4] += h * c11;
-                GK[5] += h * c12;
-                GK[6] += h * c02;
-                GK[7] += h * c12;
-                GK[8] += h * c22;
-                glog += Gw;
-            }
-            const float Gm[3] = {Gcx, Gcy, Gmz};
-            const float *R = G.R;
-            // mu: R Gm ; Sigma_j: R GK R^T
-            float RGm[3];
-            for (int p = 0; p < 3; ++p) RGm[p] = R[3 * p] * Gm[0] + R[3 * p + 1] * Gm[1] + R[3 * p + 2] * Gm[2];
-            for (int p = 0; p < 3; ++p) gmu[p] += RGm[p];
-            float RG[9];
-            for (int p = 0; p < 3; ++p)
-                for (int q = 0; q < 3; ++q)
-                    RG[3 * p + q] = R[3 * p] * GK[q] + R[3 * p + 1] * GK[3 + q] + R[3 * p + 2] * GK[6 + q];
-            for (int p = 0; p < 3; ++p)
-                for (int q = 0; q < 3; ++q)
-                    GS[3 * p + q] += RG[3 * p] * R[3 * q] + RG[3 * p + 1] * R[3 * q + 1] + RG[3 * p + 2] * R[3 * q + 2];
-            // slice frame: t -> -R Gm ; R -> d Gm^T + 2 Sigma_j R GK
-            float GR[12];
-            for (int p = 0; p < 3; ++p) {
-                const float dp = G.d[p];
-                for (int q = 0; q < 3; ++q) {
-                    float s = Sg[3 * p] * RG[q] + Sg[3 * p + 1] * RG[3 + q] + Sg[3 * p + 2] * RG[6 + q];
-                    GR[3 * p + q] = dp * Gm[q] + 2.f * s;
-                }
-                GR[9 + p] = -RGm[p];
-            }
-            if (a.use_smem) {
-                for (int e = 0; e < 12; ++e) atomicAdd(&pacc[12 * i + e], GR[e]);
-            } else {
-                for (int e = 0; e < 12; ++e) atomicAdd(&a.pose_acc[12 * i + e], (double)GR[e]);
-            }
-        }
+        for (int r = a.rec_off[j] + hl; r < r_end; r += 16)
+            record_chain(a, r, g0, g1, mu, Sg, gmu, GS, gc, glog, pacc);
+    }
+    float v[11] = {gmu[0], gmu[1], gmu[2], GS[0], GS[1], GS[2], GS[3], GS[4], GS[5], gc, glog};
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (valid && hl == 0) {
         // Sigma_j = Rj diag(s^2) Rj^T -> ls, q (through q / |q|)
+        const float GSm[9] = {v[3], v[6], v[7], v[6], v[4], v[8], v[7], v[8], v[5]};
         const float qw = a.theta[6 * N + j], qx = a.theta[7 * N + j], qy = a.theta[8 * N + j], qz = a.theta[9 * N + j];
         const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
@@ -772,11 +795,11 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
         float GRj[9];  // GS Rj
         for (int p = 0; p < 3; ++p)
             for (int q = 0; q < 3; ++q)
-                GRj[3 * p + q] = GS[3 * p] * Rj[q] + GS[3 * p + 1] * Rj[3 + q] + GS[3 * p + 2] * Rj[6 + q];
+                GRj[3 * p + q] = GSm[3 * p] * Rj[q] + GSm[3 * p + 1] * Rj[3 + q] + GSm[3 * p + 2] * Rj[6 + q];
         float dls[3];
         for (int k = 0; k < 3; ++k) {
             const float d = Rj[k] * GRj[k] + Rj[3 + k] * GRj[3 + k] + Rj[6 + k] * GRj[6 + k];
-            dls[k] = 2.f * s2[k] * d + glog;
+            dls[k] = 2.f * s2[k] * d + v[10];
         }
         float GRD[9];  // dL/dRj = 2 GS Rj D
         for (int p = 0; p < 3; ++p)
@@ -794,9 +817,9 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
         }
         const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
         float *g = a.grad;
-        g[j] = gmu[0];
-        g[N + j] = gmu[1];
-        g[2 * N + j] = gmu[2];
+        g[j] = v[0];
+        g[N + j] = v[1];
+        g[2 * N + j] = v[2];
         g[3 * N + j] = dls[0];
         g[4 * N + j] = dls[1];
         g[5 * N + j] = dls[2];
@@ -804,13 +827,14 @@ __global__ void __launch_bounds__(128) k_gauss_grad(GradArgs a) {
         g[7 * N + j] = (gq[1] - x * dot) / qn;
         g[8 * N + j] = (gq[2] - y * dot) / qn;
         g[9 * N + j] = (gq[3] - z * dot) / qn;
-        g[10 * N + j] = gc;
+        g[10 * N + j] = v[9];
+    }
     }
     if (a.use_smem) {
         __syncthreads();
         for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) {
-            const float v = pacc[e];
-            if (v != 0.f) atomicAdd(&a.pose_acc[e], (double)v);
+            const float val = pacc[e];
+            if (val != 0.f) atomicAdd(&a.pose_acc[e], (double)val);
         }
     }
 }
@@ -975,7 +999,15 @@ void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsi
 void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
     if (a.N <= 0) return;
     const size_t smem = a.use_smem ? (size_t)a.M * 12 * sizeof(float) : 0;
-    k_gauss_grad<<<cdiv(a.N, 128), 128, smem, st>>>(a);
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 148;
+    }
+    const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 6);
+    k_gauss_grad<<<blocks, 256, smem, st>>>(a);
     counted();
 }
 void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
