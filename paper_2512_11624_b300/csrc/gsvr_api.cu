@@ -250,6 +250,8 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.part = ctx->d_part.p;
     e.cap_items = std::min(grid_items, ctx->cap_items);
     e.tile_px = ctx->tile_w * ctx->tile_h;
+    e.tile_w = ctx->tile_w;
+    e.tile_h = ctx->tile_h;
     e.n_tiles = ctx->n_tiles;
     e.status = ctx->d_status.p;
     return e;
@@ -482,7 +484,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     ctx->P = P;
     ctx->n_tiles = (int)T;
     int bits = 1;
-    while ((1LL << bits) < T) ++bits;
+    while ((1LL << bits) < T + 1) ++bits;  // tile ids and the sentinel T
     ctx->sort_bits = bits;
     ctx->h_slices = sl;
     ctx->h_static = ss;
@@ -747,6 +749,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.norm_mode = ctx->cfg.norm_mode;
     b.tile_w = ctx->tile_w;
     b.tile_h = ctx->tile_h;
+    b.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
     b.tile_px_start = ctx->d_tile_px_start.p;
     b.tile_px_end = ctx->d_tile_px_end.p;
     b.rec_cnt = ctx->d_rec_cnt.p;
@@ -790,6 +793,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     KeyArgs k{};
     k.rec = ctx->d_rec.p;
     k.rec_tiles = ctx->d_rec_tiles.p;
+    k.rec_nkeys = ctx->d_rec_nkeys.p;
     k.key_off = ctx->d_key_off.p;
     k.slices = ctx->d_slices.p;
     k.tile_px_start = ctx->d_tile_px_start.p;
@@ -797,6 +801,10 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     k.n_rec = &cnt->n_rec;
     k.cap_rec = ctx->cap_rec;
     k.cap_keys = ctx->cap_keys;
+    k.tile_w = ctx->tile_w;
+    k.tile_h = ctx->tile_h;
+    k.n_tiles = ctx->n_tiles;
+    k.qcut = b.qcut;
     k.keys = ctx->d_keys.p;
     k.key_rec = ctx->d_key_rec.p;
     k.status = ctx->d_status.p;
@@ -805,12 +813,11 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     SortScratch ss{ctx->d_keys_alt.p, ctx->d_vals_alt.p, ctx->d_hist.p, scan_scratch(ctx)};
     if (n_keys_max > 0)
         CK(radix_sort_pairs(ctx->d_keys.p, nullptr, ctx->d_keys_sorted.p, ctx->d_vals_sorted.p, &cnt->n_keys,
-                            n_keys_max, ctx->sort_bits, ss, st));
+                            n_keys_max, ctx->sort_bits, ss, st, ctx->d_rec.p, ctx->d_key_rec.p, ctx->d_trec.p));
     CK(cudaMemsetAsync(ctx->d_tile_rec_start.p, 0, sizeof(int) * ctx->n_tiles, st));
     CK(cudaMemsetAsync(ctx->d_tile_rec_end.p, 0, sizeof(int) * ctx->n_tiles, st));
-    launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->d_tile_rec_start.p,
+    launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->n_tiles, ctx->d_tile_rec_start.p,
                            ctx->d_tile_rec_end.p, st);
-    launch_gather(ctx->d_rec.p, ctx->d_vals_sorted.p, ctx->d_key_rec.p, &cnt->n_keys, n_keys_max, ctx->d_trec.p, st);
     {
         gsvr_status si = ensure_item_capacity(ctx);
         if (si) return si;
@@ -854,6 +861,8 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     a.rec_off = ctx->d_rec_off.p;
     a.key_off = ctx->d_key_off.p;
     a.mom = ctx->d_mom.p;
+    a.keys = ctx->d_keys.p;
+    a.n_tiles = ctx->n_tiles;
     a.N = N;
     a.M = M;
     a.rc2 = ctx->rc2;

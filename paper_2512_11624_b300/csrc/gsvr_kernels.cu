@@ -187,14 +187,49 @@ __device__ __forceinline__ bool rec_bbox(const RecGeom &G, const SliceDev &S, fl
     return true;
 }
 
-__device__ __forceinline__ int count_live_tiles(const SliceDev &S, int tx0, int tx1, int ty0, int ty1,
-                                                const int *tps, const int *tpe) {
+// Largest value over a rectangle of pixel centres [x0, x1] x [y0, y1] (slice-
+// centred pixel units) of the record's exponent q(db, da) + log2 normal weight
+// (log2 units; q is concave, so the maximum sits at the centre when it lies
+// inside, else on an edge at the clamped stationary point).  The record's pair
+// factors inside the rectangle are at most 2^(this).  Explicit roundings keep
+// the result identical wherever it is evaluated.
+__device__ __forceinline__ float rect_max_exponent(const Rec &R, float x0, float x1, float y0, float y1) {
+    const float A = R.a.z, C = R.a.w, B = R.b.x;
+    const float X0 = __fsub_rn(x0, R.a.x), X1 = __fsub_rn(x1, R.a.x);
+    const float Y0 = __fsub_rn(y0, R.a.y), Y1 = __fsub_rn(y1, R.a.y);
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return R.b.z;
+    auto f = [&](float u, float v) {
+        return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, u), u), __fmul_rn(__fmul_rn(C, u), v)),
+                         __fmul_rn(__fmul_rn(B, v), v));
+    };
+    const float iA = __fdiv_rn(-0.5f, A), iB = __fdiv_rn(-0.5f, B);
+    float best = -INFINITY;
+    const float Xs[2] = {X0, X1}, Ys[2] = {Y0, Y1};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float v = fminf(fmaxf(__fmul_rn(__fmul_rn(C, Xs[k]), iB), Y0), Y1);
+        best = fmaxf(best, f(Xs[k], v));
+        const float u = fminf(fmaxf(__fmul_rn(__fmul_rn(C, Ys[k]), iA), X0), X1);
+        best = fmaxf(best, f(u, Ys[k]));
+    }
+    return __fadd_rn(best, R.b.z);
+}
+
+// Whether tile (tx, ty) of slice S has sampled pixels and the record reaches it.
+__device__ __forceinline__ bool tile_live(const Rec &R, const SliceDev &S, int tx, int ty, int tw, int th,
+                                          const int *tps, const int *tpe, float qcut) {
+    const int t = S.tile_base + ty * S.tiles_x + tx;
+    if (tpe[t] <= tps[t]) return false;
+    const float x0 = (float)(tx * tw) - S.cx0, x1 = (float)min(tx * tw + tw - 1, S.W - 1) - S.cx0;
+    const float y0 = (float)(ty * th) - S.cy0, y1 = (float)min(ty * th + th - 1, S.H - 1) - S.cy0;
+    return rect_max_exponent(R, x0, x1, y0, y1) >= qcut;
+}
+
+__device__ __forceinline__ int count_live_tiles(const Rec &R, const SliceDev &S, int tx0, int tx1, int ty0, int ty1,
+                                                int tw, int th, const int *tps, const int *tpe, float qcut) {
     int n = 0;
     for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const int t = S.tile_base + ty * S.tiles_x + tx;
-            n += (tpe[t] > tps[t]) ? 1 : 0;
-        }
+        for (int tx = tx0; tx <= tx1; ++tx) n += tile_live(R, S, tx, ty, tw, th, tps, tpe, qcut) ? 1 : 0;
     return n;
 }
 
@@ -328,6 +363,8 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
     }
     int n = 0;
     const int base = EMIT && live ? a.rec_off[j] : 0;
+    // the emit pass never writes past the slots its count pass reserved
+    const int room = EMIT && live ? a.rec_off[j + 1] - base : 0;
     for (int i0 = 0; i0 < a.M; i0 += kSliceChunk) {
         __syncthreads();
         const int nc = min(kSliceChunk, a.M - i0);
@@ -346,16 +383,17 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
             if (!rec_geom<true>(g0, g1, mu, S, a.rc2, a.norm_mode, G)) continue;
             int tx0, tx1, ty0, ty1;
             if (!rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, tx0, tx1, ty0, ty1)) continue;
-            const int nk = count_live_tiles(S, tx0, tx1, ty0, ty1, a.tile_px_start, a.tile_px_end);
+            const float L = kNegHalfLog2e;
+            Rec R;
+            R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
+            R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz, __int_as_float(i0 + ii));
+            const int nk =
+                count_live_tiles(R, S, tx0, tx1, ty0, ty1, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut);
             if (nk == 0) continue;
             if (EMIT) {
+                if (n >= room) continue;
                 const int r = base + n;
                 if (r < a.cap_rec) {
-                    const float L = kNegHalfLog2e;
-                    Rec R;
-                    R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
-                    R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz,
-                                      __int_as_float(i0 + ii));
                     a.rec[r] = R;
                     a.rec_tiles[r] = make_int2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
                     a.rec_nkeys[r] = nk;
@@ -367,51 +405,63 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
         }
     }
     if (!EMIT && live) a.rec_cnt[j] = n;
+    if (EMIT && live) {
+        // slots the count reserved but this pass did not fill hold empty records
+        for (int k = n; k < room; ++k) {
+            const int r = base + k;
+            if (r >= a.cap_rec) break;
+            Rec R;
+            R.a = make_float4(0.f, 0.f, -1.f, 0.f);
+            R.b = make_float4(-1.f, 0.f, -INFINITY, __int_as_float(0));
+            a.rec[r] = R;
+            a.rec_tiles[r] = make_int2(0, 0);
+            a.rec_nkeys[r] = 0;
+        }
+    }
 }
 
+// Keys of one record: exactly the count its record pass found, in row-major
+// tile order; should the tile test here come out differently, missing keys are
+// padded with the sentinel tile id n_tiles (sorted past every real tile and
+// never evaluated) and surplus ones dropped, so the key offsets always hold.
 __global__ void k_key_emit(KeyArgs a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_rec = min(*a.n_rec, a.cap_rec);
     if (r >= n_rec) return;
-    const int i = __float_as_int(a.rec[r].b.w);
+    const Rec R = a.rec[r];
+    const int i = __float_as_int(R.b.w);
     const SliceDev &S = a.slices[i];
     const int2 tb = a.rec_tiles[r];
     const int tx0 = tb.x & 0xffff, tx1 = tb.x >> 16, ty0 = tb.y & 0xffff, ty1 = tb.y >> 16;
-    int k = a.key_off[r];
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const int t = S.tile_base + ty * S.tiles_x + tx;
-            if (a.tile_px_end[t] > a.tile_px_start[t]) {
-                if (k < a.cap_keys) {
-                    a.keys[k] = (uint32_t)t;
-                    a.key_rec[k] = r;
-                } else {
-                    atomicOr(a.status, ST_CAPACITY);
-                }
-                ++k;
+    const int k0 = a.key_off[r];
+    const int k1 = k0 + a.rec_nkeys[r];
+    int k = k0;
+    for (int ty = ty0; ty <= ty1 && k < k1; ++ty)
+        for (int tx = tx0; tx <= tx1 && k < k1; ++tx) {
+            if (!tile_live(R, S, tx, ty, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut)) continue;
+            if (k < a.cap_keys) {
+                a.keys[k] = (uint32_t)(S.tile_base + ty * S.tiles_x + tx);
+                a.key_rec[k] = r;
+            } else {
+                atomicOr(a.status, ST_CAPACITY);
             }
+            ++k;
         }
+    for (; k < k1 && k < a.cap_keys; ++k) {
+        a.keys[k] = (uint32_t)a.n_tiles;
+        a.key_rec[k] = r;
+    }
 }
 
-__global__ void k_tile_rec_ranges(const uint32_t *__restrict__ keys, const int *n_keys, int cap, int *start,
-                                  int *end) {
+__global__ void k_tile_rec_ranges(const uint32_t *__restrict__ keys, const int *n_keys, int cap, int n_tiles,
+                                  int *start, int *end) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = min(*n_keys, cap);
     if (s >= n) return;
     const uint32_t t = keys[s];
+    if (t >= (uint32_t)n_tiles) return;  // sentinel keys
     if (s == 0 || keys[s - 1] != t) start[t] = s;
     if (s == n - 1 || keys[s + 1] != t) end[t] = s + 1;
-}
-
-__global__ void k_gather(const Rec *__restrict__ rec, const uint32_t *__restrict__ vals,
-                         const int *__restrict__ key_rec, const int *n_keys, int cap, Rec *__restrict__ trec) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = min(*n_keys, cap);
-    if (s >= n) return;
-    const uint32_t k = vals[s];
-    Rec R = rec[key_rec[k]];
-    R.b.w = __int_as_float((int)k);
-    trec[s] = R;
 }
 
 // ------------------------------------------------------------- work items
@@ -435,35 +485,67 @@ __global__ void k_item_fill(const int *__restrict__ first, int n_tiles, int *__r
 }
 
 // ----------------------------------------------------------------- forward
-// One CTA per work item, one thread per tile pixel.  The item's records (at most
-// kItemRecs x 32 bytes) are brought into shared memory by one 1-D bulk copy
-// (cp.async.bulk, completion on an mbarrier); every thread reads each record as
-// a broadcast and accumulates sum_r w_r exp2(q_r(pixel)).  The per-item sums go
-// to part[item][pixel]; k_fwd_reduce adds a tile's items in item order, so the
-// forward is bitwise reproducible.  COUNT: count the pairs inside the cut instead.
-template <bool COUNT>
-__global__ void __launch_bounds__(kMaxTilePx) k_fwd_items(EvalArgs a) {
+// Tile pixels are addressed densely, (row, col) inside the tile; pixels that are
+// not in the sample are evaluated but never read back.
+struct TileGeom {
+    int x0, y0, rows, cols;
+};
+__device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, int th) {
+    const int l = t - S.tile_base;
+    const int ty = l / S.tiles_x, tx = l - ty * S.tiles_x;
+    TileGeom g;
+    g.x0 = tx * tw;
+    g.y0 = ty * th;
+    g.cols = min(tw, S.W - g.x0);
+    g.rows = min(th, S.H - g.y0);
+    return g;
+}
+
+// One CTA per work item.  The item's records (at most kItemRecs x 32 bytes) come
+// into shared memory by one 1-D bulk copy (cp.async.bulk, completion on an
+// mbarrier).  The CTA is G groups of threads; in a group each thread owns a run
+// of PXR consecutive pixels of one tile row, and the groups split the records
+// (every lane of a warp reads the same record: a broadcast).  With the row
+// fixed, the record's row terms C2 da and B da^2 are formed once per PXR pixels:
+//   q = (A db + C2 da) db + B da^2,   sum += w exp2(q).
+// The groups' sums meet in shared memory; part[item][pixel] holds the item's
+// sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
+// (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
+template <bool COUNT, int PXR>
+__global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(128) Rec buf[kItemRecs];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ float red[4 * 256];
+    __shared__ unsigned char present[kMaxTilePx];
     const int i = blockIdx.x;
     if (i >= min(*a.n_items, a.cap_items)) return;
     const int t = a.item_tile[i];
     const int c = i - a.item_first[t];
-    const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
     const int rs = a.tile_rec_start[t] + c * kItemRecs;
     const int nrec = max(0, min(kItemRecs, a.tile_rec_end[t] - rs));
     const SliceDev &S = a.slices[a.tile_slice[t]];
-    const int slot = threadIdx.x;
-    const int s = ps + slot;
-    const bool valid = s < pe;
-    float pb = 0.f, pa = 0.f;
-    if (valid) {
-        const int loc = a.sampled[s] - S.pix_base;
-        const int row = loc / S.W;
-        pb = (float)(loc - row * S.W) - S.cx0;
-        pa = (float)row - S.cy0;
+    const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+    const int segs = (a.tile_w + PXR - 1) / PXR;
+    const int tpg = a.tile_h * segs;
+    const int G = max(1, (int)blockDim.x / tpg);
+    const int g = threadIdx.x / tpg, seg = threadIdx.x - g * tpg;
+    const int row = seg / segs, col0 = (seg - row * segs) * PXR;
+    const bool active = g < G && row < tg.rows;
+    const float rowf = (float)(tg.y0 + row) - S.cy0;
+    const float colf0 = (float)(tg.x0 + col0) - S.cx0;
+    if (COUNT) {
+        const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+        for (int k = threadIdx.x; k < a.tile_px; k += blockDim.x) present[k] = 0;
+        __syncthreads();
+        for (int s = ps + threadIdx.x; s < pe; s += blockDim.x) {
+            const int loc = a.sampled[s] - S.pix_base;
+            const int r0 = loc / S.W;
+            present[(r0 - tg.y0) * a.tile_w + (loc - r0 * S.W - tg.x0)] = 1;
+        }
     }
-    float acc = 0.f;
+    float acc[PXR];
+#pragma unroll
+    for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
     unsigned long long useful = 0;
     if (nrec > 0) {
         if (threadIdx.x == 0) {
@@ -483,27 +565,25 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_items(EvalArgs a) {
             __syncthreads();
             return;
         }
-        if (!COUNT) {
-#pragma unroll 8
-            for (int r = 0; r < nrec; ++r) {
+        if (active) {
+            for (int r = g; r < nrec; r += G) {
                 const float4 r0 = buf[r].a;
                 const float4 r1 = buf[r].b;
-                const float dx = pb - r0.x;
-                const float dy = pa - r0.y;
-                const float u = fmaf(r0.z, dx, r0.w * dy);
-                const float q = fmaf(u, dx, r1.x * dy * dy);
-                acc = fmaf(r1.y, ex2_approx(q), acc);
-            }
-        } else {
-            for (int r = 0; r < nrec; ++r) {
-                const float4 r0 = buf[r].a;
-                const float4 r1 = buf[r].b;
-                const float dx = pb - r0.x;
-                const float dy = pa - r0.y;
-                const float u = fmaf(r0.z, dx, r0.w * dy);
-                const float q = fmaf(u, dx, r1.x * dy * dy);
-                // full exponent (slice-plane part + normal part, log2 units) inside the cut
-                useful += (valid && q + r1.z >= a.qcut) ? 1ull : 0ull;
+                const float dy = rowf - r0.y;
+                const float cdy = r0.w * dy;
+                const float bdy = r1.x * dy * dy;
+#pragma unroll
+                for (int k = 0; k < PXR; ++k) {
+                    const float dx = (colf0 + (float)k) - r0.x;
+                    const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
+                    if (!COUNT) {
+                        acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
+                    } else {
+                        const int col = col0 + k;
+                        useful += (col < tg.cols && present[row * a.tile_w + col] && q + r1.z >= a.qcut) ? 1ull
+                                                                                                       : 0ull;
+                    }
+                }
             }
         }
     }
@@ -513,7 +593,18 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_items(EvalArgs a) {
         if ((threadIdx.x & 31) == 0 && useful) atomicAdd(a.useful, useful);
         return;
     }
-    if (valid) a.part[(size_t)i * a.tile_px + slot] = acc;
+    // groups -> one sum per dense tile pixel
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < PXR; ++k)
+            if (col0 + k < a.tile_w) red[g * a.tile_px + row * a.tile_w + col0 + k] = acc[k];
+    }
+    __syncthreads();
+    for (int px = threadIdx.x; px < a.tile_px; px += blockDim.x) {
+        float s = 0.f;
+        for (int gg = 0; gg < G; ++gg) s += red[gg * a.tile_px + px];
+        a.part[(size_t)i * a.tile_px + px] = s;
+    }
 }
 
 // Per tile: add the items' partial sums in order, then residual, dL/dI_hat and loss.
@@ -525,14 +616,18 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         if (threadIdx.x == 0) a.tile_loss[t] = 0.0;
         return;
     }
-    const int slot = threadIdx.x;
-    const int s = ps + slot;
+    const int s = ps + threadIdx.x;
     double l = 0.0;
     if (s < pe) {
+        const SliceDev &S = a.slices[a.tile_slice[t]];
+        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+        const int p = a.sampled[s];
+        const int loc = p - S.pix_base;
+        const int r0 = loc / S.W;
+        const int px = (r0 - tg.y0) * a.tile_w + (loc - r0 * S.W - tg.x0);
         float acc = 0.f;
         const int i1 = min(a.item_first[t + 1], a.cap_items);
-        for (int i = a.item_first[t]; i < i1; ++i) acc += a.part[(size_t)i * a.tile_px + slot];
-        const int p = a.sampled[s];
+        for (int i = a.item_first[t]; i < i1; ++i) acc += a.part[(size_t)i * a.tile_px + px];
         const float wp = 1.0f / (float)max(*a.n_sampled, 1);
         const float r = acc - a.I_obs[p];
         a.pred[p] = acc;
@@ -555,12 +650,23 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 }
 
 // ---------------------------------------------------------------- backward
-// One CTA per work item, thread per record (two records per thread); the
-// tile's pixels (b, a, r_bar) are broadcast from shared memory.  For each
-// (tile, record) the 6 moments sum_p g, g db, g da, g db^2, g db da, g da^2 with
-// g = r_bar_p exp2(q(p)) are written to the record's key slot (no atomics).
+// One CTA per work item, thread per record (two records per thread).  The
+// tile's r_bar values sit densely in shared memory (0 for pixels outside the
+// sample) and are read as broadcasts row by row.  Per row the record's row
+// terms are formed once and three row sums sum g, g db, g db^2 accumulate
+// (g = r_bar exp2(q)); at the end of the row they fold into the 6 moments
+// sum g, g db, g da, g db^2, g db da, g da^2, written to the record's key slot.
+__device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, float R2, float dy) {
+    m[0] += R0;
+    m[1] += R1;
+    m[2] = fmaf(R0, dy, m[2]);
+    m[3] += R2;
+    m[4] = fmaf(R1, dy, m[4]);
+    m[5] = fmaf(R0 * dy, dy, m[5]);
+}
+
 __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
-    extern __shared__ float4 spx[];  // tile_px entries
+    extern __shared__ float rb[];  // tile_h x tile_w
     const int i = blockIdx.x;
     if (i >= min(*a.n_items, a.cap_items)) return;
     const int t = a.item_tile[i];
@@ -570,12 +676,15 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
     const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
     if (ps >= pe || rs >= re) return;
     const SliceDev &S = a.slices[a.tile_slice[t]];
-    const int npx = pe - ps;
-    for (int s = threadIdx.x; s < npx; s += kThreads) {
-        const int p = a.sampled[ps + s];
+    const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+    const int tw = a.tile_w;
+    for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb[k] = 0.f;
+    __syncthreads();
+    for (int s = ps + threadIdx.x; s < pe; s += kThreads) {
+        const int p = a.sampled[s];
         const int loc = p - S.pix_base;
-        const int row = loc / S.W;
-        spx[s] = make_float4((float)(loc - row * S.W) - S.cx0, (float)row - S.cy0, a.rbar[p], 0.f);
+        const int r0 = loc / S.W;
+        rb[(r0 - tg.y0) * tw + (loc - r0 * S.W - tg.x0)] = a.rbar[p];
     }
     __syncthreads();
     const int r0 = rs + threadIdx.x;
@@ -584,44 +693,46 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
     const bool v1 = r1 < re;
     const Rec A = a.trec[r0];
     const Rec B = v1 ? a.trec[r1] : A;
-    float m0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, m1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-    for (int k = 0; k < npx; ++k) {
-        const float4 P = spx[k];
-        {
-            const float dx = P.x - A.a.x, dy = P.y - A.a.y;
-            const float u = fmaf(A.a.z, dx, A.a.w * dy);
-            const float q = fmaf(u, dx, A.b.x * dy * dy);
-            const float g = P.z * ex2_approx(q);
-            const float gx = g * dx, gy = g * dy;
-            m0[0] += g;
-            m0[1] += gx;
-            m0[2] += gy;
-            m0[3] = fmaf(gx, dx, m0[3]);
-            m0[4] = fmaf(gx, dy, m0[4]);
-            m0[5] = fmaf(gy, dy, m0[5]);
+    float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float colf0 = (float)tg.x0 - S.cx0;
+    for (int row = 0; row < tg.rows; ++row) {
+        const float rowf = (float)(tg.y0 + row) - S.cy0;
+        const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
+        const float cA = A.a.w * dyA, bA = A.b.x * dyA * dyA;
+        const float cB = B.a.w * dyB, bB = B.b.x * dyB * dyB;
+        float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+        const float *rrow = rb + row * tw;
+#pragma unroll 4
+        for (int col = 0; col < tg.cols; ++col) {
+            const float g = rrow[col];
+            const float colf = colf0 + (float)col;
+            {
+                const float dx = colf - A.a.x;
+                const float e = g * ex2_approx(fmaf(fmaf(A.a.z, dx, cA), dx, bA));
+                const float ex = e * dx;
+                A0 += e;
+                A1 += ex;
+                A2 = fmaf(ex, dx, A2);
+            }
+            {
+                const float dx = colf - B.a.x;
+                const float e = g * ex2_approx(fmaf(fmaf(B.a.z, dx, cB), dx, bB));
+                const float ex = e * dx;
+                B0 += e;
+                B1 += ex;
+                B2 = fmaf(ex, dx, B2);
+            }
         }
-        {
-            const float dx = P.x - B.a.x, dy = P.y - B.a.y;
-            const float u = fmaf(B.a.z, dx, B.a.w * dy);
-            const float q = fmaf(u, dx, B.b.x * dy * dy);
-            const float g = P.z * ex2_approx(q);
-            const float gx = g * dx, gy = g * dy;
-            m1[0] += g;
-            m1[1] += gx;
-            m1[2] += gy;
-            m1[3] = fmaf(gx, dx, m1[3]);
-            m1[4] = fmaf(gx, dy, m1[4]);
-            m1[5] = fmaf(gy, dy, m1[5]);
-        }
+        bwd_row_fold(mA, A0, A1, A2, dyA);
+        bwd_row_fold(mB, B0, B1, B2, dyB);
     }
     const int k0 = __float_as_int(A.b.w);
-    a.mom[2 * k0] = make_float4(m0[0], m0[1], m0[2], m0[3]);
-    a.mom[2 * k0 + 1] = make_float4(m0[4], m0[5], 0.f, 0.f);
+    a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
+    a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
     if (v1) {
         const int k1 = __float_as_int(B.b.w);
-        a.mom[2 * k1] = make_float4(m1[0], m1[1], m1[2], m1[3]);
-        a.mom[2 * k1 + 1] = make_float4(m1[4], m1[5], 0.f, 0.f);
+        a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
+        a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
     }
 }
 
@@ -656,6 +767,7 @@ __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const flo
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     const int k_end = min(a.key_off[r + 1], a.cap_keys);
     for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
+        if (a.keys[k] >= (uint32_t)a.n_tiles) continue;  // sentinel key: never evaluated
         const float4 u = a.mom[2 * k], v = a.mom[2 * k + 1];
         S0 += u.x;
         Sx += u.y;
@@ -952,16 +1064,10 @@ void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st) {
     k_key_emit<<<cdiv(n_rec_max, 256), 256, 0, st>>>(a);
     counted();
 }
-void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int *start, int *end,
+void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int n_tiles, int *start, int *end,
                             cudaStream_t st) {
     if (cap_keys <= 0) return;
-    k_tile_rec_ranges<<<cdiv(cap_keys, 256), 256, 0, st>>>(keys, n_keys, cap_keys, start, end);
-    counted();
-}
-void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, const int *n_keys, int cap_keys,
-                   Rec *trec, cudaStream_t st) {
-    if (cap_keys <= 0) return;
-    k_gather<<<cdiv(cap_keys, 256), 256, 0, st>>>(rec, vals, key_rec, n_keys, cap_keys, trec);
+    k_tile_rec_ranges<<<cdiv(cap_keys, 256), 256, 0, st>>>(keys, n_keys, cap_keys, n_tiles, start, end);
     counted();
 }
 static inline int round_warp(int n) { return (n + 31) / 32 * 32; }
@@ -972,24 +1078,31 @@ void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre
     else k_item_fill<<<cdiv(n_tiles, 256), 256, 0, st>>>(first, n_tiles, item_tile, cap_items);
     counted();
 }
+// Forward CTA shape: groups of tile_h x ceil(tile_w / PXR) threads, as many
+// groups as fit in 128 threads (at least one).
+template <bool COUNT>
+static void fwd_items(const EvalArgs &a, cudaStream_t st) {
+    const int pxr = a.tile_w >= 12 ? 4 : 2;
+    const int tpg = a.tile_h * ((a.tile_w + pxr - 1) / pxr);
+    const int G = std::max(1, 128 / tpg);
+    const int nt = round_warp(G * tpg);
+    if (pxr == 4) k_fwd_items<COUNT, 4><<<a.cap_items, nt, 0, st>>>(a);
+    else k_fwd_items<COUNT, 2><<<a.cap_items, nt, 0, st>>>(a);
+    counted();
+}
 void launch_forward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0) return;
-    const int nt = round_warp(a.tile_px);
-    if (a.cap_items > 0) {
-        k_fwd_items<false><<<a.cap_items, nt, 0, st>>>(a);
-        counted();
-    }
-    k_fwd_reduce<<<a.n_tiles, nt, 0, st>>>(a);
+    if (a.cap_items > 0) fwd_items<false>(a, st);
+    k_fwd_reduce<<<a.n_tiles, round_warp(a.tile_px), 0, st>>>(a);
     counted();
 }
 void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
-    k_fwd_items<true><<<a.cap_items, round_warp(a.tile_px), 0, st>>>(a);
-    counted();
+    fwd_items<true>(a, st);
 }
 void launch_backward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
-    k_bwd_items<<<a.cap_items, kThreads, (size_t)a.tile_px * sizeof(float4), st>>>(a);
+    k_bwd_items<<<a.cap_items, kThreads, (size_t)a.tile_px * sizeof(float), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st) {

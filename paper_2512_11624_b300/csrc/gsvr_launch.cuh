@@ -12,6 +12,7 @@ struct BinArgs {
     float rc2;                 // squared Mahalanobis cut: 2 ln(1 / cutoff_rel)
     int norm_mode;
     int tile_w, tile_h;
+    float qcut;                // log2(cutoff_rel): per-pair exponent cut (log2 units)
     const int *tile_px_start, *tile_px_end;
     int *rec_cnt;              // per Gaussian (count pass)
     const int *rec_off;        // per Gaussian (emit pass), N + 1
@@ -25,11 +26,14 @@ struct BinArgs {
 struct KeyArgs {
     const Rec *rec;
     const int2 *rec_tiles;
+    const int *rec_nkeys;      // keys per record (from the record pass)
     const int *key_off;        // n_rec + 1
     const SliceDev *slices;
     const int *tile_px_start, *tile_px_end;
     const int *n_rec;          // device count
     int cap_rec, cap_keys;
+    int tile_w, tile_h, n_tiles;
+    float qcut;
     uint32_t *keys;
     int *key_rec;
     unsigned *status;
@@ -57,6 +61,7 @@ struct EvalArgs {
     float *part;                      // per-item partial pixel sums (cap_items x tile_px)
     int cap_items;
     int tile_px;                      // tile_w * tile_h
+    int tile_w, tile_h;
     int n_tiles;
     unsigned *status;
 };
@@ -69,6 +74,8 @@ struct GradArgs {
     const int *rec_off;        // N + 1
     const int *key_off;        // n_rec + 1
     const float4 *mom;         // 2 per key in emit order
+    const uint32_t *keys;      // tile id per key in emit order (n_tiles = sentinel)
+    int n_tiles;
     int N, M;
     float rc2;
     int norm_mode;
@@ -84,10 +91,8 @@ void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, in
 void launch_rec_count(const BinArgs &a, cudaStream_t st);
 void launch_rec_emit(const BinArgs &a, cudaStream_t st);
 void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st);
-void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int *start, int *end,
+void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int n_tiles, int *start, int *end,
                             cudaStream_t st);
-void launch_gather(const Rec *rec, const uint32_t *vals, const int *key_rec, const int *n_keys, int cap_keys,
-                   Rec *trec, cudaStream_t st);
 // phase 0: items per tile into cnt; phase 1: item -> tile from the scanned offsets `first`
 void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre, int n_tiles, int *cnt,
                   const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st);

@@ -297,6 +297,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     b.norm_mode = norm_mode;
     b.tile_w = kTile;
     b.tile_h = kTile;
+    b.qcut = (float)std::log2((double)cutoff_rel);
     b.tile_px_start = d_tps;
     b.tile_px_end = d_tpe;
     b.rec_cnt = d_rec_cnt;
@@ -313,6 +314,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     KeyArgs k{};
     k.rec = d_rec;
     k.rec_tiles = d_rec_tiles;
+    k.rec_nkeys = d_rec_nkeys;
     k.key_off = d_key_off;
     k.slices = d_sl;
     k.tile_px_start = d_tps;
@@ -320,16 +322,20 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     k.n_rec = &d_cnt->n_rec;
     k.cap_rec = cap_rec;
     k.cap_keys = cap_keys;
+    k.tile_w = kTile;
+    k.tile_h = kTile;
+    k.n_tiles = (int)T;
+    k.qcut = b.qcut;
     k.keys = d_keys;
     k.key_rec = d_key_rec;
     k.status = d_status;
     launch_key_emit(k, cap_rec, st);
     int bits = 1;
-    while ((1LL << bits) < T) ++bits;
+    while ((1LL << bits) < T + 1) ++bits;
     const SortScratch sort_s{d_ka, d_va, d_hist, scs};
-    NA_CK(radix_sort_pairs(d_keys, nullptr, d_ks, d_vs, &d_cnt->n_keys, cap_keys, bits, sort_s, st));
-    launch_tile_rec_ranges(d_ks, &d_cnt->n_keys, cap_keys, d_trs, d_tre, st);
-    launch_gather(d_rec, d_vs, d_key_rec, &d_cnt->n_keys, cap_keys, d_trec, st);
+    NA_CK(radix_sort_pairs(d_keys, nullptr, d_ks, d_vs, &d_cnt->n_keys, cap_keys, bits, sort_s, st, d_rec, d_key_rec,
+                           d_trec));
+    launch_tile_rec_ranges(d_ks, &d_cnt->n_keys, cap_keys, (int)T, d_trs, d_tre, st);
     launch_items(d_tps, d_tpe, d_trs, d_tre, (int)T, d_item_cnt, nullptr, nullptr, 0, 0, st);
     NA_CK(scan_exclusive(d_item_cnt, d_item_first, nullptr, (int)T, (int)T, &d_cnt->n_items, scs, st));
     launch_items(nullptr, nullptr, nullptr, nullptr, (int)T, nullptr, d_item_first, d_item_tile, cap_items, 1, st);
@@ -354,6 +360,8 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     e.part = d_part;
     e.cap_items = cap_items;
     e.tile_px = kTile * kTile;
+    e.tile_w = kTile;
+    e.tile_h = kTile;
     e.n_tiles = (int)T;
     e.status = d_status;
     launch_forward(e, st);

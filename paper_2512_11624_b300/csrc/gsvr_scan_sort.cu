@@ -129,10 +129,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
     for (int d = threadIdx.x; d < 256; d += kSortThreads) hist[d * nb + blockIdx.x] = cnt[d];
 }
 
+// GATHER: instead of the values, write the tile-ordered record rec[key_rec[value]]
+// (its last word replaced by the value, i.e. the key's emit index) to trec.
+template <bool GATHER>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                                 uint32_t *kout, uint32_t *vout, const int *d_n,
                                                                 int n_max, int shift, const int *hist_scan,
-                                                                int nb) {
+                                                                int nb, const Rec *rec, const int *key_rec,
+                                                                Rec *trec) {
     constexpr int NW = kSortThreads / 32;
     __shared__ int cnt[NW][256];
     const int n = min(*d_n, n_max);
@@ -181,7 +185,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
         const unsigned d = (key[r] >> shift) & 255u;
         const int pos = hist_scan[d * nb + blockIdx.x] + cnt[w][d] + rank[r];
         kout[pos] = key[r];
-        vout[pos] = val[r];
+        if (GATHER) {
+            Rec R = rec[key_rec[val[r]]];
+            R.b.w = __int_as_float((int)val[r]);
+            trec[pos] = R;
+        } else {
+            vout[pos] = val[r];
+        }
     }
 }
 }  // namespace
@@ -203,7 +213,7 @@ int sort_blocks(int n_max) { return n_max <= 0 ? 1 : (n_max + kSortTile - 1) / k
 
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                              uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
-                             cudaStream_t st) {
+                             cudaStream_t st, const Rec *rec, const int *key_rec, Rec *trec) {
     const int nb = sort_blocks(n_max);
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     const uint32_t *ksrc = keys_in;
@@ -216,7 +226,12 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
         k_radix_hist<<<nb, kSortThreads, 0, st>>>(ksrc, d_n, n_max, shift, s.hist, nb);
         cudaError_t e = scan_exclusive(s.hist, s.hist, nullptr, 256 * nb, 256 * nb, nullptr, s.scan, st);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist, nb);
+        if (rec && p == passes - 1)
+            k_radix_scatter<true><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
+                                                               nb, rec, key_rec, trec);
+        else
+            k_radix_scatter<false><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
+                                                                nb, nullptr, nullptr, nullptr);
         note_launches(2);
         ksrc = kdst;
         vsrc = vdst;
