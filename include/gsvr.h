@@ -4,17 +4,17 @@
  *
  * Method (paper "Fast and Explicit: Slice-to-Volume Reconstruction via 3D
  * Gaussian Primitives with Analytic PSF Modeling"):
- *  - Sec. 3.1, Eq. 1 / Eq. 3: a slice pixel u of slice i is the volume
+ *  - Sec. 2.1, Eq. 1 / Eq. 3: a slice pixel u of slice i is the volume
  *    convolved with the slice-oriented PSF, read at x = T_i(u) = R_i u + t_i.
- *  - Sec. 3.2: the volume is a sum of N Gaussians, 11 parameters each
+ *  - Sec. 2.2: the volume is a sum of N Gaussians, 11 parameters each
  *    (mean mu, log-space scales ls, quaternion q = (w,x,y,z), amplitude c),
  *    Sigma_j = R(q) diag(exp(2 ls)) R(q)^T.
- *  - Sec. 3.3, Eq. 4: Sigma_obs = Sigma_j + R_i Sigma_PSF R_i^T, Sigma_PSF
+ *  - Sec. 2.3, Eq. 4: Sigma_obs = Sigma_j + R_i Sigma_PSF R_i^T, Sigma_PSF
  *    diagonal in slice coordinates; Eq. 5 (numerator): the pixel receives
  *    c_j f exp(-1/2 v^T Sigma_obs^-1 v), v = x - mu_j, with
  *    f = sqrt(det Sigma_j / det Sigma_obs) (the exact convolution of a
  *    unit-mass PSF; GSVR_NORM_EXACT) or f = 1 (GSVR_NORM_LITERAL).
- *  - Sec. 3.4: per slice a rigid motion (axis-angle r, translation tau) that
+ *  - Sec. 2.4: per slice a rigid motion (axis-angle r, translation tau) that
  *    moves the slice and rotates its PSF: R_i = Rod(r) R0_i,
  *    t_i = Rod(r) c0_i + tau, (R0_i, c0_i) the slice's nominal frame.
  *  - Loss: L = sum_p w_p (I_hat_p - I_p)^2, w_p = 1 / |sampled pixels|.
@@ -71,7 +71,7 @@ typedef enum gsvr_status {
 enum { GSVR_MEM_HOST = 0, GSVR_MEM_DEVICE = 1 };
 enum { GSVR_NORM_EXACT = 0, GSVR_NORM_LITERAL = 1 };
 
-/* One stack of parallel, contiguous slices (no gap), Sec. 3.1 / Sec. 4.
+/* One stack of parallel, contiguous slices (no gap), Sec. 2.1 / Sec. 3.2.
  * Slice k (0-based) of n is centred at origin + (k - (n-1)/2) * thickness * n_hat,
  * n_hat = third column of R.  Sigma_PSF = diag((fwhm / 2.355)^2) in slice axes. */
 typedef struct gsvr_stack_desc {
@@ -135,7 +135,7 @@ gsvr_status gsvr_create(gsvr_ctx **out, int device, void *cuda_stream, const gsv
 /* Release every buffer of the context (synchronises its stream first). */
 gsvr_status gsvr_destroy(gsvr_ctx *ctx);
 
-/* Acquisition geometry (Sec. 3.1, Sec. 4): n_stacks stack descriptions in host
+/* Acquisition geometry (Sec. 2.1, Sec. 3.2): n_stacks stack descriptions in host
  * memory.  Defines M (slices) and the pixel count; invalidates observations,
  * poses and the sample.  Synchronous. */
 gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_desc *stacks);
@@ -145,11 +145,11 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
  * Requires gsvr_set_stacks.  Makes the sample "every masked pixel". */
 gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *mask, int32_t mem);
 
-/* The N Gaussians (Sec. 3.2): theta_g = the first 11N entries of the
+/* The N Gaussians (Sec. 2.2): theta_g = the first 11N entries of the
  * parameter vector, `mem`.  Resets the Adam moments of the Gaussians. */
 gsvr_status gsvr_set_gaussians(gsvr_ctx *ctx, int64_t N, const float *theta_g, int32_t mem);
 
-/* The M slice motions (Sec. 3.4): pose[6i + 0..2] = axis-angle r,
+/* The M slice motions (Sec. 2.4): pose[6i + 0..2] = axis-angle r,
  * pose[6i + 3..5] = translation tau, `mem`.  Resets the pose Adam moments. */
 gsvr_status gsvr_set_poses(gsvr_ctx *ctx, const float *pose, int32_t mem);
 

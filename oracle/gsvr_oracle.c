@@ -9,7 +9,7 @@
  * calls it.
  *
  * What it computes (paper sections / equations):
- *  - Gaussian primitive (Sec. 3.2, Eq. 2 numerator): mean mu, covariance
+ *  - Gaussian primitive (Sec. 2.2, Eq. 2 numerator): mean mu, covariance
  *    Sigma = R S S^T R^T with S = diag(exp(ls)) (log-space scales, Nomenclature
  *    table) and R from the normalised quaternion q = (w, x, y, z); amplitude c.
  *  - Acquisition (Eq. 1, Eq. 3): pixel u of slice i sits at x = R_i u + t_i
@@ -21,7 +21,7 @@
  *    exact-convolution normalisation sqrt(det Sigma_j / det Sigma_obs)
  *    (norm_mode 0) or 1 (norm_mode 1, the literal substitution of Eq. 5).
  *    EVERY (pixel, Gaussian) pair is summed; nothing is culled.
- *  - Motion (Sec. 3.4): per slice a 6-DoF motion (r, tau), r axis-angle.  The
+ *  - Motion (Sec. 2.4): per slice a 6-DoF motion (r, tau), r axis-angle.  The
  *    slice frame is R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau.
  *  - Loss: L = sum_p w_p (I_hat_p - I_p)^2 (mean squared error, w_p = 1/|sample|).
  *  - Gradient of L with respect to mu, ls, q, c and (r, tau), written out in
@@ -422,6 +422,56 @@ static void cov_chain(const or_gauss *g, const double *G, double *dls, double *d
     dq[3] = (gq[3] - z * dot) / g->qnorm;
 }
 
+/* The same chain with every product and sum taken in absolute value: the
+ * componentwise scale of the float rounding of a computation that accumulates
+ * the covariance gradient and projects it once (|dls_k|, |dq_c| bounds). */
+static void cov_chain_abs(const or_gauss *g, const double *Gabs, double *dls, double *dq) {
+    double R[9], D[9] = {g->s2[0], 0, 0, 0, g->s2[1], 0, 0, 0, g->s2[2]};
+    for (int e = 0; e < 9; ++e) R[e] = fabs(g->Rj[e]);
+    double RtG[9], RtGR[9];
+    mat_mul_at(R, Gabs, RtG);
+    mat_mul(RtG, R, RtGR);
+    for (int k = 0; k < 3; ++k) dls[k] = 2.0 * g->s2[k] * RtGR[4 * k];
+    double GR[9], GRD[9];
+    mat_mul(Gabs, R, GR);
+    mat_mul(GR, D, GRD);
+    double w = fabs(g->qn[0]), x = fabs(g->qn[1]), y = fabs(g->qn[2]), z = fabs(g->qn[3]);
+    const double dRw[9] = {0, 2 * z, 2 * y, 2 * z, 0, 2 * x, 2 * y, 2 * x, 0};
+    const double dRx[9] = {0, 2 * y, 2 * z, 2 * y, 4 * x, 2 * w, 2 * z, 2 * w, 4 * x};
+    const double dRy[9] = {4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, 2 * w, 2 * z, 4 * y};
+    const double dRz[9] = {4 * z, 2 * w, 2 * x, 2 * w, 4 * z, 2 * y, 2 * x, 2 * y, 0};
+    double gq[4] = {0, 0, 0, 0};
+    for (int e = 0; e < 9; ++e) {
+        gq[0] += 2.0 * GRD[e] * dRw[e];
+        gq[1] += 2.0 * GRD[e] * dRx[e];
+        gq[2] += 2.0 * GRD[e] * dRy[e];
+        gq[3] += 2.0 * GRD[e] * dRz[e];
+    }
+    double n1 = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    dq[0] = (gq[0] + w * n1) / g->qnorm;
+    dq[1] = (gq[1] + x * n1) / g->qnorm;
+    dq[2] = (gq[2] + y * n1) / g->qnorm;
+    dq[3] = (gq[3] + z * n1) / g->qnorm;
+}
+
+/* Absolute-value version of pose_chain (componentwise rounding scale). */
+static void pose_chain_abs(const or_slice *s, const double *pose, const double *GRabs, const double *Gtabs,
+                           double *out6) {
+    double J[3][9], G[9], R0[9], c0[3];
+    rodrigues_jac(pose, J);
+    for (int e = 0; e < 9; ++e) R0[e] = fabs(s->R0[e]);
+    for (int a = 0; a < 3; ++a) c0[a] = fabs(s->c0[a]);
+    mat_mul_bt(GRabs, R0, G);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[3 * a + b] += Gtabs[a] * c0[b];
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        for (int e = 0; e < 9; ++e) acc += G[e] * fabs(J[k][e]);
+        out6[k] = acc;
+    }
+    for (int a = 0; a < 3; ++a) out6[3 + a] = Gtabs[a];
+}
+
 /* Chain of the slice-frame gradients (dL/dR_i, dL/dt_i) through
  * R_i = Rod(r) R0, t_i = Rod(r) c0 + tau: d r (3), d tau (3). */
 static void pose_chain(const or_slice *s, const double *pose, const double *GR, const double *Gt, double *out6) {
@@ -538,13 +588,23 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
                 for (int e = 0; e < 9; ++e) acc[e] += GR[e];
                 for (int k = 0; k < 3; ++k) acc[9 + k] += dx[k];
                 if (absgrad) {
-                    double d6[6], dls[3], dq[4];
-                    pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, dx, d6);
+                    /* componentwise scales: |.| of every product and sum of the chain */
+                    double d6[6], dls[3], dq[4], Ga[9], GRa[9], dxa[3], RDa[9], GoRDa[9];
+                    for (int e = 0; e < 9; ++e) {
+                        Ga[e] = fabs(Go[e]);
+                        RDa[e] = fabs(RD[e]);
+                    }
+                    for (int k = 0; k < 3; ++k) dxa[k] = fabs(dx[k]);
+                    mat_mul(Ga, RDa, GoRDa);
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c)
+                            GRa[3 * r + c] = dxa[r] * fabs(pu[3 * p + c]) + 2.0 * GoRDa[3 * r + c];
+                    pose_chain_abs(&m.sl[i], theta + 11 * N + 6 * i, GRa, dxa, d6);
                     for (int k = 0; k < 6; ++k) acc[12 + k] += fabs(d6[k]);
-                    cov_chain(gj, Go, dls, dq);
+                    cov_chain_abs(gj, Ga, dls, dq);
                     for (int k = 0; k < 3; ++k) {
-                        double v = dls[k] + (norm_mode == 0 ? a : 0.0);
-                        als[k] += fabs(v);
+                        double v = dls[k] + (norm_mode == 0 ? fabs(a) : 0.0);
+                        als[k] += v;
                         amu[k] += fabs(a * pr.Pv[k]);
                         if (cut) {
                             tls[k] += fabs(v);

@@ -21,7 +21,7 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
 
 // Per-slice frame and geometry.  The frame fields are rewritten from the pose
-// every forward (Sec. 3.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau, computed in
+// every forward (Sec. 2.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau, computed in
 // float64 per slice and stored as float32, plus float32 (hi, lo) pairs for the
 // three projections that fix the record centres); the rest is fixed by the
 // stack description.

@@ -1,8 +1,8 @@
 // gsvr_kernels.cu -- the compute path of libgsvr.so (sm_103a).
 //
 // Per forward:
-//   gauss_prep   Sigma_j = R(q) diag(exp(2 ls)) R(q)^T            (Sec. 3.2)
-//   pose_prep    R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau          (Sec. 3.4)
+//   gauss_prep   Sigma_j = R(q) diag(exp(2 ls)) R(q)^T            (Sec. 2.2)
+//   pose_prep    R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau          (Sec. 2.4)
 //   rec_count / rec_emit
 //                every (slice i, Gaussian j): m = R_i^T (mu_j - t_i),
 //                K = R_i^T Sigma_j R_i + Sigma_PSF (= R_i^T Sigma_obs R_i, Eq. 4);

@@ -386,6 +386,11 @@ class Context:
     def stats(self):
         return gsvr_get_stats(self.ctx)
 
+    def sample_index(self):
+        """Global pixel indices of the current sample, in the library's order (device int64)."""
+        import torch
+        return torch.from_numpy(gsvr_get_sample(self.ctx).astype("int64")).to(self.theta.device)
+
     def close(self):
         if self.ctx is not None:
             gsvr_destroy(self.ctx)

@@ -9,7 +9,7 @@ loads the CUDA library.
 
 Workloads (shapes follow the paper's acquisitions: three orthogonal thick-slice
 stacks, brain-sized field of view, motion of a few degrees / millimetres;
-Sec. 4 "Data"):
+Sec. 3.2 "Data"):
 
 - ``tiny``   2,000 Gaussians, 1 stack of 8 x 32 x 32 px (1 x 1 x 3 mm).
 - ``fetal``  ~200k Gaussians on a 0.8 mm grid inside a brain-like phantom,

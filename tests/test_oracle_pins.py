@@ -10,7 +10,7 @@ not against the oracle's own formulas.
   reduces to the volume value of Eq. 2's numerator.
 - Invariants: mass conservation of the blurred field (true only with the exact
   normalisation), linearity in the amplitudes, and joint rigid motion of volume
-  and slices (Sec. 3.4) leaving every prediction unchanged.
+  and slices (Sec. 2.4) leaving every prediction unchanged.
 - Gradients against float64 central finite differences of the loss.
 - The sampler's counter generator against SplitMix64's published first output,
   and its permutation property by brute force.
@@ -96,7 +96,7 @@ def test_rodrigues_matches_scipy(oracle, scale):
 
 
 def test_covariance_is_R_S_St_Rt(oracle):
-    """Sec. 3.2: Sigma = R S S^T R^T with log-space scales."""
+    """Sec. 2.2: Sigma = R S S^T R^T with log-space scales."""
     rng = np.random.default_rng(3)
     N = 7
     th = inputs.random_gaussians(rng, N)
@@ -118,7 +118,7 @@ def test_slice_frames_vs_scipy(oracle):
 
 
 def test_parameter_count(oracle):
-    """11 parameters per primitive (Sec. 3.2; ~550k for N = 50k)."""
+    """11 parameters per primitive (Sec. 2.2; ~550k for N = 50k)."""
     rng = np.random.default_rng(0)
     assert inputs.random_gaussians(rng, 50_000).size == 550_000
 
@@ -288,7 +288,7 @@ def rigid_transform(th, N, M, Q, b):
 
 def test_joint_rigid_motion_invariance(oracle):
     """Moving the volume and every slice by the same rigid map (Q, b) changes no
-    prediction (Sec. 3.4: the PSF rotates with the slice)."""
+    prediction (Sec. 2.4: the PSF rotates with the slice)."""
     case = inputs.random_case(9, 60, [(3, 8, 9), (2, 7, 6)], n_stacks=2)
     N, st = case["N"], case["stacks"]
     M = inputs.n_slices_total(st)
