@@ -47,7 +47,7 @@ ISSUE_PER_PAIR = {"fwd_eval": 5.0, "bwd_eval": 9.0}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fetal", choices=["fetal", "tiny"])
@@ -116,20 +116,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def kernel_source_sha():
-    h = hashlib.sha1()
-    with open(os.path.join(ROOT, "paper_2512_11624_b300", "csrc", "gsvr_kernels.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:12]
+def kernel_source_sha(kernel):
+    """Hash of the source text of one __global__ function (its definition up to the
+    matching closing brace) in csrc/gsvr_kernels.cu."""
+    src = open(os.path.join(ROOT, "paper_2512_11624_b300", "csrc", "gsvr_kernels.cu")).read()
+    at = src.find(" " + kernel + "(")
+    while at >= 0 and "__global__" not in src[max(0, src.rfind("\n", 0, at) - 200):at]:
+        at = src.find(" " + kernel + "(", at + 1)
+    if at < 0:
+        return "missing"
+    start = src.find("{", at)
+    depth, k = 0, start
+    while k < len(src):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            break
+        k += 1
+    return hashlib.sha1(src[at:k + 1].encode()).hexdigest()[:12]
 
 
 def profiled_traffic(kernel, workload_name):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current source of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for line in open(path):
         p = line.split()
         if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload_name and p[2] == sha:
@@ -343,11 +355,13 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = gsvr.gsvr_get_sample(ctx.ctx)
         rng = np.random.default_rng(7)
-        pix = rng.choice(sample, 16, replace=False)
-        t1, _, _ = cpu_oracle_sample(case, pix, n_s)
-        n_px = int(max(16, min(8192, 16 * args.cpu_seconds / max(t1, 1e-3))))
-        pix = rng.choice(sample, min(n_px, sample.size), replace=False)
-        t_cpu, u_cpu, cores = cpu_oracle_sample(case, pix, n_s)
+        n_px = 128
+        while True:  # grow the sample until the oracle runs for args.cpu_seconds
+            pix = rng.choice(sample, min(n_px, sample.size), replace=False)
+            t_cpu, u_cpu, cores = cpu_oracle_sample(case, pix, n_s)
+            if t_cpu >= 0.8 * args.cpu_seconds or n_px >= min(65536, sample.size):
+                break
+            n_px = int(min(65536, n_px * max(2.0, min(32.0, args.cpu_seconds / max(t_cpu, 1e-3)))))
         cpu = {"value": u_cpu / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                "px_per_s": len(pix) / t_cpu,
                "sample": "%d sampled pixels of one step x all %d Gaussians, fwd+bwd (all gradients), float64, "

@@ -119,7 +119,8 @@ typedef struct gsvr_views {
 /* Counters of the last forward (synchronises the stream). */
 typedef struct gsvr_stats {
     int64_t n_sampled;       /* pixels in the current sample */
-    int64_t n_records;       /* (slice, Gaussian) pairs that survived the Mahalanobis cut */
+    int64_t n_records;       /* (slice, Gaussian) candidates of the slab test (each one record; those
+                                failing the exact Mahalanobis cut carry no keys) */
     int64_t n_keys;          /* (tile, record) keys sorted */
     int64_t pairs_evaluated; /* (pixel, Gaussian) pairs the evaluation kernels visit, each pass */
     int64_t n_tiles;         /* pixel tiles in all slices */

@@ -84,7 +84,7 @@ struct gsvr_ctx {
     // binning
     DBuf<int> d_rec_cnt, d_rec_off, d_rec_nkeys, d_key_off, d_key_rec, d_tile_rec_start, d_tile_rec_end;
     DBuf<Rec> d_rec, d_trec;
-    DBuf<int2> d_rec_tiles;
+    DBuf<int2> d_rec_tiles, d_cand;
     DBuf<uint32_t> d_keys, d_keys_sorted, d_vals_sorted, d_keys_alt, d_vals_alt;
     DBuf<int> d_hist, d_scan_bsum;
     DBuf<float4> d_mom;
@@ -187,6 +187,7 @@ gsvr_status ensure_rec_capacity(gsvr_ctx *ctx, int64_t want) {
     const int cap = (int)std::min<int64_t>((int64_t)INT32_MAX - 16, std::max<int64_t>(want, 1024));
     CK(ctx->d_rec.ensure(cap));
     CK(ctx->d_rec_tiles.ensure(cap));
+    CK(ctx->d_cand.ensure(cap));
     CK(ctx->d_rec_nkeys.ensure(cap));
     CK(ctx->d_key_off.ensure((size_t)cap + 1));
     ctx->cap_rec = cap;
@@ -754,7 +755,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.tile_px_end = ctx->d_tile_px_end.p;
     b.rec_cnt = ctx->d_rec_cnt.p;
     b.status = ctx->d_status.p;
-    launch_rec_count(b, st);
+    launch_cand_count(b, st);
     CK(cudaGetLastError());
     CK(scan_exclusive(ctx->d_rec_cnt.p, ctx->d_rec_off.p, nullptr, N, N, &cnt->n_rec, scan_scratch(ctx), st));
     int n_rec_max = ctx->cap_rec;
@@ -770,11 +771,14 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
         ctx->last_n_rec = n_rec;
     }
     b.rec_off = ctx->d_rec_off.p;
+    b.n_rec = &cnt->n_rec;
+    b.cand = ctx->d_cand.p;
     b.rec = ctx->d_rec.p;
     b.rec_tiles = ctx->d_rec_tiles.p;
     b.rec_nkeys = ctx->d_rec_nkeys.p;
     b.cap_rec = ctx->cap_rec;
-    launch_rec_emit(b, st);
+    launch_cand_emit(b, st);
+    launch_records(b, n_rec_max, st);
     CK(cudaGetLastError());
     CK(scan_exclusive(ctx->d_rec_nkeys.p, ctx->d_key_off.p, &cnt->n_rec, 0, std::max(n_rec_max, 0), &cnt->n_keys,
                       scan_scratch(ctx), st));

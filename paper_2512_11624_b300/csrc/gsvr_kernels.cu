@@ -347,8 +347,12 @@ __global__ void k_set_count(int *dst, int v) { *dst = v; }
 // ------------------------------------------------------------------ binning
 constexpr int kSliceChunk = 32;
 
+// Candidates: every (slice, Gaussian) pair whose slice-normal offset passes a
+// float32 slab test with a small margin (a superset of the pairs the exact cut
+// keeps).  Thread per Gaussian, slices staged through shared memory; the count
+// pass sizes the Gaussian-major candidate list, the emit pass writes it.
 template <bool EMIT>
-__global__ void __launch_bounds__(128) k_records(BinArgs a) {
+__global__ void __launch_bounds__(128) k_cand(BinArgs a) {
     __shared__ SliceDev ssl[kSliceChunk];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = j < a.N;
@@ -363,7 +367,6 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
     }
     int n = 0;
     const int base = EMIT && live ? a.rec_off[j] : 0;
-    // the emit pass never writes past the slots its count pass reserved
     const int room = EMIT && live ? a.rec_off[j + 1] - base : 0;
     for (int i0 = 0; i0 < a.M; i0 += kSliceChunk) {
         __syncthreads();
@@ -377,47 +380,53 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
         __syncthreads();
         if (!live) continue;
         for (int ii = 0; ii < nc; ++ii) {
-            const SliceDev &S = ssl[ii];
-            if (!slab_candidate(g0, g1, mu, S, a.rc2)) continue;
-            RecGeom G;
-            if (!rec_geom<true>(g0, g1, mu, S, a.rc2, a.norm_mode, G)) continue;
-            int tx0, tx1, ty0, ty1;
-            if (!rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, tx0, tx1, ty0, ty1)) continue;
-            const float L = kNegHalfLog2e;
-            Rec R;
-            R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
-            R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz, __int_as_float(i0 + ii));
-            const int nk =
-                count_live_tiles(R, S, tx0, tx1, ty0, ty1, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut);
-            if (nk == 0) continue;
-            if (EMIT) {
-                if (n >= room) continue;
-                const int r = base + n;
-                if (r < a.cap_rec) {
-                    a.rec[r] = R;
-                    a.rec_tiles[r] = make_int2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
-                    a.rec_nkeys[r] = nk;
-                } else {
-                    atomicOr(a.status, ST_CAPACITY);
-                }
+            if (!slab_candidate(g0, g1, mu, ssl[ii], a.rc2)) continue;
+            if (EMIT && n < room) {
+                const int c = base + n;
+                if (c < a.cap_rec) a.cand[c] = make_int2(j, i0 + ii);
+                else atomicOr(a.status, ST_CAPACITY);
             }
             ++n;
         }
     }
     if (!EMIT && live) a.rec_cnt[j] = n;
-    if (EMIT && live) {
-        // slots the count reserved but this pass did not fill hold empty records
-        for (int k = n; k < room; ++k) {
-            const int r = base + k;
-            if (r >= a.cap_rec) break;
-            Rec R;
-            R.a = make_float4(0.f, 0.f, -1.f, 0.f);
-            R.b = make_float4(-1.f, 0.f, -INFINITY, __int_as_float(0));
-            a.rec[r] = R;
-            a.rec_tiles[r] = make_int2(0, 0);
-            a.rec_nkeys[r] = 0;
+    if (EMIT && live)
+        for (int k = n; k < room && base + k < a.cap_rec; ++k) a.cand[base + k] = make_int2(j, -1);
+}
+
+// Thread per candidate: the exact cut, the slice-plane conditioning, the tile
+// box and the live-tile count.  Candidates stay the records (same index, so
+// the list remains Gaussian-major); candidates that fail hold an empty record
+// with no keys.
+__global__ void __launch_bounds__(128) k_records(BinArgs a) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_cand = min(*a.n_rec, a.cap_rec);
+    if (c >= n_cand) return;
+    const int2 ji = a.cand[c];
+    const int j = ji.x, i = ji.y;
+    bool ok = i >= 0;
+    Rec R;
+    R.a = make_float4(0.f, 0.f, -1.f, 0.f);
+    R.b = make_float4(-1.f, 0.f, -INFINITY, __int_as_float(max(i, 0)));
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0, nk = 0;
+    if (ok) {
+        const SliceDev &S = a.slices[i];
+        const float mu[3] = {a.theta[j], a.theta[a.N + j], a.theta[2 * a.N + j]};
+        const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
+        RecGeom G;
+        ok = rec_geom<true>(g0, g1, mu, S, a.rc2, a.norm_mode, G) &&
+             rec_bbox(G, S, a.rc2, a.tile_w, a.tile_h, tx0, tx1, ty0, ty1);
+        if (ok) {
+            const float L = kNegHalfLog2e;
+            R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
+            R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz, __int_as_float(i));
+            nk = count_live_tiles(R, S, tx0, tx1, ty0, ty1, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end,
+                                  a.qcut);
         }
     }
+    a.rec[c] = R;
+    a.rec_tiles[c] = make_int2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+    a.rec_nkeys[c] = nk;
 }
 
 // Keys of one record: exactly the count its record pass found, in row-major
@@ -1049,14 +1058,19 @@ void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, in
     k_pose_prep<<<cdiv(M, 128), 128, 0, st>>>(pose, ss, sd, M, status);
     counted();
 }
-void launch_rec_count(const BinArgs &a, cudaStream_t st) {
+void launch_cand_count(const BinArgs &a, cudaStream_t st) {
     if (a.N <= 0) return;
-    k_records<false><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    k_cand<false><<<cdiv(a.N, 128), 128, 0, st>>>(a);
     counted();
 }
-void launch_rec_emit(const BinArgs &a, cudaStream_t st) {
+void launch_cand_emit(const BinArgs &a, cudaStream_t st) {
     if (a.N <= 0) return;
-    k_records<true><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    k_cand<true><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    counted();
+}
+void launch_records(const BinArgs &a, int n_cand_max, cudaStream_t st) {
+    if (n_cand_max <= 0) return;
+    k_records<<<cdiv(n_cand_max, 128), 128, 0, st>>>(a);
     counted();
 }
 void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st) {

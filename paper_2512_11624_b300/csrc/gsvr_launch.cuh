@@ -14,9 +14,11 @@ struct BinArgs {
     int tile_w, tile_h;
     float qcut;                // log2(cutoff_rel): per-pair exponent cut (log2 units)
     const int *tile_px_start, *tile_px_end;
-    int *rec_cnt;              // per Gaussian (count pass)
-    const int *rec_off;        // per Gaussian (emit pass), N + 1
-    Rec *rec;                  // emit pass
+    int *rec_cnt;              // candidates per Gaussian (count pass)
+    const int *rec_off;        // first candidate of each Gaussian, N + 1
+    const int *n_rec;          // device count of candidates (= records)
+    int2 *cand;                // (Gaussian, slice) per candidate; slice -1 = padding
+    Rec *rec;                  // one record per candidate
     int2 *rec_tiles;           // packed tile bounding box per record
     int *rec_nkeys;            // keys per record
     int cap_rec;
@@ -88,8 +90,9 @@ struct GradArgs {
 void launch_gauss_prep(const float *theta, int N, float4 *gpre, unsigned *status, cudaStream_t st);
 void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, int M, unsigned *status,
                       cudaStream_t st);
-void launch_rec_count(const BinArgs &a, cudaStream_t st);
-void launch_rec_emit(const BinArgs &a, cudaStream_t st);
+void launch_cand_count(const BinArgs &a, cudaStream_t st);
+void launch_cand_emit(const BinArgs &a, cudaStream_t st);
+void launch_records(const BinArgs &a, int n_cand_max, cudaStream_t st);
 void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st);
 void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int n_tiles, int *start, int *end,
                             cudaStream_t st);

@@ -209,7 +209,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     const size_t fixed = cv.used();
     // per record: Rec + tile box + key count + key offset; per key: key, key_rec, sorted key and
     // value, two ping-pong words, tile-ordered record, backward moments (unused here), histogram share
-    const size_t per_rec = sizeof(Rec) + sizeof(int2) + 2 * sizeof(int);
+    const size_t per_rec = sizeof(Rec) + 2 * sizeof(int2) + 2 * sizeof(int);
     const size_t per_key = 6 * sizeof(uint32_t) + sizeof(Rec) + 1 + (kTile * kTile * sizeof(float)) / kItemRecs + 1;
     const size_t slack = 64 * 256 + 4096 * sizeof(int) + (size_t)(2 * T + 8) * (sizeof(int) + kTile * kTile * sizeof(float));
     if (fixed + slack + per_rec + kKeysPerRecord * per_key >= kScratchBytes) {
@@ -221,6 +221,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     int cap_keys = kKeysPerRecord * cap_rec;
     Rec *d_rec = cv.take<Rec>(cap_rec);
     int2 *d_rec_tiles = cv.take<int2>(cap_rec);
+    int2 *d_cand = cv.take<int2>(cap_rec);
     int *d_rec_nkeys = cv.take<int>(cap_rec);
     int *d_key_off = cv.take<int>((size_t)cap_rec + 1);
     uint32_t *d_keys = cv.take<uint32_t>(cap_keys);
@@ -302,14 +303,17 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     b.tile_px_end = d_tpe;
     b.rec_cnt = d_rec_cnt;
     b.status = d_status;
-    launch_rec_count(b, st);
+    launch_cand_count(b, st);
     NA_CK(scan_exclusive(d_rec_cnt, d_rec_off, nullptr, (int)N, (int)N, &d_cnt->n_rec, scs, st));
     b.rec_off = d_rec_off;
+    b.n_rec = &d_cnt->n_rec;
+    b.cand = d_cand;
     b.rec = d_rec;
     b.rec_tiles = d_rec_tiles;
     b.rec_nkeys = d_rec_nkeys;
     b.cap_rec = cap_rec;
-    launch_rec_emit(b, st);
+    launch_cand_emit(b, st);
+    launch_records(b, cap_rec, st);
     NA_CK(scan_exclusive(d_rec_nkeys, d_key_off, &d_cnt->n_rec, 0, cap_rec, &d_cnt->n_keys, scs, st));
     KeyArgs k{};
     k.rec = d_rec;
