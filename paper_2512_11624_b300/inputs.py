@@ -276,7 +276,7 @@ def grid_gaussians(phantom, h=0.8, s=0.8):
     return np.concatenate([P.T, ls, q, c[None, :]], axis=0).reshape(-1), N
 
 
-def fetal(seed=0, with_truth=False):
+def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20):
     """The fetal-scale plain case: ~200k Gaussians on a 0.8 mm grid inside the
     brain phantom; axial / coronal / sagittal stacks of 40 x 192 x 192 px at
     1 x 1 x 3.5 mm centred on the origin; per-slice motion U(+-5 deg) axis
@@ -288,14 +288,22 @@ def fetal(seed=0, with_truth=False):
     stacks = [stack(40, 192, 192, 1.0, 1.0, 3.5, R) for R in (AXIAL, CORONAL, SAGITTAL)]
     M = n_slices_total(stacks)
     motion = random_motion(rng, M, 5.0, 3.0)
+    if ref_slice is not None:
+        motion[ref_slice] = 0.0  # the reference slice fixes the frame (its pose is frozen)
     I, mask = simulate_phantom_stacks(ph, stacks, motion, seed=seed)
     theta_g, N = grid_gaussians(ph)
+    if init == "flat":
+        # cold start: every amplitude from the mean observed intensity inside the brain
+        h, s = 0.8, 0.8
+        level = float(np.mean(I[mask > 0][I[mask > 0] > 0.2])) if np.any(I[mask > 0] > 0.2) else 0.5
+        theta_g = theta_g.reshape(11, N)
+        theta_g[10] = level * h ** 3 / ((2 * np.pi) ** 1.5 * s ** 3)
+        theta_g = theta_g.reshape(-1)
     theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
     out = {"name": "fetal", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
-           "n_sample": 1 << 18}
+           "n_sample": 1 << 18, "ref_slice": ref_slice, "phantom": ph}
     if with_truth:
         out["motion"] = motion
-        out["phantom"] = ph
     return out
 
 
@@ -314,3 +322,21 @@ def first_stacks(case, n):
     frac = P / n_pixels_total(case["stacks"])
     out["n_sample"] = min(int(out["mask"].sum()), int(case["n_sample"] * frac))
     return out
+
+
+def grid_probe(phantom, h=0.8, margin=2.0):
+    """An isotropic h-mm grid over the phantom's bounding box as one axial stack
+    with a zero-width PSF (each pixel then reads the volume itself), the phantom
+    value at every grid point, and the mask of points inside the phantom."""
+    ext = phantom.axes + margin
+    n = [int(np.ceil(2 * e / h)) for e in ext]
+    st = stack(n[2], n[1], n[0], h, h, h)
+    st["fwhm"] = np.zeros(3)
+    xs = (np.arange(n[0]) - 0.5 * (n[0] - 1)) * h
+    ys = (np.arange(n[1]) - 0.5 * (n[1] - 1)) * h
+    zs = (np.arange(n[2]) - 0.5 * (n[2] - 1)) * h
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    P = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], 1)
+    ref = phantom(P).astype(np.float32)
+    inside = phantom.inside(P).astype(np.uint8)
+    return st, ref, inside
