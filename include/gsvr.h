@@ -99,7 +99,9 @@ typedef struct gsvr_config {
 typedef struct gsvr_adam_cfg {
     float lr_mu, lr_ls, lr_q, lr_c, lr_rot, lr_trans; /* per-group learning rates */
     float beta1, beta2, eps;                          /* 0 -> 0.9, 0.999, 1e-8 */
-    int32_t reserved;
+    int32_t step_every;                               /* StepLR (App. A.1): rates x gamma every step_every
+                                                         steps; 0 = constant rates */
+    float gamma;                                      /* StepLR factor; 0 -> 1 */
 } gsvr_adam_cfg;
 
 /* Device views of context-owned buffers (valid until the next gsvr_set_* call that
@@ -185,8 +187,44 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx);
 gsvr_status gsvr_backward(gsvr_ctx *ctx);
 
 /* One Adam step (bias-corrected, no weight decay) on theta with the last
- * gradient; `step` is the 1-based step count used for bias correction. */
+ * gradient; `step` is the 1-based step count used for bias correction and the
+ * StepLR schedule. */
 gsvr_status gsvr_adam_step(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step);
+
+/* ---- Batched form: several independent reconstructions in one context ----
+ * Subjects: stack_subject[s] is the subject of stack s (subjects 0..n-1, each a
+ * contiguous run of stacks in order); gauss_count[k] Gaussians belong to subject
+ * k, in order (subject 0's first, each parameter component-major over all N as
+ * above).  A Gaussian is evaluated only against its own subject's slices, pixel
+ * weights are 1 / (the subject's sampled pixels) and losses are kept per
+ * subject; one set of launches serves all subjects (the evaluation kernels are
+ * persistent over the work items of every subject).  Host tables; call after
+ * gsvr_set_gaussians and gsvr_set_observations; n = 1 restores one subject. */
+gsvr_status gsvr_set_subjects(gsvr_ctx *ctx, int32_t n, const int32_t *stack_subject, const int64_t *gauss_count);
+
+/* Device sampler per subject: n_per_subject masked pixels of every subject
+ * (all of them where a subject has fewer), uniformly without replacement;
+ * subject k uses the keyed permutation of gsvr_sample_pixels with seed
+ * seed + k * 0x9E3779B97F4A7C15. */
+gsvr_status gsvr_sample_pixels_subjects(gsvr_ctx *ctx, int64_t n_per_subject, uint64_t step);
+
+/* Per-subject MSE losses of the last forward into host `out` (n >= number of
+ * subjects).  Synchronises. */
+gsvr_status gsvr_get_subject_losses(gsvr_ctx *ctx, double *out, int32_t n);
+
+/* ---- CUDA graph of one optimisation iteration ----
+ * gsvr_graph_capture records, on the context's (non-default) stream: the
+ * per-subject device sampler (n_per_subject < 0: keep the current sample),
+ * forward, backward, Adam with `cfg`, and the advance of a device iteration
+ * counter that the sampler's step and Adam's bias correction / schedule read
+ * (so every replay is the next iteration).  Requires fixed_capacity = 1 and a
+ * prior successful forward at these capacities.  gsvr_graph_launch replays it
+ * `iterations` times (asynchronous); gsvr_set_step sets the counter (the next
+ * iteration uses step and Adam step step + 1).  Capacity overflow during replay
+ * is reported by gsvr_sync_status. */
+gsvr_status gsvr_graph_capture(gsvr_ctx *ctx, int64_t n_per_subject, const gsvr_adam_cfg *cfg);
+gsvr_status gsvr_graph_launch(gsvr_ctx *ctx, int32_t iterations);
+gsvr_status gsvr_set_step(gsvr_ctx *ctx, int64_t step);
 
 /* End to end from host buffers: copy theta (11N + 6M floats, host) and the
  * pixel sample (n int32 global indices, host; n < 0 = every masked pixel) to

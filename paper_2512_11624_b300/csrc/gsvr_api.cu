@@ -63,12 +63,13 @@ struct gsvr_ctx {
     DBuf<SliceDev> d_slices;
     DBuf<SliceStatic> d_static;
     DBuf<int> d_tile_slice, d_pix_tile, d_pix_tpos, d_tile_sorted_pix;
-    std::vector<int> h_tile_sorted_pix;
+    std::vector<int> h_tile_sorted_pix, h_tile_tpos_first, h_stack_nslices;
 
     // observations
     DBuf<float> d_I;
     DBuf<uint8_t> d_mask;
     DBuf<int> d_mask_tpos, d_mask_pix_sorted;
+    std::vector<int> h_mask_tpos;
     int n_mask = 0;
 
     // parameters
@@ -101,6 +102,23 @@ struct gsvr_ctx {
 
     bool have_stacks = false, have_obs = false, have_gauss = false, have_sample = false, fwd_valid = false;
 
+    // subjects (batched form): stacks -> subject, contiguous Gaussian ranges
+    int n_subj = 1;
+    std::vector<int> h_stack_subject;   // per stack
+    std::vector<int> h_subj_slice_first, h_subj_tile_first, h_subj_mask_first;
+    std::vector<int64_t> h_subj_gauss_first;
+    DBuf<int> d_gauss_subject, d_subj_slice_first, d_subj_tile_first, d_subj_mask_first, d_subj_out_first, d_subj_cnt;
+    DBuf<double> d_subj_loss;
+    DBuf<int> d_all_first;  // {0, n_mask}: the whole mask as one sampling range
+    DBuf<int> d_single_out; // {0, n}: output offsets of a whole-mask sample
+    int64_t single_out_n = -1, subj_out_n = -1, subj_out_total = 0;
+    bool multi_gauss = false;
+
+    // CUDA graph of one optimisation iteration
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool capturing = false;
+
     // stage timing (cfg.timing)
     struct Mark {
         int stage;
@@ -115,6 +133,8 @@ struct gsvr_ctx {
     DBuf<unsigned long long> d_pairs_total, d_useful;
 
     ~gsvr_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
         for (auto &m : marks) {
             cudaEventDestroy(m.a);
             cudaEventDestroy(m.b);
@@ -249,6 +269,7 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.item_first = ctx->d_item_first.p;
     e.n_items = &ctx->d_counters.p->n_items;
     e.part = ctx->d_part.p;
+    e.subj_cnt = ctx->d_subj_cnt.p;
     e.cap_items = std::min(grid_items, ctx->cap_items);
     e.tile_px = ctx->tile_w * ctx->tile_h;
     e.tile_w = ctx->tile_w;
@@ -258,6 +279,68 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     return e;
 }
 
+// Subject tables on the device: slice / tile / mask ranges per subject and the
+// subject of every Gaussian (only when more than one subject).
+gsvr_status upload_subjects(gsvr_ctx *ctx) {
+    const int n = ctx->n_subj;
+    std::vector<int> slice_first(n + 1, 0), tile_first(n + 1, 0);
+    {
+        int sl = 0, k = 0;
+        for (int st = 0; st < ctx->n_stacks; ++st) {
+            const int sj = ctx->h_stack_subject.empty() ? 0 : ctx->h_stack_subject[st];
+            while (k < sj) slice_first[++k] = sl;
+            sl += ctx->h_stack_nslices[st];
+        }
+        while (k < n) slice_first[++k] = sl;
+    }
+    for (int k = 0; k <= n; ++k)
+        tile_first[k] = slice_first[k] < ctx->M ? ctx->h_slices[slice_first[k]].tile_base : ctx->n_tiles;
+    for (int i = 0; i < ctx->M; ++i) {
+        int sj = 0;
+        while (sj + 1 < n && slice_first[sj + 1] <= i) ++sj;
+        ctx->h_slices[i].subject = sj;
+    }
+    ctx->h_subj_slice_first = slice_first;
+    ctx->h_subj_tile_first = tile_first;
+    CK(ctx->d_subj_slice_first.ensure(n + 1));
+    CK(ctx->d_subj_tile_first.ensure(n + 1));
+    CK(ctx->d_subj_mask_first.ensure(n + 1));
+    CK(ctx->d_subj_out_first.ensure(n + 1));
+    CK(ctx->d_subj_cnt.ensure(n));
+    CK(ctx->d_subj_loss.ensure(n));
+    CK(ctx->d_all_first.ensure(2));
+    CK(ctx->d_single_out.ensure(2));
+    ctx->single_out_n = -1;
+    ctx->subj_out_n = -1;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_subj_slice_first.p, slice_first.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_subj_tile_first.p, tile_first.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_slices.p, ctx->h_slices.data(), sizeof(SliceDev) * ctx->M, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->d_subj_loss.p, 0, sizeof(double) * n));
+    return GSVR_OK;
+}
+
+// Mask ranges per subject (the masked pixels are in tile order, so subject-major).
+gsvr_status upload_mask_ranges(gsvr_ctx *ctx, const std::vector<int> &mtp) {
+    const int n = ctx->n_subj;
+    std::vector<int> mf(n + 1, 0);
+    size_t q = 0;
+    for (int k = 0; k < n; ++k) {
+        mf[k] = (int)q;
+        const int tpos_end = ctx->h_subj_tile_first[k + 1] < ctx->n_tiles
+                                 ? ctx->h_tile_tpos_first[ctx->h_subj_tile_first[k + 1]]
+                                 : (int)ctx->P;
+        while (q < mtp.size() && mtp[q] < tpos_end) ++q;
+    }
+    mf[n] = (int)mtp.size();
+    ctx->h_subj_mask_first = mf;
+    ctx->subj_out_n = -1;
+    const int all[2] = {0, (int)mtp.size()};
+    CK(cudaMemcpy(ctx->d_subj_mask_first.p, mf.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_all_first.p, all, sizeof(all), cudaMemcpyHostToDevice));
+    return GSVR_OK;
+}
+
 // Tile ranges of the current sample (sampled pixels are in tile order).
 gsvr_status finish_sample(gsvr_ctx *ctx) {
     cudaStream_t st = ctx->stream;
@@ -265,6 +348,8 @@ gsvr_status finish_sample(gsvr_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->d_tile_px_end.p, 0, sizeof(int) * ctx->n_tiles, st));
     launch_tile_px_ranges(ctx->d_sampled.p, &ctx->d_counters.p->n_sampled, (int)ctx->P, ctx->d_pix_tile.p,
                           ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, st);
+    launch_subject_counts(ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_subj_tile_first.p, ctx->n_subj,
+                          ctx->d_subj_cnt.p, st);
     CK(cudaGetLastError());
     ctx->have_sample = true;
     ctx->fwd_valid = false;
@@ -323,7 +408,7 @@ void fold_marks(gsvr_ctx *ctx) {
 
 // Stage timers: CUDA events on the context stream around each stage.
 void stage_begin(gsvr_ctx *ctx, int stage) {
-    if (!ctx->cfg.timing) return;
+    if (!ctx->cfg.timing || ctx->capturing) return;
     cudaEvent_t e = pooled_event(ctx);
     if (!e) return;
     cudaEventRecord(e, ctx->stream);
@@ -331,7 +416,7 @@ void stage_begin(gsvr_ctx *ctx, int stage) {
     ctx->open_ev[stage] = e;
 }
 void stage_end(gsvr_ctx *ctx, int stage) {
-    if (!ctx->cfg.timing || !ctx->open_ev[stage]) return;
+    if (!ctx->cfg.timing || ctx->capturing || !ctx->open_ev[stage]) return;
     cudaEvent_t e = pooled_event(ctx);
     if (!e) return;
     cudaEventRecord(e, ctx->stream);
@@ -462,6 +547,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     const int M = (int)sl.size();
     // static pixel / tile maps: tile order = slice, tile row, tile col, row-major inside the tile
     std::vector<int> tile_slice((size_t)T), pix_tile((size_t)P), tsp((size_t)P), tpos((size_t)P);
+    std::vector<int> tile_tpos_first((size_t)T);
     int64_t o = 0;
     for (int i = 0; i < M; ++i) {
         const SliceDev &v = sl[i];
@@ -469,6 +555,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
             for (int tx = 0; tx < v.tiles_x; ++tx) {
                 const int t = v.tile_base + ty * v.tiles_x + tx;
                 tile_slice[t] = i;
+                tile_tpos_first[t] = (int)o;
                 for (int a = ty * th; a < std::min(v.H, (ty + 1) * th); ++a)
                     for (int b = tx * tw; b < std::min(v.W, (tx + 1) * tw); ++b) {
                         const int p = v.pix_base + a * v.W + b;
@@ -490,6 +577,12 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     ctx->h_slices = sl;
     ctx->h_static = ss;
     ctx->h_tile_sorted_pix = tsp;
+    ctx->h_tile_tpos_first = tile_tpos_first;
+    ctx->h_stack_nslices.assign(n_stacks, 0);
+    for (int st2 = 0; st2 < n_stacks; ++st2) ctx->h_stack_nslices[st2] = stacks[st2].n_slices;
+    ctx->n_subj = 1;
+    ctx->h_stack_subject.assign(n_stacks, 0);
+    ctx->multi_gauss = false;
     cudaStream_t st = ctx->stream;
     CK(cudaStreamSynchronize(st));
     CK(ctx->d_slices.ensure(M));
@@ -523,6 +616,10 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     CK(cudaMemset(ctx->d_rbar.p, 0, sizeof(float) * P));
     ctx->any_frozen = false;
     CK(ensure_scan_scratch(ctx));
+    {
+        gsvr_status su = upload_subjects(ctx);
+        if (su) return su;
+    }
     // parameters sized for a different M are dropped
     if (ctx->have_gauss && ctx->d_theta.n != (size_t)(11 * ctx->N + 6 * M)) ctx->have_gauss = false;
     ctx->have_stacks = true;
@@ -562,6 +659,11 @@ gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *
     if (!mtp.empty()) {
         CK(cudaMemcpy(ctx->d_mask_tpos.p, mtp.data(), sizeof(int) * mtp.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->d_mask_pix_sorted.p, mps.data(), sizeof(int) * mps.size(), cudaMemcpyHostToDevice));
+    }
+    ctx->h_mask_tpos = mtp;
+    {
+        gsvr_status sm = upload_mask_ranges(ctx, mtp);
+        if (sm) return sm;
     }
     ctx->have_obs = true;
     return sample_all(ctx);
@@ -698,30 +800,124 @@ gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, 
     return compact_flags(ctx);
 }
 
+// Flags from the device sampler over `ranges` (n_ranges mask ranges, out_first on the device).
+gsvr_status sample_ranges(gsvr_ctx *ctx, int n_ranges, const int *mask_first, const int *out_first, int n_out,
+                          uint64_t step, const unsigned long long *d_step) {
+    cudaStream_t st = ctx->stream;
+    stage_begin(ctx, GSVR_STAGE_SAMPLE);
+    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
+    launch_sample_flags(n_ranges, mask_first, out_first, n_out, ctx->cfg.seed, step, d_step, ctx->d_mask_tpos.p,
+                        ctx->d_flags.p, st);
+    CK(cudaGetLastError());
+    gsvr_status s = compact_flags(ctx);
+    stage_end(ctx, GSVR_STAGE_SAMPLE);
+    return s;
+}
+
 gsvr_status gsvr_sample_pixels(gsvr_ctx *ctx, int64_t n, uint64_t step) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (!ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_observations first");
     if (n < 0 || n > ctx->n_mask) return fail(ctx, GSVR_ERR_INVALID_ARG, "sample larger than the masked pixels");
     DeviceGuard g(ctx->device);
-    cudaStream_t st = ctx->stream;
-    SamplerKeys sk{};
-    int k = 1;
-    while ((1LL << k) < ctx->n_mask) ++k;
-    sk.k = k;
-    sk.h = (k + 1) / 2;
-    const uint64_t msk = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
-    for (int r = 0; r < 4; ++r) {
-        const uint64_t key = splitmix64_at(ctx->cfg.seed, 4ULL * step + (uint64_t)r);
-        sk.xk[r] = key & msk;
-        sk.mul[r] = (key >> 32) | 1ULL;
+    if (ctx->single_out_n != n) {  // offsets uploaded once per sample size
+        const int out[2] = {0, (int)n};
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpy(ctx->d_single_out.p, out, sizeof(out), cudaMemcpyHostToDevice));
+        ctx->single_out_n = n;
     }
-    stage_begin(ctx, GSVR_STAGE_SAMPLE);
-    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
-    launch_sample_flags(ctx->n_mask, (int)n, sk, ctx->d_mask_tpos.p, ctx->d_flags.p, st);
-    CK(cudaGetLastError());
-    gsvr_status s = compact_flags(ctx);
-    stage_end(ctx, GSVR_STAGE_SAMPLE);
-    return s;
+    return sample_ranges(ctx, 1, ctx->d_all_first.p, ctx->d_single_out.p, (int)n, step, nullptr);
+}
+
+// Per-subject output offsets of a sample of n pixels per subject (fewer where a
+// subject has fewer masked pixels); uploads them and returns the total.
+int64_t subject_out_first(gsvr_ctx *ctx, int64_t n) {
+    if (ctx->subj_out_n == n) return ctx->subj_out_total;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    std::vector<int> of(ctx->n_subj + 1, 0);
+    for (int k = 0; k < ctx->n_subj; ++k) {
+        const int64_t avail = ctx->h_subj_mask_first[k + 1] - ctx->h_subj_mask_first[k];
+        of[k + 1] = of[k] + (int)std::min<int64_t>(n, avail);
+    }
+    if (cudaMemcpy(ctx->d_subj_out_first.p, of.data(), sizeof(int) * of.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    ctx->subj_out_n = n;
+    ctx->subj_out_total = of[ctx->n_subj];
+    return of[ctx->n_subj];
+}
+
+gsvr_status gsvr_sample_pixels_subjects(gsvr_ctx *ctx, int64_t n_per_subject, uint64_t step) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_observations first");
+    if (n_per_subject < 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "negative sample size");
+    DeviceGuard g(ctx->device);
+    const int64_t tot = subject_out_first(ctx, n_per_subject);
+    if (tot < 0) return fail(ctx, GSVR_ERR_CUDA, "upload of the sample offsets failed");
+    return sample_ranges(ctx, ctx->n_subj, ctx->d_subj_mask_first.p, ctx->d_subj_out_first.p, (int)tot, step,
+                         nullptr);
+}
+
+gsvr_status gsvr_set_subjects(gsvr_ctx *ctx, int32_t n, const int32_t *stack_subject, const int64_t *gauss_count) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss || !ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "set stacks, observations, Gaussians first");
+    if (n < 1 || n > 65536 || (n > 1 && (!stack_subject || !gauss_count)))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad subject count or tables");
+    std::vector<int> ss(ctx->n_stacks, 0);
+    std::vector<int64_t> gf(n + 1, 0);
+    if (n > 1) {
+        int prev = 0;
+        for (int k = 0; k < ctx->n_stacks; ++k) {
+            ss[k] = stack_subject[k];
+            if (ss[k] < prev || ss[k] > prev + 1 || ss[k] >= n)
+                return fail(ctx, GSVR_ERR_INVALID_ARG, "stack subjects must be 0..n-1, contiguous, in order");
+            prev = ss[k];
+        }
+        if (prev != n - 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "every subject needs a stack");
+        for (int k = 0; k < n; ++k) {
+            if (gauss_count[k] < 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "negative Gaussian count");
+            gf[k + 1] = gf[k] + gauss_count[k];
+        }
+        if (gf[n] != ctx->N) return fail(ctx, GSVR_ERR_INVALID_ARG, "Gaussian counts must add up to N");
+    } else {
+        gf[1] = ctx->N;
+    }
+    DeviceGuard g(ctx->device);
+    ctx->n_subj = n;
+    ctx->h_stack_subject = ss;
+    ctx->h_subj_gauss_first = gf;
+    {
+        gsvr_status su = upload_subjects(ctx);
+        if (su) return su;
+        su = upload_mask_ranges(ctx, ctx->h_mask_tpos);
+        if (su) return su;
+    }
+    ctx->multi_gauss = n > 1;
+    if (n > 1) {
+        std::vector<int> gs((size_t)ctx->N);
+        for (int k = 0; k < n; ++k)
+            for (int64_t j = gf[k]; j < gf[k + 1]; ++j) gs[(size_t)j] = k;
+        CK(ctx->d_gauss_subject.ensure((size_t)std::max<int64_t>(ctx->N, 1)));
+        if (ctx->N > 0)
+            CK(cudaMemcpy(ctx->d_gauss_subject.p, gs.data(), sizeof(int) * gs.size(), cudaMemcpyHostToDevice));
+    }
+    // the sample keeps its pixels; its per-subject counts follow the new tables
+    gsvr_status s2 = finish_sample(ctx);
+    if (s2) return s2;
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_subject_losses(gsvr_ctx *ctx, double *out, int32_t n) {
+    if (check_ctx(ctx) || !out || n < ctx->n_subj) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(out, ctx->d_subj_loss.p, sizeof(double) * ctx->n_subj, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GSVR_OK;
 }
 
 gsvr_status gsvr_forward(gsvr_ctx *ctx) {
@@ -751,6 +947,8 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.tile_w = ctx->tile_w;
     b.tile_h = ctx->tile_h;
     b.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
+    b.gauss_subject = ctx->multi_gauss ? ctx->d_gauss_subject.p : nullptr;
+    b.subj_slice_first = ctx->d_subj_slice_first.p;
     b.tile_px_start = ctx->d_tile_px_start.p;
     b.tile_px_end = ctx->d_tile_px_end.p;
     b.rec_cnt = ctx->d_rec_cnt.p;
@@ -838,7 +1036,8 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
     launch_forward(e, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
-    launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_loss.p, ctx->d_status.p, st);
+    launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_subj_tile_first.p, ctx->n_subj, ctx->d_subj_loss.p,
+                       ctx->d_loss.p, ctx->d_status.p, st);
     CK(cudaGetLastError());
     ctx->fwd_valid = true;
     return GSVR_OK;
@@ -883,24 +1082,99 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     return GSVR_OK;
 }
 
+gsvr_status adam_launch(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step, const unsigned long long *d_step) {
+    const float b1 = cfg->beta1 == 0.f ? 0.9f : cfg->beta1;
+    const float b2 = cfg->beta2 == 0.f ? 0.999f : cfg->beta2;
+    const float eps = cfg->eps == 0.f ? 1e-8f : cfg->eps;
+    const float gamma = cfg->gamma == 0.f ? 1.0f : cfg->gamma;
+    if (!(b1 > 0.f && b1 < 1.f && b2 > 0.f && b2 < 1.f && eps > 0.f && gamma > 0.f) || cfg->step_every < 0)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad Adam betas, eps or schedule");
+    const float lr[6] = {cfg->lr_mu, cfg->lr_ls, cfg->lr_q, cfg->lr_c, cfg->lr_rot, cfg->lr_trans};
+    stage_begin(ctx, GSVR_STAGE_ADAM);
+    launch_adam(ctx->d_theta.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, (int)ctx->N, ctx->M, lr, b1, b2, eps,
+                cfg->step_every, gamma, step, d_step, ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
+    stage_end(ctx, GSVR_STAGE_ADAM);
+    CK(cudaGetLastError());
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
 gsvr_status gsvr_adam_step(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
     if (!cfg || step < 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "adam config NULL or step < 1");
     DeviceGuard g(ctx->device);
-    const float b1 = cfg->beta1 == 0.f ? 0.9f : cfg->beta1;
-    const float b2 = cfg->beta2 == 0.f ? 0.999f : cfg->beta2;
-    const float eps = cfg->eps == 0.f ? 1e-8f : cfg->eps;
-    if (!(b1 > 0.f && b1 < 1.f && b2 > 0.f && b2 < 1.f && eps > 0.f))
-        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad Adam betas or eps");
-    const float lr[6] = {cfg->lr_mu, cfg->lr_ls, cfg->lr_q, cfg->lr_c, cfg->lr_rot, cfg->lr_trans};
-    const double bc1 = 1.0 - std::pow((double)b1, (double)step);
-    const double bc2 = 1.0 - std::pow((double)b2, (double)step);
-    stage_begin(ctx, GSVR_STAGE_ADAM);
-    launch_adam(ctx->d_theta.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, (int)ctx->N, ctx->M, lr, b1, b2, eps, bc1,
-                bc2, ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
-    stage_end(ctx, GSVR_STAGE_ADAM);
-    CK(cudaGetLastError());
+    return adam_launch(ctx, cfg, step, nullptr);
+}
+
+gsvr_status gsvr_set_step(gsvr_ctx *ctx, int64_t step) {
+    if (check_ctx(ctx) || step < 0) return GSVR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const unsigned long long v = (unsigned long long)step;
+    CK(cudaMemcpyAsync(&ctx->d_counters.p->step, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_graph_capture(gsvr_ctx *ctx, int64_t n_per_subject, const gsvr_adam_cfg *cfg) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->cfg.fixed_capacity) return fail(ctx, GSVR_ERR_STATE, "graph capture needs fixed_capacity = 1");
+    if (!ctx->have_gauss || !ctx->have_obs || !ctx->have_sample || !cfg)
+        return fail(ctx, GSVR_ERR_STATE, "set stacks, observations, Gaussians and a sample before capturing");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    if (!st) return fail(ctx, GSVR_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    CK(cudaStreamSynchronize(st));
+    {
+        gsvr_status si = ensure_item_capacity(ctx);
+        if (si) return si;
+    }
+    int64_t n_out = -1;
+    if (n_per_subject >= 0) {
+        n_out = subject_out_first(ctx, n_per_subject);
+        if (n_out < 0) return fail(ctx, GSVR_ERR_CUDA, "upload of the sample offsets failed");
+    }
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    if (ctx->graph) {
+        cudaGraphDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    gsvr_status s = GSVR_OK;
+    const unsigned long long *dstep = &ctx->d_counters.p->step;
+    if (n_out >= 0)
+        s = sample_ranges(ctx, ctx->n_subj, ctx->d_subj_mask_first.p, ctx->d_subj_out_first.p, (int)n_out, 0, dstep);
+    if (!s) s = gsvr_forward(ctx);
+    if (!s) s = gsvr_backward(ctx);
+    if (!s) s = adam_launch(ctx, cfg, 1, dstep);
+    if (!s) launch_advance_step(&ctx->d_counters.p->step, st);
+    ctx->capturing = false;
+    cudaGraph_t gph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &gph);
+    if (s) {
+        if (gph) cudaGraphDestroy(gph);
+        cudaGetLastError();
+        return s;
+    }
+    if (ec != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GSVR_ERR_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(ec));
+    }
+    ctx->graph = gph;
+    CK(cudaGraphInstantiate(&ctx->graph_exec, gph, 0));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_graph_launch(gsvr_ctx *ctx, int32_t iterations) {
+    if (check_ctx(ctx) || iterations < 0) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->graph_exec) return fail(ctx, GSVR_ERR_STATE, "no captured graph");
+    DeviceGuard g(ctx->device);
+    for (int k = 0; k < iterations; ++k) CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    note_launches(0);
     ctx->fwd_valid = false;
     return GSVR_OK;
 }

@@ -42,7 +42,8 @@ struct SliceDev {
     int tile_base;            // global id of the slice's first tile
     int pix_base;             // global index of the slice's first pixel
     int stack;
-    int pad_[3];
+    int subject;              // reconstruction this slice belongs to (batched form)
+    int pad_[2];
 };
 
 struct SliceStatic {
@@ -57,6 +58,8 @@ struct Counters {
     int n_keys;
     int n_items;
     unsigned long long pairs;  // pixel x record pairs visited by one evaluation pass
+    unsigned long long step;   // device iteration counter (graph replay)
+    int work_fwd, work_bwd;    // work-queue heads of the persistent evaluation kernels
 };
 
 // A (slice, Gaussian) record: the 3D Gaussian conditioned on the slice plane

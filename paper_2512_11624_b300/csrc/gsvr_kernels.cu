@@ -294,23 +294,56 @@ __global__ void k_pose_prep(const float *__restrict__ pose, const SliceStatic *_
 }
 
 // ---------------------------------------------------------------- sampling
-__global__ void k_sample_flags(int n_mask, int n_s, SamplerKeys sk, const int *__restrict__ mask_tpos,
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long ctr) {
+    unsigned long long z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Output t of the concatenated per-subject samples: subject k by binary search
+// in out_first, then the keyed 4-round bijection on k bits with cycle walking
+// (SplitMix64 round keys from seed + k * golden gamma and counter 4 step + r).
+__global__ void k_sample_flags(int n_subj, const int *__restrict__ mask_first, const int *__restrict__ out_first,
+                               int n_out, unsigned long long seed, unsigned long long step,
+                               const unsigned long long *d_step, const int *__restrict__ mask_tpos,
                                int *__restrict__ flags) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_s) return;
-    const unsigned long long msk = (sk.k >= 64) ? ~0ull : ((1ull << sk.k) - 1ull);
-    unsigned long long x = (unsigned long long)t;
-    // cycle walking terminates within 2^k steps (f permutes [0, 2^k))
+    if (t >= n_out) return;
+    int lo = 0, hi = n_subj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (out_first[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int sj = lo;
+    const int n_mask = mask_first[sj + 1] - mask_first[sj];
+    if (n_mask <= 0) return;
+    const unsigned long long stp = d_step ? *d_step : step;
+    const unsigned long long sseed = seed + (unsigned long long)sj * 0x9E3779B97F4A7C15ull;
+    int k = 1;
+    while ((1ll << k) < (long long)n_mask) ++k;
+    const int h = (k + 1) / 2;
+    const unsigned long long msk = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
+    unsigned long long xk[4], mul[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const unsigned long long key = splitmix64_at(sseed, 4ull * stp + (unsigned long long)r);
+        xk[r] = key & msk;
+        mul[r] = (key >> 32) | 1ull;
+    }
+    unsigned long long x = (unsigned long long)(t - out_first[sj]);
+    // cycle walking terminates within 2^k steps (the rounds permute [0, 2^k))
     for (unsigned long long it = 0; it <= msk; ++it) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            x = (x ^ sk.xk[r]) & msk;
-            x = (x * sk.mul[r]) & msk;
-            x ^= x >> sk.h;
+            x = (x ^ xk[r]) & msk;
+            x = (x * mul[r]) & msk;
+            x ^= x >> h;
         }
         if (x < (unsigned long long)n_mask) break;
     }
-    if (x < (unsigned long long)n_mask) flags[mask_tpos[x]] = 1;
+    if (x < (unsigned long long)n_mask) flags[mask_tpos[mask_first[sj] + (int)x]] = 1;
 }
 
 __global__ void k_flags_from_list(const int *__restrict__ idx, int n, int n_pix, const uint8_t *__restrict__ mask,
@@ -368,6 +401,57 @@ __global__ void __launch_bounds__(128) k_cand(BinArgs a) {
     int n = 0;
     const int base = EMIT && live ? a.rec_off[j] : 0;
     const int room = EMIT && live ? a.rec_off[j + 1] - base : 0;
+    // a Gaussian meets only its own subject's slices; the block walks the union
+    // of its threads' slice ranges (Gaussians of a subject are contiguous)
+    int sl0 = 0, sl1 = a.M;
+    if (a.gauss_subject) {
+        __shared__ int blo, bhi;
+        if (threadIdx.x == 0) {
+            blo = a.M;
+            bhi = 0;
+        }
+        __syncthreads();
+        if (live) {
+            const int sj = a.gauss_subject[j];
+            sl0 = a.subj_slice_first[sj];
+            sl1 = a.subj_slice_first[sj + 1];
+            atomicMin(&blo, sl0);
+            atomicMax(&bhi, sl1);
+        }
+        __syncthreads();
+        if (!live) {
+            sl0 = blo;
+            sl1 = blo;
+        }
+        const int b0 = blo, b1 = bhi;
+        __syncthreads();
+        for (int i0 = b0; i0 < b1; i0 += kSliceChunk) {
+            __syncthreads();
+            const int nc = min(kSliceChunk, b1 - i0);
+            {
+                const int words = nc * (int)(sizeof(SliceDev) / 4);
+                const int *src = reinterpret_cast<const int *>(a.slices + i0);
+                int *dst = reinterpret_cast<int *>(ssl);
+                for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+            }
+            __syncthreads();
+            if (!live) continue;
+            for (int ii = 0; ii < nc; ++ii) {
+                const int i = i0 + ii;
+                if (i < sl0 || i >= sl1 || !slab_candidate(g0, g1, mu, ssl[ii], a.rc2)) continue;
+                if (EMIT && n < room) {
+                    const int c = base + n;
+                    if (c < a.cap_rec) a.cand[c] = make_int2(j, i);
+                    else atomicOr(a.status, ST_CAPACITY);
+                }
+                ++n;
+            }
+        }
+        if (!EMIT && live) a.rec_cnt[j] = n;
+        if (EMIT && live)
+            for (int k = n; k < room && base + k < a.cap_rec; ++k) a.cand[base + k] = make_int2(j, -1);
+        return;
+    }
     for (int i0 = 0; i0 < a.M; i0 += kSliceChunk) {
         __syncthreads();
         const int nc = min(kSliceChunk, a.M - i0);
@@ -510,12 +594,13 @@ __device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, 
     return g;
 }
 
-// One CTA per work item.  The item's records (at most kItemRecs x 32 bytes) come
-// into shared memory by one 1-D bulk copy (cp.async.bulk, completion on an
-// mbarrier).  The CTA is G groups of threads; in a group each thread owns a run
-// of PXR consecutive pixels of one tile row, and the groups split the records
-// (every lane of a warp reads the same record: a broadcast).  With the row
-// fixed, the record's row terms C2 da and B da^2 are formed once per PXR pixels:
+// Persistent CTAs take work items from a queue (Counters::work_fwd).  An item's
+// records (at most kItemRecs x 32 bytes) come into shared memory by one 1-D bulk
+// copy (cp.async.bulk, completion on an mbarrier, one phase per item).  The CTA
+// is G groups of threads; in a group each thread owns a run of PXR consecutive
+// pixels of one tile row, and the groups split the records (every lane of a
+// warp reads the same record: a broadcast).  With the row fixed, the record's
+// row terms C2 da and B da^2 are formed once per PXR pixels:
 //   q = (A db + C2 da) db + B da^2,   sum += w exp2(q).
 // The groups' sums meet in shared memory; part[item][pixel] holds the item's
 // sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
@@ -526,93 +611,103 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
-    const int i = blockIdx.x;
-    if (i >= min(*a.n_items, a.cap_items)) return;
-    const int t = a.item_tile[i];
-    const int c = i - a.item_first[t];
-    const int rs = a.tile_rec_start[t] + c * kItemRecs;
-    const int nrec = max(0, min(kItemRecs, a.tile_rec_end[t] - rs));
-    const SliceDev &S = a.slices[a.tile_slice[t]];
-    const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+    __shared__ int s_item;
+    const int n_items = min(*a.n_items, a.cap_items);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t phase = 0;
+    unsigned long long useful = 0;
     const int segs = (a.tile_w + PXR - 1) / PXR;
     const int tpg = a.tile_h * segs;
     const int G = max(1, (int)blockDim.x / tpg);
     const int g = threadIdx.x / tpg, seg = threadIdx.x - g * tpg;
     const int row = seg / segs, col0 = (seg - row * segs) * PXR;
-    const bool active = g < G && row < tg.rows;
-    const float rowf = (float)(tg.y0 + row) - S.cy0;
-    const float colf0 = (float)(tg.x0 + col0) - S.cx0;
-    if (COUNT) {
-        const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-        for (int k = threadIdx.x; k < a.tile_px; k += blockDim.x) present[k] = 0;
+    for (;;) {
+        __syncthreads();  // previous item's buffers are free
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_fwd, 1);
         __syncthreads();
-        for (int s = ps + threadIdx.x; s < pe; s += blockDim.x) {
-            const int loc = a.sampled[s] - S.pix_base;
-            const int r0 = loc / S.W;
-            present[(r0 - tg.y0) * a.tile_w + (loc - r0 * S.W - tg.x0)] = 1;
-        }
-    }
-    float acc[PXR];
-#pragma unroll
-    for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
-    unsigned long long useful = 0;
-    if (nrec > 0) {
-        if (threadIdx.x == 0) {
-            mbar_init(&bar, 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t bytes = (uint32_t)nrec * (uint32_t)sizeof(Rec);
-            mbar_arrive_expect_tx(&bar, bytes);
-            bulk_g2s(&buf[0], a.trec + rs, bytes, &bar);
-        }
-        const bool ok = mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
-        if (!ok) atomicOr(a.status, ST_TIMEOUT);
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
+        const int i = s_item;
+        if (i >= n_items) break;
+        const int t = a.item_tile[i];
+        const int c = i - a.item_first[t];
+        const int rs = a.tile_rec_start[t] + c * kItemRecs;
+        const int nrec = max(0, min(kItemRecs, a.tile_rec_end[t] - rs));
+        const SliceDev &S = a.slices[a.tile_slice[t]];
+        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+        const bool active = g < G && row < tg.rows;
+        const float rowf = (float)(tg.y0 + row) - S.cy0;
+        const float colf0 = (float)(tg.x0 + col0) - S.cx0;
+        if (COUNT) {
+            const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+            for (int k = threadIdx.x; k < a.tile_px; k += blockDim.x) present[k] = 0;
             __syncthreads();
-            return;
+            for (int s2 = ps + threadIdx.x; s2 < pe; s2 += blockDim.x) {
+                const int loc = a.sampled[s2] - S.pix_base;
+                const int r0 = loc / S.W;
+                present[(r0 - tg.y0) * a.tile_w + (loc - r0 * S.W - tg.x0)] = 1;
+            }
         }
-        if (active) {
-            for (int r = g; r < nrec; r += G) {
-                const float4 r0 = buf[r].a;
-                const float4 r1 = buf[r].b;
-                const float dy = rowf - r0.y;
-                const float cdy = r0.w * dy;
-                const float bdy = r1.x * dy * dy;
+        float acc[PXR];
 #pragma unroll
-                for (int k = 0; k < PXR; ++k) {
-                    const float dx = (colf0 + (float)k) - r0.x;
-                    const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
-                    if (!COUNT) {
-                        acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
-                    } else {
-                        const int col = col0 + k;
-                        useful += (col < tg.cols && present[row * a.tile_w + col] && q + r1.z >= a.qcut) ? 1ull
-                                                                                                       : 0ull;
+        for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
+        if (nrec > 0) {
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = (uint32_t)nrec * (uint32_t)sizeof(Rec);
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar, bytes);
+                bulk_g2s(&buf[0], a.trec + rs, bytes, &bar);
+            }
+            const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
+            if (!ok) atomicOr(a.status, ST_TIMEOUT);
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase, kWaitLimitNs);
+                __syncthreads();
+                return;
+            }
+            phase ^= 1u;
+            if (active) {
+                for (int r = g; r < nrec; r += G) {
+                    const float4 r0 = buf[r].a;
+                    const float4 r1 = buf[r].b;
+                    const float dy = rowf - r0.y;
+                    const float cdy = r0.w * dy;
+                    const float bdy = r1.x * dy * dy;
+#pragma unroll
+                    for (int k = 0; k < PXR; ++k) {
+                        const float dx = (colf0 + (float)k) - r0.x;
+                        const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
+                        if (!COUNT) {
+                            acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
+                        } else {
+                            const int col = col0 + k;
+                            useful += (col < tg.cols && present[row * a.tile_w + col] && q + r1.z >= a.qcut)
+                                          ? 1ull
+                                          : 0ull;
+                        }
                     }
                 }
             }
+        }
+        if (COUNT) continue;
+        // groups -> one sum per dense tile pixel
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < PXR; ++k)
+                if (col0 + k < a.tile_w) red[g * a.tile_px + row * a.tile_w + col0 + k] = acc[k];
+        }
+        __syncthreads();
+        for (int px = threadIdx.x; px < a.tile_px; px += blockDim.x) {
+            float sum = 0.f;
+            for (int gg = 0; gg < G; ++gg) sum += red[gg * a.tile_px + px];
+            a.part[(size_t)i * a.tile_px + px] = sum;
         }
     }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) useful += __shfl_down_sync(0xffffffffu, useful, o);
         if ((threadIdx.x & 31) == 0 && useful) atomicAdd(a.useful, useful);
-        return;
-    }
-    // groups -> one sum per dense tile pixel
-    if (active) {
-#pragma unroll
-        for (int k = 0; k < PXR; ++k)
-            if (col0 + k < a.tile_w) red[g * a.tile_px + row * a.tile_w + col0 + k] = acc[k];
-    }
-    __syncthreads();
-    for (int px = threadIdx.x; px < a.tile_px; px += blockDim.x) {
-        float s = 0.f;
-        for (int gg = 0; gg < G; ++gg) s += red[gg * a.tile_px + px];
-        a.part[(size_t)i * a.tile_px + px] = s;
     }
 }
 
@@ -637,7 +732,8 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         float acc = 0.f;
         const int i1 = min(a.item_first[t + 1], a.cap_items);
         for (int i = a.item_first[t]; i < i1; ++i) acc += a.part[(size_t)i * a.tile_px + px];
-        const float wp = 1.0f / (float)max(*a.n_sampled, 1);
+        const int ns = a.subj_cnt ? a.subj_cnt[S.subject] : *a.n_sampled;
+        const float wp = 1.0f / (float)max(ns, 1);
         const float r = acc - a.I_obs[p];
         a.pred[p] = acc;
         a.rbar[p] = 2.0f * wp * r;
@@ -676,80 +772,90 @@ __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, flo
 
 __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
     extern __shared__ float rb[];  // tile_h x tile_w
-    const int i = blockIdx.x;
-    if (i >= min(*a.n_items, a.cap_items)) return;
-    const int t = a.item_tile[i];
-    const int c = i - a.item_first[t];
-    const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-    const int rs = a.tile_rec_start[t] + c * kItemRecs;
-    const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
-    if (ps >= pe || rs >= re) return;
-    const SliceDev &S = a.slices[a.tile_slice[t]];
-    const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+    __shared__ int s_item;
+    const int n_items = min(*a.n_items, a.cap_items);
     const int tw = a.tile_w;
-    for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb[k] = 0.f;
-    __syncthreads();
-    for (int s = ps + threadIdx.x; s < pe; s += kThreads) {
-        const int p = a.sampled[s];
-        const int loc = p - S.pix_base;
-        const int r0 = loc / S.W;
-        rb[(r0 - tg.y0) * tw + (loc - r0 * S.W - tg.x0)] = a.rbar[p];
-    }
-    __syncthreads();
-    const int r0 = rs + threadIdx.x;
-    if (r0 >= re) return;
-    const int r1 = r0 + kThreads;
-    const bool v1 = r1 < re;
-    const Rec A = a.trec[r0];
-    const Rec B = v1 ? a.trec[r1] : A;
-    float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float colf0 = (float)tg.x0 - S.cx0;
-    for (int row = 0; row < tg.rows; ++row) {
-        const float rowf = (float)(tg.y0 + row) - S.cy0;
-        const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
-        const float cA = A.a.w * dyA, bA = A.b.x * dyA * dyA;
-        const float cB = B.a.w * dyB, bB = B.b.x * dyB * dyB;
-        float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
-        const float *rrow = rb + row * tw;
-#pragma unroll 4
-        for (int col = 0; col < tg.cols; ++col) {
-            const float g = rrow[col];
-            const float colf = colf0 + (float)col;
-            {
-                const float dx = colf - A.a.x;
-                const float e = g * ex2_approx(fmaf(fmaf(A.a.z, dx, cA), dx, bA));
-                const float ex = e * dx;
-                A0 += e;
-                A1 += ex;
-                A2 = fmaf(ex, dx, A2);
-            }
-            {
-                const float dx = colf - B.a.x;
-                const float e = g * ex2_approx(fmaf(fmaf(B.a.z, dx, cB), dx, bB));
-                const float ex = e * dx;
-                B0 += e;
-                B1 += ex;
-                B2 = fmaf(ex, dx, B2);
-            }
+    for (;;) {
+        __syncthreads();  // previous item's r_bar tile is free
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
+        __syncthreads();
+        const int i = s_item;
+        if (i >= n_items) break;
+        const int t = a.item_tile[i];
+        const int c = i - a.item_first[t];
+        const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
+        const int rs = a.tile_rec_start[t] + c * kItemRecs;
+        const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
+        if (ps >= pe || rs >= re) continue;
+        const SliceDev &S = a.slices[a.tile_slice[t]];
+        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb[k] = 0.f;
+        __syncthreads();
+        for (int s2 = ps + threadIdx.x; s2 < pe; s2 += kThreads) {
+            const int p = a.sampled[s2];
+            const int loc = p - S.pix_base;
+            const int r0 = loc / S.W;
+            rb[(r0 - tg.y0) * tw + (loc - r0 * S.W - tg.x0)] = a.rbar[p];
         }
-        bwd_row_fold(mA, A0, A1, A2, dyA);
-        bwd_row_fold(mB, B0, B1, B2, dyB);
-    }
-    const int k0 = __float_as_int(A.b.w);
-    a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
-    a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
-    if (v1) {
-        const int k1 = __float_as_int(B.b.w);
-        a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
-        a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
+        __syncthreads();
+        const int r0 = rs + threadIdx.x;
+        if (r0 >= re) continue;
+        const int r1 = r0 + kThreads;
+        const bool v1 = r1 < re;
+        const Rec A = a.trec[r0];
+        const Rec B = v1 ? a.trec[r1] : A;
+        float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float colf0 = (float)tg.x0 - S.cx0;
+        for (int row = 0; row < tg.rows; ++row) {
+            const float rowf = (float)(tg.y0 + row) - S.cy0;
+            const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
+            const float cA = A.a.w * dyA, bA = A.b.x * dyA * dyA;
+            const float cB = B.a.w * dyB, bB = B.b.x * dyB * dyB;
+            float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+            const float *rrow = rb + row * tw;
+#pragma unroll 4
+            for (int col = 0; col < tg.cols; ++col) {
+                const float gg = rrow[col];
+                const float colf = colf0 + (float)col;
+                {
+                    const float dx = colf - A.a.x;
+                    const float e = gg * ex2_approx(fmaf(fmaf(A.a.z, dx, cA), dx, bA));
+                    const float ex = e * dx;
+                    A0 += e;
+                    A1 += ex;
+                    A2 = fmaf(ex, dx, A2);
+                }
+                {
+                    const float dx = colf - B.a.x;
+                    const float e = gg * ex2_approx(fmaf(fmaf(B.a.z, dx, cB), dx, bB));
+                    const float ex = e * dx;
+                    B0 += e;
+                    B1 += ex;
+                    B2 = fmaf(ex, dx, B2);
+                }
+            }
+            bwd_row_fold(mA, A0, A1, A2, dyA);
+            bwd_row_fold(mB, B0, B1, B2, dyB);
+        }
+        const int k0 = __float_as_int(A.b.w);
+        a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
+        a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
+        if (v1) {
+            const int k1 = __float_as_int(B.b.w);
+            a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
+            a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
+        }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, int n, double *loss,
-                                                      unsigned *status) {
+// Per-subject losses: block k sums its subject's tiles in tile order.
+__global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, int n, const int *tile_first,
+                                                      double *subj_loss) {
     __shared__ double red[32];
+    const int k = blockIdx.x;
+    const int t0 = tile_first ? tile_first[k] : 0, t1 = tile_first ? tile_first[k + 1] : n;
     double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += 1024) s += tile_loss[t];
+    for (int t = t0 + threadIdx.x; t < t1; t += 1024) s += tile_loss[t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -757,8 +863,32 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, i
     if (threadIdx.x == 0) {
         double tot = 0.0;
         for (int w = 0; w < 32; ++w) tot += red[w];
-        *loss = tot;
-        if (!isfinite(tot)) atomicOr(status, ST_NONFINITE);
+        subj_loss[k] = tot;
+    }
+}
+
+__global__ void k_loss_total(const double *subj_loss, int n_subj, double *loss, unsigned *status) {
+    double tot = 0.0;
+    for (int k = 0; k < n_subj; ++k) tot += subj_loss[k];
+    *loss = tot;
+    if (!isfinite(tot)) atomicOr(status, ST_NONFINITE);
+}
+
+// Sampled pixels per subject (sum of its tiles' pixel counts).
+__global__ void __launch_bounds__(256) k_subject_counts(const int *__restrict__ tps, const int *__restrict__ tpe,
+                                                       const int *__restrict__ tile_first, int *cnt) {
+    __shared__ int red[8];
+    const int k = blockIdx.x;
+    int s = 0;
+    for (int t = tile_first[k] + threadIdx.x; t < tile_first[k + 1]; t += 256) s += tpe[t] - tps[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        cnt[k] = tot;
     }
 }
 
@@ -1012,10 +1142,20 @@ __global__ void k_pose_grad(const double *__restrict__ acc, const SliceStatic *_
     }
 }
 
+// Adam with StepLR: lr x gamma^((t - 1) / step_every); the 1-based step t from
+// the argument or from the device iteration counter (graph replay).
 __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int N, int M, float lr0, float lr1, float lr2, float lr3, float lr4,
-                       float lr5, float b1, float b2, float eps, float ibc1, float ibc2,
-                       const uint8_t *__restrict__ frozen) {
+                       float lr5, float b1, float b2, float eps, int step_every, float gamma, long long t_host,
+                       const unsigned long long *d_step, const uint8_t *__restrict__ frozen) {
+    __shared__ float s_ibc1, s_ibc2, s_scale;
+    if (threadIdx.x == 0) {
+        const long long t = d_step ? (long long)(*d_step) + 1 : t_host;
+        s_ibc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+        s_ibc2 = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+        s_scale = step_every > 0 ? (float)pow((double)gamma, (double)((t - 1) / step_every)) : 1.0f;
+    }
+    __syncthreads();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = 11LL * N + 6LL * M;
     if (e >= n) return;
@@ -1034,8 +1174,10 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
     const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
     m[e] = mi;
     v[e] = vi;
-    th[e] -= lr * (mi * ibc1) / (sqrtf(vi * ibc2) + eps);
+    th[e] -= (lr * s_scale) * (mi * s_ibc1) / (sqrtf(vi * s_ibc2) + eps);
 }
+
+__global__ void k_advance_step(unsigned long long *d_step) { *d_step += 1ull; }
 
 inline int cdiv(int64_t a, int b) { return (int)((a + b - 1) / b); }
 
@@ -1094,14 +1236,49 @@ void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre
 }
 // Forward CTA shape: groups of tile_h x ceil(tile_w / PXR) threads, as many
 // groups as fit in 128 threads (at least one).
+int eval_blocks_per_sm(int tile_w, int tile_h, bool backward) {
+    int nb = 0;
+    if (backward) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kThreads,
+                                                      (size_t)tile_w * tile_h * sizeof(float));
+    } else {
+        const int pxr = tile_w >= 12 ? 4 : 2;
+        const int tpg = tile_h * ((tile_w + pxr - 1) / pxr);
+        const int G = std::max(1, 128 / tpg);
+        const int nt = round_warp(G * tpg);
+        if (pxr == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 4>, nt, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 2>, nt, 0);
+    }
+    cudaGetLastError();
+    return std::max(nb, 1);
+}
+static int n_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+// Persistent grid: every resident CTA of the GPU (or persistent_blocks), never
+// more CTAs than items.
+static int eval_grid(const EvalArgs &a, bool backward) {
+    const int g = a.persistent_blocks > 0 ? a.persistent_blocks
+                                          : n_sms() * eval_blocks_per_sm(a.tile_w, a.tile_h, backward);
+    return std::max(1, std::min(g, a.cap_items));
+}
 template <bool COUNT>
 static void fwd_items(const EvalArgs &a, cudaStream_t st) {
     const int pxr = a.tile_w >= 12 ? 4 : 2;
     const int tpg = a.tile_h * ((a.tile_w + pxr - 1) / pxr);
     const int G = std::max(1, 128 / tpg);
     const int nt = round_warp(G * tpg);
-    if (pxr == 4) k_fwd_items<COUNT, 4><<<a.cap_items, nt, 0, st>>>(a);
-    else k_fwd_items<COUNT, 2><<<a.cap_items, nt, 0, st>>>(a);
+    cudaMemsetAsync(&a.counters->work_fwd, 0, sizeof(int), st);
+    const int grid = eval_grid(a, false);
+    if (pxr == 4) k_fwd_items<COUNT, 4><<<grid, nt, 0, st>>>(a);
+    else k_fwd_items<COUNT, 2><<<grid, nt, 0, st>>>(a);
     counted();
 }
 void launch_forward(const EvalArgs &a, cudaStream_t st) {
@@ -1116,11 +1293,20 @@ void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
 }
 void launch_backward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
-    k_bwd_items<<<a.cap_items, kThreads, (size_t)a.tile_px * sizeof(float), st>>>(a);
+    cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
+    k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float), st>>>(a);
     counted();
 }
-void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st) {
-    k_loss_reduce<<<1, 1024, 0, st>>>(tile_loss, n_tiles, loss, status);
+void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
+                        double *loss, unsigned *status, cudaStream_t st) {
+    k_loss_reduce<<<std::max(n_subj, 1), 1024, 0, st>>>(tile_loss, n_tiles, tile_first, subj_loss);
+    k_loss_total<<<1, 1, 0, st>>>(subj_loss, std::max(n_subj, 1), loss, status);
+    counted(2);
+}
+void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first, int n_subj, int *cnt,
+                           cudaStream_t st) {
+    if (n_subj <= 0) return;
+    k_subject_counts<<<n_subj, 256, 0, st>>>(tps, tpe, tile_first, cnt);
     counted();
 }
 void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
@@ -1144,17 +1330,24 @@ void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float
     counted();
 }
 void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
-                 float b2, float eps, double bc1, double bc2, const uint8_t *frozen, cudaStream_t st) {
+                 float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
+                 const uint8_t *frozen, cudaStream_t st) {
     const int64_t n = 11LL * N + 6LL * M;
     if (n <= 0) return;
     k_adam<<<cdiv(n, 256), 256, 0, st>>>(theta, grad, m, v, N, M, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], b1, b2,
-                                         eps, (float)(1.0 / bc1), (float)(1.0 / bc2), frozen);
+                                         eps, step_every, gamma, t_host, d_step, frozen);
     counted();
 }
-void launch_sample_flags(int n_mask, int n_s, const SamplerKeys &sk, const int *mask_tpos, int *flags,
+void launch_advance_step(unsigned long long *d_step, cudaStream_t st) {
+    k_advance_step<<<1, 1, 0, st>>>(d_step);
+    counted();
+}
+void launch_sample_flags(int n_subj, const int *mask_first, const int *out_first, int n_out, uint64_t seed,
+                         uint64_t step, const unsigned long long *d_step, const int *mask_tpos, int *flags,
                          cudaStream_t st) {
-    if (n_s <= 0) return;
-    k_sample_flags<<<cdiv(n_s, 256), 256, 0, st>>>(n_mask, n_s, sk, mask_tpos, flags);
+    if (n_out <= 0) return;
+    k_sample_flags<<<cdiv(n_out, 256), 256, 0, st>>>(n_subj, mask_first, out_first, n_out, seed, step, d_step,
+                                                     mask_tpos, flags);
     counted();
 }
 void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mask, const int *pix_tpos,

@@ -18,6 +18,8 @@ struct BinArgs {
     const int *rec_off;        // first candidate of each Gaussian, N + 1
     const int *n_rec;          // device count of candidates (= records)
     int2 *cand;                // (Gaussian, slice) per candidate; slice -1 = padding
+    const int *gauss_subject;  // subject of each Gaussian (null: one subject)
+    const int *subj_slice_first;  // first slice of each subject (n_subj + 1)
     Rec *rec;                  // one record per candidate
     int2 *rec_tiles;           // packed tile bounding box per record
     int *rec_nkeys;            // keys per record
@@ -62,6 +64,8 @@ struct EvalArgs {
     const int *n_items;               // device count
     float *part;                      // per-item partial pixel sums (cap_items x tile_px)
     int cap_items;
+    const int *subj_cnt;              // sampled pixels per subject (null: *n_sampled)
+    int persistent_blocks;            // grid of the persistent evaluation kernels (0: one block per item)
     int tile_px;                      // tile_w * tile_h
     int tile_w, tile_h;
     int n_tiles;
@@ -104,19 +108,31 @@ void launch_count_pairs(const EvalArgs &a, cudaStream_t st);
 long long launch_count();  // kernels launched by this library so far
 void note_launches(int n); // count kernels launched from other translation units
 void launch_backward(const EvalArgs &a, cudaStream_t st);
-void launch_loss_reduce(const double *tile_loss, int n_tiles, double *loss, unsigned *status, cudaStream_t st);
+// Per-subject losses (subject k owns tiles [tile_first[k], tile_first[k+1]), summed in
+// tile order) and their total; tile_first null = one subject.
+void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
+                        double *loss, unsigned *status, cudaStream_t st);
+// Sampled pixels per subject: cnt[k] = sum of the subject's tile pixel counts.
+void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first, int n_subj, int *cnt,
+                           cudaStream_t st);
+// Occupancy of the evaluation kernels (blocks per SM) for the persistent grids.
+int eval_blocks_per_sm(int tile_w, int tile_h, bool backward);
 void launch_gauss_grad(const GradArgs &a, cudaStream_t st);
 void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
                       cudaStream_t st);
+// Adam with StepLR (lr x gamma^((t-1) / step_every), step_every 0 = constant); the
+// 1-based step t comes from `t_host` or, when d_step is non-null, from *d_step + 1.
 void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
-                 float b2, float eps, double bc1, double bc2, const uint8_t *frozen, cudaStream_t st);
+                 float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
+                 const uint8_t *frozen, cudaStream_t st);
+void launch_advance_step(unsigned long long *d_step, cudaStream_t st);
 
-// Sampler: round keys and multipliers of the 4-round bijection on k bits.
-struct SamplerKeys {
-    unsigned long long xk[4], mul[4];
-    int k, h;
-};
-void launch_sample_flags(int n_mask, int n_s, const SamplerKeys &sk, const int *mask_tpos, int *flags,
+// Sampler: for subject k, out_first[k+1] - out_first[k] of its mask_count[k]
+// masked pixels (tile-order positions mask_tpos[mask_first[k] + x]); the round
+// keys come from SplitMix64(seed + k * golden gamma, 4 step + r), the step from
+// `step` or, when d_step is non-null, from *d_step.
+void launch_sample_flags(int n_subj, const int *mask_first, const int *out_first, int n_out, uint64_t seed,
+                         uint64_t step, const unsigned long long *d_step, const int *mask_tpos, int *flags,
                          cudaStream_t st);
 void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mask, const int *pix_tpos,
                             int *flags, unsigned *status, cudaStream_t st);

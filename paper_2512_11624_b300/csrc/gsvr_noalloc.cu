@@ -201,6 +201,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     int *d_trs = cv.take<int>(T);
     int *d_tre = cv.take<int>(T);
     double *d_tile_loss = cv.take<double>(T);
+    double *d_subj_loss = cv.take<double>(1);
     float4 *d_gpre = cv.take<float4>(2 * N);
     int *d_rec_cnt = cv.take<int>(N + 1);
     int *d_rec_off = cv.take<int>(N + 1);
@@ -369,7 +370,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     e.n_tiles = (int)T;
     e.status = d_status;
     launch_forward(e, st);
-    launch_loss_reduce(d_tile_loss, (int)T, loss, d_status, st);
+    launch_loss_reduce(d_tile_loss, (int)T, nullptr, 1, d_subj_loss, loss, d_status, st);
     NA_CK(cudaGetLastError());
     unsigned stt = 0;
     NA_CK(cudaMemcpyAsync(&stt, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

@@ -28,7 +28,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_set_pixel_sample", "gsvr_sample_pixels", "gsvr_forward", "gsvr_backward", "gsvr_adam_step",
            "gsvr_step_host", "gsvr_get_sample", "gsvr_get_views", "gsvr_get_stats", "gsvr_sync_status",
            "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
-           "gsvr_alu_peaks"]
+           "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
+           "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -53,7 +54,7 @@ class Config(C.Structure):
 class AdamCfg(C.Structure):
     _fields_ = [("lr_mu", C.c_float), ("lr_ls", C.c_float), ("lr_q", C.c_float), ("lr_c", C.c_float),
                 ("lr_rot", C.c_float), ("lr_trans", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("reserved", C.c_int32)]
+                ("eps", C.c_float), ("step_every", C.c_int32), ("gamma", C.c_float)]
 
 
 class KernelTimes(C.Structure):
@@ -104,6 +105,12 @@ def _load():
         "gsvr_count_pairs": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "gsvr_alu_peaks": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
                            C.c_int),
+        "gsvr_set_subjects": ([vp, i32, vp, vp], C.c_int),
+        "gsvr_sample_pixels_subjects": ([vp, i64, u64], C.c_int),
+        "gsvr_get_subject_losses": ([vp, vp, i32], C.c_int),
+        "gsvr_graph_capture": ([vp, i64, C.POINTER(AdamCfg)], C.c_int),
+        "gsvr_graph_launch": ([vp, i32], C.c_int),
+        "gsvr_set_step": ([vp, i64], C.c_int),
         "gsvr_forward_noalloc": ([C.c_int, vp, i32, C.POINTER(StackDesc), i64, vp, vp, vp, i64, C.c_float, i32, vp,
                                   vp, C.c_char_p, i32], C.c_int),
     }
@@ -245,11 +252,44 @@ def gsvr_backward(ctx):
 PAPER_LR = dict(lr_mu=2.5e-2, lr_ls=2.5e-2, lr_q=1e-2, lr_c=1e-2, lr_rot=2.5e-3, lr_trans=1e-1)
 
 
-def gsvr_adam_step(ctx, step, lr=None, beta1=0.9, beta2=0.999, eps=1e-8):
+def adam_cfg(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, step_every=0, gamma=1.0):
     lr = dict(PAPER_LR, **(lr or {}))
-    cfg = AdamCfg(lr["lr_mu"], lr["lr_ls"], lr["lr_q"], lr["lr_c"], lr["lr_rot"], lr["lr_trans"], beta1, beta2,
-                  eps, 0)
+    return AdamCfg(lr["lr_mu"], lr["lr_ls"], lr["lr_q"], lr["lr_c"], lr["lr_rot"], lr["lr_trans"], beta1, beta2, eps,
+                   int(step_every or 0), float(gamma))
+
+
+def gsvr_adam_step(ctx, step, lr=None, beta1=0.9, beta2=0.999, eps=1e-8, step_every=0, gamma=1.0):
+    cfg = adam_cfg(lr, beta1, beta2, eps, step_every, gamma)
     return _check(ctx, lib.gsvr_adam_step(ctx, C.byref(cfg), int(step)))
+
+
+def gsvr_set_subjects(ctx, stack_subject, gauss_count):
+    ss = np.ascontiguousarray(stack_subject, dtype=np.int32)
+    gc = np.ascontiguousarray(gauss_count, dtype=np.int64)
+    return _check(ctx, lib.gsvr_set_subjects(ctx, int(gc.size), ss.ctypes.data, gc.ctypes.data))
+
+
+def gsvr_sample_pixels_subjects(ctx, n_per_subject, step):
+    return _check(ctx, lib.gsvr_sample_pixels_subjects(ctx, int(n_per_subject), C.c_uint64(int(step))))
+
+
+def gsvr_get_subject_losses(ctx, n):
+    out = np.zeros(int(n), np.float64)
+    _check(ctx, lib.gsvr_get_subject_losses(ctx, out.ctypes.data, int(n)))
+    return out
+
+
+def gsvr_graph_capture(ctx, n_per_subject, lr=None, beta1=0.9, beta2=0.999, eps=1e-8, step_every=0, gamma=1.0):
+    cfg = adam_cfg(lr, beta1, beta2, eps, step_every, gamma)
+    return _check(ctx, lib.gsvr_graph_capture(ctx, int(n_per_subject), C.byref(cfg)))
+
+
+def gsvr_graph_launch(ctx, iterations=1):
+    return _check(ctx, lib.gsvr_graph_launch(ctx, int(iterations)))
+
+
+def gsvr_set_step(ctx, step):
+    return _check(ctx, lib.gsvr_set_step(ctx, int(step)))
 
 
 def gsvr_step_host(ctx, theta, idx, grad_out=None, loss_out=None):

@@ -340,3 +340,67 @@ def grid_probe(phantom, h=0.8, margin=2.0):
     ref = phantom(P).astype(np.float32)
     inside = phantom.inside(P).astype(np.uint8)
     return st, ref, inside
+
+
+def concat_cases(cases):
+    """Several cases as one batched case: stacks, observations, masks and poses
+    concatenated in subject order, Gaussian parameters concatenated per
+    component (the parameter vector stays component-major over all Gaussians).
+    Adds "stack_subject" (per stack) and "gauss_count" (per subject)."""
+    Ns = [int(c["N"]) for c in cases]
+    N = sum(Ns)
+    comps = []
+    for k in range(11):
+        comps.append(np.concatenate([c["theta"][k * n:(k + 1) * n] for c, n in zip(cases, Ns)]))
+    poses = np.concatenate([c["theta"][11 * n:] for c, n in zip(cases, Ns)])
+    out = {"name": "batched", "N": N, "stacks": [s for c in cases for s in c["stacks"]],
+           "theta": np.concatenate(comps + [poses]).astype(np.float32),
+           "I": np.concatenate([c["I"] for c in cases]).astype(np.float32),
+           "mask": np.concatenate([c["mask"] for c in cases]).astype(np.uint8),
+           "stack_subject": np.array([k for k, c in enumerate(cases) for _ in c["stacks"]], np.int32),
+           "gauss_count": np.array(Ns, np.int64), "n_sample": max(int(c.get("n_sample", 0)) for c in cases)}
+    return out
+
+
+def subject_theta(theta, gauss_count, k):
+    """The 11 N_k Gaussian entries of subject k from a batched parameter vector."""
+    g = np.concatenate([[0], np.cumsum(gauss_count)]).astype(np.int64)
+    N = int(g[-1])
+    return np.concatenate([theta[c * N + g[k]:c * N + g[k + 1]] for c in range(11)])
+
+
+def batched(seed=1000, n_subjects=16, nodes=(1, 1, 3)):
+    """The batched multi-subject workload: subjects of uneven size.  Subject k
+    (seed + k): Gaussians N_k log-uniform in [50k, 500k] (brain phantom scaled so
+    its 0.8 mm grid holds N_k), 3-9 stacks (three orthogonal first, then random
+    oblique orientations), 24-60 slices of W x W px with W in {128, 160, 192,
+    224, 256} at 160 mm / W in-plane, thickness U(2.5, 4.5) mm, per-slice motion
+    U(+-15 deg) / U(+-8 mm) (the reference slice 0 of stack 0 unmoved), Rician
+    noise 2 %, mask = phantom dilated by 15 mm x scale; flat-amplitude start."""
+    cases = []
+    for k in range(n_subjects):
+        rng = np.random.default_rng(seed + k)
+        Nk = float(np.exp(rng.uniform(np.log(5e4), np.log(5e5))))
+        scale = (Nk / 200480.0) ** (1.0 / 3.0)
+        ph = BrainPhantom(seed + k, scale=scale)
+        n_st = int(rng.integers(3, 10))
+        W = int(rng.choice([128, 160, 192, 224, 256]))
+        dx = 160.0 / W
+        thick = float(rng.uniform(2.5, 4.5))
+        n_sl = int(rng.integers(24, 61))
+        Rs = [AXIAL, CORONAL, SAGITTAL] + [Rotation.random(random_state=int(rng.integers(1 << 31))).as_matrix()
+                                           for _ in range(n_st - 3)]
+        stacks = [stack(n_sl, W, W, dx, dx, thick, R) for R in Rs]
+        M = n_slices_total(stacks)
+        motion = random_motion(rng, M, 15.0, 8.0)
+        motion[n_sl // 2] = 0.0
+        I, mask = simulate_phantom_stacks(ph, stacks, motion, mask_dilate_mm=15.0 * scale, seed=seed + k,
+                                          nodes=nodes)
+        theta_g, N = grid_gaussians(ph)
+        level = float(np.mean(I[mask > 0][I[mask > 0] > 0.2])) if np.any(I[mask > 0] > 0.2) else 0.5
+        th = theta_g.reshape(11, N)
+        th[10] = level * 0.8 ** 3 / ((2 * np.pi) ** 1.5 * 0.8 ** 3)
+        cases.append({"name": "subject%d" % k, "N": N, "stacks": stacks,
+                      "theta": np.concatenate([th.reshape(-1), np.zeros(6 * M)]).astype(np.float32), "I": I,
+                      "mask": mask, "n_sample": 1 << 18, "ref_slice": n_sl // 2, "phantom": ph})
+    return cases

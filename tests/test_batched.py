@@ -1,0 +1,131 @@
+"""Batched form: several subjects in one context (one set of launches) against
+each subject alone and against the oracle; per-subject sampler against its
+definition; CUDA-graph replay of whole iterations against eager iterations."""
+import numpy as np
+import pytest
+
+from paper_2512_11624_b300 import inputs
+from tests.gpu_util import CUTOFF, describe_grad, forward_ok, grad_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11624_b300 import gsvr
+    return gsvr
+
+
+def three_subjects():
+    return [inputs.random_case(51, 120, [(3, 20, 24)], n_stacks=2, motion_deg=8.0),
+            inputs.random_case(52, 300, [(2, 33, 29), (3, 17, 21)], n_stacks=3, motion_deg=8.0),
+            inputs.random_case(53, 60, [(4, 16, 16)], n_stacks=1, motion_deg=8.0)]
+
+
+def batched_ctx(G, cases, **cfg):
+    b = inputs.concat_cases(cases)
+    ctx = G.Context(b, **cfg)
+    G.gsvr_set_subjects(ctx.ctx, b["stack_subject"], b["gauss_count"])
+    return b, ctx
+
+
+def test_batched_matches_alone_and_oracle(G, oracle):
+    cases = three_subjects()
+    b, ctx = batched_ctx(G, cases, tile_h=12, tile_w=12)
+    ctx.forward()
+    ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    pred = ctx.pred.cpu().numpy()
+    grad = ctx.grad.cpu().numpy().astype(np.float64)
+    losses = G.gsvr_get_subject_losses(ctx.ctx, len(cases))
+    assert abs(ctx.loss() - losses.sum()) <= 1e-12 * abs(losses.sum())
+    ctx.close()
+    pix0 = 0
+    pose0 = 11 * b["N"]
+    for k, c in enumerate(cases):
+        P = inputs.n_pixels_total(c["stacks"])
+        M = inputs.n_slices_total(c["stacks"])
+        alone = G.Context(c, tile_h=12, tile_w=12)
+        alone.forward()
+        alone.backward()
+        a_pred = alone.pred.cpu().numpy()
+        assert np.array_equal(pred[pix0:pix0 + P], a_pred)  # same records in the same order
+        assert abs(losses[k] - alone.loss()) <= 1e-12 * alone.loss()
+        alone.close()
+        g_k = np.concatenate([inputs.subject_theta(grad, b["gauss_count"], k), grad[pose0:pose0 + 6 * M]])
+        pix = np.arange(P)
+        _, L, g, a, _, t = oracle.forward_backward(c["stacks"], c["theta"].astype(np.float64), c["N"], pix,
+                                                   c["I"].astype(np.float64), 1.0 / P, cutoff=CUTOFF)
+        ok, worst, _ = grad_ok(g_k, g, a, t)
+        assert ok.all(), describe_grad(g_k, g, a, c["N"], M, t)
+        pix0 += P
+        pose0 += 6 * M
+
+
+def test_subject_sampler_matches_definition(G, oracle):
+    cases = three_subjects()
+    rng = np.random.default_rng(5)
+    for c in cases:
+        c["mask"] = (rng.uniform(size=c["mask"].size) < 0.7).astype(np.uint8)
+    b, ctx = batched_ctx(G, cases, seed=99)
+    n = 200
+    G.gsvr_sample_pixels_subjects(ctx.ctx, n, 4)
+    got = np.sort(G.gsvr_get_sample(ctx.ctx))
+    want = []
+    base = 0
+    for k, c in enumerate(cases):
+        order = np.array(tile_order(c["stacks"], 16, 16)) + base
+        masked = order[b["mask"][order] > 0]
+        m = min(n, masked.size)
+        pos = oracle.sample_positions(masked.size, m, (99 + k * 0x9E3779B97F4A7C15) % (1 << 64), 4)
+        want.append(masked[pos])
+        base += inputs.n_pixels_total(c["stacks"])
+    assert np.array_equal(got, np.sort(np.concatenate(want)))
+    ctx.close()
+
+
+def tile_order(stacks, th, tw):
+    out, base = [], 0
+    for s in stacks:
+        H, W = s["H"], s["W"]
+        for _ in range(s["n_slices"]):
+            for ty in range((H + th - 1) // th):
+                for tx in range((W + tw - 1) // tw):
+                    for a in range(ty * th, min(H, (ty + 1) * th)):
+                        for bb in range(tx * tw, min(W, (tx + 1) * tw)):
+                            out.append(base + a * W + bb)
+            base += H * W
+    return out
+
+
+def test_graph_replay_matches_eager(G):
+    import torch
+    cases = three_subjects()
+    lr = dict(lr_mu=5e-3, lr_ls=5e-3, lr_q=2e-3, lr_c=1e-3, lr_rot=2e-3, lr_trans=5e-2)
+    runs = []
+    for use_graph in (False, True):
+        stream = torch.cuda.Stream()
+        b, ctx = batched_ctx(G, cases, stream=stream.cuda_stream, fixed_capacity=1, cap_records=200000,
+                             cap_keys=800000, seed=7)
+        G.gsvr_set_frozen(ctx.ctx, np.array([1] + [0] * (ctx.M - 1), np.uint8))
+        ctx.forward()
+        G.gsvr_sync_status(ctx.ctx)
+        if use_graph:
+            G.gsvr_set_step(ctx.ctx, 0)
+            G.gsvr_graph_capture(ctx.ctx, 150, lr=lr, step_every=3, gamma=0.5)
+            G.gsvr_graph_launch(ctx.ctx, 7)
+        else:
+            for k in range(7):
+                G.gsvr_sample_pixels_subjects(ctx.ctx, 150, k)
+                ctx.forward()
+                ctx.backward()
+                G.gsvr_adam_step(ctx.ctx, k + 1, lr=lr, step_every=3, gamma=0.5)
+        G.gsvr_sync_status(ctx.ctx)
+        stream.synchronize()
+        runs.append(ctx.theta.cpu().numpy().astype(np.float64))
+        ctx.close()
+    e, g = runs
+    assert np.abs(e - g).max() <= 1e-4 * np.abs(e).max()
