@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fetal", choices=["fetal", "tiny"])
     ap.add_argument("--stacks", type=int, default=0, help="keep only the first n stacks (profiling captures)")
-    ap.add_argument("--tile", default="12x12")
+    ap.add_argument("--tile", default="auto",
+                    help="HxW tile (no tuning) or 'auto': the library's autotuner picks the launch shape")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -239,21 +240,45 @@ def main():
     torch.cuda.set_device(local)
     dev = local
     stream = torch.cuda.Stream(device=dev)
-    th_, tw_ = (int(v) for v in args.tile.split("x"))
     case, desc = workload(args.workload, rank, args.stacks)
     n_s = min(case["n_sample"], int(case["mask"].sum()))
     sampled = args.workload == "fetal"
 
+    def probe_counts(shape):
+        probe = gsvr.Context(case, device=dev, stream=stream.cuda_stream)
+        gsvr.gsvr_set_tiling(probe.ctx, shape)
+        if sampled:
+            gsvr.gsvr_sample_pixels(probe.ctx, n_s, 0)
+        probe.forward()
+        st = probe.stats()
+        probe.close()
+        return st
+
+    # launch shape: fixed, or the autotuner's pick (timed fwd+bwd iterations of
+    # every candidate on a fixed-capacity context, before and outside the timed region)
+    tuning = None
+    if args.tile == "auto":
+        st0 = probe_counts(gsvr.tiling(12, 12))
+        tune = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=12, tile_w=12, fixed_capacity=1,
+                            cap_records=int(st0["n_records"] * 1.5) + 4096, cap_keys=int(st0["n_keys"] * 4) + 4096)
+        best, res = gsvr.gsvr_autotune(tune.ctx, None, n_per_subject=n_s if sampled else 0, iterations=10)
+        tune.close()
+        shape = res[best]
+        tuning = {"candidates": len(res), "ms_per_iter_best": round(res[best].ms, 4),
+                  "ms_per_iter_12x12": round(res[2].ms, 4),
+                  "timed": ["%dx%d px%d fwd%d bwd%d order%d: %.4f ms" % (r.tile_h, r.tile_w, r.fwd_px_per_thread,
+                                                                          r.fwd_blocks_per_sm, r.bwd_blocks_per_sm,
+                                                                          r.queue_order, r.ms) for r in res]}
+    else:
+        th_, tw_ = (int(v) for v in args.tile.split("x"))
+        shape = gsvr.tiling(th_, tw_)
+    shape_d = {k: v for k, v in shape.as_dict().items() if k != "ms"}
     # capacities from one probe forward, then a fixed-capacity context (no host sync per step)
-    probe = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=th_, tile_w=tw_)
-    if sampled:
-        gsvr.gsvr_sample_pixels(probe.ctx, n_s, 0)
-    probe.forward()
-    st0 = probe.stats()
-    probe.close()
-    ctx = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=th_, tile_w=tw_, fixed_capacity=1,
-                       cap_records=int(st0["n_records"] * 1.5) + 4096, cap_keys=int(st0["n_keys"] * 1.5) + 4096,
-                       timing=1, seed=1234 + rank)
+    st0 = probe_counts(shape)
+    ctx = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=shape.tile_h, tile_w=shape.tile_w,
+                       fixed_capacity=1, cap_records=int(st0["n_records"] * 1.5) + 4096,
+                       cap_keys=int(st0["n_keys"] * 1.5) + 4096, timing=1, seed=1234 + rank)
+    gsvr.gsvr_set_tiling(ctx.ctx, shape)
     M = ctx.M
     gsvr.gsvr_set_frozen(ctx.ctx, np.array([1 if i == M // 6 else 0 for i in range(M)], np.uint8))
 
@@ -372,7 +397,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": desc, "tile": args.tile, "parallelism": "replicas" if ws > 1 else "single",
+                "config": {"workload": desc, "tile": "%dx%d" % (shape.tile_h, shape.tile_w), "launch_shape": shape_d,
+                           "autotune": tuning, "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (records + keys + tile records ~%.0f MB per step)" %
                                  ((stats["n_records"] * 44 + stats["n_keys"] * 108) / 1e6)},
                 "px_per_s": px_total / (ms_max / 1e3),

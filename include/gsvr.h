@@ -226,6 +226,55 @@ gsvr_status gsvr_graph_capture(gsvr_ctx *ctx, int64_t n_per_subject, const gsvr_
 gsvr_status gsvr_graph_launch(gsvr_ctx *ctx, int32_t iterations);
 gsvr_status gsvr_set_step(gsvr_ctx *ctx, int64_t step);
 
+/* ---- Launch shape and autotuner ----
+ * How the tile stage cuts the work; it does not change what is computed (the
+ * Mahalanobis cut and the records are exact per pixel; only the rounding order
+ * of the per-pixel sums follows the tiles).  The paper fixes no launch shape
+ * (its Sec. 2.5 kernels process fixed batches of points); these are the
+ * B300 kernels' knobs.
+ *   tile_h, tile_w      pixel tile (each in [4, 32]; 0 -> 16), with
+ *                       tile_h * ceil(tile_w / px) <= 256 for the forward's px
+ *   fwd_px_per_thread   forward pixels per thread along a tile row: 1, 2 or 4
+ *                       (0 -> 4 when tile_w >= 12, else 2)
+ *   fwd_blocks_per_sm,
+ *   bwd_blocks_per_sm   CTAs per SM of the persistent evaluation kernels
+ *                       (0 -> as many as fit; larger requests are clamped;
+                       -1 -> one CTA per work item, scheduled by the hardware)
+ *   queue_order         0: work items in tile order; 1: longest items first
+ *                       (one extra 9-bit radix sort of the items per forward)
+ *   ms                  written by gsvr_autotune: measured ms per iteration,
+ *                       -1 for a shape that was invalid or overflowed a fixed
+ *                       capacity */
+typedef struct gsvr_tiling {
+    int32_t tile_h, tile_w;
+    int32_t fwd_px_per_thread;
+    int32_t fwd_blocks_per_sm, bwd_blocks_per_sm;
+    int32_t queue_order;
+    float ms;
+} gsvr_tiling;
+
+/* Apply a launch shape.  A new tile shape rebuilds every tile-ordered table
+ * (pixel tiles, masked-pixel order, subject ranges) from the stored stack
+ * descriptions, observations and mask; parameters, Adam moments, subjects and
+ * frozen slices are kept; the pixel sample becomes every masked pixel and a
+ * captured graph is dropped.  Synchronises.  GSVR_ERR_INVALID_ARG for a shape
+ * outside the limits above (the context is then unchanged). */
+gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
+gsvr_status gsvr_get_tiling(gsvr_ctx *ctx, gsvr_tiling *out);
+
+/* The built-in candidate shapes: writes min(cap, total) of them to out and the
+ * total count to *n (out may be NULL when cap = 0). */
+gsvr_status gsvr_tune_space_default(gsvr_tiling *out, int32_t cap, int32_t *n);
+
+/* Time each candidate (`iterations` timed iterations of device sample of
+ * n_per_subject pixels per subject -- 0 keeps every masked pixel -- forward and
+ * backward, after one untimed iteration; CUDA events on the context's stream),
+ * write cand[c].ms, apply the fastest and return its index in *best (may be
+ * NULL).  Parameters are not updated.  Afterwards the context's pixel sample is
+ * unspecified: draw one before the next forward.  Synchronises. */
+gsvr_status gsvr_autotune(gsvr_ctx *ctx, gsvr_tiling *cand, int32_t n_cand, int64_t n_per_subject,
+                          int32_t iterations, int32_t *best);
+
 /* End to end from host buffers: copy theta (11N + 6M floats, host) and the
  * pixel sample (n int32 global indices, host; n < 0 = every masked pixel) to
  * the device, run forward and backward, copy dL/dtheta (host, 11N + 6M floats)

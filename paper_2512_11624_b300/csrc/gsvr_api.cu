@@ -54,6 +54,8 @@ struct gsvr_ctx {
     std::string err;
     float rc2 = 0.f;
     int tile_w = 16, tile_h = 16;
+    int fwd_pxr_req = 0, fwd_bps = 0, bwd_bps = 0, queue_order = 0;  // launch shape (gsvr_set_tiling)
+    std::vector<gsvr_stack_desc> h_stack_desc;
 
     // geometry
     int n_stacks = 0, M = 0, n_tiles = 0, sort_bits = 1;
@@ -90,6 +92,8 @@ struct gsvr_ctx {
     DBuf<int> d_hist, d_scan_bsum;
     DBuf<float4> d_mom;
     DBuf<int> d_item_cnt, d_item_first, d_item_tile;
+    DBuf<uint32_t> d_item_key, d_item_key_sorted, d_item_order, d_item_key_alt, d_item_val_alt;
+    DBuf<int> d_item_hist;
     DBuf<float> d_part;
     int cap_rec = 0, cap_keys = 0, cap_items = 0, grid_items = 0;
     int last_n_rec = 0, last_n_keys = 0;
@@ -180,18 +184,10 @@ bool finite_all(const float *v, int n) {
     return true;
 }
 
-// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
-// out(seed, ctr) = mix(seed + (ctr + 1) * golden gamma).
-uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
-    uint64_t z = seed + (ctr + 1ULL) * 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
 size_t scan_scratch_blocks(gsvr_ctx *ctx) {
     size_t n = std::max<size_t>({(size_t)ctx->N + 1, (size_t)ctx->P + 1, (size_t)ctx->cap_rec + 1,
-                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_keys) + 1});
+                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_keys) + 1,
+                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_items) + 1});
     return (n + kScanTile - 1) / kScanTile + 2;
 }
 
@@ -244,6 +240,16 @@ gsvr_status ensure_item_capacity(gsvr_ctx *ctx) {
         CK(ctx->d_part.ensure((size_t)want * ctx->tile_w * ctx->tile_h));
         ctx->cap_items = (int)want;
     }
+    if (ctx->queue_order && ctx->d_item_order.n < (size_t)ctx->cap_items) {
+        const size_t n = (size_t)ctx->cap_items;
+        CK(ctx->d_item_key.ensure(n));
+        CK(ctx->d_item_key_sorted.ensure(n));
+        CK(ctx->d_item_order.ensure(n));
+        CK(ctx->d_item_key_alt.ensure(n));
+        CK(ctx->d_item_val_alt.ensure(n));
+        CK(ctx->d_item_hist.ensure((size_t)256 * sort_blocks(ctx->cap_items) + 1));
+    }
+    CK(ensure_scan_scratch(ctx));
     return GSVR_OK;
 }
 
@@ -269,8 +275,12 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.item_first = ctx->d_item_first.p;
     e.n_items = &ctx->d_counters.p->n_items;
     e.part = ctx->d_part.p;
-    e.subj_cnt = ctx->d_subj_cnt.p;
+    e.subj_cnt = ctx->n_subj > 1 ? ctx->d_subj_cnt.p : nullptr;
     e.cap_items = std::min(grid_items, ctx->cap_items);
+    e.item_order = ctx->queue_order ? ctx->d_item_order.p : nullptr;
+    e.fwd_pxr = ctx->fwd_pxr_req;
+    e.fwd_bps = ctx->fwd_bps;
+    e.bwd_bps = ctx->bwd_bps;
     e.tile_px = ctx->tile_w * ctx->tile_h;
     e.tile_w = ctx->tile_w;
     e.tile_h = ctx->tile_h;
@@ -348,8 +358,9 @@ gsvr_status finish_sample(gsvr_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->d_tile_px_end.p, 0, sizeof(int) * ctx->n_tiles, st));
     launch_tile_px_ranges(ctx->d_sampled.p, &ctx->d_counters.p->n_sampled, (int)ctx->P, ctx->d_pix_tile.p,
                           ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, st);
-    launch_subject_counts(ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_subj_tile_first.p, ctx->n_subj,
-                          ctx->d_subj_cnt.p, st);
+    if (ctx->n_subj > 1)  // one subject: the weights read the total sample count
+        launch_subject_counts(ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_subj_tile_first.p, ctx->n_subj,
+                              ctx->d_subj_cnt.p, st);
     CK(cudaGetLastError());
     ctx->have_sample = true;
     ctx->fwd_valid = false;
@@ -576,6 +587,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     ctx->sort_bits = bits;
     ctx->h_slices = sl;
     ctx->h_static = ss;
+    ctx->h_stack_desc.assign(stacks, stacks + n_stacks);
     ctx->h_tile_sorted_pix = tsp;
     ctx->h_tile_tpos_first = tile_tpos_first;
     ctx->h_stack_nslices.assign(n_stacks, 0);
@@ -1030,6 +1042,12 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
                       scan_scratch(ctx), st));
     launch_items(nullptr, nullptr, nullptr, nullptr, ctx->n_tiles, nullptr, ctx->d_item_first.p, ctx->d_item_tile.p,
                  ctx->cap_items, 1, st);
+    if (ctx->queue_order) {
+        SortScratch is{ctx->d_item_key_alt.p, ctx->d_item_val_alt.p, ctx->d_item_hist.p, scan_scratch(ctx)};
+        launch_item_order(ctx->d_item_tile.p, ctx->d_item_first.p, ctx->d_tile_rec_start.p, ctx->d_tile_rec_end.p,
+                          &cnt->n_items, ctx->cap_items, ctx->d_item_key.p, ctx->d_item_key_sorted.p,
+                          ctx->d_item_order.p, is, st);
+    }
     stage_end(ctx, GSVR_STAGE_BIN);
     ctx->grid_items = ctx->n_tiles + n_keys_max / kItemRecs + 2;
     EvalArgs e = eval_args(ctx, ctx->grid_items);
@@ -1049,7 +1067,6 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     DeviceGuard g(ctx->device);
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->N, M = ctx->M;
-    Counters *cnt = ctx->d_counters.p;
     EvalArgs e = eval_args(ctx, ctx->grid_items);
     stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
     launch_backward(e, st);
@@ -1092,7 +1109,8 @@ gsvr_status adam_launch(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step, c
     const float lr[6] = {cfg->lr_mu, cfg->lr_ls, cfg->lr_q, cfg->lr_c, cfg->lr_rot, cfg->lr_trans};
     stage_begin(ctx, GSVR_STAGE_ADAM);
     launch_adam(ctx->d_theta.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, (int)ctx->N, ctx->M, lr, b1, b2, eps,
-                cfg->step_every, gamma, step, d_step, ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
+                cfg->step_every, gamma, step, d_step, ctx->d_counters.p->adam_scal,
+                ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
     stage_end(ctx, GSVR_STAGE_ADAM);
     CK(cudaGetLastError());
     ctx->fwd_valid = false;
@@ -1308,6 +1326,186 @@ gsvr_status gsvr_get_stats(gsvr_ctx *ctx, gsvr_stats *out) {
     out->tile_px_max = (int64_t)ctx->tile_w * ctx->tile_h;
     out->cap_records = ctx->cap_rec;
     out->cap_keys = ctx->cap_keys;
+    return GSVR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- launch shape
+namespace {
+gsvr_status check_tiling(gsvr_ctx *ctx, const gsvr_tiling &t) {
+    const int th = t.tile_h ? t.tile_h : 16, tw = t.tile_w ? t.tile_w : 16;
+    if (th < 4 || th > 32 || tw < 4 || tw > 32)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "tile sides must lie in [4, 32]");
+    if (t.fwd_px_per_thread != 0 && t.fwd_px_per_thread != 1 && t.fwd_px_per_thread != 2 &&
+        t.fwd_px_per_thread != 4)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "fwd_px_per_thread must be 0, 1, 2 or 4");
+    const int pxr = fwd_pxr(tw, t.fwd_px_per_thread);
+    if (th * ((tw + pxr - 1) / pxr) > 256)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "tile_h * ceil(tile_w / px_per_thread) must be <= 256");
+    if (t.fwd_blocks_per_sm < -1 || t.fwd_blocks_per_sm > 64 || t.bwd_blocks_per_sm < -1 || t.bwd_blocks_per_sm > 64)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "blocks per SM must lie in [-1, 64]");
+    if (t.queue_order != 0 && t.queue_order != 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "queue_order must be 0 or 1");
+    return GSVR_OK;
+}
+
+void drop_graph(gsvr_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+}
+
+gsvr_status tune_iteration(gsvr_ctx *ctx, int64_t n_per_subject, int step) {
+    gsvr_status s = GSVR_OK;
+    if (n_per_subject > 0)
+        s = ctx->n_subj > 1 ? gsvr_sample_pixels_subjects(ctx, n_per_subject, (uint64_t)step)
+                            : gsvr_sample_pixels(ctx, std::min<int64_t>(n_per_subject, ctx->n_mask), (uint64_t)step);
+    if (!s) s = gsvr_forward(ctx);
+    if (!s) s = gsvr_backward(ctx);
+    return s;
+}
+}  // namespace
+
+extern "C" {
+
+gsvr_status gsvr_get_tiling(gsvr_ctx *ctx, gsvr_tiling *out) {
+    if (check_ctx(ctx) || !out) return GSVR_ERR_INVALID_ARG;
+    out->tile_h = ctx->tile_h;
+    out->tile_w = ctx->tile_w;
+    out->fwd_px_per_thread = ctx->fwd_pxr_req;
+    out->fwd_blocks_per_sm = ctx->fwd_bps;
+    out->bwd_blocks_per_sm = ctx->bwd_bps;
+    out->queue_order = ctx->queue_order;
+    out->ms = 0.f;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t) {
+    if (check_ctx(ctx) || !t) return GSVR_ERR_INVALID_ARG;
+    if (gsvr_status s = check_tiling(ctx, *t)) return s;
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_tiling during graph capture");
+    DeviceGuard g(ctx->device);
+    const int th = t->tile_h ? t->tile_h : 16, tw = t->tile_w ? t->tile_w : 16;
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    ctx->fwd_pxr_req = t->fwd_px_per_thread;
+    ctx->fwd_bps = t->fwd_blocks_per_sm;
+    ctx->bwd_bps = t->bwd_blocks_per_sm;
+    ctx->queue_order = t->queue_order;
+    ctx->fwd_valid = false;
+    if (th == ctx->tile_h && tw == ctx->tile_w) return ctx->have_gauss ? ensure_item_capacity(ctx) : GSVR_OK;
+    ctx->tile_h = th;
+    ctx->tile_w = tw;
+    if (!ctx->have_stacks) return GSVR_OK;
+    // Everything in tile order is rebuilt: the stacks, then the observations and
+    // mask (kept on the device), the subjects and the frozen slices.
+    const std::vector<gsvr_stack_desc> desc = ctx->h_stack_desc;
+    const bool had_obs = ctx->have_obs;
+    const int n_subj = ctx->n_subj, M = ctx->M;
+    const std::vector<int> stack_subject = ctx->h_stack_subject;
+    std::vector<int64_t> gauss_count;
+    for (int k = 0; k < n_subj && k + 1 < (int)ctx->h_subj_gauss_first.size(); ++k)
+        gauss_count.push_back(ctx->h_subj_gauss_first[k + 1] - ctx->h_subj_gauss_first[k]);
+    std::vector<uint8_t> frozen((size_t)M, 0);
+    const bool any_frozen = ctx->any_frozen;
+    if (any_frozen) CK(cudaMemcpy(frozen.data(), ctx->d_frozen.p, (size_t)M, cudaMemcpyDeviceToHost));
+    DBuf<float> I;
+    DBuf<uint8_t> mask;
+    if (had_obs) {
+        CK(I.ensure((size_t)ctx->P));
+        CK(mask.ensure((size_t)ctx->P));
+        CK(cudaMemcpy(I.p, ctx->d_I.p, sizeof(float) * ctx->P, cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(mask.p, ctx->d_mask.p, (size_t)ctx->P, cudaMemcpyDeviceToDevice));
+    }
+    gsvr_status s = gsvr_set_stacks(ctx, (int32_t)desc.size(), desc.data());
+    if (!s && had_obs) s = gsvr_set_observations(ctx, I.p, mask.p, GSVR_MEM_DEVICE);
+    if (!s && had_obs && ctx->have_gauss && n_subj > 1 && (int)gauss_count.size() == n_subj)
+        s = gsvr_set_subjects(ctx, n_subj, stack_subject.data(), gauss_count.data());
+    if (!s && any_frozen) s = gsvr_set_frozen(ctx, frozen.data());
+    if (!s && ctx->have_gauss) s = ensure_item_capacity(ctx);
+    if (!s) CK(cudaStreamSynchronize(ctx->stream));
+    return s;
+}
+
+gsvr_status gsvr_tune_space_default(gsvr_tiling *out, int32_t cap, int32_t *n) {
+    if (!n || cap < 0 || (cap > 0 && !out)) return GSVR_ERR_INVALID_ARG;
+    // (tile_h, tile_w, fwd px per thread, fwd CTAs/SM, bwd CTAs/SM, queue order)
+    static const int32_t space[][6] = {
+        {8, 8, 0, 0, 0, 0},    {8, 8, 1, 0, 0, 0},    {12, 12, 0, 0, 0, 0},  {12, 12, 0, 0, 0, 1},
+        {12, 12, 2, 0, 0, 0},  {12, 12, 0, 4, 4, 0},  {12, 12, 0, 0, -1, 0}, {12, 12, 0, -1, -1, 0},
+        {16, 16, 0, 0, 0, 0},  {16, 16, 0, 0, 0, 1},  {16, 16, 2, 0, 0, 0},  {16, 16, 0, 0, -1, 0},
+        {8, 16, 0, 0, 0, 0},   {16, 8, 0, 0, 0, 0},   {8, 32, 0, 0, 0, 0},   {32, 8, 0, 0, 0, 0},
+        {12, 16, 0, 0, 0, 0},  {10, 10, 0, 0, 0, 0},  {10, 12, 0, 0, -1, 0}, {12, 8, 0, 0, -1, 0}};
+    const int32_t total = (int32_t)(sizeof(space) / sizeof(space[0]));
+    *n = total;
+    for (int32_t k = 0; k < std::min(cap, total); ++k) {
+        gsvr_tiling &t = out[k];
+        t.tile_h = space[k][0];
+        t.tile_w = space[k][1];
+        t.fwd_px_per_thread = space[k][2];
+        t.fwd_blocks_per_sm = space[k][3];
+        t.bwd_blocks_per_sm = space[k][4];
+        t.queue_order = space[k][5];
+        t.ms = 0.f;
+    }
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_autotune(gsvr_ctx *ctx, gsvr_tiling *cand, int32_t n_cand, int64_t n_per_subject,
+                          int32_t iterations, int32_t *best) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!cand || n_cand < 1 || iterations < 1 || iterations > 1000 || n_per_subject < 0)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "need candidates, 1..1000 iterations, n_per_subject >= 0");
+    if (!ctx->have_gauss || !ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "set stacks, observations, Gaussians first");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_autotune during graph capture");
+    DeviceGuard g(ctx->device);
+    const int32_t timing = ctx->cfg.timing;
+    ctx->cfg.timing = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        ctx->cfg.timing = timing;
+        return fail(ctx, GSVR_ERR_CUDA, "cudaEventCreate failed");
+    }
+    int bi = -1;
+    gsvr_status hard = GSVR_OK;
+    for (int32_t c = 0; c < n_cand && !hard; ++c) {
+        cand[c].ms = -1.f;
+        gsvr_status s = gsvr_set_tiling(ctx, &cand[c]);
+        if (s == GSVR_ERR_INVALID_ARG) continue;  // not a valid launch shape: skipped
+        if (s) {
+            hard = s;
+            break;
+        }
+        for (int it = 0; it <= iterations && !s; ++it) {  // iteration 0 warms up
+            if (it == 1) cudaEventRecord(e0, ctx->stream);
+            s = tune_iteration(ctx, n_per_subject, it);
+        }
+        cudaEventRecord(e1, ctx->stream);
+        const gsvr_status ss = gsvr_sync_status(ctx);  // capacity / timeout flags mark the shape unusable
+        if (s == GSVR_ERR_CAPACITY || ss == GSVR_ERR_CAPACITY) continue;
+        if (s || ss) {
+            hard = s ? s : ss;
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            hard = fail(ctx, GSVR_ERR_CUDA, "event timing failed");
+            break;
+        }
+        cand[c].ms = ms / (float)iterations;
+        if (bi < 0 || cand[c].ms < cand[bi].ms) bi = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->cfg.timing = timing;
+    if (hard) return hard;
+    if (bi < 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "no candidate launch shape ran");
+    if (best) *best = bi;
+    gsvr_status s = gsvr_set_tiling(ctx, &cand[bi]);
+    if (s) return s;
     return GSVR_OK;
 }
 

@@ -60,6 +60,7 @@ struct Counters {
     unsigned long long pairs;  // pixel x record pairs visited by one evaluation pass
     unsigned long long step;   // device iteration counter (graph replay)
     int work_fwd, work_bwd;    // work-queue heads of the persistent evaluation kernels
+    float adam_scal[4];        // Adam 1 / bias corrections and StepLR factor of a device-counted step
 };
 
 // A (slice, Gaussian) record: the 3D Gaussian conditioned on the slice plane

@@ -27,6 +27,8 @@
 //   adam         fused, per-group learning rates
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <atomic>
 
@@ -577,6 +579,20 @@ __global__ void k_item_fill(const int *__restrict__ first, int n_tiles, int *__r
     for (int i = first[t]; i < e; ++i) item_tile[i] = t;
 }
 
+// Work-queue order key of an item: kItemRecs - its record count, so that a
+// stable ascending sort hands out the longest items first (longest processing
+// time first bounds the persistent kernels' tail by the shortest items).
+__global__ void k_item_key(const int *__restrict__ item_tile, const int *__restrict__ item_first,
+                           const int *__restrict__ trs, const int *__restrict__ tre, const int *__restrict__ n_items,
+                           int cap, uint32_t *__restrict__ key) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(*n_items, cap)) return;
+    const int t = item_tile[i];
+    const int rs = trs[t] + (i - item_first[t]) * kItemRecs;
+    const int nrec = max(0, min(kItemRecs, tre[t] - rs));
+    key[i] = (uint32_t)(kItemRecs - nrec);
+}
+
 // ----------------------------------------------------------------- forward
 // Tile pixels are addressed densely, (row, col) inside the tile; pixels that are
 // not in the sample are evaluated but never read back.
@@ -628,8 +644,8 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
         __syncthreads();  // previous item's buffers are free
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_fwd, 1);
         __syncthreads();
-        const int i = s_item;
-        if (i >= n_items) break;
+        if (s_item >= n_items) break;
+        const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
         const int t = a.item_tile[i];
         const int c = i - a.item_first[t];
         const int rs = a.tile_rec_start[t] + c * kItemRecs;
@@ -779,8 +795,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
         __syncthreads();  // previous item's r_bar tile is free
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
         __syncthreads();
-        const int i = s_item;
-        if (i >= n_items) break;
+        if (s_item >= n_items) break;
+        const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
         const int t = a.item_tile[i];
         const int c = i - a.item_first[t];
         const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
@@ -1144,18 +1160,23 @@ __global__ void k_pose_grad(const double *__restrict__ acc, const SliceStatic *_
 
 // Adam with StepLR: lr x gamma^((t - 1) / step_every); the 1-based step t from
 // the argument or from the device iteration counter (graph replay).
+// Adam's per-step scalars (1 / bias corrections, StepLR factor) for a step
+// read from the device counter (graph replay), in float64 by one thread.
+__global__ void k_adam_scalars(float b1, float b2, int step_every, float gamma, const unsigned long long *d_step,
+                               float *scal) {
+    const long long t = (long long)(*d_step) + 1;
+    scal[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    scal[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+    scal[2] = step_every > 0 ? (float)pow((double)gamma, (double)((t - 1) / step_every)) : 1.0f;
+}
+
 __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int N, int M, float lr0, float lr1, float lr2, float lr3, float lr4,
-                       float lr5, float b1, float b2, float eps, int step_every, float gamma, long long t_host,
-                       const unsigned long long *d_step, const uint8_t *__restrict__ frozen) {
-    __shared__ float s_ibc1, s_ibc2, s_scale;
-    if (threadIdx.x == 0) {
-        const long long t = d_step ? (long long)(*d_step) + 1 : t_host;
-        s_ibc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
-        s_ibc2 = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
-        s_scale = step_every > 0 ? (float)pow((double)gamma, (double)((t - 1) / step_every)) : 1.0f;
-    }
-    __syncthreads();
+                       float lr5, float b1, float b2, float eps, float ibc1_h, float ibc2_h, float scale_h,
+                       const float *__restrict__ d_scal, const uint8_t *__restrict__ frozen) {
+    const float s_ibc1 = d_scal ? d_scal[0] : ibc1_h;
+    const float s_ibc2 = d_scal ? d_scal[1] : ibc2_h;
+    const float s_scale = d_scal ? d_scal[2] : scale_h;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = 11LL * N + 6LL * M;
     if (e >= n) return;
@@ -1234,20 +1255,37 @@ void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre
     else k_item_fill<<<cdiv(n_tiles, 256), 256, 0, st>>>(first, n_tiles, item_tile, cap_items);
     counted();
 }
+void launch_item_order(const int *item_tile, const int *item_first, const int *trs, const int *tre,
+                       const int *n_items, int cap_items, uint32_t *key, uint32_t *key_sorted, uint32_t *order,
+                       const SortScratch &ss, cudaStream_t st) {
+    if (cap_items <= 0) return;
+    k_item_key<<<cdiv(cap_items, 256), 256, 0, st>>>(item_tile, item_first, trs, tre, n_items, cap_items, key);
+    counted();
+    int bits = 1;
+    while ((1 << bits) <= kItemRecs) ++bits;
+    radix_sort_pairs(key, nullptr, key_sorted, order, n_items, cap_items, bits, ss, st);
+}
+// Forward pixels per thread: the requested run (1, 2 or 4), else 4 for tiles
+// at least 12 wide and 2 below.
+int fwd_pxr(int tile_w, int req) { return req == 1 || req == 2 || req == 4 ? req : (tile_w >= 12 ? 4 : 2); }
 // Forward CTA shape: groups of tile_h x ceil(tile_w / PXR) threads, as many
 // groups as fit in 128 threads (at least one).
-int eval_blocks_per_sm(int tile_w, int tile_h, bool backward) {
+int fwd_threads(int tile_w, int tile_h, int pxr) {
+    const int tpg = tile_h * ((tile_w + pxr - 1) / pxr);
+    const int G = std::max(1, 128 / tpg);
+    return round_warp(G * tpg);
+}
+int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
     if (backward) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kThreads,
                                                       (size_t)tile_w * tile_h * sizeof(float));
     } else {
-        const int pxr = tile_w >= 12 ? 4 : 2;
-        const int tpg = tile_h * ((tile_w + pxr - 1) / pxr);
-        const int G = std::max(1, 128 / tpg);
-        const int nt = round_warp(G * tpg);
+        const int pxr = fwd_pxr(tile_w, pxr_req);
+        const int nt = fwd_threads(tile_w, tile_h, pxr);
         if (pxr == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 4>, nt, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 2>, nt, 0);
+        else if (pxr == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 2>, nt, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 1>, nt, 0);
     }
     cudaGetLastError();
     return std::max(nb, 1);
@@ -1262,23 +1300,26 @@ static int n_sms() {
     }
     return n;
 }
-// Persistent grid: every resident CTA of the GPU (or persistent_blocks), never
-// more CTAs than items.
+// Persistent grid: n_SM x the requested CTAs per SM (at most as many as fit;
+// all that fit when not requested), never more CTAs than items.  A request of
+// -1 launches one CTA per item slot instead (the hardware schedules the CTAs;
+// each takes one item from the queue, the surplus ones find it empty).
 static int eval_grid(const EvalArgs &a, bool backward) {
-    const int g = a.persistent_blocks > 0 ? a.persistent_blocks
-                                          : n_sms() * eval_blocks_per_sm(a.tile_w, a.tile_h, backward);
+    const int req = backward ? a.bwd_bps : a.fwd_bps;
+    if (req < 0) return std::max(1, a.cap_items);
+    const int fit = eval_blocks_per_sm(a.tile_w, a.tile_h, backward, a.fwd_pxr);
+    const int g = n_sms() * (req > 0 ? std::min(req, fit) : fit);
     return std::max(1, std::min(g, a.cap_items));
 }
 template <bool COUNT>
 static void fwd_items(const EvalArgs &a, cudaStream_t st) {
-    const int pxr = a.tile_w >= 12 ? 4 : 2;
-    const int tpg = a.tile_h * ((a.tile_w + pxr - 1) / pxr);
-    const int G = std::max(1, 128 / tpg);
-    const int nt = round_warp(G * tpg);
+    const int pxr = fwd_pxr(a.tile_w, a.fwd_pxr);
+    const int nt = fwd_threads(a.tile_w, a.tile_h, pxr);
     cudaMemsetAsync(&a.counters->work_fwd, 0, sizeof(int), st);
     const int grid = eval_grid(a, false);
     if (pxr == 4) k_fwd_items<COUNT, 4><<<grid, nt, 0, st>>>(a);
-    else k_fwd_items<COUNT, 2><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 2) k_fwd_items<COUNT, 2><<<grid, nt, 0, st>>>(a);
+    else k_fwd_items<COUNT, 1><<<grid, nt, 0, st>>>(a);
     counted();
 }
 void launch_forward(const EvalArgs &a, cudaStream_t st) {
@@ -1331,11 +1372,20 @@ void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float
 }
 void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
                  float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
-                 const uint8_t *frozen, cudaStream_t st) {
+                 float *d_scal, const uint8_t *frozen, cudaStream_t st) {
     const int64_t n = 11LL * N + 6LL * M;
     if (n <= 0) return;
+    float h[3] = {1.f, 1.f, 1.f};
+    if (d_step) {
+        k_adam_scalars<<<1, 1, 0, st>>>(b1, b2, step_every, gamma, d_step, d_scal);
+        counted();
+    } else {
+        h[0] = (float)(1.0 / (1.0 - std::pow((double)b1, (double)t_host)));
+        h[1] = (float)(1.0 / (1.0 - std::pow((double)b2, (double)t_host)));
+        h[2] = step_every > 0 ? (float)std::pow((double)gamma, (double)((t_host - 1) / step_every)) : 1.0f;
+    }
     k_adam<<<cdiv(n, 256), 256, 0, st>>>(theta, grad, m, v, N, M, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], b1, b2,
-                                         eps, step_every, gamma, t_host, d_step, frozen);
+                                         eps, h[0], h[1], h[2], d_step ? d_scal : nullptr, frozen);
     counted();
 }
 void launch_advance_step(unsigned long long *d_step, cudaStream_t st) {

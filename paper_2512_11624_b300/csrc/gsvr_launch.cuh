@@ -65,7 +65,9 @@ struct EvalArgs {
     float *part;                      // per-item partial pixel sums (cap_items x tile_px)
     int cap_items;
     const int *subj_cnt;              // sampled pixels per subject (null: *n_sampled)
-    int persistent_blocks;            // grid of the persistent evaluation kernels (0: one block per item)
+    const uint32_t *item_order;       // work-queue order of the items (null: item index order)
+    int fwd_pxr;                      // forward pixels per thread, 1, 2 or 4 (0: by tile width)
+    int fwd_bps, bwd_bps;             // persistent CTAs per SM (0: as many as fit)
     int tile_px;                      // tile_w * tile_h
     int tile_w, tile_h;
     int n_tiles;
@@ -116,7 +118,13 @@ void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_fi
 void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first, int n_subj, int *cnt,
                            cudaStream_t st);
 // Occupancy of the evaluation kernels (blocks per SM) for the persistent grids.
-int eval_blocks_per_sm(int tile_w, int tile_h, bool backward);
+int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int fwd_pxr_req);
+int fwd_pxr(int tile_w, int req);
+int fwd_threads(int tile_w, int tile_h, int pxr);
+// Work-queue order: items sorted by descending record count (stable).
+void launch_item_order(const int *item_tile, const int *item_first, const int *trs, const int *tre,
+                       const int *n_items, int cap_items, uint32_t *key, uint32_t *key_sorted, uint32_t *order,
+                       const SortScratch &ss, cudaStream_t st);
 void launch_gauss_grad(const GradArgs &a, cudaStream_t st);
 void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
                       cudaStream_t st);
@@ -124,7 +132,7 @@ void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float
 // 1-based step t comes from `t_host` or, when d_step is non-null, from *d_step + 1.
 void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,
                  float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
-                 const uint8_t *frozen, cudaStream_t st);
+                 float *d_scal, const uint8_t *frozen, cudaStream_t st);
 void launch_advance_step(unsigned long long *d_step, cudaStream_t st);
 
 // Sampler: for subject k, out_first[k+1] - out_first[k] of its mask_count[k]

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgsvr.so")
 GSVR_OK = 0
 STATUS_NAMES = {0: "GSVR_OK", 1: "GSVR_ERR_INVALID_ARG", 2: "GSVR_ERR_CUDA", 3: "GSVR_ERR_CAPACITY",
                 4: "GSVR_ERR_NONFINITE", 5: "GSVR_ERR_TIMEOUT", 6: "GSVR_ERR_STATE", 7: "GSVR_ERR_NOMEM"}
+globals().update({v: k for k, v in STATUS_NAMES.items()})
 GSVR_MEM_HOST, GSVR_MEM_DEVICE = 0, 1
 GSVR_NORM_EXACT, GSVR_NORM_LITERAL = 0, 1
 
@@ -29,7 +30,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_step_host", "gsvr_get_sample", "gsvr_get_views", "gsvr_get_stats", "gsvr_sync_status",
            "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
-           "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step"]
+           "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
+           "gsvr_tune_space_default", "gsvr_autotune"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -60,6 +62,15 @@ class AdamCfg(C.Structure):
 class KernelTimes(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("calls", C.c_int64 * 8), ("pairs_evaluated", C.c_int64),
                 ("kernel_launches", C.c_int64)]
+
+
+class Tiling(C.Structure):
+    _fields_ = [("tile_h", C.c_int32), ("tile_w", C.c_int32), ("fwd_px_per_thread", C.c_int32),
+                ("fwd_blocks_per_sm", C.c_int32), ("bwd_blocks_per_sm", C.c_int32), ("queue_order", C.c_int32),
+                ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Views(C.Structure):
@@ -111,6 +122,10 @@ def _load():
         "gsvr_graph_capture": ([vp, i64, C.POINTER(AdamCfg)], C.c_int),
         "gsvr_graph_launch": ([vp, i32], C.c_int),
         "gsvr_set_step": ([vp, i64], C.c_int),
+        "gsvr_set_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
+        "gsvr_get_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
+        "gsvr_tune_space_default": ([C.POINTER(Tiling), i32, C.POINTER(i32)], C.c_int),
+        "gsvr_autotune": ([vp, C.POINTER(Tiling), i32, i64, i32, C.POINTER(i32)], C.c_int),
         "gsvr_forward_noalloc": ([C.c_int, vp, i32, C.POINTER(StackDesc), i64, vp, vp, vp, i64, C.c_float, i32, vp,
                                   vp, C.c_char_p, i32], C.c_int),
     }
@@ -290,6 +305,40 @@ def gsvr_graph_launch(ctx, iterations=1):
 
 def gsvr_set_step(ctx, step):
     return _check(ctx, lib.gsvr_set_step(ctx, int(step)))
+
+
+def tiling(tile_h=16, tile_w=16, fwd_px_per_thread=0, fwd_blocks_per_sm=0, bwd_blocks_per_sm=0, queue_order=0):
+    return Tiling(tile_h, tile_w, fwd_px_per_thread, fwd_blocks_per_sm, bwd_blocks_per_sm, queue_order, 0.0)
+
+
+def gsvr_set_tiling(ctx, t):
+    if isinstance(t, dict):
+        t = tiling(**{k: v for k, v in t.items() if k != "ms"})
+    return _check(ctx, lib.gsvr_set_tiling(ctx, C.byref(t)))
+
+
+def gsvr_get_tiling(ctx):
+    t = Tiling()
+    _check(ctx, lib.gsvr_get_tiling(ctx, C.byref(t)))
+    return t
+
+
+def gsvr_tune_space_default():
+    n = C.c_int32(0)
+    _check(None, lib.gsvr_tune_space_default(None, 0, C.byref(n)))
+    arr = (Tiling * n.value)()
+    _check(None, lib.gsvr_tune_space_default(arr, n.value, C.byref(n)))
+    return list(arr)
+
+
+def gsvr_autotune(ctx, candidates=None, n_per_subject=0, iterations=5):
+    """Time each launch shape (list of Tiling; default: the library's space) and
+    apply the fastest.  Returns (best index, candidates with .ms filled)."""
+    cands = list(candidates) if candidates is not None else gsvr_tune_space_default()
+    arr = (Tiling * len(cands))(*cands)
+    best = C.c_int32(-1)
+    _check(ctx, lib.gsvr_autotune(ctx, arr, len(cands), int(n_per_subject), int(iterations), C.byref(best)))
+    return best.value, list(arr)
 
 
 def gsvr_step_host(ctx, theta, idx, grad_out=None, loss_out=None):
