@@ -212,6 +212,13 @@ gsvr_status gsvr_sample_pixels_subjects(gsvr_ctx *ctx, int64_t n_per_subject, ui
  * subjects).  Synchronises. */
 gsvr_status gsvr_get_subject_losses(gsvr_ctx *ctx, double *out, int32_t n);
 
+/* Grow the record / key capacities to at least the given counts (never
+ * shrinks; contents are regenerated by the next forward).  In fixed-capacity
+ * mode this is how a caller makes room after a GSVR_ERR_CAPACITY or before the
+ * counts reach the capacity (gsvr_get_stats reports both).  A captured graph
+ * is dropped when a buffer moves.  Synchronises. */
+gsvr_status gsvr_reserve(gsvr_ctx *ctx, int64_t cap_records, int64_t cap_keys);
+
 /* ---- CUDA graph of one optimisation iteration ----
  * gsvr_graph_capture records, on the context's (non-default) stream: the
  * per-subject device sampler (n_per_subject < 0: keep the current sample),

@@ -769,6 +769,27 @@ gsvr_status gsvr_set_poses(gsvr_ctx *ctx, const float *pose, int32_t mem) {
     return GSVR_OK;
 }
 
+gsvr_status gsvr_reserve(gsvr_ctx *ctx, int64_t cap_records, int64_t cap_keys) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (cap_records < 0 || cap_keys < 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "negative capacity");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_reserve during graph capture");
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (cap_records > ctx->cap_rec || cap_keys > ctx->cap_keys) {
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
+        ctx->graph_exec = nullptr;
+        ctx->graph = nullptr;
+    }
+    gsvr_status s = ensure_rec_capacity(ctx, std::max<int64_t>(cap_records, ctx->cap_rec));
+    if (!s) s = ensure_key_capacity(ctx, std::max<int64_t>(cap_keys, ctx->cap_keys));
+    if (s) return s;
+    ctx->cfg.cap_records = std::max<int64_t>(ctx->cfg.cap_records, cap_records);
+    ctx->cfg.cap_keys = std::max<int64_t>(ctx->cfg.cap_keys, cap_keys);
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
 gsvr_status gsvr_set_frozen(gsvr_ctx *ctx, const uint8_t *frozen) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks first");
@@ -1089,7 +1110,12 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     a.norm_mode = ctx->cfg.norm_mode;
     a.grad = ctx->d_grad.p;
     a.pose_acc = ctx->d_pose_acc.p;
-    a.use_smem = (size_t)M * 12 * sizeof(float) <= 48 * 1024 ? 1 : 0;
+    a.gauss_subject = ctx->multi_gauss ? ctx->d_gauss_subject.p : nullptr;
+    a.subj_slice_first = ctx->d_subj_slice_first.p;
+    a.smem_slices = 1536;  // at most 72 KB of shared float accumulators per block
+    a.h_gauss_first = ctx->h_subj_gauss_first.data();
+    a.h_slice_first = ctx->h_subj_slice_first.data();
+    a.n_subj = ctx->n_subj;
     a.cap_rec = ctx->cap_rec;
     a.cap_keys = ctx->cap_keys;
     launch_gauss_grad(a, st);

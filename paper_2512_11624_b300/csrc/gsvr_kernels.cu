@@ -918,7 +918,7 @@ __global__ void __launch_bounds__(256) k_subject_counts(const int *__restrict__ 
 // reduced with half-warp shuffles.
 __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const float4 g0, const float4 g1,
                                              const float mu[3], const float Sg[9], float gmu[3], float GS[6],
-                                             float &gc, float &glog, float *pacc) {
+                                             float &gc, float &glog, float *pacc, int w0) {
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     const int k_end = min(a.key_off[r + 1], a.cap_keys);
     for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
@@ -1014,26 +1014,38 @@ __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const flo
         }
         GR[9 + p] = -RGm[p];
     }
-    if (a.use_smem) {
-        for (int e = 0; e < 12; ++e) atomicAdd(&pacc[12 * i + e], GR[e]);
+    if (pacc) {
+        for (int e = 0; e < 12; ++e) atomicAdd(&pacc[12 * (i - w0) + e], GR[e]);
     } else {
         for (int e = 0; e < 12; ++e) atomicAdd(&a.pose_acc[12 * i + e], (double)GR[e]);
     }
 }
 
+// Each block takes a contiguous run of Gaussians (so of at most a few
+// subjects) and accumulates its slice-frame gradients for the slices of those
+// subjects in shared memory, flushed once with float64 atomics; a block whose
+// slice window does not fit falls back to float64 global atomics per record.
 __global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
-    extern __shared__ float pacc[];  // M x 12 (when use_smem)
-    if (a.use_smem) {
-        for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) pacc[e] = 0.f;
-        __syncthreads();
-    }
+    extern __shared__ float pacc_s[];  // window x 12
     const int N = a.N;
     const int lane = threadIdx.x & 31, hl = lane & 15;
     const int per_block = blockDim.x >> 4;
-    // grid-stride over groups of Gaussians; the block flushes its slice-frame sums once
-    for (int jb = blockIdx.x * per_block; jb < N; jb += gridDim.x * per_block) {
+    const int chunk = (((N + gridDim.x - 1) / gridDim.x) + per_block - 1) / per_block * per_block;
+    const int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
+    if (j0 >= j1) return;
+    int w0 = 0, w1 = a.M;
+    if (a.gauss_subject) {
+        w0 = a.subj_slice_first[a.gauss_subject[j0]];
+        w1 = a.subj_slice_first[a.gauss_subject[j1 - 1] + 1];
+    }
+    float *pacc = (w1 - w0) <= a.smem_slices ? pacc_s : nullptr;
+    if (pacc) {
+        for (int e = threadIdx.x; e < (w1 - w0) * 12; e += blockDim.x) pacc[e] = 0.f;
+        __syncthreads();
+    }
+    for (int jb = j0; jb < j1; jb += per_block) {
     const int j = jb + (threadIdx.x >> 4);
-    const bool valid = j < N;
+    const bool valid = j < j1;
     float gmu[3] = {0.f, 0.f, 0.f}, GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gc = 0.f, glog = 0.f;
     if (valid) {
@@ -1042,7 +1054,7 @@ __global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
         const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
         const int r_end = min(a.rec_off[j + 1], a.cap_rec);
         for (int r = a.rec_off[j] + hl; r < r_end; r += 16)
-            record_chain(a, r, g0, g1, mu, Sg, gmu, GS, gc, glog, pacc);
+            record_chain(a, r, g0, g1, mu, Sg, gmu, GS, gc, glog, pacc, w0);
     }
     float v[11] = {gmu[0], gmu[1], gmu[2], GS[0], GS[1], GS[2], GS[3], GS[4], GS[5], gc, glog};
 #pragma unroll
@@ -1097,11 +1109,11 @@ __global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
         g[10 * N + j] = v[9];
     }
     }
-    if (a.use_smem) {
+    if (pacc) {
         __syncthreads();
-        for (int e = threadIdx.x; e < a.M * 12; e += blockDim.x) {
+        for (int e = threadIdx.x; e < (w1 - w0) * 12; e += blockDim.x) {
             const float val = pacc[e];
-            if (val != 0.f) atomicAdd(&a.pose_acc[e], (double)val);
+            if (val != 0.f) atomicAdd(&a.pose_acc[12 * w0 + e], (double)val);
         }
     }
 }
@@ -1352,7 +1364,6 @@ void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first
 }
 void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
     if (a.N <= 0) return;
-    const size_t smem = a.use_smem ? (size_t)a.M * 12 * sizeof(float) : 0;
     static int n_sm = 0;
     if (!n_sm) {
         int dev = 0;
@@ -1360,8 +1371,27 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (n_sm <= 0) n_sm = 148;
     }
+    GradArgs g = a;
     const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 6);
-    k_gauss_grad<<<blocks, 256, smem, st>>>(a);
+    // the widest slice window of any block (the kernel's chunking, on the host)
+    int widest = a.M;
+    if (a.gauss_subject && a.h_gauss_first && a.h_slice_first && a.n_subj > 1) {
+        const int per_block = 256 >> 4;
+        const int chunk = ((a.N + blocks - 1) / blocks + per_block - 1) / per_block * per_block;
+        auto subject_of = [&](int64_t j) {
+            return (int)(std::upper_bound(a.h_gauss_first, a.h_gauss_first + a.n_subj + 1, j) - a.h_gauss_first) - 1;
+        };
+        widest = 0;
+        for (int b = 0; b < blocks; ++b) {
+            const int64_t j0 = (int64_t)b * chunk, j1 = std::min<int64_t>(a.N, j0 + chunk);
+            if (j0 >= j1) break;
+            widest = std::max(widest, a.h_slice_first[subject_of(j1 - 1) + 1] - a.h_slice_first[subject_of(j0)]);
+        }
+    }
+    g.smem_slices = std::min(widest, a.smem_slices);
+    const size_t smem = (size_t)g.smem_slices * 12 * sizeof(float);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_gauss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gauss_grad<<<blocks, 256, smem, st>>>(g);
     counted();
 }
 void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,

@@ -89,7 +89,14 @@ struct GradArgs {
     int norm_mode;
     float *grad;               // 11N + 6M
     double *pose_acc;          // M x 12: dL/dR_i (9), dL/dt_i (3)
-    int use_smem;
+    const int *gauss_subject;  // subject of each Gaussian (null: one subject)
+    const int *subj_slice_first;
+    int smem_slices;           // slice window that fits the shared accumulators (0: none)
+    // host copies of the subject tables (n_subj + 1 entries each), used by the
+    // launcher to size the shared window
+    const int64_t *h_gauss_first;
+    const int *h_slice_first;
+    int n_subj;
     int cap_rec, cap_keys;     // reads stay inside the buffers even after an overflow
 };
 

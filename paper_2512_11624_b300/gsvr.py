@@ -31,7 +31,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
-           "gsvr_tune_space_default", "gsvr_autotune"]
+           "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -123,6 +123,7 @@ def _load():
         "gsvr_graph_launch": ([vp, i32], C.c_int),
         "gsvr_set_step": ([vp, i64], C.c_int),
         "gsvr_set_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
+        "gsvr_reserve": ([vp, i64, i64], C.c_int),
         "gsvr_get_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
         "gsvr_tune_space_default": ([C.POINTER(Tiling), i32, C.POINTER(i32)], C.c_int),
         "gsvr_autotune": ([vp, C.POINTER(Tiling), i32, i64, i32, C.POINTER(i32)], C.c_int),
@@ -339,6 +340,10 @@ def gsvr_autotune(ctx, candidates=None, n_per_subject=0, iterations=5):
     best = C.c_int32(-1)
     _check(ctx, lib.gsvr_autotune(ctx, arr, len(cands), int(n_per_subject), int(iterations), C.byref(best)))
     return best.value, list(arr)
+
+
+def gsvr_reserve(ctx, cap_records, cap_keys):
+    return _check(ctx, lib.gsvr_reserve(ctx, int(cap_records), int(cap_keys)))
 
 
 def gsvr_step_host(ctx, theta, idx, grad_out=None, loss_out=None):

@@ -47,14 +47,75 @@ PLAIN_LR = dict(lr_mu=2.5e-3, lr_ls=2.5e-3, lr_q=1e-3, lr_c=2e-3 * 0.0635, lr_ro
 PLAIN_STEP_EVERY = 200
 
 
+# A short list of launch shapes for per-reconstruction tuning (the library's
+# full space is gsvr.gsvr_tune_space_default()).
+TUNE_SHAPES = [gsvr.tiling(12, 12), gsvr.tiling(8, 16), gsvr.tiling(16, 16), gsvr.tiling(10, 10),
+               gsvr.tiling(12, 12, queue_order=1), gsvr.tiling(8, 8)]
+
+
+def make_context(case, device, stream, n_sample=None, subjects=None, tune=False, margin=2.0, shapes=None):
+    """A fixed-capacity context (no host synchronisation per iteration) for
+    `case`: record / key counts from one growth-mode forward on a sample,
+    capacities `margin` times those, launch shape from the autotuner when
+    `tune` (timed on the same sample size).  `subjects` = (stack_subject,
+    gauss_count) for a batched case.  Returns (context, launch shape)."""
+    def setup(ctx):
+        if subjects is not None:
+            gsvr.gsvr_set_subjects(ctx.ctx, subjects[0], subjects[1])
+
+    def sample(ctx, step):
+        if n_sample:
+            if subjects is not None:
+                gsvr.gsvr_sample_pixels_subjects(ctx.ctx, n_sample, step)
+            else:
+                gsvr.gsvr_sample_pixels(ctx.ctx, min(n_sample, int(case["mask"].sum())), step)
+
+    sid = stream.cuda_stream
+    probe = gsvr.Context(case, device=device, stream=sid, tile_h=12, tile_w=12)
+    setup(probe)
+    sample(probe, 0)
+    probe.forward()
+    st = probe.stats()
+    shape = gsvr.gsvr_get_tiling(probe.ctx)
+    if tune:
+        gsvr.gsvr_reserve(probe.ctx, int(st["n_records"] * margin) + 4096, int(st["n_keys"] * 2 * margin) + 4096)
+        best, res = gsvr.gsvr_autotune(probe.ctx, shapes or TUNE_SHAPES, n_per_subject=n_sample or 0, iterations=5)
+        shape = res[best]
+        sample(probe, 0)
+        probe.forward()
+        st = probe.stats()
+    probe.close()
+    ctx = gsvr.Context(case, device=device, stream=sid, tile_h=shape.tile_h, tile_w=shape.tile_w, fixed_capacity=1,
+                       cap_records=int(st["n_records"] * margin) + 4096, cap_keys=int(st["n_keys"] * margin) + 4096)
+    gsvr.gsvr_set_tiling(ctx.ctx, shape)
+    setup(ctx)
+    return ctx, shape
+
+
+def ensure_room(ctx, fill=0.75, grow=1.5):
+    """Grow a fixed-capacity context when the last forward used more than
+    `fill` of its record or key capacity.  Returns True when it grew."""
+    st = ctx.stats()
+    if st["n_records"] > fill * st["cap_records"] or st["n_keys"] > fill * st["cap_keys"]:
+        gsvr.gsvr_reserve(ctx.ctx, int(max(st["n_records"], 1) * grow / fill), int(max(st["n_keys"], 1) * grow / fill))
+        return True
+    return False
+
+
 class Reconstruction:
     """One subject: gsvr context + Adam state; `step` = sample, forward,
-    backward, Adam."""
+    backward, Adam.  `fixed` builds a fixed-capacity context (see make_context),
+    `tune` lets the autotuner pick its launch shape."""
 
     def __init__(self, case, device=0, stream=None, n_sample=None, lr=None, frozen=None,
-                 step_every=PLAIN_STEP_EVERY, gamma=0.5, **cfg):
+                 step_every=PLAIN_STEP_EVERY, gamma=0.5, fixed=False, tune=False, **cfg):
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
-        self.ctx = gsvr.Context(case, device=device, stream=self.stream.cuda_stream, **cfg)
+        if fixed or tune:
+            self.ctx, self.shape = make_context(case, device, self.stream, n_sample, tune=tune)
+        else:
+            self.ctx = gsvr.Context(case, device=device, stream=self.stream.cuda_stream, **cfg)
+            self.shape = gsvr.gsvr_get_tiling(self.ctx.ctx)
+        self.fixed = fixed or tune
         self.N = int(case["N"])
         self.n_sample = n_sample
         self.lr = dict(PLAIN_LR, **(lr or {}))
@@ -75,11 +136,7 @@ class Reconstruction:
         gsvr.gsvr_forward(self.ctx.ctx)
         gsvr.gsvr_backward(self.ctx.ctx)
         self.t += 1
-        lr = self.lr
-        if self.step_every:
-            f = self.gamma ** ((self.t - 1) // self.step_every)
-            lr = {k: v * f for k, v in self.lr.items()}
-        gsvr.gsvr_adam_step(self.ctx.ctx, self.t, lr)
+        gsvr.gsvr_adam_step(self.ctx.ctx, self.t, self.lr, step_every=self.step_every or 0, gamma=self.gamma)
 
     def run(self, iters, probe=None, eval_every=25, target_psnr=None):
         """Returns {"history": [(iteration, device_seconds, loss, psnr)], "time_to_target": s or None}."""
@@ -100,6 +157,9 @@ class Reconstruction:
             e1.synchronize()
             dev_s += e0.elapsed_time(e1) / 1e3
             done += n
+            if self.fixed:
+                gsvr.gsvr_sync_status(self.ctx.ctx)
+                ensure_room(self.ctx)
             loss = self.ctx.loss()
             p = probe.psnr(self.ctx.theta) if probe is not None else None
             hist.append((done, dev_s, loss, p))
@@ -107,6 +167,111 @@ class Reconstruction:
                 t_hit = dev_s
         gsvr.gsvr_sync_status(self.ctx.ctx)
         return {"history": hist, "time_to_target": t_hit}
+
+    def close(self):
+        self.ctx.close()
+
+
+class BatchedReconstruction:
+    """Several subjects in one context (the batched form): one set of launches
+    per iteration serves every subject -- per-subject samplers, loss weights,
+    losses and Adam bias corrections, Gaussians meeting only their subject's
+    slices -- and the whole iteration (sample, forward, backward, Adam with
+    StepLR, step counter) is one CUDA graph replayed `n` times per `advance`.
+    Subject k's reference slice is frozen."""
+
+    def __init__(self, cases, device=0, n_sample=1 << 18, lr=None, step_every=PLAIN_STEP_EVERY, gamma=0.5,
+                 tune=True, graph=True, margin=2.0):
+        self.cases = cases
+        self.b = inputs.concat_cases(cases)
+        self.n_subj = len(cases)
+        self.stream = torch.cuda.Stream(device=device)
+        self.n_sample = n_sample
+        self.lr = dict(PLAIN_LR, **(lr or {}))
+        self.step_every, self.gamma = step_every, gamma
+        self.ctx, self.shape = make_context(self.b, device, self.stream, n_sample,
+                                            subjects=(self.b["stack_subject"], self.b["gauss_count"]), tune=tune,
+                                            margin=margin)
+        M = self.ctx.M
+        f = np.zeros(M, np.uint8)
+        base = 0
+        self.slice_first = []
+        for c in cases:
+            self.slice_first.append(base)
+            if c.get("ref_slice") is not None:
+                f[base + int(c["ref_slice"])] = 1
+            base += inputs.n_slices_total(c["stacks"])
+        gsvr.gsvr_set_frozen(self.ctx.ctx, f)
+        self.graph = graph
+        self.t = 0
+        gsvr.gsvr_set_step(self.ctx.ctx, 0)
+        if graph:
+            self._capture()
+        g = np.concatenate([[0], np.cumsum(self.b["gauss_count"])]).astype(np.int64)
+        N = int(g[-1])
+        dev = self.ctx.theta.device
+        self.gauss_index = [torch.from_numpy(np.concatenate([c * N + np.arange(g[k], g[k + 1]) for c in range(11)]))
+                            .to(dev) for k in range(self.n_subj)]
+
+    def _capture(self):
+        # the capture needs a forward at the current capacities first
+        gsvr.gsvr_sample_pixels_subjects(self.ctx.ctx, self.n_sample, self.t)
+        gsvr.gsvr_forward(self.ctx.ctx)
+        gsvr.gsvr_sync_status(self.ctx.ctx)
+        gsvr.gsvr_set_step(self.ctx.ctx, self.t)
+        gsvr.gsvr_graph_capture(self.ctx.ctx, self.n_sample, lr=self.lr, step_every=self.step_every or 0,
+                                gamma=self.gamma)
+
+    def advance(self, n):
+        if self.graph:
+            gsvr.gsvr_graph_launch(self.ctx.ctx, n)
+        else:
+            for _ in range(n):
+                gsvr.gsvr_sample_pixels_subjects(self.ctx.ctx, self.n_sample, self.t)
+                gsvr.gsvr_forward(self.ctx.ctx)
+                gsvr.gsvr_backward(self.ctx.ctx)
+                self.t += 1
+                gsvr.gsvr_adam_step(self.ctx.ctx, self.t, self.lr, step_every=self.step_every or 0, gamma=self.gamma)
+            return
+        self.t += n
+
+    def subject_theta(self, k):
+        return self.ctx.theta.index_select(0, self.gauss_index[k])
+
+    def run(self, iters, probes=None, eval_every=25, targets=None):
+        """Returns {"history": [(iteration, device_seconds, [loss per subject], [psnr per subject])],
+        "time_to_target": [s or None per subject], "iters_to_target": [...]}."""
+        hist = []
+        dev_s = 0.0
+        hit_t = [None] * self.n_subj
+        hit_i = [None] * self.n_subj
+
+        def evaluate():
+            return [p.psnr(self.subject_theta(k)) for k, p in enumerate(probes)] if probes else None
+
+        hist.append((0, 0.0, None, evaluate()))
+        done = 0
+        while done < iters:
+            n = min(eval_every, iters - done)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.advance(n)
+            e1.record(self.stream)
+            e1.synchronize()
+            dev_s += e0.elapsed_time(e1) / 1e3
+            done += n
+            gsvr.gsvr_sync_status(self.ctx.ctx)
+            if ensure_room(self.ctx) and self.graph:
+                self._capture()
+            losses = gsvr.gsvr_get_subject_losses(self.ctx.ctx, self.n_subj).tolist()
+            ps = evaluate()
+            hist.append((done, dev_s, losses, ps))
+            if targets is not None and ps is not None:
+                for k in range(self.n_subj):
+                    if hit_t[k] is None and targets[k] is not None and ps[k] >= targets[k]:
+                        hit_t[k], hit_i[k] = dev_s, done
+        return {"history": hist, "time_to_target": hit_t, "iters_to_target": hit_i}
 
     def close(self):
         self.ctx.close()

@@ -129,3 +129,19 @@ def test_graph_replay_matches_eager(G):
         ctx.close()
     e, g = runs
     assert np.abs(e - g).max() <= 1e-4 * np.abs(e).max()
+
+
+def test_batched_driver_graph_equals_eager_and_descends(G):
+    from paper_2512_11624_b300.recon import BatchedReconstruction
+    cases = three_subjects()
+    runs = []
+    for graph in (False, True):
+        br = BatchedReconstruction(cases, n_sample=300, tune=False, graph=graph, lr=dict(lr_c=5e-3))
+        res = br.run(40, eval_every=10)
+        runs.append((br.ctx.theta.cpu().numpy().astype(np.float64), res["history"]))
+        br.close()
+    (te, he), (tg, hg) = runs
+    assert np.abs(te - tg).max() <= 1e-4 * np.abs(te).max()
+    first, last = np.array(he[1][2]), np.array(he[-1][2])
+    assert np.all(last < first), (first, last)
+    assert np.allclose(np.array(hg[-1][2]), last, rtol=1e-3)
