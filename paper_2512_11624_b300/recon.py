@@ -117,7 +117,7 @@ class Reconstruction:
             self.shape = gsvr.gsvr_get_tiling(self.ctx.ctx)
         self.fixed = fixed or tune
         self.N = int(case["N"])
-        self.n_sample = n_sample
+        self.n_sample = min(int(n_sample), int(np.count_nonzero(case["mask"]))) if n_sample else n_sample
         self.lr = dict(PLAIN_LR, **(lr or {}))
         self.step_every = step_every  # StepLR: learning rates x gamma every step_every iterations (App. A.1)
         self.gamma = gamma
