@@ -138,9 +138,12 @@ class BrainPhantom:
     background 0, CSF shell 0.95 between the outer ellipsoid and the cortex,
     folded cortex band 0.45 (2.5 mm thick), white matter 0.65, deep grey matter
     0.55, two ventricles 0.95.  Edges are logistic with a 0.3 mm width.
-    Semi-axes (35, 28, 25) mm times ``scale``."""
+    Semi-axes (35, 28, 25) mm times ``scale``.  ``jitter`` > 0 draws a member
+    of the same canonical-frame family: semi-axes times U(1 +- jitter), tissue
+    levels times U(1 +- jitter / 1.5) (the fold pattern always varies with
+    the seed)."""
 
-    def __init__(self, seed=0, scale=1.0):
+    def __init__(self, seed=0, scale=1.0, jitter=0.0):
         rng = np.random.default_rng(seed + 7919)
         self.axes = np.array([35.0, 28.0, 25.0]) * scale
         self.scale = scale
@@ -148,6 +151,11 @@ class BrainPhantom:
         self.kb = rng.integers(1, 6, size=8).astype(np.float64)
         self.ph = rng.uniform(0, 2 * np.pi, size=8)
         self.width = 0.3
+        # tissue levels: CSF, cortex, white matter, deep grey matter, ventricles
+        self.levels = np.array([0.95, 0.45, 0.65, 0.55, 0.95])
+        if jitter > 0:  # a member of the canonical-frame family: semi-axes and levels varied
+            self.axes = self.axes * rng.uniform(1 - jitter, 1 + jitter, size=3)
+            self.levels = self.levels * rng.uniform(1 - jitter / 1.5, 1 + jitter / 1.5, size=5)
         self.L = float(np.mean(self.axes))
 
     @staticmethod
@@ -178,10 +186,11 @@ class BrainPhantom:
         m_gm = self._ell(x, (0.0, 0.0, -2.0 * s), (12.0 * s, 8.0 * s, 6.0 * s))
         m_v = np.maximum(self._ell(x, (6.0 * s, 2.0 * s, 4.0 * s), (3.5 * s, 9.0 * s, 4.0 * s)),
                          self._ell(x, (-6.0 * s, 2.0 * s, 4.0 * s), (3.5 * s, 9.0 * s, 4.0 * s)))
-        inner = 0.65 * (1 - m_gm) + 0.55 * m_gm
-        inner = inner * (1 - m_v) + 0.95 * m_v
-        cx = 0.45 * (1 - m_wm) + inner * m_wm
-        brain = 0.95 * (1 - m_cx) + cx * m_cx
+        csf, ctx_, wm, dgm, ven = self.levels
+        inner = wm * (1 - m_gm) + dgm * m_gm
+        inner = inner * (1 - m_v) + ven * m_v
+        cx = ctx_ * (1 - m_wm) + inner * m_wm
+        brain = csf * (1 - m_cx) + cx * m_cx
         return m_out * brain
 
     def inside(self, x, dilate=0.0):

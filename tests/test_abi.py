@@ -7,10 +7,16 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_entry_points():
-    src = open(os.path.join(ROOT, "include", "gsvr.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gsvr_[a-z_0-9]+)\s*\(", src)))
+def declared_entry_points(header=None):
+    """Entry points declared in include/*.h (or in one header)."""
+    import glob
+    names = set()
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        if header and os.path.basename(path) != header:
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(gsvr_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -29,10 +35,13 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_binding_names_match_header():
-    from paper_2512_11624_b300 import gsvr
-    assert sorted(gsvr.EXPORTS) == declared_entry_points()
+    from paper_2512_11624_b300 import cnn, gsvr
+    assert sorted(gsvr.EXPORTS) == declared_entry_points("gsvr.h")
+    assert sorted(cnn.EXPORTS) == declared_entry_points("gsvr_cnn.h")
     for n in gsvr.EXPORTS:
         assert callable(getattr(gsvr, n))
+    for n in cnn.EXPORTS:
+        assert callable(getattr(cnn.lib, n))
     assert gsvr.gsvr_abi_version() == 1
 
 
