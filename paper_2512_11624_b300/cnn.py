@@ -205,10 +205,32 @@ class SliceRenderer:
         case["theta"][6] = 1.0
         self.ctx = gsvr.Context(case, device=device, stream=self.stream.cuda_stream, tile_h=12, tile_w=12)
         self.aux = aux_for_stacks(self.stacks)
+        # nominal world position of every pixel (for the acquisition mask)
+        pos = []
+        for st in self.stacks:
+            n = st["n_slices"]
+            a = (np.arange(IMAGE) - 0.5 * (IMAGE - 1)) * st["dy"]
+            b = (np.arange(IMAGE) - 0.5 * (IMAGE - 1)) * st["dx"]
+            A, Bg = np.meshgrid(a, b, indexing="ij")
+            for k in range(n):
+                c0 = st["origin"] + (k - 0.5 * (n - 1)) * st["thickness"] * st["R"][:, 2]
+                pos.append(Bg.reshape(-1, 1) * st["R"][:, 0] + A.reshape(-1, 1) * st["R"][:, 1] + c0)
+        self.pos = torch.from_numpy(np.concatenate(pos).astype(np.float32)).to("cuda:%d" % device)
+
+    def mask(self, axes, dilate_mm=15.0):
+        """Acquisition mask of every slice: the phantom's outer ellipsoid (semi-axes
+        `axes`) dilated by dilate_mm, at the nominal pixel positions (as the
+        simulated acquisitions)."""
+        import torch
+        ax = torch.tensor(np.asarray(axes, np.float32) + dilate_mm, device=self.pos.device)
+        return ((self.pos / ax) ** 2).sum(1).reshape(self.M, IMAGE, IMAGE) <= 1.0
 
     def render(self, phantom, motion):
         theta_g, N = inputs.grid_gaussians(phantom, h=self.h, s=self.h)
-        gsvr.gsvr_set_gaussians(self.ctx.ctx, N, theta_g.astype(np.float32))
+        return self.render_gaussians(theta_g, N, motion)
+
+    def render_gaussians(self, theta_g, N, motion):
+        gsvr.gsvr_set_gaussians(self.ctx.ctx, N, np.asarray(theta_g, np.float32))
         gsvr.gsvr_set_poses(self.ctx.ctx, np.asarray(motion, np.float32).reshape(-1))
         gsvr.gsvr_forward(self.ctx.ctx)
         img = self.ctx.pred.reshape(self.M, IMAGE, IMAGE).clone()
@@ -225,3 +247,102 @@ def rician(img, frac, gen):
     n1 = torch.randn(img.shape, device=img.device, generator=gen) * sd
     n2 = torch.randn(img.shape, device=img.device, generator=gen) * sd
     return torch.sqrt((img + n1) ** 2 + n2 ** 2)
+
+
+def content_fraction(img, level=0.1):
+    """Fraction of each slice's pixels above `level` times the slice set's 99th
+    percentile intensity (torch, device)."""
+    import torch
+    ref = torch.quantile(img.reshape(-1)[::97].float(), 0.99).clamp(min=1e-6)
+    return (img > level * ref).float().reshape(img.shape[0], -1).mean(1)
+
+
+def _phantom_grid(args):
+    seed, jitter, h = args
+    ph = inputs.BrainPhantom(seed, jitter=jitter)
+    theta_g, N = inputs.grid_gaussians(ph, h=h, s=h)
+    return theta_g.astype(np.float32), N, np.asarray(ph.axes)
+
+
+def make_training_set(n_phantoms, motions_per_phantom=2, n_slices=20, max_deg=20.0, max_mm=10.0, noise=0.02,
+                      seed=0, min_content=0.02, jitter=0.15, h=1.5, device=0, workers=8, log=None):
+    """Training slices rendered by the forward model: phantoms of the
+    canonical-frame family (seeds 10^6 (seed + 1) + p, disjoint from evaluation
+    seeds; their Gaussian grids built on `workers` spawned host processes),
+    Gaussians on an h-mm grid, per-slice motion U(+-max_deg) / U(+-max_mm),
+    Rician noise, zero outside the acquisition mask (phantom dilated by 15 mm),
+    per-slice unit-mean scaling; slices with less than min_content brain
+    content are dropped.  Returns device tensors (x [n][128][128],
+    aux [n][25], target [n][6])."""
+    import multiprocessing as mp
+
+    import torch
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda:%d" % device).manual_seed(seed)
+    ren = SliceRenderer(n_slices=n_slices, h=h, device=device)
+    aux_all = torch.from_numpy(ren.aux).to("cuda:%d" % device)
+    xs, auxs, tgts = [], [], []
+    jobs = [(1_000_000 * (seed + 1) + p, jitter, h) for p in range(n_phantoms)]
+    pool = mp.get_context("spawn").Pool(workers) if workers > 1 else None
+    it = pool.imap(_phantom_grid, jobs, chunksize=4) if pool else map(_phantom_grid, jobs)
+    try:
+        for p, (theta_g, N, axes) in enumerate(it):
+            msk = ren.mask(axes)
+            for _ in range(motions_per_phantom):
+                motion = inputs.random_motion(rng, ren.M, max_deg, max_mm)
+                img = ren.render_gaussians(theta_g, N, motion)
+                img = rician(img, noise, gen) * msk
+                keep = content_fraction(img) > min_content
+                xs.append(normalise_slices(img[keep]))
+                auxs.append(aux_all[keep])
+                tgts.append(torch.from_numpy(pose_target(motion)).to(img.device)[keep])
+            if log and (p + 1) % max(1, n_phantoms // 10) == 0:
+                log("rendered %d / %d phantoms, %d slices" % (p + 1, n_phantoms, sum(x.shape[0] for x in xs)))
+    finally:
+        if pool:
+            pool.close()
+            pool.join()
+    ren.close()
+    return torch.cat(xs), torch.cat(auxs), torch.cat(tgts)
+
+
+def train(net, X, A, Y, epochs=20, batch=256, lr=1e-3, seed=0, val_frac=0.05, log=None):
+    """Adam with a cosine learning-rate schedule over `epochs` passes of random
+    batches; the last val_frac of the set is held out.  Returns the history
+    [(epoch, train loss, validation loss, seconds)]."""
+    import math
+    import time
+
+    import torch
+    n = X.shape[0]
+    n_val = max(batch, int(n * val_frac))
+    n_tr = n - n_val
+    g = torch.Generator(device=X.device).manual_seed(seed)
+    hist, t, t0 = [], 0, time.time()
+    for ep in range(epochs):
+        lr_ep = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))
+        perm = torch.randperm(n_tr, device=X.device, generator=g)
+        tot = torch.zeros(1, dtype=torch.float64, device=X.device)
+        steps = 0
+        for s0 in range(0, n_tr - batch + 1, batch):
+            idx = perm[s0:s0 + batch]
+            tot += net.loss_backward(X.index_select(0, idx), A.index_select(0, idx), Y.index_select(0, idx))
+            t += 1
+            steps += 1
+            net.adam_step(t, lr=lr_ep)
+        vl = evaluate_loss(net, X[n_tr:], A[n_tr:], Y[n_tr:], batch)
+        hist.append((ep + 1, float(tot.item()) / max(steps, 1), vl, time.time() - t0))
+        if log:
+            log("epoch %d: train %.4f  val %.4f  (%.1f s)" % hist[-1])
+    return hist
+
+
+def predict(net, X, A, batch=256):
+    import torch
+    outs = [net.forward(X[s:s + batch].contiguous(), A[s:s + batch].contiguous()) for s in range(0, X.shape[0], batch)]
+    return torch.cat(outs)
+
+
+def evaluate_loss(net, X, A, Y, batch=256):
+    out = predict(net, X, A, batch)
+    return float(((out - Y) ** 2).mean().item())

@@ -285,18 +285,20 @@ def grid_gaussians(phantom, h=0.8, s=0.8):
     return np.concatenate([P.T, ls, q, c[None, :]], axis=0).reshape(-1), N
 
 
-def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20):
+def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0, motion_mm=3.0, jitter=0.0):
     """The fetal-scale plain case: ~200k Gaussians on a 0.8 mm grid inside the
     brain phantom; axial / coronal / sagittal stacks of 40 x 192 x 192 px at
     1 x 1 x 3.5 mm centred on the origin; per-slice motion U(+-5 deg) axis
     uniform on the sphere, U(+-3 mm); Rician noise 2 %; pixel mask = brain
     dilated by 15 mm; 2^18 pixels sampled per iteration.  Poses start at 0
-    (the unknown motion is what the optimisation recovers)."""
+    (the unknown motion is what the optimisation recovers).  motion_deg /
+    motion_mm widen the motion range; jitter > 0 draws the phantom from the
+    canonical-frame family (see BrainPhantom)."""
     rng = np.random.default_rng(seed)
-    ph = BrainPhantom(seed)
+    ph = BrainPhantom(seed, jitter=jitter)
     stacks = [stack(40, 192, 192, 1.0, 1.0, 3.5, R) for R in (AXIAL, CORONAL, SAGITTAL)]
     M = n_slices_total(stacks)
-    motion = random_motion(rng, M, 5.0, 3.0)
+    motion = random_motion(rng, M, motion_deg, motion_mm)
     if ref_slice is not None:
         motion[ref_slice] = 0.0  # the reference slice fixes the frame (its pose is frozen)
     I, mask = simulate_phantom_stacks(ph, stacks, motion, seed=seed)

@@ -1,6 +1,7 @@
 """Reconstruction studies on synthetic subjects (run on a GPU):
 
   python -m paper_2512_11624_b300.study batched [--subjects 16] [--iters 2000] [--out FILE]
+  python -m paper_2512_11624_b300.study learned [--phantoms 2000] [--epochs 20] [--cases 10] [--out FILE]
 
 `batched`: the batched multi-subject workload (`inputs.batched`: 16 subjects of
 uneven size).  Every subject is first reconstructed alone (its own context with
@@ -12,6 +13,20 @@ the target alone and batched; in aggregate: device seconds for all subjects'
 `iters` iterations and useful (pixel, Gaussian) pairs per second both ways.
 Evaluations (PSNR every `eval_every` iterations) are outside the timed device
 time.
+
+`learned`: the pose network (include/gsvr_cnn.h) is trained on slices that the
+forward model renders from phantoms of the canonical-frame family under motion
+U(+-20 deg) / U(+-10 mm), then initialises fetal-sized test cases (new seeds;
+motion at that range and at the plain workload's U(+-5 deg) / U(+-3 mm)): the
+network's pose for every slice with brain content, kept only where it matches
+a template volume (the family's seed-0 member) better than the nominal pose
+(normalised cross-correlation of the slice with the template rendered at
+each pose; the others fall back to nominal), then the plain optimisation
+refines.  Reported per case: pose errors (rotation angle, slice-centre
+displacement) of the network alone, after refinement and of the plain method
+from nominal, the fallback count, and seconds to the target PSNR (plain from
+nominal after `iters` iterations - 0.5 dB) both ways, the learned path
+including its inference and fallback time.
 """
 from __future__ import annotations
 
@@ -127,6 +142,153 @@ def run_batched(args):
     return out
 
 
+def _make_fetal(args):
+    seed, deg, mm = args
+    from . import inputs
+    return inputs.fetal(seed, with_truth=True, init="flat", motion_deg=deg, motion_mm=mm, jitter=0.15)
+
+
+def pose_errors(stacks, est, truth, sel):
+    """Rotation angle (deg) between the estimated and true slice rotations and
+    displacement (mm) of the slice centre, over the slices in `sel`."""
+    from scipy.spatial.transform import Rotation
+    c0 = []
+    for st in stacks:
+        n = st["n_slices"]
+        for k in range(n):
+            c0.append(st["origin"] + (k - 0.5 * (n - 1)) * st["thickness"] * st["R"][:, 2])
+    c0 = np.array(c0)[sel]
+    Re, Rt = Rotation.from_rotvec(est[sel, :3]), Rotation.from_rotvec(truth[sel, :3])
+    ang = np.rad2deg((Re.inv() * Rt).magnitude())
+    te = Re.apply(c0) + est[sel, 3:]
+    tt = Rt.apply(c0) + truth[sel, 3:]
+    d = np.linalg.norm(te - tt, axis=1)
+    return {"deg_mean": float(ang.mean()), "deg_median": float(np.median(ang)), "mm_mean": float(d.mean()),
+            "mm_median": float(np.median(d))}
+
+
+def slice_ncc(pred, obs, msk):
+    """Per-slice normalised cross-correlation over the masked pixels (torch)."""
+    import torch
+    m = msk.float()
+    n = m.sum(1).clamp(min=1.0)
+    mp = (pred * m).sum(1) / n
+    mo = (obs * m).sum(1) / n
+    dp = (pred - mp[:, None]) * m
+    do = (obs - mo[:, None]) * m
+    return (dp * do).sum(1) / torch.sqrt((dp * dp).sum(1) * (do * do).sum(1)).clamp(min=1e-20)
+
+
+def run_learned(args):
+    n_c4, n_c1 = args.cases, args.cases_c1
+    specs = [(7000 + k, 20.0, 10.0) for k in range(n_c4)] + [(8000 + k, 5.0, 3.0) for k in range(n_c1)]
+    t_gen = time.time()
+    if args.workers > 1:
+        with mp.get_context("spawn").Pool(args.workers) as pool:
+            cases = pool.map(_make_fetal, specs)
+    else:
+        cases = [_make_fetal(sp) for sp in specs]
+    t_gen = time.time() - t_gen
+    import torch
+    from . import cnn, gsvr, inputs
+    from .recon import PSNRProbe, Reconstruction
+    dev = 0
+    torch.cuda.set_device(dev)
+    log = lambda m: print(m, flush=True)
+    t0 = time.time()
+    X, A, Y = cnn.make_training_set(args.phantoms, motions_per_phantom=args.motions, seed=args.seed, log=log)
+    t_data = time.time() - t0
+    log("training set: %d slices in %.1f s" % (X.shape[0], t_data))
+    net = cnn.PoseNet(max_batch=args.batch, seed=args.seed)
+    hist = cnn.train(net, X, A, Y, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=args.seed, log=log)
+    n_train = int(X.shape[0])
+    del X, A, Y
+    torch.cuda.empty_cache()
+    out = {"training": {"slices": n_train, "phantoms": args.phantoms, "motions_per_phantom": args.motions,
+                        "data_s": t_data, "epochs": hist, "batch": args.batch, "lr": args.lr},
+           "generate_cases_s": t_gen, "iters": args.iters, "cases": []}
+    # template volume for the fallback test: the family's seed-0 member on a 1.5 mm grid
+    tmpl_theta, tmpl_N = inputs.grid_gaussians(inputs.BrainPhantom(0), h=1.5, s=1.5)
+    for (seed, deg, mm), case in zip(specs, cases):
+        M = inputs.n_slices_total(case["stacks"])
+        H = W = 192
+        truth = case["motion"]
+        ref = case["ref_slice"]
+        st = torch.cuda.Stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        I = torch.from_numpy(case["I"]).cuda().reshape(M, H, W)
+        msk = torch.from_numpy(case["mask"]).cuda().reshape(M, H, W) > 0
+        torch.cuda.synchronize()
+        t_inf0 = time.perf_counter()
+        lo = (H - cnn.IMAGE) // 2
+        crop = I[:, lo:lo + cnn.IMAGE, lo:lo + cnn.IMAGE].contiguous()
+        content = cnn.content_fraction(crop) > 0.02
+        aux = torch.from_numpy(cnn.aux_for_stacks(case["stacks"])).cuda()
+        pred = cnn.pose_from_output(cnn.predict(net, cnn.normalise_slices(crop), aux).cpu().numpy())
+        # fallback test against the template
+        tc = {"stacks": case["stacks"], "N": tmpl_N,
+              "theta": np.concatenate([tmpl_theta, np.zeros(6 * M)]).astype(np.float32), "I": case["I"],
+              "mask": case["mask"]}
+        tctx = gsvr.Context(tc, tile_h=12, tile_w=12)
+        ncc = []
+        for poses in (np.zeros((M, 6)), pred):
+            gsvr.gsvr_set_poses(tctx.ctx, poses.astype(np.float32).reshape(-1))
+            tctx.forward()
+            ncc.append(slice_ncc(tctx.pred.reshape(M, -1), I.reshape(M, -1), msk.reshape(M, -1)))
+        tctx.close()
+        use = ((ncc[1] > ncc[0]) & content).cpu().numpy()
+        use[ref] = False
+        init = np.where(use[:, None], pred, 0.0)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t_inf0
+        sel = content.cpu().numpy().copy()
+        sel[ref] = False
+        rec_out = {}
+        probe = PSNRProbe(case["phantom"], case["N"])
+        for name, poses in (("plain", np.zeros((M, 6))), ("learned", init)):
+            c = dict(case)
+            th = case["theta"].copy()
+            th[11 * case["N"]:] = poses.astype(np.float32).reshape(-1)
+            c["theta"] = th
+            rec = Reconstruction(c, n_sample=1 << 18, fixed=True)
+            res = rec.run(args.iters, probe=probe, eval_every=args.eval_every)
+            est = rec.ctx.theta[11 * case["N"]:].cpu().numpy().astype(np.float64).reshape(M, 6)
+            rec_out[name] = {"history": [(it, s_, p) for it, s_, _, p in res["history"]],
+                             "pose_error": pose_errors(case["stacks"], est, truth, sel)}
+            rec.close()
+        probe.close()
+        target = rec_out["plain"]["history"][-1][2] - 0.5
+        for name in rec_out:
+            h = rec_out[name]["history"]
+            hit = next(((it, s_) for it, s_, p in h[1:] if p >= target), (None, None))
+            extra = t_inf if name == "learned" else 0.0
+            rec_out[name]["iters_to_target"] = hit[0]
+            rec_out[name]["s_to_target"] = None if hit[1] is None else hit[1] + extra
+            rec_out[name]["psnr_final"] = h[-1][2]
+            del rec_out[name]["history"]
+        row = {"seed": seed, "motion": [deg, mm], "slices_with_content": int(sel.sum()),
+               "fallbacks": int((~use & sel).sum()), "inference_s": t_inf, "target_psnr": target,
+               "network": pose_errors(case["stacks"], pred, truth, sel),
+               "nominal": pose_errors(case["stacks"], np.zeros((M, 6)), truth, sel), **rec_out}
+        out["cases"].append(row)
+        log("case %d (+-%g deg): net %.2f deg %.2f mm | nominal %.2f deg %.2f mm | fallbacks %d/%d | "
+            "to target: plain %s s (it %s), learned %s s (it %s) | refined: plain %.2f deg, learned %.2f deg" %
+            (seed, deg, row["network"]["deg_mean"], row["network"]["mm_mean"], row["nominal"]["deg_mean"],
+             row["nominal"]["mm_mean"], row["fallbacks"], row["slices_with_content"],
+             _fmt(rec_out["plain"]["s_to_target"]), rec_out["plain"]["iters_to_target"],
+             _fmt(rec_out["learned"]["s_to_target"]), rec_out["learned"]["iters_to_target"],
+             rec_out["plain"]["pose_error"]["deg_mean"], rec_out["learned"]["pose_error"]["deg_mean"]))
+    net.close()
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(out, f, indent=1)
+    return out
+
+
+def _fmt(v):
+    return "-" if v is None else "%.2f" % v
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -139,9 +301,24 @@ def main():
     b.add_argument("--workers", type=int, default=8)
     b.add_argument("--no-graph", action="store_true")
     b.add_argument("--out", default="")
+    lr = sub.add_parser("learned")
+    lr.add_argument("--phantoms", type=int, default=2000)
+    lr.add_argument("--motions", type=int, default=2)
+    lr.add_argument("--epochs", type=int, default=20)
+    lr.add_argument("--batch", type=int, default=256)
+    lr.add_argument("--lr", type=float, default=1e-3)
+    lr.add_argument("--seed", type=int, default=0)
+    lr.add_argument("--cases", type=int, default=10)
+    lr.add_argument("--cases-c1", type=int, default=5)
+    lr.add_argument("--iters", type=int, default=2000)
+    lr.add_argument("--eval-every", type=int, default=50)
+    lr.add_argument("--workers", type=int, default=8)
+    lr.add_argument("--out", default="")
     args = ap.parse_args()
     if args.cmd == "batched":
         run_batched(args)
+    elif args.cmd == "learned":
+        run_learned(args)
 
 
 if __name__ == "__main__":
