@@ -17,17 +17,18 @@
  *          1 -> 32 -> 64 -> 128 -> 256 -> 256 -> 512 (128^2 -> 2^2 positions),
  *          each + bias + ReLU; activations NHWC bfloat16, products on the
  *          tensor cores (bfloat16 operands, float32 accumulation)
- *   mean over the 4 final positions -> 512 features (float32)
+ *   the final 2 x 2 x 512 map flattened position-major -> 2048 features
+ *          (float32; the positions keep where the anatomy sits in the slice)
  *   concatenated with aux (25 floats per slice: the stack's nominal rotation
  *          R0 row-major (9) and a 16-d sinusoidal embedding of the slice's
  *          offset along the stack normal; the caller builds it)
- *   fc1 537 -> 256 + ReLU, fc2 256 -> 6 (float32)
+ *   fc1 2073 -> 256 + ReLU, fc2 256 -> 6 (float32)
  *   output (r_0..2 in rad, tau_0..2 / 10 mm)
  *   loss   mean over the batch and the 6 outputs of (output - target)^2
  * Parameters: one float32 vector (master copy), in this order per layer l:
  *   conv_l weights [Co][3][3][Ci], conv_l bias [Co]  (l = 1..6),
- *   fc1 weights [256][537], fc1 bias [256], fc2 weights [6][256], fc2 bias [6]
- *   (2,297,350 floats); the conv weights are rounded to bfloat16 at the start
+ *   fc1 weights [256][2073], fc1 bias [256], fc2 weights [6][256], fc2 bias [6]
+ *   (2,690,566 floats); the conv weights are rounded to bfloat16 at the start
  *   of every forward.
  *
  * Conventions: as in gsvr.h (device pointers are memory of the network's

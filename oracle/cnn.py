@@ -3,9 +3,11 @@ infrastructure only; see cnn_oracle.c).
 
 Architecture (the slice-pose regressor standing in for the learned
 pre-alignment that leaves the residual motion of Sec. 3.2): `len(channels) - 1`
-conv 3x3 / stride 2 / pad 1 layers, each + bias + ReLU, NHWC; mean over the last
-feature map's positions; concatenation with the auxiliary vector (stack
-orientation and slice-position embedding); fc1 + ReLU; fc2 -> 6 outputs
+conv 3x3 / stride 2 / pad 1 layers, each + bias + ReLU, NHWC; the last feature
+map flattened position-major (its positions keep where the anatomy sits in the
+slice, which a mean over positions would discard); concatenation with the
+auxiliary vector (stack orientation and slice-position embedding); fc1 + ReLU;
+fc2 -> 6 outputs
 (r in rad, tau / 10 mm).  Loss = mean over the batch and the 6 outputs of the
 squared error.
 
@@ -92,13 +94,16 @@ def conv_wgrad(gy, x, want_abs=False):
     return (dw, db, a) if want_abs else (dw, db)
 
 
-def param_shapes(channels=ARCH_CHANNELS, hidden=ARCH_HIDDEN, aux=ARCH_AUX, out=ARCH_OUT):
+ARCH_POSITIONS = 4  # 2 x 2 final positions of a 128 x 128 input
+
+
+def param_shapes(channels=ARCH_CHANNELS, hidden=ARCH_HIDDEN, aux=ARCH_AUX, out=ARCH_OUT, positions=ARCH_POSITIONS):
     """(name, shape) in the order of the flat parameter vector."""
     shapes = []
     for l in range(1, len(channels)):
         shapes.append(("conv%d.w" % l, (channels[l], 3, 3, channels[l - 1])))
         shapes.append(("conv%d.b" % l, (channels[l],)))
-    shapes += [("fc1.w", (hidden, channels[-1] + aux)), ("fc1.b", (hidden,)), ("fc2.w", (out, hidden)),
+    shapes += [("fc1.w", (hidden, channels[-1] * positions + aux)), ("fc1.b", (hidden,)), ("fc2.w", (out, hidden)),
                ("fc2.b", (out,))]
     return shapes
 
@@ -127,7 +132,7 @@ def forward_backward(params, x, aux, target, bf16_points=True, want_grad=True):
     for l in range(1, nl + 1):
         acts.append(rnd(conv_fwd(acts[-1], ws[l - 1], params["conv%d.b" % l], relu=True)))
     last = acts[-1]
-    f = last.reshape(B, -1, last.shape[3]).mean(axis=1)
+    f = last.reshape(B, -1)
     h = np.concatenate([f, np.asarray(aux, np.float64)], axis=1)
     z1 = h @ params["fc1.w"].T + params["fc1.b"]
     a1 = np.maximum(z1, 0.0)
@@ -145,10 +150,7 @@ def forward_backward(params, x, aux, target, bf16_points=True, want_grad=True):
     g["fc1.w"] = dz1.T @ h
     g["fc1.b"] = dz1.sum(0)
     dh = dz1 @ params["fc1.w"]
-    df = dh[:, :last.shape[3]]
-    npos = last.shape[1] * last.shape[2]
-    gy = np.broadcast_to((df / npos)[:, None, None, :], last.shape) * (last > 0)
-    gy = rnd(gy)
+    gy = rnd(dh[:, :f.shape[1]].reshape(last.shape) * (last > 0))
     for l in range(nl, 0, -1):
         xin = acts[l - 1]
         g["conv%d.w" % l], g["conv%d.b" % l] = conv_wgrad(gy, xin)

@@ -1100,6 +1100,7 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     a.slices = ctx->d_slices.p;
     a.rec = ctx->d_rec.p;
     a.rec_off = ctx->d_rec_off.p;
+    a.cand = ctx->d_cand.p;
     a.key_off = ctx->d_key_off.p;
     a.mom = ctx->d_mom.p;
     a.keys = ctx->d_keys.p;

@@ -379,21 +379,13 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const bf16 *__restrict__ g,
 }
 
 // ------------------------------------------------------------ float32 head
-// f[b][c] = mean over positions of y[b][p][c]; h[b] = (f, aux).
-__global__ void k_pool_concat(const bf16 *__restrict__ y, int B, int P, int C, const float *__restrict__ aux,
-                              float *__restrict__ h) {
-    const int HD = C + kAux;
+// h[b] = (y[b] flattened position-major (p, c), aux[b]).
+__global__ void k_flatten_concat(const bf16 *__restrict__ y, int B, int F, const float *__restrict__ aux,
+                                 float *__restrict__ h) {
+    const int HD = F + kAux;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * HD; e += gridDim.x * blockDim.x) {
         const int b = e / HD, c = e - b * HD;
-        float v;
-        if (c < C) {
-            v = 0.f;
-            for (int p = 0; p < P; ++p) v += __bfloat162float(y[((size_t)b * P + p) * C + c]);
-            v /= (float)P;
-        } else {
-            v = aux[b * kAux + (c - C)];
-        }
-        h[e] = v;
+        h[e] = c < F ? __bfloat162float(y[(size_t)b * F + c]) : aux[b * kAux + (c - F)];
     }
 }
 // out[b][j] = bias[j] + sum_i W[j][i] in[b][i], optionally ReLU (z keeps the pre-activation).
@@ -451,13 +443,12 @@ __global__ void k_fc_dgrad(const float *__restrict__ d, const float *__restrict_
         din[e] = v;
     }
 }
-// g[b][p][c] = dh[b][c] / P, times (y > 0); bfloat16.
-__global__ void k_pool_grad(const float *__restrict__ dh, int B, int P, int C, int HD, const bf16 *__restrict__ y,
-                            bf16 *__restrict__ g) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * P * C; e += gridDim.x * blockDim.x) {
-        const int c = e % C, b = e / (P * C);
-        const float v = __bfloat162float(y[e]) > 0.f ? dh[b * HD + c] / (float)P : 0.f;
-        g[e] = __float2bfloat16(v);
+// g[b][f] = dh[b][f] times (y > 0) over the flattened features; bfloat16.
+__global__ void k_flatten_grad(const float *__restrict__ dh, int B, int F, int HD, const bf16 *__restrict__ y,
+                               bf16 *__restrict__ g) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * F; e += gridDim.x * blockDim.x) {
+        const int b = e / F, f = e - b * F;
+        g[e] = __float2bfloat16(__bfloat162float(y[e]) > 0.f ? dh[b * HD + f] : 0.f);
     }
 }
 __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
@@ -586,8 +577,8 @@ gsvr_status run_forward(gsvr_cnn *n, const float *x, const float *aux, int B) {
                                      nullptr, st);
         if (e != cudaSuccess) return cuda_status(n, e, "conv forward");
     }
-    const int P = layer_size(kLayers) * layer_size(kLayers), C = kCh[kLayers], HD = C + kAux;
-    k_pool_concat<<<blocks_for((int64_t)B * HD), 256, 0, st>>>(n->act[kLayers], B, P, C, aux, n->h);
+    const int F = layer_size(kLayers) * layer_size(kLayers) * kCh[kLayers], HD = F + kAux;
+    k_flatten_concat<<<blocks_for((int64_t)B * HD), 256, 0, st>>>(n->act[kLayers], B, F, aux, n->h);
     k_fc<<<blocks_for((int64_t)B * kHidden), 256, 0, st>>>(n->h, B, HD, n->params + n->off_fc1w,
                                                            n->params + n->off_fc1b, kHidden, 1, n->z1, n->a1);
     k_fc<<<blocks_for((int64_t)B * kOut), 256, 0, st>>>(n->a1, B, kHidden, n->params + n->off_fc2w,
@@ -621,7 +612,7 @@ gsvr_status gsvr_cnn_create(gsvr_cnn **out, int32_t device, void *stream, int32_
         n->off_b[l] = o;
         o += kCh[l + 1];
     }
-    const int HD = kCh[kLayers] + kAux;
+    const int HD = layer_size(kLayers) * layer_size(kLayers) * kCh[kLayers] + kAux;
     n->off_fc1w = o;
     o += (int64_t)kHidden * HD;
     n->off_fc1b = o;
@@ -721,7 +712,7 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
     cudaStream_t st = n->st;
     gsvr_status s = run_forward(n, x, aux, B);
     if (s) return s;
-    const int P = layer_size(kLayers) * layer_size(kLayers), C = kCh[kLayers], HD = C + kAux;
+    const int F = layer_size(kLayers) * layer_size(kLayers) * kCh[kLayers], HD = F + kAux;
     cudaError_t e = cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, st);
     if (e) return cuda_status(n, e, "zero gradients");
     k_mse<<<1, 256, 0, st>>>(n->out, target, B * kOut, n->dout, loss);
@@ -733,7 +724,7 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
         n->dz1, n->h, B, HD, kHidden, n->grads + n->off_fc1w, n->grads + n->off_fc1b);
     k_fc_dgrad<<<blocks_for((int64_t)B * HD), 256, 0, st>>>(n->dz1, n->params + n->off_fc1w, B, HD, kHidden, nullptr,
                                                             n->dh);
-    k_pool_grad<<<blocks_for((int64_t)B * P * C), 256, 0, st>>>(n->dh, B, P, C, HD, n->act[kLayers],
+    k_flatten_grad<<<blocks_for((int64_t)B * F), 256, 0, st>>>(n->dh, B, F, HD, n->act[kLayers],
                                                                n->gpre[kLayers]);
     e = cudaGetLastError();
     if (e) return cuda_status(n, e, "head backward");

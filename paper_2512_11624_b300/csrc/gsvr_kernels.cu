@@ -1021,16 +1021,73 @@ __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const flo
     }
 }
 
-// Each block takes a contiguous run of Gaussians (so of at most a few
-// subjects) and accumulates its slice-frame gradients for the slices of those
-// subjects in shared memory, flushed once with float64 atomics; a block whose
-// slice window does not fit falls back to float64 global atomics per record.
+// Gaussian epilogue: the summed record gradients v = (d mu (3), d Sigma (xx yy
+// zz xy xz yz), d c, d (1/2 log det Sigma)) of Gaussian j -> (mu, ls, q, c)
+// through Sigma_j = R(q / |q|) diag(exp(2 ls)) R^T (written to grad).
+__device__ __forceinline__ void gauss_epilogue(const GradArgs &a, int j, const float v[11]) {
+    const int N = a.N;
+    // Sigma_j = Rj diag(s^2) Rj^T -> ls, q (through q / |q|)
+    const float GSm[9] = {v[3], v[6], v[7], v[6], v[4], v[8], v[7], v[8], v[5]};
+    const float qw = a.theta[6 * N + j], qx = a.theta[7 * N + j], qy = a.theta[8 * N + j], qz = a.theta[9 * N + j];
+    const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
+    float Rj[9];
+    quat_rot(w, x, y, z, Rj);
+    const float s2[3] = {expf(2.f * a.theta[3 * N + j]), expf(2.f * a.theta[4 * N + j]),
+                         expf(2.f * a.theta[5 * N + j])};
+    float GRj[9];  // GS Rj
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+            GRj[3 * p + q] = GSm[3 * p] * Rj[q] + GSm[3 * p + 1] * Rj[3 + q] + GSm[3 * p + 2] * Rj[6 + q];
+    float dls[3];
+    for (int k = 0; k < 3; ++k) {
+        const float d = Rj[k] * GRj[k] + Rj[3 + k] * GRj[3 + k] + Rj[6 + k] * GRj[6 + k];
+        dls[k] = 2.f * s2[k] * d + v[10];
+    }
+    float GRD[9];  // dL/dRj = 2 GS Rj D
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) GRD[3 * p + q] = 2.f * GRj[3 * p + q] * s2[q];
+    const float dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    const float dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const float dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    const float dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    float gq[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int e = 0; e < 9; ++e) {
+        gq[0] += GRD[e] * dRw[e];
+        gq[1] += GRD[e] * dRx[e];
+        gq[2] += GRD[e] * dRy[e];
+        gq[3] += GRD[e] * dRz[e];
+    }
+    const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    float *g = a.grad;
+    g[j] = v[0];
+    g[N + j] = v[1];
+    g[2 * N + j] = v[2];
+    g[3 * N + j] = dls[0];
+    g[4 * N + j] = dls[1];
+    g[5 * N + j] = dls[2];
+    g[6 * N + j] = (gq[0] - w * dot) / qn;
+    g[7 * N + j] = (gq[1] - x * dot) / qn;
+    g[8 * N + j] = (gq[2] - y * dot) / qn;
+    g[9 * N + j] = (gq[3] - z * dot) / qn;
+    g[10 * N + j] = v[9];
+}
+
+// Thread per record.  Each block takes a contiguous run of Gaussians (so of at
+// most a few subjects) and walks it in rounds of consecutive Gaussians with at
+// most 256 records together: one record per thread, its partial Gaussian
+// gradient staged in shared memory, then one thread per Gaussian sums its
+// records' rows in record order (deterministic) and runs the epilogue.  A
+// Gaussian with more than 256 records takes a round alone (threads stride over
+// its records, then a fixed-order tree sum).  Slice-frame gradients go to a
+// shared window over the run's subjects' slices, flushed once with float64
+// atomics; a block whose window does not fit uses float64 global atomics.
 __global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
     extern __shared__ float pacc_s[];  // window x 12
-    const int N = a.N;
-    const int lane = threadIdx.x & 31, hl = lane & 15;
-    const int per_block = blockDim.x >> 4;
-    const int chunk = (((N + gridDim.x - 1) / gridDim.x) + per_block - 1) / per_block * per_block;
+    __shared__ float rows[256][12];
+    __shared__ int s_jb;
+    const int N = a.N, tid = threadIdx.x;
+    const int chunk = (N + gridDim.x - 1) / gridDim.x;
     const int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
     if (j0 >= j1) return;
     int w0 = 0, w1 = a.M;
@@ -1040,78 +1097,70 @@ __global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
     }
     float *pacc = (w1 - w0) <= a.smem_slices ? pacc_s : nullptr;
     if (pacc) {
-        for (int e = threadIdx.x; e < (w1 - w0) * 12; e += blockDim.x) pacc[e] = 0.f;
-        __syncthreads();
+        for (int e = tid; e < (w1 - w0) * 12; e += blockDim.x) pacc[e] = 0.f;
     }
-    for (int jb = j0; jb < j1; jb += per_block) {
-    const int j = jb + (threadIdx.x >> 4);
-    const bool valid = j < j1;
-    float gmu[3] = {0.f, 0.f, 0.f}, GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float gc = 0.f, glog = 0.f;
-    if (valid) {
+    auto ro = [&](int j) { return min(a.rec_off[j], a.cap_rec); };
+    auto chain = [&](int r, int j, float v[11]) {
         const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
         const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
         const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
-        const int r_end = min(a.rec_off[j + 1], a.cap_rec);
-        for (int r = a.rec_off[j] + hl; r < r_end; r += 16)
-            record_chain(a, r, g0, g1, mu, Sg, gmu, GS, gc, glog, pacc, w0);
-    }
-    float v[11] = {gmu[0], gmu[1], gmu[2], GS[0], GS[1], GS[2], GS[3], GS[4], GS[5], gc, glog};
-#pragma unroll
-    for (int k = 0; k < 11; ++k)
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (valid && hl == 0) {
-        // Sigma_j = Rj diag(s^2) Rj^T -> ls, q (through q / |q|)
-        const float GSm[9] = {v[3], v[6], v[7], v[6], v[4], v[8], v[7], v[8], v[5]};
-        const float qw = a.theta[6 * N + j], qx = a.theta[7 * N + j], qy = a.theta[8 * N + j], qz = a.theta[9 * N + j];
-        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
-        float Rj[9];
-        quat_rot(w, x, y, z, Rj);
-        const float s2[3] = {expf(2.f * a.theta[3 * N + j]), expf(2.f * a.theta[4 * N + j]),
-                             expf(2.f * a.theta[5 * N + j])};
-        float GRj[9];  // GS Rj
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q)
-                GRj[3 * p + q] = GSm[3 * p] * Rj[q] + GSm[3 * p + 1] * Rj[3 + q] + GSm[3 * p + 2] * Rj[6 + q];
-        float dls[3];
-        for (int k = 0; k < 3; ++k) {
-            const float d = Rj[k] * GRj[k] + Rj[3 + k] * GRj[3 + k] + Rj[6 + k] * GRj[6 + k];
-            dls[k] = 2.f * s2[k] * d + v[10];
+        record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0);
+    };
+    for (int ja = j0; ja < j1;) {
+        __syncthreads();  // rows and s_jb of the previous round are free
+        if (tid == 0) {
+            const int base = ro(ja);
+            int lo = ja + 1, hi = j1;  // largest jb with records [ro(ja), ro(jb)) <= 256
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ro(mid) - base <= 256) lo = mid;
+                else hi = mid - 1;
+            }
+            s_jb = lo;
         }
-        float GRD[9];  // dL/dRj = 2 GS Rj D
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) GRD[3 * p + q] = 2.f * GRj[3 * p + q] * s2[q];
-        const float dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
-        const float dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
-        const float dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
-        const float dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
-        float gq[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int e = 0; e < 9; ++e) {
-            gq[0] += GRD[e] * dRw[e];
-            gq[1] += GRD[e] * dRx[e];
-            gq[2] += GRD[e] * dRy[e];
-            gq[3] += GRD[e] * dRz[e];
+        __syncthreads();
+        const int jb = s_jb;
+        const int rb = ro(ja), re = ro(jb);
+        if (re - rb <= 256) {
+            float v[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int r = rb + tid;
+            if (r < re) chain(r, a.cand[r].x, v);
+#pragma unroll
+            for (int e = 0; e < 11; ++e) rows[tid][e] = v[e];
+            __syncthreads();
+            const int j = ja + tid;
+            if (j < jb) {
+                float sum[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const int e1 = ro(j + 1) - rb;
+                for (int rr = ro(j) - rb; rr < e1; ++rr)
+#pragma unroll
+                    for (int e = 0; e < 11; ++e) sum[e] += rows[rr][e];
+                gauss_epilogue(a, j, sum);
+            }
+        } else {
+            float v[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int r = rb + tid; r < re; r += blockDim.x) chain(r, ja, v);
+#pragma unroll
+            for (int e = 0; e < 11; ++e) rows[tid][e] = v[e];
+            for (int o = 128; o > 0; o >>= 1) {
+                __syncthreads();
+                if (tid < o)
+#pragma unroll
+                    for (int e = 0; e < 11; ++e) rows[tid][e] += rows[tid + o][e];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float sum[11];
+#pragma unroll
+                for (int e = 0; e < 11; ++e) sum[e] = rows[0][e];
+                gauss_epilogue(a, ja, sum);
+            }
         }
-        const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
-        float *g = a.grad;
-        g[j] = v[0];
-        g[N + j] = v[1];
-        g[2 * N + j] = v[2];
-        g[3 * N + j] = dls[0];
-        g[4 * N + j] = dls[1];
-        g[5 * N + j] = dls[2];
-        g[6 * N + j] = (gq[0] - w * dot) / qn;
-        g[7 * N + j] = (gq[1] - x * dot) / qn;
-        g[8 * N + j] = (gq[2] - y * dot) / qn;
-        g[9 * N + j] = (gq[3] - z * dot) / qn;
-        g[10 * N + j] = v[9];
-    }
+        ja = jb;
     }
     if (pacc) {
         __syncthreads();
-        for (int e = threadIdx.x; e < (w1 - w0) * 12; e += blockDim.x) {
+        for (int e = tid; e < (w1 - w0) * 12; e += blockDim.x) {
             const float val = pacc[e];
             if (val != 0.f) atomicAdd(&a.pose_acc[12 * w0 + e], (double)val);
         }
@@ -1376,8 +1425,7 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
     // the widest slice window of any block (the kernel's chunking, on the host)
     int widest = a.M;
     if (a.gauss_subject && a.h_gauss_first && a.h_slice_first && a.n_subj > 1) {
-        const int per_block = 256 >> 4;
-        const int chunk = ((a.N + blocks - 1) / blocks + per_block - 1) / per_block * per_block;
+        const int chunk = (a.N + blocks - 1) / blocks;
         auto subject_of = [&](int64_t j) {
             return (int)(std::upper_bound(a.h_gauss_first, a.h_gauss_first + a.n_subj + 1, j) - a.h_gauss_first) - 1;
         };

@@ -80,6 +80,7 @@ struct GradArgs {
     const SliceDev *slices;
     const Rec *rec;            // j-major records, slot b.w = slice index
     const int *rec_off;        // N + 1
+    const int2 *cand;          // (Gaussian, slice) per record
     const int *key_off;        // n_rec + 1
     const float4 *mom;         // 2 per key in emit order
     const uint32_t *keys;      // tile id per key in emit order (n_tiles = sentinel)

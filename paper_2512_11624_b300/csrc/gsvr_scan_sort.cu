@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 
 // GATHER: instead of the values, write the tile-ordered record rec[key_rec[value]]
 // (its last word replaced by the value, i.e. the key's emit index) to trec.
+// The block first orders its tile by digit in shared memory (stable), then
+// writes each digit's run to its global range with consecutive threads on
+// consecutive addresses (coalesced stores).
 template <bool GATHER>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                                 uint32_t *kout, uint32_t *vout, const int *d_n,
@@ -139,6 +142,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
                                                                 Rec *trec) {
     constexpr int NW = kSortThreads / 32;
     __shared__ int cnt[NW][256];
+    __shared__ int dstart[256];
+    __shared__ uint32_t skey[kSortTile], sval[kSortTile];
     const int n = min(*d_n, n_max);
     const int base = blockIdx.x * kSortTile;
     if (base >= n) return;
@@ -168,29 +173,41 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, per digit
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+    // per digit: exclusive prefix over warps, then the block's digit starts
+    {
+        const int d = threadIdx.x;  // kSortThreads == 256 digits
         int run = 0;
 #pragma unroll
         for (int ww = 0; ww < NW; ++ww) {
-            int c = cnt[ww][d];
+            const int c = cnt[ww][d];
             cnt[ww][d] = run;
             run += c;
         }
+        int total;
+        dstart[d] = block_excl_scan<kSortThreads>(run, total);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (rank[r] < 0) continue;
         const unsigned d = (key[r] >> shift) & 255u;
-        const int pos = hist_scan[d * nb + blockIdx.x] + cnt[w][d] + rank[r];
-        kout[pos] = key[r];
+        const int local = dstart[d] + cnt[w][d] + rank[r];
+        skey[local] = key[r];
+        sval[local] = val[r];
+    }
+    __syncthreads();
+    const int nb_keys = min(kSortTile, n - base);
+    for (int i = threadIdx.x; i < nb_keys; i += kSortThreads) {
+        const uint32_t k = skey[i];
+        const unsigned d = (k >> shift) & 255u;
+        const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
+        kout[pos] = k;
         if (GATHER) {
-            Rec R = rec[key_rec[val[r]]];
-            R.b.w = __int_as_float((int)val[r]);
+            Rec R = rec[key_rec[sval[i]]];
+            R.b.w = __int_as_float((int)sval[i]);
             trec[pos] = R;
         } else {
-            vout[pos] = val[r];
+            vout[pos] = sval[i];
         }
     }
 }

@@ -68,7 +68,7 @@ def test_bf16_rounding():
 
 
 def tiny_net(rng, channels=(1, 2, 3), hidden=4, aux=3):
-    shapes = cnn.param_shapes(list(channels), hidden, aux, 6)
+    shapes = cnn.param_shapes(list(channels), hidden, aux, 6, positions=4)
     p = {name: rng.normal(size=shp) * 0.5 for name, shp in shapes}
     return shapes, p
 
@@ -104,7 +104,7 @@ def test_network_matches_torch_autograd_float64():
     a = torch.from_numpy(x)[:, None]
     for l in range(1, 4):
         a = F.relu(F.conv2d(a, tp["conv%d.w" % l].permute(0, 3, 1, 2), tp["conv%d.b" % l], stride=2, padding=1))
-    f = a.mean(dim=(2, 3))
+    f = a.permute(0, 2, 3, 1).reshape(a.shape[0], -1)  # position-major flatten of the NHWC map
     h = torch.cat([f, torch.from_numpy(aux)], 1)
     o = F.relu(h @ tp["fc1.w"].T + tp["fc1.b"]) @ tp["fc2.w"].T + tp["fc2.b"]
     Lt = ((o - torch.from_numpy(tgt)) ** 2).mean()
@@ -119,4 +119,4 @@ def test_architecture_parameter_count():
     shapes = cnn.param_shapes()
     conv = sum(int(np.prod(s)) for n, s in shapes if n.startswith("conv"))
     assert conv == 2158080  # six 3x3 conv layers 1-32-64-128-256-256-512 with biases
-    assert sum(int(np.prod(s)) for _, s in shapes) == conv + 537 * 256 + 256 + 256 * 6 + 6
+    assert sum(int(np.prod(s)) for _, s in shapes) == conv + (2048 + 25) * 256 + 256 + 256 * 6 + 6
