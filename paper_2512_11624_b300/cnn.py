@@ -230,9 +230,12 @@ class SliceRenderer:
         return self.render_gaussians(theta_g, N, motion)
 
     def render_gaussians(self, theta_g, N, motion):
-        gsvr.gsvr_set_gaussians(self.ctx.ctx, N, np.asarray(theta_g, np.float32))
+        import torch
+        self.ctx.set_gaussians(np.asarray(theta_g, np.float32), N)
         gsvr.gsvr_set_poses(self.ctx.ctx, np.asarray(motion, np.float32).reshape(-1))
         gsvr.gsvr_forward(self.ctx.ctx)
+        # the forward runs on the renderer's stream: order the caller's stream after it
+        torch.cuda.current_stream(self.stream.device).wait_stream(self.stream)
         img = self.ctx.pred.reshape(self.M, IMAGE, IMAGE).clone()
         return img
 

@@ -445,7 +445,13 @@ def device_view(ptr, n, dtype="float32", device=0):
 
 class Context:
     """Owning wrapper: one gsvr context set up from a case dictionary
-    (``stacks``, ``N``, ``theta``, ``I``, ``mask``) as made by the input generators."""
+    (``stacks``, ``N``, ``theta``, ``I``, ``mask``) as made by the input generators.
+
+    ``theta``, ``grad``, ``pred``, ``rbar``, ``loss_t`` are zero-copy views of
+    context-owned buffers, written on the context's stream: with a stream of
+    its own, order the reading stream after it (``wait_stream``) or call
+    ``gsvr_sync_status`` first.  Changing the Gaussian count reallocates the
+    parameter buffers: use ``set_gaussians``, which refreshes the views."""
 
     def __init__(self, case, device=0, stream=None, **cfg):
         self.device = device
@@ -458,14 +464,23 @@ class Context:
         gsvr_set_gaussians(self.ctx, self.N, th[:11 * self.N])
         self.M = int(sum(s["n_slices"] for s in self.stacks))
         gsvr_set_poses(self.ctx, th[11 * self.N:11 * self.N + 6 * self.M])
+        self.refresh_views()
+
+    def refresh_views(self):
         v = gsvr_get_views(self.ctx)
         self.n_params = int(v.n_params)
         self.n_pixels = int(v.n_pixels)
-        self.theta = device_view(v.theta, v.n_params, device=device)
-        self.grad = device_view(v.grad, v.n_params, device=device)
-        self.pred = device_view(v.pred, v.n_pixels, device=device)
-        self.rbar = device_view(v.rbar, v.n_pixels, device=device)
-        self.loss_t = device_view(v.loss, 1, "float64", device=device)
+        self.theta = device_view(v.theta, v.n_params, device=self.device)
+        self.grad = device_view(v.grad, v.n_params, device=self.device)
+        self.pred = device_view(v.pred, v.n_pixels, device=self.device)
+        self.rbar = device_view(v.rbar, v.n_pixels, device=self.device)
+        self.loss_t = device_view(v.loss, 1, "float64", device=self.device)
+
+    def set_gaussians(self, theta_g, N):
+        """Replace the Gaussians (11 N floats, host or device); poses are kept."""
+        gsvr_set_gaussians(self.ctx, int(N), theta_g)
+        self.N = int(N)
+        self.refresh_views()
 
     def forward(self):
         gsvr_forward(self.ctx)
