@@ -85,8 +85,10 @@ struct gsvr_ctx {
     DBuf<int> d_flags, d_flag_pos, d_sampled, d_tile_px_start, d_tile_px_end, d_idx;
 
     // binning
+    DBuf<unsigned> d_rec_mask;
     DBuf<int> d_rec_cnt, d_rec_off, d_rec_nkeys, d_key_off, d_key_rec, d_tile_rec_start, d_tile_rec_end;
-    DBuf<Rec> d_rec, d_trec;
+    DBuf<Rec> d_rec;
+    DBuf<int2> d_tref;
     DBuf<int2> d_rec_tiles, d_cand;
     DBuf<uint32_t> d_keys, d_keys_sorted, d_vals_sorted, d_keys_alt, d_vals_alt;
     DBuf<int> d_hist, d_scan_bsum;
@@ -205,6 +207,7 @@ gsvr_status ensure_rec_capacity(gsvr_ctx *ctx, int64_t want) {
     CK(ctx->d_rec_tiles.ensure(cap));
     CK(ctx->d_cand.ensure(cap));
     CK(ctx->d_rec_nkeys.ensure(cap));
+    CK(ctx->d_rec_mask.ensure(cap));
     CK(ctx->d_key_off.ensure((size_t)cap + 1));
     ctx->cap_rec = cap;
     CK(ensure_scan_scratch(ctx));
@@ -221,7 +224,7 @@ gsvr_status ensure_key_capacity(gsvr_ctx *ctx, int64_t want) {
     CK(ctx->d_vals_sorted.ensure(cap));
     CK(ctx->d_keys_alt.ensure(cap));
     CK(ctx->d_vals_alt.ensure(cap));
-    CK(ctx->d_trec.ensure(cap));
+    CK(ctx->d_tref.ensure((size_t)cap + 2));
     CK(ctx->d_mom.ensure((size_t)cap * 2));
     CK(ctx->d_hist.ensure((size_t)256 * sort_blocks(cap) + 1));
     ctx->cap_keys = cap;
@@ -255,7 +258,8 @@ gsvr_status ensure_item_capacity(gsvr_ctx *ctx) {
 
 EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     EvalArgs e{};
-    e.trec = ctx->d_trec.p;
+    e.tref = ctx->d_tref.p;
+    e.rec = ctx->d_rec.p;
     e.tile_rec_start = ctx->d_tile_rec_start.p;
     e.tile_rec_end = ctx->d_tile_rec_end.p;
     e.tile_px_start = ctx->d_tile_px_start.p;
@@ -1007,6 +1011,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.rec = ctx->d_rec.p;
     b.rec_tiles = ctx->d_rec_tiles.p;
     b.rec_nkeys = ctx->d_rec_nkeys.p;
+    b.rec_mask = ctx->d_rec_mask.p;
     b.cap_rec = ctx->cap_rec;
     launch_cand_emit(b, st);
     launch_records(b, n_rec_max, st);
@@ -1029,6 +1034,8 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     k.rec = ctx->d_rec.p;
     k.rec_tiles = ctx->d_rec_tiles.p;
     k.rec_nkeys = ctx->d_rec_nkeys.p;
+    k.rec_mask = ctx->d_rec_mask.p;
+    k.mom = ctx->d_mom.p;
     k.key_off = ctx->d_key_off.p;
     k.slices = ctx->d_slices.p;
     k.tile_px_start = ctx->d_tile_px_start.p;
@@ -1048,7 +1055,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     SortScratch ss{ctx->d_keys_alt.p, ctx->d_vals_alt.p, ctx->d_hist.p, scan_scratch(ctx)};
     if (n_keys_max > 0)
         CK(radix_sort_pairs(ctx->d_keys.p, nullptr, ctx->d_keys_sorted.p, ctx->d_vals_sorted.p, &cnt->n_keys,
-                            n_keys_max, ctx->sort_bits, ss, st, ctx->d_rec.p, ctx->d_key_rec.p, ctx->d_trec.p));
+                            n_keys_max, ctx->sort_bits, ss, st, ctx->d_key_rec.p, ctx->d_tref.p));
     CK(cudaMemsetAsync(ctx->d_tile_rec_start.p, 0, sizeof(int) * ctx->n_tiles, st));
     CK(cudaMemsetAsync(ctx->d_tile_rec_end.p, 0, sizeof(int) * ctx->n_tiles, st));
     launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->n_tiles, ctx->d_tile_rec_start.p,

@@ -146,11 +146,10 @@ struct SortScratch {
 int sort_blocks(int n_max);
 // Stable LSD radix sort of n u32 keys (only the low `bits` bits are used) with
 // u32 values; vals_in == null means values are the identity 0..n-1.  Result in
-// keys_out / vals_out; when `rec` is given the last pass writes, instead of the
-// values, trec[pos] = rec[key_rec[value]] with its last word set to the value.
+// keys_out / vals_out; when `tref` is given the last pass writes, instead of the
+// values, tref[pos] = (key_rec[value], value).
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                              uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
-                             cudaStream_t st, const Rec *rec = nullptr, const int *key_rec = nullptr,
-                             Rec *trec = nullptr);
+                             cudaStream_t st, const int *key_rec = nullptr, int2 *tref = nullptr);
 
 }  // namespace gsvr

@@ -227,11 +227,20 @@ __device__ __forceinline__ bool tile_live(const Rec &R, const SliceDev &S, int t
     return rect_max_exponent(R, x0, x1, y0, y1) >= qcut;
 }
 
+// Live tiles of a record's box; mask gets their row-major bits when the box
+// has at most 32 tiles (else 0).
 __device__ __forceinline__ int count_live_tiles(const Rec &R, const SliceDev &S, int tx0, int tx1, int ty0, int ty1,
-                                                int tw, int th, const int *tps, const int *tpe, float qcut) {
-    int n = 0;
+                                                int tw, int th, const int *tps, const int *tpe, float qcut,
+                                                unsigned &mask) {
+    int n = 0, b = 0;
+    const bool fits = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
+    mask = 0u;
     for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) n += tile_live(R, S, tx, ty, tw, th, tps, tpe, qcut) ? 1 : 0;
+        for (int tx = tx0; tx <= tx1; ++tx, ++b)
+            if (tile_live(R, S, tx, ty, tw, th, tps, tpe, qcut)) {
+                ++n;
+                if (fits) mask |= 1u << b;
+            }
     return n;
 }
 
@@ -495,6 +504,7 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
     R.a = make_float4(0.f, 0.f, -1.f, 0.f);
     R.b = make_float4(-1.f, 0.f, -INFINITY, __int_as_float(max(i, 0)));
     int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0, nk = 0;
+    unsigned mask = 0u;
     if (ok) {
         const SliceDev &S = a.slices[i];
         const float mu[3] = {a.theta[j], a.theta[a.N + j], a.theta[2 * a.N + j]};
@@ -507,12 +517,13 @@ __global__ void __launch_bounds__(128) k_records(BinArgs a) {
             R.a = make_float4(G.cb, G.ca, L * G.P2xx * S.dx * S.dx, 2.f * L * G.P2xy * S.dx * S.dy);
             R.b = make_float4(L * G.P2yy * S.dy * S.dy, g1.w * G.w0, L * G.qz, __int_as_float(i));
             nk = count_live_tiles(R, S, tx0, tx1, ty0, ty1, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end,
-                                  a.qcut);
+                                  a.qcut, mask);
         }
     }
     a.rec[c] = R;
     a.rec_tiles[c] = make_int2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
     a.rec_nkeys[c] = nk;
+    a.rec_mask[c] = mask;
 }
 
 // Keys of one record: exactly the count its record pass found, in row-major
@@ -523,17 +534,22 @@ __global__ void k_key_emit(KeyArgs a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_rec = min(*a.n_rec, a.cap_rec);
     if (r >= n_rec) return;
+    const int k0 = a.key_off[r];
+    const int k1 = k0 + a.rec_nkeys[r];
+    if (k1 <= k0) return;
     const Rec R = a.rec[r];
     const int i = __float_as_int(R.b.w);
     const SliceDev &S = a.slices[i];
     const int2 tb = a.rec_tiles[r];
     const int tx0 = tb.x & 0xffff, tx1 = tb.x >> 16, ty0 = tb.y & 0xffff, ty1 = tb.y >> 16;
-    const int k0 = a.key_off[r];
-    const int k1 = k0 + a.rec_nkeys[r];
+    unsigned mask = a.rec_mask[r];
     int k = k0;
-    for (int ty = ty0; ty <= ty1 && k < k1; ++ty)
-        for (int tx = tx0; tx <= tx1 && k < k1; ++tx) {
-            if (!tile_live(R, S, tx, ty, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut)) continue;
+    if (mask) {  // the record pass's tile tests, row-major bits of the box
+        const int wx = tx1 - tx0 + 1;
+        while (mask && k < k1) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const int ty = ty0 + b / wx, tx = tx0 + (b - (b / wx) * wx);
             if (k < a.cap_keys) {
                 a.keys[k] = (uint32_t)(S.tile_base + ty * S.tiles_x + tx);
                 a.key_rec[k] = r;
@@ -542,9 +558,26 @@ __global__ void k_key_emit(KeyArgs a) {
             }
             ++k;
         }
-    for (; k < k1 && k < a.cap_keys; ++k) {
+    } else {
+        for (int ty = ty0; ty <= ty1 && k < k1; ++ty)
+            for (int tx = tx0; tx <= tx1 && k < k1; ++tx) {
+                if (!tile_live(R, S, tx, ty, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut)) continue;
+                if (k < a.cap_keys) {
+                    a.keys[k] = (uint32_t)(S.tile_base + ty * S.tiles_x + tx);
+                    a.key_rec[k] = r;
+                } else {
+                    atomicOr(a.status, ST_CAPACITY);
+                }
+                ++k;
+            }
+    }
+    for (; k < k1 && k < a.cap_keys; ++k) {  // padding: sentinel tile, zero moments
         a.keys[k] = (uint32_t)a.n_tiles;
         a.key_rec[k] = r;
+        if (a.mom) {
+            a.mom[2 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.mom[2 * k + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
 }
 
@@ -624,6 +657,7 @@ __device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, 
 template <bool COUNT, int PXR>
 __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(128) Rec buf[kItemRecs];
+    __shared__ __align__(16) int2 sref[kItemRecs + 2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
@@ -669,11 +703,15 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
 #pragma unroll
         for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
         if (nrec > 0) {
+            // the item's (record, emit index) list by one bulk copy from a
+            // 16-byte aligned start (an even key index), then the records
+            const int a0 = rs & ~1, off = rs - a0;
+            const int cnt = (nrec + off + 1) & ~1;
             if (threadIdx.x == 0) {
-                const uint32_t bytes = (uint32_t)nrec * (uint32_t)sizeof(Rec);
+                const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(int2);
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bar, bytes);
-                bulk_g2s(&buf[0], a.trec + rs, bytes, &bar);
+                bulk_g2s(&sref[0], a.tref + a0, bytes, &bar);
             }
             const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
             if (!ok) atomicOr(a.status, ST_TIMEOUT);
@@ -683,6 +721,8 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
                 return;
             }
             phase ^= 1u;
+            for (int k = threadIdx.x; k < nrec; k += blockDim.x) buf[k] = a.rec[sref[off + k].x];
+            __syncthreads();
             if (active) {
                 for (int r = g; r < nrec; r += G) {
                     const float4 r0 = buf[r].a;
@@ -789,6 +829,7 @@ __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, flo
 __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
     extern __shared__ float rb[];  // tile_h x tile_w
     __shared__ int s_item;
+    __shared__ int row_lo[32], row_hi[32];  // sampled column range per tile row (lo > hi: none)
     const int n_items = min(*a.n_items, a.cap_items);
     const int tw = a.tile_w;
     for (;;) {
@@ -805,24 +846,39 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
         if (ps >= pe || rs >= re) continue;
         const SliceDev &S = a.slices[a.tile_slice[t]];
         const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+        // this thread's two records: loads issued before the r_bar tile is built
+        const int r0 = rs + threadIdx.x;
+        const int r1 = r0 + kThreads;
+        const bool v0 = r0 < re, v1 = r1 < re;
+        const int2 refA = v0 ? a.tref[r0] : make_int2(0, 0);
+        const int2 refB = v1 ? a.tref[r1] : refA;
+        Rec A, B;
+        if (v0) {
+            A = a.rec[refA.x];
+            B = a.rec[refB.x];
+        }
         for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb[k] = 0.f;
+        if (threadIdx.x < 32) {
+            row_lo[threadIdx.x] = 32;
+            row_hi[threadIdx.x] = -1;
+        }
         __syncthreads();
         for (int s2 = ps + threadIdx.x; s2 < pe; s2 += kThreads) {
             const int p = a.sampled[s2];
             const int loc = p - S.pix_base;
             const int r0 = loc / S.W;
-            rb[(r0 - tg.y0) * tw + (loc - r0 * S.W - tg.x0)] = a.rbar[p];
+            const int rr = r0 - tg.y0, cc = loc - r0 * S.W - tg.x0;
+            rb[rr * tw + cc] = a.rbar[p];
+            atomicMin(&row_lo[rr], cc);
+            atomicMax(&row_hi[rr], cc);
         }
         __syncthreads();
-        const int r0 = rs + threadIdx.x;
-        if (r0 >= re) continue;
-        const int r1 = r0 + kThreads;
-        const bool v1 = r1 < re;
-        const Rec A = a.trec[r0];
-        const Rec B = v1 ? a.trec[r1] : A;
+        if (!v0) continue;
         float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float colf0 = (float)tg.x0 - S.cx0;
         for (int row = 0; row < tg.rows; ++row) {
+            const int c0 = row_lo[row], c1 = row_hi[row];  // rows and columns without samples are skipped
+            if (c0 > c1) continue;
             const float rowf = (float)(tg.y0 + row) - S.cy0;
             const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
             const float cA = A.a.w * dyA, bA = A.b.x * dyA * dyA;
@@ -830,7 +886,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
             const float *rrow = rb + row * tw;
 #pragma unroll 4
-            for (int col = 0; col < tg.cols; ++col) {
+            for (int col = c0; col <= c1; ++col) {
                 const float gg = rrow[col];
                 const float colf = colf0 + (float)col;
                 {
@@ -853,11 +909,11 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             bwd_row_fold(mA, A0, A1, A2, dyA);
             bwd_row_fold(mB, B0, B1, B2, dyB);
         }
-        const int k0 = __float_as_int(A.b.w);
+        const int k0 = refA.y;
         a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
         a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
         if (v1) {
-            const int k1 = __float_as_int(B.b.w);
+            const int k1 = refB.y;
             a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
             a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
         }
@@ -922,7 +978,6 @@ __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const flo
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     const int k_end = min(a.key_off[r + 1], a.cap_keys);
     for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
-        if (a.keys[k] >= (uint32_t)a.n_tiles) continue;  // sentinel key: never evaluated
         const float4 u = a.mom[2 * k], v = a.mom[2 * k + 1];
         S0 += u.x;
         Sx += u.y;
@@ -1279,7 +1334,10 @@ void launch_gauss_prep(const float *theta, int N, float4 *gpre, unsigned *status
 void launch_pose_prep(const float *pose, const SliceStatic *ss, SliceDev *sd, int M, unsigned *status,
                       cudaStream_t st) {
     if (M <= 0) return;
-    k_pose_prep<<<cdiv(M, 128), 128, 0, st>>>(pose, ss, sd, M, status);
+    // float64-bound per slice: spread the slices over the SMs (one per block
+    // while they are fewer than the SMs)
+    const int bs = std::max(1, std::min(128, cdiv(M, 148)));
+    k_pose_prep<<<cdiv(M, bs), bs, 0, st>>>(pose, ss, sd, M, status);
     counted();
 }
 void launch_cand_count(const BinArgs &a, cudaStream_t st) {
@@ -1445,7 +1503,8 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
 void launch_pose_grad(const double *pose_acc, const SliceStatic *ss, const float *pose, float *grad_pose, int M,
                       cudaStream_t st) {
     if (M <= 0) return;
-    k_pose_grad<<<cdiv(M, 64), 64, 0, st>>>(pose_acc, ss, pose, grad_pose, M);
+    const int bs = std::max(1, std::min(64, cdiv(M, 148)));
+    k_pose_grad<<<cdiv(M, bs), bs, 0, st>>>(pose_acc, ss, pose, grad_pose, M);
     counted();
 }
 void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int M, const float lr[6], float b1,

@@ -23,6 +23,7 @@ struct BinArgs {
     Rec *rec;                  // one record per candidate
     int2 *rec_tiles;           // packed tile bounding box per record
     int *rec_nkeys;            // keys per record
+    unsigned *rec_mask;        // live tiles of the box, row-major bits (0 when the box exceeds 32 tiles)
     int cap_rec;
     unsigned *status;
 };
@@ -31,6 +32,7 @@ struct KeyArgs {
     const Rec *rec;
     const int2 *rec_tiles;
     const int *rec_nkeys;      // keys per record (from the record pass)
+    const unsigned *rec_mask;  // live-tile bits of the record pass (0: test again)
     const int *key_off;        // n_rec + 1
     const SliceDev *slices;
     const int *tile_px_start, *tile_px_end;
@@ -40,11 +42,13 @@ struct KeyArgs {
     float qcut;
     uint32_t *keys;
     int *key_rec;
+    float4 *mom;               // backward moments: zeroed here for padding (sentinel) keys
     unsigned *status;
 };
 
 struct EvalArgs {
-    const Rec *trec;           // records in sorted (tile, Gaussian) order, slot b.w = emit index
+    const int2 *tref;          // per sorted key: (record, emit index); capacity + 2 entries
+    const Rec *rec;            // records, Gaussian-major
     const int *tile_rec_start, *tile_rec_end;
     const int *tile_px_start, *tile_px_end;
     const int *tile_slice;

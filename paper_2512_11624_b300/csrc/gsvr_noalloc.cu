@@ -209,9 +209,9 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     Counters *d_cnt = cv.take<Counters>(1);
     const size_t fixed = cv.used();
     // per record: Rec + tile box + key count + key offset; per key: key, key_rec, sorted key and
-    // value, two ping-pong words, tile-ordered record, backward moments (unused here), histogram share
-    const size_t per_rec = sizeof(Rec) + 2 * sizeof(int2) + 2 * sizeof(int);
-    const size_t per_key = 6 * sizeof(uint32_t) + sizeof(Rec) + 1 + (kTile * kTile * sizeof(float)) / kItemRecs + 1;
+    // value, two ping-pong words, (record, emit index) reference, backward moments (unused here), histogram share
+    const size_t per_rec = sizeof(Rec) + 2 * sizeof(int2) + 3 * sizeof(int);
+    const size_t per_key = 6 * sizeof(uint32_t) + sizeof(int2) + 1 + (kTile * kTile * sizeof(float)) / kItemRecs + 1;
     const size_t slack = 64 * 256 + 4096 * sizeof(int) + (size_t)(2 * T + 8) * (sizeof(int) + kTile * kTile * sizeof(float));
     if (fixed + slack + per_rec + kKeysPerRecord * per_key >= kScratchBytes) {
         set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch");
@@ -224,6 +224,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     int2 *d_rec_tiles = cv.take<int2>(cap_rec);
     int2 *d_cand = cv.take<int2>(cap_rec);
     int *d_rec_nkeys = cv.take<int>(cap_rec);
+    unsigned *d_rec_mask = cv.take<unsigned>(cap_rec);
     int *d_key_off = cv.take<int>((size_t)cap_rec + 1);
     uint32_t *d_keys = cv.take<uint32_t>(cap_keys);
     int *d_key_rec = cv.take<int>(cap_keys);
@@ -231,7 +232,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     uint32_t *d_vs = cv.take<uint32_t>(cap_keys);
     uint32_t *d_ka = cv.take<uint32_t>(cap_keys);
     uint32_t *d_va = cv.take<uint32_t>(cap_keys);
-    Rec *d_trec = cv.take<Rec>(cap_keys);
+    int2 *d_tref = cv.take<int2>((size_t)cap_keys + 2);
     int *d_hist = cv.take<int>((size_t)256 * sort_blocks(cap_keys) + 1);
     const int cap_items = (int)(T + cap_keys / kItemRecs + 2);
     int *d_item_cnt = cv.take<int>(T + 1);
@@ -312,6 +313,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     b.rec = d_rec;
     b.rec_tiles = d_rec_tiles;
     b.rec_nkeys = d_rec_nkeys;
+    b.rec_mask = d_rec_mask;
     b.cap_rec = cap_rec;
     launch_cand_emit(b, st);
     launch_records(b, cap_rec, st);
@@ -320,6 +322,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     k.rec = d_rec;
     k.rec_tiles = d_rec_tiles;
     k.rec_nkeys = d_rec_nkeys;
+    k.rec_mask = d_rec_mask;
     k.key_off = d_key_off;
     k.slices = d_sl;
     k.tile_px_start = d_tps;
@@ -338,14 +341,15 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     int bits = 1;
     while ((1LL << bits) < T + 1) ++bits;
     const SortScratch sort_s{d_ka, d_va, d_hist, scs};
-    NA_CK(radix_sort_pairs(d_keys, nullptr, d_ks, d_vs, &d_cnt->n_keys, cap_keys, bits, sort_s, st, d_rec, d_key_rec,
-                           d_trec));
+    NA_CK(radix_sort_pairs(d_keys, nullptr, d_ks, d_vs, &d_cnt->n_keys, cap_keys, bits, sort_s, st, d_key_rec,
+                           d_tref));
     launch_tile_rec_ranges(d_ks, &d_cnt->n_keys, cap_keys, (int)T, d_trs, d_tre, st);
     launch_items(d_tps, d_tpe, d_trs, d_tre, (int)T, d_item_cnt, nullptr, nullptr, 0, 0, st);
     NA_CK(scan_exclusive(d_item_cnt, d_item_first, nullptr, (int)T, (int)T, &d_cnt->n_items, scs, st));
     launch_items(nullptr, nullptr, nullptr, nullptr, (int)T, nullptr, d_item_first, d_item_tile, cap_items, 1, st);
     EvalArgs e{};
-    e.trec = d_trec;
+    e.tref = d_tref;
+    e.rec = d_rec;
     e.tile_rec_start = d_trs;
     e.tile_rec_end = d_tre;
     e.tile_px_start = d_tps;

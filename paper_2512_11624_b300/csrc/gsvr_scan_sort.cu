@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
     for (int d = threadIdx.x; d < 256; d += kSortThreads) hist[d * nb + blockIdx.x] = cnt[d];
 }
 
-// GATHER: instead of the values, write the tile-ordered record rec[key_rec[value]]
-// (its last word replaced by the value, i.e. the key's emit index) to trec.
+// GATHER: instead of the values, write tref[pos] = (key_rec[value], value): the
+// record of the key and the key's emit index, in sorted (tile) order.
 // The block first orders its tile by digit in shared memory (stable), then
 // writes each digit's run to its global range with consecutive threads on
 // consecutive addresses (coalesced stores).
@@ -138,8 +138,7 @@ template <bool GATHER>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                                 uint32_t *kout, uint32_t *vout, const int *d_n,
                                                                 int n_max, int shift, const int *hist_scan,
-                                                                int nb, const Rec *rec, const int *key_rec,
-                                                                Rec *trec) {
+                                                                int nb, const int *key_rec, int2 *tref) {
     constexpr int NW = kSortThreads / 32;
     __shared__ int cnt[NW][256];
     __shared__ int dstart[256];
@@ -197,17 +196,37 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     }
     __syncthreads();
     const int nb_keys = min(kSortTile, n - base);
-    for (int i = threadIdx.x; i < nb_keys; i += kSortThreads) {
-        const uint32_t k = skey[i];
-        const unsigned d = (k >> shift) & 255u;
-        const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
-        kout[pos] = k;
-        if (GATHER) {
-            Rec R = rec[key_rec[sval[i]]];
-            R.b.w = __int_as_float((int)sval[i]);
-            trec[pos] = R;
-        } else {
+    if (!GATHER) {
+        for (int i = threadIdx.x; i < nb_keys; i += kSortThreads) {
+            const uint32_t k = skey[i];
+            const unsigned d = (k >> shift) & 255u;
+            const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
+            kout[pos] = k;
             vout[pos] = sval[i];
+        }
+        return;
+    }
+    // gather: four independent key -> record lookups in flight per thread
+    constexpr int G = 4;
+    for (int i0 = threadIdx.x; i0 < nb_keys; i0 += G * kSortThreads) {
+        uint32_t v[G];
+        int kr[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = i0 + q * kSortThreads;
+            v[q] = i < nb_keys ? sval[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) kr[q] = i0 + q * kSortThreads < nb_keys ? key_rec[v[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int i = i0 + q * kSortThreads;
+            if (i >= nb_keys) continue;
+            const uint32_t k = skey[i];
+            const unsigned d = (k >> shift) & 255u;
+            const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
+            kout[pos] = k;
+            tref[pos] = make_int2(kr[q], (int)v[q]);
         }
     }
 }
@@ -230,7 +249,7 @@ int sort_blocks(int n_max) { return n_max <= 0 ? 1 : (n_max + kSortTile - 1) / k
 
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                              uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
-                             cudaStream_t st, const Rec *rec, const int *key_rec, Rec *trec) {
+                             cudaStream_t st, const int *key_rec, int2 *tref) {
     const int nb = sort_blocks(n_max);
     const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
     const uint32_t *ksrc = keys_in;
@@ -243,12 +262,12 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
         k_radix_hist<<<nb, kSortThreads, 0, st>>>(ksrc, d_n, n_max, shift, s.hist, nb);
         cudaError_t e = scan_exclusive(s.hist, s.hist, nullptr, 256 * nb, 256 * nb, nullptr, s.scan, st);
         if (e != cudaSuccess) return e;
-        if (rec && p == passes - 1)
+        if (tref && p == passes - 1)
             k_radix_scatter<true><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
-                                                               nb, rec, key_rec, trec);
+                                                               nb, key_rec, tref);
         else
             k_radix_scatter<false><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
-                                                                nb, nullptr, nullptr, nullptr);
+                                                                nb, nullptr, nullptr);
         note_launches(2);
         ksrc = kdst;
         vsrc = vdst;
