@@ -654,94 +654,164 @@ __device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, 
 // The groups' sums meet in shared memory; part[item][pixel] holds the item's
 // sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
 // (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Work item w (queue position) -> item, tile, first record and record count.
+struct ItemRef {
+    int i, t, rs, nrec;
+};
+__device__ __forceinline__ ItemRef item_ref(const EvalArgs &a, int w) {
+    ItemRef r;
+    r.i = a.item_order ? (int)a.item_order[w] : w;
+    r.t = a.item_tile[r.i];
+    r.rs = a.tile_rec_start[r.t] + (r.i - a.item_first[r.t]) * kItemRecs;
+    r.nrec = max(0, min(kItemRecs, a.tile_rec_end[r.t] - r.rs));
+    return r;
+}
+
+// Persistent CTAs take work items from a queue (Counters::work_fwd) and run a
+// software pipeline over them: while item n is evaluated, the records of item
+// n + 1 are in flight into shared memory (cp.async, 16 bytes at a time, through
+// the item's (record, emit index) references) and the reference list of item
+// n + 2 is in flight by one bulk copy (cp.async.bulk, mbarrier completion,
+// bounded wait).  The CTA is G groups of threads; in a group each thread owns
+// a run of PXR consecutive pixels of one tile row, and the groups split the
+// records (every lane of a warp reads the same record: a broadcast).  With the
+// row fixed, the record's row terms C2 da and B da^2 are formed once per PXR
+// pixels:
+//   q = (A db + C2 da) db + B da^2,   sum += w exp2(q).
+// The groups' sums meet in shared memory; part[item][pixel] holds the item's
+// sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
+// (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
 template <bool COUNT, int PXR>
 __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
-    __shared__ __align__(128) Rec buf[kItemRecs];
-    __shared__ __align__(16) int2 sref[kItemRecs + 2];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(128) Rec buf[2][kItemRecs];
+    __shared__ __align__(16) int2 sref[3][kItemRecs + 2];
+    __shared__ __align__(8) uint64_t bar[3];
     __shared__ float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
-    __shared__ int s_item;
+    __shared__ int s_w[3], s_off[3], s_nrec[3], s_pend[3];
+    __shared__ int s_fail;
     const int n_items = min(*a.n_items, a.cap_items);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) {
+            mbar_init(&bar[k], 1);
+            s_pend[k] = 0;
+        }
         fence_mbar_init();
+        s_fail = 0;
     }
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // bit k: parity of bar[k]'s next completion
     unsigned long long useful = 0;
     const int segs = (a.tile_w + PXR - 1) / PXR;
     const int tpg = a.tile_h * segs;
     const int G = max(1, (int)blockDim.x / tpg);
-    const int g = threadIdx.x / tpg, seg = threadIdx.x - g * tpg;
+    const int g = tid / tpg, seg = tid - g * tpg;
     const int row = seg / segs, col0 = (seg - row * segs) * PXR;
-    for (;;) {
-        __syncthreads();  // previous item's buffers are free
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_fwd, 1);
-        __syncthreads();
-        if (s_item >= n_items) break;
-        const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
-        const int t = a.item_tile[i];
-        const int c = i - a.item_first[t];
-        const int rs = a.tile_rec_start[t] + c * kItemRecs;
-        const int nrec = max(0, min(kItemRecs, a.tile_rec_end[t] - rs));
-        const SliceDev &S = a.slices[a.tile_slice[t]];
-        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+    // thread 0: take the next queue position into ring slot `slot` and start
+    // the bulk copy of its references
+    auto take = [&](int slot) {
+        const int w = atomicAdd(&a.counters->work_fwd, 1);
+        s_w[slot] = w;
+        s_nrec[slot] = 0;
+        s_off[slot] = 0;
+        if (w >= n_items) return;
+        const ItemRef ir = item_ref(a, w);
+        s_nrec[slot] = ir.nrec;
+        if (ir.nrec <= 0) return;
+        const int a0 = ir.rs & ~1, off = ir.rs - a0;
+        const int cnt = (ir.nrec + off + 1) & ~1;
+        s_off[slot] = off;
+        s_pend[slot] = 1;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[slot], (uint32_t)cnt * (uint32_t)sizeof(int2));
+        bulk_g2s(&sref[slot][0], a.tref + a0, (uint32_t)cnt * (uint32_t)sizeof(int2), &bar[slot]);
+    };
+    // all threads: wait for slot's references, then start its record copies into buf[b]
+    auto gather = [&](int slot, int b) -> bool {
+        const int nrec = s_nrec[slot];
+        if (nrec > 0) {
+            const bool ok = mbar_wait_bounded(&bar[slot], (phase >> slot) & 1u, kWaitLimitNs);
+            if (!ok) {
+                atomicOr(a.status, ST_TIMEOUT);
+                s_fail = 1;
+                return false;
+            }
+            phase ^= 1u << slot;
+            if (tid == 0) s_pend[slot] = 0;
+            const int off = s_off[slot];
+            for (int k = tid; k < 2 * nrec; k += blockDim.x) {
+                const int r = k >> 1, h = k & 1;
+                const Rec *src = a.rec + sref[slot][off + r].x;
+                cp_async16(reinterpret_cast<float4 *>(&buf[b][r]) + h, reinterpret_cast<const float4 *>(src) + h);
+            }
+        }
+        cp_async_commit();
+        return true;
+    };
+    __syncthreads();
+    if (tid == 0) {
+        take(0);
+        take(1);
+    }
+    __syncthreads();
+    gather(0, 0);
+    for (int n = 0;; ++n) {
+        __syncthreads();  // item n - 1 is done: its record buffer and red are free
+        const int cur = n % 3, nxt = (n + 1) % 3;
+        if (s_fail || s_w[cur] >= n_items) break;
+        if (tid == 0) take((n + 2) % 3);
+        gather(nxt, (n + 1) & 1);  // item n + 1 (nothing when the queue is empty)
+        cp_async_wait<1>();        // item n's records have landed (this thread's copies)
+        __syncthreads();           // ... and every thread's
+        if (s_fail) break;
+        const ItemRef ir = item_ref(a, s_w[cur]);
+        const Rec *rb = buf[n & 1];
+        const int nrec = ir.nrec;
+        const SliceDev &S = a.slices[a.tile_slice[ir.t]];
+        const TileGeom tg = tile_geom(S, ir.t, a.tile_w, a.tile_h);
         const bool active = g < G && row < tg.rows;
         const float rowf = (float)(tg.y0 + row) - S.cy0;
         const float colf0 = (float)(tg.x0 + col0) - S.cx0;
         if (COUNT) {
-            const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-            for (int k = threadIdx.x; k < a.tile_px; k += blockDim.x) present[k] = 0;
+            const int ps = a.tile_px_start[ir.t], pe = a.tile_px_end[ir.t];
+            for (int k = tid; k < a.tile_px; k += blockDim.x) present[k] = 0;
             __syncthreads();
-            for (int s2 = ps + threadIdx.x; s2 < pe; s2 += blockDim.x) {
+            for (int s2 = ps + tid; s2 < pe; s2 += blockDim.x) {
                 const int loc = a.sampled[s2] - S.pix_base;
                 const int r0 = loc / S.W;
                 present[(r0 - tg.y0) * a.tile_w + (loc - r0 * S.W - tg.x0)] = 1;
             }
+            __syncthreads();
         }
         float acc[PXR];
 #pragma unroll
         for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
-        if (nrec > 0) {
-            // the item's (record, emit index) list by one bulk copy from a
-            // 16-byte aligned start (an even key index), then the records
-            const int a0 = rs & ~1, off = rs - a0;
-            const int cnt = (nrec + off + 1) & ~1;
-            if (threadIdx.x == 0) {
-                const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(int2);
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar, bytes);
-                bulk_g2s(&sref[0], a.tref + a0, bytes, &bar);
-            }
-            const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
-            if (!ok) atomicOr(a.status, ST_TIMEOUT);
-            if (!__syncthreads_and(ok)) {
-                if (threadIdx.x == 0) mbar_wait_bounded(&bar, phase, kWaitLimitNs);
-                __syncthreads();
-                return;
-            }
-            phase ^= 1u;
-            for (int k = threadIdx.x; k < nrec; k += blockDim.x) buf[k] = a.rec[sref[off + k].x];
-            __syncthreads();
-            if (active) {
-                for (int r = g; r < nrec; r += G) {
-                    const float4 r0 = buf[r].a;
-                    const float4 r1 = buf[r].b;
-                    const float dy = rowf - r0.y;
-                    const float cdy = r0.w * dy;
-                    const float bdy = r1.x * dy * dy;
+        if (active) {
+            for (int r = g; r < nrec; r += G) {
+                const float4 r0 = rb[r].a;
+                const float4 r1 = rb[r].b;
+                const float dy = rowf - r0.y;
+                const float cdy = r0.w * dy;
+                const float bdy = r1.x * dy * dy;
 #pragma unroll
-                    for (int k = 0; k < PXR; ++k) {
-                        const float dx = (colf0 + (float)k) - r0.x;
-                        const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
-                        if (!COUNT) {
-                            acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
-                        } else {
-                            const int col = col0 + k;
-                            useful += (col < tg.cols && present[row * a.tile_w + col] && q + r1.z >= a.qcut)
-                                          ? 1ull
-                                          : 0ull;
-                        }
+                for (int k = 0; k < PXR; ++k) {
+                    const float dx = (colf0 + (float)k) - r0.x;
+                    const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
+                    if (!COUNT) {
+                        acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
+                    } else {
+                        const int col = col0 + k;
+                        useful += (col < tg.cols && present[row * a.tile_w + col] && q + r1.z >= a.qcut) ? 1ull
+                                                                                                       : 0ull;
                     }
                 }
             }
@@ -754,16 +824,23 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
                 if (col0 + k < a.tile_w) red[g * a.tile_px + row * a.tile_w + col0 + k] = acc[k];
         }
         __syncthreads();
-        for (int px = threadIdx.x; px < a.tile_px; px += blockDim.x) {
+        for (int px = tid; px < a.tile_px; px += blockDim.x) {
             float sum = 0.f;
             for (int gg = 0; gg < G; ++gg) sum += red[gg * a.tile_px + px];
-            a.part[(size_t)i * a.tile_px + px] = sum;
+            a.part[(size_t)ir.i * a.tile_px + px] = sum;
         }
     }
+    // leave no copy in flight: this thread's record copies, then (thread 0)
+    // the outstanding reference copies, each wait bounded
+    cp_async_wait<0>();
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < 3; ++k)
+            if (s_pend[k]) mbar_wait_bounded(&bar[k], (phase >> k) & 1u, kWaitLimitNs);
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) useful += __shfl_down_sync(0xffffffffu, useful, o);
-        if ((threadIdx.x & 31) == 0 && useful) atomicAdd(a.useful, useful);
+        if ((tid & 31) == 0 && useful) atomicAdd(a.useful, useful);
     }
 }
 

@@ -194,7 +194,7 @@ def run_learned(args):
     from .recon import PSNRProbe, Reconstruction
     dev = 0
     torch.cuda.set_device(dev)
-    log = lambda m: print(m, flush=True)
+    log = lambda m: print(m, flush=True)  # noqa: E731
     t0 = time.time()
     X, A, Y = cnn.make_training_set(args.phantoms, motions_per_phantom=args.motions, seed=args.seed, log=log)
     t_data = time.time() - t0
@@ -230,15 +230,22 @@ def run_learned(args):
               "theta": np.concatenate([tmpl_theta, np.zeros(6 * M)]).astype(np.float32), "I": case["I"],
               "mask": case["mask"]}
         tctx = gsvr.Context(tc, tile_h=12, tile_w=12)
+        # candidates per slice: nominal, the network's pose, its translation alone
+        trans_only = np.concatenate([np.zeros((M, 3)), pred[:, 3:]], axis=1)
+        cands = [np.zeros((M, 6)), pred, trans_only]
         ncc = []
-        for poses in (np.zeros((M, 6)), pred):
+        for poses in cands:
             gsvr.gsvr_set_poses(tctx.ctx, poses.astype(np.float32).reshape(-1))
             tctx.forward()
             ncc.append(slice_ncc(tctx.pred.reshape(M, -1), I.reshape(M, -1), msk.reshape(M, -1)))
         tctx.close()
-        use = ((ncc[1] > ncc[0]) & content).cpu().numpy()
-        use[ref] = False
-        init = np.where(use[:, None], pred, 0.0)
+        score = torch.stack(ncc).cpu().numpy()  # [3][M]
+        pick = np.argmax(score, axis=0)
+        cont = content.cpu().numpy()
+        pick[~cont] = 0
+        pick[ref] = 0
+        init = np.stack(cands)[pick, np.arange(M)]
+        use = pick > 0
         torch.cuda.synchronize()
         t_inf = time.perf_counter() - t_inf0
         sel = content.cpu().numpy().copy()
@@ -267,7 +274,9 @@ def run_learned(args):
             rec_out[name]["psnr_final"] = h[-1][2]
             del rec_out[name]["history"]
         row = {"seed": seed, "motion": [deg, mm], "slices_with_content": int(sel.sum()),
-               "fallbacks": int((~use & sel).sum()), "inference_s": t_inf, "target_psnr": target,
+               "fallbacks": int((~use & sel).sum()), "translation_only": int(((pick == 2) & sel).sum()),
+               "inference_s": t_inf, "target_psnr": target,
+               "selected": pose_errors(case["stacks"], init, truth, sel),
                "network": pose_errors(case["stacks"], pred, truth, sel),
                "nominal": pose_errors(case["stacks"], np.zeros((M, 6)), truth, sel), **rec_out}
         out["cases"].append(row)
@@ -282,6 +291,62 @@ def run_learned(args):
     if args.out:
         with open(args.out, "w") as f:
             json.dump(out, f, indent=1)
+    return out
+
+
+def conv_flops_per_slice():
+    """Multiply-adds x 2 of the six conv layers for one 128 x 128 slice (forward)."""
+    ch = [1, 32, 64, 128, 256, 256, 512]
+    f, side = 0, 128
+    for l in range(6):
+        side = (side + 1) // 2
+        f += 2 * side * side * ch[l + 1] * 9 * ch[l]
+    return f
+
+
+def run_cnnbench(args):
+    """Training-step throughput of the pose network on random slices: CUDA
+    events around `steps` steps (forward, loss, backward, Adam) after warm-up;
+    FLOPs = 3 x the conv forward FLOPs (forward, input gradient, weight
+    gradient) + the fc layers' 6 x multiply-adds; against the measured bf16
+    peak (MEASURED_PEAKS.json when present)."""
+    import torch
+    from . import cnn
+    dev = 0
+    torch.cuda.set_device(dev)
+    B = args.batch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((B, 128, 128), device="cuda", generator=g)
+    aux = torch.randn((B, 25), device="cuda", generator=g)
+    tgt = torch.randn((B, 6), device="cuda", generator=g) * 0.3
+    net = cnn.PoseNet(max_batch=B, seed=1)
+    for t in range(1, args.warmup + 1):
+        net.loss_backward(x, aux, tgt)
+        net.adam_step(t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(args.steps):
+        net.loss_backward(x, aux, tgt)
+        net.adam_step(args.warmup + 1 + t)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fc = 2 * B * ((2048 + 25) * 256 + 256 * 6)
+    flops = 3 * B * conv_flops_per_slice() + 3 * fc
+    peak = None
+    try:
+        import os
+        pk = json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                         "MEASURED_PEAKS.json")))
+        peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    except Exception:
+        peak = None
+    tf = flops / (ms / 1e3) / 1e12
+    out = {"batch": B, "ms_per_step": ms, "slices_per_s": B / (ms / 1e3), "tflops": tf, "peak_tflops": peak,
+           "frac": (tf / peak) if peak else None}
+    print(json.dumps(out), flush=True)
+    net.close()
     return out
 
 
@@ -314,8 +379,14 @@ def main():
     lr.add_argument("--eval-every", type=int, default=50)
     lr.add_argument("--workers", type=int, default=8)
     lr.add_argument("--out", default="")
+    cb = sub.add_parser("cnnbench")
+    cb.add_argument("--batch", type=int, default=256)
+    cb.add_argument("--steps", type=int, default=50)
+    cb.add_argument("--warmup", type=int, default=5)
     args = ap.parse_args()
-    if args.cmd == "batched":
+    if args.cmd == "cnnbench":
+        run_cnnbench(args)
+    elif args.cmd == "batched":
         run_batched(args)
     elif args.cmd == "learned":
         run_learned(args)
