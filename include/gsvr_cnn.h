@@ -82,8 +82,9 @@ gsvr_status gsvr_cnn_adam_step(gsvr_cnn *net, float lr, float beta1, float beta2
 
 /* ---- layer primitives (one conv layer 3x3 / stride 2 / pad 1, NHWC) ----
  * Shapes: x [B][H][W][Ci], w [Co][3][3][Ci], y / gy [B][OH][OW][Co] with
- * OH = (H + 1) / 2, OW = (W + 1) / 2.  Ci must be a multiple of 8 (the tensor
- * core path gathers 8 channels at a time), Co a multiple of 2; all pointers
+ * OH = (H + 1) / 2, OW = (W + 1) / 2.  Ci and Co must be multiples of 8 (the
+ * tensor-core path moves 8 channels at a time; the forward and the weight
+ * gradient also take Ci = 1 with Co = 32, the first layer); all pointers
  * device memory, 16-byte aligned.
  *
  * gsvr_cnn_conv_forward: y = bf16(max(conv(x, w) + bias, 0)) when relu, else
@@ -91,16 +92,15 @@ gsvr_status gsvr_cnn_adam_step(gsvr_cnn *net, float lr, float beta1, float beta2
  *   bfloat16 rounding.
  * gsvr_cnn_conv_dgrad: dx = conv^T(gy, w) (the input gradient), times
  *   (mask > 0) elementwise when mask (shape of x) is given; dx (bfloat16)
- *   and dx32 (float32, may be NULL).  dcol: caller scratch of
- *   B * OH * OW * 9 * Ci floats.
+ *   and dx32 (float32, may be NULL).  One GEMM in sub-pixel form: each output
+ *   position feeds its 2 x 2 input pixels through the taps that reach them.
  * gsvr_cnn_conv_wgrad: dw [Co][3][3][Ci] += sum over positions of gy x-patch,
  *   db [Co] += sum of gy (float32, accumulated: zero them first). */
 gsvr_status gsvr_cnn_conv_forward(void *stream, const uint16_t *x, int32_t B, int32_t H, int32_t W, int32_t Ci,
                                   const uint16_t *w, const float *bias, int32_t Co, int32_t relu, uint16_t *y,
                                   float *y32);
 gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int32_t H, int32_t W, int32_t Ci,
-                                const uint16_t *w, int32_t Co, const uint16_t *mask, float *dcol, uint16_t *dx,
-                                float *dx32);
+                                const uint16_t *w, int32_t Co, const uint16_t *mask, uint16_t *dx, float *dx32);
 gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t *x, int32_t B, int32_t H, int32_t W,
                                 int32_t Ci, int32_t Co, float *dw, float *db);
 

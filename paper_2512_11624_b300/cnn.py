@@ -30,7 +30,7 @@ _SIG = {
     "gsvr_cnn_loss_backward": ([_vp, _vp, _vp, _vp, _i32, _vp], C.c_int),
     "gsvr_cnn_adam_step": ([_vp, _f, _f, _f, _f, _i64], C.c_int),
     "gsvr_cnn_conv_forward": ([_vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _i32, _vp, _vp], C.c_int),
-    "gsvr_cnn_conv_dgrad": ([_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp], C.c_int),
+    "gsvr_cnn_conv_dgrad": ([_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp], C.c_int),
     "gsvr_cnn_conv_wgrad": ([_vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp], C.c_int),
 }
 for _name, (_args, _res) in _SIG.items():
@@ -77,11 +77,10 @@ def conv_dgrad(gy, w, H, W, mask=None, stream=None):
     import torch
     B, OH, OW, Co = gy.shape
     Ci = w.shape[3]
-    dcol = torch.empty(B * OH * OW * 9 * Ci, dtype=torch.float32, device=gy.device)
     dx = torch.empty((B, H, W, Ci), dtype=torch.bfloat16, device=gy.device)
     dx32 = torch.empty((B, H, W, Ci), dtype=torch.float32, device=gy.device)
-    _check(None, lib.gsvr_cnn_conv_dgrad(_stream(stream), _dp(gy), B, H, W, Ci, _dp(w), Co, _dp(mask), _dp(dcol),
-                                         _dp(dx), _dp(dx32)))
+    _check(None, lib.gsvr_cnn_conv_dgrad(_stream(stream), _dp(gy), B, H, W, Ci, _dp(w), Co, _dp(mask), _dp(dx),
+                                         _dp(dx32)))
     return dx, dx32
 
 

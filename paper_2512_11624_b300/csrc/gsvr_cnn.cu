@@ -58,7 +58,37 @@ __device__ __forceinline__ uint4 pack8(const bf16 v[8]) {
 
 struct ConvShape {
     int B, H, W, Ci, OH, OW, Co;
+    int lOW, lOH, lCi, lCo;  // log2 of OW, OH, Ci, Co when a power of two, else -1
 };
+
+// m = (b, oh, ow) -> its parts (shifts when the sides are powers of two)
+__device__ __forceinline__ void pos_split(const ConvShape &s, int m, int &b, int &oh, int &ow) {
+    int t;
+    if (s.lOW >= 0) {
+        ow = m & (s.OW - 1);
+        t = m >> s.lOW;
+    } else {
+        t = m / s.OW;
+        ow = m - t * s.OW;
+    }
+    if (s.lOH >= 0) {
+        oh = t & (s.OH - 1);
+        b = t >> s.lOH;
+    } else {
+        b = t / s.OH;
+        oh = t - b * s.OH;
+    }
+}
+// k = (q, c) over C channels -> q, c
+__device__ __forceinline__ void chan_split(int k, int C, int lC, int &q, int &c) {
+    if (lC >= 0) {
+        q = k >> lC;
+        c = k & (C - 1);
+    } else {
+        q = k / C;
+        c = k - q * C;
+    }
+}
 
 // ---------------------------------------------------------------- loaders
 // Each returns the 8 bfloat16 values (row, k0 .. k0 + 7) of its operand;
@@ -71,9 +101,10 @@ struct LoadIm2col {
     int rows, K;
     __device__ uint4 operator()(int m, int k0, int k_end) const {
         if (m >= rows || k0 >= k_end) return zero4();
-        const int tap = k0 / s.Ci, ci = k0 - tap * s.Ci;
-        const int kh = tap / 3, kw = tap - 3 * kh;
-        const int ow = m % s.OW, t = m / s.OW, oh = t % s.OH, b = t / s.OH;
+        int tap, ci, b, oh, ow;
+        chan_split(k0, s.Ci, s.lCi, tap, ci);
+        const int kh = (tap * 11) >> 5, kw = tap - 3 * kh;  // tap / 3 for tap < 9
+        pos_split(s, m, b, oh, ow);
         const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
         if (ih < 0 || ih >= s.H || iw < 0 || iw >= s.W) return zero4();
         return *reinterpret_cast<const uint4 *>(x + (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci);
@@ -90,50 +121,6 @@ struct LoadRows {
     }
 };
 
-// Transposed access: value (r, k) = p[k][r] of a row-major p[.][ld].
-struct LoadCols {
-    const bf16 *p;
-    int rows, ld;
-    __device__ uint4 operator()(int r, int k0, int k_end) const {
-        bf16 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            v[i] = (r < rows && k0 + i < k_end) ? p[(size_t)(k0 + i) * ld + r] : __float2bfloat16(0.f);
-        return pack8(v);
-    }
-};
-
-// Transposed im2col: value (k, m) = X(m, k) for k < K, 1 for k == K (the bias
-// column), 0 beyond.
-struct LoadIm2colT {
-    const bf16 *x;
-    ConvShape s;
-    int K;
-    __device__ uint4 operator()(int k, int m0, int m_end) const {
-        bf16 v[8];
-        if (k > K) return zero4();
-        if (k == K) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = __float2bfloat16(m0 + i < m_end ? 1.f : 0.f);
-            return pack8(v);
-        }
-        const int tap = k / s.Ci, ci = k - tap * s.Ci;
-        const int kh = tap / 3, kw = tap - 3 * kh;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int m = m0 + i;
-            v[i] = __float2bfloat16(0.f);
-            if (m < m_end) {
-                const int ow = m % s.OW, t = m / s.OW, oh = t % s.OH, b = t / s.OH;
-                const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
-                if (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
-                    v[i] = x[(((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci];
-            }
-        }
-        return pack8(v);
-    }
-};
-
 // ---------------------------------------------------------------- epilogues
 struct EpiConv {  // y = bf16(relu?(acc + bias)), y32 = the float value
     bf16 *y;
@@ -146,13 +133,6 @@ struct EpiConv {  // y = bf16(relu?(acc + bias)), y32 = the float value
         if (relu) v = fmaxf(v, 0.f);
         y[(size_t)r * cols + c] = __float2bfloat16(v);
         if (y32) y32[(size_t)r * cols + c] = v;
-    }
-};
-struct EpiStore {  // out[r][ld] = acc
-    float *out;
-    int rows, cols, ld;
-    __device__ void operator()(int r, int c, float v) const {
-        if (r < rows && c < cols) out[(size_t)r * ld + c] = v;
     }
 };
 struct EpiWgrad {  // dw[r][c] += acc for c < K; db[r] += acc for c == K
@@ -253,54 +233,177 @@ cudaError_t gemm(LA la, LB lb, EP ep, int rows, int cols, int Kred, int ksplit, 
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------- element kernels
-// dx[b][ih][iw][ci] = sum over the (kh, kw) taps whose output position exists of
-// D[(b, oh, ow)][(kh, kw, ci)], times (mask > 0) when given.
-__global__ void k_col2im(const float *__restrict__ dcol, ConvShape s, const bf16 *__restrict__ mask,
-                         bf16 *__restrict__ dx, float *__restrict__ dx32) {
-    const int64_t n = (int64_t)s.B * s.H * s.W * s.Ci;
-    const int K9 = 9 * s.Ci;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ci = (int)(e % s.Ci);
-        int64_t t = e / s.Ci;
-        const int iw = (int)(t % s.W);
-        t /= s.W;
-        const int ih = (int)(t % s.H);
-        const int b = (int)(t / s.H);
-        float v = 0.f;
+// ------------------------------------------- reduction-major operands (wgrad)
+// Loaders of the transposed form: 8 bfloat16 values (kr, c0 .. c0 + 7) of an
+// operand whose reduction index kr is the slow one; zero for kr >= kr_end.
+struct LoadRowsT {  // p[kr][ld], columns c < cols (cols % 8 == 0)
+    const bf16 *p;
+    int ld, cols;
+    __device__ uint4 operator()(int kr, int c0, int kr_end) const {
+        if (kr >= kr_end || c0 >= cols) return zero4();
+        return *reinterpret_cast<const uint4 *>(p + (size_t)kr * ld + c0);
+    }
+};
+struct LoadIm2colRowT {  // X(m = kr, k = c0 ..), the bias column K reads 1
+    LoadIm2col x;
+    int K;
+    __device__ uint4 operator()(int kr, int c0, int kr_end) const {
+        if (kr >= kr_end || c0 > K) return zero4();
+        if (c0 == K) return make_uint4(0x3F80u, 0u, 0u, 0u);  // bfloat16 1.0, then zeros
+        return x(kr, c0, K);
+    }
+};
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+constexpr int LDA_T = BM + 8, LDB_T = BN + 8;  // reduction-major tiles, padded rows
+
+// C[rows][cols] = sum over the reduction range of A(row, k) B(col, k), with both
+// operands loaded reduction-major (coalesced along rows / cols) into shared
+// memory and read with ldmatrix.trans.
+template <class LA, class LB, class EP>
+__global__ void __launch_bounds__(GT) k_gemm_t(LA la, LB lb, EP ep, int Kred, int ksplit) {
+    __shared__ __align__(16) bf16 sA[2][BK * LDA_T];
+    __shared__ __align__(16) bf16 sB[2][BK * LDB_T];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * ksplit, ke = min(Kred, kb + ksplit);
+    if (kb >= ke) return;
+    float acc[2][4][4];
 #pragma unroll
-        for (int kh = 0; kh < 3; ++kh) {
-            const int y2 = ih + 1 - kh;
-            if (y2 < 0 || (y2 & 1) || (y2 >> 1) >= s.OH) continue;
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                const int x2 = iw + 1 - kw;
-                if (x2 < 0 || (x2 & 1) || (x2 >> 1) >= s.OW) continue;
-                const int64_t m = ((int64_t)b * s.OH + (y2 >> 1)) * s.OW + (x2 >> 1);
-                v += dcol[m * K9 + (kh * 3 + kw) * s.Ci + ci];
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    uint4 ra0, ra1, rb0;
+    // A tile: 32 k x 128 rows = 512 chunks of 8 (two per thread); B: 32 x 64 = 256 (one)
+    auto load = [&](int k) {
+        ra0 = la(k + (tid >> 4), m0 + (tid & 15) * 8, ke);
+        ra1 = la(k + 16 + (tid >> 4), m0 + (tid & 15) * 8, ke);
+        rb0 = lb(k + (tid >> 3), n0 + (tid & 7) * 8, ke);
+    };
+    auto store = [&](int buf) {
+        *reinterpret_cast<uint4 *>(&sA[buf][(tid >> 4) * LDA_T + (tid & 15) * 8]) = ra0;
+        *reinterpret_cast<uint4 *>(&sA[buf][(16 + (tid >> 4)) * LDA_T + (tid & 15) * 8]) = ra1;
+        *reinterpret_cast<uint4 *>(&sB[buf][(tid >> 3) * LDB_T + (tid & 7) * 8]) = rb0;
+    };
+    load(kb);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k = kb; k < ke; k += BK) {
+        const bool more = k + BK < ke;
+        if (more) load(k + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+            const int q = lane >> 3, l7 = lane & 7;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                ldsm_x4_t(a[i], &sA[buf][(kk + (q >> 1) * 8 + l7) * LDA_T + wm * 32 + i * 16 + (q & 1) * 8]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uint32_t t[4];
+                ldsm_x4_t(t, &sB[buf][(kk + (q & 1) * 8 + l7) * LDB_T + wn * 32 + j * 16 + (q >> 1) * 8]);
+                b[2 * j][0] = t[0];
+                b[2 * j][1] = t[1];
+                b[2 * j + 1][0] = t[2];
+                b[2 * j + 1][1] = t[3];
             }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j][0], b[j][1]);
         }
+        if (more) {
+            store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = m0 + wm * 32 + i * 16 + (lane >> 2);
+            const int c = n0 + wn * 32 + j * 8 + (lane & 3) * 2;
+            ep(r, c, acc[i][j][0]);
+            ep(r, c + 1, acc[i][j][1]);
+            ep(r + 8, c, acc[i][j][2]);
+            ep(r + 8, c + 1, acc[i][j][3]);
+        }
+}
+
+template <class LA, class LB, class EP>
+cudaError_t gemm_t(LA la, LB lb, EP ep, int rows, int cols, int Kred, int ksplit, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || Kred <= 0) return cudaSuccess;
+    ksplit = std::max(BK, (ksplit + BK - 1) / BK * BK);
+    const dim3 grid((rows + BM - 1) / BM, (cols + BN - 1) / BN, (Kred + ksplit - 1) / ksplit);
+    if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidValue;
+    k_gemm_t<LA, LB, EP><<<grid, GT, 0, st>>>(la, lb, ep, Kred, ksplit);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------- input gradient, sub-pixel form
+// Output position (i, j) feeds the 2 x 2 input pixels (2i + ph, 2j + pw): for
+// ih = 2i the tap is kh = 1 from oh = i; for ih = 2i + 1 the taps are kh = 2
+// from oh = i and kh = 0 from oh = i + 1 (likewise along w).  So one GEMM per
+// layer: rows m = (b, i, j), reduction k = (dy, dx, co) over gy[b][i + dy][j + dx],
+// columns n = (ph, pw, ci), with the sub-pixel weights
+//   W'[(ph, pw, ci)][(dy, dx, co)] = W[co][kh(ph, dy)][kw(pw, dx)][ci]
+// (zero where (ph, dy) has no tap: 9 of the 16 blocks are nonzero).
+__device__ __forceinline__ int subpixel_tap(int p, int d) { return p == 0 ? (d == 0 ? 1 : -1) : (d == 0 ? 2 : 0); }
+struct LoadGy2x2 {  // A(m, k = (dy, dx, co)) = gy[b][i + dy][j + dx][co .. co + 7]
+    const bf16 *gy;
+    ConvShape s;
+    int rows;
+    __device__ uint4 operator()(int m, int k0, int k_end) const {
+        if (m >= rows || k0 >= k_end) return zero4();
+        int d, co, b, i, j;
+        chan_split(k0, s.Co, s.lCo, d, co);
+        pos_split(s, m, b, i, j);
+        const int oh = i + (d >> 1), ow = j + (d & 1);
+        if (oh >= s.OH || ow >= s.OW) return zero4();
+        return *reinterpret_cast<const uint4 *>(gy + (((size_t)b * s.OH + oh) * s.OW + ow) * s.Co + co);
+    }
+};
+// W' [4 Ci][4 Co] from W [Co][3][3][Ci]
+__global__ void k_subpixel_weights(const bf16 *__restrict__ w, int Ci, int Co, bf16 *__restrict__ wp) {
+    const int64_t n = (int64_t)16 * Ci * Co;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % (4 * Co)), r = (int)(e / (4 * Co));
+        const int d = k / Co, co = k - d * Co, ph_pw = r / Ci, ci = r - ph_pw * Ci;
+        const int kh = subpixel_tap(ph_pw >> 1, d >> 1), kw = subpixel_tap(ph_pw & 1, d & 1);
+        wp[e] = (kh < 0 || kw < 0) ? __float2bfloat16(0.f) : w[(((size_t)co * 3 + kh) * 3 + kw) * Ci + ci];
+    }
+}
+struct EpiDx2x2 {  // dx[b][2i + ph][2j + pw][ci] = acc (times mask > 0), inside the input only
+    bf16 *dx;
+    float *dx32;
+    const bf16 *mask;
+    ConvShape s;
+    int rows;
+    __device__ void operator()(int m, int n, float v) const {
+        if (m >= rows || n >= 4 * s.Ci) return;
+        int q, ci, b, i, j;
+        chan_split(n, s.Ci, s.lCi, q, ci);
+        pos_split(s, m, b, i, j);
+        const int ih = 2 * i + (q >> 1), iw = 2 * j + (q & 1);
+        if (ih >= s.H || iw >= s.W) return;
+        const size_t e = (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci;
         if (mask && !(__bfloat162float(mask[e]) > 0.f)) v = 0.f;
         dx[e] = __float2bfloat16(v);
         if (dx32) dx32[e] = v;
     }
-}
+};
 
-// Weights [Co][K] -> transposed [K][Co].
-__global__ void k_transpose_bf16(const bf16 *__restrict__ w, int Co, int K, bf16 *__restrict__ wt) {
-    __shared__ bf16 tile[32][33];
-    const int k0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int c = c0 + r, k = k0 + threadIdx.x;
-        if (c < Co && k < K) tile[r][threadIdx.x] = w[(size_t)c * K + k];
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int k = k0 + r, c = c0 + threadIdx.x;
-        if (c < Co && k < K) wt[(size_t)k * Co + c] = tile[threadIdx.x][r];
-    }
-}
-
+// ------------------------------------------------------- element kernels
 __global__ void k_to_bf16(const float *__restrict__ a, int64_t n, bf16 *__restrict__ b) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         b[e] = __float2bfloat16(a[e]);
@@ -315,9 +418,8 @@ __global__ void k_conv1_fwd(const bf16 *__restrict__ x, ConvShape s, const bf16 
     __syncthreads();
     const int64_t M = (int64_t)s.B * s.OH * s.OW;
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
-        const int ow = (int)(m % s.OW);
-        const int64_t t = m / s.OW;
-        const int oh = (int)(t % s.OH), b = (int)(t / s.OH);
+        int b, oh, ow;
+        pos_split(s, (int)m, b, oh, ow);
         float xv[9];
 #pragma unroll
         for (int kh = 0; kh < 3; ++kh)
@@ -342,42 +444,6 @@ __global__ void k_conv1_fwd(const bf16 *__restrict__ x, ConvShape s, const bf16 
     }
 }
 
-// First-layer weight gradient: lane = output channel, warps stride over positions.
-__global__ void __launch_bounds__(256) k_conv1_wgrad(const bf16 *__restrict__ g, const bf16 *__restrict__ x,
-                                                     ConvShape s, float *__restrict__ dw, float *__restrict__ db) {
-    __shared__ float red[8][32][10];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const int64_t M = (int64_t)s.B * s.OH * s.OW;
-    for (int64_t m = (int64_t)blockIdx.x * 8 + warp; m < M; m += (int64_t)gridDim.x * 8) {
-        const int ow = (int)(m % s.OW);
-        const int64_t t = m / s.OW;
-        const int oh = (int)(t % s.OH), b = (int)(t / s.OH);
-        const float gv = __bfloat162float(g[m * 32 + lane]);
-#pragma unroll
-        for (int kh = 0; kh < 3; ++kh)
-#pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
-                const float xv = (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
-                                     ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
-                                     : 0.f;
-                acc[kh * 3 + kw] = fmaf(gv, xv, acc[kh * 3 + kw]);
-            }
-        acc[9] += gv;
-    }
-#pragma unroll
-    for (int k = 0; k < 10; ++k) red[warp][lane][k] = acc[k];
-    __syncthreads();
-    for (int e = threadIdx.x; e < 320; e += blockDim.x) {
-        const int co = e / 10, k = e - 10 * co;
-        float v = 0.f;
-        for (int ww = 0; ww < 8; ++ww) v += red[ww][co][k];
-        if (k < 9) atomicAdd(&dw[co * 9 + k], v);
-        else atomicAdd(&db[co], v);
-    }
-}
-
 // ------------------------------------------------------------ float32 head
 // h[b] = (y[b] flattened position-major (p, c), aux[b]).
 __global__ void k_flatten_concat(const bf16 *__restrict__ y, int B, int F, const float *__restrict__ aux,
@@ -388,17 +454,142 @@ __global__ void k_flatten_concat(const bf16 *__restrict__ y, int B, int F, const
         h[e] = c < F ? __bfloat162float(y[(size_t)b * F + c]) : aux[b * kAux + (c - F)];
     }
 }
-// out[b][j] = bias[j] + sum_i W[j][i] in[b][i], optionally ReLU (z keeps the pre-activation).
-__global__ void k_fc(const float *__restrict__ in, int B, int I, const float *__restrict__ W,
-                     const float *__restrict__ bias, int J, int relu, float *__restrict__ z, float *__restrict__ out) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * J; e += gridDim.x * blockDim.x) {
-        const int b = e / J, j = e - b * J;
-        float v = bias[j];
-        const float *wr = W + (size_t)j * I, *xr = in + (size_t)b * I;
-        for (int i = 0; i < I; ++i) v = fmaf(wr[i], xr[i], v);
+// C[m][n] = sum_k A(m, k) B(n, k) in float32 with A(m, k) = A[m sam + k sak],
+// B(n, k) = B[n sbn + k sbk]: 64 x 64 tiles through shared memory (loads
+// coalesced along whichever index has unit stride), 4 x 4 outputs per thread.
+template <class EP>
+__global__ void __launch_bounds__(256) k_sgemm(const float *__restrict__ A, int sam, int sak,
+                                               const float *__restrict__ Bm, int sbn, int sbk, int M, int N, int Kfull,
+                                               int ksplit, EP ep) {
+    __shared__ __align__(16) float As[2][16][68];
+    __shared__ __align__(16) float Bs[2][16][68];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int kbeg = blockIdx.z * ksplit, K = min(Kfull, kbeg + ksplit);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    float ra[4], rb[4];
+    // element q of this thread's share: unit-stride index fastest across threads
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int mm = sak == 1 ? (e >> 4) : (e & 63), kk = sak == 1 ? (e & 15) : (e >> 6);
+            const int m = m0 + mm, k = k0 + kk;
+            ra[q] = (m < M && k < K) ? A[(size_t)m * sam + (size_t)k * sak] : 0.f;
+            const int nn = sbk == 1 ? (e >> 4) : (e & 63), kb = sbk == 1 ? (e & 15) : (e >> 6);
+            const int n = n0 + nn, k2 = k0 + kb;
+            rb[q] = (n < N && k2 < K) ? Bm[(size_t)n * sbn + (size_t)k2 * sbk] : 0.f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int mm = sak == 1 ? (e >> 4) : (e & 63), kk = sak == 1 ? (e & 15) : (e >> 6);
+            As[buf][kk][mm] = ra[q];
+            const int nn = sbk == 1 ? (e >> 4) : (e & 63), kb = sbk == 1 ? (e & 15) : (e >> 6);
+            Bs[buf][kb][nn] = rb[q];
+        }
+    };
+    if (kbeg < K) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = kbeg; k0 < K; k0 += 16) {
+        const bool more = k0 + 16 < K;
+        if (more) load(k0 + 16);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ep(m0 + ty * 4 + i, n0 + tx * 4 + j, acc[i][j]);
+}
+struct EpiFc {  // out = relu?(acc + bias[n]), z (may be null) keeps the pre-activation
+    float *out, *z;
+    const float *bias;
+    int M, N, relu;
+    __device__ void operator()(int m, int n, float v) const {
+        if (m >= M || n >= N) return;
+        v += bias[n];
+        if (z) z[(size_t)m * N + n] = v;
+        out[(size_t)m * N + n] = relu ? fmaxf(v, 0.f) : v;
+    }
+};
+struct EpiF {  // out[m][n] = acc, times (zin > 0) when zin is given
+    float *out;
+    const float *zin;
+    int M, N;
+    __device__ void operator()(int m, int n, float v) const {
+        if (m >= M || n >= N) return;
+        if (zin && !(zin[(size_t)m * N + n] > 0.f)) v = 0.f;
+        out[(size_t)m * N + n] = v;
+    }
+};
+struct EpiPart {  // part[split][m][n] = acc (split = blockIdx.z)
+    float *part;
+    int M, N;
+    __device__ void operator()(int m, int n, float v) const {
+        if (m < M && n < N) part[((size_t)blockIdx.z * M + m) * N + n] = v;
+    }
+};
+template <class EP>
+void sgemm(const float *A, int sam, int sak, const float *B, int sbn, int sbk, int M, int N, int K, EP ep,
+           cudaStream_t st, int splits = 1) {
+    const int ks = (K + splits - 1) / splits;
+    k_sgemm<EP><<<dim3((M + 63) / 64, (N + 63) / 64, splits), 256, 0, st>>>(A, sam, sak, B, sbn, sbk, M, N, K, ks,
+                                                                           ep);
+}
+// out = relu?(sum over splits of part + bias), z keeps the pre-activation
+__global__ void k_fc_finish(const float *__restrict__ part, int splits, int M, int N, const float *__restrict__ bias,
+                            int relu, float *__restrict__ z, float *__restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
+        float v = bias[e % N];
+        for (int q = 0; q < splits; ++q) v += part[(size_t)q * M * N + e];
         if (z) z[e] = v;
         out[e] = relu ? fmaxf(v, 0.f) : v;
     }
+}
+constexpr int kFc1Splits = 8;
+// out[e] = sum over splits of part[split][e]
+__global__ void k_part_sum(const float *__restrict__ part, int splits, int64_t n, float *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int q = 0; q < splits; ++q) v += part[(size_t)q * n + e];
+        out[e] = v;
+    }
+}
+// db[j] = sum_b d[b][j]
+__global__ void k_colsum(const float *__restrict__ d, int B, int J, float *__restrict__ db) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int b = 0;
+    for (; b + 8 <= B; b += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] += d[(size_t)(b + u) * J + j];
+    for (; b < B; ++b) v[0] += d[(size_t)b * J + j];
+    db[j] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
 }
 // d = 2 (out - target) / (6 B); loss = mean squared error (one block).
 __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ tgt, int n, float *__restrict__ d,
@@ -417,31 +608,6 @@ __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t
         __syncthreads();
     }
     if (threadIdx.x == 0 && loss) *loss = red[0] / (double)n;
-}
-// dW[j][i] = sum_b d[b][j] in[b][i]; db[j] = sum_b d[b][j].
-__global__ void k_fc_wgrad(const float *__restrict__ d, const float *__restrict__ in, int B, int I, int J,
-                           float *__restrict__ dW, float *__restrict__ db) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * (I + 1); e += gridDim.x * blockDim.x) {
-        const int j = e / (I + 1), i = e - j * (I + 1);
-        float v = 0.f;
-        if (i < I)
-            for (int b = 0; b < B; ++b) v = fmaf(d[b * J + j], in[(size_t)b * I + i], v);
-        else
-            for (int b = 0; b < B; ++b) v += d[b * J + j];
-        if (i < I) dW[(size_t)j * I + i] = v;
-        else db[j] = v;
-    }
-}
-// din[b][i] = sum_j d[b][j] W[j][i], times (zin > 0) when zin is given.
-__global__ void k_fc_dgrad(const float *__restrict__ d, const float *__restrict__ W, int B, int I, int J,
-                           const float *__restrict__ zin, float *__restrict__ din) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < B * I; e += gridDim.x * blockDim.x) {
-        const int b = e / I, i = e - b * I;
-        float v = 0.f;
-        for (int j = 0; j < J; ++j) v = fmaf(d[b * J + j], W[(size_t)j * I + i], v);
-        if (zin && !(zin[e] > 0.f)) v = 0.f;
-        din[e] = v;
-    }
 }
 // g[b][f] = dh[b][f] times (y > 0) over the flattened features; bfloat16.
 __global__ void k_flatten_grad(const float *__restrict__ dh, int B, int F, int HD, const bf16 *__restrict__ y,
@@ -466,7 +632,15 @@ __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, 
 
 int blocks_for(int64_t n, int per = 256) { return (int)std::min<int64_t>((n + per - 1) / per, 148 * 16); }
 
-ConvShape conv_shape(int B, int H, int W, int Ci, int Co) { return ConvShape{B, H, W, Ci, (H + 1) / 2, (W + 1) / 2, Co}; }
+int log2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return (1 << l) == v ? l : -1;
+}
+ConvShape conv_shape(int B, int H, int W, int Ci, int Co) {
+    const int OH = (H + 1) / 2, OW = (W + 1) / 2;
+    return ConvShape{B, H, W, Ci, OH, OW, Co, log2_exact(OW), log2_exact(OH), log2_exact(Ci), log2_exact(Co)};
+}
 
 // --------------------------------------------------------- conv operations
 cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const float *bias, int relu, bf16 *y,
@@ -480,28 +654,95 @@ cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const
                 st);
 }
 
-cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *wt, const bf16 *mask, float *dcol,
-                       bf16 *dx, float *dx32, cudaStream_t st) {
-    const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
-    k_transpose_bf16<<<dim3((K + 31) / 32, (s.Co + 31) / 32), dim3(32, 8), 0, st>>>(w, s.Co, K, wt);
-    cudaError_t e = gemm(LoadRows{gy, M, s.Co}, LoadRows{wt, K, s.Co}, EpiStore{dcol, M, K, K}, M, K, s.Co, s.Co, st);
-    if (e != cudaSuccess) return e;
-    k_col2im<<<blocks_for((int64_t)s.B * s.H * s.W * s.Ci), 256, 0, st>>>(dcol, s, mask, dx, dx32);
-    return cudaGetLastError();
+cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *wp, const bf16 *mask, bf16 *dx,
+                       float *dx32, cudaStream_t st) {
+    k_subpixel_weights<<<blocks_for((int64_t)16 * s.Ci * s.Co), 256, 0, st>>>(w, s.Ci, s.Co, wp);
+    const int rows = s.B * s.OH * s.OW;
+    return gemm(LoadGy2x2{gy, s, rows}, LoadRows{wp, 4 * s.Ci, 4 * s.Co}, EpiDx2x2{dx, dx32, mask, s, rows}, rows,
+                4 * s.Ci, 4 * s.Co, 4 * s.Co, st);
 }
 
-cudaError_t conv_wgrad(const bf16 *gy, const bf16 *x, const ConvShape &s, float *dw, float *db, cudaStream_t st) {
+// Per block: partial first-layer weight gradients of a run of positions.  Each
+// round stages 256 positions' output gradients (32 channels) and input taps
+// (9, plus 1 for the bias) in shared memory with coalesced loads; thread o
+// (and o + 256 < 320) accumulates output (co, tap) = (o / 10, o % 10) over the
+// round.  part[block][320] is added over blocks by k_conv1_wgrad_sum.
+__global__ void __launch_bounds__(256) k_conv1_wgrad_part(const bf16 *__restrict__ g, const bf16 *__restrict__ x,
+                                                          ConvShape s, float *__restrict__ part) {
+    __shared__ float sg[256][33];
+    __shared__ float sx[256][10];
+    const int tid = threadIdx.x;
+    const int M = s.B * s.OH * s.OW;
+    const int per = ((M + gridDim.x - 1) / gridDim.x + 255) / 256 * 256;
+    const int m0 = blockIdx.x * per, m1 = min(M, m0 + per);
+    const int co0 = tid / 10, k0 = tid - 10 * co0;
+    const int o1 = tid + 256, co1 = o1 / 10, k1 = o1 - 10 * co1;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int mb = m0; mb < m1; mb += 256) {
+        const int m = mb + tid;
+        if (m < m1) {
+            const uint4 *gr = reinterpret_cast<const uint4 *>(g + (size_t)m * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 u = gr[q];
+                const bf16 *h = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) sg[tid][8 * q + e] = __bfloat162float(h[e]);
+            }
+            int b, oh, ow;
+            pos_split(s, m, b, oh, ow);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int ih = 2 * oh - 1 + t / 3, iw = 2 * ow - 1 + t % 3;
+                sx[tid][t] = (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
+                                 ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
+                                 : 0.f;
+            }
+            sx[tid][9] = 1.f;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) sg[tid][e] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 10; ++t) sx[tid][t] = 0.f;
+        }
+        __syncthreads();
+        const int np = min(256, m1 - mb);
+        for (int p = 0; p < np; ++p) {
+            acc0 = fmaf(sg[p][co0], sx[p][k0], acc0);
+            if (o1 < 320) acc1 = fmaf(sg[p][co1], sx[p][k1], acc1);
+        }
+        __syncthreads();
+    }
+    part[(size_t)blockIdx.x * 320 + tid] = acc0;
+    if (o1 < 320) part[(size_t)blockIdx.x * 320 + o1] = acc1;
+}
+__global__ void k_conv1_wgrad_sum(const float *__restrict__ part, int nb, float *__restrict__ dw,
+                                  float *__restrict__ db) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 320) return;
+    float v = 0.f;
+    for (int b = 0; b < nb; ++b) v += part[(size_t)b * 320 + e];
+    const int co = e / 10, k = e - 10 * co;
+    if (k < 9) dw[co * 9 + k] += v;
+    else db[co] += v;
+}
+constexpr int kConv1Blocks = 148 * 4;
+
+cudaError_t conv_wgrad(const bf16 *gy, const bf16 *x, const ConvShape &s, float *dw, float *db, float *scratch,
+                       cudaStream_t st) {
     const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
     if (s.Ci == 1 && s.Co == 32) {
-        k_conv1_wgrad<<<std::min(std::max(1, M / 64), 148 * 8), 256, 0, st>>>(gy, x, s, dw, db);
+        const int nb = std::max(1, std::min(kConv1Blocks, (M + 255) / 256));
+        k_conv1_wgrad_part<<<nb, 256, 0, st>>>(gy, x, s, scratch);
+        k_conv1_wgrad_sum<<<2, 256, 0, st>>>(scratch, nb, dw, db);
         return cudaGetLastError();
     }
     // reduction over positions split so that the grid fills the GPU a few times
     const int tiles = ((s.Co + BM - 1) / BM) * ((K + 1 + BN - 1) / BN);
     const int splits = std::max(1, std::min((M + BK - 1) / BK, (148 * 4 + tiles - 1) / tiles));
     const int ksplit = (M + splits - 1) / splits;
-    return gemm(LoadCols{gy, s.Co, s.Co}, LoadIm2colT{x, s, K}, EpiWgrad{dw, db, s.Co, K}, s.Co, K + 1, M, ksplit,
-                st);
+    return gemm_t(LoadRowsT{gy, s.Co, s.Co}, LoadIm2colRowT{LoadIm2col{x, s, M, K}, K}, EpiWgrad{dw, db, s.Co, K},
+                  s.Co, K + 1, M, ksplit, st);
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -520,10 +761,12 @@ struct gsvr_cnn {
     int64_t off_w[kLayers], off_b[kLayers], off_fc1w, off_fc1b, off_fc2w, off_fc2b;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     bf16 *wbf = nullptr;   // bfloat16 copy of the whole parameter vector (conv weights used)
-    bf16 *wt = nullptr;    // transposed weights scratch
+    bf16 *wt = nullptr;    // sub-pixel weights scratch (input gradient)
     bf16 *act[kLayers + 1] = {};
     bf16 *gpre[kLayers + 1] = {};  // gradient at each conv output (after the ReLU mask)
-    float *dcol = nullptr;
+    float *w1part = nullptr;  // first-layer weight-gradient block partials
+    float *fc1part = nullptr; // fc1 split-K partial sums
+    float *fc1wpart = nullptr;  // fc1 weight-gradient partial sums over batch splits
     float *h = nullptr, *z1 = nullptr, *a1 = nullptr, *out = nullptr, *dout = nullptr, *dz1 = nullptr, *dh = nullptr;
     std::vector<void *> allocs;
     ~gsvr_cnn() {
@@ -579,10 +822,12 @@ gsvr_status run_forward(gsvr_cnn *n, const float *x, const float *aux, int B) {
     }
     const int F = layer_size(kLayers) * layer_size(kLayers) * kCh[kLayers], HD = F + kAux;
     k_flatten_concat<<<blocks_for((int64_t)B * HD), 256, 0, st>>>(n->act[kLayers], B, F, aux, n->h);
-    k_fc<<<blocks_for((int64_t)B * kHidden), 256, 0, st>>>(n->h, B, HD, n->params + n->off_fc1w,
-                                                           n->params + n->off_fc1b, kHidden, 1, n->z1, n->a1);
-    k_fc<<<blocks_for((int64_t)B * kOut), 256, 0, st>>>(n->a1, B, kHidden, n->params + n->off_fc2w,
-                                                        n->params + n->off_fc2b, kOut, 0, nullptr, n->out);
+    sgemm(n->h, HD, 1, n->params + n->off_fc1w, HD, 1, B, kHidden, HD, EpiPart{n->fc1part, B, kHidden}, st,
+          kFc1Splits);
+    k_fc_finish<<<blocks_for((int64_t)B * kHidden), 256, 0, st>>>(n->fc1part, kFc1Splits, B, kHidden,
+                                                                  n->params + n->off_fc1b, 1, n->z1, n->a1);
+    sgemm(n->a1, kHidden, 1, n->params + n->off_fc2w, kHidden, 1, B, kOut, kHidden,
+          EpiFc{n->out, nullptr, n->params + n->off_fc2b, B, kOut, 0}, st);
     return cuda_status(n, cudaGetLastError(), "head forward");
 }
 
@@ -634,11 +879,10 @@ gsvr_status gsvr_cnn_create(gsvr_cnn **out, int32_t device, void *stream, int32_
     fill(n->off_fc2w, (int64_t)kOut * kHidden, kHidden);
     cudaError_t e = cudaSuccess;
     const int B = max_batch;
-    size_t dcol_max = 0, wt_max = 0;
+    size_t wt_max = 0;
     for (int l = 1; l < kLayers; ++l) {
         const size_t M = (size_t)B * layer_size(l + 1) * layer_size(l + 1);
-        dcol_max = std::max(dcol_max, M * 9 * kCh[l]);
-        wt_max = std::max(wt_max, (size_t)9 * kCh[l] * kCh[l + 1]);
+        wt_max = std::max(wt_max, (size_t)16 * kCh[l] * kCh[l + 1]);
     }
     if (!e) e = n->alloc(n->params, o);
     if (!e) e = n->alloc(n->grads, o);
@@ -651,7 +895,9 @@ gsvr_status gsvr_cnn_create(gsvr_cnn **out, int32_t device, void *stream, int32_
         e = n->alloc(n->act[l], sz);
         if (!e) e = n->alloc(n->gpre[l], sz);
     }
-    if (!e) e = n->alloc(n->dcol, dcol_max);
+    if (!e) e = n->alloc(n->w1part, (size_t)kConv1Blocks * 320);
+    if (!e) e = n->alloc(n->fc1part, (size_t)kFc1Splits * B * kHidden);
+    if (!e) e = n->alloc(n->fc1wpart, (size_t)kFc1Splits * kHidden * HD);
     if (!e) e = n->alloc(n->h, (size_t)B * HD);
     if (!e) e = n->alloc(n->z1, (size_t)B * kHidden);
     if (!e) e = n->alloc(n->a1, (size_t)B * kHidden);
@@ -716,24 +962,29 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
     cudaError_t e = cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, st);
     if (e) return cuda_status(n, e, "zero gradients");
     k_mse<<<1, 256, 0, st>>>(n->out, target, B * kOut, n->dout, loss);
-    k_fc_wgrad<<<blocks_for((int64_t)kOut * (kHidden + 1)), 256, 0, st>>>(
-        n->dout, n->a1, B, kHidden, kOut, n->grads + n->off_fc2w, n->grads + n->off_fc2b);
-    k_fc_dgrad<<<blocks_for((int64_t)B * kHidden), 256, 0, st>>>(n->dout, n->params + n->off_fc2w, B, kHidden, kOut,
-                                                                 n->z1, n->dz1);
-    k_fc_wgrad<<<blocks_for((int64_t)kHidden * (HD + 1)), 256, 0, st>>>(
-        n->dz1, n->h, B, HD, kHidden, n->grads + n->off_fc1w, n->grads + n->off_fc1b);
-    k_fc_dgrad<<<blocks_for((int64_t)B * HD), 256, 0, st>>>(n->dz1, n->params + n->off_fc1w, B, HD, kHidden, nullptr,
-                                                            n->dh);
+    float *gr = n->grads;
+    const float *p = n->params;
+    sgemm(n->dout, 1, kOut, n->a1, 1, kHidden, kOut, kHidden, B, EpiF{gr + n->off_fc2w, nullptr, kOut, kHidden}, st);
+    k_colsum<<<1, 32, 0, st>>>(n->dout, B, kOut, gr + n->off_fc2b);
+    sgemm(n->dout, kOut, 1, p + n->off_fc2w, 1, kHidden, B, kHidden, kOut, EpiF{n->dz1, n->z1, B, kHidden}, st);
+    {
+        const int splits = std::max(1, std::min(kFc1Splits, B / 64));
+        sgemm(n->dz1, 1, kHidden, n->h, 1, HD, kHidden, HD, B, EpiPart{n->fc1wpart, kHidden, HD}, st, splits);
+        k_part_sum<<<blocks_for((int64_t)kHidden * HD), 256, 0, st>>>(n->fc1wpart, splits, (int64_t)kHidden * HD,
+                                                                       gr + n->off_fc1w);
+    }
+    k_colsum<<<(kHidden + 127) / 128, 128, 0, st>>>(n->dz1, B, kHidden, gr + n->off_fc1b);
+    sgemm(n->dz1, kHidden, 1, p + n->off_fc1w, 1, HD, B, HD, kHidden, EpiF{n->dh, nullptr, B, HD}, st);
     k_flatten_grad<<<blocks_for((int64_t)B * F), 256, 0, st>>>(n->dh, B, F, HD, n->act[kLayers],
                                                                n->gpre[kLayers]);
     e = cudaGetLastError();
     if (e) return cuda_status(n, e, "head backward");
     for (int l = kLayers - 1; l >= 0; --l) {
         const ConvShape sh = conv_shape(B, layer_size(l), layer_size(l), kCh[l], kCh[l + 1]);
-        e = conv_wgrad(n->gpre[l + 1], n->act[l], sh, n->grads + n->off_w[l], n->grads + n->off_b[l], st);
+        e = conv_wgrad(n->gpre[l + 1], n->act[l], sh, n->grads + n->off_w[l], n->grads + n->off_b[l], n->w1part, st);
         if (e) return cuda_status(n, e, "conv wgrad");
         if (l > 0) {
-            e = conv_dgrad(n->gpre[l + 1], sh, n->wbf + n->off_w[l], n->wt, n->act[l], n->dcol, n->gpre[l], nullptr,
+            e = conv_dgrad(n->gpre[l + 1], sh, n->wbf + n->off_w[l], n->wt, n->act[l], n->gpre[l], nullptr,
                            st);
             if (e) return cuda_status(n, e, "conv dgrad");
         }
@@ -771,19 +1022,18 @@ gsvr_status gsvr_cnn_conv_forward(void *stream, const uint16_t *x, int32_t B, in
 }
 
 gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int32_t H, int32_t W, int32_t Ci,
-                                const uint16_t *w, int32_t Co, const uint16_t *mask, float *dcol, uint16_t *dx,
-                                float *dx32) {
+                                const uint16_t *w, int32_t Co, const uint16_t *mask, uint16_t *dx, float *dx32) {
     g_cnn_error.clear();
-    if (!gy || !w || !dcol || !dx || B < 1 || H < 1 || W < 1 || Ci < 8 || (Ci % 8) || Co < 8 || (Co % 8) ||
+    if (!gy || !w || !dx || B < 1 || H < 1 || W < 1 || Ci < 8 || (Ci % 8) || Co < 8 || (Co % 8) ||
         !aligned16(gy) || !aligned16(w) || (int64_t)B * H * W > (1LL << 30))
         return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv dgrad arguments (Ci, Co multiples of 8)");
     const ConvShape s = conv_shape(B, H, W, Ci, Co);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bf16 *wt = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&wt), sizeof(bf16) * 9 * Ci * Co, st);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&wt), sizeof(bf16) * 16 * Ci * Co, st);
     if (e) return cuda_status(nullptr, e, "scratch");
     e = conv_dgrad(reinterpret_cast<const bf16 *>(gy), s, reinterpret_cast<const bf16 *>(w), wt,
-                   reinterpret_cast<const bf16 *>(mask), dcol, reinterpret_cast<bf16 *>(dx), dx32, st);
+                   reinterpret_cast<const bf16 *>(mask), reinterpret_cast<bf16 *>(dx), dx32, st);
     cudaFreeAsync(wt, st);
     return cuda_status(nullptr, e, "conv dgrad");
 }
@@ -791,14 +1041,20 @@ gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int
 gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t *x, int32_t B, int32_t H, int32_t W,
                                 int32_t Ci, int32_t Co, float *dw, float *db) {
     g_cnn_error.clear();
-    if (!gy || !x || !dw || B < 1 || H < 1 || W < 1 || Ci < 1 || (Ci % 8 && Ci != 1) || Co < 2 || (Co & 1) ||
-        (Ci == 1 && (Co != 32 || !db)) || (int64_t)B * H * W > (1LL << 30))
-        return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv wgrad arguments");
+    if (!gy || !x || !dw || B < 1 || H < 1 || W < 1 || Ci < 1 || (Ci % 8 && Ci != 1) || Co < 8 || (Co % 8) ||
+        (Ci == 1 && (Co != 32 || !db)) || !aligned16(gy) || !aligned16(x) || (int64_t)B * H * W > (1LL << 30))
+        return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv wgrad arguments (Co a multiple of 8)");
     const ConvShape s = conv_shape(B, H, W, Ci, Co);
-    return cuda_status(nullptr,
-                       conv_wgrad(reinterpret_cast<const bf16 *>(gy), reinterpret_cast<const bf16 *>(x), s, dw, db,
-                                  static_cast<cudaStream_t>(stream)),
-                       "conv wgrad");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float *scratch = nullptr;
+    if (Ci == 1) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), sizeof(float) * kConv1Blocks * 320, st);
+        if (e) return cuda_status(nullptr, e, "scratch");
+    }
+    cudaError_t e = conv_wgrad(reinterpret_cast<const bf16 *>(gy), reinterpret_cast<const bf16 *>(x), s, dw, db,
+                               scratch, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    return cuda_status(nullptr, e, "conv wgrad");
 }
 
 }  // extern "C"
