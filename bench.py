@@ -343,7 +343,8 @@ def main():
     pairs_per_launch = eval_per_step
     achieved = pairs_per_launch / (avg_ms / 1e3) / 1e9
     peak = ffma_s / ISSUE_PER_PAIR[dom] / 1e9
-    traffic = profiled_traffic({"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom], args.workload)
+    traffic = profiled_traffic({"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
+                               "%s-%dx%d" % (args.workload, shape.tile_h, shape.tile_w))
     roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
                 "traffic": traffic,
