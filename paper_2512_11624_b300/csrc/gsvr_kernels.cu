@@ -962,26 +962,27 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             const float cB = B.a.w * dyB, bB = B.b.x * dyB * dyB;
             float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
             const float *rrow = rb + row * tw;
+            const float colc = colf0 + (float)c0;
+            float dxA = colc - A.a.x, dxB = colc - B.a.x;  // advance by one pixel per column
 #pragma unroll 4
             for (int col = c0; col <= c1; ++col) {
                 const float gg = rrow[col];
-                const float colf = colf0 + (float)col;
                 {
-                    const float dx = colf - A.a.x;
-                    const float e = gg * ex2_approx(fmaf(fmaf(A.a.z, dx, cA), dx, bA));
-                    const float ex = e * dx;
+                    const float e = gg * ex2_approx(fmaf(fmaf(A.a.z, dxA, cA), dxA, bA));
+                    const float ex = e * dxA;
                     A0 += e;
                     A1 += ex;
-                    A2 = fmaf(ex, dx, A2);
+                    A2 = fmaf(ex, dxA, A2);
                 }
                 {
-                    const float dx = colf - B.a.x;
-                    const float e = gg * ex2_approx(fmaf(fmaf(B.a.z, dx, cB), dx, bB));
-                    const float ex = e * dx;
+                    const float e = gg * ex2_approx(fmaf(fmaf(B.a.z, dxB, cB), dxB, bB));
+                    const float ex = e * dxB;
                     B0 += e;
                     B1 += ex;
-                    B2 = fmaf(ex, dx, B2);
+                    B2 = fmaf(ex, dxB, B2);
                 }
+                dxA += 1.f;
+                dxB += 1.f;
             }
             bwd_row_fold(mA, A0, A1, A2, dyA);
             bwd_row_fold(mB, B0, B1, B2, dyB);
@@ -1214,7 +1215,7 @@ __device__ __forceinline__ void gauss_epilogue(const GradArgs &a, int j, const f
 // its records, then a fixed-order tree sum).  Slice-frame gradients go to a
 // shared window over the run's subjects' slices, flushed once with float64
 // atomics; a block whose window does not fit uses float64 global atomics.
-__global__ void __launch_bounds__(256) k_gauss_grad(GradArgs a) {
+__global__ void __launch_bounds__(256, 4) k_gauss_grad(GradArgs a) {
     extern __shared__ float pacc_s[];  // window x 12
     __shared__ float rows[256][12];
     __shared__ int s_jb;
@@ -1556,7 +1557,7 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
         if (n_sm <= 0) n_sm = 148;
     }
     GradArgs g = a;
-    const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 6);
+    const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 4);  // one wave at 4 CTAs / SM
     // the widest slice window of any block (the kernel's chunking, on the host)
     int widest = a.M;
     if (a.gauss_subject && a.h_gauss_first && a.h_slice_first && a.n_subj > 1) {
