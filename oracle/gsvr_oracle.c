@@ -752,3 +752,228 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------ large cases: local FD
+ * Central differences of the loss L = sum_p w (I_hat_p - I_p)^2 over a listed
+ * pixel set, for selected parameters, at sizes where the all-pairs sums above
+ * are too slow.  The closed form of Eq. 4 / Eq. 5 is unchanged; only which
+ * pairs are visited differs: a pair whose exponent has exp(-1/2 v^T P v) < cut
+ * is dropped (cut = 1e-12 keeps every pair that matters in float64), and the
+ * pairs a pixel can have are found through a uniform grid of the Gaussian
+ * means whose cell is at least the largest Euclidean radius of that cut.
+ *  - predictions I_hat_p (float64) of every listed pixel -> pred_out, and per
+ *    pixel the sum of |terms| with trunc_cut > exp(.) >= cut -> trunc_out
+ *    (what a cut at trunc_cut drops);
+ *  - a Gaussian parameter changes only that Gaussian's terms: the loss change
+ *    is summed over the listed pixels within its cut under either perturbed
+ *    value, from I_hat_p minus the old term plus the new one;
+ *  - a slice-pose parameter moves that slice's pixels and PSF: its listed
+ *    pixels are re-evaluated with the perturbed frame. */
+typedef struct {
+    double lo[3], cell;
+    int64_t n[3];
+    int64_t *start, *items;
+} or_grid;
+
+static int64_t grid_cell_of(const or_grid *G, const double *x, int64_t c[3]) {
+    for (int a = 0; a < 3; ++a) {
+        int64_t k = (int64_t)floor((x[a] - G->lo[a]) / G->cell);
+        c[a] = k < 0 ? 0 : (k >= G->n[a] ? G->n[a] - 1 : k);
+    }
+    return (c[2] * G->n[1] + c[1]) * G->n[0] + c[0];
+}
+
+static int grid_build(or_grid *G, int64_t n, const double *pts, double cell, const double *lo, const double *hi) {
+    G->cell = cell;
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        G->lo[a] = lo[a];
+        G->n[a] = (int64_t)floor((hi[a] - lo[a]) / cell) + 1;
+        if (G->n[a] < 1) G->n[a] = 1;
+        total *= G->n[a];
+    }
+    G->start = (int64_t *)calloc((size_t)total + 1, sizeof(int64_t));
+    G->items = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t *cellof = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!G->start || !G->items || !cellof) return -1;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t c[3];
+        cellof[k] = grid_cell_of(G, pts + 3 * k, c);
+        G->start[cellof[k] + 1]++;
+    }
+    for (int64_t c = 0; c < total; ++c) G->start[c + 1] += G->start[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)total);
+    memcpy(fill, G->start, sizeof(int64_t) * (size_t)total);
+    for (int64_t k = 0; k < n; ++k) G->items[fill[cellof[k]]++] = k;
+    free(fill);
+    free(cellof);
+    return 0;
+}
+
+static void grid_free(or_grid *G) {
+    free(G->start);
+    free(G->items);
+}
+
+/* Sum over the Gaussians near x of c_l f exp(-1/2 v^T P v), pairs below the cut dropped. */
+static double pred_near(const or_model *m, const or_grid *G, const double *mu, const or_frame *fr, const double *x,
+                        int norm_mode, double r2cut, double rad2, double r2t, double *trunc) {
+    int64_t c[3];
+    grid_cell_of(G, x, c);
+    double s = 0.0;
+    for (int64_t dz = -1; dz <= 1; ++dz)
+        for (int64_t dy = -1; dy <= 1; ++dy)
+            for (int64_t dx = -1; dx <= 1; ++dx) {
+                int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= G->n[0] || cy >= G->n[1] || cz >= G->n[2]) continue;
+                int64_t cell = (cz * G->n[1] + cy) * G->n[0] + cx;
+                for (int64_t q = G->start[cell]; q < G->start[cell + 1]; ++q) {
+                    int64_t l = G->items[q];
+                    double v0 = x[0] - mu[3 * l], v1 = x[1] - mu[3 * l + 1], v2 = x[2] - mu[3 * l + 2];
+                    if (v0 * v0 + v1 * v1 + v2 * v2 > rad2) continue;  /* outside every pair's cut radius */
+                    or_pair pr;
+                    eval_pair(&m->g[l], fr, x, norm_mode, &pr);
+                    double d2 = -2.0 * log(pr.e > 0.0 ? pr.e : 1e-300);
+                    if (d2 <= r2cut) {
+                        s += m->g[l].c * pr.g;
+                        if (trunc && d2 > r2t) *trunc += fabs(m->g[l].c * pr.g);
+                    }
+                }
+            }
+    return s;
+}
+
+int oracle_local_fd(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P, const int64_t *pix,
+                    const double *I_obs, double w_pix, int norm_mode, double cut, int64_t K, const int64_t *params,
+                    const double *h, double *fd_out, double *pred_out, double trunc_cut, double *trunc_out) {
+    or_model m;
+    if (model_setup(n_stacks, st, N, theta, &m)) return -1;
+    const double r2cut = -2.0 * log(cut);
+    /* the largest Euclidean cut radius over all pairs: r2cut (max Gaussian
+     * variance + max PSF variance), with 1 % margin for the perturbations */
+    double vmax = 0.0, pmax = 0.0;
+    for (int64_t j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) vmax = m.g[j].s2[a] > vmax ? m.g[j].s2[a] : vmax;
+    for (int64_t i = 0; i < m.M; ++i)
+        for (int a = 0; a < 3; ++a) pmax = m.sl[i].var[a] > pmax ? m.sl[i].var[a] : pmax;
+    const double rad2 = r2cut * (vmax + pmax) * 1.02, rad = sqrt(rad2);
+    double *mu = (double *)malloc(sizeof(double) * 3 * (size_t)(N ? N : 1));
+    double *xp = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
+    int64_t *sp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
+    double *pred = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    if (!mu || !xp || !sp || !pred) return -1;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) {
+            mu[3 * j + a] = m.g[j].mu[a];
+            lo[a] = mu[3 * j + a] < lo[a] ? mu[3 * j + a] : lo[a];
+            hi[a] = mu[3 * j + a] > hi[a] ? mu[3 * j + a] : hi[a];
+        }
+    for (int64_t p = 0; p < P; ++p) {
+        double u[3];
+        pixel_world(&m, pix[p], &sp[p], u, xp + 3 * p);
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = xp[3 * p + a] < lo[a] ? xp[3 * p + a] : lo[a];
+            hi[a] = xp[3 * p + a] > hi[a] ? xp[3 * p + a] : hi[a];
+        }
+    }
+    double cell = rad;
+    for (;;) {  /* at most 2^24 cells */
+        double cells = 1.0;
+        for (int a = 0; a < 3; ++a) cells *= floor((hi[a] - lo[a]) / cell) + 1.0;
+        if (cells <= 16777216.0) break;
+        cell *= 1.25;
+    }
+    or_grid GG, GP;
+    if (grid_build(&GG, N, mu, cell, lo, hi) || grid_build(&GP, P, xp, cell, lo, hi)) return -1;
+    const double r2t = trunc_cut > 0.0 ? -2.0 * log(trunc_cut) : 1e300;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < P; ++p) {
+        double t = 0.0;
+        pred[p] = pred_near(&m, &GG, mu, &m.fr[sp[p]], xp + 3 * p, norm_mode, r2cut, rad2, r2t, &t);
+        if (trunc_out) trunc_out[p] = t;
+    }
+    if (pred_out) memcpy(pred_out, pred, sizeof(double) * (size_t)P);
+    /* listed pixels of each slice */
+    int64_t *sl_start = (int64_t *)calloc((size_t)m.M + 1, sizeof(int64_t));
+    int64_t *sl_items = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
+    for (int64_t p = 0; p < P; ++p) sl_start[sp[p] + 1]++;
+    for (int64_t i = 0; i < m.M; ++i) sl_start[i + 1] += sl_start[i];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m.M ? m.M : 1));
+        memcpy(fill, sl_start, sizeof(int64_t) * (size_t)m.M);
+        for (int64_t p = 0; p < P; ++p) sl_items[fill[sp[p]]++] = p;
+        free(fill);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < K; ++k) {
+        const int64_t q = params[k];
+        double dL = 0.0;
+        if (q < 11 * N) {
+            const int64_t comp = q / N, j = q % N;
+            double th[2][11];
+            or_gauss gv[2];
+            for (int s = 0; s < 2; ++s) {
+                for (int e = 0; e < 11; ++e) th[s][e] = theta[e * N + j];
+                th[s][comp] += (s == 0 ? 1.0 : -1.0) * h[k];
+                gauss_setup(1, th[s], 0, &gv[s]);
+            }
+            int64_t c[3];
+            grid_cell_of(&GP, m.g[j].mu, c);
+            for (int64_t dz = -1; dz <= 1; ++dz)
+                for (int64_t dy = -1; dy <= 1; ++dy)
+                    for (int64_t dx = -1; dx <= 1; ++dx) {
+                        int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+                        if (cx < 0 || cy < 0 || cz < 0 || cx >= GP.n[0] || cy >= GP.n[1] || cz >= GP.n[2]) continue;
+                        int64_t cl = (cz * GP.n[1] + cy) * GP.n[0] + cx;
+                        for (int64_t r = GP.start[cl]; r < GP.start[cl + 1]; ++r) {
+                            int64_t p = GP.items[r];
+                            const double *x = xp + 3 * p;
+                            const or_frame *fr = &m.fr[sp[p]];
+                            double old = 0.0, nw[2];
+                            or_pair pr;
+                            eval_pair(&m.g[j], fr, x, norm_mode, &pr);
+                            if (-2.0 * log(pr.e > 0.0 ? pr.e : 1e-300) <= r2cut) old = m.g[j].c * pr.g;
+                            for (int s = 0; s < 2; ++s) {
+                                eval_pair(&gv[s], fr, x, norm_mode, &pr);
+                                nw[s] = (-2.0 * log(pr.e > 0.0 ? pr.e : 1e-300) <= r2cut) ? gv[s].c * pr.g : 0.0;
+                            }
+                            if (old == 0.0 && nw[0] == 0.0 && nw[1] == 0.0) continue;
+                            double rp = pred[p] - old + nw[0] - I_obs[p], rm = pred[p] - old + nw[1] - I_obs[p];
+                            dL += w_pix * (rp * rp - rm * rm);
+                        }
+                    }
+        } else {
+            const int64_t i = (q - 11 * N) / 6, comp = (q - 11 * N) % 6;
+            for (int s = 0; s < 2; ++s) {
+                double pose[6];
+                for (int e = 0; e < 6; ++e) pose[e] = theta[11 * N + 6 * i + e];
+                pose[comp] += (s == 0 ? 1.0 : -1.0) * h[k];
+                or_frame fr;
+                slice_frame(&m.sl[i], pose, &fr);
+                double part = 0.0;
+                for (int64_t r = sl_start[i]; r < sl_start[i + 1]; ++r) {
+                    int64_t p = sl_items[r];
+                    double u[3], x[3];
+                    pixel_local(&m.sl[i], pix[p], u);
+                    mat_vec(fr.R, u, x);
+                    for (int a = 0; a < 3; ++a) x[a] += fr.t[a];
+                    double v = pred_near(&m, &GG, mu, &fr, x, norm_mode, r2cut, rad2, 1e300, NULL) - I_obs[p];
+                    part += w_pix * v * v;
+                }
+                dL += (s == 0 ? 1.0 : -1.0) * part;
+            }
+        }
+        fd_out[k] = dL / (2.0 * h[k]);
+    }
+    grid_free(&GG);
+    grid_free(&GP);
+    free(sl_start);
+    free(sl_items);
+    free(mu);
+    free(xp);
+    free(sp);
+    free(pred);
+    model_free(&m);
+    return 0;
+}

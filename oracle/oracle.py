@@ -56,6 +56,8 @@ def lib():
         _lib.oracle_num_threads.restype = C.c_int
         _lib.oracle_count_pairs.argtypes = [C.c_int, vp, i64, vp, i64, vp, d]
         _lib.oracle_count_pairs.restype = i64
+        _lib.oracle_local_fd.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, d, i64, vp, vp, vp, vp, d, vp]
+        _lib.oracle_local_fd.restype = C.c_int
     return _lib
 
 
@@ -202,3 +204,25 @@ def sample_positions(n, n_s, seed, step):
     if rc != 0:
         raise ValueError("bad sample size")
     return out
+
+
+def local_fd(stacks, theta, N, pix, I_pix, w_pix, params, h, cut=1e-12, norm_mode=0, trunc_cut=1e-7):
+    """Large cases: central differences of the loss over the listed pixels for
+    the given parameter indices (steps h), the float64 predictions of those
+    pixels and their sums of |terms| between trunc_cut and cut; pairs below
+    `cut` are dropped (see oracle_local_fd).  Returns (fd, pred, trunc)."""
+    st = _stacks(stacks)
+    th = _f64(theta)
+    px = np.ascontiguousarray(pix, dtype=np.int64)
+    Ip = _f64(I_pix)
+    pr = np.ascontiguousarray(params, dtype=np.int64)
+    hh = _f64(h)
+    fd = np.zeros(pr.size)
+    pred = np.zeros(px.size)
+    trunc = np.zeros(px.size)
+    rc = lib().oracle_local_fd(len(stacks), st, int(N), th.ctypes.data, px.size, px.ctypes.data, Ip.ctypes.data,
+                               float(w_pix), int(norm_mode), float(cut), pr.size, pr.ctypes.data, hh.ctypes.data,
+                               fd.ctypes.data, pred.ctypes.data, float(trunc_cut), trunc.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle_local_fd failed")
+    return fd, pred, trunc

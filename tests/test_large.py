@@ -1,0 +1,82 @@
+"""The large workload (1,000,372 Gaussians, six stacks of 48 x 256^2 px, 7.1M
+masked pixels) through the CUDA path at its full size, checked on sampled
+outputs the float64 oracle can compute one by one: predictions of 20,000
+random masked pixels against the oracle's grid-searched float64 sums (which
+the small-case pins tie to the all-pairs oracle), and the gradient of the
+loss over those pixels against float64 central differences of the same loss
+for 1,000 random parameters (700 of the Gaussians' 11 components, 300 slice
+poses).  Amplitudes start 30 % off the fit so that residuals, and so the
+gradients, are far from zero."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2512_11624_b300 import inputs
+from tests.gpu_util import forward_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11624_b300 import gsvr
+    return gsvr
+
+
+def test_large_case_predictions_and_gradients(G, oracle):
+    case = inputs.large(0, amplitude_jitter=0.3)
+    N = case["N"]
+    M = inputs.n_slices_total(case["stacks"])
+    rng = np.random.default_rng(5)
+    masked = np.nonzero(case["mask"])[0]
+    pix = np.sort(rng.choice(masked, size=20000, replace=False))
+    ctx = G.Context(case, tile_h=12, tile_w=12)
+    G.gsvr_set_pixel_sample(ctx.ctx, pix.astype(np.int32))
+    ctx.forward()
+    ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    pred = ctx.pred.cpu().numpy().astype(np.float64)[pix]
+    g = ctx.grad.cpu().numpy().astype(np.float64)
+    # one full iteration over every masked pixel, timed (printed)
+    G.gsvr_set_pixel_sample(ctx.ctx, None)
+    ctx.forward()
+    ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        ctx.forward()
+        ctx.backward()
+    G.gsvr_sync_status(ctx.ctx)
+    st = ctx.stats()
+    print("large: %.1f ms per forward + backward over %d pixels (%d records, %d keys)" %
+          ((time.perf_counter() - t0) / 3 * 1e3, st["n_sampled"], st["n_records"], st["n_keys"]))
+    ctx.close()
+    th = case["theta"].astype(np.float64)
+    params = np.concatenate([rng.choice(11 * N, 700, replace=False), 11 * N + rng.choice(6 * M, 300, replace=False)])
+    scale = np.ones(params.size)
+    amp = (params >= 10 * N) & (params < 11 * N)
+    scale[amp] = np.abs(th[params[amp]])
+    h = 1e-4 * scale
+    fd, pred_ref, trunc = oracle.local_fd(case["stacks"], th, N, pix, case["I"].astype(np.float64)[pix],
+                                          1.0 / pix.size, params, h, cut=1e-12, trunc_cut=1e-7)
+    ok, worst = forward_ok(pred, pred_ref, trunc)
+    assert ok.all(), ("forward", (~ok).sum(), worst)
+    gp = g[params]
+    err = np.abs(gp - fd)
+    groups = {"mu": params < 3 * N, "ls": (params >= 3 * N) & (params < 6 * N),
+              "q": (params >= 6 * N) & (params < 10 * N), "c": amp,
+              "rot": (params >= 11 * N) & ((params - 11 * N) % 6 < 3),
+              "trans": (params >= 11 * N) & ((params - 11 * N) % 6 >= 3)}
+    for name, sel in groups.items():
+        if not sel.any():
+            continue
+        ref = np.abs(fd[sel]).max()
+        rel = err[sel] / np.maximum(np.abs(fd[sel]), 1e-3 * ref)
+        print("%-5s n=%3d  median rel %.2e  99%% %.2e  max %.2e" % (name, sel.sum(), np.median(rel),
+                                                                   np.quantile(rel, 0.99), rel.max()))
+        # float32 accumulation over ~10^3 terms per entry: 1e-3 relative, floored at 1e-3 of the group's scale
+        assert np.all(rel <= 1e-3), (name, rel.max())
