@@ -417,7 +417,7 @@ def batched(seed=1000, n_subjects=16, nodes=(1, 1, 3)):
     return cases
 
 
-def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0):
+def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0, shape_jitter=0.0):
     """The large single-subject workload: the brain phantom scaled by 2.307
     (semi-axes 80.8 / 64.6 / 57.7 mm) so that its 1.08 mm grid holds ~1M
     Gaussians (s = 1.08 mm); six stacks of 48 x 256 x 256 px at
@@ -425,7 +425,9 @@ def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0):
     45 degrees about x, y and z); per-slice motion U(+-10 deg) / U(+-5 mm)
     (slice 24 of stack 0 unmoved); Rician noise 2 %; mask = phantom dilated by
     15 mm; every masked pixel each iteration.  amplitude_jitter > 0 multiplies
-    the amplitudes by U(1 +- jitter) (a start away from the fit)."""
+    the amplitudes by U(1 +- jitter) (a start away from the fit);
+    shape_jitter > 0 adds U(+-jitter) to every log-scale and turns every
+    Gaussian by a random rotation (anisotropic, oriented primitives)."""
     rng = np.random.default_rng(seed)
     ph = BrainPhantom(seed, scale=2.307)
     turned = [Rotation.from_euler(ax, 45.0, degrees=True).as_matrix() @ AXIAL for ax in ("x", "y", "z")]
@@ -435,9 +437,14 @@ def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0):
     motion[24] = 0.0
     I, mask = simulate_phantom_stacks(ph, stacks, motion, mask_dilate_mm=15.0, seed=seed, nodes=nodes)
     theta_g, N = grid_gaussians(ph, h=1.08, s=1.08)
-    if amplitude_jitter > 0:
+    if amplitude_jitter > 0 or shape_jitter > 0:
         th = theta_g.reshape(11, N)
-        th[10] *= rng.uniform(1 - amplitude_jitter, 1 + amplitude_jitter, size=N)
+        if amplitude_jitter > 0:
+            th[10] *= rng.uniform(1 - amplitude_jitter, 1 + amplitude_jitter, size=N)
+        if shape_jitter > 0:
+            th[3:6] += rng.uniform(-shape_jitter, shape_jitter, size=(3, N))
+            q = rng.normal(size=(4, N))
+            th[6:10] = q / np.linalg.norm(q, axis=0)
         theta_g = th.reshape(-1)
     theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
     return {"name": "large", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,

@@ -1,5 +1,6 @@
 """The large workload (1,000,372 Gaussians, six stacks of 48 x 256^2 px, 7.1M
-masked pixels) through the CUDA path at its full size, checked on sampled
+masked pixels; primitives turned and stretched at random) through the CUDA
+path at its full size, checked on sampled
 outputs the float64 oracle can compute one by one: predictions of 20,000
 random masked pixels against the oracle's grid-searched float64 sums (which
 the small-case pins tie to the all-pairs oracle), and the gradient of the
@@ -28,7 +29,7 @@ def G():
 
 
 def test_large_case_predictions_and_gradients(G, oracle):
-    case = inputs.large(0, amplitude_jitter=0.3)
+    case = inputs.large(0, amplitude_jitter=0.3, shape_jitter=0.2)
     N = case["N"]
     M = inputs.n_slices_total(case["stacks"])
     rng = np.random.default_rng(5)
@@ -71,12 +72,15 @@ def test_large_case_predictions_and_gradients(G, oracle):
               "q": (params >= 6 * N) & (params < 10 * N), "c": amp,
               "rot": (params >= 11 * N) & ((params - 11 * N) % 6 < 3),
               "trans": (params >= 11 * N) & ((params - 11 * N) % 6 >= 3)}
+    top = np.abs(fd).max()
     for name, sel in groups.items():
         if not sel.any():
             continue
-        ref = np.abs(fd[sel]).max()
-        rel = err[sel] / np.maximum(np.abs(fd[sel]), 1e-3 * ref)
+        # floor: 1e-3 of the group's largest entry, and 1e-6 of the largest overall (the quaternion
+        # gradient of an isotropic Gaussian is exactly zero)
+        floor = max(1e-3 * np.abs(fd[sel]).max(), 1e-6 * top)
+        rel = err[sel] / np.maximum(np.abs(fd[sel]), floor)
         print("%-5s n=%3d  median rel %.2e  99%% %.2e  max %.2e" % (name, sel.sum(), np.median(rel),
                                                                    np.quantile(rel, 0.99), rel.max()))
-        # float32 accumulation over ~10^3 terms per entry: 1e-3 relative, floored at 1e-3 of the group's scale
+        # float32 accumulation over ~10^3 terms per entry: 1e-3 relative to the floored magnitude
         assert np.all(rel <= 1e-3), (name, rel.max())
