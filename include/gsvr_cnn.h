@@ -61,6 +61,12 @@ gsvr_status gsvr_cnn_create(gsvr_cnn **out, int32_t device, void *stream, int32_
 gsvr_status gsvr_cnn_destroy(gsvr_cnn *net);
 const char *gsvr_cnn_last_error(gsvr_cnn *net);
 
+/* Synchronise and return-and-clear the network's device status word:
+ * GSVR_ERR_TIMEOUT when a tensor-memory GEMM of an earlier call gave up a
+ * bounded wait (its output was left unwritten), else GSVR_OK.  net NULL
+ * synchronises the device and reads the word of the layer primitives. */
+gsvr_status gsvr_cnn_sync_status(gsvr_cnn *net);
+
 /* Device pointers to the float32 parameter and gradient vectors (layout above)
  * and their length.  The caller may read or overwrite the parameters between
  * calls (e.g. to load a checkpoint). */
@@ -87,6 +93,14 @@ gsvr_status gsvr_cnn_adam_step(gsvr_cnn *net, float lr, float beta1, float beta2
  * gradient also take Ci = 1 with Co = 32, the first layer); all pointers
  * device memory, 16-byte aligned.
  *
+ * Layers with at least 64 output columns (Co for the forward, 4 Ci for the
+ * input gradient) run as tcgen05.mma GEMMs with tensor-memory accumulators,
+ * their operands fetched by tensor-map copies when the reduction channels (Ci
+ * forward, Co input gradient) are a multiple of 64 and a 128-row tile is
+ * whole output rows or whole images (OW and OH OW powers of two, OW <= 128),
+ * else by per-thread 16-byte copies; a bounded wait that runs out there is
+ * reported by gsvr_cnn_sync_status(NULL).
+ *
  * gsvr_cnn_conv_forward: y = bf16(max(conv(x, w) + bias, 0)) when relu, else
  *   without the max; y32 (may be NULL) receives the float32 values before the
  *   bfloat16 rounding.
@@ -103,6 +117,19 @@ gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int
                                 const uint16_t *w, int32_t Co, const uint16_t *mask, uint16_t *dx, float *dx32);
 gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t *x, int32_t B, int32_t H, int32_t W,
                                 int32_t Ci, int32_t Co, float *dw, float *db);
+
+/* Dense GEMM C[M][N] = sum_k A[m][k] B[n][k] (bfloat16 row-major A [M][K] and
+ * B [N][K], K a multiple of 8; C float32 row-major; all three 16-byte aligned) on the
+ * tensor cores.  tensor_memory selects the kernel:
+ *   1  tcgen05.mma, accumulators in tensor memory, operand tiles fetched by
+ *      tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle)
+ *   2  tcgen05.mma with operand tiles gathered by 16-byte cp.async per thread
+ *      (the path of convolution shapes that tensor-map tiles do not cover)
+ *   0  mma.sync (register accumulators)
+ * For 1 and 2 a bounded wait that runs out sets bit 4 of the device word
+ * `status` and leaves C unwritten. */
+gsvr_status gsvr_cnn_gemm(void *stream, const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K, float *C,
+                          int32_t tensor_memory, unsigned *status);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ lib = gsvr.lib
 IMAGE, AUX, OUT = 128, 25, 6
 EXPORTS = ["gsvr_cnn_create", "gsvr_cnn_destroy", "gsvr_cnn_last_error", "gsvr_cnn_views", "gsvr_cnn_forward",
            "gsvr_cnn_loss_backward", "gsvr_cnn_adam_step", "gsvr_cnn_conv_forward", "gsvr_cnn_conv_dgrad",
-           "gsvr_cnn_conv_wgrad"]
+           "gsvr_cnn_conv_wgrad", "gsvr_cnn_gemm", "gsvr_cnn_sync_status"]
 
 _vp, _i32, _i64, _u64, _f = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
 _SIG = {
@@ -32,6 +32,8 @@ _SIG = {
     "gsvr_cnn_conv_forward": ([_vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _i32, _vp, _vp], C.c_int),
     "gsvr_cnn_conv_dgrad": ([_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp], C.c_int),
     "gsvr_cnn_conv_wgrad": ([_vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp], C.c_int),
+    "gsvr_cnn_gemm": ([_vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32, _vp], C.c_int),
+    "gsvr_cnn_sync_status": ([_vp], C.c_int),
 }
 for _name, (_args, _res) in _SIG.items():
     _fn = getattr(lib, _name)
@@ -95,6 +97,24 @@ def conv_wgrad(gy, x, stream=None):
     return dw, db
 
 
+def sync_status():
+    """Synchronise the device; raise GsvrError if a layer primitive's bounded wait ran out."""
+    _check(None, lib.gsvr_cnn_sync_status(None))
+
+
+def gemm(A, B, tensor_memory=1, stream=None):
+    """C = A B^T (A [M][K], B [N][K] bf16 CUDA tensors) in float32; returns (C, status word).
+    tensor_memory: 1 tcgen05 with tensor-map operand copies, 2 tcgen05 with per-thread copies, 0 mma.sync."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(None, lib.gsvr_cnn_gemm(_stream(stream), _dp(A), _dp(B), M, N, K, _dp(C), int(tensor_memory),
+                                   _dp(status)))
+    return C, status
+
+
 # ---------------------------------------------------------------- the model
 class PoseNet:
     """Owning wrapper of a gsvr_cnn; params / grads are zero-copy float32 views."""
@@ -128,6 +148,10 @@ class PoseNet:
 
     def adam_step(self, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(self.net, lib.gsvr_cnn_adam_step(self.net, float(lr), float(beta1), float(beta2), float(eps), int(t)))
+
+    def sync_status(self):
+        """Synchronise; raise GsvrError(GSVR_ERR_TIMEOUT) if a bounded wait ran out since the last check."""
+        _check(self.net, lib.gsvr_cnn_sync_status(self.net))
 
     def close(self):
         if self.net:
@@ -333,6 +357,7 @@ def train(net, X, A, Y, epochs=20, batch=256, lr=1e-3, seed=0, val_frac=0.05, lo
             steps += 1
             net.adam_step(t, lr=lr_ep)
         vl = evaluate_loss(net, X[n_tr:], A[n_tr:], Y[n_tr:], batch)
+        net.sync_status()
         hist.append((ep + 1, float(tot.item()) / max(steps, 1), vl, time.time() - t0))
         if log:
             log("epoch %d: train %.4f  val %.4f  (%.1f s)" % hist[-1])

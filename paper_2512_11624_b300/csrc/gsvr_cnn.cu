@@ -10,8 +10,10 @@
 // One GEMM kernel serves the three: its operand loaders produce 8 consecutive
 // reduction-index values of one row (16 bytes) and its epilogue consumes the
 // float32 accumulators.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -21,6 +23,7 @@
 #include <vector>
 
 #include "gsvr_cnn.h"
+#include "gsvr_internal.cuh"
 
 namespace {
 
@@ -47,6 +50,11 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+// two floats rounded to bfloat16, lo in the low half
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
 __device__ __forceinline__ uint4 pack8(const bf16 v[8]) {
     uint4 u;
     uint32_t *p = reinterpret_cast<uint32_t *>(&u);
@@ -109,6 +117,17 @@ struct LoadIm2col {
         if (ih < 0 || ih >= s.H || iw < 0 || iw >= s.W) return zero4();
         return *reinterpret_cast<const uint4 *>(x + (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci);
     }
+    // address of the same 8 values, nullptr where they are zero (padding, past the ends)
+    __device__ const bf16 *src(int m, int k0, int k_end) const {
+        if (m >= rows || k0 >= k_end) return nullptr;
+        int tap, ci, b, oh, ow;
+        chan_split(k0, s.Ci, s.lCi, tap, ci);
+        const int kh = (tap * 11) >> 5, kw = tap - 3 * kh;
+        pos_split(s, m, b, oh, ow);
+        const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
+        if (ih < 0 || ih >= s.H || iw < 0 || iw >= s.W) return nullptr;
+        return x + (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci;
+    }
 };
 
 // Row-major matrix p[row][ld] (ld % 8 == 0, 16-byte aligned rows).
@@ -118,6 +137,9 @@ struct LoadRows {
     __device__ uint4 operator()(int r, int k0, int k_end) const {
         if (r >= rows || k0 >= k_end) return zero4();
         return *reinterpret_cast<const uint4 *>(p + (size_t)r * ld + k0);
+    }
+    __device__ const bf16 *src(int r, int k0, int k_end) const {
+        return (r >= rows || k0 >= k_end) ? nullptr : p + (size_t)r * ld + k0;
     }
 };
 
@@ -133,6 +155,29 @@ struct EpiConv {  // y = bf16(relu?(acc + bias)), y32 = the float value
         if (relu) v = fmaxf(v, 0.f);
         y[(size_t)r * cols + c] = __float2bfloat16(v);
         if (y32) y32[(size_t)r * cols + c] = v;
+    }
+    // columns c0 .. c0 + 7 of row r (c0 % 8 == 0)
+    __device__ void vec8(int r, int c0, const float *v) const {
+        if (r >= rows) return;
+        if (c0 + 8 > cols || (cols & 7)) {
+            for (int j = 0; j < 8; ++j) (*this)(r, c0 + j, v[j]);
+            return;
+        }
+        float o[8];
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            o[j] = v[j] + (bias ? bias[c0 + j] : 0.f);
+            if (relu) o[j] = fmaxf(o[j], 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pk[j] = pack_bf16x2(o[2 * j], o[2 * j + 1]);
+        const size_t e = (size_t)r * cols + c0;
+        *reinterpret_cast<uint4 *>(y + e) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        if (y32) {
+            reinterpret_cast<float4 *>(y32 + e)[0] = make_float4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<float4 *>(y32 + e)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
     }
 };
 struct EpiWgrad {  // dw[r][c] += acc for c < K; db[r] += acc for c == K
@@ -232,6 +277,478 @@ cudaError_t gemm(LA la, LB lb, EP ep, int rows, int cols, int Kred, int ksplit, 
     k_gemm<LA, LB, EP><<<grid, GT, 0, st>>>(la, lb, ep, Kred, ksplit);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------ 5th-generation tensor cores
+// tcgen05 GEMM: C[rows][cols] = sum_k A(row, k) B(col, k) with bfloat16 operands
+// and float32 accumulators in tensor memory.  A CTA of 128 threads owns a
+// Output tile 128 x BN (BN = 64 or 128) accumulated in tensor memory, warp
+// specialised.  Warps 0-3 produce: per 64-wide K step they copy both operand
+// tiles from global memory with 16-byte cp.async (zero-filled where the loader
+// reports padding) into shared memory in the 128-byte-swizzled K-major layout
+// (8-row x 128-byte atoms, 16-byte chunk c of row r at r * 128 +
+// ((c ^ (r % 8)) * 16), atoms 1024 bytes apart); each thread signals a stage's
+// `full` barrier TC_LAG steps later, once its copies have landed and are
+// fenced for the tensor cores.  Warp 4 owns the tensor memory: one thread
+// waits for `full`, issues the four tcgen05.mma (K = 16 each) of the step and
+// commits them to the stage's `empty` barrier, which frees the stage for the
+// producers.  STAGES steps are resident; no CTA-wide barrier runs per step.
+// After the last step warps 0-3 read the accumulators back with tcgen05.ld
+// (warp w owns rows 32 w .. 32 w + 31, 32 columns per load) and store 8
+// columns at a time.
+constexpr int TC_M = 128, TC_K = 64, TC_PRODUCERS = 128, TC_THREADS = TC_PRODUCERS + 32, TC_LAG = 2;
+constexpr uint64_t kTcWaitNs = 1000000000ull;  // 1 s bound on every mbarrier wait
+template <int BN>
+struct TcCfg {
+    static constexpr int STAGES = BN == 128 ? 3 : 4;  // two CTAs per SM either way
+    static constexpr int A_BYTES = TC_M * TC_K * 2, B_BYTES = BN * TC_K * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+    // instruction descriptor, kind::f16: D float32 (bits 4-5 = 1), A and B
+    // bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(TC_M >> 4) << 24);
+    static_assert(TC_LAG < STAGES, "a producer must signal a stage before it waits to refill it");
+};
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
+    // matrix descriptor: start >> 4 [0,14), leading byte offset >> 4 [16,30)
+    // (unused by swizzled K-major layouts: 1), stride byte offset >> 4 [32,46)
+    // (1024 B between 8-row atoms), fixed 0b001 at [46,49), swizzle 128 B (2) at [61,64)
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     gsvr::smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 16-byte asynchronous copy global -> shared; src == nullptr writes zeros
+// (source size 0: nothing is read, the base pointer only stands in).
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, const void *base) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src ? src : base),
+                 "r"(src ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gsvr::smem_u32(bar)) : "memory");
+}
+
+template <class LA, class LB, class EP, int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(LA la, LB lb, EP ep, int Kred, const void *base,
+                                                        unsigned *status) {
+    using Cfg = TcCfg<BN>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const uint32_t sbase = (gsvr::smem_u32(tc_raw) + 1023u) & ~1023u;
+    const int nk = (Kred + TC_K - 1) / TC_K;
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsvr::smem_u32(&s_tmem)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            gsvr::mbar_init(&full[i], TC_PRODUCERS);
+            gsvr::mbar_init(&empty[i], 1);
+        }
+        gsvr::mbar_init(&done, 1);
+        gsvr::fence_mbar_init();
+        s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (warp < 4) {
+        // ---- producers: step kt into stage kt % S; signal step kt - TC_LAG
+        auto signal = [&](int j) {
+            cp_async_wait_group<TC_LAG>();  // this thread's copies of step j have landed
+            gsvr::fence_proxy_async_smem();  // ... and are visible to the tensor cores
+            mbar_arrive(&full[j % S]);
+        };
+        for (int kt = 0; kt < nk + TC_LAG; ++kt) {
+            if (kt < nk) {
+                const int s = kt % S;
+                if (kt >= S && !gsvr::mbar_wait_bounded(&empty[s], ((kt / S) - 1) & 1u, kTcWaitNs)) s_fail = 1;
+                if (s_fail) break;
+                const uint32_t sa = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), sb = sa + Cfg::A_BYTES;
+                const int k = kt * TC_K;
+#pragma unroll
+                for (int q = tid; q < TC_M * 8; q += TC_PRODUCERS) {
+                    const int r = q >> 3, c = q & 7;
+                    const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+                    cp_async16_zfill(sa + off, la.src(m0 + r, k + c * 8, Kred), base);
+                    if (r < BN) cp_async16_zfill(sb + off, lb.src(n0 + r, k + c * 8, Kred), base);
+                }
+            }
+            cp_async_commit_group();
+            if (kt >= TC_LAG) signal(kt - TC_LAG);
+        }
+        cp_async_wait_group<0>();
+        // ---- epilogue: wait for the last commit, read the accumulators (a
+        // warp-uniform decision: tcgen05.ld is a whole-warp instruction)
+        bool bad = s_fail;
+        if (!bad && !gsvr::mbar_wait_bounded(&done, 0u, kTcWaitNs)) bad = true;
+        bad = __any_sync(0xffffffffu, bad);
+        if (bad) s_fail = 1;
+        tc_fence_after();
+        if (!bad) {
+            const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    float f[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) f[t] = __uint_as_float(v[j + t]);
+                    ep.vec8(row, n0 + c0 + j, f);
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---- MMA issuer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % S;
+            if (s_fail || !gsvr::mbar_wait_bounded(&full[s], (kt / S) & 1u, kTcWaitNs)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk)
+                tc_mma(tmem, tc_smem_desc(a0 + kk * 32), tc_smem_desc(b0 + kk * 32), Cfg::IDESC,
+                       (kt > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty[s]);
+        }
+        tc_commit(&done);  // arrives once every MMA issued above has completed
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(status, 4u);
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                     : "memory");
+}
+
+// ---------------------------------------------- tcgen05 GEMM, TMA operands
+// Same tile, swizzled layout, tensor-memory accumulation and epilogue as
+// k_gemm_tc, with both operand tiles of a K step fetched by two tensor-map
+// copies (cp.async.bulk.tensor) issued by one thread and counted on the
+// stage's `full` barrier (expect_tx), so no thread waits on its own loads.
+// Warp 0 (one lane) produces, warp 1 (one lane) issues the MMAs, warp 2 owns
+// the tensor memory; all four warps run the epilogue.  Operand A is one of:
+//   TMA_ROWS   a row-major [rows][K] matrix: box {64, 128} at (k, m0)
+//   TMA_CONV   the forward im2col of a 3x3 / stride-2 / pad-1 convolution,
+//              read from x [B][H][W][C] through a 4-D map that steps 2 input
+//              pixels per output pixel: for K step k (tap t = k / C, channels
+//              c0 = k % C) the box starts at (c0, kw - 1, 2 oh0 + kh - 1, b0);
+//              negative and past-the-end coordinates read 0 (the padding)
+//   TMA_GY2X2  the sub-pixel input-gradient operand, gy [B][OH][OW][C] through
+//              a 4-D map: for K step k (d = k / C) the box starts at
+//              (c0, d % 2, oh0 + d / 2, b0), past-the-end rows read 0
+// For the 4-D kinds a 128-row tile is whole output rows of one image (P =
+// OH OW >= 128) or whole images (P < 128), so that the box lands in shared
+// memory in row order m = (b, oh, ow).
+enum TmaKind { TMA_ROWS = 0, TMA_CONV = 1, TMA_GY2X2 = 2 };
+struct TmaA {
+    int kind;
+    int lC;        // log2 channels per tap (4-D kinds)
+    int lP, lOW;   // log2 of positions per image and of the output width (4-D kinds)
+};
+constexpr int TMA_THREADS = 128;
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(gsvr::smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(gsvr::smem_u32(bar))
+        : "memory");
+}
+
+template <class EP, int BN>
+__global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant__ CUtensorMap mapA,
+                                                          const __grid_constant__ CUtensorMap mapB, TmaA ta, EP ep,
+                                                          int Kred, unsigned *status) {
+    using Cfg = TcCfg<BN>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const uint32_t sbase = (gsvr::smem_u32(tc_raw) + 1023u) & ~1023u;
+    const int nk = (Kred + TC_K - 1) / TC_K;
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsvr::smem_u32(&s_tmem)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            gsvr::mbar_init(&full[i], 1);
+            gsvr::mbar_init(&empty[i], 1);
+        }
+        gsvr::mbar_init(&done, 1);
+        gsvr::fence_mbar_init();
+        s_fail = 0;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (warp == 0 && lane == 0) {
+        // ---- producer
+        int b0 = 0, oh0 = 0;
+        if (ta.kind != TMA_ROWS) {
+            b0 = m0 >> ta.lP;
+            oh0 = (m0 - (b0 << ta.lP)) >> ta.lOW;
+        }
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % S;
+            if (kt >= S && !gsvr::mbar_wait_bounded(&empty[s], ((kt / S) - 1) & 1u, kTcWaitNs)) s_fail = 1;
+            if (s_fail) break;
+            const uint32_t sa = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), sb = sa + Cfg::A_BYTES;
+            const int k = kt * TC_K;
+            gsvr::mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::STAGE_BYTES);
+            if (ta.kind == TMA_ROWS) {
+                tma_load_2d(sa, &mapA, k, m0, &full[s]);
+            } else {
+                const int t = k >> ta.lC, c0 = k & ((1 << ta.lC) - 1);
+                if (ta.kind == TMA_CONV) {
+                    const int kh = (t * 11) >> 5, kw = t - 3 * kh;  // t / 3 for t < 9
+                    tma_load_4d(sa, &mapA, c0, kw - 1, 2 * oh0 + kh - 1, b0, &full[s]);
+                } else {
+                    tma_load_4d(sa, &mapA, c0, t & 1, oh0 + (t >> 1), b0, &full[s]);
+                }
+            }
+            tma_load_2d(sb, &mapB, k, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % S;
+            if (s_fail || !gsvr::mbar_wait_bounded(&full[s], (kt / S) & 1u, kTcWaitNs)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk)
+                tc_mma(tmem, tc_smem_desc(a0 + kk * 32), tc_smem_desc(b0 + kk * 32), Cfg::IDESC,
+                       (kt > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty[s]);
+        }
+        tc_commit(&done);  // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+    // ---- epilogue (all four warps; the decision is warp-uniform)
+    bool bad = s_fail;
+    if (!bad && !gsvr::mbar_wait_bounded(&done, 0u, kTcWaitNs)) bad = true;
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad) s_fail = 1;
+    tc_fence_after();
+    if (!bad) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                float f[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) f[t] = __uint_as_float(v[j + t]);
+                ep.vec8(row, n0 + c0 + j, f);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(status, 4u);
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                     : "memory");
+}
+
+// Host: the driver's tensor-map encoder, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+// bfloat16 tensor map with the 128-byte swizzle; dims / strides innermost
+// first (strides in bytes, rank - 1 of them), zero fill outside the tensor.
+bool encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
+                const uint32_t *box, const uint32_t *estride) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base),
+               reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides),
+               reinterpret_cast<const cuuint32_t *>(box), reinterpret_cast<const cuuint32_t *>(estride),
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+// [rows][K] row-major bfloat16 (K % 8 == 0, 16-byte aligned), box {64, box_rows}
+bool map_rows(CUtensorMap *m, const bf16 *p, int rows, int K, int box_rows) {
+    const uint64_t dims[2] = {(uint64_t)K, (uint64_t)rows}, strides[1] = {(uint64_t)K * 2};
+    const uint32_t box[2] = {(uint32_t)TC_K, (uint32_t)box_rows}, es[2] = {1, 1};
+    return encode_map(m, p, 2, dims, strides, box, es);
+}
+int ilog2_exact(int v) {  // log2 of a power of two, else -1
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+// Tile of 128 output rows as (images bb) x (rows bh) x (all OW columns);
+// false when the output grid does not split that way.
+bool tile_rows(const ConvShape &s, int &bh, int &bb) {
+    const int P = s.OH * s.OW;
+    if (ilog2_exact(s.OW) < 0 || ilog2_exact(P) < 0 || s.OW > 128) return false;
+    if (P >= TC_M) {
+        bh = TC_M / s.OW;
+        bb = 1;
+    } else {
+        bh = s.OH;
+        bb = TC_M / P;
+    }
+    return true;
+}
+
+template <class EP>
+cudaError_t launch_tma(const CUtensorMap &mA, const CUtensorMap &mB, TmaA ta, EP ep, int rows, int cols, int Kred,
+                       unsigned *status, cudaStream_t st) {
+    const bool narrow = cols <= 64;
+    const dim3 grid((rows + TC_M - 1) / TC_M, (cols + (narrow ? 64 : 128) - 1) / (narrow ? 64 : 128));
+    cudaError_t e;
+    if (narrow) {
+        e = cudaFuncSetAttribute(k_gemm_tma<EP, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<64>::SMEM);
+        if (e) return e;
+        k_gemm_tma<EP, 64><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
+    } else {
+        e = cudaFuncSetAttribute(k_gemm_tma<EP, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128>::SMEM);
+        if (e) return e;
+        k_gemm_tma<EP, 128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
+    }
+    return cudaGetLastError();
+}
+
+// Latched status of the tcgen05 kernels that the layer primitives launch
+// (bit 4: a bounded wait ran out); gsvr_cnn_sync_status(NULL) reads and clears it.
+__device__ unsigned g_tc_status;
+unsigned *tc_status_word() {
+    static unsigned *p = nullptr;
+    if (!p) cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_tc_status);
+    return p;
+}
+// The tensor-memory path serves GEMMs whose output has at least this many
+// columns (narrower outputs waste most of the 128-column tile).
+constexpr int kTcMinCols = 64;
+
+template <class LA, class LB, class EP, int BN>
+cudaError_t gemm_tc_n(LA la, LB lb, EP ep, int rows, int cols, int Kred, const void *base, unsigned *status,
+                      cudaStream_t st) {
+    const dim3 grid((rows + TC_M - 1) / TC_M, (cols + BN - 1) / BN);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<LA, LB, EP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<BN>::SMEM);
+    if (e) return e;
+    k_gemm_tc<LA, LB, EP, BN><<<grid, TC_THREADS, TcCfg<BN>::SMEM, st>>>(la, lb, ep, Kred, base, status);
+    return cudaGetLastError();
+}
+// base: any valid global address (stands in for the zero-filled copies)
+template <class LA, class LB, class EP>
+cudaError_t gemm_tc(LA la, LB lb, EP ep, int rows, int cols, int Kred, const void *base, unsigned *status,
+                    cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || Kred <= 0) return cudaSuccess;
+    return cols <= 64 ? gemm_tc_n<LA, LB, EP, 64>(la, lb, ep, rows, cols, Kred, base, status, st)
+                      : gemm_tc_n<LA, LB, EP, 128>(la, lb, ep, rows, cols, Kred, base, status, st);
+}
+
+// Dense C[m][n] (float32, row-major, ld = N) epilogue for the standalone GEMM.
+struct EpiDense {
+    float *c;
+    int M, N;
+    __device__ void operator()(int m, int n, float v) const {
+        if (m < M && n < N) c[(size_t)m * N + n] = v;
+    }
+    __device__ void vec8(int m, int n0, const float *v) const {
+        if (m >= M) return;
+        if (n0 + 8 > N || (N & 3)) {
+            for (int j = 0; j < 8; ++j) (*this)(m, n0 + j, v[j]);
+            return;
+        }
+        float4 *d = reinterpret_cast<float4 *>(c + (size_t)m * N + n0);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
 
 // ------------------------------------------- reduction-major operands (wgrad)
 // Loaders of the transposed form: 8 bfloat16 values (kr, c0 .. c0 + 7) of an
@@ -372,6 +889,15 @@ struct LoadGy2x2 {  // A(m, k = (dy, dx, co)) = gy[b][i + dy][j + dx][co .. co +
         if (oh >= s.OH || ow >= s.OW) return zero4();
         return *reinterpret_cast<const uint4 *>(gy + (((size_t)b * s.OH + oh) * s.OW + ow) * s.Co + co);
     }
+    __device__ const bf16 *src(int m, int k0, int k_end) const {
+        if (m >= rows || k0 >= k_end) return nullptr;
+        int d, co, b, i, j;
+        chan_split(k0, s.Co, s.lCo, d, co);
+        pos_split(s, m, b, i, j);
+        const int oh = i + (d >> 1), ow = j + (d & 1);
+        if (oh >= s.OH || ow >= s.OW) return nullptr;
+        return gy + (((size_t)b * s.OH + oh) * s.OW + ow) * s.Co + co;
+    }
 };
 // W' [4 Ci][4 Co] from W [Co][3][3][Ci]
 __global__ void k_subpixel_weights(const bf16 *__restrict__ w, int Ci, int Co, bf16 *__restrict__ wp) {
@@ -400,6 +926,29 @@ struct EpiDx2x2 {  // dx[b][2i + ph][2j + pw][ci] = acc (times mask > 0), inside
         if (mask && !(__bfloat162float(mask[e]) > 0.f)) v = 0.f;
         dx[e] = __float2bfloat16(v);
         if (dx32) dx32[e] = v;
+    }
+    // columns n0 .. n0 + 7 (n0 % 8 == 0, Ci % 8 == 0: one sub-pixel q, channels ci .. ci + 7)
+    __device__ void vec8(int m, int n0, const float *v) const {
+        if (m >= rows || n0 >= 4 * s.Ci) return;
+        int q, ci, b, i, j;
+        chan_split(n0, s.Ci, s.lCi, q, ci);
+        pos_split(s, m, b, i, j);
+        const int ih = 2 * i + (q >> 1), iw = 2 * j + (q & 1);
+        if (ih >= s.H || iw >= s.W) return;
+        const size_t e = (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci;
+        float o[8];
+        uint4 mk = mask ? *reinterpret_cast<const uint4 *>(mask + e) : make_uint4(0, 0, 0, 0);
+        const bf16 *mb = reinterpret_cast<const bf16 *>(&mk);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) o[t] = (mask && !(__bfloat162float(mb[t]) > 0.f)) ? 0.f : v[t];
+        uint32_t pk[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) pk[t] = pack_bf16x2(o[2 * t], o[2 * t + 1]);
+        *reinterpret_cast<uint4 *>(dx + e) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        if (dx32) {
+            reinterpret_cast<float4 *>(dx32 + e)[0] = make_float4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<float4 *>(dx32 + e)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
     }
 };
 
@@ -644,20 +1193,54 @@ ConvShape conv_shape(int B, int H, int W, int Ci, int Co) {
 
 // --------------------------------------------------------- conv operations
 cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const float *bias, int relu, bf16 *y,
-                         float *y32, cudaStream_t st) {
+                         float *y32, unsigned *status, cudaStream_t st) {
     const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
     if (s.Ci == 1 && s.Co == 32 && relu && !y32) {
         k_conv1_fwd<<<blocks_for(M), 256, 0, st>>>(x, s, w, bias, y);
         return cudaGetLastError();
+    }
+    if (s.Co >= kTcMinCols) {
+        const EpiConv ep{y, y32, bias, M, s.Co, relu};
+        int bh, bb;
+        if (s.Ci % 64 == 0 && tile_rows(s, bh, bb)) {
+            CUtensorMap mA, mB;
+            const uint64_t dims[4] = {(uint64_t)s.Ci, (uint64_t)s.W, (uint64_t)s.H, (uint64_t)s.B};
+            const uint64_t strides[3] = {(uint64_t)s.Ci * 2, (uint64_t)s.W * s.Ci * 2, (uint64_t)s.H * s.W * s.Ci * 2};
+            const uint32_t box[4] = {(uint32_t)TC_K, (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb};
+            const uint32_t es[4] = {1, 2, 2, 1};
+            if (encode_map(&mA, x, 4, dims, strides, box, es) && map_rows(&mB, w, s.Co, K, s.Co <= 64 ? 64 : 128))
+                return launch_tma(mA, mB, TmaA{TMA_CONV, ilog2_exact(s.Ci), ilog2_exact(s.OH * s.OW), ilog2_exact(s.OW)},
+                                  ep, M, s.Co, K, status, st);
+        }
+        return gemm_tc(LoadIm2col{x, s, M, K}, LoadRows{w, s.Co, K}, ep, M, s.Co, K, w, status, st);
     }
     return gemm(LoadIm2col{x, s, M, K}, LoadRows{w, s.Co, K}, EpiConv{y, y32, bias, M, s.Co, relu}, M, s.Co, K, K,
                 st);
 }
 
 cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *wp, const bf16 *mask, bf16 *dx,
-                       float *dx32, cudaStream_t st) {
+                       float *dx32, unsigned *status, cudaStream_t st) {
     k_subpixel_weights<<<blocks_for((int64_t)16 * s.Ci * s.Co), 256, 0, st>>>(w, s.Ci, s.Co, wp);
     const int rows = s.B * s.OH * s.OW;
+    if (4 * s.Ci >= kTcMinCols) {
+        const EpiDx2x2 ep{dx, dx32, mask, s, rows};
+        int bh, bb;
+        if (s.Co % 64 == 0 && tile_rows(s, bh, bb)) {
+            CUtensorMap mA, mB;
+            const uint64_t dims[4] = {(uint64_t)s.Co, (uint64_t)s.OW, (uint64_t)s.OH, (uint64_t)s.B};
+            const uint64_t strides[3] = {(uint64_t)s.Co * 2, (uint64_t)s.OW * s.Co * 2,
+                                         (uint64_t)s.OH * s.OW * s.Co * 2};
+            const uint32_t box[4] = {(uint32_t)TC_K, (uint32_t)s.OW, (uint32_t)bh, (uint32_t)bb};
+            const uint32_t es[4] = {1, 1, 1, 1};
+            if (encode_map(&mA, gy, 4, dims, strides, box, es) &&
+                map_rows(&mB, wp, 4 * s.Ci, 4 * s.Co, 4 * s.Ci <= 64 ? 64 : 128))
+                return launch_tma(mA, mB,
+                                  TmaA{TMA_GY2X2, ilog2_exact(s.Co), ilog2_exact(s.OH * s.OW), ilog2_exact(s.OW)}, ep,
+                                  rows, 4 * s.Ci, 4 * s.Co, status, st);
+        }
+        return gemm_tc(LoadGy2x2{gy, s, rows}, LoadRows{wp, 4 * s.Ci, 4 * s.Co}, ep, rows, 4 * s.Ci, 4 * s.Co, wp,
+                       status, st);
+    }
     return gemm(LoadGy2x2{gy, s, rows}, LoadRows{wp, 4 * s.Ci, 4 * s.Co}, EpiDx2x2{dx, dx32, mask, s, rows}, rows,
                 4 * s.Ci, 4 * s.Co, 4 * s.Co, st);
 }
@@ -768,6 +1351,7 @@ struct gsvr_cnn {
     float *fc1part = nullptr; // fc1 split-K partial sums
     float *fc1wpart = nullptr;  // fc1 weight-gradient partial sums over batch splits
     float *h = nullptr, *z1 = nullptr, *a1 = nullptr, *out = nullptr, *dout = nullptr, *dz1 = nullptr, *dh = nullptr;
+    unsigned *status = nullptr;  // device word: bit 4 = a tensor-memory GEMM's bounded wait ran out
     std::vector<void *> allocs;
     ~gsvr_cnn() {
         for (void *p : allocs) cudaFree(p);
@@ -817,7 +1401,7 @@ gsvr_status run_forward(gsvr_cnn *n, const float *x, const float *aux, int B) {
     for (int l = 0; l < kLayers; ++l) {
         const ConvShape s = conv_shape(B, layer_size(l), layer_size(l), kCh[l], kCh[l + 1]);
         cudaError_t e = conv_forward(n->act[l], s, n->wbf + n->off_w[l], n->params + n->off_b[l], 1, n->act[l + 1],
-                                     nullptr, st);
+                                     nullptr, n->status, st);
         if (e != cudaSuccess) return cuda_status(n, e, "conv forward");
     }
     const int F = layer_size(kLayers) * layer_size(kLayers) * kCh[kLayers], HD = F + kAux;
@@ -905,6 +1489,8 @@ gsvr_status gsvr_cnn_create(gsvr_cnn **out, int32_t device, void *stream, int32_
     if (!e) e = n->alloc(n->dout, (size_t)B * kOut);
     if (!e) e = n->alloc(n->dz1, (size_t)B * kHidden);
     if (!e) e = n->alloc(n->dh, (size_t)B * HD);
+    if (!e) e = n->alloc(n->status, 1);
+    if (!e) e = cudaMemset(n->status, 0, sizeof(unsigned));
     if (!e) e = cudaMemcpy(n->params, p.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(n->grads, 0, sizeof(float) * o);
     if (!e) e = cudaMemset(n->m, 0, sizeof(float) * o);
@@ -929,6 +1515,25 @@ gsvr_status gsvr_cnn_destroy(gsvr_cnn *n) {
 }
 
 const char *gsvr_cnn_last_error(gsvr_cnn *n) { return n ? n->err.c_str() : g_cnn_error.c_str(); }
+
+gsvr_status gsvr_cnn_sync_status(gsvr_cnn *n) {
+    unsigned word = 0;
+    cudaError_t e;
+    if (n) {
+        DevGuard g(n->device);
+        e = cudaStreamSynchronize(n->st);
+        if (!e) e = cudaMemcpy(&word, n->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (!e) e = cudaMemset(n->status, 0, sizeof(unsigned));
+    } else {
+        e = cudaDeviceSynchronize();
+        if (!e) e = cudaMemcpyFromSymbol(&word, g_tc_status, sizeof(unsigned));
+        const unsigned zero = 0;
+        if (!e) e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(unsigned));
+    }
+    if (e) return cuda_status(n, e, "sync status");
+    if (word & 4u) return nfail(n, GSVR_ERR_TIMEOUT, "a tensor-memory GEMM's bounded wait ran out");
+    return GSVR_OK;
+}
 
 gsvr_status gsvr_cnn_views(gsvr_cnn *n, float **params, float **grads, int64_t *n_params) {
     if (!n) return GSVR_ERR_INVALID_ARG;
@@ -985,7 +1590,7 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
         if (e) return cuda_status(n, e, "conv wgrad");
         if (l > 0) {
             e = conv_dgrad(n->gpre[l + 1], sh, n->wbf + n->off_w[l], n->wt, n->act[l], n->gpre[l], nullptr,
-                           st);
+                           n->status, st);
             if (e) return cuda_status(n, e, "conv dgrad");
         }
     }
@@ -1010,14 +1615,16 @@ gsvr_status gsvr_cnn_conv_forward(void *stream, const uint16_t *x, int32_t B, in
                                   float *y32) {
     g_cnn_error.clear();
     if (!x || !w || !y || B < 1 || H < 1 || W < 1 || Ci < 1 || Co < 2 || (Co & 1) || (Ci % 8 && Ci != 1) ||
-        !aligned16(x) || !aligned16(w) || (int64_t)B * H * W > (1LL << 30))
+        !aligned16(x) || !aligned16(w) || !aligned16(y) || (y32 && !aligned16(y32)) ||
+        (int64_t)B * H * W > (1LL << 30))
         return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv forward arguments");
     const ConvShape s = conv_shape(B, H, W, Ci, Co);
     if (Ci == 1 && !(Co == 32 && relu && !y32 && bias))
         return nfail(nullptr, GSVR_ERR_INVALID_ARG, "one input channel: Co 32, ReLU, bias, no y32");
     return cuda_status(nullptr,
                        conv_forward(reinterpret_cast<const bf16 *>(x), s, reinterpret_cast<const bf16 *>(w), bias, relu,
-                                    reinterpret_cast<bf16 *>(y), y32, static_cast<cudaStream_t>(stream)),
+                                    reinterpret_cast<bf16 *>(y), y32, tc_status_word(),
+                                    static_cast<cudaStream_t>(stream)),
                        "conv forward");
 }
 
@@ -1025,7 +1632,8 @@ gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int
                                 const uint16_t *w, int32_t Co, const uint16_t *mask, uint16_t *dx, float *dx32) {
     g_cnn_error.clear();
     if (!gy || !w || !dx || B < 1 || H < 1 || W < 1 || Ci < 8 || (Ci % 8) || Co < 8 || (Co % 8) ||
-        !aligned16(gy) || !aligned16(w) || (int64_t)B * H * W > (1LL << 30))
+        !aligned16(gy) || !aligned16(w) || !aligned16(dx) || (dx32 && !aligned16(dx32)) ||
+        (mask && !aligned16(mask)) || (int64_t)B * H * W > (1LL << 30))
         return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv dgrad arguments (Ci, Co multiples of 8)");
     const ConvShape s = conv_shape(B, H, W, Ci, Co);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1033,9 +1641,33 @@ gsvr_status gsvr_cnn_conv_dgrad(void *stream, const uint16_t *gy, int32_t B, int
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&wt), sizeof(bf16) * 16 * Ci * Co, st);
     if (e) return cuda_status(nullptr, e, "scratch");
     e = conv_dgrad(reinterpret_cast<const bf16 *>(gy), s, reinterpret_cast<const bf16 *>(w), wt,
-                   reinterpret_cast<const bf16 *>(mask), reinterpret_cast<bf16 *>(dx), dx32, st);
+                   reinterpret_cast<const bf16 *>(mask), reinterpret_cast<bf16 *>(dx), dx32, tc_status_word(), st);
     cudaFreeAsync(wt, st);
     return cuda_status(nullptr, e, "conv dgrad");
+}
+
+gsvr_status gsvr_cnn_gemm(void *stream, const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K, float *C,
+                          int32_t tensor_memory, unsigned *status) {
+    g_cnn_error.clear();
+    if (!A || !B || !C || M < 1 || N < 1 || K < 8 || (K % 8) || !aligned16(A) || !aligned16(B) || !aligned16(C) ||
+        tensor_memory < 0 || tensor_memory > 2 || (tensor_memory && !status) || (int64_t)M * K > (1LL << 31) || (int64_t)N * K > (1LL << 31))
+        return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad gemm arguments (K a multiple of 8)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const LoadRows la{reinterpret_cast<const bf16 *>(A), M, K}, lb{reinterpret_cast<const bf16 *>(B), N, K};
+    const EpiDense ep{C, M, N};
+    cudaError_t e;
+    if (tensor_memory == 1) {
+        CUtensorMap mA, mB;
+        if (!map_rows(&mA, reinterpret_cast<const bf16 *>(A), M, K, TC_M) ||
+            !map_rows(&mB, reinterpret_cast<const bf16 *>(B), N, K, N <= 64 ? 64 : 128))
+            return nfail(nullptr, GSVR_ERR_CUDA, "tensor map encoding failed");
+        e = launch_tma(mA, mB, TmaA{TMA_ROWS, 0, 0, 0}, ep, M, N, K, status, st);
+    } else if (tensor_memory == 2) {
+        e = gemm_tc(la, lb, ep, M, N, K, B, status, st);
+    } else {
+        e = gemm(la, lb, ep, M, N, K, K, st);
+    }
+    return cuda_status(nullptr, e, "gemm");
 }
 
 gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t *x, int32_t B, int32_t H, int32_t W,

@@ -50,6 +50,7 @@ def test_conv_forward(T, B, H, W, Ci, Co):
         ok, worst = close(got, ref, absref)
         assert ok.all(), worst
         assert np.array_equal(y.float().cpu().numpy(), ocnn.bf16(got).astype(np.float32))
+    cnn.sync_status()
 
 
 def test_first_layer_direct(T):
@@ -89,6 +90,7 @@ def test_conv_dgrad(T, B, H, W, Ci, Co):
     assert np.all(gotm[mask <= 0] == 0)
     assert np.array_equal(gotm[mask > 0], dx32.cpu().numpy()[mask > 0])
     assert np.array_equal(dxm.float().cpu().numpy(), ocnn.bf16(gotm).astype(np.float32))
+    cnn.sync_status()
 
 
 @pytest.mark.parametrize("B,H,W,Ci,Co", SHAPES)
@@ -105,6 +107,28 @@ def test_conv_wgrad(T, B, H, W, Ci, Co):
     adb = np.abs(gy).sum(axis=(0, 1, 2))
     ok, worst = close(db.cpu().numpy().astype(np.float64), rdb, adb)
     assert ok.all(), worst
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 72), (1000, 300, 520), (7, 129, 8), (4096, 512, 2304)])
+def test_gemm_tensor_memory(T, M, N, K):
+    """The tcgen05 GEMM (tensor-memory accumulators) with tensor-map operand
+    copies (1) and with per-thread copies (2), and the mma.sync GEMM (0),
+    against a float64 product of the same bfloat16 operands, at tile-aligned,
+    ragged and one-row-short shapes.  Both accumulate in float32, so each
+    element stays within 1e-5 of the exact value relative to sum_k |a b|
+    (a float32 sum of at most 2304 terms)."""
+    torch, cnn = T
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
+    ref = (A.double() @ B.double().T).cpu().numpy()
+    absref = (A.double().abs() @ B.double().abs().T).cpu().numpy()
+    for tm in (1, 2, 0):
+        C, status = cnn.gemm(A, B, tensor_memory=tm)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        ok, worst = close(C.cpu().numpy().astype(np.float64), ref, absref, rtol=1e-5, atol_rel=1e-5)
+        assert ok.all(), (tm, worst)
 
 
 def oracle_params(net):
@@ -146,6 +170,7 @@ def test_network_loss_and_gradients(T):
                     max(np.linalg.norm(gv[name]) * np.linalg.norm(ref), 1e-300))
         print("%s rel %.3e cos %.6f" % (name, rel, cos))
         assert rel <= 5e-2 and cos >= 0.999, (name, rel, cos)
+    net.sync_status()
     net.close()
 
 
