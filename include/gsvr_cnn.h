@@ -109,7 +109,11 @@ gsvr_status gsvr_cnn_adam_step(gsvr_cnn *net, float lr, float beta1, float beta2
  *   and dx32 (float32, may be NULL).  One GEMM in sub-pixel form: each output
  *   position feeds its 2 x 2 input pixels through the taps that reach them.
  * gsvr_cnn_conv_wgrad: dw [Co][3][3][Ci] += sum over positions of gy x-patch,
- *   db [Co] += sum of gy (float32, accumulated: zero them first). */
+ *   db [Co] += sum of gy (float32, accumulated: zero them first; dw 16-byte
+ *   aligned).  With Ci a multiple of 64 and the output grid tiled as above
+ *   (64-position steps) it runs on tcgen05.mma with both operands MN-major,
+ *   the position range split over CTAs that add their tiles atomically (the
+ *   summation order, and so the last bits, vary from run to run). */
 gsvr_status gsvr_cnn_conv_forward(void *stream, const uint16_t *x, int32_t B, int32_t H, int32_t W, int32_t Ci,
                                   const uint16_t *w, const float *bias, int32_t Co, int32_t relu, uint16_t *y,
                                   float *y32);

@@ -55,15 +55,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
 }
-__device__ __forceinline__ uint4 pack8(const bf16 v[8]) {
-    uint4 u;
-    uint32_t *p = reinterpret_cast<uint32_t *>(&u);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        p[i] = (uint32_t)__bfloat16_as_ushort(v[2 * i]) | ((uint32_t)__bfloat16_as_ushort(v[2 * i + 1]) << 16);
-    return u;
-}
-
 struct ConvShape {
     int B, H, W, Ci, OH, OW, Co;
     int lOW, lOH, lCi, lCo;  // log2 of OW, OH, Ci, Co when a power of two, else -1
@@ -667,17 +658,17 @@ int ilog2_exact(int v) {  // log2 of a power of two, else -1
     while ((1 << l) < v) ++l;
     return l;
 }
-// Tile of 128 output rows as (images bb) x (rows bh) x (all OW columns);
-// false when the output grid does not split that way.
-bool tile_rows(const ConvShape &s, int &bh, int &bb) {
+// Tile of `rows` (a power of two) output positions as (images bb) x (rows
+// bh) x (all OW columns); false when the output grid does not split that way.
+bool tile_rows(const ConvShape &s, int &bh, int &bb, int rows = TC_M) {
     const int P = s.OH * s.OW;
-    if (ilog2_exact(s.OW) < 0 || ilog2_exact(P) < 0 || s.OW > 128) return false;
-    if (P >= TC_M) {
-        bh = TC_M / s.OW;
+    if (ilog2_exact(s.OW) < 0 || ilog2_exact(P) < 0 || s.OW > rows) return false;
+    if (P >= rows) {
+        bh = rows / s.OW;
         bb = 1;
     } else {
         bh = s.OH;
-        bb = TC_M / P;
+        bb = rows / P;
     }
     return true;
 }
@@ -698,6 +689,166 @@ cudaError_t launch_tma(const CUtensorMap &mA, const CUtensorMap &mB, TmaA ta, EP
         k_gemm_tma<EP, 128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
     }
     return cudaGetLastError();
+}
+
+// ------------------------------------ tcgen05 weight gradient (MN-major)
+// dW[co][n] += sum over positions m of gy[m][co] X[m][n], n = (tap, ci) the
+// im2col column: the reduction runs over positions, which are the outer index
+// of both operands in memory, so both tiles are MN-major: per 64-position K
+// step, gy [M][Co] gives two tensor-map boxes of 64 channels x 64 positions
+// (channels contiguous, 128-byte swizzle) and the input x gives BN / 64 boxes
+// of 64 input channels x 64 positions of one tap (the stride-2 4-D map of the
+// forward, its 64-position step whole output rows or images).  The smem
+// descriptors of the MN-major 128-byte-swizzled layout take the stride between
+// 64-element channel atoms (8 KB here) as leading byte offset and the stride
+// between 8-position groups (1024 B) as stride byte offset; the instruction
+// descriptor sets transpose A and B.  The position range is split over
+// blockIdx.z; each split adds its tile into dw with float4 atomics.
+constexpr int WG_K = 64;  // positions per K step
+__device__ __forceinline__ uint64_t tc_smem_desc_mn(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(8192u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+template <int BN>
+__global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap mapG,
+                                                           const __grid_constant__ CUtensorMap mapX, TmaA tx,
+                                                           float *__restrict__ dw, int Co, int K9, int nk_total,
+                                                           int steps, unsigned *status) {
+    using Cfg = TcCfg<BN>;
+    constexpr int S = Cfg::STAGES;
+    constexpr uint32_t IDESC = Cfg::IDESC | (1u << 15) | (1u << 16);  // A and B MN-major
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int co0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * steps, ke = min(nk_total, kb + steps), nk = ke - kb;
+    const uint32_t sbase = (gsvr::smem_u32(tc_raw) + 1023u) & ~1023u;
+    if (nk <= 0) return;
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsvr::smem_u32(&s_tmem)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            gsvr::mbar_init(&full[i], 1);
+            gsvr::mbar_init(&empty[i], 1);
+        }
+        gsvr::mbar_init(&done, 1);
+        gsvr::fence_mbar_init();
+        s_fail = 0;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapG)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapX)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (warp == 0 && lane == 0) {
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % S;
+            if (i >= S && !gsvr::mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1u, kTcWaitNs)) s_fail = 1;
+            if (s_fail) break;
+            const uint32_t sa = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), sb = sa + Cfg::A_BYTES;
+            const int m = (kb + i) * WG_K;
+            const int b0 = m >> tx.lP, oh0 = (m - (b0 << tx.lP)) >> tx.lOW;
+            gsvr::mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::STAGE_BYTES);
+            tma_load_2d(sa, &mapG, co0, m, &full[s]);
+            tma_load_2d(sa + 8192u, &mapG, co0 + 64, m, &full[s]);
+#pragma unroll
+            for (int a = 0; a < BN / 64; ++a) {
+                const int n = n0 + 64 * a, t = n >> tx.lC, c0 = n & ((1 << tx.lC) - 1);
+                const int kh = (t * 11) >> 5, kw = t - 3 * kh;
+                tma_load_4d(sb + 8192u * a, &mapX, c0, kw - 1, 2 * oh0 + kh - 1, b0, &full[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % S;
+            if (s_fail || !gsvr::mbar_wait_bounded(&full[s], (i / S) & 1u, kTcWaitNs)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), b0 = a0 + Cfg::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < WG_K / 16; ++kk)  // 16 positions = two 8-position groups = 2048 B
+                tc_mma(tmem, tc_smem_desc_mn(a0 + kk * 2048), tc_smem_desc_mn(b0 + kk * 2048), IDESC,
+                       (i > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty[s]);
+        }
+        tc_commit(&done);
+    }
+    __syncwarp();
+    bool bad = s_fail;
+    if (!bad && !gsvr::mbar_wait_bounded(&done, 0u, kTcWaitNs)) bad = true;
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad) s_fail = 1;
+    tc_fence_after();
+    if (!bad) {
+        const int co = co0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (co < Co) {
+                float4 *d = reinterpret_cast<float4 *>(dw + (size_t)co * K9 + n0 + c0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    atomicAdd(d + j, make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3])));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicOr(status, 4u);
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                     : "memory");
+}
+
+// db[c] += sum over rows m of g[m][c] (bfloat16 [M][C], C % 8 == 0): block
+// (x, y) covers channels 256 y .. 256 y + 255 (lane l: 8 channels by one
+// 16-byte load) over the rows m = x, x + gridDim.x * 8, ... of its 8 warps
+// (warp w from row x * 8 + w); the warps' sums meet in shared memory, one
+// atomic per (block, channel).
+__global__ void __launch_bounds__(256) k_colsum_bf16_add(const bf16 *__restrict__ g, int M, int C,
+                                                         float *__restrict__ db) {
+    __shared__ float red[8][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c0 = blockIdx.y * 256 + lane * 8;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (c0 < C) {
+        for (int m = blockIdx.x * 8 + warp; m < M; m += gridDim.x * 8) {
+            const uint4 u = *reinterpret_cast<const uint4 *>(g + (size_t)m * C + c0);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] += __bfloat162float(h[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) red[warp][lane * 8 + e] = v[e];
+    __syncthreads();
+    const int c = blockIdx.y * 256 + threadIdx.x;
+    if (c < C) {
+        float t = 0.f;
+#pragma unroll
+        for (int w8 = 0; w8 < 8; ++w8) t += red[w8][threadIdx.x];
+        atomicAdd(&db[c], t);
+    }
 }
 
 // Latched status of the tcgen05 kernels that the layer primitives launch
@@ -958,38 +1109,85 @@ __global__ void k_to_bf16(const float *__restrict__ a, int64_t n, bf16 *__restri
         b[e] = __float2bfloat16(a[e]);
 }
 
-// First layer (one input channel, 32 outputs): a thread per output position.
-__global__ void k_conv1_fwd(const bf16 *__restrict__ x, ConvShape s, const bf16 *__restrict__ w,
-                            const float *__restrict__ bias, bf16 *__restrict__ y) {
-    __shared__ float ws[32 * 9], bs[32];
-    for (int e = threadIdx.x; e < 32 * 9; e += blockDim.x) ws[e] = __bfloat162float(w[e]);
+// First layer (one input channel, 32 outputs): four threads per output
+// position, thread q of a position computing channels 8 q .. 8 q + 7 (weights
+// read from shared memory as float4, a channel pair at a time) and storing
+// them as one 16-byte vector;
+// a warp covers 8 consecutive positions, 512 contiguous output bytes.  Each
+// iteration gathers the patches of two positions before computing, so that
+// twice the loads are in flight.
+__device__ __forceinline__ void conv1_patch(const bf16 *__restrict__ x, const ConvShape &s, int m, float xv[9]) {
+    int b, oh, ow;
+    pos_split(s, m, b, oh, ow);
+#pragma unroll
+    for (int kh = 0; kh < 3; ++kh)
+#pragma unroll
+        for (int kw = 0; kw < 3; ++kw) {
+            const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
+            xv[kh * 3 + kw] = (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
+                                  ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
+                                  : 0.f;
+        }
+}
+// shared-memory float4 read kept inside its loop (a volatile asm is not
+// hoisted), so that loop-invariant weights are re-read instead of held in
+// registers
+__device__ __forceinline__ float4 lds_f4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_addr(p)));
+    return v;
+}
+__global__ void __launch_bounds__(256) k_conv1_fwd(const bf16 *__restrict__ x, ConvShape s,
+                                                   const bf16 *__restrict__ w, const float *__restrict__ bias,
+                                                   bf16 *__restrict__ y) {
+    // wp4[(q * 4 + p) * 5 + i]: channels c = 8 q + 2 p and c + 1, their 9 taps
+    // each (floats 0-8, 9-17), 2 zero pads: one channel pair is 5 float4 reads
+    __shared__ float4 wp4[16 * 5];
+    __shared__ float bs[32];
+    float *wf = reinterpret_cast<float *>(wp4);
+    for (int e = threadIdx.x; e < 16 * 20; e += blockDim.x) {
+        const int pair = e / 20, i = e - 20 * pair, c = 2 * pair + (i >= 9 ? 1 : 0), k = i >= 9 ? i - 9 : i;
+        wf[e] = i < 18 ? __bfloat162float(w[c * 9 + k]) : 0.f;
+    }
     for (int e = threadIdx.x; e < 32; e += blockDim.x) bs[e] = bias[e];
     __syncthreads();
-    const int64_t M = (int64_t)s.B * s.OH * s.OW;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
-        int b, oh, ow;
-        pos_split(s, (int)m, b, oh, ow);
-        float xv[9];
+    const int q = threadIdx.x & 3;
+    const int64_t n = (int64_t)s.B * s.OH * s.OW * 4, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
+        const int m0 = (int)(e >> 2);
+        const bool two = e + stride < n;
+        const int m1 = two ? (int)((e + stride) >> 2) : m0;
+        float xa[9], xb[9];
+        conv1_patch(x, s, m0, xa);
+        conv1_patch(x, s, m1, xb);
+        uint32_t pa[4], pb[4];
 #pragma unroll
-        for (int kh = 0; kh < 3; ++kh)
+        for (int p = 0; p < 4; ++p) {
+            float wv[20];
 #pragma unroll
-            for (int kw = 0; kw < 3; ++kw) {
-                const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
-                xv[kh * 3 + kw] = (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
-                                      ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
-                                      : 0.f;
+            for (int i = 0; i < 5; ++i) {
+                const float4 t = lds_f4(&wp4[(q * 4 + p) * 5 + i]);
+                wv[4 * i] = t.x;
+                wv[4 * i + 1] = t.y;
+                wv[4 * i + 2] = t.z;
+                wv[4 * i + 3] = t.w;
             }
-        bf16 out[32];
+            const float b0 = bs[8 * q + 2 * p], b1 = bs[8 * q + 2 * p + 1];
+            float a0 = b0, a1 = b1, c0 = b0, c1 = b1;
 #pragma unroll
-        for (int co = 0; co < 32; ++co) {
-            float v = bs[co];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v = fmaf(ws[co * 9 + k], xv[k], v);
-            out[co] = __float2bfloat16(fmaxf(v, 0.f));
+            for (int k = 0; k < 9; ++k) {
+                a0 = fmaf(wv[k], xa[k], a0);
+                a1 = fmaf(wv[9 + k], xa[k], a1);
+                c0 = fmaf(wv[k], xb[k], c0);
+                c1 = fmaf(wv[9 + k], xb[k], c1);
+            }
+            pa[p] = pack_bf16x2(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
+            pb[p] = pack_bf16x2(fmaxf(c0, 0.f), fmaxf(c1, 0.f));
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)m * 32);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = pack8(out + 8 * q);
+        *reinterpret_cast<uint4 *>(y + (size_t)m0 * 32 + 8 * q) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+        if (two) *reinterpret_cast<uint4 *>(y + (size_t)m1 * 32 + 8 * q) = make_uint4(pb[0], pb[1], pb[2], pb[3]);
     }
 }
 
@@ -1128,17 +1326,26 @@ __global__ void k_part_sum(const float *__restrict__ part, int splits, int64_t n
         out[e] = v;
     }
 }
-// db[j] = sum_b d[b][j]
-__global__ void k_colsum(const float *__restrict__ d, int B, int J, float *__restrict__ db) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= J) return;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int b = 0;
-    for (; b + 8 <= B; b += 8)
+// db[j] += sum_b d[b][j]: block (x, y) takes columns 32 x .. 32 x + 31 (a
+// lane each) and rows 32 y .. 32 y + 31 (4 per warp); the warps meet in
+// shared memory, one atomic per (block, column).
+__global__ void __launch_bounds__(256) k_colsum_add(const float *__restrict__ d, int B, int J,
+                                                    float *__restrict__ db) {
+    __shared__ float red[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.x * 32 + lane;
+    float v = 0.f;
+    if (j < J) {
+        const int b1 = min(B, (int)blockIdx.y * 32 + 32);
+        for (int b = blockIdx.y * 32 + warp; b < b1; b += 8) v += d[(size_t)b * J + j];
+    }
+    red[warp][lane] = v;
+    __syncthreads();
+    if (warp == 0 && j < J) {
+        float t = 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] += d[(size_t)(b + u) * J + j];
-    for (; b < B; ++b) v[0] += d[(size_t)b * J + j];
-    db[j] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        for (int w8 = 0; w8 < 8; ++w8) t += red[w8][lane];
+        atomicAdd(&db[j], t);
+    }
 }
 // d = 2 (out - target) / (6 B); loss = mean squared error (one block).
 __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ tgt, int n, float *__restrict__ d,
@@ -1196,7 +1403,7 @@ cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const
                          float *y32, unsigned *status, cudaStream_t st) {
     const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
     if (s.Ci == 1 && s.Co == 32 && relu && !y32) {
-        k_conv1_fwd<<<blocks_for(M), 256, 0, st>>>(x, s, w, bias, y);
+        k_conv1_fwd<<<blocks_for((int64_t)M * 4, 256 * 4), 256, 0, st>>>(x, s, w, bias, y);
         return cudaGetLastError();
     }
     if (s.Co >= kTcMinCols) {
@@ -1245,66 +1452,72 @@ cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *
                 4 * s.Ci, 4 * s.Co, 4 * s.Co, st);
 }
 
-// Per block: partial first-layer weight gradients of a run of positions.  Each
-// round stages 256 positions' output gradients (32 channels) and input taps
-// (9, plus 1 for the bias) in shared memory with coalesced loads; thread o
-// (and o + 256 < 320) accumulates output (co, tap) = (o / 10, o % 10) over the
-// round.  part[block][320] is added over blocks by k_conv1_wgrad_sum.
+// Per block: partial first-layer weight gradients over a grid-strided set of
+// positions.  Four threads per position: thread q accumulates the 8 x 10
+// products (channels 8 q .. 8 q + 7) x (9 taps and the bias's 1) of the
+// positions it visits in registers (two positions per iteration, their loads
+// in flight together); the block then sums the lanes that share
+// q (shuffles) and the warps (shared memory) into part[block][320], ordered
+// (co, tap) with the bias last.  k_conv1_wgrad_sum adds the blocks.
 __global__ void __launch_bounds__(256) k_conv1_wgrad_part(const bf16 *__restrict__ g, const bf16 *__restrict__ x,
                                                           ConvShape s, float *__restrict__ part) {
-    __shared__ float sg[256][33];
-    __shared__ float sx[256][10];
-    const int tid = threadIdx.x;
-    const int M = s.B * s.OH * s.OW;
-    const int per = ((M + gridDim.x - 1) / gridDim.x + 255) / 256 * 256;
-    const int m0 = blockIdx.x * per, m1 = min(M, m0 + per);
-    const int co0 = tid / 10, k0 = tid - 10 * co0;
-    const int o1 = tid + 256, co1 = o1 / 10, k1 = o1 - 10 * co1;
-    float acc0 = 0.f, acc1 = 0.f;
-    for (int mb = m0; mb < m1; mb += 256) {
-        const int m = mb + tid;
-        if (m < m1) {
-            const uint4 *gr = reinterpret_cast<const uint4 *>(g + (size_t)m * 32);
+    __shared__ float red[8][320];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, q = lane & 3;
+    float acc[8][10];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 u = gr[q];
-                const bf16 *h = reinterpret_cast<const bf16 *>(&u);
+    for (int c = 0; c < 8; ++c)
 #pragma unroll
-                for (int e = 0; e < 8; ++e) sg[tid][8 * q + e] = __bfloat162float(h[e]);
-            }
-            int b, oh, ow;
-            pos_split(s, m, b, oh, ow);
+        for (int t = 0; t < 10; ++t) acc[c][t] = 0.f;
+    const int64_t n = (int64_t)s.B * s.OH * s.OW * 4, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < n; e += 2 * stride) {
+        // two positions per iteration (their loads in flight together); the
+        // second is skipped past the end by a zero gradient
+        const int m0 = (int)(e >> 2);
+        const bool two = e + stride < n;
+        const int m1 = two ? (int)((e + stride) >> 2) : m0;
+        const uint4 u0 = *reinterpret_cast<const uint4 *>(g + (size_t)m0 * 32 + 8 * q);
+        const uint4 u1 = two ? *reinterpret_cast<const uint4 *>(g + (size_t)m1 * 32 + 8 * q) : make_uint4(0, 0, 0, 0);
+        float xa[9], xb[9];
+        conv1_patch(x, s, m0, xa);
+        conv1_patch(x, s, m1, xb);
+        const bf16 *h0 = reinterpret_cast<const bf16 *>(&u0), *h1 = reinterpret_cast<const bf16 *>(&u1);
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const int ih = 2 * oh - 1 + t / 3, iw = 2 * ow - 1 + t % 3;
-                sx[tid][t] = (ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
-                                 ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
-                                 : 0.f;
-            }
-            sx[tid][9] = 1.f;
-        } else {
+        for (int c = 0; c < 8; ++c) {
+            const float g0 = __bfloat162float(h0[c]), g1 = __bfloat162float(h1[c]);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) sg[tid][e] = 0.f;
-#pragma unroll
-            for (int t = 0; t < 10; ++t) sx[tid][t] = 0.f;
+            for (int t = 0; t < 9; ++t) acc[c][t] = fmaf(g1, xb[t], fmaf(g0, xa[t], acc[c][t]));
+            acc[c][9] += g0 + g1;
         }
-        __syncthreads();
-        const int np = min(256, m1 - mb);
-        for (int p = 0; p < np; ++p) {
-            acc0 = fmaf(sg[p][co0], sx[p][k0], acc0);
-            if (o1 < 320) acc1 = fmaf(sg[p][co1], sx[p][k1], acc1);
-        }
-        __syncthreads();
     }
-    part[(size_t)blockIdx.x * 320 + tid] = acc0;
-    if (o1 < 320) part[(size_t)blockIdx.x * 320 + o1] = acc1;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int t = 0; t < 10; ++t) {
+            float v = acc[c][t];
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (lane < 4) red[warp][(8 * q + c) * 10 + t] = v;
+        }
+    __syncthreads();
+    for (int o = tid; o < 320; o += blockDim.x) {
+        float v = 0.f;
+#pragma unroll
+        for (int w8 = 0; w8 < 8; ++w8) v += red[w8][o];
+        part[(size_t)blockIdx.x * 320 + o] = v;
+    }
 }
+// dw[co][tap] += sum over blocks of part[.][co * 10 + tap], db[co] likewise
+// (tap 9): a warp per output, lanes striding over the blocks.
 __global__ void k_conv1_wgrad_sum(const float *__restrict__ part, int nb, float *__restrict__ dw,
                                   float *__restrict__ db) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= 320) return;
     float v = 0.f;
-    for (int b = 0; b < nb; ++b) v += part[(size_t)b * 320 + e];
+    for (int b = lane; b < nb; b += 32) v += part[(size_t)b * 320 + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane) return;
     const int co = e / 10, k = e - 10 * co;
     if (k < 9) dw[co * 9 + k] += v;
     else db[co] += v;
@@ -1312,13 +1525,50 @@ __global__ void k_conv1_wgrad_sum(const float *__restrict__ part, int nb, float 
 constexpr int kConv1Blocks = 148 * 4;
 
 cudaError_t conv_wgrad(const bf16 *gy, const bf16 *x, const ConvShape &s, float *dw, float *db, float *scratch,
-                       cudaStream_t st) {
+                       unsigned *status, cudaStream_t st) {
     const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
     if (s.Ci == 1 && s.Co == 32) {
-        const int nb = std::max(1, std::min(kConv1Blocks, (M + 255) / 256));
+        const int nb = std::max(1, std::min(kConv1Blocks, (4 * M + 255) / 256));
         k_conv1_wgrad_part<<<nb, 256, 0, st>>>(gy, x, s, scratch);
-        k_conv1_wgrad_sum<<<2, 256, 0, st>>>(scratch, nb, dw, db);
+        k_conv1_wgrad_sum<<<320 * 32 / 256, 256, 0, st>>>(scratch, nb, dw, db);
         return cudaGetLastError();
+    }
+    int bh, bb;
+    if (s.Ci % 64 == 0 && tile_rows(s, bh, bb, WG_K)) {
+        // tensor-memory path: bias gradient by a column sum, dW by k_wgrad_tma
+        CUtensorMap mG, mX;
+        const uint64_t gd[2] = {(uint64_t)s.Co, (uint64_t)M}, gs[1] = {(uint64_t)s.Co * 2};
+        const uint32_t gb[2] = {64, (uint32_t)WG_K}, ge[2] = {1, 1};
+        const uint64_t xd[4] = {(uint64_t)s.Ci, (uint64_t)s.W, (uint64_t)s.H, (uint64_t)s.B};
+        const uint64_t xs[3] = {(uint64_t)s.Ci * 2, (uint64_t)s.W * s.Ci * 2, (uint64_t)s.H * s.W * s.Ci * 2};
+        const uint32_t xb[4] = {64, (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb}, xe[4] = {1, 2, 2, 1};
+        if (encode_map(&mG, gy, 2, gd, gs, gb, ge) && encode_map(&mX, x, 4, xd, xs, xb, xe)) {
+            if (db) {
+                const int cb = (s.Co + 255) / 256, bx = std::max(1, std::min((M + 63) / 64, 592 / cb));
+                k_colsum_bf16_add<<<dim3(bx, cb), 256, 0, st>>>(gy, M, s.Co, db);
+            }
+            const int bn = (K % 128 == 0) ? 128 : 64;
+            const int nk = (M + WG_K - 1) / WG_K, tiles = ((s.Co + TC_M - 1) / TC_M) * (K / bn);
+            const int splits = std::max(1, std::min(nk, (148 * 2 + tiles - 1) / tiles));
+            const int steps = (nk + splits - 1) / splits;
+            const dim3 grid((s.Co + TC_M - 1) / TC_M, K / bn, (nk + steps - 1) / steps);
+            const TmaA tx{TMA_CONV, ilog2_exact(s.Ci), ilog2_exact(s.OH * s.OW), ilog2_exact(s.OW)};
+            cudaError_t e;
+            if (bn == 128) {
+                e = cudaFuncSetAttribute(k_wgrad_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<128>::SMEM);
+                if (e) return e;
+                k_wgrad_tma<128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk, steps,
+                                                                              status);
+            } else {
+                e = cudaFuncSetAttribute(k_wgrad_tma<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<64>::SMEM);
+                if (e) return e;
+                k_wgrad_tma<64><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk, steps,
+                                                                            status);
+            }
+            return cudaGetLastError();
+        }
     }
     // reduction over positions split so that the grid fills the GPU a few times
     const int tiles = ((s.Co + BM - 1) / BM) * ((K + 1 + BN - 1) / BN);
@@ -1570,7 +1820,7 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
     float *gr = n->grads;
     const float *p = n->params;
     sgemm(n->dout, 1, kOut, n->a1, 1, kHidden, kOut, kHidden, B, EpiF{gr + n->off_fc2w, nullptr, kOut, kHidden}, st);
-    k_colsum<<<1, 32, 0, st>>>(n->dout, B, kOut, gr + n->off_fc2b);
+    k_colsum_add<<<dim3(1, (B + 31) / 32), 256, 0, st>>>(n->dout, B, kOut, gr + n->off_fc2b);
     sgemm(n->dout, kOut, 1, p + n->off_fc2w, 1, kHidden, B, kHidden, kOut, EpiF{n->dz1, n->z1, B, kHidden}, st);
     {
         const int splits = std::max(1, std::min(kFc1Splits, B / 64));
@@ -1578,7 +1828,7 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
         k_part_sum<<<blocks_for((int64_t)kHidden * HD), 256, 0, st>>>(n->fc1wpart, splits, (int64_t)kHidden * HD,
                                                                        gr + n->off_fc1w);
     }
-    k_colsum<<<(kHidden + 127) / 128, 128, 0, st>>>(n->dz1, B, kHidden, gr + n->off_fc1b);
+    k_colsum_add<<<dim3((kHidden + 31) / 32, (B + 31) / 32), 256, 0, st>>>(n->dz1, B, kHidden, gr + n->off_fc1b);
     sgemm(n->dz1, kHidden, 1, p + n->off_fc1w, 1, HD, B, HD, kHidden, EpiF{n->dh, nullptr, B, HD}, st);
     k_flatten_grad<<<blocks_for((int64_t)B * F), 256, 0, st>>>(n->dh, B, F, HD, n->act[kLayers],
                                                                n->gpre[kLayers]);
@@ -1586,7 +1836,8 @@ gsvr_status gsvr_cnn_loss_backward(gsvr_cnn *n, const float *x, const float *aux
     if (e) return cuda_status(n, e, "head backward");
     for (int l = kLayers - 1; l >= 0; --l) {
         const ConvShape sh = conv_shape(B, layer_size(l), layer_size(l), kCh[l], kCh[l + 1]);
-        e = conv_wgrad(n->gpre[l + 1], n->act[l], sh, n->grads + n->off_w[l], n->grads + n->off_b[l], n->w1part, st);
+        e = conv_wgrad(n->gpre[l + 1], n->act[l], sh, n->grads + n->off_w[l], n->grads + n->off_b[l], n->w1part,
+                       n->status, st);
         if (e) return cuda_status(n, e, "conv wgrad");
         if (l > 0) {
             e = conv_dgrad(n->gpre[l + 1], sh, n->wbf + n->off_w[l], n->wt, n->act[l], n->gpre[l], nullptr,
@@ -1674,7 +1925,8 @@ gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t
                                 int32_t Ci, int32_t Co, float *dw, float *db) {
     g_cnn_error.clear();
     if (!gy || !x || !dw || B < 1 || H < 1 || W < 1 || Ci < 1 || (Ci % 8 && Ci != 1) || Co < 8 || (Co % 8) ||
-        (Ci == 1 && (Co != 32 || !db)) || !aligned16(gy) || !aligned16(x) || (int64_t)B * H * W > (1LL << 30))
+        (Ci == 1 && (Co != 32 || !db)) || !aligned16(gy) || !aligned16(x) || !aligned16(dw) ||
+        (int64_t)B * H * W > (1LL << 30))
         return nfail(nullptr, GSVR_ERR_INVALID_ARG, "bad conv wgrad arguments (Co a multiple of 8)");
     const ConvShape s = conv_shape(B, H, W, Ci, Co);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1684,7 +1936,7 @@ gsvr_status gsvr_cnn_conv_wgrad(void *stream, const uint16_t *gy, const uint16_t
         if (e) return cuda_status(nullptr, e, "scratch");
     }
     cudaError_t e = conv_wgrad(reinterpret_cast<const bf16 *>(gy), reinterpret_cast<const bf16 *>(x), s, dw, db,
-                               scratch, st);
+                               scratch, tc_status_word(), st);
     if (scratch) cudaFreeAsync(scratch, st);
     return cuda_status(nullptr, e, "conv wgrad");
 }
