@@ -170,6 +170,40 @@ struct EpiConv {  // y = bf16(relu?(acc + bias)), y32 = the float value
             reinterpret_cast<float4 *>(y32 + e)[1] = make_float4(o[4], o[5], o[6], o[7]);
         }
     }
+    // columns c0 .. c0 + 31 (c0 % 32 == 0): the bias is read before any store
+    __device__ void vec32(int r, int c0, const float *v) const {
+        if (r >= rows) return;
+        if (c0 + 32 > cols || (cols & 7) || !bias) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) vec8(r, c0 + j, v + j);
+            return;
+        }
+        float o[32];
+        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 b = __ldg(b4 + j);
+            o[4 * j] = v[4 * j] + b.x;
+            o[4 * j + 1] = v[4 * j + 1] + b.y;
+            o[4 * j + 2] = v[4 * j + 2] + b.z;
+            o[4 * j + 3] = v[4 * j + 3] + b.w;
+        }
+        if (relu) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) o[j] = fmaxf(o[j], 0.f);
+        }
+        const size_t e = (size_t)r * cols + c0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            reinterpret_cast<uint4 *>(y + e)[g] =
+                make_uint4(pack_bf16x2(o[8 * g], o[8 * g + 1]), pack_bf16x2(o[8 * g + 2], o[8 * g + 3]),
+                           pack_bf16x2(o[8 * g + 4], o[8 * g + 5]), pack_bf16x2(o[8 * g + 6], o[8 * g + 7]));
+        if (y32) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                reinterpret_cast<float4 *>(y32 + e)[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+        }
+    }
 };
 struct EpiWgrad {  // dw[r][c] += acc for c < K; db[r] += acc for c == K
     float *dw, *db;
@@ -308,6 +342,12 @@ __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
            ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
 }
 
+// K-major, 64-byte swizzle: 8-row x 64-byte atoms 512 bytes apart, swizzle mode 4
+__device__ __forceinline__ uint64_t tc_smem_desc64(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(512u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
+}
+
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -421,13 +461,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(LA la, LB lb, EP ep, int
                       "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float f[32];
 #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-                    float f[8];
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) f[t] = __uint_as_float(v[j + t]);
-                    ep.vec8(row, n0 + c0 + j, f);
-                }
+                for (int t = 0; t < 32; ++t) f[t] = __uint_as_float(v[t]);
+                ep.vec32(row, n0 + c0, f);
             }
         }
     } else if (lane == 0) {
@@ -499,7 +536,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-template <class EP, int BN>
+// Operand A outside the tensor (padding past the last tap): a batch index no
+// tensor reaches, so the whole box reads 0.
+constexpr int kTmaNowhere = 1 << 20;
+
+template <class EP, int BN, int SW>
 __global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, TmaA ta, EP ep,
                                                           int Kred, unsigned *status) {
@@ -546,20 +587,26 @@ __global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant_
             if (kt >= S && !gsvr::mbar_wait_bounded(&empty[s], ((kt / S) - 1) & 1u, kTcWaitNs)) s_fail = 1;
             if (s_fail) break;
             const uint32_t sa = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), sb = sa + Cfg::A_BYTES;
-            const int k = kt * TC_K;
             gsvr::mbar_arrive_expect_tx(&full[s], (uint32_t)Cfg::STAGE_BYTES);
-            if (ta.kind == TMA_ROWS) {
-                tma_load_2d(sa, &mapA, k, m0, &full[s]);
-            } else {
-                const int t = k >> ta.lC, c0 = k & ((1 << ta.lC) - 1);
-                if (ta.kind == TMA_CONV) {
-                    const int kh = (t * 11) >> 5, kw = t - 3 * kh;  // t / 3 for t < 9
-                    tma_load_4d(sa, &mapA, c0, kw - 1, 2 * oh0 + kh - 1, b0, &full[s]);
+            // SW = 128: one box of 64 K per operand; SW = 64: two boxes of 32 K
+            // (each a 64-byte-swizzled block of its own: A 8 KB, B BN x 64 B)
+#pragma unroll
+            for (int h = 0; h < 128 / SW; ++h) {
+                const int k = kt * TC_K + h * (SW / 2);
+                const uint32_t da = sa + (uint32_t)(h * TC_M * SW), db = sb + (uint32_t)(h * BN * SW);
+                if (ta.kind == TMA_ROWS) {
+                    tma_load_2d(da, &mapA, k, m0, &full[s]);
                 } else {
-                    tma_load_4d(sa, &mapA, c0, t & 1, oh0 + (t >> 1), b0, &full[s]);
+                    const int t = k >> ta.lC, c0 = k & ((1 << ta.lC) - 1);
+                    if (ta.kind == TMA_CONV) {
+                        const int kh = (t * 11) >> 5, kw = t - 3 * kh;  // t / 3 for t < 9
+                        tma_load_4d(da, &mapA, c0, kw - 1, 2 * oh0 + kh - 1, t < 9 ? b0 : kTmaNowhere, &full[s]);
+                    } else {
+                        tma_load_4d(da, &mapA, c0, t & 1, oh0 + (t >> 1), t < 4 ? b0 : kTmaNowhere, &full[s]);
+                    }
                 }
+                tma_load_2d(db, &mapB, k, n0, &full[s]);
             }
-            tma_load_2d(sb, &mapB, k, n0, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
@@ -571,10 +618,19 @@ __global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant_
             }
             tc_fence_after();
             const uint32_t a0 = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), b0 = a0 + Cfg::A_BYTES;
+            if (SW == 128) {
 #pragma unroll
-            for (int kk = 0; kk < TC_K / 16; ++kk)
-                tc_mma(tmem, tc_smem_desc(a0 + kk * 32), tc_smem_desc(b0 + kk * 32), Cfg::IDESC,
-                       (kt > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < TC_K / 16; ++kk)
+                    tc_mma(tmem, tc_smem_desc(a0 + kk * 32), tc_smem_desc(b0 + kk * 32), Cfg::IDESC,
+                           (kt > 0 || kk > 0) ? 1u : 0u);
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < TC_K / 16; ++kk) {
+                    const uint32_t h = kk >> 1, o = (kk & 1) * 32;
+                    tc_mma(tmem, tc_smem_desc64(a0 + h * TC_M * 64 + o), tc_smem_desc64(b0 + h * BN * 64 + o),
+                           Cfg::IDESC, (kt > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
             tc_commit(&empty[s]);
         }
         tc_commit(&done);  // arrives once every MMA issued above has completed
@@ -602,13 +658,10 @@ __global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant_
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float f[32];
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                float f[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) f[t] = __uint_as_float(v[j + t]);
-                ep.vec8(row, n0 + c0 + j, f);
-            }
+            for (int t = 0; t < 32; ++t) f[t] = __uint_as_float(v[t]);
+            ep.vec32(row, n0 + c0, f);
         }
     }
     tc_fence_before();
@@ -637,20 +690,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // bfloat16 tensor map with the 128-byte swizzle; dims / strides innermost
 // first (strides in bytes, rank - 1 of them), zero fill outside the tensor.
 bool encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
-                const uint32_t *box, const uint32_t *estride) {
+                const uint32_t *box, const uint32_t *estride, int sw = 128) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void *>(base),
                reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides),
                reinterpret_cast<const cuuint32_t *>(box), reinterpret_cast<const cuuint32_t *>(estride),
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-// [rows][K] row-major bfloat16 (K % 8 == 0, 16-byte aligned), box {64, box_rows}
-bool map_rows(CUtensorMap *m, const bf16 *p, int rows, int K, int box_rows) {
+// [rows][K] row-major bfloat16 (K % 8 == 0, 16-byte aligned), box {sw / 2, box_rows}
+bool map_rows(CUtensorMap *m, const bf16 *p, int rows, int K, int box_rows, int sw = 128) {
     const uint64_t dims[2] = {(uint64_t)K, (uint64_t)rows}, strides[1] = {(uint64_t)K * 2};
-    const uint32_t box[2] = {(uint32_t)TC_K, (uint32_t)box_rows}, es[2] = {1, 1};
-    return encode_map(m, p, 2, dims, strides, box, es);
+    const uint32_t box[2] = {(uint32_t)(sw / 2), (uint32_t)box_rows}, es[2] = {1, 1};
+    return encode_map(m, p, 2, dims, strides, box, es, sw);
 }
 int ilog2_exact(int v) {  // log2 of a power of two, else -1
     if (v <= 0 || (v & (v - 1))) return -1;
@@ -673,22 +727,25 @@ bool tile_rows(const ConvShape &s, int &bh, int &bb, int rows = TC_M) {
     return true;
 }
 
+template <class EP, int BN, int SW>
+cudaError_t launch_tma_n(const CUtensorMap &mA, const CUtensorMap &mB, TmaA ta, EP ep, int rows, int cols, int Kred,
+                         unsigned *status, cudaStream_t st) {
+    const dim3 grid((rows + TC_M - 1) / TC_M, (cols + BN - 1) / BN);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tma<EP, BN, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+    if (e) return e;
+    k_gemm_tma<EP, BN, SW><<<grid, TMA_THREADS, TcCfg<BN>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
+    return cudaGetLastError();
+}
+// sw: the swizzle span of both maps (128: boxes of 64 K, 64: boxes of 32 K)
 template <class EP>
 cudaError_t launch_tma(const CUtensorMap &mA, const CUtensorMap &mB, TmaA ta, EP ep, int rows, int cols, int Kred,
-                       unsigned *status, cudaStream_t st) {
-    const bool narrow = cols <= 64;
-    const dim3 grid((rows + TC_M - 1) / TC_M, (cols + (narrow ? 64 : 128) - 1) / (narrow ? 64 : 128));
-    cudaError_t e;
-    if (narrow) {
-        e = cudaFuncSetAttribute(k_gemm_tma<EP, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<64>::SMEM);
-        if (e) return e;
-        k_gemm_tma<EP, 64><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
-    } else {
-        e = cudaFuncSetAttribute(k_gemm_tma<EP, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128>::SMEM);
-        if (e) return e;
-        k_gemm_tma<EP, 128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mA, mB, ta, ep, Kred, status);
-    }
-    return cudaGetLastError();
+                       unsigned *status, cudaStream_t st, int sw = 128) {
+    if (cols <= 64)
+        return sw == 64 ? launch_tma_n<EP, 64, 64>(mA, mB, ta, ep, rows, cols, Kred, status, st)
+                        : launch_tma_n<EP, 64, 128>(mA, mB, ta, ep, rows, cols, Kred, status, st);
+    return sw == 64 ? launch_tma_n<EP, 128, 64>(mA, mB, ta, ep, rows, cols, Kred, status, st)
+                    : launch_tma_n<EP, 128, 128>(mA, mB, ta, ep, rows, cols, Kred, status, st);
 }
 
 // ------------------------------------ tcgen05 weight gradient (MN-major)
@@ -709,7 +766,15 @@ __device__ __forceinline__ uint64_t tc_smem_desc_mn(uint32_t saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(8192u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
            ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
 }
-template <int BN>
+// MN-major, 64-byte swizzle: 32-element atoms 4 KB apart (leading), 8-position
+// groups 512 B apart (stride)
+__device__ __forceinline__ uint64_t tc_smem_desc_mn64(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(4096u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
+}
+// XSW: swizzle span of the input's boxes (128: 64 channels of a tap per box,
+// 64: 32 channels, for Ci = 32)
+template <int BN, int XSW>
 __global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap mapG,
                                                            const __grid_constant__ CUtensorMap mapX, TmaA tx,
                                                            float *__restrict__ dw, int Co, int K9, int nk_total,
@@ -759,10 +824,11 @@ __global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant
             tma_load_2d(sa, &mapG, co0, m, &full[s]);
             tma_load_2d(sa + 8192u, &mapG, co0 + 64, m, &full[s]);
 #pragma unroll
-            for (int a = 0; a < BN / 64; ++a) {
-                const int n = n0 + 64 * a, t = n >> tx.lC, c0 = n & ((1 << tx.lC) - 1);
+            for (int a = 0; a < BN / (XSW / 2); ++a) {
+                const int n = n0 + (XSW / 2) * a, t = n >> tx.lC, c0 = n & ((1 << tx.lC) - 1);
                 const int kh = (t * 11) >> 5, kw = t - 3 * kh;
-                tma_load_4d(sb + 8192u * a, &mapX, c0, kw - 1, 2 * oh0 + kh - 1, b0, &full[s]);
+                tma_load_4d(sb + (uint32_t)(a * (XSW / 2) * WG_K * 2), &mapX, c0, kw - 1, 2 * oh0 + kh - 1,
+                            t < 9 ? b0 : kTmaNowhere, &full[s]);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -775,8 +841,9 @@ __global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant
             tc_fence_after();
             const uint32_t a0 = sbase + (uint32_t)(s * Cfg::STAGE_BYTES), b0 = a0 + Cfg::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < WG_K / 16; ++kk)  // 16 positions = two 8-position groups = 2048 B
-                tc_mma(tmem, tc_smem_desc_mn(a0 + kk * 2048), tc_smem_desc_mn(b0 + kk * 2048), IDESC,
+            for (int kk = 0; kk < WG_K / 16; ++kk)  // 16 positions = two 8-position groups
+                tc_mma(tmem, tc_smem_desc_mn(a0 + kk * 2048),
+                       XSW == 128 ? tc_smem_desc_mn(b0 + kk * 2048) : tc_smem_desc_mn64(b0 + kk * 1024), IDESC,
                        (i > 0 || kk > 0) ? 1u : 0u);
             tc_commit(&empty[s]);
         }
@@ -791,7 +858,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant
     if (!bad) {
         const int co = co0 + warp * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < BN && n0 + c0 < K9; c0 += 32) {  // K9 % 32 == 0
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
@@ -826,24 +893,32 @@ __global__ void __launch_bounds__(TMA_THREADS) k_wgrad_tma(const __grid_constant
 // 16-byte load) over the rows m = x, x + gridDim.x * 8, ... of its 8 warps
 // (warp w from row x * 8 + w); the warps' sums meet in shared memory, one
 // atomic per (block, channel).
-__global__ void __launch_bounds__(256) k_colsum_bf16_add(const bf16 *__restrict__ g, int M, int C,
+// lpr lanes per row (a power of two: C / 8 when that is one below 32, else
+// 32 with the lanes past the channels idle), 32 / lpr rows per warp step.
+__global__ void __launch_bounds__(256) k_colsum_bf16_add(const bf16 *__restrict__ g, int M, int C, int lpr,
                                                          float *__restrict__ db) {
     __shared__ float red[8][256];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c0 = blockIdx.y * 256 + lane * 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, rpw = 32 / lpr;
+    const int cg = lane % lpr, sub = lane / lpr, c0 = blockIdx.y * 256 + cg * 8;
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (c0 < C) {
-        for (int m = blockIdx.x * 8 + warp; m < M; m += gridDim.x * 8) {
+        for (int m = (blockIdx.x * 8 + warp) * rpw + sub; m < M; m += gridDim.x * 8 * rpw) {
             const uint4 u = *reinterpret_cast<const uint4 *>(g + (size_t)m * C + c0);
             const bf16 *h = reinterpret_cast<const bf16 *>(&u);
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] += __bfloat162float(h[e]);
         }
     }
+    for (int off = lpr; off < 32; off <<= 1)
 #pragma unroll
-    for (int e = 0; e < 8; ++e) red[warp][lane * 8 + e] = v[e];
+        for (int e = 0; e < 8; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], off);
+    if (lane < lpr) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) red[warp][lane * 8 + e] = v[e];
+    }
     __syncthreads();
     const int c = blockIdx.y * 256 + threadIdx.x;
-    if (c < C) {
+    if (threadIdx.x < lpr * 8 && c < C) {
         float t = 0.f;
 #pragma unroll
         for (int w8 = 0; w8 < 8; ++w8) t += red[w8][threadIdx.x];
@@ -898,6 +973,10 @@ struct EpiDense {
         float4 *d = reinterpret_cast<float4 *>(c + (size_t)m * N + n0);
         d[0] = make_float4(v[0], v[1], v[2], v[3]);
         d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    __device__ void vec32(int m, int n0, const float *v) const {
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) vec8(m, n0 + j, v + j);
     }
 };
 
@@ -1078,27 +1157,37 @@ struct EpiDx2x2 {  // dx[b][2i + ph][2j + pw][ci] = acc (times mask > 0), inside
         dx[e] = __float2bfloat16(v);
         if (dx32) dx32[e] = v;
     }
-    // columns n0 .. n0 + 7 (n0 % 8 == 0, Ci % 8 == 0: one sub-pixel q, channels ci .. ci + 7)
-    __device__ void vec8(int m, int n0, const float *v) const {
-        if (m >= rows || n0 >= 4 * s.Ci) return;
-        int q, ci, b, i, j;
-        chan_split(n0, s.Ci, s.lCi, q, ci);
+    // columns n0 .. n0 + 31 as four 8-column groups: every mask load is
+    // issued before any store
+    __device__ void vec32(int m, int n0, const float *v) const {
+        if (m >= rows) return;
+        int b, i, j;
         pos_split(s, m, b, i, j);
-        const int ih = 2 * i + (q >> 1), iw = 2 * j + (q & 1);
-        if (ih >= s.H || iw >= s.W) return;
-        const size_t e = (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci;
-        float o[8];
-        uint4 mk = mask ? *reinterpret_cast<const uint4 *>(mask + e) : make_uint4(0, 0, 0, 0);
-        const bf16 *mb = reinterpret_cast<const bf16 *>(&mk);
+        size_t e[4];
+        bool ok[4];
+        uint4 mk[4];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) o[t] = (mask && !(__bfloat162float(mb[t]) > 0.f)) ? 0.f : v[t];
-        uint32_t pk[4];
+        for (int g = 0; g < 4; ++g) {
+            int q, ci;
+            chan_split(n0 + 8 * g, s.Ci, s.lCi, q, ci);
+            const int ih = 2 * i + (q >> 1), iw = 2 * j + (q & 1);
+            ok[g] = n0 + 8 * g < 4 * s.Ci && ih < s.H && iw < s.W;
+            e[g] = ok[g] ? (((size_t)b * s.H + ih) * s.W + iw) * s.Ci + ci : 0;
+            mk[g] = (ok[g] && mask) ? __ldg(reinterpret_cast<const uint4 *>(mask + e[g])) : make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) pk[t] = pack_bf16x2(o[2 * t], o[2 * t + 1]);
-        *reinterpret_cast<uint4 *>(dx + e) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        if (dx32) {
-            reinterpret_cast<float4 *>(dx32 + e)[0] = make_float4(o[0], o[1], o[2], o[3]);
-            reinterpret_cast<float4 *>(dx32 + e)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        for (int g = 0; g < 4; ++g) {
+            if (!ok[g]) continue;
+            const bf16 *mb = reinterpret_cast<const bf16 *>(&mk[g]);
+            float o[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) o[t] = (mask && !(__bfloat162float(mb[t]) > 0.f)) ? 0.f : v[8 * g + t];
+            *reinterpret_cast<uint4 *>(dx + e[g]) = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]),
+                                                               pack_bf16x2(o[4], o[5]), pack_bf16x2(o[6], o[7]));
+            if (dx32) {
+                reinterpret_cast<float4 *>(dx32 + e[g])[0] = make_float4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<float4 *>(dx32 + e[g])[1] = make_float4(o[4], o[5], o[6], o[7]);
+            }
         }
     }
 };
@@ -1409,15 +1498,17 @@ cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const
     if (s.Co >= kTcMinCols) {
         const EpiConv ep{y, y32, bias, M, s.Co, relu};
         int bh, bb;
-        if (s.Ci % 64 == 0 && tile_rows(s, bh, bb)) {
+        const int sw = s.Ci % 64 == 0 ? 128 : s.Ci == 32 ? 64 : 0;  // box of sw / 2 channels
+        if (sw && tile_rows(s, bh, bb)) {
             CUtensorMap mA, mB;
             const uint64_t dims[4] = {(uint64_t)s.Ci, (uint64_t)s.W, (uint64_t)s.H, (uint64_t)s.B};
             const uint64_t strides[3] = {(uint64_t)s.Ci * 2, (uint64_t)s.W * s.Ci * 2, (uint64_t)s.H * s.W * s.Ci * 2};
-            const uint32_t box[4] = {(uint32_t)TC_K, (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb};
+            const uint32_t box[4] = {(uint32_t)(sw / 2), (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb};
             const uint32_t es[4] = {1, 2, 2, 1};
-            if (encode_map(&mA, x, 4, dims, strides, box, es) && map_rows(&mB, w, s.Co, K, s.Co <= 64 ? 64 : 128))
+            if (encode_map(&mA, x, 4, dims, strides, box, es, sw) &&
+                map_rows(&mB, w, s.Co, K, s.Co <= 64 ? 64 : 128, sw))
                 return launch_tma(mA, mB, TmaA{TMA_CONV, ilog2_exact(s.Ci), ilog2_exact(s.OH * s.OW), ilog2_exact(s.OW)},
-                                  ep, M, s.Co, K, status, st);
+                                  ep, M, s.Co, K, status, st, sw);
         }
         return gemm_tc(LoadIm2col{x, s, M, K}, LoadRows{w, s.Co, K}, ep, M, s.Co, K, w, status, st);
     }
@@ -1534,38 +1625,49 @@ cudaError_t conv_wgrad(const bf16 *gy, const bf16 *x, const ConvShape &s, float 
         return cudaGetLastError();
     }
     int bh, bb;
-    if (s.Ci % 64 == 0 && tile_rows(s, bh, bb, WG_K)) {
+    const int xsw = s.Ci % 64 == 0 ? 128 : s.Ci == 32 ? 64 : 0;  // input boxes of xsw / 2 channels
+    if (xsw && tile_rows(s, bh, bb, WG_K)) {
         // tensor-memory path: bias gradient by a column sum, dW by k_wgrad_tma
         CUtensorMap mG, mX;
         const uint64_t gd[2] = {(uint64_t)s.Co, (uint64_t)M}, gs[1] = {(uint64_t)s.Co * 2};
         const uint32_t gb[2] = {64, (uint32_t)WG_K}, ge[2] = {1, 1};
         const uint64_t xd[4] = {(uint64_t)s.Ci, (uint64_t)s.W, (uint64_t)s.H, (uint64_t)s.B};
         const uint64_t xs[3] = {(uint64_t)s.Ci * 2, (uint64_t)s.W * s.Ci * 2, (uint64_t)s.H * s.W * s.Ci * 2};
-        const uint32_t xb[4] = {64, (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb}, xe[4] = {1, 2, 2, 1};
-        if (encode_map(&mG, gy, 2, gd, gs, gb, ge) && encode_map(&mX, x, 4, xd, xs, xb, xe)) {
+        const uint32_t xb[4] = {(uint32_t)(xsw / 2), (uint32_t)(2 * s.OW), (uint32_t)(2 * bh), (uint32_t)bb};
+        const uint32_t xe[4] = {1, 2, 2, 1};
+        if (encode_map(&mG, gy, 2, gd, gs, gb, ge) && encode_map(&mX, x, 4, xd, xs, xb, xe, xsw)) {
             if (db) {
-                const int cb = (s.Co + 255) / 256, bx = std::max(1, std::min((M + 63) / 64, 592 / cb));
-                k_colsum_bf16_add<<<dim3(bx, cb), 256, 0, st>>>(gy, M, s.Co, db);
+                const int cb = (s.Co + 255) / 256;
+                const int lpr = (s.Co < 256 && ilog2_exact(s.Co / 8) >= 0) ? s.Co / 8 : 32;
+                const int rows_per_block = 8 * (32 / lpr) * 4;  // ~4 rows per lane
+                const int bx = std::max(1, std::min((M + rows_per_block - 1) / rows_per_block, 4096));
+                k_colsum_bf16_add<<<dim3(bx, cb), 256, 0, st>>>(gy, M, s.Co, lpr, db);
             }
-            const int bn = (K % 128 == 0) ? 128 : 64;
-            const int nk = (M + WG_K - 1) / WG_K, tiles = ((s.Co + TC_M - 1) / TC_M) * (K / bn);
+            const int bn = (K % 128 == 0) ? 128 : 64, ntile = (K + bn - 1) / bn;
+            const int nk = (M + WG_K - 1) / WG_K, tiles = ((s.Co + TC_M - 1) / TC_M) * ntile;
             const int splits = std::max(1, std::min(nk, (148 * 2 + tiles - 1) / tiles));
             const int steps = (nk + splits - 1) / splits;
-            const dim3 grid((s.Co + TC_M - 1) / TC_M, K / bn, (nk + steps - 1) / steps);
+            const dim3 grid((s.Co + TC_M - 1) / TC_M, ntile, (nk + steps - 1) / steps);
             const TmaA tx{TMA_CONV, ilog2_exact(s.Ci), ilog2_exact(s.OH * s.OW), ilog2_exact(s.OW)};
             cudaError_t e;
-            if (bn == 128) {
-                e = cudaFuncSetAttribute(k_wgrad_tma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (bn == 128) {  // K % 128 == 0 implies Ci % 64 == 0 here (K = 9 Ci)
+                e = cudaFuncSetAttribute(k_wgrad_tma<128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TcCfg<128>::SMEM);
                 if (e) return e;
-                k_wgrad_tma<128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk, steps,
-                                                                              status);
-            } else {
-                e = cudaFuncSetAttribute(k_wgrad_tma<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                k_wgrad_tma<128, 128><<<grid, TMA_THREADS, TcCfg<128>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk,
+                                                                                   steps, status);
+            } else if (xsw == 128) {
+                e = cudaFuncSetAttribute(k_wgrad_tma<64, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TcCfg<64>::SMEM);
                 if (e) return e;
-                k_wgrad_tma<64><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk, steps,
-                                                                            status);
+                k_wgrad_tma<64, 128><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk,
+                                                                                 steps, status);
+            } else {
+                e = cudaFuncSetAttribute(k_wgrad_tma<64, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<64>::SMEM);
+                if (e) return e;
+                k_wgrad_tma<64, 64><<<grid, TMA_THREADS, TcCfg<64>::SMEM, st>>>(mG, mX, tx, dw, s.Co, K, nk,
+                                                                                steps, status);
             }
             return cudaGetLastError();
         }
