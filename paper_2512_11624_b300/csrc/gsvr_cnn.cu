@@ -1198,13 +1198,11 @@ __global__ void k_to_bf16(const float *__restrict__ a, int64_t n, bf16 *__restri
         b[e] = __float2bfloat16(a[e]);
 }
 
-// First layer (one input channel, 32 outputs): four threads per output
-// position, thread q of a position computing channels 8 q .. 8 q + 7 (weights
-// read from shared memory as float4, a channel pair at a time) and storing
-// them as one 16-byte vector;
-// a warp covers 8 consecutive positions, 512 contiguous output bytes.  Each
-// iteration gathers the patches of two positions before computing, so that
-// twice the loads are in flight.
+// First layer (one input channel, 32 outputs).  Forward: a thread per output
+// position gathers its 3 x 3 patch once and computes all 32 channels, the
+// weights read from shared memory as float4 that every lane of the warp
+// shares (broadcast); the 64 output bytes of a position are four 16-byte
+// stores.  The weight gradient (below) uses four threads per position.
 __device__ __forceinline__ void conv1_patch(const bf16 *__restrict__ x, const ConvShape &s, int m, float xv[9]) {
     int b, oh, ow;
     pos_split(s, m, b, oh, ow);
@@ -1231,52 +1229,41 @@ __device__ __forceinline__ float4 lds_f4(const float4 *p) {
 __global__ void __launch_bounds__(256) k_conv1_fwd(const bf16 *__restrict__ x, ConvShape s,
                                                    const bf16 *__restrict__ w, const float *__restrict__ bias,
                                                    bf16 *__restrict__ y) {
-    // wp4[(q * 4 + p) * 5 + i]: channels c = 8 q + 2 p and c + 1, their 9 taps
-    // each (floats 0-8, 9-17), 2 zero pads: one channel pair is 5 float4 reads
-    __shared__ float4 wp4[16 * 5];
+    __shared__ float4 ws4[32 * 9 / 4];  // [co][tap] row-major: channel pair (2c, 2c + 1) = floats 18 c .. 18 c + 17
     __shared__ float bs[32];
-    float *wf = reinterpret_cast<float *>(wp4);
-    for (int e = threadIdx.x; e < 16 * 20; e += blockDim.x) {
-        const int pair = e / 20, i = e - 20 * pair, c = 2 * pair + (i >= 9 ? 1 : 0), k = i >= 9 ? i - 9 : i;
-        wf[e] = i < 18 ? __bfloat162float(w[c * 9 + k]) : 0.f;
-    }
+    float *ws = reinterpret_cast<float *>(ws4);
+    for (int e = threadIdx.x; e < 32 * 9; e += blockDim.x) ws[e] = __bfloat162float(w[e]);
     for (int e = threadIdx.x; e < 32; e += blockDim.x) bs[e] = bias[e];
     __syncthreads();
-    const int q = threadIdx.x & 3;
-    const int64_t n = (int64_t)s.B * s.OH * s.OW * 4, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += 2 * stride) {
-        const int m0 = (int)(e >> 2);
-        const bool two = e + stride < n;
-        const int m1 = two ? (int)((e + stride) >> 2) : m0;
-        float xa[9], xb[9];
-        conv1_patch(x, s, m0, xa);
-        conv1_patch(x, s, m1, xb);
-        uint32_t pa[4], pb[4];
+    const int64_t M = (int64_t)s.B * s.OH * s.OW;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        float xv[9];
+        conv1_patch(x, s, (int)m, xv);
+        uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)m * 32);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            float wv[20];
+        for (int g = 0; g < 4; ++g) {  // channels 8 g .. 8 g + 7: floats 72 g .. 72 g + 71 = 18 float4
+            float wv[72];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const float4 t = lds_f4(&wp4[(q * 4 + p) * 5 + i]);
+            for (int i = 0; i < 18; ++i) {
+                const float4 t = lds_f4(&ws4[18 * g + i]);
                 wv[4 * i] = t.x;
                 wv[4 * i + 1] = t.y;
                 wv[4 * i + 2] = t.z;
                 wv[4 * i + 3] = t.w;
             }
-            const float b0 = bs[8 * q + 2 * p], b1 = bs[8 * q + 2 * p + 1];
-            float a0 = b0, a1 = b1, c0 = b0, c1 = b1;
+            uint32_t pk[4];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                a0 = fmaf(wv[k], xa[k], a0);
-                a1 = fmaf(wv[9 + k], xa[k], a1);
-                c0 = fmaf(wv[k], xb[k], c0);
-                c1 = fmaf(wv[9 + k], xb[k], c1);
+            for (int c = 0; c < 8; c += 2) {
+                float v0 = bs[8 * g + c], v1 = bs[8 * g + c + 1];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    v0 = fmaf(wv[c * 9 + k], xv[k], v0);
+                    v1 = fmaf(wv[(c + 1) * 9 + k], xv[k], v1);
+                }
+                pk[c / 2] = pack_bf16x2(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
             }
-            pa[p] = pack_bf16x2(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
-            pb[p] = pack_bf16x2(fmaxf(c0, 0.f), fmaxf(c1, 0.f));
+            dst[g] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        *reinterpret_cast<uint4 *>(y + (size_t)m0 * 32 + 8 * q) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
-        if (two) *reinterpret_cast<uint4 *>(y + (size_t)m1 * 32 + 8 * q) = make_uint4(pb[0], pb[1], pb[2], pb[3]);
     }
 }
 
@@ -1492,7 +1479,7 @@ cudaError_t conv_forward(const bf16 *x, const ConvShape &s, const bf16 *w, const
                          float *y32, unsigned *status, cudaStream_t st) {
     const int M = s.B * s.OH * s.OW, K = 9 * s.Ci;
     if (s.Ci == 1 && s.Co == 32 && relu && !y32) {
-        k_conv1_fwd<<<blocks_for((int64_t)M * 4, 256 * 4), 256, 0, st>>>(x, s, w, bias, y);
+        k_conv1_fwd<<<blocks_for(M, 256 * 2), 256, 0, st>>>(x, s, w, bias, y);
         return cudaGetLastError();
     }
     if (s.Co >= kTcMinCols) {
@@ -1543,6 +1530,27 @@ cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *
                 4 * s.Ci, 4 * s.Co, 4 * s.Co, st);
 }
 
+// The 3 x 3 patch of position m for the four lanes of a quad (lane q holds
+// taps q, q + 4 and, for q = 0, 8): each lane gathers at most three taps and
+// the quad exchanges them by shuffles.  Called by whole warps.
+__device__ __forceinline__ void conv1_patch_quad(const bf16 *__restrict__ x, const ConvShape &s, int m, int lane,
+                                                 float xv[9]) {
+    const int q = lane & 3;
+    int b, oh, ow;
+    pos_split(s, m, b, oh, ow);
+    float mine[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int t = q + 4 * u, kh = (t * 11) >> 5, kw = t - 3 * kh;
+        const int ih = 2 * oh - 1 + kh, iw = 2 * ow - 1 + kw;
+        mine[u] = (t < 9 && ih >= 0 && ih < s.H && iw >= 0 && iw < s.W)
+                      ? __bfloat162float(x[((size_t)b * s.H + ih) * s.W + iw])
+                      : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) xv[t] = __shfl_sync(0xffffffffu, mine[t >> 2], (lane & ~3) | (t & 3));
+}
+
 // Per block: partial first-layer weight gradients over a grid-strided set of
 // positions.  Four threads per position: thread q accumulates the 8 x 10
 // products (channels 8 q .. 8 q + 7) x (9 taps and the bias's 1) of the
@@ -1550,7 +1558,7 @@ cudaError_t conv_dgrad(const bf16 *gy, const ConvShape &s, const bf16 *w, bf16 *
 // in flight together); the block then sums the lanes that share
 // q (shuffles) and the warps (shared memory) into part[block][320], ordered
 // (co, tap) with the bias last.  k_conv1_wgrad_sum adds the blocks.
-__global__ void __launch_bounds__(256) k_conv1_wgrad_part(const bf16 *__restrict__ g, const bf16 *__restrict__ x,
+__global__ void __launch_bounds__(256, 2) k_conv1_wgrad_part(const bf16 *__restrict__ g, const bf16 *__restrict__ x,
                                                           ConvShape s, float *__restrict__ part) {
     __shared__ float red[8][320];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, q = lane & 3;
@@ -1560,17 +1568,18 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad_part(const bf16 *__restrict
 #pragma unroll
         for (int t = 0; t < 10; ++t) acc[c][t] = 0.f;
     const int64_t n = (int64_t)s.B * s.OH * s.OW * 4, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < n; e += 2 * stride) {
-        // two positions per iteration (their loads in flight together); the
-        // second is skipped past the end by a zero gradient
-        const int m0 = (int)(e >> 2);
-        const bool two = e + stride < n;
-        const int m1 = two ? (int)((e + stride) >> 2) : m0;
-        const uint4 u0 = *reinterpret_cast<const uint4 *>(g + (size_t)m0 * 32 + 8 * q);
-        const uint4 u1 = two ? *reinterpret_cast<const uint4 *>(g + (size_t)m1 * 32 + 8 * q) : make_uint4(0, 0, 0, 0);
+    // warp-uniform trip count (the patch exchange is a whole-warp shuffle):
+    // lanes past the end take position 0 with a zero gradient
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < n; base += 2 * stride) {
+        // two positions per iteration (their loads in flight together)
+        const int64_t e0 = base + lane, e1 = e0 + stride;
+        const bool v0 = e0 < n, v1 = e1 < n;
+        const int m0 = v0 ? (int)(e0 >> 2) : 0, m1 = v1 ? (int)(e1 >> 2) : 0;
+        const uint4 u0 = v0 ? *reinterpret_cast<const uint4 *>(g + (size_t)m0 * 32 + 8 * q) : make_uint4(0, 0, 0, 0);
+        const uint4 u1 = v1 ? *reinterpret_cast<const uint4 *>(g + (size_t)m1 * 32 + 8 * q) : make_uint4(0, 0, 0, 0);
         float xa[9], xb[9];
-        conv1_patch(x, s, m0, xa);
-        conv1_patch(x, s, m1, xb);
+        conv1_patch_quad(x, s, m0, lane, xa);
+        conv1_patch_quad(x, s, m1, lane, xb);
         const bf16 *h0 = reinterpret_cast<const bf16 *>(&u0), *h1 = reinterpret_cast<const bf16 *>(&u1);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
