@@ -1206,20 +1206,21 @@ __device__ __forceinline__ void gauss_epilogue(const GradArgs &a, int j, const f
     g[10 * N + j] = v[9];
 }
 
-// Thread per record.  Each block takes a contiguous run of Gaussians (so of at
-// most a few subjects) and walks it in rounds of consecutive Gaussians with at
-// most 256 records together: one record per thread, its partial Gaussian
-// gradient staged in shared memory, then one thread per Gaussian sums its
-// records' rows in record order (deterministic) and runs the epilogue.  A
-// Gaussian with more than 256 records takes a round alone (threads stride over
-// its records, then a fixed-order tree sum).  Slice-frame gradients go to a
+// Warp-centric.  Each block takes a contiguous run of Gaussians (so of at
+// most a few subjects) and splits its records evenly over its 8 warps, each
+// warp's range starting at a Gaussian's first record (records are stored
+// Gaussian-major), so every Gaussian belongs to one warp.  A warp walks its
+// range 32 records at a time, a record per lane; the lanes' 11 partial
+// Gaussian gradients are summed per Gaussian by a segmented inclusive scan
+// over the lanes (shuffles, fixed order: deterministic), a Gaussian that
+// continues past the batch carries its partial sum into the next, and the
+// lane holding a Gaussian's last record runs the epilogue.  Gaussians without
+// records keep the zero the launcher wrote.  Slice-frame gradients go to a
 // shared window over the run's subjects' slices, flushed once with float64
 // atomics; a block whose window does not fit uses float64 global atomics.
-__global__ void __launch_bounds__(256, 4) k_gauss_grad(GradArgs a) {
+__global__ void __launch_bounds__(256, 3) k_gauss_grad(GradArgs a) {
     extern __shared__ float pacc_s[];  // window x 12
-    __shared__ float rows[256][12];
-    __shared__ int s_jb;
-    const int N = a.N, tid = threadIdx.x;
+    const int N = a.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (N + gridDim.x - 1) / gridDim.x;
     const int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
     if (j0 >= j1) return;
@@ -1232,64 +1233,58 @@ __global__ void __launch_bounds__(256, 4) k_gauss_grad(GradArgs a) {
     if (pacc) {
         for (int e = tid; e < (w1 - w0) * 12; e += blockDim.x) pacc[e] = 0.f;
     }
+    __syncthreads();
     auto ro = [&](int j) { return min(a.rec_off[j], a.cap_rec); };
-    auto chain = [&](int r, int j, float v[11]) {
-        const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
-        const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
-        const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
-        record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0);
+    const int R0 = ro(j0), R1 = ro(j1);
+    // first record >= x that starts its Gaussian (R1 if none): whole warp
+    auto first_head = [&](int x) {
+        for (int base = x; base < R1; base += 32) {
+            const int r = base + lane;
+            const unsigned hb = __ballot_sync(0xffffffffu, r < R1 && r == ro(a.cand[r].x));
+            if (hb) return base + __ffs(hb) - 1;
+        }
+        return R1;
     };
-    for (int ja = j0; ja < j1;) {
-        __syncthreads();  // rows and s_jb of the previous round are free
-        if (tid == 0) {
-            const int base = ro(ja);
-            int lo = ja + 1, hi = j1;  // largest jb with records [ro(ja), ro(jb)) <= 256
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (ro(mid) - base <= 256) lo = mid;
-                else hi = mid - 1;
-            }
-            s_jb = lo;
+    const int L = (R1 - R0 + 7) / 8;
+    const int rs = warp == 0 ? R0 : first_head(min(R1, R0 + warp * L));
+    const int re = warp == 7 ? R1 : first_head(min(R1, R0 + (warp + 1) * L));
+    float carry[11];
+    int carry_j = -1;
+    for (int base = rs; base < re; base += 32) {
+        const int r = base + lane;
+        const bool valid = r < re;
+        const int j = valid ? a.cand[r].x : -2 - lane;  // invalid lanes: segments of their own
+        float v[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
+            const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
+            const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
+            record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0);
         }
-        __syncthreads();
-        const int jb = s_jb;
-        const int rb = ro(ja), re = ro(jb);
-        if (re - rb <= 256) {
-            float v[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const int r = rb + tid;
-            if (r < re) chain(r, a.cand[r].x, v);
+        // segmented inclusive scan: lanes of one Gaussian are contiguous
 #pragma unroll
-            for (int e = 0; e < 11; ++e) rows[tid][e] = v[e];
-            __syncthreads();
-            const int j = ja + tid;
-            if (j < jb) {
-                float sum[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                const int e1 = ro(j + 1) - rb;
-                for (int rr = ro(j) - rb; rr < e1; ++rr)
+        for (int off = 1; off < 32; off <<= 1) {
+            const int ju = __shfl_up_sync(0xffffffffu, j, off);
+            const bool same = lane >= off && ju == j;
 #pragma unroll
-                    for (int e = 0; e < 11; ++e) sum[e] += rows[rr][e];
-                gauss_epilogue(a, j, sum);
-            }
-        } else {
-            float v[11] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int r = rb + tid; r < re; r += blockDim.x) chain(r, ja, v);
-#pragma unroll
-            for (int e = 0; e < 11; ++e) rows[tid][e] = v[e];
-            for (int o = 128; o > 0; o >>= 1) {
-                __syncthreads();
-                if (tid < o)
-#pragma unroll
-                    for (int e = 0; e < 11; ++e) rows[tid][e] += rows[tid + o][e];
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float sum[11];
-#pragma unroll
-                for (int e = 0; e < 11; ++e) sum[e] = rows[0][e];
-                gauss_epilogue(a, ja, sum);
+            for (int e = 0; e < 11; ++e) {
+                const float vu = __shfl_up_sync(0xffffffffu, v[e], off);
+                if (same) v[e] += vu;
             }
         }
-        ja = jb;
+        if (j == carry_j) {
+#pragma unroll
+            for (int e = 0; e < 11; ++e) v[e] += carry[e];
+        }
+        const int jn = __shfl_down_sync(0xffffffffu, j, 1);
+        const bool seg_end = valid && (lane == 31 || jn != j);
+        if (seg_end && r + 1 == ro(j + 1)) gauss_epilogue(a, j, v);
+        // the Gaussian of lane 31 continues into the next batch unless it ended here
+        const int jl = __shfl_sync(0xffffffffu, j, 31);
+        const bool cont = __shfl_sync(0xffffffffu, valid && r + 1 < ro(j + 1), 31);
+#pragma unroll
+        for (int e = 0; e < 11; ++e) carry[e] = __shfl_sync(0xffffffffu, v[e], 31);
+        carry_j = cont ? jl : -1;
     }
     if (pacc) {
         __syncthreads();
@@ -1557,7 +1552,7 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
         if (n_sm <= 0) n_sm = 148;
     }
     GradArgs g = a;
-    const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 4);  // one wave at 4 CTAs / SM
+    const int blocks = std::min(cdiv((int64_t)a.N * 16, 256), n_sm * 3);  // one wave at 3 CTAs / SM
     // the widest slice window of any block (the kernel's chunking, on the host)
     int widest = a.M;
     if (a.gauss_subject && a.h_gauss_first && a.h_slice_first && a.n_subj > 1) {
@@ -1575,6 +1570,8 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
     g.smem_slices = std::min(widest, a.smem_slices);
     const size_t smem = (size_t)g.smem_slices * 12 * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_gauss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Gaussians without records get no epilogue: their gradient is this zero
+    cudaMemsetAsync(g.grad, 0, sizeof(float) * 11 * (size_t)a.N, st);
     k_gauss_grad<<<blocks, 256, smem, st>>>(g);
     counted();
 }
