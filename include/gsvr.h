@@ -267,6 +267,36 @@ typedef struct gsvr_tiling {
  * captured graph is dropped.  Synchronises.  GSVR_ERR_INVALID_ARG for a shape
  * outside the limits above (the context is then unchanged). */
 gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
+
+/* Normalised top-K forward model (Sec. 2.2, Eq. 2; Eq. 5 with sigma_i = 1;
+ * Sec. 2.5 "Sparse Computation (Top-K)").  With K >= 1 every later forward
+ * predicts a sampled pixel as
+ *     I_hat = sum_{j in S} c_j E_j / (sum_{j in S} E_j + delta),
+ *     E_j = exp(-1/2 v^T Sigma_obs,ij^-1 v), v = T_i(u) - mu_j,
+ *     Sigma_obs,ij = Sigma_j + R_i Sigma_PSF R_i^T (Eq. 4, no normalisation factor),
+ * S = the K Gaussians whose means are nearest the pixel's world position in
+ * Euclidean distance (ties to the smaller index), found exactly by a shell
+ * search of a uniform grid over the means (about 16 means per cell, at most
+ * 2^16 cells).  The grid is rebuilt every `refresh_every` forwards (1 = every
+ * forward: exact neighbours; larger values search the cells of an older build
+ * with the current means, as the paper refreshes its index periodically).
+ * The loss stays the MSE; gsvr_backward gives the exact gradient for the
+ * neighbour sets of the last forward (the selection is piecewise constant).
+ * K = 0 restores the plain sum of gsvr_forward.  One subject only
+ * (GSVR_ERR_STATE otherwise, at gsvr_forward).
+ * Arguments: 0 <= K <= 64; delta > 0 and finite; refresh_every >= 1; else
+ * GSVR_ERR_INVALID_ARG.  Synchronises the stream; sizes the buffers when
+ * Gaussians are set (GSVR_ERR_NOMEM on failure). */
+gsvr_status gsvr_set_topk(gsvr_ctx *ctx, int32_t K, float delta, int32_t refresh_every);
+
+/* Neighbour sets of the last top-K forward (synchronises): *n_out = number of
+ * sampled pixels; with host buffers pix [cap], nbr [cap][K], cnt [cap] (all
+ * non-NULL, cap >= *n_out) also the sampled global pixels in evaluation order,
+ * their neighbours (Gaussian indices, in no particular order) and neighbour
+ * counts (K, or N when N < K).  Passing all three NULL only queries *n_out.
+ * GSVR_ERR_STATE without a current top-K forward. */
+gsvr_status gsvr_get_topk_neighbors(gsvr_ctx *ctx, int32_t *pix, int32_t *nbr, int32_t *cnt, int64_t cap,
+                                    int64_t *n_out);
 gsvr_status gsvr_get_tiling(gsvr_ctx *ctx, gsvr_tiling *out);
 
 /* The built-in candidate shapes: writes min(cap, total) of them to out and the

@@ -147,9 +147,15 @@ def _drod_dr(r):
     return out
 
 
-def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None):
+def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, want_abs=False):
     """(pred, loss, grad, nbr) in float64; grad has the parameter-vector layout
-    (11 N Gaussian entries component-major, then (r, tau) per slice)."""
+    (11 N Gaussian entries component-major, then (r, tau) per slice).  With
+    want_abs, also A (same layout): the sum of the absolute values of the
+    products a float32 evaluation adds up for the entry, per (pixel,
+    neighbour) pair: the pair's contribution for the means, amplitudes and
+    poses; for the log-scales and the quaternion, every product of the chain
+    through Sigma_j = R(q / |q|) diag(exp(2 ls)) R^T (whose terms cancel for
+    near-isotropic Gaussians, where the exact entry is near 0)."""
     th = np.asarray(theta, np.float64)
     N = int(N)
     c = th[10 * N:11 * N]
@@ -214,4 +220,59 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None):
             grad[11 * N + 6 * i + kk] = np.sum(GRod * D)
         grad[11 * N + 6 * i + 3:11 * N + 6 * i + 6] = Gti[i]
         i += 1
-    return pred, loss, grad, nbr
+    if not want_abs:
+        return pred, loss, grad, nbr
+    # per-pair contributions, each pushed through the same (linear) chains
+    A = np.zeros_like(grad)
+    absmu = np.zeros((N, 3))
+    np.add.at(absmu, nbr, np.abs(g_mu))
+    for k in range(3):
+        A[k * N:(k + 1) * N] = absmu[:, k]
+    absc = np.zeros(N)
+    np.add.at(absc, nbr, np.abs(dc_pair))
+    A[10 * N:11 * N] = absc
+    qn_all = np.linalg.norm(q, axis=1)
+    qh_all = q / qn_all[:, None]
+    Rq_all = np.array([_o.quat_to_rot(qh_all[j]) for j in range(N)])
+    s2_all = np.exp(2.0 * ls)
+    Dq_all = np.array([_drot_dquat(qh_all[j]) for j in range(N)])       # (N,4,3,3)
+    Rq_p, s2_p = Rq_all[nbr], s2_all[nbr]
+    aR, aG = np.abs(Rq_p), np.abs(G)
+    # ls_k: terms 2 s_k^2 Rq[a,k] G[a,b] Rq[b,k]
+    dls_abs = 2.0 * s2_p * np.einsum("pkai,pkab,pkbi->pki", aR, aG, aR)
+    absls = np.zeros((N, 3))
+    np.add.at(absls, nbr, dls_abs)
+    for k in range(3):
+        A[(3 + k) * N:(4 + k) * N] = absls[:, k]
+    # q: dL/dRq[a,b] = 2 sum_c G[a,c] Rq[c,b] s_b^2, then products with dR/dq_e, then the projection
+    T = 2.0 * np.einsum("pkac,pkcb,pkb->pkab", aG, aR, s2_p)
+    aD = np.abs(Dq_all[nbr])                                            # (P,K,4,3,3)
+    te = np.einsum("pkab,pkeab->pke", T, aD)
+    qh_p = np.abs(qh_all[nbr])
+    absq_pair = (te + qh_p * np.einsum("pke,pke->pk", qh_p, te)[:, :, None]) / qn_all[nbr][:, :, None]
+    absq = np.zeros((N, 4))
+    np.add.at(absq, nbr, absq_pair)
+    for k in range(4):
+        A[(6 + k) * N:(7 + k) * N] = absq[:, k]
+    gx_pair = -(gam[:, :, None] * Pv)                                   # (P,K,3)
+    GR_pair = np.einsum("pka,pb->pkab", gx_pair, u) + 2.0 * np.einsum("pkab,pbc,pc->pkac", G, Rs, var[sl])
+    R0s, c0s, dRods = [], [], []
+    i = 0
+    for (s_, k_, _) in _slices(stacks):
+        R0 = np.asarray(s_["R"], np.float64)
+        R0s.append(R0)
+        c0s.append(np.asarray(s_["origin"], np.float64) + (k_ - 0.5 * (int(s_["n_slices"]) - 1)) *
+                   float(s_["thickness"]) * R0[:, 2])
+        dRods.append(np.array(_drod_dr(pose[i, :3])))
+        i += 1
+    R0s, c0s, dRods = np.array(R0s), np.array(c0s), np.array(dRods)
+    GRod_pair = np.einsum("pkab,pcb->pkac", GR_pair, R0s[sl]) + np.einsum("pka,pb->pkab", gx_pair, c0s[sl])
+    dr_pair = np.einsum("pkab,peab->pke", GRod_pair, dRods[sl])
+    absr = np.zeros((M, 3))
+    abst = np.zeros((M, 3))
+    np.add.at(absr, sl, np.abs(dr_pair).sum(1))
+    np.add.at(abst, sl, np.abs(gx_pair).sum(1))
+    for i in range(M):
+        A[11 * N + 6 * i:11 * N + 6 * i + 3] = absr[i]
+        A[11 * N + 6 * i + 3:11 * N + 6 * i + 6] = abst[i]
+    return pred, loss, grad, nbr, A

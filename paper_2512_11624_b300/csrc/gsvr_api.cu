@@ -97,6 +97,16 @@ struct gsvr_ctx {
     DBuf<uint32_t> d_item_key, d_item_key_sorted, d_item_order, d_item_key_alt, d_item_val_alt;
     DBuf<int> d_item_hist;
     DBuf<float> d_part;
+    // normalised top-K form (gsvr_set_topk); K = 0: the plain sum
+    int topk_K = 0, topk_refresh = 1;
+    float topk_delta = 1e-8f, topk_per_cell = 16.f;
+    int64_t topk_calls = 0, topk_n_dev = -1;  // topk_n_dev: the N held in d_topk_n
+    DBuf<TopkGrid> d_topk_grid;
+    DBuf<uint32_t> d_topk_keys, d_topk_keys_sorted, d_topk_gidx, d_topk_kalt, d_topk_valt;
+    DBuf<int> d_topk_hist, d_topk_cstart, d_topk_cend, d_topk_nbr, d_topk_ncnt, d_topk_n;
+    DBuf<float2> d_topk_pstat;
+    DBuf<double> d_topk_loss_part;
+    DBuf<float> d_topk_gacc;
     int cap_rec = 0, cap_keys = 0, cap_items = 0, grid_items = 0;
     int last_n_rec = 0, last_n_keys = 0;
 
@@ -189,6 +199,7 @@ bool finite_all(const float *v, int n) {
 size_t scan_scratch_blocks(gsvr_ctx *ctx) {
     size_t n = std::max<size_t>({(size_t)ctx->N + 1, (size_t)ctx->P + 1, (size_t)ctx->cap_rec + 1,
                                  (size_t)256 * (size_t)sort_blocks(ctx->cap_keys) + 1,
+                                 (size_t)256 * (size_t)sort_blocks((int)ctx->N) + 1,
                                  (size_t)256 * (size_t)sort_blocks(ctx->cap_items) + 1});
     return (n + kScanTile - 1) / kScanTile + 2;
 }
@@ -957,6 +968,112 @@ gsvr_status gsvr_get_subject_losses(gsvr_ctx *ctx, double *out, int32_t n) {
     return GSVR_OK;
 }
 
+// ---------------------------------------------- normalised top-K form (F1)
+int topk_cap_px(gsvr_ctx *ctx) { return std::max(ctx->n_mask, 1); }
+
+gsvr_status topk_ensure(gsvr_ctx *ctx) {
+    const size_t N = (size_t)std::max<int64_t>(ctx->N, 1), cap = (size_t)topk_cap_px(ctx);
+    const size_t nb = (cap + kTopkThreads - 1) / kTopkThreads;
+    const bool need = ctx->d_topk_keys.n < N || ctx->d_topk_gacc.n < 10 * N ||
+                      ctx->d_topk_nbr.n < cap * (size_t)ctx->topk_K || ctx->d_topk_loss_part.n < nb ||
+                      ctx->d_topk_hist.n < (size_t)256 * sort_blocks((int)N) + 1 ||
+                      ctx->d_scan_bsum.n < scan_scratch_blocks(ctx) + 1 || ctx->topk_n_dev != ctx->N;
+    if (!need) return GSVR_OK;
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "top-K buffers must be sized before graph capture");
+    CK(ctx->d_topk_grid.ensure(1));
+    CK(ctx->d_topk_keys.ensure(N));
+    CK(ctx->d_topk_keys_sorted.ensure(N));
+    CK(ctx->d_topk_gidx.ensure(N));
+    CK(ctx->d_topk_kalt.ensure(N));
+    CK(ctx->d_topk_valt.ensure(N));
+    CK(ctx->d_topk_hist.ensure((size_t)256 * sort_blocks((int)N) + 1));
+    CK(ctx->d_topk_cstart.ensure(kTopkMaxCells));
+    CK(ctx->d_topk_cend.ensure(kTopkMaxCells));
+    CK(ctx->d_topk_nbr.ensure(cap * (size_t)ctx->topk_K));
+    CK(ctx->d_topk_ncnt.ensure(cap));
+    CK(ctx->d_topk_pstat.ensure(cap));
+    CK(ctx->d_topk_loss_part.ensure(nb));
+    CK(ctx->d_topk_gacc.ensure(10 * N));
+    CK(ctx->d_topk_n.ensure(1));
+    CK(ensure_scan_scratch(ctx));
+    const int n = (int)ctx->N;
+    CK(cudaMemcpyAsync(ctx->d_topk_n.p, &n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->topk_n_dev = ctx->N;
+    ctx->topk_calls = 0;  // a new Gaussian count: the next forward rebuilds the grid
+    return GSVR_OK;
+}
+
+TopkArgs topk_args(gsvr_ctx *ctx) {
+    TopkArgs a{};
+    a.theta = ctx->d_theta.p;
+    a.gpre = ctx->d_gpre.p;
+    a.slices = ctx->d_slices.p;
+    a.N = (int)ctx->N;
+    a.M = ctx->M;
+    a.sampled = ctx->d_sampled.p;
+    a.n_sampled = &ctx->d_counters.p->n_sampled;
+    a.I_obs = ctx->d_I.p;
+    a.pred = ctx->d_pred.p;
+    a.rbar = ctx->d_rbar.p;
+    a.pstat = ctx->d_topk_pstat.p;
+    a.nbr = ctx->d_topk_nbr.p;
+    a.ncnt = ctx->d_topk_ncnt.p;
+    a.loss_part = ctx->d_topk_loss_part.p;
+    a.grid = ctx->d_topk_grid.p;
+    a.cell_start = ctx->d_topk_cstart.p;
+    a.cell_end = ctx->d_topk_cend.p;
+    a.gidx = ctx->d_topk_gidx.p;
+    a.gacc = ctx->d_topk_gacc.p;
+    a.pose_acc = ctx->d_pose_acc.p;
+    a.K = ctx->topk_K;
+    a.delta = ctx->topk_delta;
+    a.cap_px = topk_cap_px(ctx);
+    a.status = ctx->d_status.p;
+    return a;
+}
+
+gsvr_status topk_forward(gsvr_ctx *ctx) {
+    if (ctx->n_subj > 1) return fail(ctx, GSVR_ERR_STATE, "the top-K form takes one subject");
+    if (gsvr_status s = topk_ensure(ctx)) return s;
+    cudaStream_t st = ctx->stream;
+    const int N = (int)ctx->N;
+    stage_begin(ctx, GSVR_STAGE_BIN);
+    if (ctx->topk_calls % ctx->topk_refresh == 0) {
+        launch_topk_grid(ctx->d_theta.p, N, ctx->topk_per_cell, ctx->d_topk_grid.p, ctx->d_topk_keys.p, st);
+        SortScratch ss{ctx->d_topk_kalt.p, ctx->d_topk_valt.p, ctx->d_topk_hist.p, scan_scratch(ctx)};
+        CK(radix_sort_pairs(ctx->d_topk_keys.p, nullptr, ctx->d_topk_keys_sorted.p, ctx->d_topk_gidx.p,
+                            ctx->d_topk_n.p, N, 16, ss, st));
+        CK(cudaMemsetAsync(ctx->d_topk_cstart.p, 0, sizeof(int) * kTopkMaxCells, st));
+        CK(cudaMemsetAsync(ctx->d_topk_cend.p, 0, sizeof(int) * kTopkMaxCells, st));
+        launch_topk_cell_ranges(ctx->d_topk_keys_sorted.p, N, ctx->d_topk_cstart.p, ctx->d_topk_cend.p, st);
+    }
+    stage_end(ctx, GSVR_STAGE_BIN);
+    stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
+    launch_topk_forward(topk_args(ctx), topk_cap_px(ctx), ctx->d_loss.p, st);
+    stage_end(ctx, GSVR_STAGE_FWD_EVAL);
+    CK(cudaGetLastError());
+    ++ctx->topk_calls;
+    ctx->fwd_valid = true;
+    return GSVR_OK;
+}
+
+gsvr_status topk_backward(gsvr_ctx *ctx) {
+    cudaStream_t st = ctx->stream;
+    const int N = (int)ctx->N, M = ctx->M;
+    stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
+    CK(cudaMemsetAsync(ctx->d_topk_gacc.p, 0, sizeof(float) * 10 * (size_t)N, st));
+    CK(cudaMemsetAsync(ctx->d_pose_acc.p, 0, sizeof(double) * 12 * M, st));
+    launch_topk_backward(topk_args(ctx), topk_cap_px(ctx), st);
+    stage_end(ctx, GSVR_STAGE_BWD_EVAL);
+    stage_begin(ctx, GSVR_STAGE_GRAD);
+    launch_topk_epilogue(ctx->d_theta.p, ctx->d_topk_gacc.p, N, ctx->d_grad.p, st);
+    launch_pose_grad(ctx->d_pose_acc.p, ctx->d_static.p, ctx->d_theta.p + 11LL * N, ctx->d_grad.p + 11LL * N, M, st);
+    stage_end(ctx, GSVR_STAGE_GRAD);
+    CK(cudaGetLastError());
+    return GSVR_OK;
+}
+
 gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (!ctx->have_gauss || !ctx->have_obs || !ctx->have_sample)
@@ -971,6 +1088,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     launch_gauss_prep(ctx->d_theta.p, N, ctx->d_gpre.p, ctx->d_status.p, st);
     launch_pose_prep(ctx->d_theta.p + 11LL * N, ctx->d_static.p, ctx->d_slices.p, M, ctx->d_status.p, st);
     stage_end(ctx, GSVR_STAGE_PREP);
+    if (ctx->topk_K > 0) return topk_forward(ctx);
     stage_begin(ctx, GSVR_STAGE_BIN);
 
     BinArgs b{};
@@ -1095,6 +1213,7 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     DeviceGuard g(ctx->device);
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->N, M = ctx->M;
+    if (ctx->topk_K > 0) return topk_backward(ctx);
     EvalArgs e = eval_args(ctx, ctx->grid_items);
     stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
     launch_backward(e, st);
@@ -1180,6 +1299,9 @@ gsvr_status gsvr_graph_capture(gsvr_ctx *ctx, int64_t n_per_subject, const gsvr_
     {
         gsvr_status si = ensure_item_capacity(ctx);
         if (si) return si;
+    }
+    if (ctx->topk_K > 0) {
+        if (gsvr_status sk = topk_ensure(ctx)) return sk;
     }
     int64_t n_out = -1;
     if (n_per_subject >= 0) {
@@ -1412,6 +1534,41 @@ gsvr_status gsvr_get_tiling(gsvr_ctx *ctx, gsvr_tiling *out) {
     out->bwd_blocks_per_sm = ctx->bwd_bps;
     out->queue_order = ctx->queue_order;
     out->ms = 0.f;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_get_topk_neighbors(gsvr_ctx *ctx, int32_t *pix, int32_t *nbr, int32_t *cnt, int64_t cap,
+                                    int64_t *n_out) {
+    if (check_ctx(ctx) || !n_out) return GSVR_ERR_INVALID_ARG;
+    if (ctx->topk_K <= 0 || !ctx->fwd_valid) return fail(ctx, GSVR_ERR_STATE, "needs a top-K forward");
+    DeviceGuard g(ctx->device);
+    int ns = 0;
+    CK(cudaMemcpyAsync(&ns, &ctx->d_counters.p->n_sampled, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ns = std::min(ns, topk_cap_px(ctx));
+    *n_out = ns;
+    if (!pix && !nbr && !cnt) return GSVR_OK;
+    if (cap < ns || !pix || !nbr || !cnt) return fail(ctx, GSVR_ERR_INVALID_ARG, "need pix, nbr, cnt with cap >= n");
+    CK(cudaMemcpy(pix, ctx->d_sampled.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nbr, ctx->d_topk_nbr.p, sizeof(int) * (size_t)ns * ctx->topk_K, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt, ctx->d_topk_ncnt.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_topk(gsvr_ctx *ctx, int32_t K, float delta, int32_t refresh_every) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (K < 0 || K > kTopkMaxK || !(delta > 0.f) || !std::isfinite(delta) || refresh_every < 1)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "top-K needs 0 <= K <= 64, delta > 0 finite, refresh_every >= 1");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_topk during graph capture");
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    ctx->topk_K = K;
+    ctx->topk_delta = delta;
+    ctx->topk_refresh = refresh_every;
+    ctx->topk_calls = 0;
+    ctx->fwd_valid = false;
+    if (K > 0 && ctx->have_gauss) return topk_ensure(ctx);
     return GSVR_OK;
 }
 

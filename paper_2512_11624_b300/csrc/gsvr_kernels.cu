@@ -1389,6 +1389,450 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
 
 __global__ void k_advance_step(unsigned long long *d_step) { *d_step += 1ull; }
 
+// ============================================ normalised top-K forward model
+// Eq. 2 with every covariance replaced by its observed covariance (Eq. 4) and
+// the ratio of Eq. 5 (sigma_i = 1): I_hat = sum_S c_j E_j / (sum_S E_j + delta),
+// E_j = exp(-1/2 v^T Sigma_obs^-1 v), S = the K means nearest the pixel's world
+// position (Sec. 2.5, Top-K), ties to the smaller index.  The neighbours come
+// from an exact shell search of a uniform grid over the means.
+
+// order-preserving float <-> int for atomic min / max
+__device__ __forceinline__ int f2o(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float o2f(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7FFFFFFF); }
+
+__global__ void k_topk_box_init(TopkGrid *g) {
+    for (int a = 0; a < 3; ++a) {
+        g->box[a] = 0x7FFFFFFF;
+        g->box[3 + a] = (int)0x80000000;
+    }
+}
+__global__ void __launch_bounds__(256) k_topk_box(const float *__restrict__ th, int N, TopkGrid *g) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int o = j < N ? f2o(th[(size_t)a * N + j]) : 0;
+        lo[a] = j < N ? o : 0x7FFFFFFF;
+        hi[a] = j < N ? o : (int)0x80000000;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&g->box[a], lo[a]);
+            atomicMax(&g->box[3 + a], hi[a]);
+        }
+}
+// cell size h = (box volume x per_cell / N)^(1/3), grown by 10 % steps until the
+// cell count fits kTopkMaxCells; cell index = floor((x - org) / h) per axis
+__global__ void k_topk_grid_params(TopkGrid *g, int N, float per_cell) {
+    float lo[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = o2f(g->box[a]);
+        ext[a] = fmaxf(o2f(g->box[3 + a]) - lo[a], 1e-3f);
+    }
+    float h = cbrtf(ext[0] * ext[1] * ext[2] * per_cell / (float)max(N, 1));
+    int n[3];
+    for (int it = 0; it < 200; ++it) {
+        long long tot = 1;
+        for (int a = 0; a < 3; ++a) {
+            n[a] = (int)floorf(ext[a] / h) + 1;
+            tot *= n[a];
+        }
+        if (tot <= kTopkMaxCells) break;
+        h *= 1.1f;
+    }
+    for (int a = 0; a < 3; ++a) {
+        g->org[a] = lo[a];
+        g->n[a] = n[a];
+    }
+    g->h = h;
+    g->inv_h = 1.0f / h;
+    g->n_cells = n[0] * n[1] * n[2];
+}
+__device__ __forceinline__ int topk_cell_axis(const TopkGrid &g, int a, float x) {
+    const float f = floorf((x - g.org[a]) * g.inv_h);
+    return (int)fminf(fmaxf(f, 0.f), (float)(g.n[a] - 1));
+}
+__global__ void k_topk_cell_keys(const float *__restrict__ th, int N, const TopkGrid *__restrict__ gp,
+                                 uint32_t *__restrict__ keys) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const TopkGrid g = *gp;
+    const int cx = topk_cell_axis(g, 0, th[j]), cy = topk_cell_axis(g, 1, th[(size_t)N + j]);
+    const int cz = topk_cell_axis(g, 2, th[2 * (size_t)N + j]);
+    keys[j] = (uint32_t)((cz * g.n[1] + cy) * g.n[0] + cx);
+}
+__global__ void k_topk_cell_ranges(const uint32_t *__restrict__ keys, int N, int *__restrict__ start,
+                                   int *__restrict__ end) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const uint32_t c = keys[k];
+    if (k == 0 || keys[k - 1] != c) start[c] = k;
+    if (k == N - 1 || keys[k + 1] != c) end[c] = k + 1;
+}
+
+// The sample's slice (binary search over the slices' first pixels), its world
+// position and local coordinate.
+struct TopkPixel {
+    int i;
+    double x[3];  // world position in float64: v = x - mu keeps its low bits far from the origin
+    float u[2];
+};
+__device__ __forceinline__ TopkPixel topk_pixel(const TopkArgs &a, int p) {
+    int lo = 0, hi = a.M - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.slices[mid].pix_base <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    TopkPixel q;
+    q.i = lo;
+    const SliceDev &S = a.slices[lo];
+    const int loc = p - S.pix_base, row = loc / S.W, col = loc - row * S.W;
+    q.u[0] = ((float)col - S.cx0) * S.dx;
+    q.u[1] = ((float)row - S.cy0) * S.dy;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        q.x[k] = (double)S.R[3 * k] * q.u[0] + (double)S.R[3 * k + 1] * q.u[1] + (double)S.t[k];
+    return q;
+}
+// Sigma_obs = Sigma_j + R_i Sigma_PSF R_i^T = L L^T (Cholesky, 3 x 3): the
+// quadratic form v^T Sigma_obs^-1 v = |L^-1 v|^2 by forward substitution
+// (backward stable, unlike an explicit inverse of an anisotropic Sigma_obs),
+// and Sigma_obs^-1 v = L^-T (L^-1 v) by back substitution.
+struct TopkChol {
+    float i00, l10, l20, i11, l21, i22;  // L with its diagonal stored inverted
+};
+__device__ __forceinline__ TopkChol topk_chol(const float4 g0, const float4 g1, const float sp[6]) {
+    const float a = g0.x + sp[0], d = g0.y + sp[1], f = g0.z + sp[2];
+    const float b = g0.w + sp[3], c = g1.x + sp[4], e = g1.y + sp[5];
+    TopkChol L;
+    const float l00 = sqrtf(a);
+    L.i00 = 1.0f / l00;
+    L.l10 = b * L.i00;
+    L.l20 = c * L.i00;
+    const float l11 = sqrtf(fmaxf(d - L.l10 * L.l10, 0.f));
+    L.i11 = 1.0f / l11;
+    L.l21 = (e - L.l20 * L.l10) * L.i11;
+    L.i22 = 1.0f / sqrtf(fmaxf(f - L.l20 * L.l20 - L.l21 * L.l21, 0.f));
+    return L;
+}
+__device__ __forceinline__ void topk_fsub(const TopkChol &L, float vx, float vy, float vz, float w[3]) {
+    w[0] = vx * L.i00;
+    w[1] = (vy - L.l10 * w[0]) * L.i11;
+    w[2] = (vz - L.l20 * w[0] - L.l21 * w[1]) * L.i22;
+}
+__device__ __forceinline__ void topk_bsub(const TopkChol &L, const float w[3], float z[3]) {
+    z[2] = w[2] * L.i22;
+    z[1] = (w[1] - L.l21 * z[2]) * L.i11;
+    z[0] = (w[0] - L.l10 * z[1] - L.l20 * z[2]) * L.i00;
+}
+// R diag(var) R^T of a slice (symmetric 6)
+__device__ __forceinline__ void topk_psf(const SliceDev &S, float sp[6]) {
+    auto e = [&](int p, int q) {
+        return S.R[3 * p] * S.var[0] * S.R[3 * q] + S.R[3 * p + 1] * S.var[1] * S.R[3 * q + 1] +
+               S.R[3 * p + 2] * S.var[2] * S.R[3 * q + 2];
+    };
+    sp[0] = e(0, 0);
+    sp[1] = e(1, 1);
+    sp[2] = e(2, 2);
+    sp[3] = e(0, 1);
+    sp[4] = e(0, 2);
+    sp[5] = e(1, 2);
+}
+
+// Forward: thread per sample.  The K nearest are kept in a max-heap (by
+// (d^2, j)) in shared memory, column `tid` of hd / hj.  Shells of cells at
+// Chebyshev distance 0, 1, 2, ... around the pixel's cell are scanned until
+// the heap is full and its largest distance is inside the box the scanned
+// shells cover (or the whole grid has been scanned).
+__global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
+    extern __shared__ unsigned char topk_raw[];
+    float *hd = reinterpret_cast<float *>(topk_raw);
+    int *hj = reinterpret_cast<int *>(hd + a.K * kTopkThreads);
+    __shared__ double red[kTopkThreads / 32];
+    const int tid = threadIdx.x;
+    const int ns = min(*a.n_sampled, a.cap_px);
+    const int s = blockIdx.x * kTopkThreads + tid;
+    double l = 0.0;
+    if (s < ns) {
+        const int p = a.sampled[s];
+        const TopkPixel q = topk_pixel(a, p);
+        const TopkGrid g = *a.grid;
+        const int N = a.N, K = a.K;
+        float *d = hd + tid;
+        int *jj = hj + tid;
+        auto less = [](float d1, int j1, float d2, int j2) { return d1 < d2 || (d1 == d2 && j1 < j2); };
+        int cnt = 0;
+        auto offer = [&](float d2, int j) {
+            if (cnt < K) {  // push, sift up
+                int pos = cnt++;
+                while (pos > 0) {
+                    const int par = (pos - 1) >> 1;
+                    const float dp = d[par * kTopkThreads];
+                    const int jp = jj[par * kTopkThreads];
+                    if (!less(dp, jp, d2, j)) break;
+                    d[pos * kTopkThreads] = dp;
+                    jj[pos * kTopkThreads] = jp;
+                    pos = par;
+                }
+                d[pos * kTopkThreads] = d2;
+                jj[pos * kTopkThreads] = j;
+            } else if (less(d2, j, d[0], jj[0])) {  // replace the largest, sift down
+                int pos = 0;
+                for (;;) {
+                    int ch = 2 * pos + 1;
+                    if (ch >= K) break;
+                    if (ch + 1 < K && less(d[ch * kTopkThreads], jj[ch * kTopkThreads], d[(ch + 1) * kTopkThreads],
+                                           jj[(ch + 1) * kTopkThreads]))
+                        ++ch;
+                    const float dc = d[ch * kTopkThreads];
+                    const int jc = jj[ch * kTopkThreads];
+                    if (!less(d2, j, dc, jc)) break;
+                    d[pos * kTopkThreads] = dc;
+                    jj[pos * kTopkThreads] = jc;
+                    pos = ch;
+                }
+                d[pos * kTopkThreads] = d2;
+                jj[pos * kTopkThreads] = j;
+            }
+        };
+        int c[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[k] = topk_cell_axis(g, k, (float)q.x[k]);
+        auto scan_cell = [&](int cx, int cy, int cz) {
+            const int cell = (cz * g.n[1] + cy) * g.n[0] + cx;
+            const int k1 = a.cell_end[cell];
+            for (int k = a.cell_start[cell]; k < k1; ++k) {
+                const int j = (int)a.gidx[k];
+                const float vx = (float)(q.x[0] - (double)a.theta[j]);
+                const float vy = (float)(q.x[1] - (double)a.theta[(size_t)N + j]);
+                const float vz = (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]);
+                offer(vx * vx + vy * vy + vz * vz, j);
+            }
+        };
+        for (int sh = 0; N > 0; ++sh) {  // (no grid is built without Gaussians)
+            const int z0 = max(c[2] - sh, 0), z1 = min(c[2] + sh, g.n[2] - 1);
+            const int y0 = max(c[1] - sh, 0), y1 = min(c[1] + sh, g.n[1] - 1);
+            for (int cz = z0; cz <= z1; ++cz)
+                for (int cy = y0; cy <= y1; ++cy) {
+                    if (abs(cz - c[2]) == sh || abs(cy - c[1]) == sh) {
+                        const int x0 = max(c[0] - sh, 0), x1 = min(c[0] + sh, g.n[0] - 1);
+                        for (int cx = x0; cx <= x1; ++cx) scan_cell(cx, cy, cz);
+                    } else {
+                        if (c[0] - sh >= 0) scan_cell(c[0] - sh, cy, cz);
+                        if (sh > 0 && c[0] + sh < g.n[0]) scan_cell(c[0] + sh, cy, cz);
+                    }
+                }
+            bool all = true;
+            float rho = 3.4e38f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                all = all && c[k] - sh <= 0 && c[k] + sh >= g.n[k] - 1;
+                const float lo = g.org[k] + (float)(c[k] - sh) * g.h, hi = g.org[k] + (float)(c[k] + sh + 1) * g.h;
+                rho = fminf(rho, fminf((float)q.x[k] - lo, hi - (float)q.x[k]));
+            }
+            if (all) break;
+            if (cnt == K && rho > 0.f && d[0] <= rho * rho) break;
+        }
+        // the ratio over the neighbours
+        const SliceDev &S = a.slices[q.i];
+        float sp[6];
+        topk_psf(S, sp);
+        double num = 0.0, den = 0.0;
+        for (int e = 0; e < cnt; ++e) {
+            const int j = jj[e * kTopkThreads];
+            const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
+            const TopkChol L = topk_chol(g0, g1, sp);
+            float w[3];
+            topk_fsub(L, (float)(q.x[0] - (double)a.theta[j]), (float)(q.x[1] - (double)a.theta[(size_t)N + j]),
+                      (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]), w);
+            const float E = expf(-0.5f * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+            num += (double)g1.w * (double)E;
+            den += (double)E;
+            a.nbr[(size_t)s * K + e] = j;
+        }
+        a.ncnt[s] = cnt;
+        const float D = (float)(den + (double)a.delta);
+        const float Ih = (float)(num / (den + (double)a.delta));
+        const float w = 1.0f / (float)max(ns, 1);
+        const float r = Ih - a.I_obs[p];
+        a.pred[p] = Ih;
+        a.rbar[p] = 2.f * w * r;
+        a.pstat[s] = make_float2(Ih, D);
+        l = (double)w * (double)r * (double)r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((tid & 31) == 0) red[tid >> 5] = l;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kTopkThreads / 32; ++w) t += red[w];
+        a.loss_part[blockIdx.x] = t;
+    }
+}
+__global__ void __launch_bounds__(256) k_topk_loss_total(const double *__restrict__ part, int nb, double *loss,
+                                                         unsigned *status) {
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) s += part[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        *loss = t;
+        if (!isfinite(t)) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// Backward: thread per sample.  With gbar = dL/dI_hat, D = sum E + delta and
+// gam = gbar (c_j - I_hat) / D * E_j (dL/dE_j times E_j), per neighbour:
+//   dL/dc_j += gbar E_j / D,  dL/dmu_j += gam P v,  dL/dSigma_j += 1/2 gam P v v^T P,
+//   dL/dx -= gam P v (pixel position), and Sigma_obs's R_i S R_i^T term gives
+//   dL/dR_i += 2 G R_i diag(var) with G the summed dL/dSigma_obs; x = R_i u + t_i
+//   gives dL/dR_i += dL/dx u^T, dL/dt_i += dL/dx.
+// A block's samples are consecutive in tile order, so they share most
+// neighbours: per-Gaussian sums go to a shared-memory hash table (open
+// addressing, kTopkHash slots) and per-slice sums to a small table, flushed with
+// one global atomic per (block, Gaussian, component); an insertion that finds
+// no slot adds to global memory directly.
+constexpr int kTopkHash = 1024, kTopkPoseSlots = 8;
+__global__ void __launch_bounds__(kTopkThreads) k_topk_bwd(TopkArgs a) {
+    __shared__ int hk[kTopkHash];
+    __shared__ float hv[10][kTopkHash];
+    __shared__ int pk[kTopkPoseSlots];
+    __shared__ float pv[12][kTopkPoseSlots];
+    const int tid = threadIdx.x, N = a.N, K = a.K;
+    for (int e = tid; e < kTopkHash; e += kTopkThreads) {
+        hk[e] = -1;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) hv[c][e] = 0.f;
+    }
+    if (tid < kTopkPoseSlots) {
+        pk[tid] = -1;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) pv[c][tid] = 0.f;
+    }
+    __syncthreads();
+    const int ns = min(*a.n_sampled, a.cap_px);
+    const int s = blockIdx.x * kTopkThreads + tid;
+    if (s < ns) {
+        const int p = a.sampled[s];
+        const TopkPixel q = topk_pixel(a, p);
+        const SliceDev &S = a.slices[q.i];
+        float sp[6];
+        topk_psf(S, sp);
+        const float2 st = a.pstat[s];
+        const float Ih = st.x, D = st.y, gbar = a.rbar[p];
+        float gx[3] = {0.f, 0.f, 0.f}, Go[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int cnt = a.ncnt[s];
+        for (int e = 0; e < cnt; ++e) {
+            const int j = a.nbr[(size_t)s * K + e];
+            const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
+            const TopkChol L = topk_chol(g0, g1, sp);
+            float w[3], z[3];
+            topk_fsub(L, (float)(q.x[0] - (double)a.theta[j]), (float)(q.x[1] - (double)a.theta[(size_t)N + j]),
+                      (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]), w);
+            topk_bsub(L, w, z);
+            const float px = z[0], py = z[1], pz = z[2];  // Sigma_obs^-1 v
+            const float E = expf(-0.5f * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+            const float gam = gbar * (g1.w - Ih) / D * E;
+            const float hg = 0.5f * gam;
+            float val[10] = {gam * px, gam * py, gam * pz, hg * px * px, hg * py * py, hg * pz * pz,
+                             hg * px * py, hg * px * pz, hg * py * pz, gbar * E / D};
+            gx[0] -= val[0];
+            gx[1] -= val[1];
+            gx[2] -= val[2];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Go[c] += val[3 + c];
+            // shared slot of Gaussian j
+            unsigned hh = ((unsigned)j * 2654435761u) >> (32 - 10);
+            int slot = -1;
+            for (int probe = 0; probe < 64; ++probe) {
+                const int old = atomicCAS(&hk[hh], -1, j);
+                if (old == -1 || old == j) {
+                    slot = (int)hh;
+                    break;
+                }
+                hh = (hh + 1) & (kTopkHash - 1);
+            }
+            if (slot >= 0) {
+#pragma unroll
+                for (int c = 0; c < 10; ++c) atomicAdd(&hv[c][slot], val[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 10; ++c) atomicAdd(&a.gacc[(size_t)c * N + j], val[c]);
+            }
+        }
+        // slice frame: dL/dR_i = dL/dx u^T + 2 G R diag(var), dL/dt_i = dL/dx
+        const float Gm[9] = {Go[0], Go[3], Go[4], Go[3], Go[1], Go[5], Go[4], Go[5], Go[2]};
+        float GR[12];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const float GRS = Gm[3 * r] * S.R[cc] + Gm[3 * r + 1] * S.R[3 + cc] + Gm[3 * r + 2] * S.R[6 + cc];
+                GR[3 * r + cc] = 2.f * GRS * S.var[cc] + gx[r] * (cc < 2 ? q.u[cc] : 0.f);
+            }
+        GR[9] = gx[0];
+        GR[10] = gx[1];
+        GR[11] = gx[2];
+        int slot = -1;
+        for (int probe = 0; probe < kTopkPoseSlots; ++probe) {
+            const int hh = (q.i + probe) & (kTopkPoseSlots - 1);
+            const int old = atomicCAS(&pk[hh], -1, q.i);
+            if (old == -1 || old == q.i) {
+                slot = hh;
+                break;
+            }
+        }
+        if (slot >= 0) {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) atomicAdd(&pv[c][slot], GR[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) atomicAdd(&a.pose_acc[12 * q.i + c], (double)GR[c]);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kTopkHash; e += kTopkThreads) {
+        const int j = hk[e];
+        if (j < 0) continue;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) {
+            const float v = hv[c][e];
+            if (v != 0.f) atomicAdd(&a.gacc[(size_t)c * N + j], v);
+        }
+    }
+    if (tid < kTopkPoseSlots && pk[tid] >= 0) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) atomicAdd(&a.pose_acc[12 * pk[tid] + c], (double)pv[c][tid]);
+    }
+}
+__global__ void k_topk_epilogue(GradArgs a, const float *__restrict__ gacc) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.N) return;
+    float v[11];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) v[c] = gacc[(size_t)c * a.N + j];
+    v[10] = 0.f;  // no log-determinant factor in the ratio
+    gauss_epilogue(a, j, v);
+}
+
 inline int cdiv(int64_t a, int b) { return (int)((a + b - 1) / b); }
 
 std::atomic<long long> g_launches{0};
@@ -1632,6 +2076,42 @@ void launch_tile_px_ranges(const int *sampled, const int *n_sampled, int cap, co
 }
 void launch_set_count(int *dst, int v, cudaStream_t st) {
     k_set_count<<<1, 1, 0, st>>>(dst, v);
+    counted();
+}
+
+void launch_topk_grid(const float *theta, int N, float per_cell, TopkGrid *g, uint32_t *keys, cudaStream_t st) {
+    if (N <= 0) return;
+    k_topk_box_init<<<1, 1, 0, st>>>(g);
+    k_topk_box<<<cdiv(N, 256), 256, 0, st>>>(theta, N, g);
+    k_topk_grid_params<<<1, 1, 0, st>>>(g, N, per_cell);
+    k_topk_cell_keys<<<cdiv(N, 256), 256, 0, st>>>(theta, N, g, keys);
+    counted(4);
+}
+void launch_topk_cell_ranges(const uint32_t *keys_sorted, int N, int *cell_start, int *cell_end, cudaStream_t st) {
+    if (N <= 0) return;
+    k_topk_cell_ranges<<<cdiv(N, 256), 256, 0, st>>>(keys_sorted, N, cell_start, cell_end);
+    counted();
+}
+void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream_t st) {
+    const int nb = std::max(1, cdiv(cap_px, kTopkThreads));
+    const size_t smem = (size_t)a.K * kTopkThreads * (sizeof(float) + sizeof(int));
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_topk_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_topk_fwd<<<nb, kTopkThreads, smem, st>>>(a);
+    k_topk_loss_total<<<1, 256, 0, st>>>(a.loss_part, nb, loss, a.status);
+    counted(2);
+}
+void launch_topk_backward(const TopkArgs &a, int cap_px, cudaStream_t st) {
+    const int nb = std::max(1, cdiv(cap_px, kTopkThreads));
+    k_topk_bwd<<<nb, kTopkThreads, 0, st>>>(a);
+    counted();
+}
+void launch_topk_epilogue(const float *theta, const float *gacc, int N, float *grad, cudaStream_t st) {
+    if (N <= 0) return;
+    GradArgs g{};
+    g.theta = theta;
+    g.N = N;
+    g.grad = grad;
+    k_topk_epilogue<<<cdiv(N, 256), 256, 0, st>>>(g, gacc);
     counted();
 }
 void note_launches(int n) { counted(n); }

@@ -162,4 +162,53 @@ void launch_tile_px_ranges(const int *sampled, const int *n_sampled, int cap, co
                            int *end, cudaStream_t st);
 void launch_set_count(int *dst, int v, cudaStream_t st);
 
+// ---- normalised top-K forward (Eq. 2 with Sigma_obs, Eq. 5 ratio; Sec. 2.5 Top-K)
+// Uniform grid over the Gaussian means: cell size from the means' bounding box
+// so that a cell holds about `per_cell` means, at most `max_cells` cells.
+struct TopkGrid {
+    float org[3];
+    float h, inv_h;
+    int n[3];
+    int n_cells;
+    int box[6];  // order-preserving integer images of the means' min (xyz) and max (xyz)
+};
+constexpr int kTopkMaxK = 64;
+constexpr int kTopkThreads = 128;
+constexpr int kTopkMaxCells = 1 << 16;
+struct TopkArgs {
+    const float *theta;      // 11 N + 6 M (means and amplitudes read here)
+    const float4 *gpre;      // Sigma_j and c per Gaussian (k_gauss_prep)
+    const SliceDev *slices;
+    int N, M;
+    const int *sampled;      // sampled global pixels
+    const int *n_sampled;
+    const float *I_obs;
+    float *pred, *rbar;
+    float2 *pstat;           // per sample: (I_hat, sum E + delta)
+    int *nbr;                // per sample: K Gaussian indices
+    int *ncnt;               // per sample: neighbours found (< K only when N < K)
+    double *loss_part;       // per forward block
+    const TopkGrid *grid;
+    const int *cell_start, *cell_end;
+    const uint32_t *gidx;    // Gaussian indices in cell order
+    float *gacc;             // 10 x N: d mu (3), d Sigma (xx yy zz xy xz yz), d c
+    double *pose_acc;        // M x 12
+    int K;
+    float delta;
+    int cap_px;
+    unsigned *status;
+};
+// Grid build: bounding box, cell size, cell keys; the caller sorts the keys
+// (stable radix, Gaussian index as value) and calls launch_topk_cell_ranges.
+void launch_topk_grid(const float *theta, int N, float per_cell, TopkGrid *g, uint32_t *keys, cudaStream_t st);
+void launch_topk_cell_ranges(const uint32_t *keys_sorted, int N, int *cell_start, int *cell_end, cudaStream_t st);
+// Forward: K nearest by a shell search of the grid, the ratio per sampled
+// pixel, residuals and per-block loss partials; then the loss total.
+void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream_t st);
+// Backward: per (pixel, neighbour) gradients summed per block in shared memory
+// (Gaussians by hashing, slices by a small table), then added to gacc and
+// pose_acc; the Gaussian epilogue maps gacc to the parameter gradient.
+void launch_topk_backward(const TopkArgs &a, int cap_px, cudaStream_t st);
+void launch_topk_epilogue(const float *theta, const float *gacc, int N, float *grad, cudaStream_t st);
+
 }  // namespace gsvr

@@ -31,7 +31,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
-           "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve"]
+           "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -123,6 +123,8 @@ def _load():
         "gsvr_graph_launch": ([vp, i32], C.c_int),
         "gsvr_set_step": ([vp, i64], C.c_int),
         "gsvr_set_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
+        "gsvr_set_topk": ([vp, C.c_int32, C.c_float, C.c_int32], C.c_int),
+        "gsvr_get_topk_neighbors": ([vp, vp, vp, vp, i64, C.POINTER(i64)], C.c_int),
         "gsvr_reserve": ([vp, i64, i64], C.c_int),
         "gsvr_get_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
         "gsvr_tune_space_default": ([C.POINTER(Tiling), i32, C.POINTER(i32)], C.c_int),
@@ -316,6 +318,23 @@ def gsvr_set_tiling(ctx, t):
     if isinstance(t, dict):
         t = tiling(**{k: v for k, v in t.items() if k != "ms"})
     return _check(ctx, lib.gsvr_set_tiling(ctx, C.byref(t)))
+
+
+def gsvr_set_topk(ctx, K, delta=1e-8, refresh_every=1):
+    """Normalised top-K forward (K >= 1) or the plain sum (K = 0)."""
+    return _check(ctx, lib.gsvr_set_topk(ctx, int(K), float(delta), int(refresh_every)))
+
+
+def gsvr_get_topk_neighbors(ctx, K):
+    """(pix (n,), nbr (n, K), cnt (n,)) of the last top-K forward, in evaluation order."""
+    n = C.c_int64(0)
+    _check(ctx, lib.gsvr_get_topk_neighbors(ctx, None, None, None, 0, C.byref(n)))
+    pix = np.zeros(n.value, np.int32)
+    nbr = np.zeros((n.value, int(K)), np.int32)
+    cnt = np.zeros(n.value, np.int32)
+    _check(ctx, lib.gsvr_get_topk_neighbors(ctx, pix.ctypes.data, nbr.ctypes.data, cnt.ctypes.data, n.value,
+                                            C.byref(n)))
+    return pix, nbr, cnt
 
 
 def gsvr_get_tiling(ctx):
