@@ -338,9 +338,17 @@ static void pixel_world(const or_model *m, int64_t p, int64_t *slice, double *u,
     *slice = i;
 }
 
-/* Forward: pred[p] = sum over ALL Gaussians; loss = sum_p w_pix (pred - I)^2. */
+/* Data loss of one residual r = pred - I: MSE w r^2 (loss_kind 0) or the
+ * paper's L1 w |r| (loss_kind 1, Sec. 2.5 "Loss Function"), and its derivative
+ * in r (the L1 subgradient takes sign(0) = 0). */
+static double data_loss(int loss_kind, double w, double r) { return loss_kind ? w * fabs(r) : w * r * r; }
+static double data_dloss(int loss_kind, double w, double r) {
+    return loss_kind ? w * (double)((r > 0.0) - (r < 0.0)) : 2.0 * w * r;
+}
+
+/* Forward: pred[p] = sum over ALL Gaussians; loss = sum_p of the data loss. */
 int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
-                   const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, double *pred,
+                   const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, int loss_kind, double *pred,
                    double *loss) {
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
@@ -357,10 +365,7 @@ int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *th
             s += m.g[j].c * pr.g;
         }
         pred[p] = s;
-        if (I_obs) {
-            double r = s - I_obs[p];
-            L += w_pix * r * r;
-        }
+        if (I_obs) L += data_loss(loss_kind, w_pix, s - I_obs[p]);
     }
     if (loss) *loss = L;
     model_free(&m);
@@ -500,7 +505,7 @@ static void pose_chain(const or_slice *s, const double *pose, const double *GR, 
  * gradients always include every pair of the selected Gaussians.
  */
 int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
-                            const int64_t *pix, const double *I_obs, double w_pix, int norm_mode,
+                            const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, int loss_kind,
                             const uint8_t *sel, double *pred, double *loss, double *grad, double *absgrad,
                             double cutoff, double *trunc_pred, double *trunc_grad) {
     const int want_trunc = cutoff > 0.0 && trunc_grad != NULL && absgrad != NULL;
@@ -527,8 +532,8 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
         if (pred) pred[p] = s;
         if (trunc_pred) trunc_pred[p] = tr;
         double r = s - I_obs[p];
-        L += w_pix * r * r;
-        rbar[p] = 2.0 * w_pix * r;
+        L += data_loss(loss_kind, w_pix, r);
+        rbar[p] = data_dloss(loss_kind, w_pix, r);
     }
     if (loss) *loss = L;
     memset(grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));

@@ -36,9 +36,9 @@ def lib():
         path = _build.build()
         _lib = C.CDLL(path)
         d, i64, vp = C.c_double, C.c_int64, C.c_void_p
-        _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp]
-        _lib.oracle_forward_backward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, vp, vp, vp,
-                                                 vp, vp, d, vp, vp]
+        _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, C.c_int, vp, vp]
+        _lib.oracle_forward_backward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, C.c_int, vp, vp,
+                                                 vp, vp, vp, d, vp, vp]
         _lib.oracle_adam.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, d, d, i64, vp]
         _lib.oracle_adam.restype = None
         _lib.oracle_build_slices.argtypes = [C.c_int, vp, vp, vp]
@@ -96,8 +96,19 @@ def num_threads():
     return int(lib().oracle_num_threads())
 
 
-def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0):
-    """Predictions for the listed global pixels and the MSE loss (float64)."""
+def scale_reg(theta, N, lambda_reg, s_target):
+    """The scale regulariser of the paper's loss (Sec. 2.5, "Loss Function"):
+    lambda_reg * sum_j sum_k (s_jk - s_target)^2 with s_jk = exp(ls_jk) the
+    Gaussian's scales in mm; returns (value, gradient in the 3 N log-scales)."""
+    N = int(N)
+    s = np.exp(_f64(theta)[3 * N:6 * N])
+    d = s - float(s_target)
+    return float(lambda_reg) * float(np.sum(d * d)), 2.0 * float(lambda_reg) * d * s
+
+
+def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0, loss_kind=0, lambda_reg=0.0, s_target=1.6):
+    """Predictions for the listed global pixels and the loss (float64): data
+    term MSE (loss_kind 0) or L1 (1), plus the scale regulariser."""
     st = _stacks(stacks)
     th = _f64(theta)
     pix = np.ascontiguousarray(pix, dtype=np.int64)
@@ -105,16 +116,22 @@ def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0):
     pred = np.zeros(len(pix), np.float64)
     loss = np.zeros(1, np.float64)
     rc = lib().oracle_forward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
-                              float(w_pix), int(norm_mode), _p(pred), _p(loss))
+                              float(w_pix), int(norm_mode), int(loss_kind), _p(pred), _p(loss))
     if rc != 0:
         raise RuntimeError("oracle_forward failed")
-    return pred, float(loss[0])
+    L = float(loss[0])
+    if lambda_reg:
+        L += scale_reg(th, N, lambda_reg, s_target)[0]
+    return pred, L
 
 
-def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True, cutoff=None):
+def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True, cutoff=None,
+                     loss_kind=0, lambda_reg=0.0, s_target=1.6):
     """(pred, loss, grad, absgrad) in float64; grad has the parameter-vector layout.
     With `cutoff`, returns (pred, loss, grad, absgrad, trunc_pred, trunc_grad): the
-    sums of |pair contributions| over the pairs below the cutoff, per output."""
+    sums of |pair contributions| over the pairs below the cutoff, per output.
+    loss_kind 0 / 1: MSE / L1 data term; lambda_reg > 0 adds the scale
+    regulariser (its gradient terms counted in absgrad)."""
     st = _stacks(stacks)
     th = _f64(theta)
     pix = np.ascontiguousarray(pix, dtype=np.int64)
@@ -131,10 +148,17 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None,
     if cutoff and absg is None:
         absg = np.zeros(n, np.float64)
     rc = lib().oracle_forward_backward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
-                                       float(w_pix), int(norm_mode), _p(s), _p(pred), _p(loss), _p(grad),
-                                       _p(absg), float(cutoff or 0.0), _p(tp), _p(tg))
+                                       float(w_pix), int(norm_mode), int(loss_kind), _p(s), _p(pred), _p(loss),
+                                       _p(grad), _p(absg), float(cutoff or 0.0), _p(tp), _p(tg))
     if rc != 0:
         raise RuntimeError("oracle_forward_backward failed")
+    if lambda_reg:
+        Nn = int(N)
+        Lr, gr = scale_reg(th, Nn, lambda_reg, s_target)
+        loss[0] += Lr
+        grad[3 * Nn:6 * Nn] += gr
+        if absg is not None:
+            absg[3 * Nn:6 * Nn] += np.abs(gr)
     if cutoff:
         return pred, float(loss[0]), grad, absg, tp, tg
     return pred, float(loss[0]), grad, absg

@@ -100,9 +100,11 @@ def _pairs(stacks, theta, N, pix, K, nbr):
     return x, sl, u, R, nbr, Pv, E, var
 
 
-def forward(stacks, theta, N, pix, K, delta, nbr=None, I_obs=None, w_pix=1.0):
-    """(pred, loss, nbr): predictions of the listed pixels, the MSE loss when
-    I_obs is given (else 0), and the neighbour sets used."""
+def forward(stacks, theta, N, pix, K, delta, nbr=None, I_obs=None, w_pix=1.0, loss_kind=0, lambda_reg=0.0,
+            s_target=1.6):
+    """(pred, loss, nbr): predictions of the listed pixels, the loss when I_obs
+    is given (data term MSE, loss_kind 0, or L1, 1, plus the scale regulariser
+    of oracle.scale_reg), and the neighbour sets used."""
     th = np.asarray(theta, np.float64)
     c = th[10 * int(N):11 * int(N)]
     _, _, _, _, nbr, _, E, _ = _pairs(stacks, th, N, pix, K, nbr)
@@ -111,7 +113,10 @@ def forward(stacks, theta, N, pix, K, delta, nbr=None, I_obs=None, w_pix=1.0):
     pred = num / den
     loss = 0.0
     if I_obs is not None:
-        loss = float((w_pix * (pred - np.asarray(I_obs, np.float64)) ** 2).sum())
+        r = pred - np.asarray(I_obs, np.float64)
+        loss = float((w_pix * (np.abs(r) if loss_kind else r * r)).sum())
+        if lambda_reg:
+            loss += _o.scale_reg(th, N, lambda_reg, s_target)[0]
     return pred, loss, nbr
 
 
@@ -147,7 +152,8 @@ def _drod_dr(r):
     return out
 
 
-def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, want_abs=False):
+def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, want_abs=False, loss_kind=0,
+                     lambda_reg=0.0, s_target=1.6):
     """(pred, loss, grad, nbr) in float64; grad has the parameter-vector layout
     (11 N Gaussian entries component-major, then (r, tau) per slice).  With
     want_abs, also A (same layout): the sum of the absolute values of the
@@ -165,8 +171,13 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, wa
     pred = num / den
     I = np.asarray(I_obs, np.float64)
     w = np.broadcast_to(np.asarray(w_pix, np.float64), pred.shape)
-    loss = float((w * (pred - I) ** 2).sum())
-    gbar = 2.0 * w * (pred - I)                                   # dL/dI_hat
+    r = pred - I
+    if loss_kind:                                                 # L1, subgradient sign(0) = 0
+        loss = float((w * np.abs(r)).sum())
+        gbar = w * np.sign(r)
+    else:                                                         # MSE
+        loss = float((w * r * r).sum())
+        gbar = 2.0 * w * r                                        # dL/dI_hat
     gam = gbar[:, None] * (c[nbr] - pred[:, None]) / den[:, None] * E  # dL/dE times E
     dc_pair = gbar[:, None] * E / den[:, None]
     # per pair: dL/dmu = gam P v ; dL/dSigma_obs = 1/2 gam P v v^T P ; dL/dx = -gam P v
@@ -220,6 +231,11 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, wa
             grad[11 * N + 6 * i + kk] = np.sum(GRod * D)
         grad[11 * N + 6 * i + 3:11 * N + 6 * i + 6] = Gti[i]
         i += 1
+    g_reg = None
+    if lambda_reg:
+        L_reg, g_reg = _o.scale_reg(th, N, lambda_reg, s_target)
+        loss += L_reg
+        grad[3 * N:6 * N] += g_reg
     if not want_abs:
         return pred, loss, grad, nbr
     # per-pair contributions, each pushed through the same (linear) chains
@@ -275,4 +291,6 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, wa
     for i in range(M):
         A[11 * N + 6 * i:11 * N + 6 * i + 3] = absr[i]
         A[11 * N + 6 * i + 3:11 * N + 6 * i + 6] = abst[i]
+    if g_reg is not None:
+        A[3 * N:6 * N] += np.abs(g_reg)
     return pred, loss, grad, nbr, A

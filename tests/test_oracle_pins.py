@@ -414,3 +414,33 @@ def test_truncation_sums(oracle):
     assert np.allclose(r1[4], np.abs(r1[0]), rtol=1e-12)  # positive amplitudes
     r2 = oracle.forward_backward(st, th, N, pix, I, 1.0 / len(pix), cutoff=1e-3)
     assert np.all(r2[5] <= r2[3] * (1 + 1e-12)) and np.all(r2[4] <= np.abs(r2[0]) * (1 + 1e-12))
+
+
+# ----------------------------------------------------- paper objective (L1 + scale regulariser)
+def test_l1_and_scale_regulariser_match_central_differences(oracle):
+    """The paper's loss (Sec. 2.5): sum of |I - I_hat| plus lambda_reg times
+    sum_j |s_j - s_target|^2 (scales in mm).  Value against a direct numpy
+    evaluation from the oracle's predictions; gradient against central
+    differences (residuals away from the L1 kink)."""
+    case = inputs.random_case(14, 10, [(2, 5, 6)], n_stacks=2, extent=3.0, motion_deg=10.0)
+    N, st = case["N"], case["stacks"]
+    th = case["theta"].astype(np.float64)
+    pix = np.arange(inputs.n_pixels_total(st))
+    I = case["I"].astype(np.float64)[pix] + 0.05
+    w, lam, s_t = 1.0 / len(pix), 2.5e-3, 1.6
+    pred, L = oracle.forward(st, th, N, pix, I, w, loss_kind=1, lambda_reg=lam, s_target=s_t)
+    scales = np.exp(th[3 * N:6 * N])
+    assert np.isclose(L, w * np.abs(pred - I).sum() + lam * ((scales - s_t) ** 2).sum(), rtol=1e-13)
+    assert np.abs(pred - I).min() > 1e-4
+    _, L0, g, _ = oracle.forward_backward(st, th, N, pix, I, w, loss_kind=1, lambda_reg=lam, s_target=s_t)
+    assert np.isclose(L0, L, rtol=1e-13)
+    fd = np.zeros_like(g)
+    for e in range(th.size):
+        h = 1e-6 * max(1.0, abs(th[e]))
+        tp, tm = th.copy(), th.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd[e] = (oracle.forward(st, tp, N, pix, I, w, loss_kind=1, lambda_reg=lam, s_target=s_t)[1] -
+                 oracle.forward(st, tm, N, pix, I, w, loss_kind=1, lambda_reg=lam, s_target=s_t)[1]) / (2 * h)
+    err = np.abs(g - fd)
+    assert np.all(err <= 1e-6 * np.abs(g) + 1e-9 * np.abs(g).max()), (err.max(), np.argmax(err))

@@ -125,3 +125,27 @@ def test_gradient_matches_central_differences(topk, K, delta):
                  topk.forward(st, tm, N, pix, K, delta, nbr=nbr, I_obs=I, w_pix=w)[1]) / (2 * h)
     err = np.abs(g - fd)
     assert np.all(err <= 1e-6 * np.abs(g) + 1e-9 * np.abs(g).max()), (err.max(), np.argmax(err))
+
+
+def test_l1_and_scale_regulariser_gradient(topk):
+    """The paper's loss on the top-K model (L1 data term plus the scale
+    regulariser) against central differences, neighbour sets fixed."""
+    case = inputs.random_case(15, 12, [(2, 5, 5)], n_stacks=2, extent=3.0, motion_deg=10.0)
+    N, st = case["N"], case["stacks"]
+    th = case["theta"].astype(np.float64)
+    pix = np.arange(inputs.n_pixels_total(st))
+    I = case["I"].astype(np.float64)[pix] + 0.05
+    w, lam, s_t, K, delta = 1.0 / len(pix), 2.5e-3, 1.6, 6, 1e-3
+    kw = dict(loss_kind=1, lambda_reg=lam, s_target=s_t)
+    pred, _, g, nbr = topk.forward_backward(st, th, N, pix, I, w, K, delta, **kw)
+    assert np.abs(pred - I).min() > 1e-4
+    fd = np.zeros_like(g)
+    for e in range(th.size):
+        h = 1e-6 * max(1.0, abs(th[e]))
+        tp, tm = th.copy(), th.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd[e] = (topk.forward(st, tp, N, pix, K, delta, nbr=nbr, I_obs=I, w_pix=w, **kw)[1] -
+                 topk.forward(st, tm, N, pix, K, delta, nbr=nbr, I_obs=I, w_pix=w, **kw)[1]) / (2 * h)
+    err = np.abs(g - fd)
+    assert np.all(err <= 1e-6 * np.abs(g) + 1e-9 * np.abs(g).max()), (err.max(), np.argmax(err))
