@@ -268,6 +268,17 @@ typedef struct gsvr_tiling {
  * outside the limits above (the context is then unchanged). */
 gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
 
+/* Objective (Sec. 2.5, "Loss Function").  loss_kind 0: the MSE data term
+ * sum_p w_p (I_hat - I)^2 (default); 1: the paper's L1 data term
+ * sum_p w_p |I_hat - I| (subgradient sign(0) = 0).  lambda_reg > 0 adds the
+ * scale regulariser lambda_reg sum_j sum_k (exp(ls_jk) - s_target)^2 (scales
+ * in mm; the paper's s_target = 1.6 mm, lambda_reg = 2.5e-3) to the loss and
+ * its gradient to the log-scales; in the batched form it enters the total
+ * loss only, not the per-subject losses.  Applies to both forward models.
+ * GSVR_ERR_INVALID_ARG for another loss_kind, lambda_reg < 0 or not finite,
+ * s_target <= 0 or not finite.  Synchronises the stream. */
+gsvr_status gsvr_set_objective(gsvr_ctx *ctx, int32_t loss_kind, float lambda_reg, float s_target);
+
 /* Normalised top-K forward model (Sec. 2.2, Eq. 2; Eq. 5 with sigma_i = 1;
  * Sec. 2.5 "Sparse Computation (Top-K)").  With K >= 1 every later forward
  * predicts a sampled pixel as
@@ -278,13 +289,15 @@ gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
  * Euclidean distance (ties to the smaller index), found exactly by a shell
  * search of a uniform grid over the means (about 16 means per cell, at most
  * 2^16 cells).  The grid is rebuilt every `refresh_every` forwards (1 = every
- * forward: exact neighbours; larger values search the cells of an older build
- * with the current means, as the paper refreshes its index periodically).
- * The loss stays the MSE; gsvr_backward gives the exact gradient for the
- * neighbour sets of the last forward (the selection is piecewise constant).
+ * forward: exact neighbours; larger values select the neighbours by the means
+ * as of the last build, as the paper's periodically refreshed index does,
+ * while the ratio itself uses the current means).
+ * The loss is the one gsvr_set_objective selects; gsvr_backward gives the
+ * exact gradient for the neighbour sets of the last forward (the selection
+ * is piecewise constant).
  * K = 0 restores the plain sum of gsvr_forward.  One subject only
  * (GSVR_ERR_STATE otherwise, at gsvr_forward).
- * Arguments: 0 <= K <= 64; delta > 0 and finite; refresh_every >= 1; else
+ * Arguments: 0 <= K <= 128; delta > 0 and finite; refresh_every >= 1; else
  * GSVR_ERR_INVALID_ARG.  Synchronises the stream; sizes the buffers when
  * Gaussians are set (GSVR_ERR_NOMEM on failure). */
 gsvr_status gsvr_set_topk(gsvr_ctx *ctx, int32_t K, float delta, int32_t refresh_every);

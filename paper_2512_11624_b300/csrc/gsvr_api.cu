@@ -97,6 +97,9 @@ struct gsvr_ctx {
     DBuf<uint32_t> d_item_key, d_item_key_sorted, d_item_order, d_item_key_alt, d_item_val_alt;
     DBuf<int> d_item_hist;
     DBuf<float> d_part;
+    // objective (gsvr_set_objective): data term and scale regulariser
+    int loss_kind = 0;
+    float lambda_reg = 0.f, s_target = 1.6f;
     // normalised top-K form (gsvr_set_topk); K = 0: the plain sum
     int topk_K = 0, topk_refresh = 1;
     float topk_delta = 1e-8f, topk_per_cell = 16.f;
@@ -105,6 +108,7 @@ struct gsvr_ctx {
     DBuf<uint32_t> d_topk_keys, d_topk_keys_sorted, d_topk_gidx, d_topk_kalt, d_topk_valt;
     DBuf<int> d_topk_hist, d_topk_cstart, d_topk_cend, d_topk_nbr, d_topk_ncnt, d_topk_n;
     DBuf<float2> d_topk_pstat;
+    DBuf<float4> d_topk_gm;
     DBuf<double> d_topk_loss_part;
     DBuf<float> d_topk_gacc;
     int cap_rec = 0, cap_keys = 0, cap_items = 0, grid_items = 0;
@@ -297,6 +301,7 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.fwd_bps = ctx->fwd_bps;
     e.bwd_bps = ctx->bwd_bps;
     e.tile_px = ctx->tile_w * ctx->tile_h;
+    e.l1 = ctx->loss_kind;
     e.tile_w = ctx->tile_w;
     e.tile_h = ctx->tile_h;
     e.n_tiles = ctx->n_tiles;
@@ -973,7 +978,7 @@ int topk_cap_px(gsvr_ctx *ctx) { return std::max(ctx->n_mask, 1); }
 
 gsvr_status topk_ensure(gsvr_ctx *ctx) {
     const size_t N = (size_t)std::max<int64_t>(ctx->N, 1), cap = (size_t)topk_cap_px(ctx);
-    const size_t nb = (cap + kTopkThreads - 1) / kTopkThreads;
+    const size_t nb = (cap + 63) / 64;  // forward blocks of 64 or 128 threads
     const bool need = ctx->d_topk_keys.n < N || ctx->d_topk_gacc.n < 10 * N ||
                       ctx->d_topk_nbr.n < cap * (size_t)ctx->topk_K || ctx->d_topk_loss_part.n < nb ||
                       ctx->d_topk_hist.n < (size_t)256 * sort_blocks((int)N) + 1 ||
@@ -984,6 +989,7 @@ gsvr_status topk_ensure(gsvr_ctx *ctx) {
     CK(ctx->d_topk_keys.ensure(N));
     CK(ctx->d_topk_keys_sorted.ensure(N));
     CK(ctx->d_topk_gidx.ensure(N));
+    CK(ctx->d_topk_gm.ensure(N));
     CK(ctx->d_topk_kalt.ensure(N));
     CK(ctx->d_topk_valt.ensure(N));
     CK(ctx->d_topk_hist.ensure((size_t)256 * sort_blocks((int)N) + 1));
@@ -1024,11 +1030,13 @@ TopkArgs topk_args(gsvr_ctx *ctx) {
     a.cell_start = ctx->d_topk_cstart.p;
     a.cell_end = ctx->d_topk_cend.p;
     a.gidx = ctx->d_topk_gidx.p;
+    a.gm = ctx->d_topk_gm.p;
     a.gacc = ctx->d_topk_gacc.p;
     a.pose_acc = ctx->d_pose_acc.p;
     a.K = ctx->topk_K;
     a.delta = ctx->topk_delta;
     a.cap_px = topk_cap_px(ctx);
+    a.l1 = ctx->loss_kind;
     a.status = ctx->d_status.p;
     return a;
 }
@@ -1047,10 +1055,12 @@ gsvr_status topk_forward(gsvr_ctx *ctx) {
         CK(cudaMemsetAsync(ctx->d_topk_cstart.p, 0, sizeof(int) * kTopkMaxCells, st));
         CK(cudaMemsetAsync(ctx->d_topk_cend.p, 0, sizeof(int) * kTopkMaxCells, st));
         launch_topk_cell_ranges(ctx->d_topk_keys_sorted.p, N, ctx->d_topk_cstart.p, ctx->d_topk_cend.p, st);
+        launch_topk_gather_means(ctx->d_theta.p, ctx->d_topk_gidx.p, N, ctx->d_topk_gm.p, st);
     }
     stage_end(ctx, GSVR_STAGE_BIN);
     stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
     launch_topk_forward(topk_args(ctx), topk_cap_px(ctx), ctx->d_loss.p, st);
+    if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
     CK(cudaGetLastError());
     ++ctx->topk_calls;
@@ -1068,6 +1078,7 @@ gsvr_status topk_backward(gsvr_ctx *ctx) {
     stage_end(ctx, GSVR_STAGE_BWD_EVAL);
     stage_begin(ctx, GSVR_STAGE_GRAD);
     launch_topk_epilogue(ctx->d_theta.p, ctx->d_topk_gacc.p, N, ctx->d_grad.p, st);
+    if (ctx->lambda_reg > 0.f) launch_scale_reg_grad(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_grad.p, st);
     launch_pose_grad(ctx->d_pose_acc.p, ctx->d_static.p, ctx->d_theta.p + 11LL * N, ctx->d_grad.p + 11LL * N, M, st);
     stage_end(ctx, GSVR_STAGE_GRAD);
     CK(cudaGetLastError());
@@ -1202,6 +1213,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
     launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_subj_tile_first.p, ctx->n_subj, ctx->d_subj_loss.p,
                        ctx->d_loss.p, ctx->d_status.p, st);
+    if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
     CK(cudaGetLastError());
     ctx->fwd_valid = true;
     return GSVR_OK;
@@ -1246,6 +1258,7 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     a.cap_rec = ctx->cap_rec;
     a.cap_keys = ctx->cap_keys;
     launch_gauss_grad(a, st);
+    if (ctx->lambda_reg > 0.f) launch_scale_reg_grad(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_grad.p, st);
     launch_pose_grad(ctx->d_pose_acc.p, ctx->d_static.p, ctx->d_theta.p + 11LL * N, ctx->d_grad.p + 11LL * N, M, st);
     stage_end(ctx, GSVR_STAGE_GRAD);
     CK(cudaGetLastError());
@@ -1555,10 +1568,26 @@ gsvr_status gsvr_get_topk_neighbors(gsvr_ctx *ctx, int32_t *pix, int32_t *nbr, i
     return GSVR_OK;
 }
 
+gsvr_status gsvr_set_objective(gsvr_ctx *ctx, int32_t loss_kind, float lambda_reg, float s_target) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if ((loss_kind != 0 && loss_kind != 1) || !(lambda_reg >= 0.f) || !std::isfinite(lambda_reg) ||
+        !(s_target > 0.f) || !std::isfinite(s_target))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "objective needs loss_kind 0 or 1, lambda_reg >= 0, s_target > 0");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_objective during graph capture");
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    ctx->loss_kind = loss_kind;
+    ctx->lambda_reg = lambda_reg;
+    ctx->s_target = s_target;
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
 gsvr_status gsvr_set_topk(gsvr_ctx *ctx, int32_t K, float delta, int32_t refresh_every) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (K < 0 || K > kTopkMaxK || !(delta > 0.f) || !std::isfinite(delta) || refresh_every < 1)
-        return fail(ctx, GSVR_ERR_INVALID_ARG, "top-K needs 0 <= K <= 64, delta > 0 finite, refresh_every >= 1");
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "top-K needs 0 <= K <= 128, delta > 0 finite, refresh_every >= 1");
     if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_topk during graph capture");
     DeviceGuard g(ctx->device);
     CK(cudaStreamSynchronize(ctx->stream));

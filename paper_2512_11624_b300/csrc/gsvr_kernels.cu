@@ -869,8 +869,13 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         const float wp = 1.0f / (float)max(ns, 1);
         const float r = acc - a.I_obs[p];
         a.pred[p] = acc;
-        a.rbar[p] = 2.0f * wp * r;
-        l = (double)(wp * r * r);
+        if (a.l1) {  // L1: w |r|, subgradient w sign(r) (sign(0) = 0)
+            a.rbar[p] = wp * (float)((r > 0.f) - (r < 0.f));
+            l = (double)(wp * fabsf(r));
+        } else {
+            a.rbar[p] = 2.0f * wp * r;
+            l = (double)(wp * r * r);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
@@ -1481,6 +1486,14 @@ __global__ void k_topk_cell_ranges(const uint32_t *__restrict__ keys, int N, int
     if (k == N - 1 || keys[k + 1] != c) end[c] = k + 1;
 }
 
+__global__ void k_topk_gather_means(const float *__restrict__ th, const uint32_t *__restrict__ gidx, int N,
+                                    float4 *__restrict__ gm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int j = (int)gidx[k];
+    gm[k] = make_float4(th[j], th[(size_t)N + j], th[2 * (size_t)N + j], __int_as_float(j));
+}
+
 // The sample's slice (binary search over the slices' first pixels), its world
 // position and local coordinate.
 struct TopkPixel {
@@ -1551,19 +1564,24 @@ __device__ __forceinline__ void topk_psf(const SliceDev &S, float sp[6]) {
     sp[5] = e(1, 2);
 }
 
-// Forward: thread per sample.  The K nearest are kept in a max-heap (by
-// (d^2, j)) in shared memory, column `tid` of hd / hj.  Shells of cells at
+// Forward: thread per sample (blocks of 128 threads, 64 when K > 64 so that the
+// heaps fit shared memory).  The K nearest are kept in a max-heap (by
+// (d^2, j)) in shared memory, column `tid` of hd / hj (stride blockDim.x).
+// Candidates are the cell-ordered means of the last grid build (one 16-byte
+// read each); once the heap is full, a cell whose box lies farther than the
+// heap's largest distance is skipped without reading it.  Shells of cells at
 // Chebyshev distance 0, 1, 2, ... around the pixel's cell are scanned until
 // the heap is full and its largest distance is inside the box the scanned
 // shells cover (or the whole grid has been scanned).
 __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
     extern __shared__ unsigned char topk_raw[];
+    const int BS = blockDim.x;  // heap stride
     float *hd = reinterpret_cast<float *>(topk_raw);
-    int *hj = reinterpret_cast<int *>(hd + a.K * kTopkThreads);
+    int *hj = reinterpret_cast<int *>(hd + a.K * BS);
     __shared__ double red[kTopkThreads / 32];
     const int tid = threadIdx.x;
     const int ns = min(*a.n_sampled, a.cap_px);
-    const int s = blockIdx.x * kTopkThreads + tid;
+    const int s = blockIdx.x * BS + tid;
     double l = 0.0;
     if (s < ns) {
         const int p = a.sampled[s];
@@ -1579,46 +1597,58 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
                 int pos = cnt++;
                 while (pos > 0) {
                     const int par = (pos - 1) >> 1;
-                    const float dp = d[par * kTopkThreads];
-                    const int jp = jj[par * kTopkThreads];
+                    const float dp = d[par * BS];
+                    const int jp = jj[par * BS];
                     if (!less(dp, jp, d2, j)) break;
-                    d[pos * kTopkThreads] = dp;
-                    jj[pos * kTopkThreads] = jp;
+                    d[pos * BS] = dp;
+                    jj[pos * BS] = jp;
                     pos = par;
                 }
-                d[pos * kTopkThreads] = d2;
-                jj[pos * kTopkThreads] = j;
+                d[pos * BS] = d2;
+                jj[pos * BS] = j;
             } else if (less(d2, j, d[0], jj[0])) {  // replace the largest, sift down
                 int pos = 0;
                 for (;;) {
                     int ch = 2 * pos + 1;
                     if (ch >= K) break;
-                    if (ch + 1 < K && less(d[ch * kTopkThreads], jj[ch * kTopkThreads], d[(ch + 1) * kTopkThreads],
-                                           jj[(ch + 1) * kTopkThreads]))
+                    if (ch + 1 < K && less(d[ch * BS], jj[ch * BS], d[(ch + 1) * BS],
+                                           jj[(ch + 1) * BS]))
                         ++ch;
-                    const float dc = d[ch * kTopkThreads];
-                    const int jc = jj[ch * kTopkThreads];
+                    const float dc = d[ch * BS];
+                    const int jc = jj[ch * BS];
                     if (!less(d2, j, dc, jc)) break;
-                    d[pos * kTopkThreads] = dc;
-                    jj[pos * kTopkThreads] = jc;
+                    d[pos * BS] = dc;
+                    jj[pos * BS] = jc;
                     pos = ch;
                 }
-                d[pos * kTopkThreads] = d2;
-                jj[pos * kTopkThreads] = j;
+                d[pos * BS] = d2;
+                jj[pos * BS] = j;
             }
         };
         int c[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) c[k] = topk_cell_axis(g, k, (float)q.x[k]);
+        const float xf[3] = {(float)q.x[0], (float)q.x[1], (float)q.x[2]};
         auto scan_cell = [&](int cx, int cy, int cz) {
+            if (cnt == K) {  // prune: squared distance from x to the cell's box
+                const int cc[3] = {cx, cy, cz};
+                float m2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float lo = g.org[k] + (float)cc[k] * g.h, hi = lo + g.h;
+                    const float dk = fmaxf(fmaxf(lo - xf[k], xf[k] - hi), 0.f);
+                    m2 = fmaf(dk, dk, m2);
+                }
+                if (m2 > d[0] * (1.0f + 1e-5f)) return;
+            }
             const int cell = (cz * g.n[1] + cy) * g.n[0] + cx;
             const int k1 = a.cell_end[cell];
             for (int k = a.cell_start[cell]; k < k1; ++k) {
-                const int j = (int)a.gidx[k];
-                const float vx = (float)(q.x[0] - (double)a.theta[j]);
-                const float vy = (float)(q.x[1] - (double)a.theta[(size_t)N + j]);
-                const float vz = (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]);
-                offer(vx * vx + vy * vy + vz * vz, j);
+                const float4 m = a.gm[k];
+                const float vx = (float)(q.x[0] - (double)m.x);
+                const float vy = (float)(q.x[1] - (double)m.y);
+                const float vz = (float)(q.x[2] - (double)m.z);
+                offer(vx * vx + vy * vy + vz * vz, __float_as_int(m.w));
             }
         };
         for (int sh = 0; N > 0; ++sh) {  // (no grid is built without Gaussians)
@@ -1651,7 +1681,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
         topk_psf(S, sp);
         double num = 0.0, den = 0.0;
         for (int e = 0; e < cnt; ++e) {
-            const int j = jj[e * kTopkThreads];
+            const int j = jj[e * BS];
             const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
             const TopkChol L = topk_chol(g0, g1, sp);
             float w[3];
@@ -1668,9 +1698,14 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
         const float w = 1.0f / (float)max(ns, 1);
         const float r = Ih - a.I_obs[p];
         a.pred[p] = Ih;
-        a.rbar[p] = 2.f * w * r;
         a.pstat[s] = make_float2(Ih, D);
-        l = (double)w * (double)r * (double)r;
+        if (a.l1) {
+            a.rbar[p] = w * (float)((r > 0.f) - (r < 0.f));
+            l = (double)w * fabs((double)r);
+        } else {
+            a.rbar[p] = 2.f * w * r;
+            l = (double)w * (double)r * (double)r;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
@@ -1678,7 +1713,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int w = 0; w < kTopkThreads / 32; ++w) t += red[w];
+        for (int w = 0; w < BS / 32; ++w) t += red[w];
         a.loss_part[blockIdx.x] = t;
     }
 }
@@ -1831,6 +1866,32 @@ __global__ void k_topk_epilogue(GradArgs a, const float *__restrict__ gacc) {
     for (int c = 0; c < 10; ++c) v[c] = gacc[(size_t)c * a.N + j];
     v[10] = 0.f;  // no log-determinant factor in the ratio
     gauss_epilogue(a, j, v);
+}
+
+__global__ void __launch_bounds__(1024) k_scale_reg_loss(const float *__restrict__ th, int N, float lambda,
+                                                          float s_target, double *loss) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < 3 * N; e += 1024) {
+        const double d = (double)expf(th[(size_t)3 * N + e]) - (double)s_target;
+        s += d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 32; ++w) t += red[w];
+        *loss += (double)lambda * t;
+    }
+}
+__global__ void k_scale_reg_grad(const float *__restrict__ th, int N, float lambda, float s_target,
+                                 float *__restrict__ grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * N) return;
+    const float sc = expf(th[(size_t)3 * N + e]);
+    grad[(size_t)3 * N + e] += 2.f * lambda * (sc - s_target) * sc;
 }
 
 inline int cdiv(int64_t a, int b) { return (int)((a + b - 1) / b); }
@@ -2092,11 +2153,27 @@ void launch_topk_cell_ranges(const uint32_t *keys_sorted, int N, int *cell_start
     k_topk_cell_ranges<<<cdiv(N, 256), 256, 0, st>>>(keys_sorted, N, cell_start, cell_end);
     counted();
 }
+void launch_scale_reg_loss(const float *theta, int N, float lambda, float s_target, double *loss, cudaStream_t st) {
+    if (N <= 0) return;
+    k_scale_reg_loss<<<1, 1024, 0, st>>>(theta, N, lambda, s_target, loss);
+    counted();
+}
+void launch_scale_reg_grad(const float *theta, int N, float lambda, float s_target, float *grad, cudaStream_t st) {
+    if (N <= 0) return;
+    k_scale_reg_grad<<<cdiv(3LL * N, 256), 256, 0, st>>>(theta, N, lambda, s_target, grad);
+    counted();
+}
+void launch_topk_gather_means(const float *theta, const uint32_t *gidx, int N, float4 *gm, cudaStream_t st) {
+    if (N <= 0) return;
+    k_topk_gather_means<<<cdiv(N, 256), 256, 0, st>>>(theta, gidx, N, gm);
+    counted();
+}
 void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream_t st) {
-    const int nb = std::max(1, cdiv(cap_px, kTopkThreads));
-    const size_t smem = (size_t)a.K * kTopkThreads * (sizeof(float) + sizeof(int));
+    const int bs = a.K > 64 ? 64 : kTopkThreads;
+    const int nb = std::max(1, cdiv(cap_px, bs));
+    const size_t smem = (size_t)a.K * bs * (sizeof(float) + sizeof(int));
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_topk_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_topk_fwd<<<nb, kTopkThreads, smem, st>>>(a);
+    k_topk_fwd<<<nb, bs, smem, st>>>(a);
     k_topk_loss_total<<<1, 256, 0, st>>>(a.loss_part, nb, loss, a.status);
     counted(2);
 }

@@ -73,6 +73,7 @@ struct EvalArgs {
     int fwd_pxr;                      // forward pixels per thread, 1, 2 or 4 (0: by tile width)
     int fwd_bps, bwd_bps;             // persistent CTAs per SM (0: as many as fit)
     int tile_px;                      // tile_w * tile_h
+    int l1;                           // data term: 0 MSE, 1 L1 (the paper's)
     int tile_w, tile_h;
     int n_tiles;
     unsigned *status;
@@ -172,7 +173,7 @@ struct TopkGrid {
     int n_cells;
     int box[6];  // order-preserving integer images of the means' min (xyz) and max (xyz)
 };
-constexpr int kTopkMaxK = 64;
+constexpr int kTopkMaxK = 128;
 constexpr int kTopkThreads = 128;
 constexpr int kTopkMaxCells = 1 << 16;
 struct TopkArgs {
@@ -191,17 +192,21 @@ struct TopkArgs {
     const TopkGrid *grid;
     const int *cell_start, *cell_end;
     const uint32_t *gidx;    // Gaussian indices in cell order
+    const float4 *gm;        // (mu, Gaussian index) in cell order, as of the last grid build
     float *gacc;             // 10 x N: d mu (3), d Sigma (xx yy zz xy xz yz), d c
     double *pose_acc;        // M x 12
     int K;
     float delta;
     int cap_px;
+    int l1;                  // data term: 0 MSE, 1 L1
     unsigned *status;
 };
 // Grid build: bounding box, cell size, cell keys; the caller sorts the keys
 // (stable radix, Gaussian index as value) and calls launch_topk_cell_ranges.
 void launch_topk_grid(const float *theta, int N, float per_cell, TopkGrid *g, uint32_t *keys, cudaStream_t st);
 void launch_topk_cell_ranges(const uint32_t *keys_sorted, int N, int *cell_start, int *cell_end, cudaStream_t st);
+// gm[k] = (mu of Gaussian gidx[k], gidx[k] as float bits): the search reads one 16-byte record per candidate
+void launch_topk_gather_means(const float *theta, const uint32_t *gidx, int N, float4 *gm, cudaStream_t st);
 // Forward: K nearest by a shell search of the grid, the ratio per sampled
 // pixel, residuals and per-block loss partials; then the loss total.
 void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream_t st);
@@ -210,5 +215,11 @@ void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream
 // pose_acc; the Gaussian epilogue maps gacc to the parameter gradient.
 void launch_topk_backward(const TopkArgs &a, int cap_px, cudaStream_t st);
 void launch_topk_epilogue(const float *theta, const float *gacc, int N, float *grad, cudaStream_t st);
+
+// Scale regulariser of the paper's loss (Sec. 2.5): lambda sum_j sum_k
+// (exp(ls_jk) - s_target)^2 added to *loss (one block, fixed order), and its
+// gradient 2 lambda (s - s_target) s added to the log-scale gradients.
+void launch_scale_reg_loss(const float *theta, int N, float lambda, float s_target, double *loss, cudaStream_t st);
+void launch_scale_reg_grad(const float *theta, int N, float lambda, float s_target, float *grad, cudaStream_t st);
 
 }  // namespace gsvr

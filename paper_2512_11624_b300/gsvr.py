@@ -31,7 +31,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_timing_reset", "gsvr_get_kernel_times", "gsvr_count_pairs", "gsvr_forward_noalloc",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
-           "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors"]
+           "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
+           "gsvr_set_objective"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -124,6 +125,7 @@ def _load():
         "gsvr_set_step": ([vp, i64], C.c_int),
         "gsvr_set_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
         "gsvr_set_topk": ([vp, C.c_int32, C.c_float, C.c_int32], C.c_int),
+        "gsvr_set_objective": ([vp, C.c_int32, C.c_float, C.c_float], C.c_int),
         "gsvr_get_topk_neighbors": ([vp, vp, vp, vp, i64, C.POINTER(i64)], C.c_int),
         "gsvr_reserve": ([vp, i64, i64], C.c_int),
         "gsvr_get_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
@@ -323,6 +325,11 @@ def gsvr_set_tiling(ctx, t):
 def gsvr_set_topk(ctx, K, delta=1e-8, refresh_every=1):
     """Normalised top-K forward (K >= 1) or the plain sum (K = 0)."""
     return _check(ctx, lib.gsvr_set_topk(ctx, int(K), float(delta), int(refresh_every)))
+
+
+def gsvr_set_objective(ctx, loss_kind=0, lambda_reg=0.0, s_target=1.6):
+    """Data term (0 MSE, 1 L1) and scale regulariser of the loss."""
+    return _check(ctx, lib.gsvr_set_objective(ctx, int(loss_kind), float(lambda_reg), float(s_target)))
 
 
 def gsvr_get_topk_neighbors(ctx, K):

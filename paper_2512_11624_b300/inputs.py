@@ -285,6 +285,35 @@ def grid_gaussians(phantom, h=0.8, s=0.8):
     return np.concatenate([P.T, ls, q, c[None, :]], axis=0).reshape(-1), N
 
 
+def background_gaussians(phantom, h=2.4, margin=15.0):
+    """Zero-amplitude isotropic Gaussians (scale h) on an h-mm grid over the
+    band within `margin` mm outside the phantom: the background a normalised
+    (ratio) model must represent explicitly, since its prediction tends to the
+    nearest Gaussians' amplitudes however far they are."""
+    ext = np.asarray(phantom.axes) + margin
+    axes = [np.arange(-e + 0.5 * h, e, h) for e in ext]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
+    P = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], 1)
+    P = P[phantom.inside(P, margin) & ~phantom.inside(P)]
+    N = P.shape[0]
+    ls = np.full((3, N), np.log(h))
+    q = np.zeros((4, N))
+    q[0] = 1.0
+    return np.concatenate([P.T, ls, q, np.zeros((1, N))], axis=0).reshape(-1), N
+
+
+def with_gaussians(case, theta_g_extra, n_extra):
+    """The case with n_extra more Gaussians appended (component-major layout)."""
+    N = case["N"]
+    g = case["theta"][:11 * N].reshape(11, N)
+    e = np.asarray(theta_g_extra, np.float32).reshape(11, n_extra)
+    out = dict(case)
+    out["N"] = N + n_extra
+    out["theta"] = np.concatenate([np.concatenate([g, e], axis=1).reshape(-1), case["theta"][11 * N:]]).astype(
+        np.float32)
+    return out
+
+
 def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0, motion_mm=3.0, jitter=0.0):
     """The fetal-scale plain case: ~200k Gaussians on a 0.8 mm grid inside the
     brain phantom; axial / coronal / sagittal stacks of 40 x 192 x 192 px at

@@ -17,12 +17,17 @@ from . import gsvr, inputs
 
 
 class PSNRProbe:
-    def __init__(self, phantom, N, device=0, h=0.8, stream=None):
+    """`topk` = (K, delta): read the normalised top-K volume of Eq. 2 instead of
+    the plain sum."""
+
+    def __init__(self, phantom, N, device=0, h=0.8, stream=None, topk=None):
         st, ref, inside = inputs.grid_probe(phantom, h)
         self.N = int(N)
         case = {"stacks": [st], "N": self.N, "theta": np.zeros(11 * self.N + 6 * st["n_slices"], np.float32),
                 "I": ref, "mask": inside}
         self.ctx = gsvr.Context(case, device=device, stream=stream, tile_h=16, tile_w=16)
+        if topk:
+            gsvr.gsvr_set_topk(self.ctx.ctx, int(topk[0]), float(topk[1]), 1)
         self.n_points = int(inside.sum())
 
     def psnr(self, theta_g):
@@ -105,10 +110,11 @@ def ensure_room(ctx, fill=0.75, grow=1.5):
 class Reconstruction:
     """One subject: gsvr context + Adam state; `step` = sample, forward,
     backward, Adam.  `fixed` builds a fixed-capacity context (see make_context),
-    `tune` lets the autotuner pick its launch shape."""
+    `tune` lets the autotuner pick its launch shape, `topk` = (K, delta,
+    refresh_every) switches to the normalised top-K model (gsvr_set_topk)."""
 
     def __init__(self, case, device=0, stream=None, n_sample=None, lr=None, frozen=None,
-                 step_every=PLAIN_STEP_EVERY, gamma=0.5, fixed=False, tune=False, **cfg):
+                 step_every=PLAIN_STEP_EVERY, gamma=0.5, fixed=False, tune=False, topk=None, **cfg):
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         if fixed or tune:
             self.ctx, self.shape = make_context(case, device, self.stream, n_sample, tune=tune)
@@ -116,6 +122,8 @@ class Reconstruction:
             self.ctx = gsvr.Context(case, device=device, stream=self.stream.cuda_stream, **cfg)
             self.shape = gsvr.gsvr_get_tiling(self.ctx.ctx)
         self.fixed = fixed or tune
+        if topk:
+            gsvr.gsvr_set_topk(self.ctx.ctx, int(topk[0]), float(topk[1]), int(topk[2]) if len(topk) > 2 else 1)
         self.N = int(case["N"])
         self.n_sample = min(int(n_sample), int(np.count_nonzero(case["mask"]))) if n_sample else n_sample
         self.lr = dict(PLAIN_LR, **(lr or {}))

@@ -2,6 +2,8 @@
 
   python -m paper_2512_11624_b300.study batched [--subjects 16] [--iters 2000] [--out FILE]
   python -m paper_2512_11624_b300.study learned [--phantoms 2000] [--epochs 20] [--cases 10] [--out FILE]
+  python -m paper_2512_11624_b300.study topk [--k 10 20 50 80] [--iters 600] [--out FILE]
+  python -m paper_2512_11624_b300.study cnnbench [--batch 256] [--steps 50]
 
 `batched`: the batched multi-subject workload (`inputs.batched`: 16 subjects of
 uneven size).  Every subject is first reconstructed alone (its own context with
@@ -354,6 +356,98 @@ def _fmt(v):
     return "-" if v is None else "%.2f" % v
 
 
+def run_topk(args):
+    """The normalised top-K model (Eq. 2 / Eq. 5 ratio over the K nearest
+    Gaussians) against the plain sum on the fetal workload: per configuration,
+    `iters` iterations (2^18 sampled pixels, Adam with StepLR), device seconds
+    per iteration, stage times, PSNR of the volume each model defines (the
+    top-K model's probe reads the ratio, the plain one the sum) every
+    `eval_every` iterations, and the device seconds to the plain run's final
+    PSNR - 0.5 dB.  The ratio's amplitudes are O(1) colours: its initial c is
+    the plain initial c divided by the plain sum's grid factor h^3 / ((2 pi)^(3/2) s^3),
+    and its c learning rate the plain one divided by the same factor.  A ratio
+    model predicts the nearest Gaussians' colours however far they are, so its
+    runs also start with zero-amplitude background Gaussians (2.4 mm grid) over
+    the 15 mm band of the pixel mask outside the brain.  `loss` / `lambda_reg`
+    / `s_target` set the ratio runs' objective (Sec. 2.5): the regulariser's
+    weight is the paper's per-pixel-sum weight divided by the sample size (our
+    data term is a mean over the sampled pixels), and s_target defaults to
+    the Gaussians' initial scale and spacing (0.8 mm; the paper's 1.6 mm goes
+    with its 10-80 k Gaussians per brain, ours are 200 k)."""
+    import torch
+    from . import gsvr, inputs
+    from .recon import PLAIN_LR, PSNRProbe, Reconstruction
+    torch.cuda.set_device(0)
+    case = inputs.fetal(args.seed)
+    N = case["N"]
+    factor = 1.0 / (2 * np.pi) ** 1.5  # h^3 / ((2 pi)^(3/2) s^3) with h = s = 0.8 mm
+    configs = [("plain", None)] + [("topk K=%d" % K, (K, args.delta, args.refresh)) for K in args.k]
+    out = []
+    target = None
+    for name, tk in configs:
+        c = dict(case)
+        lr = None
+        if tk:
+            th = case["theta"].copy()
+            th[10 * N:11 * N] /= factor
+            c["theta"] = th
+            bg, nb = inputs.background_gaussians(case["phantom"])
+            c = inputs.with_gaussians(c, bg, nb)
+            lr = dict(lr_c=PLAIN_LR["lr_c"] / factor)
+        # plain: the fixed-capacity context of the other studies (no host
+        # synchronisation per iteration); top-K: no capacities involved
+        rec = (Reconstruction(c, n_sample=args.n_sample, lr=lr, topk=tk, timing=1) if tk else
+               Reconstruction(c, n_sample=args.n_sample, fixed=True))
+        if tk:
+            gsvr.gsvr_set_objective(rec.ctx.ctx, 1 if args.loss == "l1" else 0, args.lambda_reg / args.n_sample,
+                                    args.s_target)
+        probe = PSNRProbe(case["phantom"], c["N"], topk=(tk[0], tk[1]) if tk else None)
+        if tk:
+            gsvr.gsvr_timing_reset(rec.ctx.ctx)
+        res = rec.run(args.iters, probe=probe, eval_every=args.eval_every, target_psnr=target)
+        hist = res["history"]
+        iters = hist[-1][0]
+        stage = None
+        if tk:
+            kt = gsvr.gsvr_get_kernel_times(rec.ctx.ctx)
+            stage = {k: kt["ms"][k] / max(iters, 1) for k in ("sample", "prep", "bin", "fwd_eval", "bwd_eval",
+                                                              "grad", "adam")}
+        row = {"model": name, "K": tk[0] if tk else None, "delta": tk[1] if tk else None,
+               "loss": args.loss if tk else "mse", "lambda_reg": args.lambda_reg if tk else 0.0,
+               "s_target": args.s_target if tk else None,
+               "refresh_every": tk[2] if tk else None, "iters": iters, "ms_per_iter": 1e3 * hist[-1][1] / iters,
+               "stage_ms_per_iter": stage, "psnr": [(h[0], h[3]) for h in hist],
+               "seconds_to_target": res["time_to_target"], "target_psnr": target,
+               "pairs_per_s": (args.n_sample * tk[0] / (hist[-1][1] / iters)) if tk else None}
+        if target is None:
+            target = hist[-1][3] - 0.5
+            row["target_psnr"] = target
+            row["seconds_to_target"] = next((h[1] for h in hist if h[3] is not None and h[3] >= target), None)
+        print(json.dumps(row), flush=True)
+        out.append(row)
+        probe.close()
+        rec.close()
+    if args.out:
+        json.dump(out, open(args.out, "w"), indent=1)
+
+
+def run_topk_step(args):
+    """A few plain top-K iterations (forward + backward) on the fetal workload's
+    2^18-pixel sample: the command the top-K kernels are profiled with."""
+    import torch
+    from . import gsvr, inputs
+    torch.cuda.set_device(0)
+    ctx = gsvr.Context(inputs.fetal(0))
+    gsvr.gsvr_sample_pixels(ctx.ctx, 1 << 18, 0)
+    gsvr.gsvr_set_topk(ctx.ctx, args.k, args.delta, 1)
+    for _ in range(args.steps):
+        ctx.forward()
+        ctx.backward()
+    gsvr.gsvr_sync_status(ctx.ctx)
+    print(json.dumps({"K": args.k, "loss": ctx.loss()}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -383,8 +477,28 @@ def main():
     cb.add_argument("--batch", type=int, default=256)
     cb.add_argument("--steps", type=int, default=50)
     cb.add_argument("--warmup", type=int, default=5)
+    tk = sub.add_parser("topk")
+    tk.add_argument("--k", type=int, nargs="+", default=[10, 20, 50, 80])
+    tk.add_argument("--delta", type=float, default=1e-8)
+    tk.add_argument("--refresh", type=int, default=1)
+    tk.add_argument("--iters", type=int, default=600)
+    tk.add_argument("--eval-every", type=int, default=100)
+    tk.add_argument("--n-sample", type=int, default=1 << 18)
+    tk.add_argument("--seed", type=int, default=0)
+    tk.add_argument("--loss", choices=["mse", "l1"], default="mse")
+    tk.add_argument("--lambda-reg", type=float, default=0.0)
+    tk.add_argument("--s-target", type=float, default=0.8)
+    tk.add_argument("--out", default="")
+    ts = sub.add_parser("topk-step")
+    ts.add_argument("--k", type=int, default=50)
+    ts.add_argument("--delta", type=float, default=1e-8)
+    ts.add_argument("--steps", type=int, default=3)
     args = ap.parse_args()
-    if args.cmd == "cnnbench":
+    if args.cmd == "topk":
+        run_topk(args)
+    elif args.cmd == "topk-step":
+        run_topk_step(args)
+    elif args.cmd == "cnnbench":
         run_cnnbench(args)
     elif args.cmd == "batched":
         run_batched(args)

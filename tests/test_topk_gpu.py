@@ -4,7 +4,7 @@ gsvr_set_topk) against the float64 oracle of ``oracle/topk.py``.
 - Forward values within 1e-5 relative (floored at 1e-3 of the case maximum),
   gradients within 1e-4 relative plus 2e-6 of the sum of |pair terms|, as on
   the plain path; cases with K below, at and above N, a lone Gaussian, two
-  oblique stacks with motion, K = 64.
+  oblique stacks with motion, K = 64 and 128 (the forward's 64-thread blocks).
 - The neighbour sets are unique except at distance ties (lattice-placed
   Gaussians tie often), so the GPU's sets are read back and checked to be valid
   K-nearest sets (no left-out mean nearer than an included one, beyond float32
@@ -79,6 +79,7 @@ def run(G, case, K, delta, sample=None, refresh=1):
     (23, 30, [(2, 9, 7)], 1, 50, 1e-2),
     (24, 1, [(1, 6, 5)], 1, 1, 1e-2),
     (25, 200, [(2, 16, 16), (3, 11, 13)], 2, 64, 1e-4),
+    (31, 300, [(2, 15, 14)], 2, 128, 1e-4),
 ])
 def test_matches_oracle(G, topk, seed, N, sizes, n_stacks, K, delta):
     case = inputs.random_case(seed, N, sizes, n_stacks=n_stacks, extent=4.0, motion_deg=8.0)
@@ -128,7 +129,7 @@ def test_k_zero_restores_plain_sum(G):
 def test_argument_checks(G):
     case = inputs.random_case(28, 10, [(1, 6, 6)], n_stacks=1)
     ctx = G.Context(case)
-    for K, d, r in [(65, 1e-3, 1), (-1, 1e-3, 1), (5, 0.0, 1), (5, float("nan"), 1), (5, 1e-3, 0)]:
+    for K, d, r in [(129, 1e-3, 1), (-1, 1e-3, 1), (5, 0.0, 1), (5, float("nan"), 1), (5, 1e-3, 0)]:
         with pytest.raises(G.GsvrError) as e:
             G.gsvr_set_topk(ctx.ctx, K, d, r)
         assert "INVALID_ARG" in str(e.value)
