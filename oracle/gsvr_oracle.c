@@ -346,10 +346,31 @@ static double data_dloss(int loss_kind, double w, double r) {
     return loss_kind ? w * (double)((r > 0.0) - (r < 0.0)) : 2.0 * w * r;
 }
 
-/* Forward: pred[p] = sum over ALL Gaussians; loss = sum_p of the data loss. */
+/* Per-slice outlier terms (Sec. 2.4): slw = NULL, or 2 M values: log sigma_i
+ * (intensity scale: the prediction is sigma_i times the model) then
+ * log omega_i (aleatoric weight: a pixel of slice i costs
+ * w (loss(r) / omega_i + log omega_i)).  pixel_terms gives, for a model value s
+ * of slice i, the prediction, the loss and dL/ds; the per-slice derivatives
+ * in log sigma_i and log omega_i are added to gsl (when not NULL). */
+static void pixel_terms(const double *slw, int64_t M, int64_t i, int loss_kind, double w, double s, double I,
+                        double *pred, double *L, double *dLds, double *gsl) {
+    const double sig = slw ? exp(slw[i]) : 1.0, lw = slw ? slw[M + i] : 0.0, iw = exp(-lw);
+    const double r = sig * s - I;
+    const double l = data_loss(loss_kind, w, r), dl = data_dloss(loss_kind, w, r);
+    *pred = sig * s;
+    *L = l * iw + (slw ? w * lw : 0.0);
+    *dLds = sig * dl * iw;
+    if (gsl) {
+        gsl[i] += dl * iw * sig * s;
+        gsl[M + i] += w - l * iw;
+    }
+}
+
+/* Forward: pred[p] = sum over ALL Gaussians (times sigma_i); loss = sum_p of the
+ * pixel losses. */
 int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
-                   const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, int loss_kind, double *pred,
-                   double *loss) {
+                   const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, int loss_kind,
+                   const double *slw, double *pred, double *loss) {
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
     double L = 0.0;
@@ -364,8 +385,9 @@ int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *th
             eval_pair(&m.g[j], &m.fr[i], x, norm_mode, &pr);
             s += m.g[j].c * pr.g;
         }
-        pred[p] = s;
-        if (I_obs) L += data_loss(loss_kind, w_pix, s - I_obs[p]);
+        double lp = 0.0, dl;
+        pixel_terms(slw, m.M, i, loss_kind, w_pix, s, I_obs ? I_obs[p] : 0.0, &pred[p], &lp, &dl, NULL);
+        if (I_obs) L += lp;
     }
     if (loss) *loss = L;
     model_free(&m);
@@ -506,8 +528,8 @@ static void pose_chain(const or_slice *s, const double *pose, const double *GR, 
  */
 int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
                             const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, int loss_kind,
-                            const uint8_t *sel, double *pred, double *loss, double *grad, double *absgrad,
-                            double cutoff, double *trunc_pred, double *trunc_grad) {
+                            const double *slw, double *slw_grad, const uint8_t *sel, double *pred, double *loss,
+                            double *grad, double *absgrad, double cutoff, double *trunc_pred, double *trunc_grad) {
     const int want_trunc = cutoff > 0.0 && trunc_grad != NULL && absgrad != NULL;
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
@@ -516,6 +538,7 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
     double *px = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
     double *pu = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
     int64_t *psl = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
+    double *pmod = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double L = 0.0;
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : L)
     for (int64_t p = 0; p < P; ++p) {
@@ -529,13 +552,21 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
             s += m.g[j].c * pr.g;
             if (pr.e < cutoff) tr += fabs(m.g[j].c * pr.g);
         }
-        if (pred) pred[p] = s;
+        double pr_, lp;
+        pixel_terms(slw, M, i, loss_kind, w_pix, s, I_obs[p], &pr_, &lp, &rbar[p], NULL);
+        if (pred) pred[p] = pr_;
         if (trunc_pred) trunc_pred[p] = tr;
-        double r = s - I_obs[p];
-        L += data_loss(loss_kind, w_pix, r);
-        rbar[p] = data_dloss(loss_kind, w_pix, r);
+        pmod[p] = s;
+        L += lp;
     }
     if (loss) *loss = L;
+    if (slw_grad) {  /* per-slice sums in pixel order */
+        memset(slw_grad, 0, sizeof(double) * (size_t)(2 * M));
+        for (int64_t p = 0; p < P; ++p) {
+            double a, b, c;
+            pixel_terms(slw, M, psl[p], loss_kind, w_pix, pmod[p], I_obs[p], &a, &b, &c, slw_grad);
+        }
+    }
     memset(grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
     if (absgrad) memset(absgrad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
     if (want_trunc) memset(trunc_grad, 0, sizeof(double) * (size_t)(11 * N + 6 * M));
@@ -672,6 +703,7 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
     }
     free(pacc);
     free(rbar);
+    free(pmod);
     free(px);
     free(pu);
     free(psl);

@@ -36,9 +36,9 @@ def lib():
         path = _build.build()
         _lib = C.CDLL(path)
         d, i64, vp = C.c_double, C.c_int64, C.c_void_p
-        _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, C.c_int, vp, vp]
+        _lib.oracle_forward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, C.c_int, vp, vp, vp]
         _lib.oracle_forward_backward.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, C.c_int, vp, vp,
-                                                 vp, vp, vp, d, vp, vp]
+                                                 vp, vp, vp, vp, vp, d, vp, vp]
         _lib.oracle_adam.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, d, d, i64, vp]
         _lib.oracle_adam.restype = None
         _lib.oracle_build_slices.argtypes = [C.c_int, vp, vp, vp]
@@ -106,17 +106,20 @@ def scale_reg(theta, N, lambda_reg, s_target):
     return float(lambda_reg) * float(np.sum(d * d)), 2.0 * float(lambda_reg) * d * s
 
 
-def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0, loss_kind=0, lambda_reg=0.0, s_target=1.6):
+def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0, loss_kind=0, lambda_reg=0.0, s_target=1.6,
+            slw=None):
     """Predictions for the listed global pixels and the loss (float64): data
-    term MSE (loss_kind 0) or L1 (1), plus the scale regulariser."""
+    term MSE (loss_kind 0) or L1 (1), plus the scale regulariser; slw (2 M:
+    log sigma_i, log omega_i) switches on the per-slice outlier terms."""
     st = _stacks(stacks)
     th = _f64(theta)
     pix = np.ascontiguousarray(pix, dtype=np.int64)
     I = _f64(I_obs) if I_obs is not None else None
     pred = np.zeros(len(pix), np.float64)
     loss = np.zeros(1, np.float64)
+    sw = _f64(slw) if slw is not None else None
     rc = lib().oracle_forward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
-                              float(w_pix), int(norm_mode), int(loss_kind), _p(pred), _p(loss))
+                              float(w_pix), int(norm_mode), int(loss_kind), _p(sw), _p(pred), _p(loss))
     if rc != 0:
         raise RuntimeError("oracle_forward failed")
     L = float(loss[0])
@@ -126,12 +129,14 @@ def forward(stacks, theta, N, pix, I_obs=None, w_pix=1.0, norm_mode=0, loss_kind
 
 
 def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None, want_abs=True, cutoff=None,
-                     loss_kind=0, lambda_reg=0.0, s_target=1.6):
+                     loss_kind=0, lambda_reg=0.0, s_target=1.6, slw=None, slw_grad=None):
     """(pred, loss, grad, absgrad) in float64; grad has the parameter-vector layout.
     With `cutoff`, returns (pred, loss, grad, absgrad, trunc_pred, trunc_grad): the
     sums of |pair contributions| over the pairs below the cutoff, per output.
     loss_kind 0 / 1: MSE / L1 data term; lambda_reg > 0 adds the scale
-    regulariser (its gradient terms counted in absgrad)."""
+    regulariser (its gradient terms counted in absgrad).  slw (2 M: log sigma_i,
+    log omega_i) switches on the per-slice outlier terms; their gradient is
+    written to slw_grad (2 M, when given)."""
     st = _stacks(stacks)
     th = _f64(theta)
     pix = np.ascontiguousarray(pix, dtype=np.int64)
@@ -147,9 +152,13 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, norm_mode=0, sel=None,
     tg = np.zeros(n, np.float64) if cutoff else None
     if cutoff and absg is None:
         absg = np.zeros(n, np.float64)
+    sw = _f64(slw) if slw is not None else None
+    if slw_grad is not None:
+        assert slw_grad.dtype == np.float64 and slw_grad.flags.c_contiguous and slw_grad.size == 2 * M
     rc = lib().oracle_forward_backward(len(stacks), C.addressof(st), int(N), _p(th), len(pix), _p(pix), _p(I),
-                                       float(w_pix), int(norm_mode), int(loss_kind), _p(s), _p(pred), _p(loss),
-                                       _p(grad), _p(absg), float(cutoff or 0.0), _p(tp), _p(tg))
+                                       float(w_pix), int(norm_mode), int(loss_kind), _p(sw), _p(slw_grad), _p(s),
+                                       _p(pred), _p(loss), _p(grad), _p(absg), float(cutoff or 0.0), _p(tp),
+                                       _p(tg))
     if rc != 0:
         raise RuntimeError("oracle_forward_backward failed")
     if lambda_reg:

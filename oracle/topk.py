@@ -100,21 +100,40 @@ def _pairs(stacks, theta, N, pix, K, nbr):
     return x, sl, u, R, nbr, Pv, E, var
 
 
+def _slice_terms(slw, M, sl, model, I, w, loss_kind):
+    """Per-slice outlier terms (Sec. 2.4): prediction sigma_i * model, pixel
+    loss w (l(r) / omega_i + log omega_i) with log sigma_i = slw[i], log
+    omega_i = slw[M + i] (slw None: sigma = omega = 1 without the log term).
+    Returns (pred, per-pixel loss, dL/dmodel, per-pixel d/dlog sigma, d/dlog omega)."""
+    w = np.broadcast_to(np.asarray(w, np.float64), model.shape)
+    sig = np.exp(slw[sl]) if slw is not None else np.ones_like(model)
+    lw = slw[M + sl] if slw is not None else np.zeros_like(model)
+    iw = np.exp(-lw)
+    pred = sig * model
+    r = pred - I
+    l = w * (np.abs(r) if loss_kind else r * r)
+    dl = w * (np.sign(r) if loss_kind else 2.0 * r)
+    loss_p = l * iw + (w * lw if slw is not None else 0.0)
+    return pred, loss_p, sig * dl * iw, dl * iw * sig * model, w - l * iw
+
+
 def forward(stacks, theta, N, pix, K, delta, nbr=None, I_obs=None, w_pix=1.0, loss_kind=0, lambda_reg=0.0,
-            s_target=1.6):
+            s_target=1.6, slw=None):
     """(pred, loss, nbr): predictions of the listed pixels, the loss when I_obs
     is given (data term MSE, loss_kind 0, or L1, 1, plus the scale regulariser
-    of oracle.scale_reg), and the neighbour sets used."""
+    of oracle.scale_reg and the per-slice terms of slw), and the neighbour sets."""
     th = np.asarray(theta, np.float64)
     c = th[10 * int(N):11 * int(N)]
-    _, _, _, _, nbr, _, E, _ = _pairs(stacks, th, N, pix, K, nbr)
+    _, sl, _, R, nbr, _, E, _ = _pairs(stacks, th, N, pix, K, nbr)
     num = (c[nbr] * E).sum(1)
     den = E.sum(1) + float(delta)
-    pred = num / den
+    model = num / den
+    sw = np.asarray(slw, np.float64) if slw is not None else None
+    I = np.asarray(I_obs, np.float64) if I_obs is not None else np.zeros_like(model)
+    pred, loss_p, _, _, _ = _slice_terms(sw, R.shape[0], sl, model, I, w_pix, loss_kind)
     loss = 0.0
     if I_obs is not None:
-        r = pred - np.asarray(I_obs, np.float64)
-        loss = float((w_pix * (np.abs(r) if loss_kind else r * r)).sum())
+        loss = float(loss_p.sum())
         if lambda_reg:
             loss += _o.scale_reg(th, N, lambda_reg, s_target)[0]
     return pred, loss, nbr
@@ -153,7 +172,7 @@ def _drod_dr(r):
 
 
 def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, want_abs=False, loss_kind=0,
-                     lambda_reg=0.0, s_target=1.6):
+                     lambda_reg=0.0, s_target=1.6, slw=None, slw_grad=None):
     """(pred, loss, grad, nbr) in float64; grad has the parameter-vector layout
     (11 N Gaussian entries component-major, then (r, tau) per slice).  With
     want_abs, also A (same layout): the sum of the absolute values of the
@@ -168,17 +187,18 @@ def forward_backward(stacks, theta, N, pix, I_obs, w_pix, K, delta, nbr=None, wa
     x, sl, u, R, nbr, Pv, E, var = _pairs(stacks, th, N, pix, K, nbr)
     num = (c[nbr] * E).sum(1)
     den = E.sum(1) + float(delta)
-    pred = num / den
+    model = num / den
     I = np.asarray(I_obs, np.float64)
-    w = np.broadcast_to(np.asarray(w_pix, np.float64), pred.shape)
-    r = pred - I
-    if loss_kind:                                                 # L1, subgradient sign(0) = 0
-        loss = float((w * np.abs(r)).sum())
-        gbar = w * np.sign(r)
-    else:                                                         # MSE
-        loss = float((w * r * r).sum())
-        gbar = 2.0 * w * r                                        # dL/dI_hat
-    gam = gbar[:, None] * (c[nbr] - pred[:, None]) / den[:, None] * E  # dL/dE times E
+    sw = np.asarray(slw, np.float64) if slw is not None else None
+    pred, loss_p, gbar, gsig, gomg = _slice_terms(sw, R.shape[0], sl, model, I, w_pix, loss_kind)
+    loss = float(loss_p.sum())
+    if slw_grad is not None:
+        Ms = R.shape[0]
+        slw_grad[:] = 0.0
+        np.add.at(slw_grad[:Ms], sl, gsig)
+        np.add.at(slw_grad[Ms:], sl, gomg)
+    pred_model = model                                            # the ratio before sigma_i
+    gam = gbar[:, None] * (c[nbr] - pred_model[:, None]) / den[:, None] * E  # dL/dE times E
     dc_pair = gbar[:, None] * E / den[:, None]
     # per pair: dL/dmu = gam P v ; dL/dSigma_obs = 1/2 gam P v v^T P ; dL/dx = -gam P v
     g_mu = gam[:, :, None] * Pv

@@ -444,3 +444,51 @@ def test_l1_and_scale_regulariser_match_central_differences(oracle):
                  oracle.forward(st, tm, N, pix, I, w, loss_kind=1, lambda_reg=lam, s_target=s_t)[1]) / (2 * h)
     err = np.abs(g - fd)
     assert np.all(err <= 1e-6 * np.abs(g) + 1e-9 * np.abs(g).max()), (err.max(), np.argmax(err))
+
+
+@pytest.mark.parametrize("loss_kind", [0, 1])
+def test_slice_scale_and_aleatoric_weight(oracle, loss_kind):
+    """The per-slice outlier terms of Sec. 2.4 (log sigma_i, log omega_i): the
+    prediction is exactly sigma_i times the plain one; the weight's gradient
+    vanishes at omega_i = the slice's mean pixel loss (the minimiser of
+    l / omega + log omega); all gradients against central differences."""
+    case = inputs.random_case(16, 8, [(2, 5, 6), (1, 4, 5)], n_stacks=2, extent=3.0, motion_deg=10.0)
+    N, st = case["N"], case["stacks"]
+    M = inputs.n_slices_total(st)
+    th = case["theta"].astype(np.float64)
+    pix = np.arange(inputs.n_pixels_total(st))
+    I = case["I"].astype(np.float64)[pix] + 0.05
+    w = 1.0 / len(pix)
+    rng = np.random.default_rng(3)
+    slw = np.concatenate([rng.normal(0, 0.2, M), rng.normal(0, 0.5, M)])
+    p0, _ = oracle.forward(st, th, N, pix, I, w, loss_kind=loss_kind)
+    p1, _ = oracle.forward(st, th, N, pix, I, w, loss_kind=loss_kind, slw=slw)
+    sl = np.searchsorted(np.cumsum([0] + [s["H"] * s["W"] for s in st for _ in range(s["n_slices"])])[1:], pix,
+                         side="right")
+    assert np.allclose(p1, np.exp(slw[sl]) * p0, rtol=1e-14, atol=0)
+    # omega at the slice's mean loss: zero derivative
+    r = np.exp(slw[sl]) * p0 - I
+    l = w * (np.abs(r) if loss_kind else r * r)
+    opt = slw.copy()
+    opt[M:] = np.log(np.bincount(sl, l, M) / np.bincount(sl, np.full(len(pix), w), M))
+    gs = np.zeros(2 * M)
+    oracle.forward_backward(st, th, N, pix, I, w, loss_kind=loss_kind, slw=opt, slw_grad=gs)
+    assert np.abs(gs[M:]).max() <= 1e-12
+    # central differences in theta and in the slice terms
+    gs = np.zeros(2 * M)
+    _, L0, g, _ = oracle.forward_backward(st, th, N, pix, I, w, loss_kind=loss_kind, slw=slw, slw_grad=gs)
+    full = np.concatenate([g, gs])
+    x0 = np.concatenate([th, slw])
+    n = th.size
+
+    def L(x):
+        return oracle.forward(st, x[:n], N, pix, I, w, loss_kind=loss_kind, slw=x[n:])[1]
+    fd = np.zeros_like(full)
+    for e in range(x0.size):
+        h = 1e-6 * max(1.0, abs(x0[e]))
+        xp, xm = x0.copy(), x0.copy()
+        xp[e] += h
+        xm[e] -= h
+        fd[e] = (L(xp) - L(xm)) / (2 * h)
+    err = np.abs(full - fd)
+    assert np.all(err <= 1e-6 * np.abs(full) + 1e-9 * np.abs(full).max()), (err.max(), np.argmax(err))

@@ -149,3 +149,39 @@ def test_l1_and_scale_regulariser_gradient(topk):
                  topk.forward(st, tm, N, pix, K, delta, nbr=nbr, I_obs=I, w_pix=w, **kw)[1]) / (2 * h)
     err = np.abs(g - fd)
     assert np.all(err <= 1e-6 * np.abs(g) + 1e-9 * np.abs(g).max()), (err.max(), np.argmax(err))
+
+
+def test_slice_terms_gradient(topk):
+    """The per-slice outlier terms (log sigma_i, log omega_i) on the top-K
+    model: prediction = sigma_i times the ratio, gradients against central
+    differences (neighbour sets fixed)."""
+    case = inputs.random_case(17, 10, [(2, 5, 5)], n_stacks=2, extent=3.0, motion_deg=10.0)
+    N, st = case["N"], case["stacks"]
+    M = inputs.n_slices_total(st)
+    th = case["theta"].astype(np.float64)
+    pix = np.arange(inputs.n_pixels_total(st))
+    I = case["I"].astype(np.float64)[pix] + 0.05
+    w, K, delta = 1.0 / len(pix), 5, 1e-3
+    rng = np.random.default_rng(4)
+    slw = np.concatenate([rng.normal(0, 0.2, M), rng.normal(0, 0.5, M)])
+    p0, _, nbr = topk.forward(st, th, N, pix, K, delta)
+    p1, _, _ = topk.forward(st, th, N, pix, K, delta, nbr=nbr, slw=slw)
+    sl = pix // (st[0]["H"] * st[0]["W"])
+    assert np.allclose(p1, np.exp(slw[sl]) * p0, rtol=1e-14, atol=0)
+    gs = np.zeros(2 * M)
+    _, _, g, _ = topk.forward_backward(st, th, N, pix, I, w, K, delta, nbr=nbr, loss_kind=1, slw=slw, slw_grad=gs)
+    full = np.concatenate([g, gs])
+    x0 = np.concatenate([th, slw])
+    n = th.size
+
+    def L(x):
+        return topk.forward(st, x[:n], N, pix, K, delta, nbr=nbr, I_obs=I, w_pix=w, loss_kind=1, slw=x[n:])[1]
+    fd = np.zeros_like(full)
+    for e in range(x0.size):
+        h = 1e-6 * max(1.0, abs(x0[e]))
+        xp, xm = x0.copy(), x0.copy()
+        xp[e] += h
+        xm[e] -= h
+        fd[e] = (L(xp) - L(xm)) / (2 * h)
+    err = np.abs(full - fd)
+    assert np.all(err <= 1e-6 * np.abs(full) + 1e-9 * np.abs(full).max()), (err.max(), np.argmax(err))
