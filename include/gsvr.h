@@ -279,6 +279,25 @@ gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
  * s_target <= 0 or not finite.  Synchronises the stream. */
 gsvr_status gsvr_set_objective(gsvr_ctx *ctx, int32_t loss_kind, float lambda_reg, float s_target);
 
+/* Per-slice outlier terms (Sec. 2.4): a learnable intensity scale sigma_i
+ * (Eq. 5's factor: every prediction of slice i is sigma_i times the model) and
+ * an aleatoric weight omega_i, read as the pixel loss
+ * w_p (l(I_hat - I) / omega_i + log omega_i) with l the data term of
+ * gsvr_set_objective.  Both are held as logarithms (log sigma_i, log omega_i),
+ * 2 M floats, zero (sigma = omega = 1) when switched on.  The forward also
+ * writes their gradients (they need no backward pass); gsvr_adam_step steps
+ * them with lr_log_sigma / lr_log_omega on the same schedule as the other
+ * groups; a frozen slice (gsvr_set_frozen) keeps its sigma (the intensity
+ * gauge: sigma_i and the amplitudes trade off).  enable = 0 switches them
+ * off (predictions and loss as without them).  gsvr_set_stacks switches them
+ * off.  Both forward models.  GSVR_ERR_STATE before gsvr_set_stacks;
+ * GSVR_ERR_INVALID_ARG for negative or non-finite rates.  Synchronises. */
+gsvr_status gsvr_set_slice_weights(gsvr_ctx *ctx, int32_t enable, float lr_log_sigma, float lr_log_omega);
+/* Device views of the per-slice terms (log sigma_i for i < M, then log
+ * omega_i) and of their gradients; the caller may write the parameters
+ * between calls.  GSVR_ERR_STATE when they are off. */
+gsvr_status gsvr_slice_weight_views(gsvr_ctx *ctx, float **params, float **grads, int32_t *M);
+
 /* Normalised top-K forward model (Sec. 2.2, Eq. 2; Eq. 5 with sigma_i = 1;
  * Sec. 2.5 "Sparse Computation (Top-K)").  With K >= 1 every later forward
  * predicts a sampled pixel as

@@ -100,6 +100,11 @@ struct gsvr_ctx {
     // objective (gsvr_set_objective): data term and scale regulariser
     int loss_kind = 0;
     float lambda_reg = 0.f, s_target = 1.6f;
+    // per-slice outlier terms (gsvr_set_slice_weights): log sigma_i, log omega_i
+    bool slw_on = false;
+    float lr_slw_sig = 1e-3f, lr_slw_omg = 1e-2f;
+    DBuf<float> d_slw, d_slw_grad, d_slw_m, d_slw_v;
+    DBuf<double> d_slw_gacc;
     // normalised top-K form (gsvr_set_topk); K = 0: the plain sum
     int topk_K = 0, topk_refresh = 1;
     float topk_delta = 1e-8f, topk_per_cell = 16.f;
@@ -302,6 +307,9 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.bwd_bps = ctx->bwd_bps;
     e.tile_px = ctx->tile_w * ctx->tile_h;
     e.l1 = ctx->loss_kind;
+    e.slw = ctx->slw_on ? ctx->d_slw.p : nullptr;
+    e.slw_gacc = ctx->d_slw_gacc.p;
+    e.M = ctx->M;
     e.tile_w = ctx->tile_w;
     e.tile_h = ctx->tile_h;
     e.n_tiles = ctx->n_tiles;
@@ -535,6 +543,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (n_stacks <= 0 || !stacks) return fail(ctx, GSVR_ERR_INVALID_ARG, "need at least one stack");
     DeviceGuard g(ctx->device);
+    ctx->slw_on = false;  // per-slice terms are sized by the slices: set them again
     const int tw = ctx->tile_w, th = ctx->tile_h;
     std::vector<SliceDev> sl;
     std::vector<SliceStatic> ss;
@@ -1037,6 +1046,8 @@ TopkArgs topk_args(gsvr_ctx *ctx) {
     a.delta = ctx->topk_delta;
     a.cap_px = topk_cap_px(ctx);
     a.l1 = ctx->loss_kind;
+    a.slw = ctx->slw_on ? ctx->d_slw.p : nullptr;
+    a.slw_gacc = ctx->d_slw_gacc.p;
     a.status = ctx->d_status.p;
     return a;
 }
@@ -1061,6 +1072,7 @@ gsvr_status topk_forward(gsvr_ctx *ctx) {
     stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
     launch_topk_forward(topk_args(ctx), topk_cap_px(ctx), ctx->d_loss.p, st);
     if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
+    if (ctx->slw_on) launch_slw_grad(ctx->d_slw_gacc.p, 2 * ctx->M, ctx->d_slw_grad.p, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
     CK(cudaGetLastError());
     ++ctx->topk_calls;
@@ -1096,6 +1108,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     const bool grow = !ctx->cfg.fixed_capacity;
     stage_begin(ctx, GSVR_STAGE_PREP);
     CK(cudaMemsetAsync(&cnt->pairs, 0, sizeof(unsigned long long), st));
+    if (ctx->slw_on) CK(cudaMemsetAsync(ctx->d_slw_gacc.p, 0, sizeof(double) * 2 * (size_t)M, st));
     launch_gauss_prep(ctx->d_theta.p, N, ctx->d_gpre.p, ctx->d_status.p, st);
     launch_pose_prep(ctx->d_theta.p + 11LL * N, ctx->d_static.p, ctx->d_slices.p, M, ctx->d_status.p, st);
     stage_end(ctx, GSVR_STAGE_PREP);
@@ -1214,6 +1227,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_subj_tile_first.p, ctx->n_subj, ctx->d_subj_loss.p,
                        ctx->d_loss.p, ctx->d_status.p, st);
     if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
+    if (ctx->slw_on) launch_slw_grad(ctx->d_slw_gacc.p, 2 * M, ctx->d_slw_grad.p, st);
     CK(cudaGetLastError());
     ctx->fwd_valid = true;
     return GSVR_OK;
@@ -1277,6 +1291,10 @@ gsvr_status adam_launch(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step, c
     launch_adam(ctx->d_theta.p, ctx->d_grad.p, ctx->d_m.p, ctx->d_v.p, (int)ctx->N, ctx->M, lr, b1, b2, eps,
                 cfg->step_every, gamma, step, d_step, ctx->d_counters.p->adam_scal,
                 ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
+    if (ctx->slw_on)
+        launch_adam_slw(ctx->d_slw.p, ctx->d_slw_grad.p, ctx->d_slw_m.p, ctx->d_slw_v.p, ctx->M, ctx->lr_slw_sig,
+                        ctx->lr_slw_omg, b1, b2, eps, cfg->step_every, gamma, step, d_step,
+                        ctx->d_counters.p->adam_scal, ctx->any_frozen ? ctx->d_frozen.p : nullptr, ctx->stream);
     stage_end(ctx, GSVR_STAGE_ADAM);
     CK(cudaGetLastError());
     ctx->fwd_valid = false;
@@ -1565,6 +1583,43 @@ gsvr_status gsvr_get_topk_neighbors(gsvr_ctx *ctx, int32_t *pix, int32_t *nbr, i
     CK(cudaMemcpy(pix, ctx->d_sampled.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(nbr, ctx->d_topk_nbr.p, sizeof(int) * (size_t)ns * ctx->topk_K, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(cnt, ctx->d_topk_ncnt.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_set_slice_weights(gsvr_ctx *ctx, int32_t enable, float lr_log_sigma, float lr_log_omega) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!(lr_log_sigma >= 0.f) || !(lr_log_omega >= 0.f) || !std::isfinite(lr_log_sigma) ||
+        !std::isfinite(lr_log_omega))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "slice-weight learning rates must be >= 0 and finite");
+    if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks before gsvr_set_slice_weights");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_slice_weights during graph capture");
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    ctx->fwd_valid = false;
+    ctx->slw_on = enable != 0;
+    ctx->lr_slw_sig = lr_log_sigma;
+    ctx->lr_slw_omg = lr_log_omega;
+    if (!ctx->slw_on) return GSVR_OK;
+    const size_t n = 2 * (size_t)ctx->M;
+    CK(ctx->d_slw.ensure(n));
+    CK(ctx->d_slw_grad.ensure(n));
+    CK(ctx->d_slw_m.ensure(n));
+    CK(ctx->d_slw_v.ensure(n));
+    CK(ctx->d_slw_gacc.ensure(n));
+    for (DBuf<float> *b : {&ctx->d_slw, &ctx->d_slw_grad, &ctx->d_slw_m, &ctx->d_slw_v})
+        CK(cudaMemsetAsync(b->p, 0, sizeof(float) * n, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_slw_gacc.p, 0, sizeof(double) * n, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_slice_weight_views(gsvr_ctx *ctx, float **params, float **grads, int32_t *M) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->slw_on) return fail(ctx, GSVR_ERR_STATE, "slice weights are off");
+    if (params) *params = ctx->d_slw.p;
+    if (grads) *grads = ctx->d_slw_grad.p;
+    if (M) *M = ctx->M;
     return GSVR_OK;
 }
 

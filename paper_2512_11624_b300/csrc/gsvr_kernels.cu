@@ -844,9 +844,31 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     }
 }
 
+// Per-slice outlier terms of a pixel of slice i (Sec. 2.4): prediction
+// sigma_i * model, loss w (l(r) / omega_i + log omega_i) with l the data term;
+// returns dL/dmodel and the pixel's derivatives in log sigma_i and log omega_i
+// (slw null: sigma = omega = 1 without the log term).
+struct SlwTerms {
+    float pred, dLdm, gsig, gomg;
+    double loss;
+};
+__device__ __forceinline__ SlwTerms slw_terms(const float *slw, int M, int i, int l1, float w, float model, float I) {
+    const float sig = slw ? expf(slw[i]) : 1.f, lw = slw ? slw[M + i] : 0.f, iw = slw ? expf(-lw) : 1.f;
+    SlwTerms t;
+    t.pred = sig * model;
+    const float r = t.pred - I;
+    const float l = l1 ? w * fabsf(r) : w * r * r;
+    const float dl = l1 ? w * (float)((r > 0.f) - (r < 0.f)) : 2.f * w * r;
+    t.loss = (double)l * (double)iw + (slw ? (double)w * (double)lw : 0.0);
+    t.dLdm = sig * dl * iw;
+    t.gsig = dl * iw * t.pred;
+    t.gomg = w - l * iw;
+    return t;
+}
+
 // Per tile: add the items' partial sums in order, then residual, dL/dI_hat and loss.
 __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
-    __shared__ double red[kMaxTilePx / 32];
+    __shared__ double red[kMaxTilePx / 32], red_s[kMaxTilePx / 32], red_o[kMaxTilePx / 32];
     const int t = blockIdx.x;
     const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
     if (ps >= pe) {
@@ -854,7 +876,7 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         return;
     }
     const int s = ps + threadIdx.x;
-    double l = 0.0;
+    double l = 0.0, gs = 0.0, go = 0.0;
     if (s < pe) {
         const SliceDev &S = a.slices[a.tile_slice[t]];
         const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
@@ -867,24 +889,38 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         for (int i = a.item_first[t]; i < i1; ++i) acc += a.part[(size_t)i * a.tile_px + px];
         const int ns = a.subj_cnt ? a.subj_cnt[S.subject] : *a.n_sampled;
         const float wp = 1.0f / (float)max(ns, 1);
-        const float r = acc - a.I_obs[p];
-        a.pred[p] = acc;
-        if (a.l1) {  // L1: w |r|, subgradient w sign(r) (sign(0) = 0)
-            a.rbar[p] = wp * (float)((r > 0.f) - (r < 0.f));
-            l = (double)(wp * fabsf(r));
-        } else {
-            a.rbar[p] = 2.0f * wp * r;
-            l = (double)(wp * r * r);
-        }
+        // data term (MSE or L1, subgradient sign(0) = 0) and the per-slice terms
+        const SlwTerms st = slw_terms(a.slw, a.M, a.tile_slice[t], a.l1, wp, acc, a.I_obs[p]);
+        a.pred[p] = st.pred;
+        a.rbar[p] = st.dLdm;
+        l = st.loss;
+        gs = (double)st.gsig;
+        go = (double)st.gomg;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_down_sync(0xffffffffu, l, o);
+        gs += __shfl_down_sync(0xffffffffu, gs, o);
+        go += __shfl_down_sync(0xffffffffu, go, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = l;
+        red_s[threadIdx.x >> 5] = gs;
+        red_o[threadIdx.x >> 5] = go;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        double sum = 0.0, ss = 0.0, so = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sum += red[w];
+            ss += red_s[w];
+            so += red_o[w];
+        }
         a.tile_loss[t] = sum;
+        if (a.slw) {  // one tile = one slice
+            atomicAdd(&a.slw_gacc[a.tile_slice[t]], ss);
+            atomicAdd(&a.slw_gacc[a.M + a.tile_slice[t]], so);
+        }
         const unsigned long long np =
             (unsigned long long)(pe - ps) * (unsigned long long)(a.tile_rec_end[t] - a.tile_rec_start[t]);
         atomicAdd(&a.counters->pairs, np);
@@ -1394,12 +1430,35 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
 
 __global__ void k_advance_step(unsigned long long *d_step) { *d_step += 1ull; }
 
+__global__ void k_adam_slw(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                           float *__restrict__ v, int M, float lr_sig, float lr_omg, float b1, float b2, float eps,
+                           float ibc1_h, float ibc2_h, float scale_h, const float *__restrict__ d_scal,
+                           const uint8_t *__restrict__ frozen) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * M) return;
+    if (e < M && frozen && frozen[e]) return;  // the reference slice fixes the intensity scale
+    const float s_ibc1 = d_scal ? d_scal[0] : ibc1_h, s_ibc2 = d_scal ? d_scal[1] : ibc2_h;
+    const float s_scale = d_scal ? d_scal[2] : scale_h;
+    const float lr = e < M ? lr_sig : lr_omg;
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= (lr * s_scale) * (mi * s_ibc1) / (sqrtf(vi * s_ibc2) + eps);
+}
+__global__ void k_slw_grad(const double *__restrict__ gacc, int n, float *__restrict__ grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) grad[e] = (float)gacc[e];
+}
+
 // ============================================ normalised top-K forward model
 // Eq. 2 with every covariance replaced by its observed covariance (Eq. 4) and
 // the ratio of Eq. 5 (sigma_i = 1): I_hat = sum_S c_j E_j / (sum_S E_j + delta),
 // E_j = exp(-1/2 v^T Sigma_obs^-1 v), S = the K means nearest the pixel's world
 // position (Sec. 2.5, Top-K), ties to the smaller index.  The neighbours come
 // from an exact shell search of a uniform grid over the means.
+
 
 // order-preserving float <-> int for atomic min / max
 __device__ __forceinline__ int f2o(float f) {
@@ -1696,15 +1755,14 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
         const float D = (float)(den + (double)a.delta);
         const float Ih = (float)(num / (den + (double)a.delta));
         const float w = 1.0f / (float)max(ns, 1);
-        const float r = Ih - a.I_obs[p];
-        a.pred[p] = Ih;
-        a.pstat[s] = make_float2(Ih, D);
-        if (a.l1) {
-            a.rbar[p] = w * (float)((r > 0.f) - (r < 0.f));
-            l = (double)w * fabs((double)r);
-        } else {
-            a.rbar[p] = 2.f * w * r;
-            l = (double)w * (double)r * (double)r;
+        const SlwTerms st = slw_terms(a.slw, a.M, q.i, a.l1, w, Ih, a.I_obs[p]);
+        a.pred[p] = st.pred;
+        a.rbar[p] = st.dLdm;
+        a.pstat[s] = make_float2(Ih, D);  // the ratio before sigma_i: the backward's I_hat
+        l = st.loss;
+        if (a.slw) {
+            atomicAdd(&a.slw_gacc[q.i], (double)st.gsig);
+            atomicAdd(&a.slw_gacc[a.M + q.i], (double)st.gomg);
         }
     }
 #pragma unroll
@@ -2103,6 +2161,25 @@ void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int
     }
     k_adam<<<cdiv(n, 256), 256, 0, st>>>(theta, grad, m, v, N, M, lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], b1, b2,
                                          eps, h[0], h[1], h[2], d_step ? d_scal : nullptr, frozen);
+    counted();
+}
+void launch_adam_slw(float *p, const float *g, float *m, float *v, int M, float lr_sig, float lr_omg, float b1,
+                     float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
+                     const float *d_scal, const uint8_t *frozen, cudaStream_t st) {
+    if (M <= 0) return;
+    float h[3] = {1.f, 1.f, 1.f};
+    if (!d_step) {
+        h[0] = (float)(1.0 / (1.0 - std::pow((double)b1, (double)t_host)));
+        h[1] = (float)(1.0 / (1.0 - std::pow((double)b2, (double)t_host)));
+        h[2] = step_every > 0 ? (float)std::pow((double)gamma, (double)((t_host - 1) / step_every)) : 1.0f;
+    }
+    k_adam_slw<<<cdiv(2LL * M, 256), 256, 0, st>>>(p, g, m, v, M, lr_sig, lr_omg, b1, b2, eps, h[0], h[1], h[2],
+                                                   d_step ? d_scal : nullptr, frozen);
+    counted();
+}
+void launch_slw_grad(const double *gacc, int n, float *grad, cudaStream_t st) {
+    if (n <= 0) return;
+    k_slw_grad<<<cdiv(n, 256), 256, 0, st>>>(gacc, n, grad);
     counted();
 }
 void launch_advance_step(unsigned long long *d_step, cudaStream_t st) {

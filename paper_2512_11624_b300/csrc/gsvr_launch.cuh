@@ -74,6 +74,9 @@ struct EvalArgs {
     int fwd_bps, bwd_bps;             // persistent CTAs per SM (0: as many as fit)
     int tile_px;                      // tile_w * tile_h
     int l1;                           // data term: 0 MSE, 1 L1 (the paper's)
+    const float *slw;                 // per-slice log sigma_i (M) then log omega_i (M), or null
+    double *slw_gacc;                 // their gradients (2 M, accumulated by the forward)
+    int M;
     int tile_w, tile_h;
     int n_tiles;
     unsigned *status;
@@ -147,6 +150,15 @@ void launch_adam(float *theta, const float *grad, float *m, float *v, int N, int
                  float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
                  float *d_scal, const uint8_t *frozen, cudaStream_t st);
 void launch_advance_step(unsigned long long *d_step, cudaStream_t st);
+// Adam on the per-slice terms (2 M: log sigma_i with lr_sig, log omega_i with
+// lr_omg), same schedule and step as launch_adam (call it after launch_adam,
+// whose device scalars it reads when d_step is given); frozen slices keep
+// their sigma (the intensity gauge), not their omega.
+void launch_adam_slw(float *p, const float *g, float *m, float *v, int M, float lr_sig, float lr_omg, float b1,
+                     float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
+                     const float *d_scal, const uint8_t *frozen, cudaStream_t st);
+// float copy of the forward's float64 per-slice gradient sums
+void launch_slw_grad(const double *gacc, int n, float *grad, cudaStream_t st);
 
 // Sampler: for subject k, out_first[k+1] - out_first[k] of its mask_count[k]
 // masked pixels (tile-order positions mask_tpos[mask_first[k] + x]); the round
@@ -199,6 +211,8 @@ struct TopkArgs {
     float delta;
     int cap_px;
     int l1;                  // data term: 0 MSE, 1 L1
+    const float *slw;        // per-slice log sigma_i, log omega_i (2 M) or null
+    double *slw_gacc;        // their gradients (2 M)
     unsigned *status;
 };
 // Grid build: bounding box, cell size, cell keys; the caller sorts the keys

@@ -32,7 +32,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
-           "gsvr_set_objective"]
+           "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -126,6 +126,8 @@ def _load():
         "gsvr_set_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
         "gsvr_set_topk": ([vp, C.c_int32, C.c_float, C.c_int32], C.c_int),
         "gsvr_set_objective": ([vp, C.c_int32, C.c_float, C.c_float], C.c_int),
+        "gsvr_set_slice_weights": ([vp, C.c_int32, C.c_float, C.c_float], C.c_int),
+        "gsvr_slice_weight_views": ([vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32)], C.c_int),
         "gsvr_get_topk_neighbors": ([vp, vp, vp, vp, i64, C.POINTER(i64)], C.c_int),
         "gsvr_reserve": ([vp, i64, i64], C.c_int),
         "gsvr_get_tiling": ([vp, C.POINTER(Tiling)], C.c_int),
@@ -330,6 +332,18 @@ def gsvr_set_topk(ctx, K, delta=1e-8, refresh_every=1):
 def gsvr_set_objective(ctx, loss_kind=0, lambda_reg=0.0, s_target=1.6):
     """Data term (0 MSE, 1 L1) and scale regulariser of the loss."""
     return _check(ctx, lib.gsvr_set_objective(ctx, int(loss_kind), float(lambda_reg), float(s_target)))
+
+
+def gsvr_set_slice_weights(ctx, enable=1, lr_log_sigma=1e-3, lr_log_omega=1e-2):
+    """Per-slice intensity scale and aleatoric weight (log sigma_i, log omega_i)."""
+    return _check(ctx, lib.gsvr_set_slice_weights(ctx, int(enable), float(lr_log_sigma), float(lr_log_omega)))
+
+
+def gsvr_slice_weight_views(ctx):
+    """(params, grads): zero-copy float32 CUDA tensors of 2 M entries each."""
+    p, g, m = C.c_void_p(), C.c_void_p(), C.c_int32()
+    _check(ctx, lib.gsvr_slice_weight_views(ctx, C.byref(p), C.byref(g), C.byref(m)))
+    return device_view(p.value, 2 * m.value), device_view(g.value, 2 * m.value)
 
 
 def gsvr_get_topk_neighbors(ctx, K):
