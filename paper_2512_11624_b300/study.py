@@ -401,6 +401,8 @@ def run_topk(args):
         if tk:
             gsvr.gsvr_set_objective(rec.ctx.ctx, 1 if args.loss == "l1" else 0, args.lambda_reg / args.n_sample,
                                     args.s_target)
+            if args.slice_weights:
+                gsvr.gsvr_set_slice_weights(rec.ctx.ctx, 1)
         probe = PSNRProbe(case["phantom"], c["N"], topk=(tk[0], tk[1]) if tk else None)
         if tk:
             gsvr.gsvr_timing_reset(rec.ctx.ctx)
@@ -414,6 +416,7 @@ def run_topk(args):
                                                               "grad", "adam")}
         row = {"model": name, "K": tk[0] if tk else None, "delta": tk[1] if tk else None,
                "loss": args.loss if tk else "mse", "lambda_reg": args.lambda_reg if tk else 0.0,
+               "slice_weights": bool(args.slice_weights and tk),
                "s_target": args.s_target if tk else None,
                "refresh_every": tk[2] if tk else None, "iters": iters, "ms_per_iter": 1e3 * hist[-1][1] / iters,
                "stage_ms_per_iter": stage, "psnr": [(h[0], h[3]) for h in hist],
@@ -488,6 +491,7 @@ def main():
     tk.add_argument("--loss", choices=["mse", "l1"], default="mse")
     tk.add_argument("--lambda-reg", type=float, default=0.0)
     tk.add_argument("--s-target", type=float, default=0.8)
+    tk.add_argument("--slice-weights", action="store_true")
     tk.add_argument("--out", default="")
     ts = sub.add_parser("topk-step")
     ts.add_argument("--k", type=int, default=50)
