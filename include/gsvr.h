@@ -279,6 +279,26 @@ gsvr_status gsvr_set_tiling(gsvr_ctx *ctx, const gsvr_tiling *t);
  * s_target <= 0 or not finite.  Synchronises the stream. */
 gsvr_status gsvr_set_objective(gsvr_ctx *ctx, int32_t loss_kind, float lambda_reg, float s_target);
 
+/* Content-adaptive initialisation of the means (Sec. 2.5, "Content-Adaptive
+ * Initialization"): n means drawn from P_init proportional to
+ * (1 - lambda_init) |grad I_i(u)| + lambda_init over the masked pixels of the
+ * observations, each placed at its pixel's world position T_i(u) under
+ * `pose` (host, M x 6 (r, tau) per slice; NULL = no motion), jittered
+ * uniformly within the pixel's voxel (dx x dy x slice thickness).
+ * Deterministic: |grad I| by central differences (one-sided at the border) in
+ * float32 with every operation rounded alone, integer weights
+ * floor(1024 ((1 - lambda) |grad I| + lambda)), an int64 cumulative sum T,
+ * draw k = the first pixel whose cumulative weight exceeds
+ * floor(SplitMix64(seed, k) T / 2^64), jitter uniforms = 24-bit fractions of
+ * SplitMix64(seed, 2^40 + 3 k + a).
+ * mu: device [3][n] (x row, y row, z row, as the parameter vector's means);
+ * pix: device [n] (the drawn global pixels) or NULL; *total_weight (host, may be
+ * NULL) = T.  Synchronises.  GSVR_ERR_STATE before stacks and observations;
+ * GSVR_ERR_INVALID_ARG for n < 0 or > 2^30, lambda_init outside [0, 1], a
+ * non-finite pose, or T = 0 (no masked pixel carries weight). */
+gsvr_status gsvr_init_means(gsvr_ctx *ctx, const float *pose, int64_t n, float lambda_init, uint64_t seed, float *mu,
+                            int32_t *pix, int64_t *total_weight);
+
 /* Per-slice outlier terms (Sec. 2.4): a learnable intensity scale sigma_i
  * (Eq. 5's factor: every prediction of slice i is sigma_i times the model) and
  * an aleatoric weight omega_i, read as the pixel loss

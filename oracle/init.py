@@ -70,38 +70,40 @@ def weights(stacks, I, mask, lambda_init):
     return np.where(np.asarray(mask) != 0, q, 0)
 
 
-def draw_pixels(W, n, seed):
-    """Pixel of each of n draws: the first index whose cumulative weight
-    exceeds floor(x_k T / 2^64)."""
+def draw_pixels(W, ks, seed):
+    """Pixel of draws ks: the first index whose cumulative weight exceeds
+    floor(x_k T / 2^64)."""
     C = np.cumsum(np.asarray(W, np.int64))
     T = int(C[-1])
     if T <= 0:
         raise ValueError("no weight to draw from")
-    t = np.array([(_o.splitmix64(seed, k) * T) >> 64 for k in range(int(n))], dtype=object)
+    t = np.array([(_o.splitmix64(seed, int(k)) * T) >> 64 for k in ks], dtype=object)
     return np.searchsorted(C, t.astype(np.int64), side="right")
 
 
-def jitter(n, seed):
-    """(n, 3) uniforms in [-1/2, 1/2): 24-bit fractions of SplitMix64 outputs
-    at counters 2^40 + 3 k + a."""
-    out = np.zeros((int(n), 3))
-    for k in range(int(n)):
+def jitter(ks, seed):
+    """(len(ks), 3) uniforms in [-1/2, 1/2): 24-bit fractions of SplitMix64
+    outputs at counters 2^40 + 3 k + a."""
+    out = np.zeros((len(ks), 3))
+    for n, k in enumerate(ks):
         for a in range(3):
-            x = _o.splitmix64(seed, JITTER_CTR + 3 * k + a)
-            out[k, a] = (x >> 40) * 2.0 ** -24 - 0.5
+            x = _o.splitmix64(seed, JITTER_CTR + 3 * int(k) + a)
+            out[n, a] = (x >> 40) * 2.0 ** -24 - 0.5
     return out
 
 
-def init_means(stacks, I, mask, theta_pose, n, lambda_init, seed):
-    """(mu (n, 3) float64, pixel index (n)) of the content-adaptive draw, with
-    the slice frames of the given poses (M x 6)."""
+def init_means(stacks, I, mask, theta_pose, n, lambda_init, seed, ks=None):
+    """(mu (len, 3) float64, pixel index (len)) of draws ks (default 0 .. n-1)
+    of the content-adaptive initialisation, with the slice frames of the given
+    poses (M x 6)."""
+    ks = np.arange(int(n)) if ks is None else np.asarray(ks)
     W = weights(stacks, I, mask, lambda_init)
-    pix = draw_pixels(W, n, seed)
+    pix = draw_pixels(W, ks, seed)
     R, t = _o.slice_frames(stacks, np.asarray(theta_pose, np.float64))
     sl = _slices(stacks)
     firsts = np.array([b for (_, _, b) in sl], np.int64)
-    j = jitter(n, seed)
-    mu = np.zeros((int(n), 3))
+    j = jitter(ks, seed)
+    mu = np.zeros((len(ks), 3))
     for k, p in enumerate(pix):
         i = int(np.searchsorted(firsts, p, side="right") - 1)
         s, _, b = sl[i]

@@ -105,6 +105,9 @@ struct gsvr_ctx {
     float lr_slw_sig = 1e-3f, lr_slw_omg = 1e-2f;
     DBuf<float> d_slw, d_slw_grad, d_slw_m, d_slw_v;
     DBuf<double> d_slw_gacc;
+    // content-adaptive initialisation scratch (gsvr_init_means)
+    DBuf<int64_t> d_init_w, d_init_c, d_init_s;
+    DBuf<float> d_init_pose, d_init_thick;
     // normalised top-K form (gsvr_set_topk); K = 0: the plain sum
     int topk_K = 0, topk_refresh = 1;
     float topk_delta = 1e-8f, topk_per_cell = 16.f;
@@ -1583,6 +1586,48 @@ gsvr_status gsvr_get_topk_neighbors(gsvr_ctx *ctx, int32_t *pix, int32_t *nbr, i
     CK(cudaMemcpy(pix, ctx->d_sampled.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(nbr, ctx->d_topk_nbr.p, sizeof(int) * (size_t)ns * ctx->topk_K, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(cnt, ctx->d_topk_ncnt.p, sizeof(int) * (size_t)ns, cudaMemcpyDeviceToHost));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_init_means(gsvr_ctx *ctx, const float *pose, int64_t n, float lambda_init, uint64_t seed,
+                            float *mu, int32_t *pix, int64_t *total_weight) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_stacks || !ctx->have_obs)
+        return fail(ctx, GSVR_ERR_STATE, "set stacks and observations before gsvr_init_means");
+    if (n < 0 || n > (int64_t)1 << 30 || (n > 0 && !mu) || !(lambda_init >= 0.f && lambda_init <= 1.f))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "need 0 <= n <= 2^30, mu for n > 0, 0 <= lambda_init <= 1");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_init_means during graph capture");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int M = ctx->M;
+    const int64_t P = ctx->P;
+    std::vector<float> hp((size_t)6 * M, 0.f), th;
+    if (pose) {
+        if (!finite_all(pose, 6 * M)) return fail(ctx, GSVR_ERR_INVALID_ARG, "non-finite pose");
+        std::copy(pose, pose + 6 * M, hp.begin());
+    }
+    for (const gsvr_stack_desc &d : ctx->h_stack_desc)
+        for (int k = 0; k < d.n_slices; ++k) th.push_back(d.thickness);
+    CK(ctx->d_init_pose.ensure((size_t)6 * M));
+    CK(ctx->d_init_thick.ensure((size_t)M));
+    CK(ctx->d_init_w.ensure((size_t)P));
+    CK(ctx->d_init_c.ensure((size_t)P));
+    CK(ctx->d_init_s.ensure((size_t)(P + 4095) / 4096 + 1));
+    CK(cudaMemcpyAsync(ctx->d_init_pose.p, hp.data(), sizeof(float) * hp.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_init_thick.p, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, st));
+    // slice frames of these poses (the next forward rebuilds them from the parameters)
+    launch_pose_prep(ctx->d_init_pose.p, ctx->d_static.p, ctx->d_slices.p, M, ctx->d_status.p, st);
+    launch_init_weights(ctx->d_I.p, ctx->d_mask.p, ctx->d_slices.p, M, P, lambda_init, ctx->d_init_w.p,
+                        ctx->d_init_c.p, ctx->d_init_s.p, st);
+    int64_t T = 0;
+    CK(cudaMemcpyAsync(&T, ctx->d_init_c.p + (P - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->fwd_valid = false;
+    if (total_weight) *total_weight = T;
+    if (T <= 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "no masked pixel carries weight (flat slices with lambda_init 0)");
+    launch_init_draw(ctx->d_init_c.p, P, seed, n, ctx->d_slices.p, M, ctx->d_init_thick.p, mu, pix, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
     return GSVR_OK;
 }
 

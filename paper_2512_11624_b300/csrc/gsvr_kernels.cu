@@ -1430,6 +1430,106 @@ __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, floa
 
 __global__ void k_advance_step(unsigned long long *d_step) { *d_step += 1ull; }
 
+// ------------------------------------ content-adaptive initialisation (Sec. 2.5)
+__device__ __forceinline__ int slice_of_pixel(const SliceDev *__restrict__ sl, int M, int64_t p) {
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)sl[mid].pix_base <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__global__ void k_init_weights(const float *__restrict__ I, const uint8_t *__restrict__ mask,
+                               const SliceDev *__restrict__ sl, int M, int64_t P, float lam, int64_t *__restrict__ W) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    if (!mask[p]) {
+        W[p] = 0;
+        return;
+    }
+    const SliceDev &S = sl[slice_of_pixel(sl, M, p)];
+    const int loc = (int)(p - S.pix_base), row = loc / S.W, col = loc - row * S.W;
+    const int cm = max(col - 1, 0), cp = min(col + 1, S.W - 1), rm = max(row - 1, 0), rp = min(row + 1, S.H - 1);
+    const float *img = I + S.pix_base;
+    // central differences, one-sided at the border; no fused multiply-add anywhere
+    float gx = __fdiv_rn(__fsub_rn(img[row * S.W + cp], img[row * S.W + cm]), __fmul_rn(S.dx, (float)(cp - cm)));
+    float gy = __fdiv_rn(__fsub_rn(img[rp * S.W + col], img[rm * S.W + col]), __fmul_rn(S.dy, (float)(rp - rm)));
+    if (!isfinite(gx)) gx = 0.f;
+    if (!isfinite(gy)) gy = 0.f;
+    const float g = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+    const float w = __fadd_rn(__fmul_rn(__fsub_rn(1.f, lam), g), lam);
+    W[p] = (int64_t)floorf(__fmul_rn(w, 1024.f));
+}
+// int64 inclusive scan: 4096 per block (256 threads x 16), block totals, offsets
+__global__ void __launch_bounds__(256) k_scan64_block(const int64_t *__restrict__ in, int64_t P,
+                                                       int64_t *__restrict__ out, int64_t *__restrict__ tot) {
+    __shared__ int64_t red[256];
+    const int64_t base = (int64_t)blockIdx.x * 4096 + (int64_t)threadIdx.x * 16;
+    int64_t v[16], s = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v[k] = base + k < P ? in[base + k] : 0;
+        s += v[k];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {  // inclusive Hillis-Steele over the thread sums
+        const int64_t add = threadIdx.x >= o ? red[threadIdx.x - o] : 0;
+        __syncthreads();
+        red[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int64_t run = red[threadIdx.x] - s;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        run += v[k];
+        if (base + k < P) out[base + k] = run;
+    }
+    if (threadIdx.x == 255) tot[blockIdx.x] = red[255];
+}
+__global__ void k_scan64_tops(int64_t *tot, int nb) {  // exclusive, one thread (nb is small)
+    int64_t run = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t t = tot[b];
+        tot[b] = run;
+        run += t;
+    }
+}
+__global__ void k_scan64_add(int64_t *__restrict__ out, int64_t P, const int64_t *__restrict__ tot) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) out[p] += tot[p / 4096];
+}
+__global__ void k_init_draw(const int64_t *__restrict__ C, int64_t P, uint64_t seed, int64_t n,
+                            const SliceDev *__restrict__ sl, int M, const float *__restrict__ thick,
+                            float *__restrict__ mu, int *__restrict__ pix) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const unsigned long long T = (unsigned long long)C[P - 1];
+    const unsigned long long t = __umul64hi(splitmix64_at(seed, (unsigned long long)k), T);
+    int64_t lo = 0, hi = P - 1;  // first p with C[p] > t
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((unsigned long long)C[mid] > t) hi = mid;
+        else lo = mid + 1;
+    }
+    const int i = slice_of_pixel(sl, M, lo);
+    const SliceDev &S = sl[i];
+    const int loc = (int)(lo - S.pix_base), row = loc / S.W, col = loc - row * S.W;
+    double j[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        j[a] = (double)(splitmix64_at(seed, (1ull << 40) + 3ull * (unsigned long long)k + a) >> 40) * 0x1p-24 - 0.5;
+    const double u0 = ((double)col + j[0] - (double)S.cx0) * (double)S.dx;
+    const double u1 = ((double)row + j[1] - (double)S.cy0) * (double)S.dy;
+    const double u2 = j[2] * (double)thick[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        mu[(size_t)a * n + k] =
+            (float)((double)S.R[3 * a] * u0 + (double)S.R[3 * a + 1] * u1 + (double)S.R[3 * a + 2] * u2 + (double)S.t[a]);
+    if (pix) pix[k] = (int)lo;
+}
+
 __global__ void k_adam_slw(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                            float *__restrict__ v, int M, float lr_sig, float lr_omg, float b1, float b2, float eps,
                            float ibc1_h, float ibc2_h, float scale_h, const float *__restrict__ d_scal,
@@ -2175,6 +2275,22 @@ void launch_adam_slw(float *p, const float *g, float *m, float *v, int M, float 
     }
     k_adam_slw<<<cdiv(2LL * M, 256), 256, 0, st>>>(p, g, m, v, M, lr_sig, lr_omg, b1, b2, eps, h[0], h[1], h[2],
                                                    d_step ? d_scal : nullptr, frozen);
+    counted();
+}
+void launch_init_weights(const float *I, const uint8_t *mask, const SliceDev *slices, int M, int64_t P, float lam,
+                         int64_t *W, int64_t *C, int64_t *scratch, cudaStream_t st) {
+    if (P <= 0) return;
+    const int nb = cdiv(P, 4096);
+    k_init_weights<<<cdiv(P, 256), 256, 0, st>>>(I, mask, slices, M, P, lam, W);
+    k_scan64_block<<<nb, 256, 0, st>>>(W, P, C, scratch);
+    k_scan64_tops<<<1, 1, 0, st>>>(scratch, nb);
+    k_scan64_add<<<cdiv(P, 256), 256, 0, st>>>(C, P, scratch);
+    counted(4);
+}
+void launch_init_draw(const int64_t *C, int64_t P, uint64_t seed, int64_t n, const SliceDev *slices, int M,
+                      const float *thickness, float *mu, int *pix, cudaStream_t st) {
+    if (n <= 0 || P <= 0) return;
+    k_init_draw<<<cdiv(n, 256), 256, 0, st>>>(C, P, seed, n, slices, M, thickness, mu, pix);
     counted();
 }
 void launch_slw_grad(const double *gacc, int n, float *grad, cudaStream_t st) {

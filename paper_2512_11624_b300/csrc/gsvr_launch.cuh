@@ -157,6 +157,17 @@ void launch_advance_step(unsigned long long *d_step, cudaStream_t st);
 void launch_adam_slw(float *p, const float *g, float *m, float *v, int M, float lr_sig, float lr_omg, float b1,
                      float b2, float eps, int step_every, float gamma, long long t_host, const unsigned long long *d_step,
                      const float *d_scal, const uint8_t *frozen, cudaStream_t st);
+// ---- content-adaptive initialisation of the means (Sec. 2.5)
+// W[p] = floor(1024 ((1 - lam) |grad I_p| + lam)) over masked pixels (0
+// elsewhere), the gradient in float32 with every operation rounded alone;
+// C = inclusive prefix sum of W (int64, `scratch` >= cdiv(P, 4096) + 1 entries).
+void launch_init_weights(const float *I, const uint8_t *mask, const SliceDev *slices, int M, int64_t P, float lam,
+                         int64_t *W, int64_t *C, int64_t *scratch, cudaStream_t st);
+// Draw k: pixel = first p with C[p] > floor(splitmix64(seed, k) T / 2^64), T =
+// C[P-1]; mean = that pixel's world position jittered by uniforms from
+// splitmix64(seed, 2^40 + 3 k + a) within its voxel (dx, dy, thickness).
+void launch_init_draw(const int64_t *C, int64_t P, uint64_t seed, int64_t n, const SliceDev *slices, int M,
+                      const float *thickness, float *mu, int *pix, cudaStream_t st);
 // float copy of the forward's float64 per-slice gradient sums
 void launch_slw_grad(const double *gacc, int n, float *grad, cudaStream_t st);
 

@@ -32,7 +32,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
-           "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views"]
+           "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -127,6 +127,7 @@ def _load():
         "gsvr_set_topk": ([vp, C.c_int32, C.c_float, C.c_int32], C.c_int),
         "gsvr_set_objective": ([vp, C.c_int32, C.c_float, C.c_float], C.c_int),
         "gsvr_set_slice_weights": ([vp, C.c_int32, C.c_float, C.c_float], C.c_int),
+        "gsvr_init_means": ([vp, vp, i64, C.c_float, u64, vp, vp, C.POINTER(i64)], C.c_int),
         "gsvr_slice_weight_views": ([vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32)], C.c_int),
         "gsvr_get_topk_neighbors": ([vp, vp, vp, vp, i64, C.POINTER(i64)], C.c_int),
         "gsvr_reserve": ([vp, i64, i64], C.c_int),
@@ -332,6 +333,22 @@ def gsvr_set_topk(ctx, K, delta=1e-8, refresh_every=1):
 def gsvr_set_objective(ctx, loss_kind=0, lambda_reg=0.0, s_target=1.6):
     """Data term (0 MSE, 1 L1) and scale regulariser of the loss."""
     return _check(ctx, lib.gsvr_set_objective(ctx, int(loss_kind), float(lambda_reg), float(s_target)))
+
+
+def gsvr_init_means(ctx, n, lambda_init=0.0, seed=0, pose=None):
+    """Content-adaptive means: (mu (3, n) float32 CUDA tensor, drawn pixels (n,) int32 CUDA tensor, total weight)."""
+    import torch
+    m = max(int(n), 0)  # the library checks n itself
+    mu = torch.empty((3, m), dtype=torch.float32, device="cuda")
+    pix = torch.empty(m, dtype=torch.int32, device="cuda")
+    tot = C.c_int64(0)
+    pp = None
+    if pose is not None:
+        pose = np.ascontiguousarray(pose, np.float32)
+        pp = pose.ctypes.data
+    _check(ctx, lib.gsvr_init_means(ctx, pp, int(n), float(lambda_init), C.c_uint64(int(seed)),
+                                    mu.data_ptr() if m else None, pix.data_ptr() if m else None, C.byref(tot)))
+    return mu, pix, int(tot.value)
 
 
 def gsvr_set_slice_weights(ctx, enable=1, lr_log_sigma=1e-3, lr_log_omega=1e-2):
