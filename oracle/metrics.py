@@ -41,10 +41,6 @@ def _window_3d():
     return g[:, None, None] * g[None, :, None] * g[None, None, :]
 
 
-def _as_volume(a, shape):
-    return np.asarray(a, np.float64).reshape(shape)
-
-
 def local_stats(X, Y, voxels=None):
     """(mu_X, mu_Y, s_X^2, s_Y^2, s_XY) at every voxel of the (D, H, W) grid, or
     at the flat voxel indices `voxels`, from the renormalised 3D window.  Every
@@ -59,6 +55,8 @@ def local_stats(X, Y, voxels=None):
         for dz in range(-RADIUS, RADIUS + 1):
             for dy in range(-RADIUS, RADIUS + 1):
                 for dx in range(-RADIUS, RADIUS + 1):
+                    if abs(dz) >= D or abs(dy) >= H or abs(dx) >= W:
+                        continue  # the offset leaves the grid from every voxel
                     w = w3[dz + RADIUS, dy + RADIUS, dx + RADIUS]
                     # output voxels v whose neighbour v + o is on the grid
                     oz = slice(max(0, -dz), min(D, D - dz))

@@ -4,7 +4,7 @@ NCC), against facts that do not come from the oracle's own formulas:
 - the local weighted moments (window, border renormalisation, population
   moments) against scipy's separable Gaussian filter, normalised by the filter
   of ones ("constant" border), on every voxel of a ragged grid and at single
-  voxels (the per-voxel path);
+  voxels (the per-voxel path), and on grids smaller than the window;
 - SSIM(X, X) = 1 for any X;
 - constant volumes a, b: no variance, SSIM = (2ab + C1)/(a^2 + b^2 + C1) with
   C1 = (0.01 L)^2 (the luminance term alone);
@@ -44,6 +44,13 @@ def _vols(seed, shape=(9, 13, 16)):
     X = ndimage.gaussian_filter(rng.uniform(0, 1, shape), 1.0) + 0.1 * rng.uniform(0, 1, shape)
     Y = 0.8 * X + 0.15 * rng.normal(0, 1, shape) + 0.05
     return X, Y
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 6), (1, 7, 12)])
+def test_local_moments_smaller_than_window(met, shape):
+    X, Y = _vols(8, shape)
+    for a, b in zip(met.local_stats(X, Y), _scipy_moments(X, Y)):
+        assert np.allclose(a, b, rtol=1e-10, atol=1e-13)
 
 
 def test_local_moments_match_scipy(met):
