@@ -426,6 +426,47 @@ const char *gsvr_last_error(gsvr_ctx *ctx);
  * allocates a 1 KB buffer. */
 gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex2_per_s, double *sm_count);
 
+/* Measurement helper (not part of the method): float64 DFMA throughput of the
+ * whole device in instructions per second, measured the same way; the roofline
+ * denominator of the float64 metric passes of gsvr_volume_metrics.
+ * Synchronous; allocates a 1 KB buffer. */
+gsvr_status gsvr_fp64_peak(int device, double *dfma_per_s);
+
+/* Image-quality metrics of a reconstructed volume X against its ground truth
+ * Y on the same grid: the evaluation of Sec. 3 (Table 1 reports PSNR, SSIM and
+ * NCC; the paper does not state their parameters, the readings are these).
+ *   PSNR = 10 log10(L^2 / MSE) over the masked voxels, L = data_range.
+ *   NCC  = the Pearson correlation of X and Y over the masked voxels.
+ *   SSIM = Wang et al. (2004) with K1 = 0.01, K2 = 0.03 and the Gaussian window
+ *          of standard deviation 1.5 voxels and radius 5, in 3D the product
+ *          window of 11 x 11 x 11 voxels; near the grid border the window keeps
+ *          its in-grid voxels and is renormalised over them; local moments are
+ *          weighted population moments over every grid voxel of the window
+ *          (masked or not); the SSIM map is averaged over the masked voxels.
+ * Arguments:
+ *   device       CUDA device (made current for the call; the previous one is
+ *                restored).
+ *   cuda_stream  cudaStream_t to issue the work on (NULL = legacy default).
+ *   D, H, W      grid size; X, Y are float32 device arrays of D*H*W voxels,
+ *                row-major with x fastest (index (z*H + y)*W + x).
+ *   mask         uint8 device array of D*H*W voxels (non-zero = counted), or
+ *                NULL for every voxel.
+ *   data_range   L > 0.
+ *   out          host double[3]: PSNR (dB; +inf when X = Y on the mask), mean
+ *                SSIM, NCC (NaN when X or Y is constant on the mask).
+ *   ssim_map     optional float64 device array of D*H*W voxels receiving the
+ *                SSIM map at every voxel (masked or not); NULL = not written.
+ *   msg, msg_len optional buffer for an error text.
+ * Scratch of 80 bytes per voxel is kept per device between calls (grown with
+ * cudaMalloc when a larger grid comes, held until the process exits); calls
+ * are serialised on it.  Synchronises the stream.
+ * Errors: GSVR_ERR_INVALID_ARG (no such device, a size <= 0 or above 2^30 per
+ * axis, a NULL volume or out, data_range not finite and positive, a mask that
+ * selects no voxel: out then holds NaN), GSVR_ERR_NOMEM (scratch), GSVR_ERR_CUDA. */
+gsvr_status gsvr_volume_metrics(int device, void *cuda_stream, int64_t D, int64_t H, int64_t W, const float *X,
+                                const float *Y, const uint8_t *mask, double data_range, double *out,
+                                double *ssim_map, char *msg, int32_t msg_len);
+
 /* Forward pass without any device allocation (this entry point has no
  * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
  * code running inside a host framework or plug-in whose device memory is owned

@@ -84,3 +84,56 @@ extern "C" gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex
     if (sm_count) *sm_count = nsm;
     return err == cudaSuccess ? GSVR_OK : GSVR_ERR_CUDA;
 }
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_peak_dfma(double *out, int iters, double b, double c) {
+    double a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = 1e-3 * (double)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+    if (s == 12345.678) out[threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" gsvr_status gsvr_fp64_peak(int device, double *dfma_per_s) {
+    if (!dfma_per_s) return GSVR_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return GSVR_ERR_INVALID_ARG;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    double *out = nullptr;
+    if (cudaMalloc(&out, 256 * sizeof(double)) != cudaSuccess) return GSVR_ERR_NOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = nsm * 8, threads = 256, iters = 64;
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        float ms = 0;
+        cudaEventRecord(e0);
+        k_peak_dfma<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = fmax(best, (double)blocks * threads * iters * 16.0 * kChains / (ms * 1e-3));
+    }
+    gsvr::note_launches(3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    const cudaError_t err = cudaGetLastError();
+    *dfma_per_s = best;
+    return err == cudaSuccess ? GSVR_OK : GSVR_ERR_CUDA;
+}

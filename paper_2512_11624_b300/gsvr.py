@@ -32,7 +32,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_alu_peaks", "gsvr_set_subjects", "gsvr_sample_pixels_subjects", "gsvr_get_subject_losses",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
-           "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means"]
+           "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means",
+           "gsvr_volume_metrics", "gsvr_fp64_peak"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -136,6 +137,9 @@ def _load():
         "gsvr_autotune": ([vp, C.POINTER(Tiling), i32, i64, i32, C.POINTER(i32)], C.c_int),
         "gsvr_forward_noalloc": ([C.c_int, vp, i32, C.POINTER(StackDesc), i64, vp, vp, vp, i64, C.c_float, i32, vp,
                                   vp, C.c_char_p, i32], C.c_int),
+        "gsvr_volume_metrics": ([C.c_int, vp, i64, i64, i64, vp, vp, vp, C.c_double, C.POINTER(C.c_double), vp,
+                                 C.c_char_p, i32], C.c_int),
+        "gsvr_fp64_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -463,6 +467,46 @@ def gsvr_alu_peaks(device=0):
     f, e, n = C.c_double(), C.c_double(), C.c_double()
     _check(None, lib.gsvr_alu_peaks(int(device), C.byref(f), C.byref(e), C.byref(n)))
     return f.value, e.value, int(n.value)
+
+
+def gsvr_fp64_peak(device=0):
+    """float64 DFMA instructions/s measured on `device`."""
+    d = C.c_double()
+    _check(None, lib.gsvr_fp64_peak(int(device), C.byref(d)))
+    return d.value
+
+
+def gsvr_volume_metrics(X, Y, mask=None, data_range=1.0, ssim_map=None, stream=None):
+    """(PSNR, SSIM, NCC) of the float32 CUDA volume X (D, H, W) against Y over
+    `mask` (uint8 CUDA tensor of the same shape, or None for every voxel);
+    `ssim_map`, a float64 CUDA tensor of the same shape, receives the SSIM map.
+    Synchronises the stream."""
+    import torch
+    if X.dim() != 3 or tuple(Y.shape) != tuple(X.shape):
+        raise ValueError("X and Y must be volumes (D, H, W) of one shape")
+    for t, dt in ((X, torch.float32), (Y, torch.float32)):
+        if not t.is_cuda or t.dtype != dt:
+            raise ValueError("X and Y must be float32 CUDA tensors")
+    X, Y = X.contiguous(), Y.contiguous()
+    if mask is not None:
+        if tuple(mask.shape) != tuple(X.shape) or mask.dtype != torch.uint8 or not mask.is_cuda:
+            raise ValueError("mask must be a uint8 CUDA tensor shaped like X")
+        mask = mask.contiguous()
+    if ssim_map is not None and (tuple(ssim_map.shape) != tuple(X.shape) or ssim_map.dtype != torch.float64 or
+                                 not ssim_map.is_contiguous()):
+        raise ValueError("ssim_map must be a contiguous float64 CUDA tensor shaped like X")
+    device = X.device.index
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    D, H, W = X.shape
+    out = (C.c_double * 3)()
+    buf = C.create_string_buffer(256)
+    st = lib.gsvr_volume_metrics(int(device), C.c_void_p(int(stream)), int(D), int(H), int(W), X.data_ptr(),
+                                 Y.data_ptr(), mask.data_ptr() if mask is not None else None, float(data_range),
+                                 out, ssim_map.data_ptr() if ssim_map is not None else None, buf, 256)
+    if st != GSVR_OK:
+        raise GsvrError(st, buf.value.decode())
+    return out[0], out[1], out[2]
 
 
 def gsvr_forward_noalloc(stacks, N, theta, I, idx, pred, loss, device=0, stream=None, cutoff_rel=1e-7,

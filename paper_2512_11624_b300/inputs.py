@@ -478,3 +478,22 @@ def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0, shape_jitter=0.0):
     theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
     return {"name": "large", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
             "n_sample": int(mask.sum()), "ref_slice": 24, "phantom": ph, "motion": motion}
+
+
+def metric_volumes(seed, shape, noise=0.05, blur=1.0):
+    """A reference volume Y (smooth random field in [0, 1], with a sharp-edged
+    ellipsoid for structure) and a degraded copy X (blurred by `blur` voxels,
+    Gaussian noise of standard deviation `noise`, 3 % gain and 0.02 offset)
+    on a grid of `shape` (D, H, W), float32, with the mask of the ellipsoid
+    dilated by 2 voxels: the inputs of the image-quality metrics."""
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    D, H, W = shape
+    f = ndimage.gaussian_filter(rng.uniform(0, 1, shape), 2.0)
+    f = (f - f.min()) / max(f.max() - f.min(), 1e-12)
+    z, y, x = np.meshgrid(*[(np.arange(n) - 0.5 * (n - 1)) / max(0.5 * n, 1.0) for n in shape], indexing="ij")
+    r = (x / 0.7) ** 2 + (y / 0.6) ** 2 + (z / 0.8) ** 2
+    Y = np.clip(0.35 * f + 0.6 * (r < 1.0), 0.0, 1.0)
+    X = 1.03 * ndimage.gaussian_filter(Y, blur) + 0.02 + noise * rng.normal(0, 1, shape)
+    mask = ndimage.binary_dilation(r < 1.0, iterations=2)
+    return X.astype(np.float32), Y.astype(np.float32), mask.astype(np.uint8)

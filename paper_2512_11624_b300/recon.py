@@ -4,7 +4,9 @@ sampled pixels, with PSNR against a reference volume and time to a PSNR target.
 
 `PSNRProbe` reads the Gaussian volume V(x) on an isotropic grid through the
 same forward (a stack of grid "slices" with a zero-width PSF reads V itself) and
-returns PSNR = -10 log10(MSE) for intensities in [0, 1].  Iteration time counts
+returns PSNR = -10 log10(MSE) for intensities in [0, 1]; `PSNRProbe.metrics`
+reads V at every grid point and returns PSNR, SSIM and NCC over the phantom's
+voxels (gsvr_volume_metrics, data range 1).  Iteration time counts
 device time of the optimisation steps only (CUDA events around each block of
 iterations); evaluations run outside it.
 """
@@ -29,6 +31,26 @@ class PSNRProbe:
         if topk:
             gsvr.gsvr_set_topk(self.ctx.ctx, int(topk[0]), float(topk[1]), 1)
         self.n_points = int(inside.sum())
+        self.shape = (st["n_slices"], st["H"], st["W"])
+        self._grid_case = dict(case, mask=np.ones_like(inside))
+        self._device, self._stream, self._topk = device, stream, topk
+        self._full = None
+        self._ref = torch.from_numpy(ref.reshape(self.shape)).to("cuda:%d" % device)
+        self._inside = torch.from_numpy(inside.reshape(self.shape)).to("cuda:%d" % device)
+
+    def metrics(self, theta_g):
+        """(PSNR, SSIM, NCC) of the volume read at every grid point against the
+        phantom, over the phantom's voxels."""
+        if self._full is None:
+            self._full = gsvr.Context(self._grid_case, device=self._device, stream=self._stream, tile_h=16, tile_w=16)
+            if self._topk:
+                gsvr.gsvr_set_topk(self._full.ctx, int(self._topk[0]), float(self._topk[1]), 1)
+        self._full.theta[:11 * self.N].copy_(theta_g[:11 * self.N])
+        gsvr.gsvr_forward(self._full.ctx)
+        gsvr.gsvr_sync_status(self._full.ctx)
+        X = self._full.pred.view(self.shape)
+        return gsvr.gsvr_volume_metrics(X, self._ref, self._inside, 1.0,
+                                        stream=self._stream)
 
     def psnr(self, theta_g):
         """theta_g: the first 11 N entries of a parameter vector (CUDA tensor)."""
@@ -39,6 +61,8 @@ class PSNRProbe:
 
     def close(self):
         self.ctx.close()
+        if self._full is not None:
+            self._full.close()
 
 
 # Learning rates per Adam step on 2^18-pixel mini-batches.  Pose rates are the

@@ -4,6 +4,8 @@
   python -m paper_2512_11624_b300.study learned [--phantoms 2000] [--epochs 20] [--cases 10] [--out FILE]
   python -m paper_2512_11624_b300.study topk [--k 10 20 50 80] [--iters 600] [--out FILE]
   python -m paper_2512_11624_b300.study cnnbench [--batch 256] [--steps 50]
+  python -m paper_2512_11624_b300.study init [--model plain|topk] [--density-scales] [--lambdas 0 0.5 1] [--out FILE]
+  python -m paper_2512_11624_b300.study metrics [--h 0.8 0.5 0.4]
 
 `batched`: the batched multi-subject workload (`inputs.batched`: 16 subjects of
 uneven size).  Every subject is first reconstructed alone (its own context with
@@ -434,6 +436,131 @@ def run_topk(args):
         json.dump(out, open(args.out, "w"), indent=1)
 
 
+def density_scales(mu, cell=2.0, smin=0.4, smax=4.0):
+    """Isotropic scale per mean from the local density of the means: the count
+    of means in each `cell`-mm cube, s = density^(-1/3) (the local spacing),
+    clipped to [smin, smax] mm.  mu: (3, N) CUDA tensor."""
+    import torch
+    lo = mu.min(dim=1, keepdim=True).values
+    idx = ((mu - lo) / cell).floor().long()
+    dims = idx.max(dim=1).values + 1
+    key = (idx[0] * dims[1] + idx[1]) * dims[2] + idx[2]
+    cnt = torch.zeros(int(dims.prod()), device=mu.device).scatter_add_(0, key, torch.ones(key.shape, device=mu.device))
+    return (cnt[key] / cell ** 3).pow(-1.0 / 3.0).clamp(smin, smax)
+
+
+def run_init(args):
+    """Content-adaptive initialisation (Sec. 2.5) against the grid start on the
+    fetal workload.  Every run has the grid's Gaussian count and identity
+    rotations and differs in where the means start, their scales and their
+    amplitudes.  "grid": means on the 0.8 mm grid inside the brain, scale
+    0.8 mm, one flat amplitude (the mean observed brain intensity).
+    "adaptive lambda": means drawn by gsvr_init_means from the slices at their
+    nominal poses with mixing weight lambda, each amplitude the observed
+    intensity of its drawn pixel (the paper does not say how scales and
+    colours start); scales 0.8 mm, or with `--density-scales` the local spacing
+    of the drawn means (density_scales), since a plain sum of Gaussians adds
+    up where means cluster.  Plain sum (`--model plain`): amplitudes carry the
+    factor h^3 / ((2 pi)^(3/2) s^3) with h the spacing (= s).  Normalised top-K
+    model (`--model topk`, K = `--k`): amplitudes are the colours themselves,
+    and zero-colour background Gaussians cover the mask band outside the brain
+    as in the top-K study.  Reported per run: the device time of the
+    initialisation, PSNR every `eval_every` iterations, and PSNR / SSIM / NCC
+    of the volume against the phantom (gsvr_volume_metrics over the phantom's
+    voxels) at the start and after `iters` iterations, with the device seconds
+    of the iterations."""
+    import torch
+    from . import gsvr, inputs
+    from .recon import PLAIN_LR, PSNRProbe, Reconstruction
+    torch.cuda.set_device(0)
+    flat = inputs.fetal(args.seed, init="flat")
+    N = flat["N"]
+    M = inputs.n_slices_total(flat["stacks"])
+    topk = args.model == "topk"
+    grid_factor = 1.0 / (2 * np.pi) ** 1.5  # h^3 / ((2 pi)^(3/2) s^3) with h = s
+    configs = [("grid", None)] + [("adaptive lambda=%g" % lam, lam) for lam in args.lambdas]
+    out = []
+    for name, lam in configs:
+        case = dict(flat)
+        init_ms = None
+        g = flat["theta"][:11 * N].reshape(11, N).copy()
+        if lam is not None:
+            ctx = gsvr.Context(flat)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            zero = np.zeros((M, 6), np.float32)
+            gsvr.gsvr_init_means(ctx.ctx, N, lam, args.seed + 1, pose=zero)  # warm-up
+            torch.cuda.synchronize()
+            e0.record()
+            mu, pix, _ = gsvr.gsvr_init_means(ctx.ctx, N, lam, args.seed + 1, pose=zero)
+            e1.record()
+            e1.synchronize()
+            init_ms = e0.elapsed_time(e1)
+            ctx.close()
+            s = density_scales(mu) if args.density_scales else torch.full((N,), 0.8, device=mu.device)
+            g[0:3] = mu.cpu().numpy()
+            g[3:6] = np.log(s.cpu().numpy())[None, :]
+            g[10] = np.asarray(flat["I"], np.float32)[pix.cpu().numpy()] * (1.0 if topk else grid_factor)
+        elif topk:
+            g[10] /= grid_factor
+        case["theta"] = np.concatenate([g.reshape(-1), flat["theta"][11 * N:]]).astype(np.float32)
+        if topk:
+            bg, nb = inputs.background_gaussians(case["phantom"])
+            case = inputs.with_gaussians(case, bg, nb)
+            rec = Reconstruction(case, n_sample=args.n_sample, lr=dict(lr_c=PLAIN_LR["lr_c"] / grid_factor),
+                                 topk=(args.k, 1e-8, 1))
+            probe = PSNRProbe(case["phantom"], case["N"], topk=(args.k, 1e-8))
+        else:
+            rec = Reconstruction(case, n_sample=args.n_sample, fixed=True)
+            probe = PSNRProbe(case["phantom"], N)
+        m0 = probe.metrics(rec.ctx.theta)
+        res = rec.run(args.iters, probe=probe, eval_every=args.eval_every)
+        m1 = probe.metrics(rec.ctx.theta)
+        hist = res["history"]
+        row = {"model": args.model, "K": args.k if topk else None, "init": name, "lambda_init": lam,
+               "density_scales": bool(args.density_scales and lam is not None), "N": N, "init_ms": init_ms,
+               "iters": hist[-1][0], "seconds": hist[-1][1], "psnr": [(h[0], h[3]) for h in hist],
+               "start": {"psnr": m0[0], "ssim": m0[1], "ncc": m0[2]},
+               "end": {"psnr": m1[0], "ssim": m1[1], "ncc": m1[2]}}
+        print(json.dumps(row), flush=True)
+        out.append(row)
+        probe.close()
+        rec.close()
+    if args.out:
+        json.dump(out, open(args.out, "w"), indent=1)
+
+
+def run_metrics_bench(args):
+    """Device time of gsvr_volume_metrics on evaluation grids of the fetal
+    phantom (0.8 mm and finer), with the float64 DFMA throughput it reaches
+    (165 window DFMA per voxel) against the measured DFMA peak."""
+    import torch
+    from . import gsvr, inputs
+    torch.cuda.set_device(0)
+    peak = gsvr.gsvr_fp64_peak(0)
+    ph = inputs.BrainPhantom(0)
+    rows = []
+    for h in args.h:
+        st, ref, inside = inputs.grid_probe(ph, h)
+        shape = (st["n_slices"], st["H"], st["W"])
+        Y = torch.from_numpy(ref.reshape(shape)).cuda()
+        X = (Y + 0.02 * torch.randn(shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1))).float()
+        msk = torch.from_numpy(inside.reshape(shape)).cuda()
+        for _ in range(3):
+            gsvr.gsvr_volume_metrics(X, Y, msk, 1.0)
+        ts = []
+        for _ in range(args.reps):
+            t0 = time.perf_counter()
+            res = gsvr.gsvr_volume_metrics(X, Y, msk, 1.0)
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        V = int(np.prod(shape))
+        row = {"h_mm": h, "shape": shape, "voxels": V, "ms": 1e3 * t, "psnr_ssim_ncc": res,
+               "dfma_per_s": 165.0 * V / t, "dfma_peak": peak, "frac": 165.0 * V / t / peak}
+        print(json.dumps(row), flush=True)
+        rows.append(row)
+    return rows
+
+
 def run_topk_step(args):
     """A few plain top-K iterations (forward + backward) on the fetal workload's
     2^18-pixel sample: the command the top-K kernels are profiled with."""
@@ -497,8 +624,25 @@ def main():
     ts.add_argument("--k", type=int, default=50)
     ts.add_argument("--delta", type=float, default=1e-8)
     ts.add_argument("--steps", type=int, default=3)
+    it = sub.add_parser("init")
+    it.add_argument("--lambdas", type=float, nargs="+", default=[0.0, 0.5, 1.0])
+    it.add_argument("--iters", type=int, default=600)
+    it.add_argument("--eval-every", type=int, default=100)
+    it.add_argument("--n-sample", type=int, default=1 << 18)
+    it.add_argument("--seed", type=int, default=0)
+    it.add_argument("--model", choices=["plain", "topk"], default="plain")
+    it.add_argument("--k", type=int, default=50)
+    it.add_argument("--density-scales", action="store_true")
+    it.add_argument("--out", default="")
+    mb = sub.add_parser("metrics")
+    mb.add_argument("--h", type=float, nargs="+", default=[0.8, 0.5, 0.4])
+    mb.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
-    if args.cmd == "topk":
+    if args.cmd == "init":
+        run_init(args)
+    elif args.cmd == "metrics":
+        run_metrics_bench(args)
+    elif args.cmd == "topk":
         run_topk(args)
     elif args.cmd == "topk-step":
         run_topk_step(args)
