@@ -432,6 +432,61 @@ gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex2_per_s, do
  * Synchronous; allocates a 1 KB buffer. */
 gsvr_status gsvr_fp64_peak(int device, double *dfma_per_s);
 
+/* Coarse-to-fine densification: split, clone and prune of the Gaussians.  The
+ * paper names progressive densification (after 3D Gaussian Splatting, Kerbl
+ * et al. 2023) as future work ("Limitations and Future Work": start with few
+ * large Gaussians, split adaptively) without giving a rule; this is the rule:
+ *  - statistic: per Gaussian the sums of ||dL/dmu_j|| and of dL/dmu_j over the
+ *    backward passes since the last densification (gsvr_densify_accumulate
+ *    after each gsvr_backward) and the number of those passes;
+ *  - decision (float32): prune when |c_j| < prune_amplitude; else, when the
+ *    mean norm (sum / passes; 0 with no pass) exceeds grad_threshold, split if
+ *    the largest log-scale exceeds log_scale_threshold, clone otherwise; else
+ *    keep;
+ *  - split: two children at mu_j +- d a (a = the principal axis, the
+ *    rotation's column of the largest log-scale, first on ties;
+ *    d = s sqrt(1 - 1/phi^2), s that scale), principal scale s / phi: the pair
+ *    has the parent's mean and covariance;
+ *  - clone: two copies at mu_j +- delta u (u = direction of the summed mean
+ *    gradient, the principal axis if it is zero; delta = clone_offset x the
+ *    smallest scale);
+ *  - amplitudes: mass_preserving = 1 (the plain sum) gives c phi / 2 (split) or
+ *    c / 2 (clone), keeping the summed mass; 0 (the normalised top-K model,
+ *    where c is a colour) keeps c;
+ *  - layout: Gaussians in index order, a kept one once (with its Adam
+ *    moments), a split or cloned one as its two children (+ first; moments 0),
+ *    a pruned one not at all; slice poses and their moments unchanged. */
+typedef struct gsvr_densify_cfg {
+    float grad_threshold;      /* split or clone above this mean ||dL/dmu_j|| */
+    float log_scale_threshold; /* split (not clone) above this largest log-scale */
+    float prune_amplitude;     /* remove when |c_j| is below it (0: never), >= 0 */
+    float split_factor;        /* phi > 1 (3D Gaussian Splatting uses 1.6) */
+    float clone_offset;        /* kappa >= 0 */
+    int32_t mass_preserving;   /* 1 or 0, see above */
+    int64_t max_gaussians;     /* refuse above this count (0: 2^26) */
+} gsvr_densify_cfg;
+
+/* Add ||dL/dmu_j|| and dL/dmu_j of the gradient buffer (the last
+ * gsvr_backward) to the statistics and count one pass.  The statistics restart
+ * (zero) after gsvr_set_gaussians and gsvr_densify.  Asynchronous; graph
+ * capturable once sized (one call outside capture sizes them). */
+gsvr_status gsvr_densify_accumulate(gsvr_ctx *ctx);
+
+/* Read (set = 0) or write (set = 1) the statistics: acc = host float[4 N]
+ * (per Gaussian: sum of norms, sum of the three gradient components), count =
+ * passes.  Synchronises.  GSVR_ERR_INVALID_ARG for NULL pointers (acc may be
+ * NULL when N = 0) or a negative count. */
+gsvr_status gsvr_densify_stats(gsvr_ctx *ctx, float *acc, int32_t *count, int32_t set);
+
+/* Apply the rule above to the context's Gaussians: the parameter vector and
+ * Adam moments are rebuilt for the new count N' (views from gsvr_get_views
+ * change), the gradient is zeroed, capacities follow N', a captured CUDA graph
+ * is dropped, and the statistics restart.  counts (host int64[4], may be NULL)
+ * = {N', split, cloned, pruned}.  Synchronises.  Errors: GSVR_ERR_INVALID_ARG
+ * (bad configuration), GSVR_ERR_STATE (no Gaussians, a batched context, during
+ * graph capture), GSVR_ERR_CAPACITY (N' > max_gaussians; nothing changed). */
+gsvr_status gsvr_densify(gsvr_ctx *ctx, const gsvr_densify_cfg *cfg, int64_t *counts);
+
 /* Image-quality metrics of a reconstructed volume X against its ground truth
  * Y on the same grid: the evaluation of Sec. 3 (Table 1 reports PSNR, SSIM and
  * NCC; the paper does not state their parameters, the readings are these).

@@ -108,6 +108,11 @@ struct gsvr_ctx {
     // content-adaptive initialisation scratch (gsvr_init_means)
     DBuf<int64_t> d_init_w, d_init_c, d_init_s;
     DBuf<float> d_init_pose, d_init_thick;
+    // densification statistics and scratch (gsvr_densify_accumulate, gsvr_densify)
+    DBuf<float4> d_dens_acc;          // per Gaussian: sum ||dL/dmu||, sum dL/dmu
+    DBuf<int> d_dens_cnt, d_dens_nout, d_dens_off, d_dens_misc;
+    DBuf<uint8_t> d_dens_kind;
+    int64_t dens_n = -1;              // the N the statistics are sized for (-1: restart them)
     // normalised top-K form (gsvr_set_topk); K = 0: the plain sum
     int topk_K = 0, topk_refresh = 1;
     float topk_delta = 1e-8f, topk_per_cell = 16.f;
@@ -713,6 +718,27 @@ gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *
     return sample_all(ctx);
 }
 
+// Record and key capacities for N Gaussians (the configured ones in
+// fixed-capacity mode, else at least 8 records per Gaussian) and the scan
+// scratch they imply.
+gsvr_status gauss_capacities(gsvr_ctx *ctx, int64_t N) {
+    if (ctx->cfg.fixed_capacity) {
+        gsvr_status s = ensure_rec_capacity(ctx, ctx->cfg.cap_records);
+        if (s) return s;
+        s = ensure_key_capacity(ctx, ctx->cfg.cap_keys);
+        if (s) return s;
+    } else {
+        const int64_t want_r = ctx->cfg.cap_records > 0 ? ctx->cfg.cap_records : std::max<int64_t>(4096, 8 * N);
+        const int64_t want_k = ctx->cfg.cap_keys > 0 ? ctx->cfg.cap_keys : 4 * want_r;
+        gsvr_status s = ensure_rec_capacity(ctx, std::max<int64_t>(ctx->cap_rec, want_r));
+        if (s) return s;
+        s = ensure_key_capacity(ctx, std::max<int64_t>(ctx->cap_keys, want_k));
+        if (s) return s;
+    }
+    CK(ensure_scan_scratch(ctx));
+    return GSVR_OK;
+}
+
 gsvr_status gsvr_set_gaussians(gsvr_ctx *ctx, int64_t N, const float *theta_g, int32_t mem) {
     if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
     if (!ctx->have_stacks) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks first");
@@ -762,23 +788,10 @@ gsvr_status gsvr_set_gaussians(gsvr_ctx *ctx, int64_t N, const float *theta_g, i
         CK(cudaMemsetAsync(ctx->d_m.p, 0, sizeof(float) * 11 * N, st));
         CK(cudaMemsetAsync(ctx->d_v.p, 0, sizeof(float) * 11 * N, st));
     }
-    // initial capacities
-    if (ctx->cfg.fixed_capacity) {
-        gsvr_status s = ensure_rec_capacity(ctx, ctx->cfg.cap_records);
-        if (s) return s;
-        s = ensure_key_capacity(ctx, ctx->cfg.cap_keys);
-        if (s) return s;
-    } else {
-        const int64_t want_r = ctx->cfg.cap_records > 0 ? ctx->cfg.cap_records : std::max<int64_t>(4096, 8 * N);
-        const int64_t want_k = ctx->cfg.cap_keys > 0 ? ctx->cfg.cap_keys : 4 * want_r;
-        gsvr_status s = ensure_rec_capacity(ctx, std::max<int64_t>(ctx->cap_rec, want_r));
-        if (s) return s;
-        s = ensure_key_capacity(ctx, std::max<int64_t>(ctx->cap_keys, want_k));
-        if (s) return s;
-    }
-    CK(ensure_scan_scratch(ctx));
+    if (gsvr_status s = gauss_capacities(ctx, N)) return s;
     ctx->have_gauss = true;
     ctx->fwd_valid = false;
+    ctx->dens_n = -1;  // densification statistics restart
     return GSVR_OK;
 }
 
@@ -1681,6 +1694,149 @@ gsvr_status gsvr_set_objective(gsvr_ctx *ctx, int32_t loss_kind, float lambda_re
     ctx->lambda_reg = lambda_reg;
     ctx->s_target = s_target;
     ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+// ------------------------------------------------------------ densification
+}  // extern "C"
+
+namespace {
+
+template <class T>
+void swap_buf(DBuf<T> &a, DBuf<T> &b) {
+    std::swap(a.p, b.p);
+    std::swap(a.n, b.n);
+}
+
+// Statistics sized for the current N, zeroed when N changed since they were.
+gsvr_status dens_ensure(gsvr_ctx *ctx) {
+    if (ctx->dens_n == ctx->N && ctx->d_dens_acc.p && ctx->d_dens_cnt.p) return GSVR_OK;
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "densification statistics must be sized before graph capture");
+    const size_t n = (size_t)std::max<int64_t>(ctx->N, 1);
+    CK(ctx->d_dens_acc.ensure(n));
+    CK(ctx->d_dens_cnt.ensure(1));
+    CK(cudaMemsetAsync(ctx->d_dens_acc.p, 0, sizeof(float4) * n, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_dens_cnt.p, 0, sizeof(int), ctx->stream));
+    ctx->dens_n = ctx->N;
+    return GSVR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gsvr_status gsvr_densify_accumulate(gsvr_ctx *ctx) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
+    DeviceGuard g(ctx->device);
+    if (gsvr_status s = dens_ensure(ctx)) return s;
+    launch_dens_accum(ctx->d_grad.p, (int)ctx->N, ctx->d_dens_acc.p, ctx->d_dens_cnt.p, ctx->stream);
+    CK(cudaGetLastError());
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_densify_stats(gsvr_ctx *ctx, float *acc, int32_t *count, int32_t set) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
+    if ((ctx->N > 0 && !acc) || !count || (set != 0 && set != 1))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad statistics pointer or direction");
+    if (set && *count < 0) return fail(ctx, GSVR_ERR_INVALID_ARG, "negative pass count");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_densify_stats during graph capture");
+    DeviceGuard g(ctx->device);
+    if (gsvr_status s = dens_ensure(ctx)) return s;
+    const size_t bytes = sizeof(float4) * (size_t)ctx->N;
+    cudaStream_t st = ctx->stream;
+    if (set) {
+        if (bytes) CK(cudaMemcpyAsync(ctx->d_dens_acc.p, acc, bytes, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_dens_cnt.p, count, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    } else {
+        if (bytes) CK(cudaMemcpyAsync(acc, ctx->d_dens_acc.p, bytes, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(count, ctx->d_dens_cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_densify(gsvr_ctx *ctx, const gsvr_densify_cfg *cfg, int64_t *counts) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_gaussians first");
+    if (!cfg || !std::isfinite(cfg->grad_threshold) || !std::isfinite(cfg->log_scale_threshold) ||
+        !(cfg->prune_amplitude >= 0.f) || !std::isfinite(cfg->prune_amplitude) || !(cfg->split_factor > 1.f) ||
+        !std::isfinite(cfg->split_factor) || !(cfg->clone_offset >= 0.f) || !std::isfinite(cfg->clone_offset) ||
+        (cfg->mass_preserving != 0 && cfg->mass_preserving != 1) || cfg->max_gaussians < 0)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "bad densification configuration");
+    if (ctx->n_subj > 1) return fail(ctx, GSVR_ERR_STATE, "densification of a batched context is not supported");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_densify during graph capture");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    if (gsvr_status s = dens_ensure(ctx)) return s;
+    const int N = (int)ctx->N, M = ctx->M;
+    const int64_t cap = cfg->max_gaussians > 0 ? std::min<int64_t>(cfg->max_gaussians, 1LL << 26) : (1LL << 26);
+    int h[4] = {0, 0, 0, 0};  // split, cloned, pruned, new count
+    if (N > 0) {
+        CK(ctx->d_dens_kind.ensure((size_t)N));
+        CK(ctx->d_dens_nout.ensure((size_t)N + 1));
+        CK(ctx->d_dens_off.ensure((size_t)N + 1));
+        CK(ctx->d_dens_misc.ensure(4));
+        CK(cudaMemsetAsync(ctx->d_dens_misc.p, 0, sizeof(int) * 4, st));
+        launch_dens_decide(ctx->d_theta.p, N, ctx->d_dens_acc.p, ctx->d_dens_cnt.p, cfg->grad_threshold,
+                           cfg->log_scale_threshold, cfg->prune_amplitude, ctx->d_dens_kind.p, ctx->d_dens_nout.p,
+                           ctx->d_dens_misc.p, st);
+        CK(ensure_scan_scratch(ctx));
+        CK(scan_exclusive(ctx->d_dens_nout.p, ctx->d_dens_off.p, nullptr, N, N, ctx->d_dens_misc.p + 3,
+                          scan_scratch(ctx), st));
+        CK(cudaMemcpyAsync(h, ctx->d_dens_misc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    const int64_t N2 = N > 0 ? h[3] : 0;
+    if (N2 > cap) return fail(ctx, GSVR_ERR_CAPACITY, "densification would exceed max_gaussians; nothing changed");
+    if (N > 0 && (h[0] || h[1] || h[2])) {
+        const size_t np2 = (size_t)(11 * N2 + 6 * M);
+        DBuf<float> t2, m2, v2;
+        CK(t2.ensure(np2));
+        CK(m2.ensure(np2));
+        CK(v2.ensure(np2));
+        DensParams p{};
+        p.split_factor = cfg->split_factor;
+        p.log_split_factor = (float)std::log((double)cfg->split_factor);
+        p.split_offset = (float)std::sqrt(1.0 - 1.0 / ((double)cfg->split_factor * (double)cfg->split_factor));
+        p.clone_offset = cfg->clone_offset;
+        p.mass_preserving = cfg->mass_preserving;
+        launch_dens_emit(ctx->d_theta.p, ctx->d_m.p, ctx->d_v.p, N, ctx->d_dens_acc.p, ctx->d_dens_kind.p,
+                         ctx->d_dens_off.p, (int)N2, p, t2.p, m2.p, v2.p, st);
+        if (M > 0) {
+            const size_t pb = sizeof(float) * 6 * (size_t)M;
+            CK(cudaMemcpyAsync(t2.p + 11 * N2, ctx->d_theta.p + 11 * (int64_t)N, pb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(m2.p + 11 * N2, ctx->d_m.p + 11 * (int64_t)N, pb, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(v2.p + 11 * N2, ctx->d_v.p + 11 * (int64_t)N, pb, cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaStreamSynchronize(st));  // the old buffers are read until here
+        swap_buf(ctx->d_theta, t2);
+        swap_buf(ctx->d_m, m2);
+        swap_buf(ctx->d_v, v2);
+        ctx->d_grad.release();
+        CK(ctx->d_grad.ensure(np2));
+        CK(cudaMemsetAsync(ctx->d_grad.p, 0, sizeof(float) * np2, st));
+        CK(ctx->d_gpre.ensure((size_t)2 * N2));
+        CK(ctx->d_rec_cnt.ensure((size_t)N2 + 1));
+        CK(ctx->d_rec_off.ensure((size_t)N2 + 1));
+        ctx->N = N2;
+        if (gsvr_status s = gauss_capacities(ctx, N2)) return s;
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
+        ctx->graph_exec = nullptr;
+        ctx->graph = nullptr;
+        ctx->fwd_valid = false;
+    }
+    ctx->dens_n = -1;  // the statistics restart (sized for the new count)
+    if (gsvr_status s = dens_ensure(ctx)) return s;
+    CK(cudaStreamSynchronize(st));
+    if (counts) {
+        counts[0] = ctx->N;
+        counts[1] = h[0];
+        counts[2] = h[1];
+        counts[3] = h[2];
+    }
     return GSVR_OK;
 }
 

@@ -247,4 +247,20 @@ void launch_topk_epilogue(const float *theta, const float *gacc, int N, float *g
 void launch_scale_reg_loss(const float *theta, int N, float lambda, float s_target, double *loss, cudaStream_t st);
 void launch_scale_reg_grad(const float *theta, int N, float lambda, float s_target, float *grad, cudaStream_t st);
 
+// densification (split / clone / prune)
+enum : int { kDensPrune = 0, kDensKeep = 1, kDensSplit = 2, kDensClone = 3 };
+struct DensParams {
+    float split_factor;      // phi
+    float log_split_factor;  // ln phi
+    float split_offset;      // sqrt(1 - 1 / phi^2)
+    float clone_offset;      // kappa
+    int mass_preserving;
+};
+void launch_dens_accum(const float *grad, int N, float4 *acc, int *cnt, cudaStream_t st);
+void launch_dens_decide(const float *theta, int N, const float4 *acc, const int *cnt, float tau_g, float tau_ls,
+                        float eps_c, uint8_t *kind, int *nout, int *counts, cudaStream_t st);
+void launch_dens_emit(const float *theta, const float *m, const float *v, int N, const float4 *acc,
+                      const uint8_t *kind, const int *off, int N2, const DensParams &p, float *theta2, float *m2,
+                      float *v2, cudaStream_t st);
+
 }  // namespace gsvr

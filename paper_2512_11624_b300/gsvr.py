@@ -33,7 +33,8 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_graph_capture", "gsvr_graph_launch", "gsvr_set_step", "gsvr_set_tiling", "gsvr_get_tiling",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
            "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means",
-           "gsvr_volume_metrics", "gsvr_fp64_peak"]
+           "gsvr_volume_metrics", "gsvr_fp64_peak", "gsvr_densify_accumulate", "gsvr_densify_stats",
+           "gsvr_densify"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -53,6 +54,12 @@ class Config(C.Structure):
     _fields_ = [("cutoff_rel", C.c_float), ("tile_h", C.c_int32), ("tile_w", C.c_int32), ("norm_mode", C.c_int32),
                 ("fixed_capacity", C.c_int32), ("timing", C.c_int32), ("cap_records", C.c_int64),
                 ("cap_keys", C.c_int64), ("seed", C.c_uint64)]
+
+
+class DensifyCfg(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("log_scale_threshold", C.c_float), ("prune_amplitude", C.c_float),
+                ("split_factor", C.c_float), ("clone_offset", C.c_float), ("mass_preserving", C.c_int32),
+                ("max_gaussians", C.c_int64)]
 
 
 class AdamCfg(C.Structure):
@@ -140,6 +147,9 @@ def _load():
         "gsvr_volume_metrics": ([C.c_int, vp, i64, i64, i64, vp, vp, vp, C.c_double, C.POINTER(C.c_double), vp,
                                  C.c_char_p, i32], C.c_int),
         "gsvr_fp64_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+        "gsvr_densify_accumulate": ([vp], C.c_int),
+        "gsvr_densify_stats": ([vp, vp, C.POINTER(i32), i32], C.c_int),
+        "gsvr_densify": ([vp, C.POINTER(DensifyCfg), C.POINTER(i64)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -469,6 +479,35 @@ def gsvr_alu_peaks(device=0):
     return f.value, e.value, int(n.value)
 
 
+def gsvr_densify_accumulate(ctx):
+    """Add the last backward's ||dL/dmu_j|| and dL/dmu_j to the densification statistics."""
+    return _check(ctx, lib.gsvr_densify_accumulate(ctx))
+
+
+def gsvr_densify_stats(ctx, N, acc=None, count=None):
+    """Without `acc`: read the statistics, (acc (N, 4) float32, pass count).
+    With `acc` ((N, 4) float32) and `count`: write them."""
+    if acc is None:
+        a = np.zeros((int(N), 4), np.float32)
+        c = C.c_int32(0)
+        _check(ctx, lib.gsvr_densify_stats(ctx, a.ctypes.data if N else None, C.byref(c), 0))
+        return a, int(c.value)
+    a = np.ascontiguousarray(acc, np.float32).reshape(int(N), 4)
+    c = C.c_int32(int(count))
+    _check(ctx, lib.gsvr_densify_stats(ctx, a.ctypes.data if N else None, C.byref(c), 1))
+    return a, int(count)
+
+
+def gsvr_densify(ctx, grad_threshold, log_scale_threshold, prune_amplitude=0.0, split_factor=1.6,
+                 clone_offset=0.5, mass_preserving=1, max_gaussians=0):
+    """Split / clone / prune; returns (new N, split, cloned, pruned)."""
+    cfg = DensifyCfg(float(grad_threshold), float(log_scale_threshold), float(prune_amplitude), float(split_factor),
+                     float(clone_offset), int(mass_preserving), int(max_gaussians))
+    out = (C.c_int64 * 4)()
+    _check(ctx, lib.gsvr_densify(ctx, C.byref(cfg), out))
+    return tuple(int(x) for x in out)
+
+
 def gsvr_fp64_peak(device=0):
     """float64 DFMA instructions/s measured on `device`."""
     d = C.c_double()
@@ -573,6 +612,8 @@ class Context:
         self.n_pixels = int(v.n_pixels)
         self.theta = device_view(v.theta, v.n_params, device=self.device)
         self.grad = device_view(v.grad, v.n_params, device=self.device)
+        self.adam_m = device_view(v.adam_m, v.n_params, device=self.device)
+        self.adam_v = device_view(v.adam_v, v.n_params, device=self.device)
         self.pred = device_view(v.pred, v.n_pixels, device=self.device)
         self.rbar = device_view(v.rbar, v.n_pixels, device=self.device)
         self.loss_t = device_view(v.loss, 1, "float64", device=self.device)
@@ -582,6 +623,13 @@ class Context:
         gsvr_set_gaussians(self.ctx, int(N), theta_g)
         self.N = int(N)
         self.refresh_views()
+
+    def densify(self, grad_threshold, log_scale_threshold, **kw):
+        """gsvr_densify, then refresh N and the views; returns (N, split, cloned, pruned)."""
+        out = gsvr_densify(self.ctx, grad_threshold, log_scale_threshold, **kw)
+        self.N = out[0]
+        self.refresh_views()
+        return out
 
     def forward(self):
         gsvr_forward(self.ctx)

@@ -497,3 +497,17 @@ def metric_volumes(seed, shape, noise=0.05, blur=1.0):
     X = 1.03 * ndimage.gaussian_filter(Y, blur) + 0.02 + noise * rng.normal(0, 1, shape)
     mask = ndimage.binary_dilation(r < 1.0, iterations=2)
     return X.astype(np.float32), Y.astype(np.float32), mask.astype(np.uint8)
+
+
+def densify_stats(seed, N, count=4, scale=1.0):
+    """Densification statistics of N Gaussians after `count` passes: summed
+    gradient norms (log-normal, heavy-tailed like real mean-gradient norms,
+    median `scale` per pass) and summed gradient vectors whose norm does not
+    exceed that sum; float32 (N, 4)."""
+    rng = np.random.default_rng(seed)
+    n = scale * count * rng.lognormal(0.0, 1.0, N)
+    d = rng.normal(0, 1, (N, 3))
+    d /= np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 1e-12)
+    frac = rng.uniform(0.2, 1.0, (N, 1))
+    acc = np.concatenate([n[:, None], d * frac * n[:, None]], axis=1)
+    return acc.astype(np.float32), int(count)

@@ -38,11 +38,26 @@ class PSNRProbe:
         self._ref = torch.from_numpy(ref.reshape(self.shape)).to("cuda:%d" % device)
         self._inside = torch.from_numpy(inside.reshape(self.shape)).to("cuda:%d" % device)
 
-    def metrics(self, theta_g):
+    def _resize(self, N):
+        """Follow a new Gaussian count (after a densification)."""
+        N = int(N)
+        if N == self.N:
+            return
+        self.N = N
+        zeros = np.zeros(11 * N, np.float32)
+        self.ctx.set_gaussians(zeros, N)
+        if self._full is not None:
+            self._full.set_gaussians(zeros, N)
+
+    def metrics(self, theta_g, N=None):
         """(PSNR, SSIM, NCC) of the volume read at every grid point against the
         phantom, over the phantom's voxels."""
+        if N is not None:
+            self._resize(N)
         if self._full is None:
-            self._full = gsvr.Context(self._grid_case, device=self._device, stream=self._stream, tile_h=16, tile_w=16)
+            M = int(self._grid_case["stacks"][0]["n_slices"])
+            grid = dict(self._grid_case, N=self.N, theta=np.zeros(11 * self.N + 6 * M, np.float32))
+            self._full = gsvr.Context(grid, device=self._device, stream=self._stream, tile_h=16, tile_w=16)
             if self._topk:
                 gsvr.gsvr_set_topk(self._full.ctx, int(self._topk[0]), float(self._topk[1]), 1)
         self._full.theta[:11 * self.N].copy_(theta_g[:11 * self.N])
@@ -52,8 +67,11 @@ class PSNRProbe:
         return gsvr.gsvr_volume_metrics(X, self._ref, self._inside, 1.0,
                                         stream=self._stream)
 
-    def psnr(self, theta_g):
-        """theta_g: the first 11 N entries of a parameter vector (CUDA tensor)."""
+    def psnr(self, theta_g, N=None):
+        """theta_g: the first 11 N entries of a parameter vector (CUDA tensor);
+        N: its Gaussian count when it changed since the probe was made."""
+        if N is not None:
+            self._resize(N)
         self.ctx.theta[:11 * self.N].copy_(theta_g[:11 * self.N])
         gsvr.gsvr_forward(self.ctx.ctx)
         mse = self.ctx.loss()
@@ -176,7 +194,7 @@ class Reconstruction:
         dev_s = 0.0
         t_hit = None
         if probe is not None:
-            hist.append((0, 0.0, None, probe.psnr(self.ctx.theta)))
+            hist.append((0, 0.0, None, probe.psnr(self.ctx.theta, self.ctx.N)))
         done = 0
         while done < iters:
             n = min(eval_every, iters - done)
@@ -193,7 +211,7 @@ class Reconstruction:
                 gsvr.gsvr_sync_status(self.ctx.ctx)
                 ensure_room(self.ctx)
             loss = self.ctx.loss()
-            p = probe.psnr(self.ctx.theta) if probe is not None else None
+            p = probe.psnr(self.ctx.theta, self.ctx.N) if probe is not None else None
             hist.append((done, dev_s, loss, p))
             if t_hit is None and target_psnr is not None and p is not None and p >= target_psnr:
                 t_hit = dev_s

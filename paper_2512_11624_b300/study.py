@@ -6,6 +6,7 @@
   python -m paper_2512_11624_b300.study cnnbench [--batch 256] [--steps 50]
   python -m paper_2512_11624_b300.study init [--model plain|topk] [--density-scales] [--lambdas 0 0.5 1] [--out FILE]
   python -m paper_2512_11624_b300.study metrics [--h 0.8 0.5 0.4]
+  python -m paper_2512_11624_b300.study densify [--h0 2.4] [--every 50] [--frac 0.5] [--out FILE]
 
 `batched`: the batched multi-subject workload (`inputs.batched`: 16 subjects of
 uneven size).  Every subject is first reconstructed alone (its own context with
@@ -529,6 +530,83 @@ def run_init(args):
         json.dump(out, open(args.out, "w"), indent=1)
 
 
+def run_densify(args):
+    """Coarse-to-fine densification (the paper's future work, after 3D
+    Gaussian Splatting) against the 0.8 mm grid start on the fetal workload,
+    plain sum, both in growth mode (capacities follow the Gaussian count).
+    "grid": 200,480 Gaussians on the 0.8 mm grid, scale 0.8 mm.  "coarse":
+    Gaussians on a `h0`-mm grid with scale h0, then every `every` iterations
+    until `stop` the fraction `frac` of Gaussians with the largest mean
+    ||dL/dmu|| (the threshold is that quantile of the statistics) is split
+    (largest scale above `split_mm`) or cloned, until the grid's count.  Both
+    start from one flat amplitude (the mean observed brain intensity) times
+    the plain sum's factor h^3 / ((2 pi)^(3/2) s^3).  Reported: the Gaussian
+    count and PSNR every `eval_every` iterations, device seconds of the
+    iterations and of the densifications (CUDA events), and PSNR / SSIM / NCC
+    after `iters` iterations."""
+    import torch
+    from . import gsvr, inputs
+    from .recon import PSNRProbe, Reconstruction
+    torch.cuda.set_device(0)
+    flat = inputs.fetal(args.seed, init="flat")
+    N_grid = flat["N"]
+    I, mask = flat["I"], flat["mask"]
+    level = float(np.mean(I[mask > 0][I[mask > 0] > 0.2]))
+    out = []
+    for name in ("grid", "coarse"):
+        case = dict(flat)
+        if name == "coarse":
+            g, N = inputs.grid_gaussians(flat["phantom"], h=args.h0, s=args.h0)
+            g = g.reshape(11, N)
+            g[10] = level / (2 * np.pi) ** 1.5
+            case["N"] = N
+            case["theta"] = np.concatenate([g.reshape(-1), flat["theta"][11 * N_grid:]]).astype(np.float32)
+        rec = Reconstruction(case, n_sample=args.n_sample)
+        probe = PSNRProbe(case["phantom"], case["N"])
+        ctx = rec.ctx
+        hist = [(0, 0.0, int(ctx.N), probe.psnr(ctx.theta, ctx.N))]
+        dev_s = dens_s = 0.0
+        events = []
+        for it in range(1, args.iters + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(rec.stream)
+            rec.step()
+            if name == "coarse":
+                gsvr.gsvr_densify_accumulate(ctx.ctx)
+            e1.record(rec.stream)
+            events.append((e0, e1))
+            if name == "coarse" and it % args.every == 0 and it <= args.stop and ctx.N < N_grid:
+                for a, b in events:
+                    b.synchronize()
+                    dev_s += a.elapsed_time(b) / 1e3
+                events = []
+                acc, cnt = gsvr.gsvr_densify_stats(ctx.ctx, ctx.N)
+                thr = float(np.quantile(acc[:, 0] / max(cnt, 1), 1.0 - args.frac))
+                d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                d0.record(rec.stream)
+                res = ctx.densify(thr, float(np.log(args.split_mm)), max_gaussians=N_grid)
+                d1.record(rec.stream)
+                d1.synchronize()
+                dens_s += d0.elapsed_time(d1) / 1e3
+                print(json.dumps({"iteration": it, "densify": res, "threshold": thr}), flush=True)
+            if it % args.eval_every == 0:
+                for a, b in events:
+                    b.synchronize()
+                    dev_s += a.elapsed_time(b) / 1e3
+                events = []
+                hist.append((it, dev_s, int(ctx.N), probe.psnr(ctx.theta, ctx.N)))
+        m = probe.metrics(ctx.theta, ctx.N)
+        row = {"start": name, "h0_mm": args.h0 if name == "coarse" else 0.8, "N_start": int(case["N"]),
+               "N_end": int(ctx.N), "iters": args.iters, "seconds": dev_s, "densify_seconds": dens_s,
+               "history": hist, "end": {"psnr": m[0], "ssim": m[1], "ncc": m[2]}}
+        print(json.dumps(row), flush=True)
+        out.append(row)
+        probe.close()
+        rec.close()
+    if args.out:
+        json.dump(out, open(args.out, "w"), indent=1)
+
+
 def run_metrics_bench(args):
     """Device time of gsvr_volume_metrics on evaluation grids of the fetal
     phantom (0.8 mm and finer), with the float64 DFMA throughput it reaches
@@ -634,12 +712,25 @@ def main():
     it.add_argument("--k", type=int, default=50)
     it.add_argument("--density-scales", action="store_true")
     it.add_argument("--out", default="")
+    dn = sub.add_parser("densify")
+    dn.add_argument("--h0", type=float, default=2.4)
+    dn.add_argument("--every", type=int, default=50)
+    dn.add_argument("--stop", type=int, default=400)
+    dn.add_argument("--frac", type=float, default=0.5)
+    dn.add_argument("--split-mm", type=float, default=1.2)
+    dn.add_argument("--iters", type=int, default=600)
+    dn.add_argument("--eval-every", type=int, default=50)
+    dn.add_argument("--n-sample", type=int, default=1 << 18)
+    dn.add_argument("--seed", type=int, default=0)
+    dn.add_argument("--out", default="")
     mb = sub.add_parser("metrics")
     mb.add_argument("--h", type=float, nargs="+", default=[0.8, 0.5, 0.4])
     mb.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
     if args.cmd == "init":
         run_init(args)
+    elif args.cmd == "densify":
+        run_densify(args)
     elif args.cmd == "metrics":
         run_metrics_bench(args)
     elif args.cmd == "topk":
