@@ -35,13 +35,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Gaussian-pixel pairs/s & slice px/s; sec to fixed PSNR vs plain, 1 B300"
 UNIT = "pairs/s"
-# Algorithmic issue slots per (sampled pixel, record) pair of the tile kernels in
-# their row form (row terms formed once per row and amortised away):
-#   forward  db = b - cb; q = (A db + C2 da) db + B da^2 (2 FFMA); ex2; sum += w e   -> 4 FP32 + 1 MUFU
-#   backward db; q (2 FFMA); ex2; g = r e; row sums g, g db, g db^2 (FADD, FMUL+FADD, FFMA) -> 8 FP32 + 1 MUFU
-# The MUFU ex2 rate (~32/clk/SM measured) is a quarter of the FP32 issue rate, so
-# the pairs are FP32-issue bound: peak pairs/s = measured FFMA instr/s / slots.
-ISSUE_PER_PAIR = {"fwd_eval": 5.0, "bwd_eval": 9.0}
+# Algorithmic work per (sampled pixel, record) pair of the tile kernels in their
+# row form (row terms formed once per row and amortised away):
+#   forward  db = b - cb; q = (A db + C2 da) db + B da^2 (2 FFMA); ex2; sum += w e
+#            -> 4 FP32 + 1 MUFU, scalar instructions: 5 issue slots
+#   backward db; q (2 FFMA); ex2; g = r e; row sums g, g db, g db^2 (FADD, FMUL+FADD, FFMA)
+#            -> 8 FP32 lane operations + 1 MUFU, issued as packed f32x2 instructions
+#            (two records per thread side by side): 4 packed + 1 MUFU issue slots
+# Measured on B300: scalar FFMA issues at 4 warp instructions per clock per SM (the
+# issue limit), packed FFMA2 at half that rate (the same 128 FP32 lanes per clock),
+# MUFU ex2 at about a quarter.  So the scalar forward is issue bound (peak pairs/s =
+# FFMA instr/s / 5) and the packed backward FP32-pipe bound (peak = FFMA lane
+# operations/s / 8; its issue slots, 5, and its MUFU share are below that).
+PAIR_BOUND = {"fwd_eval": ("FP32 issue", 5.0), "bwd_eval": ("FP32 pipe", 8.0)}
 
 
 def parse():
@@ -337,19 +343,22 @@ def main():
 
     # roofline of the dominant tile kernel (FP32 issue bound), peak measured on this GPU now
     ffma_s, ex2_s, n_sm = gsvr.gsvr_alu_peaks(dev)
+    ffma2_s = gsvr.gsvr_ffma2_peak(dev)
     f_mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0
     dom = max(("fwd_eval", "bwd_eval"), key=lambda s: kt["ms"][s])
     avg_ms = kt["ms"][dom] / max(kt["calls"][dom], 1)
     pairs_per_launch = eval_per_step
     achieved = pairs_per_launch / (avg_ms / 1e3) / 1e9
-    peak = ffma_s / ISSUE_PER_PAIR[dom] / 1e9
+    bound_name, per_pair = PAIR_BOUND[dom]
+    peak = ffma_s / per_pair / 1e9
     traffic = profiled_traffic({"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
                                "%s-%dx%d" % (args.workload, shape.tile_h, shape.tile_w))
     roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
                 "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "peak_basis": "measured FFMA rate %.3e instr/s (%d SMs, ex2.approx %.3e/s) / %.0f issue slots per "
-                              "sampled (pixel, record) pair" % (ffma_s, n_sm, ex2_s, ISSUE_PER_PAIR[dom])}
+                "peak_basis": "%s bound: measured FFMA rate %.3e instr/s (%d SMs; packed FFMA2 %.3e instr/s, "
+                              "ex2.approx %.3e/s) / %.0f per sampled (pixel, record) pair"
+                              % (bound_name, ffma_s, n_sm, ffma2_s, ex2_s, per_pair)}
 
     # end to end through the host-buffer call
     e2e = None

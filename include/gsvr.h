@@ -432,6 +432,13 @@ gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex2_per_s, do
  * Synchronous; allocates a 1 KB buffer. */
 gsvr_status gsvr_fp64_peak(int device, double *dfma_per_s);
 
+/* Measurement helper (not part of the method): packed two-wide float32 FMA
+ * (PTX fma.rn.f32x2) throughput of the whole device in instructions per
+ * second (each instruction two FMAs), measured the same way; with the FFMA
+ * rate it fixes the roofline of tile kernels that use packed arithmetic.
+ * Synchronous; allocates a 1 KB buffer. */
+gsvr_status gsvr_ffma2_peak(int device, double *ffma2_per_s);
+
 /* Coarse-to-fine densification: split, clone and prune of the Gaussians.  The
  * paper names progressive densification (after 3D Gaussian Splatting, Kerbl
  * et al. 2023) as future work ("Limitations and Future Work": start with few

@@ -929,12 +929,14 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 }
 
 // ---------------------------------------------------------------- backward
-// One CTA per work item, thread per record (two records per thread).  The
-// tile's r_bar values sit densely in shared memory (0 for pixels outside the
-// sample) and are read as broadcasts row by row.  Per row the record's row
-// terms are formed once and three row sums sum g, g db, g db^2 accumulate
-// (g = r_bar exp2(q)); at the end of the row they fold into the 6 moments
-// sum g, g db, g da, g db^2, g db da, g da^2, written to the record's key slot.
+// One CTA per work item, thread per record (two records per thread, evaluated
+// side by side in the two lanes of packed f32x2 instructions).  The tile's
+// r_bar values sit densely in shared memory (0 for pixels outside the sample),
+// each stored twice so one 64-bit load feeds both lanes, and are read as
+// broadcasts row by row.  Per row the record's row terms are formed once and
+// three row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q)); at the
+// end of the row they fold into the 6 moments sum g, g db, g da, g db^2,
+// g db da, g da^2, written to the record's key slot.
 __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, float R2, float dy) {
     m[0] += R0;
     m[1] += R1;
@@ -945,7 +947,7 @@ __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, flo
 }
 
 __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
-    extern __shared__ float rb[];  // tile_h x tile_w
+    extern __shared__ float2 rb2[];  // tile_h x tile_w, each r_bar duplicated for the packed lanes
     __shared__ int s_item;
     __shared__ int row_lo[32], row_hi[32];  // sampled column range per tile row (lo > hi: none)
     const int n_items = min(*a.n_items, a.cap_items);
@@ -975,7 +977,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             A = a.rec[refA.x];
             B = a.rec[refB.x];
         }
-        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb[k] = 0.f;
+        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb2[k] = make_float2(0.f, 0.f);
         if (threadIdx.x < 32) {
             row_lo[threadIdx.x] = 32;
             row_hi[threadIdx.x] = -1;
@@ -986,7 +988,8 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             const int loc = p - S.pix_base;
             const int r0 = loc / S.W;
             const int rr = r0 - tg.y0, cc = loc - r0 * S.W - tg.x0;
-            rb[rr * tw + cc] = a.rbar[p];
+            const float g = a.rbar[p];
+            rb2[rr * tw + cc] = make_float2(g, g);
             atomicMin(&row_lo[rr], cc);
             atomicMax(&row_hi[rr], cc);
         }
@@ -994,39 +997,35 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
         if (!v0) continue;
         float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float colf0 = (float)tg.x0 - S.cx0;
+        // records A and B side by side in the two lanes of packed float32
+        // operations: per column one shared load, 7 packed FP32 and 2 ex2 for
+        // the two (pixel, record) pairs
+        const float2 az = make_float2(A.a.z, B.a.z);
+        const float2 one = make_float2(1.f, 1.f);
         for (int row = 0; row < tg.rows; ++row) {
             const int c0 = row_lo[row], c1 = row_hi[row];  // rows and columns without samples are skipped
             if (c0 > c1) continue;
             const float rowf = (float)(tg.y0 + row) - S.cy0;
             const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
-            const float cA = A.a.w * dyA, bA = A.b.x * dyA * dyA;
-            const float cB = B.a.w * dyB, bB = B.b.x * dyB * dyB;
-            float A0 = 0.f, A1 = 0.f, A2 = 0.f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
-            const float *rrow = rb + row * tw;
+            const float2 cc = make_float2(A.a.w * dyA, B.a.w * dyB);
+            const float2 bb = make_float2(A.b.x * dyA * dyA, B.b.x * dyB * dyB);
+            float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
+            const float2 *rrow = rb2 + row * tw;
             const float colc = colf0 + (float)c0;
-            float dxA = colc - A.a.x, dxB = colc - B.a.x;  // advance by one pixel per column
+            float2 dx = make_float2(colc - A.a.x, colc - B.a.x);  // advance by one pixel per column
 #pragma unroll 4
             for (int col = c0; col <= c1; ++col) {
-                const float gg = rrow[col];
-                {
-                    const float e = gg * ex2_approx(fmaf(fmaf(A.a.z, dxA, cA), dxA, bA));
-                    const float ex = e * dxA;
-                    A0 += e;
-                    A1 += ex;
-                    A2 = fmaf(ex, dxA, A2);
-                }
-                {
-                    const float e = gg * ex2_approx(fmaf(fmaf(B.a.z, dxB, cB), dxB, bB));
-                    const float ex = e * dxB;
-                    B0 += e;
-                    B1 += ex;
-                    B2 = fmaf(ex, dxB, B2);
-                }
-                dxA += 1.f;
-                dxB += 1.f;
+                const float2 gg = rrow[col];
+                const float2 q = f2_fma(f2_fma(az, dx, cc), dx, bb);
+                const float2 e = f2_mul(gg, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+                const float2 ex = f2_mul(e, dx);
+                s0 = f2_add(s0, e);
+                s1 = f2_add(s1, ex);
+                s2 = f2_fma(ex, dx, s2);
+                dx = f2_add(dx, one);
             }
-            bwd_row_fold(mA, A0, A1, A2, dyA);
-            bwd_row_fold(mB, B0, B1, B2, dyB);
+            bwd_row_fold(mA, s0.x, s1.x, s2.x, dyA);
+            bwd_row_fold(mB, s0.y, s1.y, s2.y, dyB);
         }
         const int k0 = refA.y;
         a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
@@ -2134,7 +2133,7 @@ int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
     if (backward) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kThreads,
-                                                      (size_t)tile_w * tile_h * sizeof(float));
+                                                      (size_t)tile_w * tile_h * sizeof(float2));
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
@@ -2190,7 +2189,7 @@ void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
 void launch_backward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
     cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
-    k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float), st>>>(a);
+    k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float2), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,

@@ -34,7 +34,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
            "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means",
            "gsvr_volume_metrics", "gsvr_fp64_peak", "gsvr_densify_accumulate", "gsvr_densify_stats",
-           "gsvr_densify"]
+           "gsvr_densify", "gsvr_ffma2_peak"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -147,6 +147,7 @@ def _load():
         "gsvr_volume_metrics": ([C.c_int, vp, i64, i64, i64, vp, vp, vp, C.c_double, C.POINTER(C.c_double), vp,
                                  C.c_char_p, i32], C.c_int),
         "gsvr_fp64_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+        "gsvr_ffma2_peak": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
         "gsvr_densify_accumulate": ([vp], C.c_int),
         "gsvr_densify_stats": ([vp, vp, C.POINTER(i32), i32], C.c_int),
         "gsvr_densify": ([vp, C.POINTER(DensifyCfg), C.POINTER(i64)], C.c_int),
@@ -506,6 +507,13 @@ def gsvr_densify(ctx, grad_threshold, log_scale_threshold, prune_amplitude=0.0, 
     out = (C.c_int64 * 4)()
     _check(ctx, lib.gsvr_densify(ctx, C.byref(cfg), out))
     return tuple(int(x) for x in out)
+
+
+def gsvr_ffma2_peak(device=0):
+    """Packed float32 FMA (f32x2) instructions/s measured on `device`."""
+    d = C.c_double()
+    _check(None, lib.gsvr_ffma2_peak(int(device), C.byref(d)))
+    return d.value
 
 
 def gsvr_fp64_peak(device=0):
