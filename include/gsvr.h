@@ -183,7 +183,10 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx);
 /* Adjoint of the last forward: dL/dtheta for every Gaussian parameter and
  * every slice pose, recomputing each pair from the sorted tile lists (nothing
  * per pair is stored by the forward).  Requires a forward since the last
- * change of parameters, sample or observations. */
+ * change of parameters, sample or observations.  dL/dI_hat is read from the
+ * rbar buffer (gsvr_views) at the sampled pixels: the forward writes the
+ * loss's values there, and a caller may overwrite them (for example with the
+ * gradient of a downstream loss of the predictions) before this call. */
 gsvr_status gsvr_backward(gsvr_ctx *ctx);
 
 /* One Adam step (bias-corrected, no weight decay) on theta with the last

@@ -129,8 +129,7 @@ struct gsvr_ctx {
 
     // outputs
     DBuf<float> d_pred, d_rbar;
-    DBuf<float> d_rbar_s;  // r_bar in sample order (written by the forward for the backward)
-    DBuf<int> d_tpos_s;    // tile-local (row << 8 | col) in sample order
+    DBuf<int> d_tpos_s;    // tile-local (row << 8 | col) in sample order (written by the forward)
     DBuf<double> d_tile_loss, d_loss, d_pose_acc;
     DBuf<unsigned> d_status;
     DBuf<Counters> d_counters;
@@ -301,7 +300,6 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.I_obs = ctx->d_I.p;
     e.pred = ctx->d_pred.p;
     e.rbar = ctx->d_rbar.p;
-    e.rbar_s = ctx->d_rbar_s.p;
     e.tpos_s = ctx->d_tpos_s.p;
     e.tile_loss = ctx->d_tile_loss.p;
     e.mom = ctx->d_mom.p;
@@ -657,7 +655,6 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     CK(ctx->d_sampled.ensure(P));
     CK(ctx->d_pred.ensure(P));
     CK(ctx->d_rbar.ensure(P));
-    CK(ctx->d_rbar_s.ensure(P));
     CK(ctx->d_tpos_s.ensure(P));
     CK(ctx->d_tile_px_start.ensure(T));
     CK(ctx->d_tile_px_end.ensure(T));

@@ -893,10 +893,7 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         const SlwTerms st = slw_terms(a.slw, a.M, a.tile_slice[t], a.l1, wp, acc, a.I_obs[p]);
         a.pred[p] = st.pred;
         a.rbar[p] = st.dLdm;
-        if (a.rbar_s) {  // the backward's r_bar tile, in sample order
-            a.rbar_s[s] = st.dLdm;
-            a.tpos_s[s] = ((r0 - tg.y0) << 8) | (loc - r0 * S.W - tg.x0);
-        }
+        if (a.tpos_s) a.tpos_s[s] = ((r0 - tg.y0) << 8) | (loc - r0 * S.W - tg.x0);  // for the backward
         l = st.loss;
         gs = (double)st.gsig;
         go = (double)st.gomg;
@@ -988,9 +985,10 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
         }
         __syncthreads();
         for (int s2 = ps + threadIdx.x; s2 < pe; s2 += kThreads) {
-            // two independent loads per sampled pixel (written by the forward)
+            // r_bar from the per-pixel buffer (a caller may have replaced the
+            // forward's values there); the tile-local position from the forward
             const int rc = a.tpos_s[s2];
-            const float g = a.rbar_s[s2];
+            const float g = a.rbar[a.sampled[s2]];
             const int rr = rc >> 8, cc = rc & 255;
             rb2[rr * tw + cc] = make_float2(g, g);
             atomicMin(&row_lo[rr], cc);

@@ -57,8 +57,7 @@ struct EvalArgs {
     const int *n_sampled;
     const float *I_obs;        // per global pixel
     float *pred, *rbar;        // per global pixel
-    float *rbar_s;             // r_bar per sample position (null: not written)
-    int *tpos_s;               // tile-local (row << 8 | col) per sample position (with rbar_s)
+    int *tpos_s;               // tile-local (row << 8 | col) per sample position (null: not written)
     double *tile_loss;         // per tile
     float4 *mom;               // 2 per key (backward)
     Counters *counters;
