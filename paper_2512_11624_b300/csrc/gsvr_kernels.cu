@@ -1723,156 +1723,241 @@ __device__ __forceinline__ void topk_psf(const SliceDev &S, float sp[6]) {
     sp[5] = e(1, 2);
 }
 
-// Forward: thread per sample (blocks of 128 threads, 64 when K > 64 so that the
-// heaps fit shared memory).  The K nearest are kept in a max-heap (by
-// (d^2, j)) in shared memory, column `tid` of hd / hj (stride blockDim.x).
-// Candidates are the cell-ordered means of the last grid build (one 16-byte
-// read each); once the heap is full, a cell whose box lies farther than the
-// heap's largest distance is skipped without reading it.  Shells of cells at
-// Chebyshev distance 0, 1, 2, ... around the pixel's cell are scanned until
-// the heap is full and its largest distance is inside the box the scanned
-// shells cover (or the whole grid has been scanned).
+// Forward: a warp per sample.  Block b owns samples [128 b, 128 b + 128); its
+// warp w takes samples 128 b + w, + 4, ... in order.  The K nearest means of
+// the sample's world position x are kept in shared memory as a sorted list of
+// 64-bit keys (d^2 bits << 32 | j): ordering keys orders by (d^2, j), the
+// smaller index winning ties.  Candidates are the cell-ordered means of the
+// last grid build; the lanes test 32 at a time (one 16-byte read each)
+// against the list's largest key (every candidate passes
+// until the list holds K); the passing keys are sorted across the warp by a
+// shuffle bitonic network and merged into the list by ranks (binary searches),
+// keeping the K smallest; passing keys are staged and merged 32 at a time, and
+// before each stopping test.  Distances are float32 about the corner of x's cell
+// (x - o in float64 once per sample, mu - o in float32 per candidate: errors of
+// a few 1e-7 mm at millimetre distances).  Cells are visited in shells of
+// Chebyshev distance 0, 1, 2, ... around x's cell, 32 cells of a shell at a
+// time (lane l tests cell l and reads its range; each round takes one
+// candidate of its own cell per lane); once the list is full a cell whose box
+// lies farther than its largest distance is skipped unread; the search stops
+// when the list is full and its largest distance is at most the distance from
+// x to the nearest face of the scanned box with grid cells beyond it (every
+// unscanned mean lies beyond such a face), or when no such face is left.  The ratio
+// is then formed over the neighbours in parallel across the lanes, with
+// float64 sums reduced in a fixed order.
+constexpr int kTopkWarps = kTopkThreads / 32;
+
+struct TopkList {
+    unsigned long long *cur, *alt;  // sorted keys (cur) and the merge target (alt)
+    unsigned long long *stage;      // the round's sorted keys (32)
+    int cnt;                        // keys held (warp-uniform)
+    unsigned long long tau;         // largest key when cnt == K, else all ones
+};
+
+// Merge this round's passing keys (one per lane, all ones where none) into the list.
+__device__ __forceinline__ void topk_merge(TopkList &T, unsigned long long v, int m, int K, int lane) {
+    // ascending bitonic sort of the 32 lanes' keys (all-ones keys sort last)
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, stride);
+            const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+            v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
+        }
+    T.stage[lane] = v;
+    __syncwarp();
+    const int n = T.cnt;
+    // the round's key i goes to i + (list keys below it)
+    if (lane < m) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T.cur[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        const int pos = lane + lo;
+        if (pos < K) T.alt[pos] = v;
+    }
+    // list key e goes to e + (round keys below it)
+    for (int e = lane; e < n; e += 32) {
+        const unsigned long long x = T.cur[e];
+        int lo = 0, hi = m;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T.stage[mid] < x) lo = mid + 1;
+            else hi = mid;
+        }
+        const int pos = e + lo;
+        if (pos < K) T.alt[pos] = x;
+    }
+    __syncwarp();
+    unsigned long long *t = T.cur;
+    T.cur = T.alt;
+    T.alt = t;
+    T.cnt = min(n + m, K);
+    T.tau = T.cnt == K ? T.cur[K - 1] : ~0ull;
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kTopkThreads) k_topk_fwd(TopkArgs a) {
-    extern __shared__ unsigned char topk_raw[];
-    const int BS = blockDim.x;  // heap stride
-    float *hd = reinterpret_cast<float *>(topk_raw);
-    int *hj = reinterpret_cast<int *>(hd + a.K * BS);
-    __shared__ double red[kTopkThreads / 32];
-    const int tid = threadIdx.x;
+    __shared__ unsigned long long s_list[kTopkWarps][2][kTopkMaxK];
+    __shared__ unsigned long long s_stage[kTopkWarps][32];
+    __shared__ unsigned long long s_pend[kTopkWarps][64];  // passing keys not merged yet
+    __shared__ double red[kTopkWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ns = min(*a.n_sampled, a.cap_px);
-    const int s = blockIdx.x * BS + tid;
-    double l = 0.0;
-    if (s < ns) {
+    const int N = a.N, K = a.K;
+    double lsum = 0.0;  // lane 0: this warp's losses, in sample order
+    for (int t = w; t < kTopkThreads; t += kTopkWarps) {
+        const int s = blockIdx.x * kTopkThreads + t;
+        if (s >= ns) break;
         const int p = a.sampled[s];
         const TopkPixel q = topk_pixel(a, p);
-        const TopkGrid g = *a.grid;
-        const int N = a.N, K = a.K;
-        float *d = hd + tid;
-        int *jj = hj + tid;
-        auto less = [](float d1, int j1, float d2, int j2) { return d1 < d2 || (d1 == d2 && j1 < j2); };
-        int cnt = 0;
-        auto offer = [&](float d2, int j) {
-            if (cnt < K) {  // push, sift up
-                int pos = cnt++;
-                while (pos > 0) {
-                    const int par = (pos - 1) >> 1;
-                    const float dp = d[par * BS];
-                    const int jp = jj[par * BS];
-                    if (!less(dp, jp, d2, j)) break;
-                    d[pos * BS] = dp;
-                    jj[pos * BS] = jp;
-                    pos = par;
-                }
-                d[pos * BS] = d2;
-                jj[pos * BS] = j;
-            } else if (less(d2, j, d[0], jj[0])) {  // replace the largest, sift down
-                int pos = 0;
-                for (;;) {
-                    int ch = 2 * pos + 1;
-                    if (ch >= K) break;
-                    if (ch + 1 < K && less(d[ch * BS], jj[ch * BS], d[(ch + 1) * BS],
-                                           jj[(ch + 1) * BS]))
-                        ++ch;
-                    const float dc = d[ch * BS];
-                    const int jc = jj[ch * BS];
-                    if (!less(d2, j, dc, jc)) break;
-                    d[pos * BS] = dc;
-                    jj[pos * BS] = jc;
-                    pos = ch;
-                }
-                d[pos * BS] = d2;
-                jj[pos * BS] = j;
-            }
-        };
-        int c[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) c[k] = topk_cell_axis(g, k, (float)q.x[k]);
-        const float xf[3] = {(float)q.x[0], (float)q.x[1], (float)q.x[2]};
-        auto scan_cell = [&](int cx, int cy, int cz) {
-            if (cnt == K) {  // prune: squared distance from x to the cell's box
-                const int cc[3] = {cx, cy, cz};
-                float m2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float lo = g.org[k] + (float)cc[k] * g.h, hi = lo + g.h;
-                    const float dk = fmaxf(fmaxf(lo - xf[k], xf[k] - hi), 0.f);
-                    m2 = fmaf(dk, dk, m2);
-                }
-                if (m2 > d[0] * (1.0f + 1e-5f)) return;
-            }
-            const int cell = (cz * g.n[1] + cy) * g.n[0] + cx;
-            const int k1 = a.cell_end[cell];
-            for (int k = a.cell_start[cell]; k < k1; ++k) {
-                const float4 m = a.gm[k];
-                const float vx = (float)(q.x[0] - (double)m.x);
-                const float vy = (float)(q.x[1] - (double)m.y);
-                const float vz = (float)(q.x[2] - (double)m.z);
-                offer(vx * vx + vy * vy + vz * vz, __float_as_int(m.w));
-            }
-        };
-        for (int sh = 0; N > 0; ++sh) {  // (no grid is built without Gaussians)
-            const int z0 = max(c[2] - sh, 0), z1 = min(c[2] + sh, g.n[2] - 1);
-            const int y0 = max(c[1] - sh, 0), y1 = min(c[1] + sh, g.n[1] - 1);
-            for (int cz = z0; cz <= z1; ++cz)
-                for (int cy = y0; cy <= y1; ++cy) {
-                    if (abs(cz - c[2]) == sh || abs(cy - c[1]) == sh) {
-                        const int x0 = max(c[0] - sh, 0), x1 = min(c[0] + sh, g.n[0] - 1);
-                        for (int cx = x0; cx <= x1; ++cx) scan_cell(cx, cy, cz);
-                    } else {
-                        if (c[0] - sh >= 0) scan_cell(c[0] - sh, cy, cz);
-                        if (sh > 0 && c[0] + sh < g.n[0]) scan_cell(c[0] + sh, cy, cz);
-                    }
-                }
-            bool all = true;
-            float rho = 3.4e38f;
+        TopkList T{s_list[w][0], s_list[w][1], s_stage[w], 0, ~0ull};
+        if (N > 0) {  // (no grid is built without Gaussians)
+            const TopkGrid g = *a.grid;
+            int c[3];
+            float o[3], xo[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                all = all && c[k] - sh <= 0 && c[k] + sh >= g.n[k] - 1;
-                const float lo = g.org[k] + (float)(c[k] - sh) * g.h, hi = g.org[k] + (float)(c[k] + sh + 1) * g.h;
-                rho = fminf(rho, fminf((float)q.x[k] - lo, hi - (float)q.x[k]));
+                c[k] = topk_cell_axis(g, k, (float)q.x[k]);
+                o[k] = g.org[k] + (float)c[k] * g.h;
+                xo[k] = (float)(q.x[k] - (double)o[k]);
             }
-            if (all) break;
-            if (cnt == K && rho > 0.f && d[0] <= rho * rho) break;
+            // passing keys are staged and merged 32 at a time (and before every
+            // stopping test), so the list's largest key tightens at each merge
+            unsigned long long *P = s_pend[w];
+            int pc = 0;
+            auto flush = [&]() {
+                for (int h = 0; h < pc; h += 32) {
+                    const int m = min(pc - h, 32);
+                    topk_merge(T, lane < m ? P[h + lane] : ~0ull, m, K, lane);
+                }
+                pc = 0;
+            };
+            for (int sh = 0;; ++sh) {
+                // the cells of shell sh (Chebyshev distance sh from c, clipped to
+                // the grid), 32 at a time: lane l tests and reads cell l of the batch
+                int lo3[3], n3[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    lo3[k] = max(c[k] - sh, 0);
+                    n3[k] = min(c[k] + sh, g.n[k] - 1) - lo3[k] + 1;
+                }
+                const int total = n3[0] * n3[1] * n3[2];
+                for (int b0 = 0; b0 < total; b0 += 32) {
+                    const int idx = b0 + lane;
+                    int k0 = 0, k1 = 0;
+                    if (idx < total) {
+                        const int cx = lo3[0] + idx % n3[0], cy = lo3[1] + (idx / n3[0]) % n3[1];
+                        const int cz = lo3[2] + idx / (n3[0] * n3[1]);
+                        const int cc[3] = {cx, cy, cz};
+                        const int cheb = max(max(abs(cx - c[0]), abs(cy - c[1])), abs(cz - c[2]));
+                        bool take = cheb == sh;
+                        if (take && T.cnt == K) {  // prune: squared distance from x to the cell's box
+                            float m2 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float lo = (float)(cc[k] - c[k]) * g.h, hi = lo + g.h;
+                                const float dk = fmaxf(fmaxf(lo - xo[k], xo[k] - hi), 0.f);
+                                m2 = fmaf(dk, dk, m2);
+                            }
+                            take = m2 <= __uint_as_float((unsigned)(T.tau >> 32)) * (1.0f + 1e-5f);
+                        }
+                        if (take) {
+                            const int cell = (cz * g.n[1] + cy) * g.n[0] + cx;
+                            k0 = a.cell_start[cell];
+                            k1 = a.cell_end[cell];
+                        }
+                    }
+                    // rounds: one candidate of its own cell per lane
+                    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)(k1 - k0));
+                    for (int r = 0; r < rounds; ++r) {
+                        const int k = k0 + r;
+                        unsigned long long key = ~0ull;
+                        if (k < k1) {
+                            const float4 m = a.gm[k];
+                            const float vx = xo[0] - (m.x - o[0]), vy = xo[1] - (m.y - o[1]), vz = xo[2] - (m.z - o[2]);
+                            const float d2 = fmaf(vz, vz, fmaf(vy, vy, vx * vx));
+                            key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__float_as_int(m.w);
+                        }
+                        const bool pass = key < T.tau;
+                        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                        if (bal) {
+                            if (pass) P[pc + __popc(bal & ((1u << lane) - 1u))] = key;
+                            pc += __popc(bal);
+                            __syncwarp();
+                            if (pc >= 32) flush();
+                        }
+                    }
+                }
+                if (pc > 0) flush();
+                // unscanned cells lie beyond the faces of the scanned box that have
+                // grid cells beyond them; rho = distance from x to the nearest such face
+                bool all = true;
+                float rho = 3.4e38f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if (c[k] - sh > 0) {
+                        all = false;
+                        rho = fminf(rho, xo[k] + (float)sh * g.h);
+                    }
+                    if (c[k] + sh < g.n[k] - 1) {
+                        all = false;
+                        rho = fminf(rho, (float)(sh + 1) * g.h - xo[k]);
+                    }
+                }
+                if (all) break;
+                if (T.cnt == K && rho > 0.f && __uint_as_float((unsigned)(T.tau >> 32)) <= rho * rho) break;
+            }
         }
-        // the ratio over the neighbours
+        // the ratio over the neighbours, lanes in parallel
+        const int cnt = T.cnt;
         const SliceDev &S = a.slices[q.i];
         float sp[6];
         topk_psf(S, sp);
         double num = 0.0, den = 0.0;
-        for (int e = 0; e < cnt; ++e) {
-            const int j = jj[e * BS];
+        for (int e = lane; e < cnt; e += 32) {
+            const int j = (int)(unsigned)(T.cur[e] & 0xffffffffull);
             const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
             const TopkChol L = topk_chol(g0, g1, sp);
-            float w[3];
+            float wv[3];
             topk_fsub(L, (float)(q.x[0] - (double)a.theta[j]), (float)(q.x[1] - (double)a.theta[(size_t)N + j]),
-                      (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]), w);
-            const float E = expf(-0.5f * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+                      (float)(q.x[2] - (double)a.theta[2 * (size_t)N + j]), wv);
+            const float E = expf(-0.5f * (wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]));
             num += (double)g1.w * (double)E;
             den += (double)E;
             a.nbr[(size_t)s * K + e] = j;
         }
-        a.ncnt[s] = cnt;
-        const float D = (float)(den + (double)a.delta);
-        const float Ih = (float)(num / (den + (double)a.delta));
-        const float w = 1.0f / (float)max(ns, 1);
-        const SlwTerms st = slw_terms(a.slw, a.M, q.i, a.l1, w, Ih, a.I_obs[p]);
-        a.pred[p] = st.pred;
-        a.rbar[p] = st.dLdm;
-        a.pstat[s] = make_float2(Ih, D);  // the ratio before sigma_i: the backward's I_hat
-        l = st.loss;
-        if (a.slw) {
-            atomicAdd(&a.slw_gacc[q.i], (double)st.gsig);
-            atomicAdd(&a.slw_gacc[a.M + q.i], (double)st.gomg);
-        }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((tid & 31) == 0) red[tid >> 5] = l;
+        for (int off = 16; off > 0; off >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, off);
+            den += __shfl_xor_sync(0xffffffffu, den, off);
+        }
+        if (lane == 0) {
+            a.ncnt[s] = cnt;
+            const float D = (float)(den + (double)a.delta);
+            const float Ih = (float)(num / (den + (double)a.delta));
+            const float wp = 1.0f / (float)max(ns, 1);
+            const SlwTerms st = slw_terms(a.slw, a.M, q.i, a.l1, wp, Ih, a.I_obs[p]);
+            a.pred[p] = st.pred;
+            a.rbar[p] = st.dLdm;
+            a.pstat[s] = make_float2(Ih, D);  // the ratio before sigma_i: the backward's I_hat
+            lsum += st.loss;
+            if (a.slw) {
+                atomicAdd(&a.slw_gacc[q.i], (double)st.gsig);
+                atomicAdd(&a.slw_gacc[a.M + q.i], (double)st.gomg);
+            }
+        }
+        __syncwarp();  // the list is free for the next sample
+    }
+    if (lane == 0) red[w] = lsum;
     __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < BS / 32; ++w) t += red[w];
-        a.loss_part[blockIdx.x] = t;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < kTopkWarps; ++k) tot += red[k];
+        a.loss_part[blockIdx.x] = tot;
     }
 }
 __global__ void __launch_bounds__(256) k_topk_loss_total(const double *__restrict__ part, int nb, double *loss,
@@ -2362,11 +2447,8 @@ void launch_topk_gather_means(const float *theta, const uint32_t *gidx, int N, f
     counted();
 }
 void launch_topk_forward(const TopkArgs &a, int cap_px, double *loss, cudaStream_t st) {
-    const int bs = a.K > 64 ? 64 : kTopkThreads;
-    const int nb = std::max(1, cdiv(cap_px, bs));
-    const size_t smem = (size_t)a.K * bs * (sizeof(float) + sizeof(int));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_topk_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_topk_fwd<<<nb, bs, smem, st>>>(a);
+    const int nb = std::max(1, cdiv(cap_px, kTopkThreads));
+    k_topk_fwd<<<nb, kTopkThreads, 0, st>>>(a);
     k_topk_loss_total<<<1, 256, 0, st>>>(a.loss_part, nb, loss, a.status);
     counted(2);
 }
