@@ -11,7 +11,11 @@ Prints one JSON line.  `value` counts (pixel, Gaussian) pairs inside the
 1e-7 cut (the pairs the method needs) per second of whole-step device time;
 `px_per_s` counts sampled slice pixels.  `e2e` is the same metric through the
 host-buffer C-ABI call (gsvr_step_host: parameters and pixel list uploaded
-from pinned memory, gradient and loss read back every step).
+from pinned memory, gradient and loss read back every step).  The timed
+region launches each step's kernels eagerly (with stage events, from which the
+roofline's kernel time comes); `graph` times the same step replayed as one
+CUDA graph per iteration (gsvr_graph_capture / gsvr_graph_launch), separately
+after it.
 
 --impl reference times the FP64 brute-force CPU oracle on bounded pixel
 samples of the same workload (the oracle is this project's reference program).
@@ -360,6 +364,28 @@ def main():
                               "ex2.approx %.3e/s) / %.0f per sampled (pixel, record) pair"
                               % (bound_name, ffma_s, n_sm, ffma2_s, ex2_s, per_pair)}
 
+    # the same step replayed as one CUDA graph per iteration (gsvr_graph_capture /
+    # gsvr_graph_launch: sampler, forward, backward, Adam, no host launches),
+    # timed separately after the eager timed region
+    kg = max(3, min(args.steps, 500))
+    gsvr.gsvr_graph_capture(ctx.ctx, n_s if sampled else -1)
+    gsvr.gsvr_set_step(ctx.ctx, args.warmup + args.steps + 3)
+    gsvr.gsvr_graph_launch(ctx.ctx, 3)
+    gsvr.gsvr_sync_status(ctx.ctx)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    gsvr.gsvr_graph_launch(ctx.ctx, kg)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gsvr.gsvr_sync_status(ctx.ctx)
+    g_ms = reduce_max(g0.elapsed_time(g1), ws)
+    graph = {"ms_per_step": g_ms / kg, "value": reduce_sum(useful_per_step * kg, ws) / (g_ms / 1e3),
+             "unit": UNIT, "steps": kg}
+
     # end to end through the host-buffer call
     e2e = None
     if not args.no_e2e:
@@ -416,7 +442,7 @@ def main():
                 "useful_fraction": useful_frac,
                 "stage_ms_per_step": {k: v / args.steps for k, v in kt["ms"].items()},
                 "records_per_step": stats["n_records"], "keys_per_step": stats["n_keys"],
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "graph": graph, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": kt["kernel_launches"], "clocks": clk}
         print(json.dumps(line), flush=True)
     ctx.close()
