@@ -430,6 +430,24 @@ def main():
 
     if rank == 0:
         stats = ctx.stats()
+        # HBM-bound stages against the measured copy bandwidth: algorithmic bytes per
+        # step (prep: 44 B read + 40 B written per Gaussian; binning: ~68 B per slab
+        # candidate record (read 40, write 24, count 4) and 44 B per key (emit 8, two
+        # 8-bit radix passes of 8 B read + 8 B write, tile offset 4); Adam: 28 B per
+        # parameter) over the stage's CUDA-event time in the timed region
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
+        hbm_basis = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6400 GB/s"
+        hbm = float(hbm or 6400.0)
+        n_par = 11 * case["N"] + 6 * M
+        stage_bytes = {"prep": 84.0 * case["N"], "bin": 68.0 * stats["n_records"] + 44.0 * stats["n_keys"],
+                       "adam": 28.0 * n_par}
+        hbm_stages = {"peak_gbs": hbm, "peak_basis": hbm_basis}
+        for k, b in stage_bytes.items():
+            ms_k = kt["ms"][k] / max(args.steps, 1)
+            gbs = b / (ms_k / 1e3) / 1e9 if ms_k > 0 else None
+            hbm_stages[k] = {"bytes_per_step": b, "ms_per_step": ms_k, "achieved_gbs": gbs,
+                             "frac": gbs / hbm if gbs else None}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -442,7 +460,7 @@ def main():
                 "useful_fraction": useful_frac,
                 "stage_ms_per_step": {k: v / args.steps for k, v in kt["ms"].items()},
                 "records_per_step": stats["n_records"], "keys_per_step": stats["n_keys"],
-                "roofline": roofline, "graph": graph, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "hbm_stages": hbm_stages, "graph": graph, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": kt["kernel_launches"], "clocks": clk}
         print(json.dumps(line), flush=True)
     ctx.close()
