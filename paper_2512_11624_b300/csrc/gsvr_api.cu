@@ -71,6 +71,7 @@ struct gsvr_ctx {
     DBuf<float> d_I;
     DBuf<uint8_t> d_mask;
     DBuf<int> d_mask_tpos, d_mask_pix_sorted;
+    DBuf<int> d_pix_mrank;  // per pixel: rank among the masked pixels in tile order (-1: unmasked)
     std::vector<int> h_mask_tpos;
     int n_mask = 0;
 
@@ -415,12 +416,18 @@ gsvr_status sample_all(gsvr_ctx *ctx) {
     return finish_sample(ctx);
 }
 
-// Compact flagged tile-order positions into the sample.
+// Compact the flagged masked-rank positions into the sample (ranks follow the
+// tile order, so the sample comes out in tile order).
 gsvr_status compact_flags(gsvr_ctx *ctx) {
     cudaStream_t st = ctx->stream;
-    CK(scan_exclusive(ctx->d_flags.p, ctx->d_flag_pos.p, nullptr, (int)ctx->P, (int)ctx->P,
-                      &ctx->d_counters.p->n_sampled, scan_scratch(ctx), st));
-    launch_compact(ctx->d_flags.p, ctx->d_flag_pos.p, ctx->d_tile_sorted_pix.p, (int)ctx->P, ctx->d_sampled.p, st);
+    if (ctx->n_mask > 0) {
+        CK(scan_exclusive(ctx->d_flags.p, ctx->d_flag_pos.p, nullptr, ctx->n_mask, ctx->n_mask,
+                          &ctx->d_counters.p->n_sampled, scan_scratch(ctx), st));
+        launch_compact(ctx->d_flags.p, ctx->d_flag_pos.p, ctx->d_mask_pix_sorted.p, ctx->n_mask, ctx->d_sampled.p,
+                       st);
+    } else {
+        launch_set_count(&ctx->d_counters.p->n_sampled, 0, st);
+    }
     CK(cudaGetLastError());
     return finish_sample(ctx);
 }
@@ -706,6 +713,12 @@ gsvr_status gsvr_set_observations(gsvr_ctx *ctx, const float *I, const uint8_t *
         }
     }
     ctx->n_mask = (int)mtp.size();
+    {
+        std::vector<int> mrank((size_t)P, -1);
+        for (size_t q = 0; q < mps.size(); ++q) mrank[(size_t)mps[q]] = (int)q;
+        CK(ctx->d_pix_mrank.ensure((size_t)P));
+        CK(cudaMemcpy(ctx->d_pix_mrank.p, mrank.data(), sizeof(int) * (size_t)P, cudaMemcpyHostToDevice));
+    }
     CK(ctx->d_mask_tpos.ensure(mtp.size()));
     CK(ctx->d_mask_pix_sorted.ensure(mps.size()));
     if (!mtp.empty()) {
@@ -874,9 +887,9 @@ gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, 
         CK(cudaMemcpyAsync(ctx->d_idx.p, idx, sizeof(int) * n, cudaMemcpyHostToDevice, st));
         didx = ctx->d_idx.p;
     }
-    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
-    launch_flags_from_list(didx, (int)n, (int)ctx->P, ctx->d_mask.p, ctx->d_pix_tpos.p, ctx->d_flags.p,
-                           ctx->d_status.p, st);
+    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->n_mask, st));
+    launch_flags_from_list_rank(didx, (int)n, (int)ctx->P, ctx->d_pix_mrank.p, ctx->d_flags.p, ctx->d_status.p,
+                                st);
     CK(cudaGetLastError());
     return compact_flags(ctx);
 }
@@ -886,8 +899,8 @@ gsvr_status sample_ranges(gsvr_ctx *ctx, int n_ranges, const int *mask_first, co
                           uint64_t step, const unsigned long long *d_step) {
     cudaStream_t st = ctx->stream;
     stage_begin(ctx, GSVR_STAGE_SAMPLE);
-    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->P, st));
-    launch_sample_flags(n_ranges, mask_first, out_first, n_out, ctx->cfg.seed, step, d_step, ctx->d_mask_tpos.p,
+    CK(cudaMemsetAsync(ctx->d_flags.p, 0, sizeof(int) * ctx->n_mask, st));
+    launch_sample_flags(n_ranges, mask_first, out_first, n_out, ctx->cfg.seed, step, d_step, nullptr,
                         ctx->d_flags.p, st);
     CK(cudaGetLastError());
     gsvr_status s = compact_flags(ctx);

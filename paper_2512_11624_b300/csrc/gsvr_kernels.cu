@@ -354,7 +354,10 @@ __global__ void k_sample_flags(int n_subj, const int *__restrict__ mask_first, c
         }
         if (x < (unsigned long long)n_mask) break;
     }
-    if (x < (unsigned long long)n_mask) flags[mask_tpos[mask_first[sj] + (int)x]] = 1;
+    if (x < (unsigned long long)n_mask) {
+        const int m = mask_first[sj] + (int)x;  // rank among the masked pixels in tile order
+        flags[mask_tpos ? mask_tpos[m] : m] = 1;
+    }
 }
 
 __global__ void k_flags_from_list(const int *__restrict__ idx, int n, int n_pix, const uint8_t *__restrict__ mask,
@@ -367,6 +370,22 @@ __global__ void k_flags_from_list(const int *__restrict__ idx, int n, int n_pix,
         return;
     }
     if (mask[p]) flags[pix_tpos[p]] = 1;
+}
+
+// List sample in masked-rank space: pix_mrank[p] = rank of pixel p among the
+// masked pixels in tile order (-1 outside the mask).
+__global__ void k_flags_from_list_rank(const int *__restrict__ idx, int n, int n_pix,
+                                       const int *__restrict__ pix_mrank, int *__restrict__ flags,
+                                       unsigned *status) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int p = idx[k];
+    if (p < 0 || p >= n_pix) {
+        atomicOr(status, ST_INDEX);
+        return;
+    }
+    const int m = pix_mrank[p];
+    if (m >= 0) flags[m] = 1;
 }
 
 __global__ void k_compact(const int *__restrict__ flags, const int *__restrict__ pos,
@@ -2399,6 +2418,12 @@ void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mas
                             int *flags, unsigned *status, cudaStream_t st) {
     if (n <= 0) return;
     k_flags_from_list<<<cdiv(n, 256), 256, 0, st>>>(idx, n, n_pix, mask, pix_tpos, flags, status);
+    counted();
+}
+void launch_flags_from_list_rank(const int *idx, int n, int n_pix, const int *pix_mrank, int *flags,
+                                 unsigned *status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_flags_from_list_rank<<<cdiv(n, 256), 256, 0, st>>>(idx, n, n_pix, pix_mrank, flags, status);
     counted();
 }
 void launch_compact(const int *flags, const int *pos, const int *tile_sorted_pix, int n_pix, int *sampled,

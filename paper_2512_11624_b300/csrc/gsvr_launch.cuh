@@ -181,6 +181,8 @@ void launch_sample_flags(int n_subj, const int *mask_first, const int *out_first
                          cudaStream_t st);
 void launch_flags_from_list(const int *idx, int n, int n_pix, const uint8_t *mask, const int *pix_tpos,
                             int *flags, unsigned *status, cudaStream_t st);
+void launch_flags_from_list_rank(const int *idx, int n, int n_pix, const int *pix_mrank, int *flags,
+                                 unsigned *status, cudaStream_t st);
 void launch_compact(const int *flags, const int *pos, const int *tile_sorted_pix, int n_pix, int *sampled,
                     cudaStream_t st);
 void launch_tile_px_ranges(const int *sampled, const int *n_sampled, int cap, const int *pix_tile, int *start,
