@@ -365,7 +365,9 @@ def train(net, X, A, Y, epochs=20, batch=256, lr=1e-3, seed=0, val_frac=0.05, lo
 
 
 def predict(net, X, A, batch=256):
+    """Network outputs for X, A in batches of at most the network's max_batch."""
     import torch
+    batch = max(1, min(int(batch), net.max_batch))
     outs = [net.forward(X[s:s + batch].contiguous(), A[s:s + batch].contiguous()) for s in range(0, X.shape[0], batch)]
     return torch.cat(outs)
 
