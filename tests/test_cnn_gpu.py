@@ -203,3 +203,20 @@ def test_fit_reduces_loss(T):
         net.adam_step(t, lr=1e-3)
     assert L < 0.2 * first, (first, L)
     net.close()
+
+
+def test_predict_batches_within_max_batch(T):
+    """cnn.predict splits its input into batches of at most the network's
+    max_batch (whatever batch is asked) and gives each sample the output a
+    single-sample forward gives it."""
+    torch, cnn = T
+    rng = np.random.default_rng(12)
+    net = cnn.PoseNet(max_batch=4, seed=2)
+    x = torch.from_numpy(rng.uniform(0, 1, size=(10, 128, 128)).astype(np.float32)).cuda()
+    aux = torch.from_numpy(rng.normal(size=(10, 25)).astype(np.float32)).cuda()
+    out = cnn.predict(net, x, aux, batch=256).cpu().numpy()
+    assert out.shape == (10, 6)
+    for k in (0, 5, 9):
+        one = net.forward(x[k:k + 1].contiguous(), aux[k:k + 1].contiguous()).cpu().numpy()
+        assert np.allclose(out[k], one[0], rtol=1e-3, atol=1e-4)  # other batch shapes may take other GEMM paths
+    net.close()
