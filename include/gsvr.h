@@ -215,6 +215,20 @@ gsvr_status gsvr_sample_pixels_subjects(gsvr_ctx *ctx, int64_t n_per_subject, ui
  * subjects).  Synchronises. */
 gsvr_status gsvr_get_subject_losses(gsvr_ctx *ctx, double *out, int32_t n);
 
+/* Retire subjects from (active[k] = 0) or return them to (1) the batched
+ * sampler (gsvr_sample_pixels_subjects and captured iterations): a retired
+ * subject draws no pixels, so it adds no work and receives zero gradient, and
+ * its Adam moments (Gaussians and slice poses) are zeroed when it is retired,
+ * so Adam leaves its parameters unchanged (with the scale regulariser on, its
+ * Gaussians still follow the regulariser's gradient).  Its loss reads 0.  A
+ * subject returned to the sample restarts Adam from zero moments.  active:
+ * host array of n_subj flags, NULL = every subject active; at least one must
+ * stay active.  Drops a captured CUDA graph (the sample size changes: capture
+ * again).  Synchronises.  Errors: GSVR_ERR_STATE (before the Gaussians and
+ * observations, during graph capture), GSVR_ERR_INVALID_ARG (no active
+ * subject). */
+gsvr_status gsvr_set_subject_active(gsvr_ctx *ctx, const uint8_t *active);
+
 /* Grow the record / key capacities to at least the given counts (never
  * shrinks; contents are regenerated by the next forward).  In fixed-capacity
  * mode this is how a caller makes room after a GSVR_ERR_CAPACITY or before the

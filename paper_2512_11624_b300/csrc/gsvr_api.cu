@@ -147,6 +147,7 @@ struct gsvr_ctx {
     DBuf<int> d_all_first;  // {0, n_mask}: the whole mask as one sampling range
     DBuf<int> d_single_out; // {0, n}: output offsets of a whole-mask sample
     int64_t single_out_n = -1, subj_out_n = -1, subj_out_total = 0;
+    std::vector<uint8_t> h_subj_active;  // per subject (empty: every subject active)
     bool multi_gauss = false;
 
     // CUDA graph of one optimisation iteration
@@ -639,6 +640,7 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     ctx->h_stack_nslices.assign(n_stacks, 0);
     for (int st2 = 0; st2 < n_stacks; ++st2) ctx->h_stack_nslices[st2] = stacks[st2].n_slices;
     ctx->n_subj = 1;
+    ctx->h_subj_active.clear();
     ctx->h_stack_subject.assign(n_stacks, 0);
     ctx->multi_gauss = false;
     cudaStream_t st = ctx->stream;
@@ -933,7 +935,8 @@ int64_t subject_out_first(gsvr_ctx *ctx, int64_t n) {
     std::vector<int> of(ctx->n_subj + 1, 0);
     for (int k = 0; k < ctx->n_subj; ++k) {
         const int64_t avail = ctx->h_subj_mask_first[k + 1] - ctx->h_subj_mask_first[k];
-        of[k + 1] = of[k] + (int)std::min<int64_t>(n, avail);
+        const bool on = ctx->h_subj_active.empty() || ctx->h_subj_active[(size_t)k];
+        of[k + 1] = of[k] + (on ? (int)std::min<int64_t>(n, avail) : 0);
     }
     if (cudaMemcpy(ctx->d_subj_out_first.p, of.data(), sizeof(int) * of.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess) {
@@ -954,6 +957,53 @@ gsvr_status gsvr_sample_pixels_subjects(gsvr_ctx *ctx, int64_t n_per_subject, ui
     if (tot < 0) return fail(ctx, GSVR_ERR_CUDA, "upload of the sample offsets failed");
     return sample_ranges(ctx, ctx->n_subj, ctx->d_subj_mask_first.p, ctx->d_subj_out_first.p, (int)tot, step,
                          nullptr);
+}
+
+gsvr_status gsvr_set_subject_active(gsvr_ctx *ctx, const uint8_t *active) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!ctx->have_gauss || !ctx->have_obs) return fail(ctx, GSVR_ERR_STATE, "set stacks, observations, Gaussians first");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_subject_active during graph capture");
+    const int n = ctx->n_subj;
+    std::vector<uint8_t> next((size_t)n, 1);
+    if (active) {
+        bool any = false;
+        for (int k = 0; k < n; ++k) {
+            next[(size_t)k] = active[k] ? 1 : 0;
+            any = any || next[(size_t)k];
+        }
+        if (!any) return fail(ctx, GSVR_ERR_INVALID_ARG, "at least one subject must stay active");
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const std::vector<uint8_t> prev = ctx->h_subj_active.empty() ? std::vector<uint8_t>((size_t)n, 1)
+                                                                 : ctx->h_subj_active;
+    const int64_t N = ctx->N;
+    for (int k = 0; k < n; ++k) {
+        if (!prev[(size_t)k] || next[(size_t)k]) continue;
+        // a subject leaving the sample: its Adam moments restart at zero, so the
+        // zero gradient it now receives leaves its parameters where they are
+        const int64_t g0 = n > 1 ? ctx->h_subj_gauss_first[(size_t)k] : 0;
+        const int64_t g1 = n > 1 ? ctx->h_subj_gauss_first[(size_t)k + 1] : N;
+        for (int c = 0; c < 11 && g1 > g0; ++c) {
+            CK(cudaMemsetAsync(ctx->d_m.p + (size_t)c * N + g0, 0, sizeof(float) * (size_t)(g1 - g0), st));
+            CK(cudaMemsetAsync(ctx->d_v.p + (size_t)c * N + g0, 0, sizeof(float) * (size_t)(g1 - g0), st));
+        }
+        const int s0 = n > 1 ? ctx->h_subj_slice_first[(size_t)k] : 0;
+        const int s1 = n > 1 ? ctx->h_subj_slice_first[(size_t)k + 1] : ctx->M;
+        if (s1 > s0) {
+            CK(cudaMemsetAsync(ctx->d_m.p + 11 * N + 6 * (int64_t)s0, 0, sizeof(float) * 6 * (size_t)(s1 - s0), st));
+            CK(cudaMemsetAsync(ctx->d_v.p + 11 * N + 6 * (int64_t)s0, 0, sizeof(float) * 6 * (size_t)(s1 - s0), st));
+        }
+    }
+    ctx->h_subj_active = next;
+    ctx->subj_out_n = -1;  // per-subject sample offsets are recomputed
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->fwd_valid = false;
+    CK(cudaStreamSynchronize(st));
+    return GSVR_OK;
 }
 
 gsvr_status gsvr_set_subjects(gsvr_ctx *ctx, int32_t n, const int32_t *stack_subject, const int64_t *gauss_count) {
@@ -982,6 +1032,7 @@ gsvr_status gsvr_set_subjects(gsvr_ctx *ctx, int32_t n, const int32_t *stack_sub
     }
     DeviceGuard g(ctx->device);
     ctx->n_subj = n;
+    ctx->h_subj_active.clear();
     ctx->h_stack_subject = ss;
     ctx->h_subj_gauss_first = gf;
     {

@@ -34,7 +34,7 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
            "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means",
            "gsvr_volume_metrics", "gsvr_fp64_peak", "gsvr_densify_accumulate", "gsvr_densify_stats",
-           "gsvr_densify", "gsvr_ffma2_peak"]
+           "gsvr_densify", "gsvr_ffma2_peak", "gsvr_set_subject_active"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -128,6 +128,7 @@ def _load():
         "gsvr_set_subjects": ([vp, i32, vp, vp], C.c_int),
         "gsvr_sample_pixels_subjects": ([vp, i64, u64], C.c_int),
         "gsvr_get_subject_losses": ([vp, vp, i32], C.c_int),
+        "gsvr_set_subject_active": ([vp, vp], C.c_int),
         "gsvr_graph_capture": ([vp, i64, C.POINTER(AdamCfg)], C.c_int),
         "gsvr_graph_launch": ([vp, i32], C.c_int),
         "gsvr_set_step": ([vp, i64], C.c_int),
@@ -299,6 +300,14 @@ def adam_cfg(lr=None, beta1=0.9, beta2=0.999, eps=1e-8, step_every=0, gamma=1.0)
 def gsvr_adam_step(ctx, step, lr=None, beta1=0.9, beta2=0.999, eps=1e-8, step_every=0, gamma=1.0):
     cfg = adam_cfg(lr, beta1, beta2, eps, step_every, gamma)
     return _check(ctx, lib.gsvr_adam_step(ctx, C.byref(cfg), int(step)))
+
+
+def gsvr_set_subject_active(ctx, active=None):
+    """Retire (0) or return (1) subjects of the batched sampler; None = all active."""
+    if active is None:
+        return _check(ctx, lib.gsvr_set_subject_active(ctx, None))
+    a = np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
+    return _check(ctx, lib.gsvr_set_subject_active(ctx, a.ctypes.data))
 
 
 def gsvr_set_subjects(ctx, stack_subject, gauss_count):

@@ -288,13 +288,17 @@ class BatchedReconstruction:
     def subject_theta(self, k):
         return self.ctx.theta.index_select(0, self.gauss_index[k])
 
-    def run(self, iters, probes=None, eval_every=25, targets=None):
+    def run(self, iters, probes=None, eval_every=25, targets=None, retire=False):
         """Returns {"history": [(iteration, device_seconds, [loss per subject], [psnr per subject])],
-        "time_to_target": [s or None per subject], "iters_to_target": [...]}."""
+        "time_to_target": [s or None per subject], "iters_to_target": [...]}.  With
+        `retire`, a subject that reaches its target leaves the batch
+        (gsvr_set_subject_active: no more pixels, parameters kept) and the run
+        ends once every subject has reached its target."""
         hist = []
         dev_s = 0.0
         hit_t = [None] * self.n_subj
         hit_i = [None] * self.n_subj
+        active = np.ones(self.n_subj, np.uint8)
 
         def evaluate():
             return [p.psnr(self.subject_theta(k)) for k, p in enumerate(probes)] if probes else None
@@ -321,6 +325,15 @@ class BatchedReconstruction:
                 for k in range(self.n_subj):
                     if hit_t[k] is None and targets[k] is not None and ps[k] >= targets[k]:
                         hit_t[k], hit_i[k] = dev_s, done
+                if retire:
+                    if all(h is not None for h in hit_t):
+                        break
+                    newly = [k for k in range(self.n_subj) if hit_t[k] is not None and active[k]]
+                    if newly:
+                        active[newly] = 0
+                        gsvr.gsvr_set_subject_active(self.ctx.ctx, active)
+                        if self.graph:
+                            self._capture()
         return {"history": hist, "time_to_target": hit_t, "iters_to_target": hit_i}
 
     def close(self):

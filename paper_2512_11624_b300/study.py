@@ -134,6 +134,19 @@ def run_batched(args):
     if all(v is not None for v in all_alone + all_b):
         out["all_targets"] = {"alone_sequential_s": float(sum(all_alone)), "batched_s": float(max(all_b))}
     out["speedup_device_time"] = alone_total / bt
+    if args.retire:
+        # the batch again, converged subjects leaving it (same targets)
+        br.close()
+        br = BatchedReconstruction(subjects, device=dev, n_sample=args.n_sample, tune=True, graph=not args.no_graph)
+        rr = br.run(args.iters, probes=probes, eval_every=args.eval_every, targets=targets, retire=True)
+        rt = rr["time_to_target"]
+        for k, s in enumerate(out["subjects"]):
+            s["batched_retire"] = {"iters_to_target": rr["iters_to_target"][k], "s_to_target": rt[k]}
+        out["batched_retire"] = {"device_s": rr["history"][-1][1],
+                                 "s_all_targets": max(rt) if all(v is not None for v in rt) else None}
+        print("batched, converged subjects retired: every target after %s s (alone sequential %s s)" %
+              (out["batched_retire"]["s_all_targets"], out.get("all_targets", {}).get("alone_sequential_s")),
+              flush=True)
     print("batched: %.3f ms/iter (%d subjects), alone total %.2f s vs batched %.2f s -> %.2fx; useful pairs/s "
           "%.3g alone vs %.3g batched" % (1e3 * bt / args.iters, args.subjects, alone_total, bt, alone_total / bt,
                                           out["alone"]["useful_pairs_per_s"], out["batched"]["useful_pairs_per_s"]),
@@ -667,6 +680,7 @@ def main():
     b.add_argument("--n-sample", type=int, default=1 << 18)
     b.add_argument("--workers", type=int, default=8)
     b.add_argument("--no-graph", action="store_true")
+    b.add_argument("--retire", action="store_true")
     b.add_argument("--out", default="")
     lr = sub.add_parser("learned")
     lr.add_argument("--phantoms", type=int, default=2000)

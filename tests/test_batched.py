@@ -145,3 +145,88 @@ def test_batched_driver_graph_equals_eager_and_descends(G):
     first, last = np.array(he[1][2]), np.array(he[-1][2])
     assert np.all(last < first), (first, last)
     assert np.allclose(np.array(hg[-1][2]), last, rtol=1e-3)
+
+
+def test_retired_subject_keeps_its_parameters(G):
+    """gsvr_set_subject_active: a retired subject draws no pixels, its loss reads
+    0 and its parameters (Gaussians and slice poses) stay bit for bit while the
+    others keep moving, in eager and graph iterations; returned to the sample,
+    it moves again; retiring every subject is refused."""
+    import torch
+    cases = three_subjects()
+    lr = dict(lr_mu=5e-3, lr_ls=5e-3, lr_q=2e-3, lr_c=1e-3, lr_rot=2e-3, lr_trans=5e-2)
+    stream = torch.cuda.Stream()
+    b, ctx = batched_ctx(G, cases, stream=stream.cuda_stream, fixed_capacity=1, cap_records=200000,
+                         cap_keys=800000, seed=7)
+    gc = b["gauss_count"]
+    M = [inputs.n_slices_total(c["stacks"]) for c in cases]
+    P = [inputs.n_pixels_total(c["stacks"]) for c in cases]
+    pose0 = 11 * b["N"] + 6 * M[0]
+
+    def subject1():
+        th = ctx.theta.cpu().numpy()
+        return np.concatenate([inputs.subject_theta(th, gc, 1), th[pose0:pose0 + 6 * M[1]]])
+
+    def step(k):
+        G.gsvr_sample_pixels_subjects(ctx.ctx, 150, k)
+        ctx.forward()
+        ctx.backward()
+        G.gsvr_adam_step(ctx.ctx, k + 1, lr=lr)
+
+    for k in range(3):
+        step(k)
+    G.gsvr_set_subject_active(ctx.ctx, [1, 0, 1])
+    before = subject1()
+    others = ctx.theta.cpu().numpy().copy()
+    for k in range(3, 6):
+        step(k)
+    G.gsvr_sync_status(ctx.ctx)
+    assert np.array_equal(subject1(), before)
+    sample = G.gsvr_get_sample(ctx.ctx)
+    assert not np.any((sample >= P[0]) & (sample < P[0] + P[1]))
+    assert np.sum(sample < P[0]) == 150 and np.sum(sample >= P[0] + P[1]) == 150
+    losses = G.gsvr_get_subject_losses(ctx.ctx, 3)
+    assert losses[1] == 0.0 and losses[0] > 0.0 and losses[2] > 0.0
+    g0 = inputs.subject_theta(ctx.theta.cpu().numpy(), gc, 0)
+    assert not np.array_equal(g0, inputs.subject_theta(others, gc, 0))
+    # graph iterations with the subject retired
+    ctx.forward()
+    G.gsvr_sync_status(ctx.ctx)
+    G.gsvr_set_step(ctx.ctx, 6)
+    G.gsvr_graph_capture(ctx.ctx, 150, lr=lr)
+    G.gsvr_graph_launch(ctx.ctx, 4)
+    G.gsvr_sync_status(ctx.ctx)
+    stream.synchronize()
+    assert np.array_equal(subject1(), before)
+    # back in the sample: it moves again
+    G.gsvr_set_subject_active(ctx.ctx, None)
+    for k in range(10, 13):
+        step(k)
+    G.gsvr_sync_status(ctx.ctx)
+    assert not np.array_equal(subject1(), before)
+    with pytest.raises(G.GsvrError):
+        G.gsvr_set_subject_active(ctx.ctx, [0, 0, 0])
+    ctx.close()
+
+
+def test_batched_driver_retires_converged_subjects(G):
+    """The driver with `retire`: every subject reaches its (easy) target, the
+    retired ones stop moving, and the run ends once all have reached it."""
+    from paper_2512_11624_b300.recon import BatchedReconstruction
+
+    class LossProbe:  # "PSNR" read from the subject's own loss history
+        def __init__(self, br, k):
+            self.br, self.k = br, k
+            self.n = 0
+
+        def psnr(self, theta_g):
+            self.n += 1
+            return float(self.n)  # rises by one per evaluation
+
+    cases = three_subjects()
+    br = BatchedReconstruction(cases, n_sample=300, tune=False, graph=True, lr=dict(lr_c=5e-3))
+    probes = [LossProbe(br, k) for k in range(3)]
+    res = br.run(200, probes=probes, eval_every=10, targets=[2.0, 4.0, 3.0], retire=True)
+    assert res["iters_to_target"] == [10, 30, 20]
+    assert res["history"][-1][0] == 30  # stopped once every target was reached
+    br.close()
