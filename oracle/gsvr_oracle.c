@@ -366,6 +366,21 @@ static void pixel_terms(const double *slw, int64_t M, int64_t i, int loss_kind, 
     }
 }
 
+/* Sum of x[0..n) in index order with Neumaier's compensation: the result does
+ * not depend on the thread schedule that produced the terms, and its error is
+ * about one rounding of the total (a plain running sum would add a rounding
+ * of the running total per term, which central differences of the loss
+ * amplify by 1 / (2 h)). */
+static double sum_in_order(const double *x, int64_t n) {
+    double s = 0.0, c = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double t = s + x[k];
+        c += fabs(s) >= fabs(x[k]) ? (s - t) + x[k] : (x[k] - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
 /* Forward: pred[p] = sum over ALL Gaussians (times sigma_i); loss = sum_p of the
  * pixel losses. */
 int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
@@ -373,8 +388,10 @@ int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *th
                    const double *slw, double *pred, double *loss) {
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
-    double L = 0.0;
-#pragma omp parallel for schedule(dynamic, 8) reduction(+ : L)
+    /* per-pixel loss terms, summed afterwards in pixel order (the sum is then
+     * the same whatever the thread schedule) */
+    double *lt = (double *)calloc((size_t)(P ? P : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 8)
     for (int64_t p = 0; p < P; ++p) {
         int64_t i;
         double u[3], x[3];
@@ -387,8 +404,10 @@ int oracle_forward(int n_stacks, const or_stack *st, int64_t N, const double *th
         }
         double lp = 0.0, dl;
         pixel_terms(slw, m.M, i, loss_kind, w_pix, s, I_obs ? I_obs[p] : 0.0, &pred[p], &lp, &dl, NULL);
-        if (I_obs) L += lp;
+        lt[p] = I_obs ? lp : 0.0;
     }
+    const double L = sum_in_order(lt, P);
+    free(lt);
     if (loss) *loss = L;
     model_free(&m);
     return 0;
@@ -539,8 +558,8 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
     double *pu = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
     int64_t *psl = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
     double *pmod = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
-    double L = 0.0;
-#pragma omp parallel for schedule(dynamic, 8) reduction(+ : L)
+    double *lt = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));  /* per-pixel loss terms */
+#pragma omp parallel for schedule(dynamic, 8)
     for (int64_t p = 0; p < P; ++p) {
         int64_t i;
         pixel_world(&m, pix[p], &i, &pu[3 * p], &px[3 * p]);
@@ -557,8 +576,10 @@ int oracle_forward_backward(int n_stacks, const or_stack *st, int64_t N, const d
         if (pred) pred[p] = pr_;
         if (trunc_pred) trunc_pred[p] = tr;
         pmod[p] = s;
-        L += lp;
+        lt[p] = lp;
     }
+    const double L = sum_in_order(lt, P);
+    free(lt);
     if (loss) *loss = L;
     if (slw_grad) {  /* per-slice sums in pixel order */
         memset(slw_grad, 0, sizeof(double) * (size_t)(2 * M));
