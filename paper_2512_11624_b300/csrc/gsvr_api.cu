@@ -148,6 +148,7 @@ struct gsvr_ctx {
     DBuf<int> d_single_out; // {0, n}: output offsets of a whole-mask sample
     int64_t single_out_n = -1, subj_out_n = -1, subj_out_total = 0;
     std::vector<uint8_t> h_subj_active;  // per subject (empty: every subject active)
+    DBuf<uint8_t> d_subj_active;         // its device copy (read by the candidate pass)
     bool multi_gauss = false;
 
     // CUDA graph of one optimisation iteration
@@ -996,6 +997,8 @@ gsvr_status gsvr_set_subject_active(gsvr_ctx *ctx, const uint8_t *active) {
         }
     }
     ctx->h_subj_active = next;
+    CK(ctx->d_subj_active.ensure((size_t)n));
+    CK(cudaMemcpyAsync(ctx->d_subj_active.p, next.data(), (size_t)n, cudaMemcpyHostToDevice, st));
     ctx->subj_out_n = -1;  // per-subject sample offsets are recomputed
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
@@ -1210,6 +1213,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.tile_h = ctx->tile_h;
     b.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
     b.gauss_subject = ctx->multi_gauss ? ctx->d_gauss_subject.p : nullptr;
+    b.subj_active = ctx->multi_gauss && !ctx->h_subj_active.empty() ? ctx->d_subj_active.p : nullptr;
     b.subj_slice_first = ctx->d_subj_slice_first.p;
     b.tile_px_start = ctx->d_tile_px_start.p;
     b.tile_px_end = ctx->d_tile_px_end.p;

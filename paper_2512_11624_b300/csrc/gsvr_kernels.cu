@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(128) k_cand(BinArgs a) {
             bhi = 0;
         }
         __syncthreads();
-        if (live) {
+        const bool on = live && (!a.subj_active || a.subj_active[a.gauss_subject[j]]);
+        if (on) {
             const int sj = a.gauss_subject[j];
             sl0 = a.subj_slice_first[sj];
             sl1 = a.subj_slice_first[sj + 1];
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(128) k_cand(BinArgs a) {
             atomicMax(&bhi, sl1);
         }
         __syncthreads();
-        if (!live) {
+        if (!on) {  // (a retired subject's Gaussians meet no slice: no records, no work)
             sl0 = blo;
             sl1 = blo;
         }

@@ -20,6 +20,7 @@ struct BinArgs {
     int2 *cand;                // (Gaussian, slice) per candidate; slice -1 = padding
     const int *gauss_subject;  // subject of each Gaussian (null: one subject)
     const int *subj_slice_first;  // first slice of each subject (n_subj + 1)
+    const uint8_t *subj_active;   // per subject, 0 = retired: its Gaussians meet no slice (null: all active)
     Rec *rec;                  // one record per candidate
     int2 *rec_tiles;           // packed tile bounding box per record
     int *rec_nkeys;            // keys per record
