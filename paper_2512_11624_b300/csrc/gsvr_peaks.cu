@@ -107,6 +107,14 @@ __global__ void __launch_bounds__(256) k_peak_dfma(double *out, int iters, doubl
 
 extern "C" gsvr_status gsvr_fp64_peak(int device, double *dfma_per_s) {
     if (!dfma_per_s) return GSVR_ERR_INVALID_ARG;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    struct Restore {
+        int prev;
+        ~Restore() {
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+    } restore{prev};
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return GSVR_ERR_INVALID_ARG;
@@ -161,6 +169,14 @@ __global__ void __launch_bounds__(256) k_peak_ffma2(float *out, int iters, float
 
 extern "C" gsvr_status gsvr_ffma2_peak(int device, double *ffma2_per_s) {
     if (!ffma2_per_s) return GSVR_ERR_INVALID_ARG;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    struct Restore {
+        int prev;
+        ~Restore() {
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+    } restore{prev};
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return GSVR_ERR_INVALID_ARG;
