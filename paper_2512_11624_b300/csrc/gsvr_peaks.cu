@@ -46,6 +46,14 @@ __global__ void __launch_bounds__(256) k_peak_ex2(float *out, int iters) {
 
 extern "C" gsvr_status gsvr_alu_peaks(int device, double *ffma_per_s, double *ex2_per_s, double *sm_count) {
     if (!ffma_per_s || !ex2_per_s) return GSVR_ERR_INVALID_ARG;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    struct Restore {
+        int prev;
+        ~Restore() {
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+    } restore{prev};
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return GSVR_ERR_INVALID_ARG;
