@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_gemm_tma(const __grid_constant_
                      : "memory");
 }
 
-// Host: the driver's tensor-map encoder, looked up once through the runtime.
+// Host: the CUDA driver API's tensor-map encoder, looked up once through the runtime.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;

@@ -1774,7 +1774,7 @@ struct TopkList {
     unsigned long long tau;         // largest key when cnt == K, else all ones
 };
 
-// Merge this round's passing keys (one per lane, all ones where none) into the list.
+// Merge a set of passing keys (one per lane, all ones where none) into the list.
 __device__ __forceinline__ void topk_merge(TopkList &T, unsigned long long v, int m, int K, int lane) {
     // ascending bitonic sort of the 32 lanes' keys (all-ones keys sort last)
 #pragma unroll

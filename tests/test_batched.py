@@ -210,7 +210,7 @@ def test_retired_subject_keeps_its_parameters(G):
 
 
 def test_batched_driver_retires_converged_subjects(G):
-    """The driver with `retire`: every subject reaches its (easy) target, the
+    """BatchedReconstruction.run with `retire`: every subject reaches its (easy) target, the
     retired ones stop moving, and the run ends once all have reached it."""
     from paper_2512_11624_b300.recon import BatchedReconstruction
 
