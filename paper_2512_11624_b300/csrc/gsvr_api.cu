@@ -1612,8 +1612,8 @@ gsvr_status check_tiling(gsvr_ctx *ctx, const gsvr_tiling &t) {
     if (th < 4 || th > 32 || tw < 4 || tw > 32)
         return fail(ctx, GSVR_ERR_INVALID_ARG, "tile sides must lie in [4, 32]");
     if (t.fwd_px_per_thread != 0 && t.fwd_px_per_thread != 1 && t.fwd_px_per_thread != 2 &&
-        t.fwd_px_per_thread != 4)
-        return fail(ctx, GSVR_ERR_INVALID_ARG, "fwd_px_per_thread must be 0, 1, 2 or 4");
+        t.fwd_px_per_thread != 4 && t.fwd_px_per_thread != 8)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "fwd_px_per_thread must be 0, 1, 2, 4 or 8");
     const int pxr = fwd_pxr(tw, t.fwd_px_per_thread);
     if (th * ((tw + pxr - 1) / pxr) > 256)
         return fail(ctx, GSVR_ERR_INVALID_ARG, "tile_h * ceil(tile_w / px_per_thread) must be <= 256");

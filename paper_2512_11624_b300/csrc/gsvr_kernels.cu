@@ -2227,7 +2227,10 @@ void launch_item_order(const int *item_tile, const int *item_first, const int *t
 }
 // Forward pixels per thread: the requested run (1, 2 or 4), else 4 for tiles
 // at least 12 wide and 2 below.
-int fwd_pxr(int tile_w, int req) { return req == 1 || req == 2 || req == 4 ? req : (tile_w >= 12 ? 4 : 2); }
+int fwd_pxr(int tile_w, int req) {
+    if (req == 1 || req == 2 || req == 4 || req == 8) return req;
+    return tile_w >= 16 ? 8 : (tile_w >= 12 ? 4 : 2);  // the row terms amortised over the longest run
+}
 // Forward CTA shape: groups of tile_h x ceil(tile_w / PXR) threads, as many
 // groups as fit in 128 threads (at least one).
 int fwd_threads(int tile_w, int tile_h, int pxr) {
@@ -2243,7 +2246,8 @@ int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
-        if (pxr == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 4>, nt, 0);
+        if (pxr == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 8>, nt, 0);
+        else if (pxr == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 4>, nt, 0);
         else if (pxr == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 2>, nt, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 1>, nt, 0);
     }
@@ -2277,7 +2281,8 @@ static void fwd_items(const EvalArgs &a, cudaStream_t st) {
     const int nt = fwd_threads(a.tile_w, a.tile_h, pxr);
     cudaMemsetAsync(&a.counters->work_fwd, 0, sizeof(int), st);
     const int grid = eval_grid(a, false);
-    if (pxr == 4) k_fwd_items<COUNT, 4><<<grid, nt, 0, st>>>(a);
+    if (pxr == 8) k_fwd_items<COUNT, 8><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 4) k_fwd_items<COUNT, 4><<<grid, nt, 0, st>>>(a);
     else if (pxr == 2) k_fwd_items<COUNT, 2><<<grid, nt, 0, st>>>(a);
     else k_fwd_items<COUNT, 1><<<grid, nt, 0, st>>>(a);
     counted();

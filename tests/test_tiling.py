@@ -12,7 +12,8 @@ SHAPES = [dict(tile_h=16, tile_w=16), dict(tile_h=8, tile_w=8, fwd_px_per_thread
           dict(tile_h=12, tile_w=12, queue_order=1), dict(tile_h=32, tile_w=8, fwd_blocks_per_sm=1, bwd_blocks_per_sm=1),
           dict(tile_h=8, tile_w=32, fwd_px_per_thread=4, queue_order=1), dict(tile_h=12, tile_w=16, fwd_px_per_thread=2),
           dict(tile_h=5, tile_w=7, fwd_px_per_thread=1, fwd_blocks_per_sm=3),
-          dict(tile_h=12, tile_w=12, fwd_blocks_per_sm=-1, bwd_blocks_per_sm=-1, queue_order=1)]
+          dict(tile_h=12, tile_w=12, fwd_blocks_per_sm=-1, bwd_blocks_per_sm=-1, queue_order=1),
+          dict(tile_h=8, tile_w=16, fwd_px_per_thread=8), dict(tile_h=6, tile_w=20, fwd_px_per_thread=8)]
 
 
 def test_default_space_is_valid_host_logic():
@@ -22,8 +23,8 @@ def test_default_space_is_valid_host_logic():
     space = gsvr.gsvr_tune_space_default()
     assert len(space) >= 8
     for t in space:
-        px = t.fwd_px_per_thread or (4 if t.tile_w >= 12 else 2)
-        assert 4 <= t.tile_h <= 32 and 4 <= t.tile_w <= 32 and px in (1, 2, 4)
+        px = t.fwd_px_per_thread or (8 if t.tile_w >= 16 else (4 if t.tile_w >= 12 else 2))
+        assert 4 <= t.tile_h <= 32 and 4 <= t.tile_w <= 32 and px in (1, 2, 4, 8)
         assert t.tile_h * -(-t.tile_w // px) <= 256
         assert t.queue_order in (0, 1)
 
