@@ -875,7 +875,7 @@ static void grid_free(or_grid *G) {
 
 /* Sum over the Gaussians near x of c_l f exp(-1/2 v^T P v), pairs below the cut dropped. */
 static double pred_near(const or_model *m, const or_grid *G, const double *mu, const or_frame *fr, const double *x,
-                        int norm_mode, double r2cut, double rad2, double r2t, double *trunc) {
+                        int norm_mode, double r2cut, double rad2, double r2t, double *trunc, double *absum) {
     int64_t c[3];
     grid_cell_of(G, x, c);
     double s = 0.0;
@@ -895,6 +895,7 @@ static double pred_near(const or_model *m, const or_grid *G, const double *mu, c
                     if (d2 <= r2cut) {
                         s += m->g[l].c * pr.g;
                         if (trunc && d2 > r2t) *trunc += fabs(m->g[l].c * pr.g);
+                        if (absum) *absum += fabs(m->g[l].c * pr.g);
                     }
                 }
             }
@@ -948,7 +949,7 @@ int oracle_local_fd(int n_stacks, const or_stack *st, int64_t N, const double *t
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t p = 0; p < P; ++p) {
         double t = 0.0;
-        pred[p] = pred_near(&m, &GG, mu, &m.fr[sp[p]], xp + 3 * p, norm_mode, r2cut, rad2, r2t, &t);
+        pred[p] = pred_near(&m, &GG, mu, &m.fr[sp[p]], xp + 3 * p, norm_mode, r2cut, rad2, r2t, &t, NULL);
         if (trunc_out) trunc_out[p] = t;
     }
     if (pred_out) memcpy(pred_out, pred, sizeof(double) * (size_t)P);
@@ -1016,7 +1017,7 @@ int oracle_local_fd(int n_stacks, const or_stack *st, int64_t N, const double *t
                     pixel_local(&m.sl[i], pix[p], u);
                     mat_vec(fr.R, u, x);
                     for (int a = 0; a < 3; ++a) x[a] += fr.t[a];
-                    double v = pred_near(&m, &GG, mu, &fr, x, norm_mode, r2cut, rad2, 1e300, NULL) - I_obs[p];
+                    double v = pred_near(&m, &GG, mu, &fr, x, norm_mode, r2cut, rad2, 1e300, NULL, NULL) - I_obs[p];
                     part += w_pix * v * v;
                 }
                 dL += (s == 0 ? 1.0 : -1.0) * part;
@@ -1032,6 +1033,329 @@ int oracle_local_fd(int n_stacks, const or_stack *st, int64_t N, const double *t
     free(xp);
     free(sp);
     free(pred);
+    model_free(&m);
+    return 0;
+}
+
+/* ------------------------------------------- large cases: analytic gradient
+ * The analytic gradient of L = sum_p w (I_hat_p - I_p)^2 over a listed pixel
+ * set, at sizes where the all-pairs loops of oracle_forward_backward are too
+ * slow.  The per-pair expressions are those of oracle_forward_backward (the
+ * derivative of Eq. 5's numerator with Sigma_obs of Eq. 4, chained through
+ * Sigma = R S S^T R^T and the slice frame); only which pairs are visited
+ * differs, exactly as in oracle_local_fd: a pair with exp(-1/2 v^T P v) < cut
+ * is dropped, and the pairs are found through uniform grids of the Gaussian
+ * means and of the pixel positions with cells no smaller than the largest
+ * Euclidean radius of that cut.
+ *   pred_out, trunc_pred: I_hat_p (float64) and the sum of |terms| of the
+ *     pairs with trunc_cut > exp(.) >= cut (what a cut at trunc_cut drops);
+ *   loss_out: the loss over the listed pixels;
+ *   gsel, asel, tsel (11 x n_sel, entry k of selected Gaussian s at
+ *     [k * n_sel + s], k in the parameter order mu, ls, q, c): the gradient of
+ *     every component of the Gaussians sel[0..n_sel), the sum of |terms| of
+ *     each (the same componentwise scales as oracle_forward_backward's
+ *     absgrad) and that sum over the pairs below trunc_cut;
+ *   gpose, apose, tpose (6 M): the same for every slice pose (r, tau);
+ *   bsel (11 x n_sel), bpose (6 M): the sum of |terms| with each pixel's
+ *     residual weight 2 w (I_hat_p - I_p) replaced by 2 w sum_j |c_j g_pj|, the
+ *     scale at which a relative rounding error of the prediction I_hat_p
+ *     (a sum of |terms| summing to that) moves the gradient. */
+typedef struct {
+    double a, dc, Go[9], gmu[3], dx[3], GR[9];
+} or_pair_grad;
+
+/* Contributions of one pair (residual weight rbar) to the gradient. */
+static void pair_grad(const or_gauss *gj, const or_slice *s, const or_frame *fr, const or_pair *pr, const double *u,
+                      double rbar, int norm_mode, or_pair_grad *o) {
+    o->a = rbar * gj->c * pr->g;
+    o->dc = rbar * pr->g;
+    const double pk = norm_mode == 0 ? 1.0 : 0.0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) o->Go[3 * r + c] = 0.5 * o->a * (pr->Pv[r] * pr->Pv[c] - pk * pr->P[3 * r + c]);
+    for (int k = 0; k < 3; ++k) {
+        o->gmu[k] = o->a * pr->Pv[k];
+        o->dx[k] = -o->a * pr->Pv[k];
+    }
+    double D[9] = {s->var[0], 0, 0, 0, s->var[1], 0, 0, 0, s->var[2]}, RD[9], GoRD[9];
+    mat_mul(fr->R, D, RD);
+    mat_mul(o->Go, RD, GoRD);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) o->GR[3 * r + c] = o->dx[r] * u[c] + 2.0 * GoRD[3 * r + c];
+}
+
+/* Componentwise |.| scales of one pair's contributions: pose (6), log-scales
+ * (3), quaternion (4). */
+static void pair_grad_abs(const or_gauss *gj, const or_slice *s, const or_frame *fr, const double *pose,
+                          const or_pair_grad *o, const double *u, int norm_mode, double *d6, double *als,
+                          double *aq) {
+    double Ga[9], RDa[9], GoRDa[9], GRa[9], dxa[3];
+    double D[9] = {s->var[0], 0, 0, 0, s->var[1], 0, 0, 0, s->var[2]}, RD[9];
+    mat_mul(fr->R, D, RD);
+    for (int e = 0; e < 9; ++e) {
+        Ga[e] = fabs(o->Go[e]);
+        RDa[e] = fabs(RD[e]);
+    }
+    for (int k = 0; k < 3; ++k) dxa[k] = fabs(o->dx[k]);
+    mat_mul(Ga, RDa, GoRDa);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) GRa[3 * r + c] = dxa[r] * fabs(u[c]) + 2.0 * GoRDa[3 * r + c];
+    pose_chain_abs(s, pose, GRa, dxa, d6);
+    double dls[3];
+    cov_chain_abs(gj, Ga, dls, aq);
+    for (int k = 0; k < 3; ++k) als[k] = dls[k] + (norm_mode == 0 ? fabs(o->a) : 0.0);
+}
+
+/* Indices of the grid items within Euclidean distance sqrt(rad2) of x
+ * (the 27 cells around x's cell); returns the count, growing *buf. */
+static int64_t grid_near(const or_grid *G, const double *pts, const double *x, double rad2, int64_t **buf,
+                         int64_t *cap) {
+    int64_t c[3], n = 0;
+    grid_cell_of(G, x, c);
+    for (int64_t dz = -1; dz <= 1; ++dz)
+        for (int64_t dy = -1; dy <= 1; ++dy)
+            for (int64_t dx = -1; dx <= 1; ++dx) {
+                int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= G->n[0] || cy >= G->n[1] || cz >= G->n[2]) continue;
+                int64_t cell = (cz * G->n[1] + cy) * G->n[0] + cx;
+                for (int64_t q = G->start[cell]; q < G->start[cell + 1]; ++q) {
+                    int64_t l = G->items[q];
+                    double v0 = x[0] - pts[3 * l], v1 = x[1] - pts[3 * l + 1], v2 = x[2] - pts[3 * l + 2];
+                    if (v0 * v0 + v1 * v1 + v2 * v2 > rad2) continue;
+                    if (n == *cap) {
+                        *cap = *cap ? 2 * *cap : 4096;
+                        *buf = (int64_t *)realloc(*buf, sizeof(int64_t) * (size_t)*cap);
+                    }
+                    (*buf)[n++] = l;
+                }
+            }
+    return n;
+}
+
+int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double *theta, int64_t P,
+                      const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, double cut,
+                      double trunc_cut, int64_t n_sel, const int64_t *sel, double *pred_out, double *trunc_pred,
+                      double *loss_out, double *gsel, double *asel, double *tsel, double *gpose, double *apose,
+                      double *tpose, double *bsel, double *bpose) {
+    or_model m;
+    if (model_setup(n_stacks, st, N, theta, &m)) return -1;
+    const int64_t M = m.M;
+    const double r2cut = -2.0 * log(cut);
+    const double r2t = trunc_cut > 0.0 ? -2.0 * log(trunc_cut) : 1e300;
+    double vmax = 0.0, pmax = 0.0;
+    for (int64_t j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) vmax = m.g[j].s2[a] > vmax ? m.g[j].s2[a] : vmax;
+    for (int64_t i = 0; i < M; ++i)
+        for (int a = 0; a < 3; ++a) pmax = m.sl[i].var[a] > pmax ? m.sl[i].var[a] : pmax;
+    const double rad2 = r2cut * (vmax + pmax) * 1.02, rad = sqrt(rad2);
+    double *mu = (double *)malloc(sizeof(double) * 3 * (size_t)(N ? N : 1));
+    double *xp = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
+    double *up = (double *)malloc(sizeof(double) * 3 * (size_t)(P ? P : 1));
+    int64_t *sp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P ? P : 1));
+    double *pred = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *rbar = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *lt = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *rabs = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    if (!mu || !xp || !up || !sp || !pred || !rbar || !lt || !rabs) return -1;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) {
+            mu[3 * j + a] = m.g[j].mu[a];
+            lo[a] = mu[3 * j + a] < lo[a] ? mu[3 * j + a] : lo[a];
+            hi[a] = mu[3 * j + a] > hi[a] ? mu[3 * j + a] : hi[a];
+        }
+    for (int64_t p = 0; p < P; ++p) {
+        pixel_world(&m, pix[p], &sp[p], up + 3 * p, xp + 3 * p);
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = xp[3 * p + a] < lo[a] ? xp[3 * p + a] : lo[a];
+            hi[a] = xp[3 * p + a] > hi[a] ? xp[3 * p + a] : hi[a];
+        }
+    }
+    double cell = rad;
+    for (;;) {
+        double cells = 1.0;
+        for (int a = 0; a < 3; ++a) cells *= floor((hi[a] - lo[a]) / cell) + 1.0;
+        if (cells <= 16777216.0) break;
+        cell *= 1.25;
+    }
+    or_grid GG, GP;
+    if (grid_build(&GG, N, mu, cell, lo, hi) || grid_build(&GP, P, xp, cell, lo, hi)) return -1;
+
+    /* predictions, residual weights and loss terms */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < P; ++p) {
+        double t = 0.0, ab = 0.0;
+        pred[p] = pred_near(&m, &GG, mu, &m.fr[sp[p]], xp + 3 * p, norm_mode, r2cut, rad2, r2t, &t, &ab);
+        if (trunc_pred) trunc_pred[p] = t;
+        const double r = pred[p] - I_obs[p];
+        rbar[p] = 2.0 * w_pix * r;
+        rabs[p] = 2.0 * w_pix * ab;
+        lt[p] = w_pix * r * r;
+    }
+    if (pred_out) memcpy(pred_out, pred, sizeof(double) * (size_t)P);
+    if (loss_out) *loss_out = sum_in_order(lt, P);
+
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    /* slice poses: pixel-major, per-thread slice accumulators dL/dR_i (9),
+     * dL/dt_i (3), |.| of the pose entries (6), |.| below trunc_cut (6), |.| at
+     * the prediction-scale residual weights (6) */
+    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 30, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 30;
+        int64_t *buf = NULL, cap = 0;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t p = 0; p < P; ++p) {
+            const int64_t i = sp[p];
+            const double *x = xp + 3 * p, *u = up + 3 * p;
+            const int64_t n = grid_near(&GG, mu, x, rad2, &buf, &cap);
+            double *acc = my + 30 * i;
+            for (int64_t k = 0; k < n; ++k) {
+                const or_gauss *gj = &m.g[buf[k]];
+                or_pair pr;
+                eval_pair(gj, &m.fr[i], x, norm_mode, &pr);
+                const double d2 = -2.0 * log(pr.e > 0.0 ? pr.e : 1e-300);
+                if (d2 > r2cut) continue;
+                or_pair_grad o;
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, u, rbar[p], norm_mode, &o);
+                for (int e = 0; e < 9; ++e) acc[e] += o.GR[e];
+                for (int a = 0; a < 3; ++a) acc[9 + a] += o.dx[a];
+                double d6[6], als[3], aq[4];
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &o, u, norm_mode, d6, als, aq);
+                for (int a = 0; a < 6; ++a) acc[12 + a] += fabs(d6[a]);
+                if (d2 > r2t)
+                    for (int a = 0; a < 6; ++a) acc[18 + a] += fabs(d6[a]);
+                or_pair_grad ob;
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, u, rabs[p], norm_mode, &ob);
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &ob, u, norm_mode, d6, als, aq);
+                for (int a = 0; a < 6; ++a) acc[24 + a] += fabs(d6[a]);
+            }
+        }
+        free(buf);
+    }
+    for (int64_t i = 0; i < M; ++i) {
+        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0}, tb[6] = {0}, bb[6] = {0};
+        for (int t = 0; t < nthreads; ++t) {
+            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 30;
+            for (int e = 0; e < 9; ++e) GR[e] += acc[e];
+            for (int a = 0; a < 3; ++a) Gt[a] += acc[9 + a];
+            for (int a = 0; a < 6; ++a) ab[a] += acc[12 + a];
+            for (int a = 0; a < 6; ++a) tb[a] += acc[18 + a];
+            for (int a = 0; a < 6; ++a) bb[a] += acc[24 + a];
+        }
+        double d6[6];
+        pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, Gt, d6);
+        for (int a = 0; a < 6; ++a) {
+            if (gpose) gpose[6 * i + a] = d6[a];
+            if (apose) apose[6 * i + a] = ab[a];
+            if (tpose) tpose[6 * i + a] = tb[a];
+            if (bpose) bpose[6 * i + a] = bb[a];
+        }
+    }
+    free(pacc);
+
+    /* selected Gaussians: Gaussian-major over the listed pixels near the mean */
+#pragma omp parallel
+    {
+        int64_t *buf = NULL, cap = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < n_sel; ++s) {
+            const int64_t j = sel[s];
+            const or_gauss *gj = &m.g[j];
+            double gmu[3] = {0, 0, 0}, GS[9] = {0}, gc = 0.0, gld = 0.0;
+            double amu[3] = {0, 0, 0}, als[3] = {0, 0, 0}, aq[4] = {0, 0, 0, 0}, ac = 0.0;
+            double tmu[3] = {0, 0, 0}, tls[3] = {0, 0, 0}, tq[4] = {0, 0, 0, 0}, tc = 0.0;
+            double bmu[3] = {0, 0, 0}, bls[3] = {0, 0, 0}, bq[4] = {0, 0, 0, 0}, bc = 0.0;
+            const int64_t n = grid_near(&GP, xp, gj->mu, rad2, &buf, &cap);
+            for (int64_t k = 0; k < n; ++k) {
+                const int64_t p = buf[k], i = sp[p];
+                or_pair pr;
+                eval_pair(gj, &m.fr[i], xp + 3 * p, norm_mode, &pr);
+                const double d2 = -2.0 * log(pr.e > 0.0 ? pr.e : 1e-300);
+                if (d2 > r2cut) continue;
+                or_pair_grad o;
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, up + 3 * p, rbar[p], norm_mode, &o);
+                gc += o.dc;
+                for (int e = 0; e < 9; ++e) GS[e] += o.Go[e];
+                for (int a = 0; a < 3; ++a) gmu[a] += o.gmu[a];
+                if (norm_mode == 0) gld += 0.5 * o.a;
+                double d6[6], pls[3], pq[4];
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &o, up + 3 * p, norm_mode, d6, pls,
+                              pq);
+                const int below = d2 > r2t;
+                for (int a = 0; a < 3; ++a) {
+                    amu[a] += fabs(o.gmu[a]);
+                    als[a] += pls[a];
+                    if (below) {
+                        tmu[a] += fabs(o.gmu[a]);
+                        tls[a] += pls[a];
+                    }
+                }
+                for (int a = 0; a < 4; ++a) {
+                    aq[a] += pq[a];
+                    if (below) tq[a] += pq[a];
+                }
+                ac += fabs(o.dc);
+                if (below) tc += fabs(o.dc);
+                or_pair_grad ob;
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, up + 3 * p, rabs[p], norm_mode, &ob);
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &ob, up + 3 * p, norm_mode, d6, pls,
+                              pq);
+                for (int a = 0; a < 3; ++a) {
+                    bmu[a] += fabs(ob.gmu[a]);
+                    bls[a] += pls[a];
+                }
+                for (int a = 0; a < 4; ++a) bq[a] += pq[a];
+                bc += fabs(ob.dc);
+            }
+            double dls[3], dq[4];
+            cov_chain(gj, GS, dls, dq);
+            double g11[11], a11[11], t11[11], b11[11];
+            for (int a = 0; a < 3; ++a) {
+                g11[a] = gmu[a];
+                g11[3 + a] = dls[a] + 2.0 * gld;
+                a11[a] = amu[a];
+                a11[3 + a] = als[a];
+                t11[a] = tmu[a];
+                t11[3 + a] = tls[a];
+                b11[a] = bmu[a];
+                b11[3 + a] = bls[a];
+            }
+            for (int a = 0; a < 4; ++a) {
+                g11[6 + a] = dq[a];
+                a11[6 + a] = aq[a];
+                t11[6 + a] = tq[a];
+                b11[6 + a] = bq[a];
+            }
+            g11[10] = gc;
+            a11[10] = ac;
+            t11[10] = tc;
+            b11[10] = bc;
+            for (int a = 0; a < 11; ++a) {
+                if (gsel) gsel[a * n_sel + s] = g11[a];
+                if (asel) asel[a * n_sel + s] = a11[a];
+                if (tsel) tsel[a * n_sel + s] = t11[a];
+                if (bsel) bsel[a * n_sel + s] = b11[a];
+            }
+        }
+        free(buf);
+    }
+    grid_free(&GG);
+    grid_free(&GP);
+    free(mu);
+    free(xp);
+    free(up);
+    free(sp);
+    free(pred);
+    free(rbar);
+    free(lt);
+    free(rabs);
     model_free(&m);
     return 0;
 }

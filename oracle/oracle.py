@@ -58,6 +58,9 @@ def lib():
         _lib.oracle_count_pairs.restype = i64
         _lib.oracle_local_fd.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, d, i64, vp, vp, vp, vp, d, vp]
         _lib.oracle_local_fd.restype = C.c_int
+        _lib.oracle_local_grad.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, d, d, i64, vp, vp, vp, vp,
+                                           vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.oracle_local_grad.restype = C.c_int
     return _lib
 
 
@@ -259,3 +262,45 @@ def local_fd(stacks, theta, N, pix, I_pix, w_pix, params, h, cut=1e-12, norm_mod
     if rc != 0:
         raise RuntimeError("oracle_local_fd failed")
     return fd, pred, trunc
+
+
+def local_grad(stacks, theta, N, pix, I_pix, w_pix, sel, cut=1e-12, norm_mode=0, trunc_cut=1e-7):
+    """Large cases: the analytic gradient of the MSE loss over the listed
+    pixels (float64; pairs below `cut` dropped, pairs found through uniform
+    grids; see oracle_local_grad).  Returns a dict:
+    pred, trunc_pred (per listed pixel), loss;
+    g_sel, a_sel, t_sel (11 x len(sel): gradient, sum of |terms| and that sum
+    below trunc_cut, for every component of the selected Gaussians, rows in
+    the parameter order mu_xyz, ls_012, q_wxyz, c);
+    g_pose, a_pose, t_pose (6 M, the slice poses r, tau);
+    b_sel, b_pose: the sums of |terms| with every residual weight
+    2 w (I_hat_p - I_p) replaced by 2 w sum_j |c_j g_pj| (the scale at which a
+    relative rounding error of the predictions moves each gradient entry)."""
+    st = _stacks(stacks)
+    th = _f64(theta)
+    px = np.ascontiguousarray(pix, dtype=np.int64)
+    Ip = _f64(I_pix)
+    sl = np.ascontiguousarray(sel, dtype=np.int64)
+    M = num_slices(stacks)
+    out = {"pred": np.zeros(px.size), "trunc_pred": np.zeros(px.size), "loss": np.zeros(1)}
+    for k in ("g_sel", "a_sel", "t_sel", "b_sel"):
+        out[k] = np.zeros((11, sl.size))
+    for k in ("g_pose", "a_pose", "t_pose", "b_pose"):
+        out[k] = np.zeros(6 * M)
+    rc = lib().oracle_local_grad(len(stacks), st, int(N), th.ctypes.data, px.size, px.ctypes.data,
+                                 Ip.ctypes.data, float(w_pix), int(norm_mode), float(cut), float(trunc_cut),
+                                 sl.size, _p(sl) if sl.size else None, *[_p(out[k]) for k in (
+                                     "pred", "trunc_pred", "loss", "g_sel", "a_sel", "t_sel", "g_pose", "a_pose",
+                                     "t_pose", "b_sel", "b_pose")])
+    if rc != 0:
+        raise RuntimeError("oracle_local_grad failed")
+    out["loss"] = float(out["loss"][0])
+    return out
+
+
+def select_entries(N, M, sel):
+    """Parameter-vector indices of local_grad's outputs: (11 x len(sel)) for
+    the selected Gaussians' components, then the 6 M pose entries."""
+    sel = np.asarray(sel, dtype=np.int64)
+    comp = np.arange(11)[:, None] * int(N) + sel[None, :]
+    return comp, 11 * int(N) + np.arange(6 * int(M))
