@@ -546,6 +546,80 @@ gsvr_status gsvr_volume_metrics(int device, void *cuda_stream, int64_t D, int64_
                                 const float *Y, const uint8_t *mask, double data_range, double *out,
                                 double *ssim_map, char *msg, int32_t msg_len);
 
+/* Pixel weight of the loss (Sec. 2.5 takes the loss over the sampled points;
+ * here w_p = 1 / |sample|, its mean).  n_total > 0 sets w_p = 1 / n_total for
+ * every sampled pixel (every subject) instead of 1 / (this context's sample
+ * size), so that contexts holding disjoint parts of one reconstruction's
+ * slices (one per rank of a data-parallel split) each compute their exact
+ * share of the global loss and gradient: summing the contexts' losses and
+ * Gaussian gradients gives the global ones.  n_total = 0 restores the
+ * default.  Drops a captured graph.
+ * Errors: GSVR_ERR_INVALID_ARG (n_total < 0 or > 2^40), GSVR_ERR_STATE
+ * (during graph capture). */
+gsvr_status gsvr_set_sample_total(gsvr_ctx *ctx, int64_t n_total);
+
+/* Test hook for failure detection (no counterpart in the paper).  Every
+ * device-side wait of the library is bounded (1 s) and, when it runs out,
+ * latches a status bit that gsvr_sync_status reports as GSVR_ERR_TIMEOUT while
+ * the context stays usable.  To exercise that path without a fault, the next
+ * n_forwards calls of gsvr_forward make block 0 of the tile evaluation wait,
+ * for its first work item, on a shared-memory barrier that nothing ever
+ * completes, bounded by limit_ns (1 us .. 1 s); the wait runs out, the block
+ * stops taking work and still waits, with the normal bound, for the copies it
+ * started.  That forward's results are invalid (GSVR_ERR_TIMEOUT at the next
+ * gsvr_sync_status); the forwards after it are normal.
+ * Errors: GSVR_ERR_INVALID_ARG (bad counts or limit), GSVR_ERR_STATE (during
+ * graph capture). */
+gsvr_status gsvr_test_wait_timeout(gsvr_ctx *ctx, int32_t n_forwards, int64_t limit_ns);
+
+/* ---- checkpoint / resume.
+ * The optimisation state of the reconstruction: the Gaussian parameters
+ * (Sec. 2.2: mean, log-scales, quaternion, amplitude), the slice poses
+ * (Sec. 2.4), the Adam moments and the position in the step schedule (App. A.1:
+ * Adam with StepLR over hundreds of epochs, long enough that a run may need to
+ * stop and resume).  A checkpoint is one versioned binary file (host byte
+ * order): magic "GSVRCKPT", version 1, then tagged sections -- configuration
+ * (cutoff, normalisation, sampler seed, launch shape), stack descriptions,
+ * parameters with Adam m and v (11N + 6M float32 each), the device step
+ * counter (gsvr_set_step; drives the device sampler and the StepLR / bias
+ * correction of graph-replayed steps), frozen slices, objective, per-slice
+ * weights with their Adam state, top-K settings, subject tables and active
+ * flags, densification statistics -- and a 64-bit FNV-1a hash of all of it.
+ * Observations and masks are inputs, not state: they are not stored. */
+typedef struct gsvr_checkpoint_header {
+    int32_t version, n_stacks, n_slices, reserved;
+    int64_t n_pixels, n_gaussians, step;
+} gsvr_checkpoint_header;
+
+/* Writes the context's state to `path` (host file; written under path + ".tmp"
+ * and renamed over `path`).  Synchronises the stream.
+ * Errors: GSVR_ERR_STATE (no Gaussians yet, or during graph capture),
+ * GSVR_ERR_INVALID_ARG (NULL path, the file cannot be written), GSVR_ERR_CUDA. */
+gsvr_status gsvr_save(gsvr_ctx *ctx, const char *path);
+
+/* Restores a state written by gsvr_save into a context that already holds the
+ * same stacks (compared byte for byte) and its observations
+ * (gsvr_set_stacks, gsvr_set_observations): Gaussians (N may differ from the
+ * context's), poses, Adam moments, step counter, launch shape, sampler seed,
+ * cutoff and normalisation, frozen slices, objective, slice weights, top-K
+ * settings, subjects and densification statistics.  After it, the same pixel
+ * sample gives bitwise the forward, the Gaussian gradient and the Adam step of
+ * the Gaussians the saved context would have given (the slice-pose gradients
+ * are float atomics in a thread-timing order: equal to rounding, on any run).  Drops a captured graph (capture again); the top-K
+ * neighbour grid is rebuilt at the next forward.  The file is checked before
+ * anything changes.
+ * Errors: GSVR_ERR_INVALID_ARG (NULL path, unreadable file, bad magic,
+ * unsupported version, hash mismatch, malformed section), GSVR_ERR_STATE
+ * (stacks or observations not set, stacks differ, during graph capture),
+ * GSVR_ERR_NOMEM, GSVR_ERR_CUDA.  A failure after the checks leaves the
+ * context partly restored. */
+gsvr_status gsvr_load(gsvr_ctx *ctx, const char *path);
+
+/* Reads and checks a checkpoint file without a context or GPU: framing, magic,
+ * version, hash and the sizes of the required sections; fills *out.
+ * Errors: GSVR_ERR_INVALID_ARG (with the reason in msg when msg_len > 0). */
+gsvr_status gsvr_checkpoint_info(const char *path, gsvr_checkpoint_header *out, char *msg, int32_t msg_len);
+
 /* Forward pass without any device allocation (this entry point has no
  * counterpart in the paper; it exists for callers that cannot call cudaMalloc:
  * code running inside a host framework or plug-in whose device memory is owned
@@ -560,18 +634,25 @@ gsvr_status gsvr_volume_metrics(int device, void *cuda_stream, int64_t D, int64_
  *   theta       11N + 6M float32 parameters (device), the layout above.
  *   I           observed intensity per global pixel (device float32).
  *   idx, n_idx  sampled global pixel indices (device int32, duplicates count
- *               once); n_idx = -1 samples every pixel (idx may be NULL).
+ *               once, at most 2^30 entries; an index outside [0, P) returns
+ *               GSVR_ERR_INVALID_ARG); n_idx = -1 samples every pixel (idx may
+ *               be NULL).
  *   cutoff_rel, norm_mode  as in gsvr_config (0 -> 1e-7).
  *   pred        per global pixel (device float32); only sampled pixels written.
  *   loss        the MSE loss (device double).
  *   msg, msg_len optional host buffer receiving an error description.
- * Limits: problems whose tile maps, sample lists, records and keys do not fit
- * in 32 MiB (roughly up to ~10^5 pixels and ~10^5 (slice, Gaussian) records)
- * are rejected with GSVR_ERR_INVALID_ARG before any work, or return
- * GSVR_ERR_CAPACITY when the records or keys found on the device overflow.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture on that
- * device.  Every call shares the array and leaves its contents behind (each
+ * Limits: every pixel costs 29 bytes of the array (tile maps, sample lists,
+ * residual, mask), so at most 1,157,049 pixels fit, fewer once the tiles
+ * (about 1 KiB each) and Gaussians (40 bytes each) take their share; the rest
+ * holds records at about 212 bytes each (a record, its candidate, tile box
+ * and room for 4 keys with their sort buffers).  A problem whose pixel, tile
+ * and Gaussian arrays leave no room for records is rejected with
+ * GSVR_ERR_INVALID_ARG before any work; one whose (slice, Gaussian) records or
+ * keys found on the device overflow that room returns GSVR_ERR_CAPACITY
+ * (writes past the room are skipped; pred and loss are then incomplete).
+ * Every call looks up the array's device address (cudaGetSymbolAddress);
+ * the first call on a device also loads the library's device code there and
+ * should come before any stream capture on that device.  Every call shares the array and leaves its contents behind (each
  * call clears what must start at zero), so calls that overlap on the GPU --
  * on different streams or threads -- race and must not be issued.  The call
  * synchronises `cuda_stream` before it returns (to report device status). */

@@ -1059,7 +1059,10 @@ int oracle_local_fd(int n_stacks, const or_stack *st, int64_t N, const double *t
  *   bsel (11 x n_sel), bpose (6 M): the sum of |terms| with each pixel's
  *     residual weight 2 w (I_hat_p - I_p) replaced by 2 w sum_j |c_j g_pj|, the
  *     scale at which a relative rounding error of the prediction I_hat_p
- *     (a sum of |terms| summing to that) moves the gradient. */
+ *     (a sum of |terms| summing to that) moves the gradient;
+ *   btsel (11 x n_sel), btpose (6 M): the same with the residual weight
+ *     replaced by 2 w trunc_pred_p, how far dropping the pairs below trunc_cut
+ *     from the predictions moves the gradient through the residuals. */
 typedef struct {
     double a, dc, Go[9], gmu[3], dx[3], GR[9];
 } or_pair_grad;
@@ -1135,7 +1138,7 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
                       const int64_t *pix, const double *I_obs, double w_pix, int norm_mode, double cut,
                       double trunc_cut, int64_t n_sel, const int64_t *sel, double *pred_out, double *trunc_pred,
                       double *loss_out, double *gsel, double *asel, double *tsel, double *gpose, double *apose,
-                      double *tpose, double *bsel, double *bpose) {
+                      double *tpose, double *bsel, double *bpose, double *btsel, double *btpose) {
     or_model m;
     if (model_setup(n_stacks, st, N, theta, &m)) return -1;
     const int64_t M = m.M;
@@ -1155,7 +1158,8 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
     double *rbar = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double *lt = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double *rabs = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
-    if (!mu || !xp || !up || !sp || !pred || !rbar || !lt || !rabs) return -1;
+    double *rtr = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    if (!mu || !xp || !up || !sp || !pred || !rbar || !lt || !rabs || !rtr) return -1;
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t j = 0; j < N; ++j)
         for (int a = 0; a < 3; ++a) {
@@ -1189,6 +1193,7 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
         const double r = pred[p] - I_obs[p];
         rbar[p] = 2.0 * w_pix * r;
         rabs[p] = 2.0 * w_pix * ab;
+        rtr[p] = 2.0 * w_pix * t;
         lt[p] = w_pix * r * r;
     }
     if (pred_out) memcpy(pred_out, pred, sizeof(double) * (size_t)P);
@@ -1200,22 +1205,23 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
 #endif
     /* slice poses: pixel-major, per-thread slice accumulators dL/dR_i (9),
      * dL/dt_i (3), |.| of the pose entries (6), |.| below trunc_cut (6), |.| at
-     * the prediction-scale residual weights (6) */
-    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 30, sizeof(double));
+     * the prediction-scale residual weights (6), |.| at the truncation-scale
+     * residual weights (6) */
+    double *pacc = (double *)calloc((size_t)nthreads * (size_t)(M ? M : 1) * 36, sizeof(double));
 #pragma omp parallel
     {
         int tid = 0;
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 30;
+        double *my = pacc + (size_t)tid * (size_t)(M ? M : 1) * 36;
         int64_t *buf = NULL, cap = 0;
 #pragma omp for schedule(dynamic, 64)
         for (int64_t p = 0; p < P; ++p) {
             const int64_t i = sp[p];
             const double *x = xp + 3 * p, *u = up + 3 * p;
             const int64_t n = grid_near(&GG, mu, x, rad2, &buf, &cap);
-            double *acc = my + 30 * i;
+            double *acc = my + 36 * i;
             for (int64_t k = 0; k < n; ++k) {
                 const or_gauss *gj = &m.g[buf[k]];
                 or_pair pr;
@@ -1235,19 +1241,23 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
                 pair_grad(gj, &m.sl[i], &m.fr[i], &pr, u, rabs[p], norm_mode, &ob);
                 pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &ob, u, norm_mode, d6, als, aq);
                 for (int a = 0; a < 6; ++a) acc[24 + a] += fabs(d6[a]);
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, u, rtr[p], norm_mode, &ob);
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &ob, u, norm_mode, d6, als, aq);
+                for (int a = 0; a < 6; ++a) acc[30 + a] += fabs(d6[a]);
             }
         }
         free(buf);
     }
     for (int64_t i = 0; i < M; ++i) {
-        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0}, tb[6] = {0}, bb[6] = {0};
+        double GR[9] = {0}, Gt[3] = {0}, ab[6] = {0}, tb[6] = {0}, bb[6] = {0}, bt[6] = {0};
         for (int t = 0; t < nthreads; ++t) {
-            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 30;
+            const double *acc = pacc + ((size_t)t * (size_t)M + (size_t)i) * 36;
             for (int e = 0; e < 9; ++e) GR[e] += acc[e];
             for (int a = 0; a < 3; ++a) Gt[a] += acc[9 + a];
             for (int a = 0; a < 6; ++a) ab[a] += acc[12 + a];
             for (int a = 0; a < 6; ++a) tb[a] += acc[18 + a];
             for (int a = 0; a < 6; ++a) bb[a] += acc[24 + a];
+            for (int a = 0; a < 6; ++a) bt[a] += acc[30 + a];
         }
         double d6[6];
         pose_chain(&m.sl[i], theta + 11 * N + 6 * i, GR, Gt, d6);
@@ -1256,6 +1266,7 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
             if (apose) apose[6 * i + a] = ab[a];
             if (tpose) tpose[6 * i + a] = tb[a];
             if (bpose) bpose[6 * i + a] = bb[a];
+            if (btpose) btpose[6 * i + a] = bt[a];
         }
     }
     free(pacc);
@@ -1272,6 +1283,7 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
             double amu[3] = {0, 0, 0}, als[3] = {0, 0, 0}, aq[4] = {0, 0, 0, 0}, ac = 0.0;
             double tmu[3] = {0, 0, 0}, tls[3] = {0, 0, 0}, tq[4] = {0, 0, 0, 0}, tc = 0.0;
             double bmu[3] = {0, 0, 0}, bls[3] = {0, 0, 0}, bq[4] = {0, 0, 0, 0}, bc = 0.0;
+            double umu[3] = {0, 0, 0}, uls[3] = {0, 0, 0}, uq[4] = {0, 0, 0, 0}, uc = 0.0;
             const int64_t n = grid_near(&GP, xp, gj->mu, rad2, &buf, &cap);
             for (int64_t k = 0; k < n; ++k) {
                 const int64_t p = buf[k], i = sp[p];
@@ -1313,10 +1325,19 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
                 }
                 for (int a = 0; a < 4; ++a) bq[a] += pq[a];
                 bc += fabs(ob.dc);
+                pair_grad(gj, &m.sl[i], &m.fr[i], &pr, up + 3 * p, rtr[p], norm_mode, &ob);
+                pair_grad_abs(gj, &m.sl[i], &m.fr[i], theta + 11 * N + 6 * i, &ob, up + 3 * p, norm_mode, d6, pls,
+                              pq);
+                for (int a = 0; a < 3; ++a) {
+                    umu[a] += fabs(ob.gmu[a]);
+                    uls[a] += pls[a];
+                }
+                for (int a = 0; a < 4; ++a) uq[a] += pq[a];
+                uc += fabs(ob.dc);
             }
             double dls[3], dq[4];
             cov_chain(gj, GS, dls, dq);
-            double g11[11], a11[11], t11[11], b11[11];
+            double g11[11], a11[11], t11[11], b11[11], u11[11];
             for (int a = 0; a < 3; ++a) {
                 g11[a] = gmu[a];
                 g11[3 + a] = dls[a] + 2.0 * gld;
@@ -1326,22 +1347,27 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
                 t11[3 + a] = tls[a];
                 b11[a] = bmu[a];
                 b11[3 + a] = bls[a];
+                u11[a] = umu[a];
+                u11[3 + a] = uls[a];
             }
             for (int a = 0; a < 4; ++a) {
                 g11[6 + a] = dq[a];
                 a11[6 + a] = aq[a];
                 t11[6 + a] = tq[a];
                 b11[6 + a] = bq[a];
+                u11[6 + a] = uq[a];
             }
             g11[10] = gc;
             a11[10] = ac;
             t11[10] = tc;
             b11[10] = bc;
+            u11[10] = uc;
             for (int a = 0; a < 11; ++a) {
                 if (gsel) gsel[a * n_sel + s] = g11[a];
                 if (asel) asel[a * n_sel + s] = a11[a];
                 if (tsel) tsel[a * n_sel + s] = t11[a];
                 if (bsel) bsel[a * n_sel + s] = b11[a];
+                if (btsel) btsel[a * n_sel + s] = u11[a];
             }
         }
         free(buf);
@@ -1356,6 +1382,7 @@ int oracle_local_grad(int n_stacks, const or_stack *st, int64_t N, const double 
     free(rbar);
     free(lt);
     free(rabs);
+    free(rtr);
     model_free(&m);
     return 0;
 }

@@ -59,7 +59,7 @@ def lib():
         _lib.oracle_local_fd.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, d, i64, vp, vp, vp, vp, d, vp]
         _lib.oracle_local_fd.restype = C.c_int
         _lib.oracle_local_grad.argtypes = [C.c_int, vp, i64, vp, i64, vp, vp, d, C.c_int, d, d, i64, vp, vp, vp, vp,
-                                           vp, vp, vp, vp, vp, vp, vp, vp]
+                                           vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib.oracle_local_grad.restype = C.c_int
     return _lib
 
@@ -275,7 +275,9 @@ def local_grad(stacks, theta, N, pix, I_pix, w_pix, sel, cut=1e-12, norm_mode=0,
     g_pose, a_pose, t_pose (6 M, the slice poses r, tau);
     b_sel, b_pose: the sums of |terms| with every residual weight
     2 w (I_hat_p - I_p) replaced by 2 w sum_j |c_j g_pj| (the scale at which a
-    relative rounding error of the predictions moves each gradient entry)."""
+    relative rounding error of the predictions moves each gradient entry);
+    bt_sel, bt_pose: the same with 2 w trunc_pred_p (how far dropping the pairs
+    below trunc_cut from the predictions moves each entry through the residuals)."""
     st = _stacks(stacks)
     th = _f64(theta)
     px = np.ascontiguousarray(pix, dtype=np.int64)
@@ -283,15 +285,15 @@ def local_grad(stacks, theta, N, pix, I_pix, w_pix, sel, cut=1e-12, norm_mode=0,
     sl = np.ascontiguousarray(sel, dtype=np.int64)
     M = num_slices(stacks)
     out = {"pred": np.zeros(px.size), "trunc_pred": np.zeros(px.size), "loss": np.zeros(1)}
-    for k in ("g_sel", "a_sel", "t_sel", "b_sel"):
+    for k in ("g_sel", "a_sel", "t_sel", "b_sel", "bt_sel"):
         out[k] = np.zeros((11, sl.size))
-    for k in ("g_pose", "a_pose", "t_pose", "b_pose"):
+    for k in ("g_pose", "a_pose", "t_pose", "b_pose", "bt_pose"):
         out[k] = np.zeros(6 * M)
     rc = lib().oracle_local_grad(len(stacks), st, int(N), th.ctypes.data, px.size, px.ctypes.data,
                                  Ip.ctypes.data, float(w_pix), int(norm_mode), float(cut), float(trunc_cut),
                                  sl.size, _p(sl) if sl.size else None, *[_p(out[k]) for k in (
                                      "pred", "trunc_pred", "loss", "g_sel", "a_sel", "t_sel", "g_pose", "a_pose",
-                                     "t_pose", "b_sel", "b_pose")])
+                                     "t_pose", "b_sel", "b_pose", "bt_sel", "bt_pose")])
     if rc != 0:
         raise RuntimeError("oracle_local_grad failed")
     out["loss"] = float(out["loss"][0])

@@ -105,7 +105,7 @@ struct gsvr_ctx {
     bool slw_on = false;
     float lr_slw_sig = 1e-3f, lr_slw_omg = 1e-2f;
     DBuf<float> d_slw, d_slw_grad, d_slw_m, d_slw_v;
-    DBuf<double> d_slw_gacc;
+    DBuf<double> d_slw_gacc, d_slw_tile;
     // content-adaptive initialisation scratch (gsvr_init_means)
     DBuf<int64_t> d_init_w, d_init_c, d_init_s;
     DBuf<float> d_init_pose, d_init_thick;
@@ -136,6 +136,9 @@ struct gsvr_ctx {
     DBuf<Counters> d_counters;
 
     bool have_stacks = false, have_obs = false, have_gauss = false, have_sample = false, fwd_valid = false;
+    int64_t sample_total = 0;      // gsvr_set_sample_total: pixel weight 1 / sample_total (0: own sample size)
+    int test_wait_forwards = 0;    // gsvr_test_wait_timeout: forwards left that run the hook
+    int64_t test_wait_ns = 0;
 
     // subjects (batched form): stacks -> subject, contiguous Gaussian ranges
     int n_subj = 1;
@@ -322,11 +325,14 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.l1 = ctx->loss_kind;
     e.slw = ctx->slw_on ? ctx->d_slw.p : nullptr;
     e.slw_gacc = ctx->d_slw_gacc.p;
+    e.slw_tile = ctx->d_slw_tile.p;
     e.M = ctx->M;
     e.tile_w = ctx->tile_w;
     e.tile_h = ctx->tile_h;
     e.n_tiles = ctx->n_tiles;
     e.status = ctx->d_status.p;
+    e.n_weight = ctx->sample_total;
+    e.qcut = (float)std::log2((double)ctx->cfg.cutoff_rel);
     return e;
 }
 
@@ -1135,6 +1141,7 @@ TopkArgs topk_args(gsvr_ctx *ctx) {
     a.slw = ctx->slw_on ? ctx->d_slw.p : nullptr;
     a.slw_gacc = ctx->d_slw_gacc.p;
     a.status = ctx->d_status.p;
+    a.n_weight = ctx->sample_total;
     return a;
 }
 
@@ -1192,6 +1199,10 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     const int N = (int)ctx->N, M = ctx->M;
     Counters *cnt = ctx->d_counters.p;
     const bool grow = !ctx->cfg.fixed_capacity;
+    if (ctx->slw_on && ctx->d_slw_tile.n < 2 * (size_t)std::max(ctx->n_tiles, 1)) {
+        if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "per-tile slice-weight buffer must exist before capture");
+        CK(ctx->d_slw_tile.ensure(2 * (size_t)std::max(ctx->n_tiles, 1)));
+    }
     stage_begin(ctx, GSVR_STAGE_PREP);
     CK(cudaMemsetAsync(&cnt->pairs, 0, sizeof(unsigned long long), st));
     if (ctx->slw_on) CK(cudaMemsetAsync(ctx->d_slw_gacc.p, 0, sizeof(double) * 2 * (size_t)M, st));
@@ -1308,9 +1319,14 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     stage_end(ctx, GSVR_STAGE_BIN);
     ctx->grid_items = ctx->n_tiles + n_keys_max / kItemRecs + 2;
     EvalArgs e = eval_args(ctx, ctx->grid_items);
+    if (ctx->test_wait_forwards > 0) {
+        e.wait_test_ns = ctx->test_wait_ns;
+        --ctx->test_wait_forwards;
+    }
     stage_begin(ctx, GSVR_STAGE_FWD_EVAL);
     launch_forward(e, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
+    if (ctx->slw_on) launch_slw_slices(ctx->d_slw_tile.p, ctx->d_slices.p, M, ctx->d_slw_gacc.p, st);
     launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_subj_tile_first.p, ctx->n_subj, ctx->d_subj_loss.p,
                        ctx->d_loss.p, ctx->d_status.p, st);
     if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
@@ -1394,6 +1410,31 @@ gsvr_status gsvr_adam_step(gsvr_ctx *ctx, const gsvr_adam_cfg *cfg, int64_t step
     if (!cfg || step < 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "adam config NULL or step < 1");
     DeviceGuard g(ctx->device);
     return adam_launch(ctx, cfg, step, nullptr);
+}
+
+gsvr_status gsvr_set_sample_total(gsvr_ctx *ctx, int64_t n_total) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (n_total < 0 || n_total > (int64_t)1 << 40) return fail(ctx, GSVR_ERR_INVALID_ARG, "n_total must be in [0, 2^40]");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_set_sample_total during graph capture");
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->sample_total = n_total;
+    ctx->fwd_valid = false;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_test_wait_timeout(gsvr_ctx *ctx, int32_t n_forwards, int64_t limit_ns) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (n_forwards < 0 || limit_ns < 1000 || limit_ns > 1000000000)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "n_forwards >= 0 and limit_ns in [1e3, 1e9] needed");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_test_wait_timeout during graph capture");
+    ctx->test_wait_forwards = n_forwards;
+    ctx->test_wait_ns = limit_ns;
+    return GSVR_OK;
 }
 
 gsvr_status gsvr_set_step(gsvr_ctx *ctx, int64_t step) {
@@ -1736,6 +1777,7 @@ gsvr_status gsvr_set_slice_weights(gsvr_ctx *ctx, int32_t enable, float lr_log_s
     CK(ctx->d_slw_m.ensure(n));
     CK(ctx->d_slw_v.ensure(n));
     CK(ctx->d_slw_gacc.ensure(n));
+    CK(ctx->d_slw_tile.ensure(2 * (size_t)std::max(ctx->n_tiles, 1)));
     for (DBuf<float> *b : {&ctx->d_slw, &ctx->d_slw_grad, &ctx->d_slw_m, &ctx->d_slw_v})
         CK(cudaMemsetAsync(b->p, 0, sizeof(float) * n, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_slw_gacc.p, 0, sizeof(double) * n, ctx->stream));
@@ -2053,6 +2095,486 @@ gsvr_status gsvr_autotune(gsvr_ctx *ctx, gsvr_tiling *cand, int32_t n_cand, int6
     if (best) *best = bi;
     gsvr_status s = gsvr_set_tiling(ctx, &cand[bi]);
     if (s) return s;
+    return GSVR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- checkpoints
+// File layout (host byte order, the writer's): magic "GSVRCKPT", u32 version,
+// u32 section count, then sections (u32 tag, u32 0, u64 byte length, payload),
+// then u64 FNV-1a hash of every byte before it.
+namespace {
+
+constexpr char kCkptMagic[8] = {'G', 'S', 'V', 'R', 'C', 'K', 'P', 'T'};
+constexpr uint32_t kCkptVersion = 1;
+enum : uint32_t {
+    kSecConfig = 1,
+    kSecGeometry = 2,
+    kSecParams = 3,
+    kSecStep = 4,
+    kSecFrozen = 5,
+    kSecObjective = 6,
+    kSecSliceWeights = 7,
+    kSecTopk = 8,
+    kSecSubjects = 9,
+    kSecDensify = 10,
+    kSecCount = 10
+};
+
+uint64_t fnv1a(const unsigned char *p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t k = 0; k < n; ++k) {
+        h ^= p[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct CkptWriter {
+    std::vector<unsigned char> buf;
+    size_t sec_len_at = 0;
+    template <class T>
+    void put(const T &v) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+        buf.insert(buf.end(), b, b + sizeof(T));
+    }
+    void put_bytes(const void *p, size_t n) {
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(p);
+        buf.insert(buf.end(), b, b + n);
+    }
+    void begin(uint32_t tag) {
+        put(tag);
+        put(uint32_t(0));
+        sec_len_at = buf.size();
+        put(uint64_t(0));
+    }
+    void end() {
+        const uint64_t len = buf.size() - sec_len_at - sizeof(uint64_t);
+        std::memcpy(&buf[sec_len_at], &len, sizeof(len));
+    }
+};
+
+// One parsed checkpoint: every section's payload, validated for framing.
+struct CkptFile {
+    std::vector<unsigned char> data;
+    const unsigned char *sec[kSecCount + 1] = {};
+    uint64_t len[kSecCount + 1] = {};
+};
+
+struct CkptReader {
+    const unsigned char *p;
+    uint64_t n, off = 0;
+    bool ok = true;
+    template <class T>
+    T get() {
+        T v{};
+        if (off + sizeof(T) > n) {
+            ok = false;
+            return v;
+        }
+        std::memcpy(&v, p + off, sizeof(T));
+        off += sizeof(T);
+        return v;
+    }
+    const unsigned char *take(uint64_t bytes) {
+        if (bytes > n || off + bytes > n) {
+            ok = false;
+            return nullptr;
+        }
+        const unsigned char *q = p + off;
+        off += bytes;
+        return q;
+    }
+};
+
+// Reads and checks the framing of a checkpoint: magic, version, hash, section
+// tags (each known, at most once; config, geometry, params and step present).
+std::string ckpt_read(const char *path, CkptFile &f) {
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return "cannot open checkpoint file";
+    std::fseek(fp, 0, SEEK_END);
+    const long sz = std::ftell(fp);
+    std::fseek(fp, 0, SEEK_SET);
+    if (sz < 0) {
+        std::fclose(fp);
+        return "cannot size checkpoint file";
+    }
+    f.data.resize((size_t)sz);
+    const size_t got = sz > 0 ? std::fread(f.data.data(), 1, (size_t)sz, fp) : 0;
+    std::fclose(fp);
+    if (got != (size_t)sz) return "short read of checkpoint file";
+    if (f.data.size() < 16 + sizeof(uint64_t) || std::memcmp(f.data.data(), kCkptMagic, 8) != 0)
+        return "not a gsvr checkpoint (bad magic)";
+    uint32_t version = 0, nsec = 0;
+    std::memcpy(&version, f.data.data() + 8, 4);
+    std::memcpy(&nsec, f.data.data() + 12, 4);
+    if (version != kCkptVersion) return "unsupported checkpoint version " + std::to_string(version);
+    const size_t body = f.data.size() - sizeof(uint64_t);
+    uint64_t h = 0;
+    std::memcpy(&h, f.data.data() + body, sizeof(h));
+    if (h != fnv1a(f.data.data(), body)) return "checkpoint hash mismatch (truncated or corrupted file)";
+    CkptReader r{f.data.data(), body, 16};
+    for (uint32_t s = 0; s < nsec; ++s) {
+        const uint32_t tag = r.get<uint32_t>();
+        r.get<uint32_t>();
+        const uint64_t len = r.get<uint64_t>();
+        const unsigned char *q = r.take(len);
+        if (!r.ok) return "checkpoint section runs past the end of the file";
+        if (tag < 1 || tag > kSecCount || f.sec[tag]) return "unknown or repeated checkpoint section";
+        f.sec[tag] = q;
+        f.len[tag] = len;
+    }
+    if (r.off != body) return "trailing bytes after the last checkpoint section";
+    for (uint32_t t : {kSecConfig, kSecGeometry, kSecParams, kSecStep})
+        if (!f.sec[t]) return "checkpoint lacks a required section";
+    return "";
+}
+
+struct CkptHead {
+    int32_t n_stacks = 0, M = 0;
+    int64_t P = 0, N = 0;
+    uint64_t step = 0;
+};
+
+std::string ckpt_head(const CkptFile &f, CkptHead &h) {
+    CkptReader g{f.sec[kSecGeometry], f.len[kSecGeometry]};
+    h.n_stacks = g.get<int32_t>();
+    h.M = g.get<int32_t>();
+    h.P = g.get<int64_t>();
+    if (!g.ok || h.n_stacks < 1 || h.M < 1 || h.P < 1 ||
+        f.len[kSecGeometry] != 16 + (uint64_t)h.n_stacks * sizeof(gsvr_stack_desc))
+        return "malformed checkpoint geometry section";
+    CkptReader p{f.sec[kSecParams], f.len[kSecParams]};
+    h.N = p.get<int64_t>();
+    if (!p.ok || h.N < 0 || h.N > (1LL << 26) ||
+        f.len[kSecParams] != 8 + 3ull * sizeof(float) * (uint64_t)(11 * h.N + 6 * (int64_t)h.M))
+        return "malformed checkpoint parameter section";
+    CkptReader s{f.sec[kSecStep], f.len[kSecStep]};
+    h.step = s.get<uint64_t>();
+    if (!s.ok || f.len[kSecStep] != 8) return "malformed checkpoint step section";
+    return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+gsvr_status gsvr_checkpoint_info(const char *path, gsvr_checkpoint_header *out, char *msg, int32_t msg_len) {
+    auto say = [&](const std::string &m) {
+        if (msg && msg_len > 0) {
+            std::strncpy(msg, m.c_str(), (size_t)msg_len - 1);
+            msg[msg_len - 1] = '\0';
+        }
+    };
+    say("");
+    if (!path || !out) {
+        say("path or out is NULL");
+        return GSVR_ERR_INVALID_ARG;
+    }
+    CkptFile f;
+    std::string e = ckpt_read(path, f);
+    CkptHead h;
+    if (e.empty()) e = ckpt_head(f, h);
+    if (!e.empty()) {
+        say(e);
+        return GSVR_ERR_INVALID_ARG;
+    }
+    out->version = (int32_t)kCkptVersion;
+    out->n_stacks = h.n_stacks;
+    out->n_slices = h.M;
+    out->n_pixels = h.P;
+    out->n_gaussians = h.N;
+    out->step = (int64_t)h.step;
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_save(gsvr_ctx *ctx, const char *path) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!path) return fail(ctx, GSVR_ERR_INVALID_ARG, "path is NULL");
+    if (!ctx->have_gauss) return fail(ctx, GSVR_ERR_STATE, "nothing to save before gsvr_set_gaussians");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_save during graph capture");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    const int M = ctx->M;
+    const int64_t N = ctx->N;
+    const size_t np = (size_t)(11 * N + 6 * M);
+    std::vector<float> th(np), m(np), v(np);
+    CK(cudaMemcpy(th.data(), ctx->d_theta.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(m.data(), ctx->d_m.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(v.data(), ctx->d_v.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    Counters cnt{};
+    CK(cudaMemcpy(&cnt, ctx->d_counters.p, sizeof(Counters), cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> frozen((size_t)M, 0);
+    if (ctx->any_frozen) CK(cudaMemcpy(frozen.data(), ctx->d_frozen.p, (size_t)M, cudaMemcpyDeviceToHost));
+
+    CkptWriter w;
+    w.put_bytes(kCkptMagic, 8);
+    w.put(kCkptVersion);
+    w.put(uint32_t(0));  // section count, patched below
+    uint32_t nsec = 0;
+    w.begin(kSecConfig);
+    w.put(ctx->cfg.cutoff_rel);
+    w.put(ctx->cfg.norm_mode);
+    w.put(ctx->cfg.seed);
+    for (int32_t x : {ctx->tile_h, ctx->tile_w, ctx->fwd_pxr_req, ctx->fwd_bps, ctx->bwd_bps, ctx->queue_order})
+        w.put(x);
+    w.end();
+    ++nsec;
+    w.begin(kSecGeometry);
+    w.put((int32_t)ctx->n_stacks);
+    w.put((int32_t)M);
+    w.put((int64_t)ctx->P);
+    w.put_bytes(ctx->h_stack_desc.data(), sizeof(gsvr_stack_desc) * ctx->h_stack_desc.size());
+    w.end();
+    ++nsec;
+    w.begin(kSecParams);
+    w.put((int64_t)N);
+    w.put_bytes(th.data(), sizeof(float) * np);
+    w.put_bytes(m.data(), sizeof(float) * np);
+    w.put_bytes(v.data(), sizeof(float) * np);
+    w.end();
+    ++nsec;
+    w.begin(kSecStep);
+    w.put((uint64_t)cnt.step);
+    w.end();
+    ++nsec;
+    w.begin(kSecFrozen);
+    w.put_bytes(frozen.data(), frozen.size());
+    w.end();
+    ++nsec;
+    w.begin(kSecObjective);
+    w.put((int32_t)ctx->loss_kind);
+    w.put(ctx->lambda_reg);
+    w.put(ctx->s_target);
+    w.end();
+    ++nsec;
+    w.begin(kSecSliceWeights);
+    w.put((int32_t)(ctx->slw_on ? 1 : 0));
+    w.put(ctx->lr_slw_sig);
+    w.put(ctx->lr_slw_omg);
+    if (ctx->slw_on) {
+        std::vector<float> sp(2 * (size_t)M);
+        for (DBuf<float> *b : {&ctx->d_slw, &ctx->d_slw_m, &ctx->d_slw_v}) {
+            CK(cudaMemcpy(sp.data(), b->p, sizeof(float) * sp.size(), cudaMemcpyDeviceToHost));
+            w.put_bytes(sp.data(), sizeof(float) * sp.size());
+        }
+    }
+    w.end();
+    ++nsec;
+    w.begin(kSecTopk);
+    w.put((int32_t)ctx->topk_K);
+    w.put((int32_t)ctx->topk_refresh);
+    w.put(ctx->topk_delta);
+    w.put(ctx->topk_per_cell);
+    w.end();
+    ++nsec;
+    w.begin(kSecSubjects);
+    w.put((int32_t)ctx->n_subj);
+    if (ctx->n_subj > 1) {
+        w.put_bytes(ctx->h_stack_subject.data(), sizeof(int) * (size_t)ctx->n_stacks);
+        w.put_bytes(ctx->h_subj_gauss_first.data(), sizeof(int64_t) * ((size_t)ctx->n_subj + 1));
+    }
+    w.put((int32_t)ctx->h_subj_active.size());
+    w.put_bytes(ctx->h_subj_active.data(), ctx->h_subj_active.size());
+    w.end();
+    ++nsec;
+    w.begin(kSecDensify);
+    const int64_t dn = (ctx->dens_n == N && ctx->d_dens_acc.p && ctx->d_dens_cnt.p) ? N : -1;
+    w.put(dn);
+    if (dn >= 0) {
+        std::vector<float4> acc((size_t)std::max<int64_t>(N, 1));
+        int c = 0;
+        CK(cudaMemcpy(acc.data(), ctx->d_dens_acc.p, sizeof(float4) * acc.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&c, ctx->d_dens_cnt.p, sizeof(int), cudaMemcpyDeviceToHost));
+        w.put_bytes(acc.data(), sizeof(float4) * (size_t)N);
+        w.put((int32_t)c);
+    }
+    w.end();
+    ++nsec;
+    std::memcpy(&w.buf[12], &nsec, sizeof(nsec));
+    const uint64_t h = fnv1a(w.buf.data(), w.buf.size());
+    w.put(h);
+
+    // written to a temporary name, then renamed over `path`
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *fp = std::fopen(tmp.c_str(), "wb");
+    if (!fp) return fail(ctx, GSVR_ERR_INVALID_ARG, "cannot open checkpoint file for writing");
+    const size_t put = std::fwrite(w.buf.data(), 1, w.buf.size(), fp);
+    const int cl = std::fclose(fp);
+    if (put != w.buf.size() || cl != 0 || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "writing the checkpoint file failed");
+    }
+    return GSVR_OK;
+}
+
+gsvr_status gsvr_load(gsvr_ctx *ctx, const char *path) {
+    if (check_ctx(ctx)) return GSVR_ERR_INVALID_ARG;
+    if (!path) return fail(ctx, GSVR_ERR_INVALID_ARG, "path is NULL");
+    if (!ctx->have_stacks || !ctx->have_obs)
+        return fail(ctx, GSVR_ERR_STATE, "gsvr_set_stacks and gsvr_set_observations before gsvr_load");
+    if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "gsvr_load during graph capture");
+    CkptFile f;
+    std::string e = ckpt_read(path, f);
+    CkptHead hd;
+    if (e.empty()) e = ckpt_head(f, hd);
+    if (!e.empty()) return fail(ctx, GSVR_ERR_INVALID_ARG, e);
+    // the context must hold the same acquisition (stacks compared byte for byte)
+    if (hd.n_stacks != ctx->n_stacks || hd.M != ctx->M || hd.P != ctx->P ||
+        std::memcmp(f.sec[kSecGeometry] + 16, ctx->h_stack_desc.data(),
+                    sizeof(gsvr_stack_desc) * (size_t)ctx->n_stacks) != 0)
+        return fail(ctx, GSVR_ERR_STATE, "checkpoint stacks differ from the context's");
+    const int M = ctx->M;
+    const int64_t N = hd.N;
+    const size_t np = (size_t)(11 * N + 6 * M);
+    // parse every optional section before changing anything
+    CkptReader rc{f.sec[kSecConfig], f.len[kSecConfig]};
+    const float cutoff = rc.get<float>();
+    const int32_t norm_mode = rc.get<int32_t>();
+    const uint64_t seed = rc.get<uint64_t>();
+    gsvr_tiling tl{};
+    tl.tile_h = rc.get<int32_t>();
+    tl.tile_w = rc.get<int32_t>();
+    tl.fwd_px_per_thread = rc.get<int32_t>();
+    tl.fwd_blocks_per_sm = rc.get<int32_t>();
+    tl.bwd_blocks_per_sm = rc.get<int32_t>();
+    tl.queue_order = rc.get<int32_t>();
+    if (!rc.ok || rc.off != rc.n || !(cutoff > 0.f && cutoff < 1.f) ||
+        (norm_mode != GSVR_NORM_EXACT && norm_mode != GSVR_NORM_LITERAL))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed checkpoint config section");
+    if (gsvr_status s = check_tiling(ctx, tl)) return s;
+    // the payload is copied out: sections follow one another at any byte offset
+    std::vector<float> th(3 * np);
+    std::memcpy(th.data(), f.sec[kSecParams] + 8, sizeof(float) * th.size());
+    std::vector<uint8_t> frozen((size_t)M, 0);
+    if (f.sec[kSecFrozen]) {
+        if (f.len[kSecFrozen] != (uint64_t)M) return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed frozen section");
+        std::memcpy(frozen.data(), f.sec[kSecFrozen], (size_t)M);
+    }
+    int32_t loss_kind = 0;
+    float lambda_reg = 0.f, s_target = 1.6f;
+    if (f.sec[kSecObjective]) {
+        CkptReader r{f.sec[kSecObjective], f.len[kSecObjective]};
+        loss_kind = r.get<int32_t>();
+        lambda_reg = r.get<float>();
+        s_target = r.get<float>();
+        if (!r.ok || r.off != r.n) return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed objective section");
+    }
+    int32_t slw_on = 0;
+    float lr_sig = 1e-3f, lr_omg = 1e-2f;
+    std::vector<float> slw;
+    if (f.sec[kSecSliceWeights]) {
+        CkptReader r{f.sec[kSecSliceWeights], f.len[kSecSliceWeights]};
+        slw_on = r.get<int32_t>();
+        lr_sig = r.get<float>();
+        lr_omg = r.get<float>();
+        if (slw_on) {
+            const unsigned char *q = r.take(3ull * 2 * sizeof(float) * (uint64_t)M);
+            if (q) {
+                slw.resize(6 * (size_t)M);
+                std::memcpy(slw.data(), q, sizeof(float) * slw.size());
+            }
+        }
+        if (!r.ok || r.off != r.n) return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed slice-weight section");
+    }
+    int32_t topk_K = 0, topk_refresh = 1;
+    float topk_delta = 1e-8f, topk_per_cell = 16.f;
+    if (f.sec[kSecTopk]) {
+        CkptReader r{f.sec[kSecTopk], f.len[kSecTopk]};
+        topk_K = r.get<int32_t>();
+        topk_refresh = r.get<int32_t>();
+        topk_delta = r.get<float>();
+        topk_per_cell = r.get<float>();
+        if (!r.ok || r.off != r.n || !(topk_per_cell > 0.f))
+            return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed top-K section");
+    }
+    int32_t n_subj = 1, n_active = 0;
+    std::vector<int32_t> stack_subject;
+    std::vector<int64_t> gauss_count;
+    std::vector<uint8_t> active;
+    if (f.sec[kSecSubjects]) {
+        CkptReader r{f.sec[kSecSubjects], f.len[kSecSubjects]};
+        n_subj = r.get<int32_t>();
+        if (n_subj > 1 && n_subj <= 65536) {
+            stack_subject.resize((size_t)ctx->n_stacks);
+            std::vector<int64_t> gf((size_t)n_subj + 1);
+            const unsigned char *a = r.take(sizeof(int32_t) * stack_subject.size());
+            const unsigned char *b = r.take(sizeof(int64_t) * gf.size());
+            if (a && b) {
+                std::memcpy(stack_subject.data(), a, sizeof(int32_t) * stack_subject.size());
+                std::memcpy(gf.data(), b, sizeof(int64_t) * gf.size());
+                for (int k = 0; k < n_subj; ++k) gauss_count.push_back(gf[(size_t)k + 1] - gf[(size_t)k]);
+            }
+        }
+        n_active = r.get<int32_t>();
+        if (n_active > 0 && n_active == n_subj) {
+            const unsigned char *a = r.take((uint64_t)n_active);
+            if (a) active.assign(a, a + n_active);
+        } else if (n_active != 0) {
+            r.ok = false;
+        }
+        if (!r.ok || r.off != r.n || n_subj < 1 || n_subj > 65536)
+            return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed subject section");
+    }
+    int64_t dens_n = -1;
+    std::vector<float4> dens_acc;
+    int32_t dens_cnt = 0;
+    if (f.sec[kSecDensify]) {
+        CkptReader r{f.sec[kSecDensify], f.len[kSecDensify]};
+        dens_n = r.get<int64_t>();
+        if (dens_n >= 0) {
+            if (dens_n != N) r.ok = false;
+            else if (const unsigned char *q = r.take(sizeof(float4) * (uint64_t)N)) {
+                dens_acc.resize((size_t)std::max<int64_t>(N, 1));
+                std::memcpy(dens_acc.data(), q, sizeof(float4) * (size_t)N);
+            }
+            dens_cnt = r.get<int32_t>();
+        }
+        if (!r.ok || r.off != r.n) return fail(ctx, GSVR_ERR_INVALID_ARG, "malformed densification section");
+    }
+
+    // apply: configuration and launch shape, parameters, then the optimiser state
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    drop_graph(ctx);
+    ctx->cfg.cutoff_rel = cutoff;
+    ctx->cfg.norm_mode = norm_mode;
+    ctx->cfg.seed = seed;
+    ctx->rc2 = (float)(2.0 * std::log(1.0 / (double)cutoff));
+    if (gsvr_status s = gsvr_set_tiling(ctx, &tl)) return s;
+    if (gsvr_status s = gsvr_set_gaussians(ctx, N, th.data(), GSVR_MEM_HOST)) return s;
+    if (n_subj > 1) {
+        if (gsvr_status s = gsvr_set_subjects(ctx, n_subj, stack_subject.data(), gauss_count.data())) return s;
+    } else if (ctx->n_subj != 1) {
+        if (gsvr_status s = gsvr_set_subjects(ctx, 1, nullptr, nullptr)) return s;
+    }
+    if (!active.empty())
+        if (gsvr_status s = gsvr_set_subject_active(ctx, active.data())) return s;
+    if (gsvr_status s = gsvr_set_frozen(ctx, frozen.data())) return s;
+    if (gsvr_status s = gsvr_set_objective(ctx, loss_kind, lambda_reg, s_target)) return s;
+    if (gsvr_status s = gsvr_set_slice_weights(ctx, slw_on, lr_sig, lr_omg)) return s;
+    ctx->topk_per_cell = topk_per_cell;
+    if (gsvr_status s = gsvr_set_topk(ctx, topk_K, topk_delta, topk_refresh)) return s;
+    // parameters, Adam moments and step counter exactly as saved
+    CK(cudaMemcpy(ctx->d_theta.p, th.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_m.p, th.data() + np, sizeof(float) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_v.p, th.data() + 2 * np, sizeof(float) * np, cudaMemcpyHostToDevice));
+    if (!slw.empty()) {
+        const size_t n2 = 2 * (size_t)M;
+        CK(cudaMemcpy(ctx->d_slw.p, slw.data(), sizeof(float) * n2, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_slw_m.p, slw.data() + n2, sizeof(float) * n2, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_slw_v.p, slw.data() + 2 * n2, sizeof(float) * n2, cudaMemcpyHostToDevice));
+    }
+    if (!dens_acc.empty()) {
+        if (gsvr_status s = dens_ensure(ctx)) return s;
+        CK(cudaMemcpy(ctx->d_dens_acc.p, dens_acc.data(), sizeof(float4) * (size_t)N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_dens_cnt.p, &dens_cnt, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    if (gsvr_status s = gsvr_set_step(ctx, (int64_t)hd.step)) return s;
+    ctx->fwd_valid = false;
     return GSVR_OK;
 }
 

@@ -77,11 +77,16 @@ struct EvalArgs {
     int tile_px;                      // tile_w * tile_h
     int l1;                           // data term: 0 MSE, 1 L1 (the paper's)
     const float *slw;                 // per-slice log sigma_i (M) then log omega_i (M), or null
-    double *slw_gacc;                 // their gradients (2 M, accumulated by the forward)
+    double *slw_gacc;                 // their gradients (2 M)
+    double *slw_tile;                 // per tile: the tile's terms of the two (2 per tile, plain forward)
     int M;
     int tile_w, tile_h;
     int n_tiles;
     unsigned *status;
+    int64_t n_weight;                 // > 0: pixel weight 1 / n_weight (gsvr_set_sample_total), else 1 / sample size
+    // test hook (gsvr_test_wait_timeout): > 0 makes block 0's first record wait
+    // of the forward wait, bounded by this many ns, on a barrier nothing completes
+    int64_t wait_test_ns;
 };
 
 struct GradArgs {
@@ -172,6 +177,8 @@ void launch_init_draw(const int64_t *C, int64_t P, uint64_t seed, int64_t n, con
                       const float *thickness, float *mu, int *pix, cudaStream_t st);
 // float copy of the forward's float64 per-slice gradient sums
 void launch_slw_grad(const double *gacc, int n, float *grad, cudaStream_t st);
+// gacc[i], gacc[M + i] = slice i's per-tile terms (slw_tile) summed in tile order
+void launch_slw_slices(const double *slw_tile, const SliceDev *slices, int M, double *gacc, cudaStream_t st);
 
 // Sampler: for subject k, out_first[k+1] - out_first[k] of its mask_count[k]
 // masked pixels (tile-order positions mask_tpos[mask_first[k] + x]); the round
@@ -228,6 +235,7 @@ struct TopkArgs {
     int l1;                  // data term: 0 MSE, 1 L1
     const float *slw;        // per-slice log sigma_i, log omega_i (2 M) or null
     double *slw_gacc;        // their gradients (2 M)
+    int64_t n_weight;        // > 0: pixel weight 1 / n_weight, else 1 / sample size
     unsigned *status;
 };
 // Grid build: bounding box, cell size, cell keys; the caller sorts the keys

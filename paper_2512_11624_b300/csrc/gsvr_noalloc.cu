@@ -15,7 +15,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "gsvr_launch.cuh"
@@ -28,11 +27,13 @@ constexpr size_t kScratchBytes = 32ull << 20;  // 32 MiB per device
 constexpr int kMaxDevices = 64;
 constexpr int kTile = 16;
 constexpr int kKeysPerRecord = 4;  // key capacity = 4 x record capacity
+// Fixed scratch cost of one pixel: tile map, tile-order list and position,
+// sample flags, flag offsets, sample list, residual (7 int32) and the mask byte.
+constexpr size_t kPixelBytes = 7 * sizeof(int) + 1;
+// Largest pixel count: the pixel arrays alone fill the scratch.
+constexpr int64_t kMaxPixels = (int64_t)(kScratchBytes / kPixelBytes);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
 
 void set_msg(char *msg, int32_t len, const char *text) {
     if (msg && len > 0) {
@@ -41,16 +42,14 @@ void set_msg(char *msg, int32_t len, const char *text) {
     }
 }
 
-// Device address of g_scratch on the current device, looked up once per device.
-cudaError_t scratch_address(int dev, void **out) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+// Device address of g_scratch on the current device.  Looked up on every call
+// (cheap once the library's module is loaded on the device), so a device reset
+// or a re-created primary context never leaves a stale address behind.
+cudaError_t scratch_address(void **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -106,8 +105,8 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
         }
         const int64_t tx = (d.W + kTile - 1) / kTile, ty = (d.H + kTile - 1) / kTile;
         const int64_t slice_px = (int64_t)d.H * d.W;
-        if ((int64_t)d.n_slices * slice_px > (int64_t)(kScratchBytes / 16) || P > (int64_t)(kScratchBytes / 16)) {
-            set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch");
+        if ((int64_t)d.n_slices * slice_px > kMaxPixels || P > kMaxPixels) {
+            set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch (pixel arrays)");
             return GSVR_ERR_INVALID_ARG;
         }
         for (int k = 0; k < d.n_slices; ++k) {
@@ -135,15 +134,15 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
             ss.push_back(st);
             P += slice_px;
             T += tx * ty;
-            if (P > (int64_t)(kScratchBytes / 16)) {
-                set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch");
+            if (P > kMaxPixels) {
+                set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch (pixel arrays)");
                 return GSVR_ERR_INVALID_ARG;
             }
         }
     }
     const int M = (int)sl.size();
-    if (n_idx > P) {
-        set_msg(msg, msg_len, "sample longer than the pixel count");
+    if (n_idx > (int64_t)INT32_MAX / 2) {  // duplicates are allowed (counted once), as in gsvr_set_pixel_sample
+        set_msg(msg, msg_len, "sample list longer than 2^30 entries");
         return GSVR_ERR_INVALID_ARG;
     }
     std::vector<int> tile_slice((size_t)T), pix_tile((size_t)P), tsp((size_t)P), tpos((size_t)P);
@@ -179,7 +178,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     } restore{prev, device};
     void *base = nullptr;
     cudaGetLastError();
-    if (scratch_address(device, &base) != cudaSuccess) {
+    if (scratch_address(&base) != cudaSuccess) {
         cudaGetLastError();
         set_msg(msg, msg_len, "cudaGetSymbolAddress of the scratch array failed");
         return GSVR_ERR_CUDA;
@@ -214,7 +213,9 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     const size_t per_key = 6 * sizeof(uint32_t) + sizeof(int2) + 1 + (kTile * kTile * sizeof(float)) / kItemRecs + 1;
     const size_t slack = 64 * 256 + 4096 * sizeof(int) + (size_t)(2 * T + 8) * (sizeof(int) + kTile * kTile * sizeof(float));
     if (fixed + slack + per_rec + kKeysPerRecord * per_key >= kScratchBytes) {
-        set_msg(msg, msg_len, "problem larger than the 32 MiB no-allocation scratch");
+        set_msg(msg, msg_len,
+                "problem larger than the 32 MiB no-allocation scratch (pixel, tile and Gaussian arrays leave "
+                "no room for records)");
         return GSVR_ERR_INVALID_ARG;
     }
     const size_t room = kScratchBytes - fixed - slack;
@@ -373,6 +374,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     e.tile_h = kTile;
     e.n_tiles = (int)T;
     e.status = d_status;
+    e.qcut = b.qcut;
     launch_forward(e, st);
     launch_loss_reduce(d_tile_loss, (int)T, nullptr, 1, d_subj_loss, loss, d_status, st);
     NA_CK(cudaGetLastError());

@@ -34,7 +34,9 @@ EXPORTS = ["gsvr_abi_version", "gsvr_last_error", "gsvr_create", "gsvr_destroy",
            "gsvr_tune_space_default", "gsvr_autotune", "gsvr_reserve", "gsvr_set_topk", "gsvr_get_topk_neighbors",
            "gsvr_set_objective", "gsvr_set_slice_weights", "gsvr_slice_weight_views", "gsvr_init_means",
            "gsvr_volume_metrics", "gsvr_fp64_peak", "gsvr_densify_accumulate", "gsvr_densify_stats",
-           "gsvr_densify", "gsvr_ffma2_peak", "gsvr_set_subject_active"]
+           "gsvr_densify", "gsvr_ffma2_peak", "gsvr_set_subject_active", "gsvr_save", "gsvr_load",
+           "gsvr_checkpoint_info", "gsvr_test_wait_timeout",
+           "gsvr_set_sample_total"]
 STAGES = ["sample", "prep", "bin", "fwd_eval", "bwd_eval", "grad", "adam", "unused"]
 
 
@@ -80,6 +82,11 @@ class Tiling(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CheckpointHeader(C.Structure):
+    _fields_ = [("version", C.c_int32), ("n_stacks", C.c_int32), ("n_slices", C.c_int32), ("reserved", C.c_int32),
+                ("n_pixels", C.c_int64), ("n_gaussians", C.c_int64), ("step", C.c_int64)]
 
 
 class Views(C.Structure):
@@ -152,6 +159,11 @@ def _load():
         "gsvr_densify_accumulate": ([vp], C.c_int),
         "gsvr_densify_stats": ([vp, vp, C.POINTER(i32), i32], C.c_int),
         "gsvr_densify": ([vp, C.POINTER(DensifyCfg), C.POINTER(i64)], C.c_int),
+        "gsvr_save": ([vp, C.c_char_p], C.c_int),
+        "gsvr_test_wait_timeout": ([vp, i32, i64], C.c_int),
+        "gsvr_set_sample_total": ([vp, i64], C.c_int),
+        "gsvr_load": ([vp, C.c_char_p], C.c_int),
+        "gsvr_checkpoint_info": ([C.c_char_p, C.POINTER(CheckpointHeader), C.c_char_p, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -586,6 +598,36 @@ def gsvr_forward_noalloc(stacks, N, theta, I, idx, pred, loss, device=0, stream=
     return st
 
 
+def gsvr_set_sample_total(ctx, n_total):
+    """Pixel weight 1 / n_total (the global sample size of a sharded reconstruction); 0 = own sample size."""
+    return _check(ctx, lib.gsvr_set_sample_total(ctx, int(n_total)))
+
+
+def gsvr_test_wait_timeout(ctx, n_forwards=1, limit_ns=2_000_000):
+    """Test hook: the next n forwards run out one bounded device wait (see gsvr.h)."""
+    return _check(ctx, lib.gsvr_test_wait_timeout(ctx, int(n_forwards), int(limit_ns)))
+
+
+def gsvr_save(ctx, path):
+    """Write the context's optimisation state to `path` (see gsvr.h)."""
+    return _check(ctx, lib.gsvr_save(ctx, os.fsencode(path)))
+
+
+def gsvr_load(ctx, path):
+    """Restore a state written by gsvr_save (stacks and observations set first)."""
+    return _check(ctx, lib.gsvr_load(ctx, os.fsencode(path)))
+
+
+def gsvr_checkpoint_info(path):
+    """Check a checkpoint file without a context or GPU; returns its header as a dict."""
+    h = CheckpointHeader()
+    buf = C.create_string_buffer(256)
+    st = lib.gsvr_checkpoint_info(os.fsencode(path), C.byref(h), buf, 256)
+    if st != GSVR_OK:
+        raise GsvrError(st, buf.value.decode())
+    return {k: getattr(h, k) for k, _ in CheckpointHeader._fields_ if k != "reserved"}
+
+
 # --------------------------------------------------------------- torch views
 class _CudaArray:
     def __init__(self, ptr, shape, typestr):
@@ -639,6 +681,16 @@ class Context:
         """Replace the Gaussians (11 N floats, host or device); poses are kept."""
         gsvr_set_gaussians(self.ctx, int(N), theta_g)
         self.N = int(N)
+        self.refresh_views()
+
+    def save(self, path):
+        """gsvr_save: the optimisation state to a checkpoint file."""
+        gsvr_save(self.ctx, path)
+
+    def load(self, path):
+        """gsvr_load, then refresh N and the views (the Gaussian count may change)."""
+        gsvr_load(self.ctx, path)
+        self.N = int(gsvr_checkpoint_info(path)["n_gaussians"])
         self.refresh_views()
 
     def densify(self, grad_threshold, log_scale_threshold, **kw):

@@ -314,7 +314,25 @@ def with_gaussians(case, theta_g_extra, n_extra):
     return out
 
 
-def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0, motion_mm=3.0, jitter=0.0):
+def jitter_gaussians(rng, theta_g, N, amplitude_jitter=0.0, shape_jitter=0.0):
+    """A start away from the fit: amplitude_jitter > 0 multiplies the
+    amplitudes by U(1 +- jitter); shape_jitter > 0 adds U(+-jitter) to every
+    log-scale and turns every Gaussian by a random rotation (anisotropic,
+    oriented primitives, so that every gradient group is nonzero)."""
+    if not (amplitude_jitter > 0 or shape_jitter > 0):
+        return theta_g
+    th = theta_g.reshape(11, N).copy()
+    if amplitude_jitter > 0:
+        th[10] *= rng.uniform(1 - amplitude_jitter, 1 + amplitude_jitter, size=N)
+    if shape_jitter > 0:
+        th[3:6] += rng.uniform(-shape_jitter, shape_jitter, size=(3, N))
+        q = rng.normal(size=(4, N))
+        th[6:10] = q / np.linalg.norm(q, axis=0)
+    return th.reshape(-1)
+
+
+def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0, motion_mm=3.0, jitter=0.0,
+          amplitude_jitter=0.0, shape_jitter=0.0):
     """The fetal-scale plain case: ~200k Gaussians on a 0.8 mm grid inside the
     brain phantom; axial / coronal / sagittal stacks of 40 x 192 x 192 px at
     1 x 1 x 3.5 mm centred on the origin; per-slice motion U(+-5 deg) axis
@@ -322,7 +340,8 @@ def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0
     dilated by 15 mm; 2^18 pixels sampled per iteration.  Poses start at 0
     (the unknown motion is what the optimisation recovers).  motion_deg /
     motion_mm widen the motion range; jitter > 0 draws the phantom from the
-    canonical-frame family (see BrainPhantom)."""
+    canonical-frame family (see BrainPhantom); amplitude_jitter and
+    shape_jitter move the start away from the fit (jitter_gaussians)."""
     rng = np.random.default_rng(seed)
     ph = BrainPhantom(seed, jitter=jitter)
     stacks = [stack(40, 192, 192, 1.0, 1.0, 3.5, R) for R in (AXIAL, CORONAL, SAGITTAL)]
@@ -339,6 +358,7 @@ def fetal(seed=0, with_truth=False, init="phantom", ref_slice=20, motion_deg=5.0
         theta_g = theta_g.reshape(11, N)
         theta_g[10] = level * h ** 3 / ((2 * np.pi) ** 1.5 * s ** 3)
         theta_g = theta_g.reshape(-1)
+    theta_g = jitter_gaussians(rng, theta_g, N, amplitude_jitter, shape_jitter)
     theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
     out = {"name": "fetal", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
            "n_sample": 1 << 18, "ref_slice": ref_slice, "phantom": ph}
@@ -466,15 +486,7 @@ def large(seed=0, nodes=(1, 1, 3), amplitude_jitter=0.0, shape_jitter=0.0):
     motion[24] = 0.0
     I, mask = simulate_phantom_stacks(ph, stacks, motion, mask_dilate_mm=15.0, seed=seed, nodes=nodes)
     theta_g, N = grid_gaussians(ph, h=1.08, s=1.08)
-    if amplitude_jitter > 0 or shape_jitter > 0:
-        th = theta_g.reshape(11, N)
-        if amplitude_jitter > 0:
-            th[10] *= rng.uniform(1 - amplitude_jitter, 1 + amplitude_jitter, size=N)
-        if shape_jitter > 0:
-            th[3:6] += rng.uniform(-shape_jitter, shape_jitter, size=(3, N))
-            q = rng.normal(size=(4, N))
-            th[6:10] = q / np.linalg.norm(q, axis=0)
-        theta_g = th.reshape(-1)
+    theta_g = jitter_gaussians(rng, theta_g, N, amplitude_jitter, shape_jitter)
     theta = np.concatenate([theta_g, np.zeros(6 * M)]).astype(np.float32)
     return {"name": "large", "N": N, "stacks": stacks, "theta": theta, "I": I, "mask": mask,
             "n_sample": int(mask.sum()), "ref_slice": 24, "phantom": ph, "motion": motion}

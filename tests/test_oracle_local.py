@@ -110,3 +110,25 @@ def test_local_grad_prediction_scale_sums(oracle):
                                                                                  rtol=1e-12)
     assert np.allclose(out0["a_sel"], out["b_sel"], rtol=1e-12) and np.allclose(out0["a_pose"], out["b_pose"],
                                                                                 rtol=1e-12)
+
+
+def test_local_grad_truncation_scale_sums(oracle):
+    """bt_sel / bt_pose are the |term| sums with each residual weight replaced
+    by 2 w trunc_pred_p; with observations I_p = I_hat_p - trunc_pred_p that is
+    the residual weight itself, so they equal that call's a_sel / a_pose."""
+    case = inputs.random_case(13, 120, [(3, 14, 13), (2, 12, 12)], n_stacks=2, motion_deg=8.0, motion_mm=3.0,
+                              s_hi=3.0)
+    N = case["N"]
+    th = case["theta"].astype(np.float64)
+    P = inputs.n_pixels_total(case["stacks"])
+    rng = np.random.default_rng(6)
+    pix = np.sort(rng.choice(P, size=P // 2, replace=False))
+    sel = np.sort(rng.choice(N, size=50, replace=False))
+    w = 1.0 / pix.size
+    out = oracle.local_grad(case["stacks"], th, N, pix, case["I"].astype(np.float64)[pix], w, sel, cut=1e-12,
+                            trunc_cut=1e-4)
+    assert out["trunc_pred"].max() > 0 and out["bt_sel"].max() > 0
+    out2 = oracle.local_grad(case["stacks"], th, N, pix, out["pred"] - out["trunc_pred"], w, sel, cut=1e-12,
+                             trunc_cut=1e-4)
+    assert np.allclose(out2["a_sel"], out["bt_sel"], rtol=1e-9, atol=1e-300)
+    assert np.allclose(out2["a_pose"], out["bt_pose"], rtol=1e-9, atol=1e-300)

@@ -2,7 +2,7 @@
 gsvr_set_topk) against the float64 oracle of ``oracle/topk.py``.
 
 - Forward values within 1e-5 relative (floored at 1e-3 of the case maximum),
-  gradients within 1e-4 relative plus 2e-6 of the sum of |pair terms|, as on
+  gradients within 1e-4 relative plus 1e-6 of the sum of |pair terms|, as on
   the plain path; cases with K below, at and above N, a lone Gaussian, two
   oblique stacks with motion, K = 64 and 128 (the forward's 64-thread blocks).
 - The neighbour sets are unique except at distance ties (lattice-placed
