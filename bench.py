@@ -1,21 +1,30 @@
 #!/usr/bin/env python
 """Benchmark: one optimisation step of the analytic-PSF Gaussian slice model.
 
-A step = sample 2^18 masked pixels on the device, forward (Gaussian and slice
-preprocessing, Mahalanobis cut, (tile, record) keys, radix sort, tile
-evaluation with the fused MSE loss), backward (tile adjoint, gradient
-epilogue) and the fused Adam update, on the fetal-scale synthetic workload
-(~200k Gaussians, 3 orthogonal stacks of 40 x 192 x 192 px at 1 x 1 x 3.5 mm).
+A step = forward (Gaussian and slice preprocessing, Mahalanobis cut, (tile,
+record) keys, radix sort, tile evaluation with the fused MSE loss), backward
+(tile adjoint, gradient epilogue) and the fused Adam update.
+
+Headline workload (default, --workload large): the 1M-Gaussian large case --
+1,000,372 Gaussians, six stacks of 48 x 256 x 256 px at 0.8 x 0.8 x 3.0 mm,
+motion U(+-10 deg)/U(+-5 mm), every masked pixel (7.09M) in every step; the
+step is the sequence of library calls the torch.autograd.Function front end
+(autograd.SliceLoss) makes.  The fetal case (200k Gaussians, 3 x 40 x 192^2 px,
+2^18 pixels drawn by the device sampler each step) is measured after it and
+reported under the "fetal" key.
 
 Prints one JSON line.  `value` counts (pixel, Gaussian) pairs inside the
 1e-7 cut (the pairs the method needs) per second of whole-step device time;
-`px_per_s` counts sampled slice pixels.  `e2e` is the same metric through the
+`px_per_s` counts slice pixels.  `e2e` is the same metric through the
 host-buffer C-ABI call (gsvr_step_host: parameters and pixel list uploaded
-from pinned memory, gradient and loss read back every step).  The timed
-region launches each step's kernels eagerly (with stage events, from which the
-roofline's kernel time comes); `graph` times the same step replayed as one
-CUDA graph per iteration (gsvr_graph_capture / gsvr_graph_launch), separately
-after it.
+from pinned memory, gradient and loss read back every step).  `roofline`
+holds, for the dominant tile kernel, the in-cut pairs per launch, the average
+launch time (CUDA events), the FP32 operations per pair the method needs (17
+for the backward, 7 for the forward) and the FFMA lane-operation rate measured
+on the same GPU, so that frac = pairs / time x FP32 per pair / FFMA rate can
+be recomputed from the line.  The timed region launches each step's kernels
+eagerly (with stage events); `graph` times the same step replayed as one CUDA
+graph per iteration (gsvr_graph_capture / gsvr_graph_launch).
 
 --impl reference times the FP64 brute-force CPU oracle on bounded pixel
 samples of the same workload (the oracle is this project's reference program).
@@ -39,19 +48,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Gaussian-pixel pairs/s & slice px/s; sec to fixed PSNR vs plain, 1 B300"
 UNIT = "pairs/s"
-# Algorithmic work per (sampled pixel, record) pair of the tile kernels in their
-# row form (row terms formed once per row and amortised away):
-#   forward  db = b - cb; q = (A db + C2 da) db + B da^2 (2 FFMA); ex2; sum += w e
-#            -> 4 FP32 + 1 MUFU, scalar instructions: 5 issue slots
-#   backward db; q (2 FFMA); ex2; g = r e; row sums g, g db, g db^2 (FADD, FMUL+FADD, FFMA)
-#            -> 8 FP32 lane operations + 1 MUFU, issued as packed f32x2 instructions
-#            (two records per thread side by side): 4 packed + 1 MUFU issue slots
-# Measured on B300: scalar FFMA issues at 4 warp instructions per clock per SM (the
-# issue limit), packed FFMA2 at half that rate (the same 128 FP32 lanes per clock),
-# MUFU ex2 at about a quarter.  So the scalar forward is issue bound (peak pairs/s =
-# FFMA instr/s / 5) and the packed backward FP32-pipe bound (peak = FFMA lane
-# operations/s / 8; its issue slots, 5, and its MUFU share are below that).
-PAIR_BOUND = {"fwd_eval": ("FP32 issue", 5.0), "bwd_eval": ("FP32 pipe", 8.0)}
+# Algorithmic FP32 work per (pixel, Gaussian) pair inside the cut, as the
+# method states it (the 3D form reduced to the slice plane): forward q, exp and
+# the weighted sum (7 FP32 + 1 MUFU); backward the same plus the six moment
+# contributions of g, g db, g da, g db^2, g db da, g da^2 (17 FP32 + 1 MUFU).
+# The roofline pair rate of a kernel is the measured FFMA lane-operation rate
+# divided by its count.
+FP32_PER_PAIR = {"fwd_eval": 7.0, "bwd_eval": 17.0}
+KERNEL_OF = {"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}
 
 
 def parse():
@@ -60,7 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fetal", choices=["fetal", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "fetal", "tiny"])
+    ap.add_argument("--no-fetal", action="store_true", help="skip the secondary fetal measurement")
     ap.add_argument("--stacks", type=int, default=0, help="keep only the first n stacks (profiling captures)")
     ap.add_argument("--tile", default="auto",
                     help="HxW tile (no tuning) or 'auto': the library's autotuner picks the launch shape")
@@ -72,15 +77,20 @@ def parse():
 
 def workload(name, seed, n_stacks=0):
     from paper_2512_11624_b300 import inputs
-    if name == "fetal":
+    if name == "large":
+        case = inputs.large(seed)
+        desc = ("large: %d Gaussians (1.08 mm grid in a brain phantom scaled 2.307x), 6 stacks of 48 x 256 x 256 "
+                "px at 0.8 x 0.8 x 3.0 mm (axial, coronal, sagittal, axial turned 45 deg about x, y, z), motion "
+                "U(+-10 deg)/U(+-5 mm), every masked pixel (%d) per step, Adam" % (case["N"], int(case["mask"].sum())))
+    elif name == "fetal":
         case = inputs.fetal(seed)
-        if n_stacks:
-            case = inputs.first_stacks(case, n_stacks)
         desc = ("fetal: %d Gaussians (0.8 mm grid in a brain phantom), 3 orthogonal stacks of 40 x 192 x 192 px "
                 "at 1 x 1 x 3.5 mm, motion U(+-5 deg)/U(+-3 mm), 2^18 sampled px/step, Adam" % case["N"])
     else:
         case = inputs.tiny(seed)
         desc = "tiny: 2000 Gaussians, 1 stack of 8 x 32 x 32 px, all pixels, Adam"
+    if n_stacks:
+        case = inputs.first_stacks(case, n_stacks)
     return case, desc
 
 
@@ -231,7 +241,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
+            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas" if ws > 1 else "single"},
             "px_per_s": px_s,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d random masked pixels per step x every Gaussian, fwd+bwd, float64" % n_px},
@@ -239,26 +249,24 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    ws, rank, local = dist_setup()
-    if args.impl == "reference":
-        run_reference(args, ws, rank)
-        return
-    import torch
-    from paper_2512_11624_b300 import gsvr
-    torch.cuda.set_device(local)
-    dev = local
-    stream = torch.cuda.Stream(device=dev)
-    case, desc = workload(args.workload, rank, args.stacks)
-    n_s = min(case["n_sample"], int(case["mask"].sum()))
-    sampled = args.workload == "fetal"
+def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_e2e, with_cpu, clocks_on):
+    """Times `steps` optimisation steps of one workload; returns its JSON fields."""
+    case, desc = workload(name, rank, args.stacks)
+    sampled = name == "fetal"  # the fetal case draws 2^18 pixels per step; the others use every masked pixel
+    n_mask = int(case["mask"].sum())
+    n_s = min(case["n_sample"], n_mask) if sampled else n_mask
+
+    def set_sample(c, k):
+        if sampled:
+            gsvr.gsvr_sample_pixels(c.ctx, n_s, k)
 
     def probe_counts(shape):
         probe = gsvr.Context(case, device=dev, stream=stream.cuda_stream)
         gsvr.gsvr_set_tiling(probe.ctx, shape)
         if sampled:
             gsvr.gsvr_sample_pixels(probe.ctx, n_s, 0)
+        else:
+            gsvr.gsvr_set_pixel_sample(probe.ctx, None)
         probe.forward()
         st = probe.stats()
         probe.close()
@@ -271,11 +279,13 @@ def main():
         st0 = probe_counts(gsvr.tiling(12, 12))
         tune = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=12, tile_w=12, fixed_capacity=1,
                             cap_records=int(st0["n_records"] * 1.5) + 4096, cap_keys=int(st0["n_keys"] * 4) + 4096)
-        best, res = gsvr.gsvr_autotune(tune.ctx, None, n_per_subject=n_s if sampled else 0, iterations=10)
+        if not sampled:
+            gsvr.gsvr_set_pixel_sample(tune.ctx, None)
+        best, res = gsvr.gsvr_autotune(tune.ctx, None, n_per_subject=n_s if sampled else 0,
+                                       iterations=10 if sampled else 3)
         tune.close()
         shape = res[best]
         tuning = {"candidates": len(res), "ms_per_iter_best": round(res[best].ms, 4),
-                  "ms_per_iter_12x12": round(res[2].ms, 4),
                   "timed": ["%dx%d px%d fwd%d bwd%d order%d: %.4f ms" % (r.tile_h, r.tile_w, r.fwd_px_per_thread,
                                                                           r.fwd_blocks_per_sm, r.bwd_blocks_per_sm,
                                                                           r.queue_order, r.ms) for r in res]}
@@ -286,91 +296,95 @@ def main():
     # capacities from one probe forward, then a fixed-capacity context (no host sync per step)
     st0 = probe_counts(shape)
     ctx = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=shape.tile_h, tile_w=shape.tile_w,
-                       fixed_capacity=1, cap_records=int(st0["n_records"] * 1.5) + 4096,
-                       cap_keys=int(st0["n_keys"] * 1.5) + 4096, timing=1, seed=1234 + rank)
+                       fixed_capacity=1, cap_records=int(st0["n_records"] * 1.3) + 4096,
+                       cap_keys=int(st0["n_keys"] * 1.3) + 4096, timing=1, seed=1234 + rank)
     gsvr.gsvr_set_tiling(ctx.ctx, shape)
+    if not sampled:
+        gsvr.gsvr_set_pixel_sample(ctx.ctx, None)
     M = ctx.M
-    gsvr.gsvr_set_frozen(ctx.ctx, np.array([1 if i == M // 6 else 0 for i in range(M)], np.uint8))
+    ref_slice = case.get("ref_slice", M // 6)
+    gsvr.gsvr_set_frozen(ctx.ctx, np.array([1 if i == ref_slice else 0 for i in range(M)], np.uint8))
 
     def step(k):
-        if sampled:
-            gsvr.gsvr_sample_pixels(ctx.ctx, n_s, k)
+        set_sample(ctx, k)
         gsvr.gsvr_forward(ctx.ctx)
         gsvr.gsvr_backward(ctx.ctx)
         gsvr.gsvr_adam_step(ctx.ctx, k + 1)
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k)
     gsvr.gsvr_sync_status(ctx.ctx)
     gsvr.gsvr_timing_reset(ctx.ctx)
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
+    clocks = None
+    if clocks_on:
         uuid = None
-    clocks = ClockSampler(uuid)
-    time.sleep(0.3)
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            uuid = None
+        clocks = ClockSampler(uuid)
+        time.sleep(0.3)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for k in range(args.steps):
-        step(args.warmup + k)
+    for k in range(steps):
+        step(warmup + k)
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     gsvr.gsvr_sync_status(ctx.ctx)
     kt = gsvr.gsvr_get_kernel_times(ctx.ctx)
     ms_max = reduce_max(ms, ws)
 
-    # pairs inside the cut: counted on 3 further steps' samples (outside the timed region)
-    u_sum = e_sum = 0
-    for k in range(3):
-        if sampled:
-            gsvr.gsvr_sample_pixels(ctx.ctx, n_s, args.warmup + args.steps + k)
+    # pairs inside the cut per step: counted exactly (count pass over the sampled pixels)
+    # on the current parameters, outside the timed region (3 more samples when sampling)
+    u_sum = t_sum = 0
+    n_count = 3 if sampled else 1
+    for k in range(n_count):
+        set_sample(ctx, warmup + steps + k)
         gsvr.gsvr_forward(ctx.ctx)
         u, e = gsvr.gsvr_count_pairs(ctx.ctx)
         u_sum += u
-        e_sum += e
-    useful_frac = u_sum / max(e_sum, 1)
-    eval_per_step = kt["pairs_evaluated"] / args.steps
-    useful_per_step = useful_frac * eval_per_step
-    useful_total = reduce_sum(useful_per_step * args.steps, ws)
-    px_total = reduce_sum(float(n_s) * args.steps, ws)
+        t_sum += e
+    useful_per_step = u_sum / n_count
+    tile_pairs_per_step = t_sum / n_count
+    useful_total = reduce_sum(useful_per_step * steps, ws)
+    px_total = reduce_sum(float(n_s) * steps, ws)
     value = useful_total / (ms_max / 1e3)
 
-    # roofline of the dominant tile kernel (FP32 issue bound), peak measured on this GPU now
+    # roofline of both tile kernels: in-cut pairs per launch over the kernel's
+    # average launch time, against the measured FFMA lane-operation rate / the
+    # method's FP32 operations per pair
     ffma_s, ex2_s, n_sm = gsvr.gsvr_alu_peaks(dev)
     ffma2_s = gsvr.gsvr_ffma2_peak(dev)
-    f_mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0
-    dom = max(("fwd_eval", "bwd_eval"), key=lambda s: kt["ms"][s])
-    avg_ms = kt["ms"][dom] / max(kt["calls"][dom], 1)
-    pairs_per_launch = eval_per_step
-    achieved = pairs_per_launch / (avg_ms / 1e3) / 1e9
-    bound_name, per_pair = PAIR_BOUND[dom]
-    peak = ffma_s / per_pair / 1e9
-    traffic = profiled_traffic({"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
-                               "%s-%dx%d" % (args.workload, shape.tile_h, shape.tile_w))
-    roofline = {"bound": "alu", "kernel": {"fwd_eval": "k_fwd_items", "bwd_eval": "k_bwd_items"}[dom],
-                "achieved": achieved, "peak": peak, "unit": "Gpair/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_basis": "%s bound: measured FFMA rate %.3e instr/s (%d SMs; packed FFMA2 %.3e instr/s, "
-                              "ex2.approx %.3e/s) / %.0f per sampled (pixel, record) pair"
-                              % (bound_name, ffma_s, n_sm, ffma2_s, ex2_s, per_pair)}
+    kernels = {}
+    for stg in ("fwd_eval", "bwd_eval"):
+        avg_ms = kt["ms"][stg] / max(kt["calls"][stg], 1)
+        achieved = useful_per_step / (avg_ms / 1e3) / 1e9
+        peak = ffma_s / FP32_PER_PAIR[stg] / 1e9
+        kernels[stg] = {"kernel": KERNEL_OF[stg], "pairs_per_launch": useful_per_step, "avg_launch_ms": avg_ms,
+                        "fp32_per_pair": FP32_PER_PAIR[stg], "achieved": achieved, "peak": peak,
+                        "frac": achieved / peak}
+    dom = max(("fwd_eval", "bwd_eval"), key=lambda k: kt["ms"][k])
+    traffic = profiled_traffic(KERNEL_OF[dom], "%s-%dx%d" % (name, shape.tile_h, shape.tile_w))
+    roofline = dict(kernels[dom], bound="alu", unit="Gpair/s", traffic=traffic, ffma_lane_ops_per_s=ffma_s,
+                    peak_basis="measured FFMA rate %.4e lane-ops/s on this GPU (%d SMs; packed FFMA2 %.3e instr/s, "
+                               "ex2.approx %.3e/s) / %.0f FP32 operations per in-cut pair (MEASURED_PEAKS.json "
+                               "has no FP32 figure)" % (ffma_s, n_sm, ffma2_s, ex2_s, FP32_PER_PAIR[dom]),
+                    other=kernels["fwd_eval" if dom == "bwd_eval" else "bwd_eval"])
 
-    # the same step replayed as one CUDA graph per iteration (gsvr_graph_capture /
-    # gsvr_graph_launch: sampler, forward, backward, Adam, no host launches),
-    # timed separately after the eager timed region
-    kg = max(3, min(args.steps, 500))
+    # the same step replayed as one CUDA graph per iteration, timed separately after the eager region
+    kg = max(3, min(steps, 200))
     try:
         gsvr.gsvr_graph_capture(ctx.ctx, n_s if sampled else -1)
-        gsvr.gsvr_set_step(ctx.ctx, args.warmup + args.steps + 3)
+        gsvr.gsvr_set_step(ctx.ctx, warmup + steps + 3)
         gsvr.gsvr_graph_launch(ctx.ctx, 3)
         gsvr.gsvr_sync_status(ctx.ctx)
         g_err = None
@@ -395,35 +409,35 @@ def main():
 
     # end to end through the host-buffer call
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         rng = np.random.default_rng(99 + rank)
         masked = np.nonzero(case["mask"])[0].astype(np.int32)
-        ke = max(3, min(args.steps, 20))
-        lists = [np.sort(rng.choice(masked, n_s, replace=False)).astype(np.int32) for _ in range(ke + 2)]
+        ke = max(3, min(steps, 20))
+        if sampled:
+            lists = [np.sort(rng.choice(masked, n_s, replace=False)).astype(np.int32) for _ in range(ke + 2)]
+        else:
+            lists = [masked] * (ke + 2)
         theta_h = torch.from_numpy(case["theta"].astype(np.float32)).pin_memory()
         grad_h = torch.empty_like(theta_h).pin_memory()
         loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
-        idx_h = [torch.from_numpy(l).pin_memory() for l in lists]
+        idx_h = [torch.from_numpy(l).pin_memory() for l in lists[:ke + 2 if sampled else 1]]
         for k in range(2):
-            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[k], grad_h, loss_h)
-        gsvr.gsvr_timing_reset(ctx.ctx)
+            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[k % len(idx_h)], grad_h, loss_h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(ke):
-            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[2 + k], grad_h, loss_h)
-        dt = time.perf_counter() - t0
-        kt2 = gsvr.gsvr_get_kernel_times(ctx.ctx)
-        dt = reduce_max(dt, ws)
-        e2e_useful = reduce_sum(useful_frac * kt2["pairs_evaluated"], ws)
-        e2e = {"value": e2e_useful / dt, "unit": UNIT,
+            gsvr.gsvr_step_host(ctx.ctx, theta_h, idx_h[(2 + k) % len(idx_h)], grad_h, loss_h)
+        dt = reduce_max(time.perf_counter() - t0, ws)
+        e2e = {"value": reduce_sum(useful_per_step * ke, ws) / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(theta_h.numel() * 4 + n_s * 4),
-               "d2h_bytes_per_step": int(grad_h.numel() * 4 + 8), "steps": ke}
+               "d2h_bytes_per_step": int(grad_h.numel() * 4 + 8), "steps": ke,
+               "pairs_per_step": "the eager region's in-cut pairs per step"}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if with_cpu and rank == 0 and ws == 1:
         sample = gsvr.gsvr_get_sample(ctx.ctx)
         rng = np.random.default_rng(7)
-        n_px = 128
+        n_px = 16
         while True:  # grow the sample until the oracle runs for args.cpu_seconds
             pix = rng.choice(sample, min(n_px, sample.size), replace=False)
             t_cpu, u_cpu, cores = cpu_oracle_sample(case, pix, n_s)
@@ -432,45 +446,83 @@ def main():
             n_px = int(min(65536, n_px * max(2.0, min(32.0, args.cpu_seconds / max(t_cpu, 1e-3)))))
         cpu = {"value": u_cpu / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                "px_per_s": len(pix) / t_cpu,
-               "sample": "%d sampled pixels of one step x all %d Gaussians, fwd+bwd (all gradients), float64, "
-                         "%.1f s" % (len(pix), case["N"], t_cpu)}
+               "sample": "%d of the step's pixels x all %d Gaussians, fwd+bwd (all gradients), float64, %.1f s" %
+                         (len(pix), case["N"], t_cpu)}
 
-    if rank == 0:
-        stats = ctx.stats()
-        # HBM-bound stages against the measured copy bandwidth: algorithmic bytes per
-        # step (prep: 44 B read + 40 B written per Gaussian; binning: ~68 B per slab
-        # candidate record (read 40, write 24, count 4) and 44 B per key (emit 8, two
-        # 8-bit radix passes of 8 B read + 8 B write, tile offset 4); Adam: 28 B per
-        # parameter) over the stage's CUDA-event time in the timed region
-        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        hbm = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
-        hbm_basis = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6400 GB/s"
-        hbm = float(hbm or 6400.0)
-        n_par = 11 * case["N"] + 6 * M
-        stage_bytes = {"prep": 84.0 * case["N"], "bin": 68.0 * stats["n_records"] + 44.0 * stats["n_keys"],
-                       "adam": 28.0 * n_par}
-        hbm_stages = {"peak_gbs": hbm, "peak_basis": hbm_basis}
-        for k, b in stage_bytes.items():
-            ms_k = kt["ms"][k] / max(args.steps, 1)
-            gbs = b / (ms_k / 1e3) / 1e9 if ms_k > 0 else None
-            hbm_stages[k] = {"bytes_per_step": b, "ms_per_step": ms_k, "achieved_gbs": gbs,
-                             "frac": gbs / hbm if gbs else None}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": desc, "tile": "%dx%d" % (shape.tile_h, shape.tile_w), "launch_shape": shape_d,
-                           "autotune": tuning, "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (records + keys + tile records ~%.0f MB per step)" %
-                                 ((stats["n_records"] * 44 + stats["n_keys"] * 108) / 1e6)},
-                "px_per_s": px_total / (ms_max / 1e3),
-                "evaluated_pairs_per_s": eval_per_step * args.steps * ws / (ms_max / 1e3),
-                "useful_fraction": useful_frac,
-                "stage_ms_per_step": {k: v / args.steps for k, v in kt["ms"].items()},
-                "records_per_step": stats["n_records"], "keys_per_step": stats["n_keys"],
-                "roofline": roofline, "hbm_stages": hbm_stages, "graph": graph, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": kt["kernel_launches"], "clocks": clk}
-        print(json.dumps(line), flush=True)
+    stats = ctx.stats()
+    # HBM-bound stages against the measured copy bandwidth: algorithmic bytes per
+    # step (prep: 44 B read + 40 B written per Gaussian; binning: ~68 B per slab
+    # candidate record (read 40, write 24, count 4) and 44 B per key (emit 8, two
+    # 8-bit radix passes of 8 B read + 8 B write, tile offset 4); Adam: 28 B per
+    # parameter) over the stage's CUDA-event time in the timed region
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None
+    hbm_basis = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6400 GB/s"
+    hbm = float(hbm or 6400.0)
+    n_par = 11 * case["N"] + 6 * M
+    stage_bytes = {"prep": 84.0 * case["N"], "bin": 68.0 * stats["n_records"] + 44.0 * stats["n_keys"],
+                   "adam": 28.0 * n_par}
+    hbm_stages = {"peak_gbs": hbm, "peak_basis": hbm_basis}
+    for k, b in stage_bytes.items():
+        ms_k = kt["ms"][k] / max(steps, 1)
+        gbs = b / (ms_k / 1e3) / 1e9 if ms_k > 0 else None
+        hbm_stages[k] = {"bytes_per_step": b, "ms_per_step": ms_k, "achieved_gbs": gbs,
+                         "frac": gbs / hbm if gbs else None}
+    # adjoint memory: what the recompute design keeps against one float32 per in-cut pair
+    kept = stats["n_keys"] * (32 + 32 + 4 + 4) + stats["n_records"] * (32 + 8 + 4 + 4)
+    memory = {"recompute_bytes": int(kept), "store_per_pair_bytes": int(useful_per_step * 4),
+              "note": "recompute keeps records, keys, tile-ordered references and per-key moments; storing one "
+                      "float32 factor per in-cut pair is the alternative"}
+    out = {"value": value, "ms_per_step": ms_max / steps, "desc": desc, "n_sample": n_s,
+           "tile": "%dx%d" % (shape.tile_h, shape.tile_w), "launch_shape": shape_d, "autotune": tuning,
+           "l2": "inputs larger than L2 (records + keys + tile records ~%.0f MB per step)" %
+                 ((stats["n_records"] * 44 + stats["n_keys"] * 108) / 1e6),
+           "px_per_s": px_total / (ms_max / 1e3), "useful_pairs_per_step": useful_per_step,
+           "tile_pairs_per_step": tile_pairs_per_step,
+           "useful_fraction": useful_per_step / max(tile_pairs_per_step, 1),
+           "stage_ms_per_step": {k: v / steps for k, v in kt["ms"].items()},
+           "records_per_step": stats["n_records"], "keys_per_step": stats["n_keys"], "roofline": roofline,
+           "hbm_stages": hbm_stages, "graph": graph, "cpu_baseline": cpu, "e2e": e2e, "memory": memory,
+           "gpu_launches": kt["kernel_launches"], "clocks": clk}
     ctx.close()
+    return out
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    from paper_2512_11624_b300 import gsvr
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=local)
+    head = measure(args, gsvr, torch, local, stream, args.workload, rank, ws, args.steps, args.warmup,
+                   not args.no_e2e, not args.no_cpu_baseline, True)
+    fetal = None
+    if args.workload == "large" and not args.no_fetal:
+        fs = max(3, min(args.steps * 5, 1000))
+        f = measure(args, gsvr, torch, local, stream, "fetal", rank, ws, fs, max(args.warmup, 3), False, False, False)
+        fetal = {k: f[k] for k in ("value", "ms_per_step", "desc", "tile", "px_per_s", "useful_pairs_per_step",
+                                   "tile_pairs_per_step", "useful_fraction", "stage_ms_per_step", "roofline",
+                                   "hbm_stages", "graph", "gpu_launches")}
+        fetal["steps"] = fs
+    if rank == 0:
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": head["desc"], "tile": head["tile"], "launch_shape": head["launch_shape"],
+                           "autotune": head["autotune"], "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": head["l2"]},
+                "px_per_s": head["px_per_s"], "useful_pairs_per_step": head["useful_pairs_per_step"],
+                "tile_pairs_per_step": head["tile_pairs_per_step"], "useful_fraction": head["useful_fraction"],
+                "stage_ms_per_step": head["stage_ms_per_step"], "records_per_step": head["records_per_step"],
+                "keys_per_step": head["keys_per_step"], "roofline": head["roofline"],
+                "hbm_stages": head["hbm_stages"], "graph": head["graph"], "cpu_baseline": head["cpu_baseline"],
+                "e2e": head["e2e"], "memory": head["memory"], "gpu_launches": head["gpu_launches"],
+                "clocks": head["clocks"], "fetal": fetal}
+        print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 

@@ -663,47 +663,6 @@ __device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, 
     return g;
 }
 
-// The record's in-cut columns of one tile row.  In the row at slice-centred
-// height rowf the exponent q(db) + log2 w_z is a downward parabola in db,
-//   A db^2 + C2 da db + (B da^2 + kappa),  kappa = log2 normal weight - qcut >= 0,
-// so the pixels inside the cut form one run: centre -C2 da / (2A), half-width
-// sqrt(D) / (2|A|), D = (C2 da)^2 - 4 A (B da^2 + kappa).  Returns the tile-local
-// columns [lo, hi] of that run clipped to [clo, chi] (false: empty).  The
-// half-width carries a 1e-3 px margin, so rounding never drops a pixel inside.
-__device__ __forceinline__ bool rec_row_span(const Rec &R, float rowf, float colf0, float qcut, int clo, int chi,
-                                             int &lo, int &hi) {
-    const float A = R.a.z, C2 = R.a.w, B = R.b.x;
-    const float da = rowf - R.a.y;
-    const float kap = fmaxf(R.b.z - qcut, 0.f);
-    const float cd = C2 * da;
-    const float D = fmaf(cd, cd, -4.f * A * fmaf(B * da, da, kap));
-    if (!(D >= 0.f)) return false;
-    const float ia = -0.5f / A;  // 1 / (2 |A|)
-    const float h = fmaf(sqrtf(D), ia, 1e-3f);
-    const float c = fmaf(cd, ia, R.a.x - colf0);
-    const float l = fminf(fmaxf(c - h, -1.f), 64.f), u = fminf(fmaxf(c + h, -1.f), 64.f);
-    lo = max((int)ceilf(l), clo);
-    hi = min((int)floorf(u), chi);
-    return lo <= hi;
-}
-
-// Tile rows [r0, r1] the record's in-cut ellipse can reach: D >= 0 needs
-// da^2 <= 4 A kappa / (C2^2 - 4 A B) (the denominator is < 0 for a
-// positive-definite conic; a degenerate one keeps every row).
-__device__ __forceinline__ void rec_row_range(const Rec &R, float rowf0, float qcut, int rows, int &r0, int &r1) {
-    const float A = R.a.z, C2 = R.a.w, B = R.b.x;
-    const float kap = fmaxf(R.b.z - qcut, 0.f);
-    const float den = fmaf(C2, C2, -4.f * A * B);
-    r0 = 0;
-    r1 = rows - 1;
-    if (den < 0.f) {
-        const float ext = sqrtf(4.f * A * kap / den) + 1e-3f;
-        const float c = R.a.y - rowf0;  // the record's centre row, tile-local
-        r0 = max(r0, (int)ceilf(fmaxf(c - ext, -1.f)));
-        r1 = min(r1, (int)floorf(fminf(c + ext, 64.f)));
-    }
-}
-
 // Persistent CTAs take work items from a queue (Counters::work_fwd).  An item's
 // records (at most kItemRecs x 32 bytes) come into shared memory by one 1-D bulk
 // copy (cp.async.bulk, completion on an mbarrier, one phase per item).  The CTA
@@ -748,6 +707,8 @@ __device__ __forceinline__ ItemRef item_ref(const EvalArgs &a, int w) {
 // row fixed, the record's row terms C2 da and B da^2 are formed once per PXR
 // pixels:
 //   q = (A db + C2 da) db + B da^2,   sum += w exp2(q).
+// Runs of two or more pixels are evaluated two pixels per packed f32x2
+// instruction (each lane the IEEE scalar operation).
 // The groups' sums meet in shared memory; part[item][pixel] holds the item's
 // sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
 // (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
@@ -759,8 +720,6 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(8) uint64_t bar_never;  // initialised, never arrived on (test hook only)
     __shared__ float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
-    __shared__ uint32_t rmask[256 * (kItemRecs / 32)];  // per run: bits of the records reaching it
-    __shared__ int row_lo[32], row_hi[32];              // sampled column range per tile row
     __shared__ int s_w[3], s_off[3], s_nrec[3], s_pend[3];
     __shared__ int s_fail;
     const int n_items = min(*a.n_items, a.cap_items);
@@ -865,67 +824,39 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
         float acc[PXR];
 #pragma unroll
         for (int k = 0; k < PXR; ++k) acc[k] = 0.f;
-        if (!COUNT) {
-            // Which records reach which run (PXR pixels of one row): a record's
-            // in-cut span of each row (rec_row_span), clipped to the row's sampled
-            // columns, sets the record's bit in the runs it overlaps.  Bits are
-            // set by atomicOr, so the masks do not depend on thread timing.
-            constexpr int kWords = kItemRecs / 32;
-            const int runs = tpg;
-            for (int k = tid; k < runs * kWords; k += blockDim.x) rmask[k] = 0u;
-            if (tid < 32) {
-                row_lo[tid] = 32;
-                row_hi[tid] = -1;
-            }
-            __syncthreads();
-            const int ps = a.tile_px_start[ir.t], pe = a.tile_px_end[ir.t];
-            for (int s2 = ps + tid; s2 < pe; s2 += blockDim.x) {
-                const int loc = a.sampled[s2] - S.pix_base;
-                const int r0 = loc / S.W;
-                atomicMin(&row_lo[r0 - tg.y0], loc - r0 * S.W - tg.x0);
-                atomicMax(&row_hi[r0 - tg.y0], loc - r0 * S.W - tg.x0);
-            }
-            __syncthreads();
-            const float rowf0 = (float)tg.y0 - S.cy0, colf00 = (float)tg.x0 - S.cx0;
-            for (int k = tid; k < nrec; k += blockDim.x) {
-                const Rec R = rb[k];
-                int r0, r1;
-                rec_row_range(R, rowf0, a.qcut, tg.rows, r0, r1);
-                for (int rw = r0; rw <= r1; ++rw) {
-                    int lo, hi;
-                    if (row_lo[rw] > row_hi[rw] ||
-                        !rec_row_span(R, rowf0 + (float)rw, colf00, a.qcut, row_lo[rw], row_hi[rw], lo, hi))
-                        continue;
-                    for (int j = lo / PXR; j <= hi / PXR; ++j)
-                        atomicOr(&rmask[(rw * segs + j) * kWords + (k >> 5)], 1u << (k & 31));
-                }
-            }
-            __syncthreads();
-            // group g takes mask words g, g + G, ...; a lane walks its run's bits in
-            // record order (the sum order is fixed: bitwise reproducible)
-            if (active) {
-                const int nw = (nrec + 31) >> 5;
-                const uint32_t *mrun = rmask + seg * kWords;
-                for (int w = g; w < nw; w += G) {
-                    uint32_t m = mrun[w];
-                    while (m) {
-                        const int r = (w << 5) + __ffs(m) - 1;
-                        m &= m - 1u;
-                        const float4 r0 = rb[r].a;
-                        const float4 r1 = rb[r].b;
-                        const float dy = rowf - r0.y;
-                        const float cdy = r0.w * dy;
-                        const float bdy = r1.x * dy * dy;
+        if (active) {
+            if (!COUNT && PXR >= 2) {
+                // two pixels per packed f32x2 instruction (the scalar loop below is issue
+                // bound at 5 slots per pair; packed, the FP32 pipe and MUFU bound it)
+                constexpr int H2 = PXR >= 2 ? PXR / 2 : 1;
+                float2 colk[H2], acc2[H2];
 #pragma unroll
-                        for (int k = 0; k < PXR; ++k) {
-                            const float dx = (colf0 + (float)k) - r0.x;
-                            const float q = fmaf(fmaf(r0.z, dx, cdy), dx, bdy);
-                            acc[k] = fmaf(r1.y, ex2_approx(q), acc[k]);
-                        }
+                for (int k = 0; k < H2; ++k) {
+                    colk[k] = make_float2(colf0 + (float)(2 * k), colf0 + (float)(2 * k + 1));
+                    acc2[k] = make_float2(0.f, 0.f);
+                }
+                for (int r = g; r < nrec; r += G) {
+                    const float4 r0 = rb[r].a;
+                    const float4 r1 = rb[r].b;
+                    const float dy = rowf - r0.y;
+                    const float2 cdy = make_float2(r0.w * dy, r0.w * dy);
+                    const float bdy1 = r1.x * dy * dy;
+                    const float2 bdy = make_float2(bdy1, bdy1);
+                    const float2 az = make_float2(r0.z, r0.z), ncb = make_float2(-r0.x, -r0.x);
+                    const float2 w2 = make_float2(r1.y, r1.y);
+#pragma unroll
+                    for (int k = 0; k < H2; ++k) {
+                        const float2 dx = f2_add(colk[k], ncb);
+                        const float2 q = f2_fma(f2_fma(az, dx, cdy), dx, bdy);
+                        acc2[k] = f2_fma(w2, make_float2(ex2_approx(q.x), ex2_approx(q.y)), acc2[k]);
                     }
                 }
-            }
-        } else if (active) {
+#pragma unroll
+                for (int k = 0; k < H2; ++k) {
+                    acc[2 * k] = acc2[k].x;
+                    if (2 * k + 1 < PXR) acc[2 * k + 1] = acc2[k].y;
+                }
+            } else
             for (int r = g; r < nrec; r += G) {
                 const float4 r0 = rb[r].a;
                 const float4 r1 = rb[r].b;
@@ -1063,19 +994,14 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 }
 
 // ---------------------------------------------------------------- backward
-// One CTA per work item (at most kItemRecs records of one tile), persistent
-// over the work queue.  The tile's r_bar values sit densely in shared memory
-// (0 for pixels outside the sample), with each row's sampled column range.
-//  1. Each thread takes two records and cuts each into units: one per tile row
-//     whose in-cut span meets the row's sampled range (rec_row_span).
-//  2. The units are counting-sorted by length, longest first, so that a warp's
-//     64 units (two per thread, side by side in the lanes of packed f32x2
-//     instructions) have nearly equal trip counts.
-//  3. A unit runs over its span: g = r_bar exp2(q) and the row sums g, g db,
-//     g db^2, stored at (record, row).
-//  4. Per record the rows fold, in row order, into the 6 moments sum g, g db,
-//     g da, g db^2, g db da, g da^2, written to the record's key slot.
-// Every sum has one fixed order, so the moments are bitwise reproducible.
+// One CTA per work item, thread per record (two records per thread, evaluated
+// side by side in the two lanes of packed f32x2 instructions).  The tile's
+// r_bar values sit densely in shared memory (0 for pixels outside the sample),
+// each stored twice so one 64-bit load feeds both lanes, and are read as
+// broadcasts row by row.  Per row the record's row terms are formed once and
+// three row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q)); at the
+// end of the row they fold into the 6 moments sum g, g db, g da, g db^2,
+// g db da, g da^2, written to the record's key slot.
 __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, float R2, float dy) {
     m[0] += R0;
     m[1] += R1;
@@ -1085,32 +1011,15 @@ __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, flo
     m[5] = fmaf(R0 * dy, dy, m[5]);
 }
 
-// Shared-memory bytes of k_bwd_units for a tile shape.
-__host__ __device__ constexpr size_t bwd_smem_bytes(int tile_w, int tile_h) {
-    return (size_t)kItemRecs * sizeof(Rec)                                   // records
-           + (size_t)kItemRecs * tile_h * 3 * sizeof(float)                  // row sums per (record, row)
-           + (size_t)kItemRecs * tile_h * sizeof(uint32_t)                   // unit descriptors
-           + (size_t)kItemRecs * tile_h * sizeof(uint16_t)                   // sorted order
-           + (((size_t)tile_w * tile_h * sizeof(float) + 15) & ~(size_t)15); // r_bar tile
-}
-
-__global__ void __launch_bounds__(kThreads) k_bwd_units(EvalArgs a) {
-    extern __shared__ __align__(16) unsigned char bsm[];
-    const int tw = a.tile_w, th = a.tile_h;
-    const int ucap = kItemRecs * th;
-    Rec *recs = reinterpret_cast<Rec *>(bsm);
-    float *rsum = reinterpret_cast<float *>(recs + kItemRecs);          // [record][row][3]
-    uint32_t *udesc = reinterpret_cast<uint32_t *>(rsum + 3 * ucap);     // record | row << 8 | lo << 13 | (len-1) << 18
-    uint16_t *order = reinterpret_cast<uint16_t *>(udesc + ucap);
-    float *rb = reinterpret_cast<float *>(bsm + (bwd_smem_bytes(tw, th) - (((size_t)tw * th * 4 + 15) & ~(size_t)15)));
-    __shared__ int s_item, s_nu;
-    __shared__ int row_lo[32], row_hi[32];
-    __shared__ int hist[33];
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
+    extern __shared__ float2 rb2[];  // tile_h x tile_w, each r_bar duplicated for the packed lanes
+    __shared__ int s_item;
+    __shared__ int row_lo[32], row_hi[32];  // sampled column range per tile row (lo > hi: none)
     const int n_items = min(*a.n_items, a.cap_items);
+    const int tw = a.tile_w;
     for (;;) {
-        __syncthreads();  // the previous item's shared data is free
-        if (tid == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
+        __syncthreads();  // previous item's r_bar tile is free
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
         __syncthreads();
         if (s_item >= n_items) break;
         const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
@@ -1121,102 +1030,57 @@ __global__ void __launch_bounds__(kThreads) k_bwd_units(EvalArgs a) {
         const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
         if (ps >= pe || rs >= re) continue;
         const SliceDev &S = a.slices[a.tile_slice[t]];
-        const TileGeom tg = tile_geom(S, t, tw, th);
-        const int nrec = re - rs;
-        // this thread's records (local k = tid, tid + kThreads) and their key slots
-        const int kA = tid, kB = tid + kThreads;
-        int slotA = -1, slotB = -1;
-        if (kA < nrec) {
-            const int2 ref = a.tref[rs + kA];
-            recs[kA] = a.rec[ref.x];
-            slotA = ref.y;
+        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
+        // this thread's two records: loads issued before the r_bar tile is built
+        const int r0 = rs + threadIdx.x;
+        const int r1 = r0 + kThreads;
+        const bool v0 = r0 < re, v1 = r1 < re;
+        const int2 refA = v0 ? a.tref[r0] : make_int2(0, 0);
+        const int2 refB = v1 ? a.tref[r1] : refA;
+        Rec A, B;
+        if (v0) {
+            A = a.rec[refA.x];
+            B = a.rec[refB.x];
         }
-        if (kB < nrec) {
-            const int2 ref = a.tref[rs + kB];
-            recs[kB] = a.rec[ref.x];
-            slotB = ref.y;
+        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb2[k] = make_float2(0.f, 0.f);
+        if (threadIdx.x < 32) {
+            row_lo[threadIdx.x] = 32;
+            row_hi[threadIdx.x] = -1;
         }
-        for (int k = tid; k < a.tile_px; k += kThreads) rb[k] = 0.f;
-        for (int k = tid; k < nrec * th * 3; k += kThreads) rsum[k] = 0.f;
-        if (tid < 32) {
-            row_lo[tid] = 32;
-            row_hi[tid] = -1;
-        }
-        if (tid <= 32) hist[tid] = 0;
-        if (tid == 0) s_nu = 0;
         __syncthreads();
-        for (int s2 = ps + tid; s2 < pe; s2 += kThreads) {
+        for (int s2 = ps + threadIdx.x; s2 < pe; s2 += kThreads) {
             // r_bar from the per-pixel buffer (a caller may have replaced the
             // forward's values there); the tile-local position from the forward
             const int rc = a.tpos_s[s2];
+            const float g = a.rbar[a.sampled[s2]];
             const int rr = rc >> 8, cc = rc & 255;
-            rb[rr * tw + cc] = a.rbar[a.sampled[s2]];
+            rb2[rr * tw + cc] = make_float2(g, g);
             atomicMin(&row_lo[rr], cc);
             atomicMax(&row_hi[rr], cc);
         }
         __syncthreads();
-        const float rowf0 = (float)tg.y0 - S.cy0;
+        if (!v0) continue;
+        float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float colf0 = (float)tg.x0 - S.cx0;
-        // 1. units of this thread's two records
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = h ? kB : kA;
-            if (k >= nrec) continue;
-            const Rec R = recs[k];
-            int r0, r1;
-            rec_row_range(R, rowf0, a.qcut, tg.rows, r0, r1);
-            for (int row = r0; row <= r1; ++row) {
-                int lo, hi;
-                if (row_lo[row] > row_hi[row] ||
-                    !rec_row_span(R, rowf0 + (float)row, colf0, a.qcut, row_lo[row], row_hi[row], lo, hi))
-                    continue;
-                const int u = atomicAdd(&s_nu, 1);
-                udesc[u] = (uint32_t)k | ((uint32_t)row << 8) | ((uint32_t)lo << 13) | ((uint32_t)(hi - lo) << 18);
-                atomicAdd(&hist[hi - lo], 1);
-            }
-        }
-        __syncthreads();
-        // 2. counting sort by length, longest first (order within a length is free:
-        //    every unit's sums are stored by (record, row))
-        const int nu = s_nu;
-        if (tid == 0) {
-            int run = 0;
-            for (int L = 31; L >= 0; --L) {
-                const int n = hist[L];
-                hist[L] = run;
-                run += n;
-            }
-        }
-        __syncthreads();
-        for (int u = tid; u < nu; u += kThreads) {
-            const int L = (int)((udesc[u] >> 18) & 31u);
-            order[atomicAdd(&hist[L], 1)] = (uint16_t)u;
-        }
-        __syncthreads();
-        // 3. units two at a time, in the two lanes of packed FP32 instructions
+        // records A and B side by side in the two lanes of packed float32
+        // operations: per column one shared load, 7 packed FP32 and 2 ex2 for
+        // the two (pixel, record) pairs
+        const float2 az = make_float2(A.a.z, B.a.z);
         const float2 one = make_float2(1.f, 1.f);
-        for (int pu = 2 * tid; pu < nu; pu += 2 * kThreads) {
-            const uint32_t dA = udesc[order[pu]];
-            const bool hasB = pu + 1 < nu;
-            const uint32_t dB = hasB ? udesc[order[pu + 1]] : dA;
-            const int ka = (int)(dA & 255u), rowa = (int)((dA >> 8) & 31u), loa = (int)((dA >> 13) & 31u);
-            const int kb = (int)(dB & 255u), rowb = (int)((dB >> 8) & 31u), lob = (int)((dB >> 13) & 31u);
-            const int La = (int)((dA >> 18) & 31u) + 1;
-            const int Lb = hasB ? (int)((dB >> 18) & 31u) + 1 : 0;  // Lb <= La (sorted)
-            const float4 A0 = recs[ka].a, B0 = recs[kb].a;
-            const float Ab = recs[ka].b.x, Bb = recs[kb].b.x;
-            const float dyA = rowf0 + (float)rowa - A0.y, dyB = rowf0 + (float)rowb - B0.y;
-            const float2 az = make_float2(A0.z, B0.z);
-            const float2 cc = make_float2(A0.w * dyA, B0.w * dyB);
-            const float2 bb = make_float2(Ab * dyA * dyA, Bb * dyB * dyB);
-            float2 dx = make_float2(colf0 + (float)loa - A0.x, colf0 + (float)lob - B0.x);
-            const float *ra = rb + rowa * tw + loa;
-            const float *rbp = rb + rowb * tw + lob;
+        for (int row = 0; row < tg.rows; ++row) {
+            const int c0 = row_lo[row], c1 = row_hi[row];  // rows and columns without samples are skipped
+            if (c0 > c1) continue;
+            const float rowf = (float)(tg.y0 + row) - S.cy0;
+            const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
+            const float2 cc = make_float2(A.a.w * dyA, B.a.w * dyB);
+            const float2 bb = make_float2(A.b.x * dyA * dyA, B.b.x * dyB * dyB);
             float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
-#pragma unroll 2
-            for (int j = 0; j < La; ++j) {
-                const float gb = rbp[min(j, max(Lb - 1, 0))];
-                const float2 gg = make_float2(ra[j], j < Lb ? gb : 0.f);
+            const float2 *rrow = rb2 + row * tw;
+            const float colc = colf0 + (float)c0;
+            float2 dx = make_float2(colc - A.a.x, colc - B.a.x);  // advance by one pixel per column
+#pragma unroll 4
+            for (int col = c0; col <= c1; ++col) {
+                const float2 gg = rrow[col];
                 const float2 q = f2_fma(f2_fma(az, dx, cc), dx, bb);
                 const float2 e = f2_mul(gg, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
                 const float2 ex = f2_mul(e, dx);
@@ -1225,31 +1089,16 @@ __global__ void __launch_bounds__(kThreads) k_bwd_units(EvalArgs a) {
                 s2 = f2_fma(ex, dx, s2);
                 dx = f2_add(dx, one);
             }
-            float *oa = rsum + 3 * (ka * th + rowa);
-            oa[0] = s0.x;
-            oa[1] = s1.x;
-            oa[2] = s2.x;
-            if (hasB) {
-                float *ob = rsum + 3 * (kb * th + rowb);
-                ob[0] = s0.y;
-                ob[1] = s1.y;
-                ob[2] = s2.y;
-            }
+            bwd_row_fold(mA, s0.x, s1.x, s2.x, dyA);
+            bwd_row_fold(mB, s0.y, s1.y, s2.y, dyB);
         }
-        __syncthreads();
-        // 4. fold each record's rows in row order (rows without a unit hold zeros)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = h ? kB : kA;
-            const int slot = h ? slotB : slotA;
-            if (k >= nrec) continue;
-            const float ca = recs[k].a.y;
-            float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const float *rsk = rsum + 3 * k * th;
-            for (int row = 0; row < tg.rows; ++row)
-                bwd_row_fold(m, rsk[3 * row], rsk[3 * row + 1], rsk[3 * row + 2], rowf0 + (float)row - ca);
-            a.mom[2 * slot] = make_float4(m[0], m[1], m[2], m[3]);
-            a.mom[2 * slot + 1] = make_float4(m[4], m[5], 0.f, 0.f);
+        const int k0 = refA.y;
+        a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
+        a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
+        if (v1) {
+            const int k1 = refB.y;
+            a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
+            a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
         }
     }
 }
@@ -2433,25 +2282,11 @@ int fwd_threads(int tile_w, int tile_h, int pxr) {
     const int G = std::max(1, 128 / tpg);
     return round_warp(G * tpg);
 }
-// k_bwd_units' dynamic shared memory above the default 48 KB needs an opt-in
-// per device; the largest size allowed so far is remembered per device.
-static void bwd_allow_smem(size_t bytes) {
-    static std::atomic<size_t> allowed[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return;
-    if (bytes > allowed[dev].load()) {
-        if (cudaFuncSetAttribute(k_bwd_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-            allowed[dev].store(bytes);
-        cudaGetLastError();
-    }
-}
-
 int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
     if (backward) {
-        bwd_allow_smem(bwd_smem_bytes(tile_w, tile_h));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_units, kThreads, bwd_smem_bytes(tile_w, tile_h));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kThreads,
+                                                      (size_t)tile_w * tile_h * sizeof(float2));
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
@@ -2509,9 +2344,7 @@ void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
 void launch_backward(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
     cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
-    const size_t smem = bwd_smem_bytes(a.tile_w, a.tile_h);
-    bwd_allow_smem(smem);
-    k_bwd_units<<<eval_grid(a, true), kThreads, smem, st>>>(a);
+    k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float2), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
