@@ -562,11 +562,11 @@ gsvr_status gsvr_set_sample_total(gsvr_ctx *ctx, int64_t n_total);
  * device-side wait of the library is bounded (1 s) and, when it runs out,
  * latches a status bit that gsvr_sync_status reports as GSVR_ERR_TIMEOUT while
  * the context stays usable.  To exercise that path without a fault, the next
- * n_forwards calls of gsvr_forward make block 0 of the tile evaluation wait,
- * for its first work item, on a shared-memory barrier that nothing ever
- * completes, bounded by limit_ns (1 us .. 1 s); the wait runs out, the block
- * stops taking work and still waits, with the normal bound, for the copies it
- * started.  That forward's results are invalid (GSVR_ERR_TIMEOUT at the next
+ * n_forwards calls of gsvr_forward make every block of the tile evaluation
+ * wait, for its first work item with records, on a shared-memory barrier that
+ * nothing ever completes, bounded by limit_ns (1 us .. 1 s); the wait runs
+ * out, the block stops taking work and still waits, with the normal bound,
+ * for the copies it started.  That forward's results are invalid (GSVR_ERR_TIMEOUT at the next
  * gsvr_sync_status); the forwards after it are normal.
  * Errors: GSVR_ERR_INVALID_ARG (bad counts or limit), GSVR_ERR_STATE (during
  * graph capture). */

@@ -222,9 +222,9 @@ bool finite_all(const float *v, int n) {
 
 size_t scan_scratch_blocks(gsvr_ctx *ctx) {
     size_t n = std::max<size_t>({(size_t)ctx->N + 1, (size_t)ctx->P + 1, (size_t)ctx->cap_rec + 1,
-                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_keys) + 1,
-                                 (size_t)256 * (size_t)sort_blocks((int)ctx->N) + 1,
-                                 (size_t)256 * (size_t)sort_blocks(ctx->cap_items) + 1});
+                                 sort_hist_size(ctx->cap_keys),
+                                 sort_hist_size((int)ctx->N),
+                                 sort_hist_size(ctx->cap_items)});
     return (n + kScanTile - 1) / kScanTile + 2;
 }
 
@@ -261,7 +261,7 @@ gsvr_status ensure_key_capacity(gsvr_ctx *ctx, int64_t want) {
     CK(ctx->d_vals_alt.ensure(cap));
     CK(ctx->d_tref.ensure((size_t)cap + 2));
     CK(ctx->d_mom.ensure((size_t)cap * 2));
-    CK(ctx->d_hist.ensure((size_t)256 * sort_blocks(cap) + 1));
+    CK(ctx->d_hist.ensure(sort_hist_size(cap)));
     ctx->cap_keys = cap;
     CK(ensure_scan_scratch(ctx));
     return ensure_item_capacity(ctx);
@@ -285,7 +285,7 @@ gsvr_status ensure_item_capacity(gsvr_ctx *ctx) {
         CK(ctx->d_item_order.ensure(n));
         CK(ctx->d_item_key_alt.ensure(n));
         CK(ctx->d_item_val_alt.ensure(n));
-        CK(ctx->d_item_hist.ensure((size_t)256 * sort_blocks(ctx->cap_items) + 1));
+        CK(ctx->d_item_hist.ensure(sort_hist_size(ctx->cap_items)));
     }
     CK(ensure_scan_scratch(ctx));
     return GSVR_OK;
@@ -1082,7 +1082,7 @@ gsvr_status topk_ensure(gsvr_ctx *ctx) {
     const size_t nb = (cap + 63) / 64;  // forward blocks of 64 or 128 threads
     const bool need = ctx->d_topk_keys.n < N || ctx->d_topk_gacc.n < 10 * N ||
                       ctx->d_topk_nbr.n < cap * (size_t)ctx->topk_K || ctx->d_topk_loss_part.n < nb ||
-                      ctx->d_topk_hist.n < (size_t)256 * sort_blocks((int)N) + 1 ||
+                      ctx->d_topk_hist.n < sort_hist_size((int)N) ||
                       ctx->d_scan_bsum.n < scan_scratch_blocks(ctx) + 1 || ctx->topk_n_dev != ctx->N;
     if (!need) return GSVR_OK;
     if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "top-K buffers must be sized before graph capture");
@@ -1093,7 +1093,7 @@ gsvr_status topk_ensure(gsvr_ctx *ctx) {
     CK(ctx->d_topk_gm.ensure(N));
     CK(ctx->d_topk_kalt.ensure(N));
     CK(ctx->d_topk_valt.ensure(N));
-    CK(ctx->d_topk_hist.ensure((size_t)256 * sort_blocks((int)N) + 1));
+    CK(ctx->d_topk_hist.ensure(sort_hist_size((int)N)));
     CK(ctx->d_topk_cstart.ensure(kTopkMaxCells));
     CK(ctx->d_topk_cend.ensure(kTopkMaxCells));
     CK(ctx->d_topk_nbr.ensure(cap * (size_t)ctx->topk_K));
@@ -1296,8 +1296,6 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     if (n_keys_max > 0)
         CK(radix_sort_pairs(ctx->d_keys.p, nullptr, ctx->d_keys_sorted.p, ctx->d_vals_sorted.p, &cnt->n_keys,
                             n_keys_max, ctx->sort_bits, ss, st, ctx->d_key_rec.p, ctx->d_tref.p));
-    CK(cudaMemsetAsync(ctx->d_tile_rec_start.p, 0, sizeof(int) * ctx->n_tiles, st));
-    CK(cudaMemsetAsync(ctx->d_tile_rec_end.p, 0, sizeof(int) * ctx->n_tiles, st));
     launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->n_tiles, ctx->d_tile_rec_start.p,
                            ctx->d_tile_rec_end.p, st);
     {

@@ -16,6 +16,8 @@ constexpr int kScanTile = 4096;   // items per block of the scans
 constexpr int kSortThreads = 256; // 8 warps
 constexpr int kSortItems = 16;    // keys per thread per radix pass (4096 per block)
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortDigitMax = 9;    // widest radix digit (bits) of one sort pass
+constexpr int kSortRadixMax = 1 << kSortDigitMax;
 
 // Device status word bits (latched; read by gsvr_sync_status).
 enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
@@ -172,7 +174,10 @@ struct SortScratch {
     ScanScratch scan;
 };
 int sort_blocks(int n_max);
-// Stable LSD radix sort of n u32 keys (only the low `bits` bits are used) with
+// ints of the per-pass digit histogram (any digit width up to kSortDigitMax)
+size_t sort_hist_size(int n_max);
+// Stable LSD radix sort of n u32 keys (only the low `bits` bits are used, in
+// ceil(bits / 9) passes of equal digit width) with
 // u32 values; vals_in == null means values are the identity 0..n-1.  Result in
 // keys_out / vals_out; when `tref` is given the last pass writes, instead of the
 // values, tref[pos] = (key_rec[value], value).

@@ -195,7 +195,11 @@ __device__ __forceinline__ bool rec_bbox(const RecGeom &G, const SliceDev &S, fl
 // inside, else on an edge at the clamped stationary point).  The record's pair
 // factors inside the rectangle are at most 2^(this).  Explicit roundings keep
 // the result identical wherever it is evaluated.
-__device__ __forceinline__ float rect_max_exponent(const Rec &R, float x0, float x1, float y0, float y1) {
+// iAB = (-1/2 / A, -1/2 / B) of the record (rec_inv_ab), taken once per record.
+__device__ __forceinline__ float2 rec_inv_ab(const Rec &R) {
+    return make_float2(__fdiv_rn(-0.5f, R.a.z), __fdiv_rn(-0.5f, R.b.x));
+}
+__device__ __forceinline__ float rect_max_exponent(const Rec &R, float2 iAB, float x0, float x1, float y0, float y1) {
     const float A = R.a.z, C = R.a.w, B = R.b.x;
     const float X0 = __fsub_rn(x0, R.a.x), X1 = __fsub_rn(x1, R.a.x);
     const float Y0 = __fsub_rn(y0, R.a.y), Y1 = __fsub_rn(y1, R.a.y);
@@ -204,7 +208,7 @@ __device__ __forceinline__ float rect_max_exponent(const Rec &R, float x0, float
         return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, u), u), __fmul_rn(__fmul_rn(C, u), v)),
                          __fmul_rn(__fmul_rn(B, v), v));
     };
-    const float iA = __fdiv_rn(-0.5f, A), iB = __fdiv_rn(-0.5f, B);
+    const float iA = iAB.x, iB = iAB.y;
     float best = -INFINITY;
     const float Xs[2] = {X0, X1}, Ys[2] = {Y0, Y1};
 #pragma unroll
@@ -218,13 +222,13 @@ __device__ __forceinline__ float rect_max_exponent(const Rec &R, float x0, float
 }
 
 // Whether tile (tx, ty) of slice S has sampled pixels and the record reaches it.
-__device__ __forceinline__ bool tile_live(const Rec &R, const SliceDev &S, int tx, int ty, int tw, int th,
+__device__ __forceinline__ bool tile_live(const Rec &R, float2 iAB, const SliceDev &S, int tx, int ty, int tw, int th,
                                           const int *tps, const int *tpe, float qcut) {
     const int t = S.tile_base + ty * S.tiles_x + tx;
     if (tpe[t] <= tps[t]) return false;
     const float x0 = (float)(tx * tw) - S.cx0, x1 = (float)min(tx * tw + tw - 1, S.W - 1) - S.cx0;
     const float y0 = (float)(ty * th) - S.cy0, y1 = (float)min(ty * th + th - 1, S.H - 1) - S.cy0;
-    return rect_max_exponent(R, x0, x1, y0, y1) >= qcut;
+    return rect_max_exponent(R, iAB, x0, x1, y0, y1) >= qcut;
 }
 
 // Live tiles of a record's box; mask gets their row-major bits when the box
@@ -234,10 +238,11 @@ __device__ __forceinline__ int count_live_tiles(const Rec &R, const SliceDev &S,
                                                 unsigned &mask) {
     int n = 0, b = 0;
     const bool fits = (tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 32;
+    const float2 iAB = rec_inv_ab(R);
     mask = 0u;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx, ++b)
-            if (tile_live(R, S, tx, ty, tw, th, tps, tpe, qcut)) {
+            if (tile_live(R, iAB, S, tx, ty, tw, th, tps, tpe, qcut)) {
                 ++n;
                 if (fits) mask |= 1u << b;
             }
@@ -579,9 +584,11 @@ __global__ void k_key_emit(KeyArgs a) {
             ++k;
         }
     } else {
+        const float2 iAB = rec_inv_ab(R);
         for (int ty = ty0; ty <= ty1 && k < k1; ++ty)
             for (int tx = tx0; tx <= tx1 && k < k1; ++tx) {
-                if (!tile_live(R, S, tx, ty, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut)) continue;
+                if (!tile_live(R, iAB, S, tx, ty, a.tile_w, a.tile_h, a.tile_px_start, a.tile_px_end, a.qcut))
+                    continue;
                 if (k < a.cap_keys) {
                     a.keys[k] = (uint32_t)(S.tile_base + ty * S.tiles_x + tx);
                     a.key_rec[k] = r;
@@ -601,15 +608,24 @@ __global__ void k_key_emit(KeyArgs a) {
     }
 }
 
+// Thread per tile: its run [start, end) in the sorted keys, by two binary
+// searches (sentinel keys, tile id n_tiles, sort past every real tile).
 __global__ void k_tile_rec_ranges(const uint32_t *__restrict__ keys, const int *n_keys, int cap, int n_tiles,
                                   int *start, int *end) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
     const int n = min(*n_keys, cap);
-    if (s >= n) return;
-    const uint32_t t = keys[s];
-    if (t >= (uint32_t)n_tiles) return;  // sentinel keys
-    if (s == 0 || keys[s - 1] != t) start[t] = s;
-    if (s == n - 1 || keys[s + 1] != t) end[t] = s + 1;
+    auto lower = [&](uint32_t v) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(keys + mid) < v) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    start[t] = lower((uint32_t)t);
+    end[t] = lower((uint32_t)t + 1u);
 }
 
 // ------------------------------------------------------------- work items
@@ -760,9 +776,9 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
         bulk_g2s(&sref[slot][0], a.tref + a0, (uint32_t)cnt * (uint32_t)sizeof(int2), &bar[slot]);
     };
     // all threads: wait for slot's references, then start its record copies into buf[b].
-    // Under the test hook block 0's first such wait is on bar_never instead and
-    // runs out after a.wait_test_ns; the copy it skipped is drained below.
-    bool test_wait = a.wait_test_ns > 0 && blockIdx.x == 0;
+    // Under the test hook every block's first such wait is on bar_never instead
+    // and runs out after a.wait_test_ns; the copies it skipped are drained below.
+    bool test_wait = a.wait_test_ns > 0;
     auto gather = [&](int slot, int b) -> bool {
         const int nrec = s_nrec[slot];
         if (nrec > 0) {
@@ -2247,8 +2263,9 @@ void launch_key_emit(const KeyArgs &a, int n_rec_max, cudaStream_t st) {
 }
 void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_keys, int n_tiles, int *start, int *end,
                             cudaStream_t st) {
-    if (cap_keys <= 0) return;
-    k_tile_rec_ranges<<<cdiv(cap_keys, 256), 256, 0, st>>>(keys, n_keys, cap_keys, n_tiles, start, end);
+    // every tile is written, also when there are no keys (cap_keys 0: empty ranges, keys never read)
+    if (n_tiles <= 0) return;
+    k_tile_rec_ranges<<<cdiv(n_tiles, 256), 256, 0, st>>>(keys, n_keys, std::max(cap_keys, 0), n_tiles, start, end);
     counted();
 }
 static inline int round_warp(int n) { return (n + 31) / 32 * 32; }

@@ -84,8 +84,8 @@ struct EvalArgs {
     int n_tiles;
     unsigned *status;
     int64_t n_weight;                 // > 0: pixel weight 1 / n_weight (gsvr_set_sample_total), else 1 / sample size
-    // test hook (gsvr_test_wait_timeout): > 0 makes block 0's first record wait
-    // of the forward wait, bounded by this many ns, on a barrier nothing completes
+    // test hook (gsvr_test_wait_timeout): > 0 makes every block's first record
+    // wait of the forward wait, bounded by this many ns, on a barrier nothing completes
     int64_t wait_test_ns;
 };
 

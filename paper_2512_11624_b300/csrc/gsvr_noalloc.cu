@@ -234,14 +234,14 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     uint32_t *d_ka = cv.take<uint32_t>(cap_keys);
     uint32_t *d_va = cv.take<uint32_t>(cap_keys);
     int2 *d_tref = cv.take<int2>((size_t)cap_keys + 2);
-    int *d_hist = cv.take<int>((size_t)256 * sort_blocks(cap_keys) + 1);
+    int *d_hist = cv.take<int>(sort_hist_size(cap_keys));
     const int cap_items = (int)(T + cap_keys / kItemRecs + 2);
     int *d_item_cnt = cv.take<int>(T + 1);
     int *d_item_first = cv.take<int>(T + 1);
     int *d_item_tile = cv.take<int>(cap_items);
     float *d_part = cv.take<float>((size_t)cap_items * kTile * kTile);
     const size_t scan_n = std::max<size_t>({(size_t)N + 1, (size_t)P + 1, (size_t)cap_rec + 1,
-                                            (size_t)256 * (size_t)sort_blocks(cap_keys) + 1});
+                                            sort_hist_size(cap_keys)});
     const int bsum_blocks = (int)((scan_n + kScanTile - 1) / kScanTile + 2);
     int *d_bsum = cv.take<int>((size_t)bsum_blocks + 1);
     if (cv.used() > kScratchBytes) {

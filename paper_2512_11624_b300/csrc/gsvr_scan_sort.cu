@@ -7,6 +7,8 @@
 // an exclusive scan of the digit-major histogram, and a stable scatter whose
 // in-block ranks come from warp-level __match_any_sync over (warp, round, lane)
 // order, so equal keys keep their input order.
+#include <algorithm>
+
 #include "gsvr_launch.cuh"
 
 namespace gsvr {
@@ -110,11 +112,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int *in, int *
 }
 
 // ---------------------------------------------------------------- radix sort
+template <int RADIX>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *keys, const int *d_n, int n_max,
                                                              int shift, int *hist, int nb) {
-    __shared__ int cnt[256];
+    __shared__ int cnt[RADIX];
     const int n = min(*d_n, n_max);
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) cnt[d] = 0;
+    for (int d = threadIdx.x; d < RADIX; d += kSortThreads) cnt[d] = 0;
     __syncthreads();
     const int base = blockIdx.x * kSortTile;
     if (base < n) {
@@ -122,11 +125,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 #pragma unroll 4
         for (int r = 0; r < kSortItems; ++r) {
             int idx = base + w * (32 * kSortItems) + r * 32 + lane;
-            if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255u], 1);
+            if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & (RADIX - 1u)], 1);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) hist[d * nb + blockIdx.x] = cnt[d];
+    for (int d = threadIdx.x; d < RADIX; d += kSortThreads) hist[d * nb + blockIdx.x] = cnt[d];
 }
 
 // GATHER: instead of the values, write tref[pos] = (key_rec[value], value): the
@@ -134,20 +137,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 // The block first orders its tile by digit in shared memory (stable), then
 // writes each digit's run to its global range with consecutive threads on
 // consecutive addresses (coalesced stores).
-template <bool GATHER>
+template <bool GATHER, int RADIX>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                                 uint32_t *kout, uint32_t *vout, const int *d_n,
                                                                 int n_max, int shift, const int *hist_scan,
                                                                 int nb, const int *key_rec, int2 *tref) {
     constexpr int NW = kSortThreads / 32;
-    __shared__ int cnt[NW][256];
-    __shared__ int dstart[256];
+    constexpr int DPT = RADIX / kSortThreads;  // digits per thread in the digit scans
+    // per-warp digit counts fit 16 bits (a warp ranks 32 x kSortItems keys)
+    __shared__ unsigned short cnt[NW][RADIX];
+    __shared__ int dstart[RADIX];
     __shared__ uint32_t skey[kSortTile], sval[kSortTile];
     const int n = min(*d_n, n_max);
     const int base = blockIdx.x * kSortTile;
     if (base >= n) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    for (int d = lane; d < RADIX; d += 32) cnt[w][d] = 0;
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[kSortItems], val[kSortItems];
@@ -158,14 +163,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
         const bool ok = idx < n;
         key[r] = ok ? kin[idx] : 0u;
         val[r] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
-        const unsigned d = ok ? ((key[r] >> shift) & 255u) : 256u;
+        const unsigned d = ok ? ((key[r] >> shift) & (RADIX - 1u)) : (unsigned)RADIX;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = 0;
         if (ok) before = cnt[w][d];
         __syncwarp();
         if (ok) {
             rank[r] = before + __popc(peers & lt);
-            if ((peers & lt) == 0) cnt[w][d] = before + __popc(peers);
+            if ((peers & lt) == 0) cnt[w][d] = (unsigned short)(before + __popc(peers));
         } else {
             rank[r] = -1;
         }
@@ -173,23 +178,35 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, then the block's digit starts
+    // (thread t owns digits t * DPT .. t * DPT + DPT - 1)
     {
-        const int d = threadIdx.x;  // kSortThreads == 256 digits
-        int run = 0;
+        int runs[DPT], sum = 0;
 #pragma unroll
-        for (int ww = 0; ww < NW; ++ww) {
-            const int c = cnt[ww][d];
-            cnt[ww][d] = run;
-            run += c;
+        for (int k = 0; k < DPT; ++k) {
+            const int d = threadIdx.x * DPT + k;
+            int run = 0;
+#pragma unroll
+            for (int ww = 0; ww < NW; ++ww) {
+                const int c = cnt[ww][d];
+                cnt[ww][d] = (unsigned short)run;
+                run += c;
+            }
+            runs[k] = run;
+            sum += run;
         }
         int total;
-        dstart[d] = block_excl_scan<kSortThreads>(run, total);
+        int start = block_excl_scan<kSortThreads>(sum, total);
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+            dstart[threadIdx.x * DPT + k] = start;
+            start += runs[k];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (rank[r] < 0) continue;
-        const unsigned d = (key[r] >> shift) & 255u;
+        const unsigned d = (key[r] >> shift) & (RADIX - 1u);
         const int local = dstart[d] + cnt[w][d] + rank[r];
         skey[local] = key[r];
         sval[local] = val[r];
@@ -199,7 +216,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     if (!GATHER) {
         for (int i = threadIdx.x; i < nb_keys; i += kSortThreads) {
             const uint32_t k = skey[i];
-            const unsigned d = (k >> shift) & 255u;
+            const unsigned d = (k >> shift) & (RADIX - 1u);
             const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
             kout[pos] = k;
             vout[pos] = sval[i];
@@ -223,7 +240,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
             const int i = i0 + q * kSortThreads;
             if (i >= nb_keys) continue;
             const uint32_t k = skey[i];
-            const unsigned d = (k >> shift) & 255u;
+            const unsigned d = (k >> shift) & (RADIX - 1u);
             const int pos = hist_scan[d * nb + blockIdx.x] + (i - dstart[d]);
             kout[pos] = k;
             tref[pos] = make_int2(kr[q], (int)v[q]);
@@ -247,27 +264,42 @@ cudaError_t scan_exclusive(const int *in, int *out, const int *d_n, int n_static
 
 int sort_blocks(int n_max) { return n_max <= 0 ? 1 : (n_max + kSortTile - 1) / kSortTile; }
 
+size_t sort_hist_size(int n_max) { return (size_t)kSortRadixMax * (size_t)sort_blocks(n_max) + 1; }
+
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                              uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
                              cudaStream_t st, const int *key_rec, int2 *tref) {
     const int nb = sort_blocks(n_max);
-    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    // passes of equal digit width, at most 9 bits (512 bins): 16-bit keys take two
+    // 8-bit passes, 17- and 18-bit keys two 9-bit passes
+    const int passes = bits <= 0 ? 1 : (bits + kSortDigitMax - 1) / kSortDigitMax;
+    const int width = bits <= 0 ? 8 : std::max(1, (bits + passes - 1) / passes);
+    const bool wide = width > 8;
+    const int radix = wide ? 512 : 256;
     const uint32_t *ksrc = keys_in;
     const uint32_t *vsrc = vals_in;
     for (int p = 0; p < passes; ++p) {
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t *kdst = to_out ? keys_out : s.keys_alt;
         uint32_t *vdst = to_out ? vals_out : s.vals_alt;
-        const int shift = 8 * p;
-        k_radix_hist<<<nb, kSortThreads, 0, st>>>(ksrc, d_n, n_max, shift, s.hist, nb);
-        cudaError_t e = scan_exclusive(s.hist, s.hist, nullptr, 256 * nb, 256 * nb, nullptr, s.scan, st);
+        const int shift = width * p;
+        if (wide) k_radix_hist<512><<<nb, kSortThreads, 0, st>>>(ksrc, d_n, n_max, shift, s.hist, nb);
+        else k_radix_hist<256><<<nb, kSortThreads, 0, st>>>(ksrc, d_n, n_max, shift, s.hist, nb);
+        cudaError_t e = scan_exclusive(s.hist, s.hist, nullptr, radix * nb, radix * nb, nullptr, s.scan, st);
         if (e != cudaSuccess) return e;
-        if (tref && p == passes - 1)
-            k_radix_scatter<true><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
-                                                               nb, key_rec, tref);
+        const bool last = tref && p == passes - 1;
+        if (last && wide)
+            k_radix_scatter<true, 512><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift,
+                                                                    s.hist, nb, key_rec, tref);
+        else if (last)
+            k_radix_scatter<true, 256><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift,
+                                                                    s.hist, nb, key_rec, tref);
+        else if (wide)
+            k_radix_scatter<false, 512><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift,
+                                                                     s.hist, nb, nullptr, nullptr);
         else
-            k_radix_scatter<false><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift, s.hist,
-                                                                nb, nullptr, nullptr);
+            k_radix_scatter<false, 256><<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, d_n, n_max, shift,
+                                                                     s.hist, nb, nullptr, nullptr);
         note_launches(2);
         ksrc = kdst;
         vsrc = vdst;

@@ -1,8 +1,8 @@
 """Failure detection without a GPU fault: a bounded device-side wait that runs
-out.  The test hook gsvr_test_wait_timeout makes the next forward's block 0
-wait for its first work item on a shared-memory barrier that nothing
-completes (bounded at 2 ms); the wait runs out, the block drains the copies
-it started (normal 1 s bound) and stops.  The host reads GSVR_ERR_TIMEOUT at
+out.  The test hook gsvr_test_wait_timeout makes every block of the next
+forward wait, for its first work item with records, on a shared-memory
+barrier that nothing completes (bounded at 2 ms); the wait runs out, the
+block drains the copies it started (normal 1 s bound) and stops.  The host reads GSVR_ERR_TIMEOUT at
 gsvr_sync_status, and the context stays usable: the next forward is normal
 and gives bitwise the predictions of the forward before the hook."""
 import numpy as np
