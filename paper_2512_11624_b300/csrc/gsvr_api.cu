@@ -131,6 +131,8 @@ struct gsvr_ctx {
     // outputs
     DBuf<float> d_pred, d_rbar;
     DBuf<int> d_tpos_s;    // tile-local (row << 8 | col) in sample order (written by the forward)
+    DBuf<short2> d_row_rng;  // per tile row: sampled column range (written by the forward)
+    DBuf<float> d_rbar_tile; // dense r_bar per tile pixel (built by the backward)
     DBuf<double> d_tile_loss, d_loss, d_pose_acc;
     DBuf<unsigned> d_status;
     DBuf<Counters> d_counters;
@@ -307,6 +309,9 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.pred = ctx->d_pred.p;
     e.rbar = ctx->d_rbar.p;
     e.tpos_s = ctx->d_tpos_s.p;
+    e.row_rng = ctx->d_row_rng.p;
+    e.rbar_tile = ctx->d_rbar_tile.p;
+    e.pix_tile = ctx->d_pix_tile.p;
     e.tile_loss = ctx->d_tile_loss.p;
     e.mom = ctx->d_mom.p;
     e.counters = ctx->d_counters.p;
@@ -672,6 +677,8 @@ gsvr_status gsvr_set_stacks(gsvr_ctx *ctx, int32_t n_stacks, const gsvr_stack_de
     CK(ctx->d_pred.ensure(P));
     CK(ctx->d_rbar.ensure(P));
     CK(ctx->d_tpos_s.ensure(P));
+    CK(ctx->d_row_rng.ensure((size_t)std::max(T, (int64_t)1) * ctx->tile_h));
+    CK(ctx->d_rbar_tile.ensure((size_t)std::max(T, (int64_t)1) * ctx->tile_h * ctx->tile_w));
     CK(ctx->d_tile_px_start.ensure(T));
     CK(ctx->d_tile_px_end.ensure(T));
     CK(ctx->d_tile_rec_start.ensure(T));
@@ -1343,7 +1350,7 @@ gsvr_status gsvr_backward(gsvr_ctx *ctx) {
     if (ctx->topk_K > 0) return topk_backward(ctx);
     EvalArgs e = eval_args(ctx, ctx->grid_items);
     stage_begin(ctx, GSVR_STAGE_BWD_EVAL);
-    launch_backward(e, st);
+    launch_backward(e, (int)ctx->n_mask, st);
     stage_end(ctx, GSVR_STAGE_BWD_EVAL);
     stage_begin(ctx, GSVR_STAGE_GRAD);
     CK(cudaMemsetAsync(ctx->d_pose_acc.p, 0, sizeof(double) * 12 * M, st));

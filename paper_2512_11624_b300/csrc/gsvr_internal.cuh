@@ -83,29 +83,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// Packed two-wide float32 arithmetic (PTX f32x2, sm_100 family): each lane is
-// the IEEE round-to-nearest scalar operation; two lanes per issue slot.
-__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
-    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
-}
-__device__ __forceinline__ float2 f2_from(unsigned long long b) {
-    return make_float2(__uint_as_float((uint32_t)b), __uint_as_float((uint32_t)(b >> 32)));
-}
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
-    return f2_from(d);
-}
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-    return f2_from(d);
-}
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-    return f2_from(d);
-}
+// Packed two-wide float32 arithmetic (f32x2, sm_100 family) through the
+// compiler's float2 builtins: each lane is the IEEE round-to-nearest scalar
+// operation, two lanes per issue slot, and the compiler keeps the operands in
+// register pairs (no packing moves around each instruction).
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -946,6 +946,7 @@ __device__ __forceinline__ SlwTerms slw_terms(const float *slw, int M, int i, in
 // Per tile: add the items' partial sums in order, then residual, dL/dI_hat and loss.
 __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
     __shared__ double red[kMaxTilePx / 32], red_s[kMaxTilePx / 32], red_o[kMaxTilePx / 32];
+    __shared__ int rlo[32], rhi[32];  // sampled column range per tile row
     const int t = blockIdx.x;
     const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
     if (ps >= pe) {
@@ -955,6 +956,11 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         }
         return;
     }
+    if (threadIdx.x < 32) {
+        rlo[threadIdx.x] = 32;
+        rhi[threadIdx.x] = -1;
+    }
+    __syncthreads();
     const int s = ps + threadIdx.x;
     double l = 0.0, gs = 0.0, go = 0.0;
     if (s < pe) {
@@ -974,6 +980,8 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         a.pred[p] = st.pred;
         a.rbar[p] = st.dLdm;
         if (a.tpos_s) a.tpos_s[s] = ((r0 - tg.y0) << 8) | (loc - r0 * S.W - tg.x0);  // for the backward
+        atomicMin(&rlo[r0 - tg.y0], loc - r0 * S.W - tg.x0);
+        atomicMax(&rhi[r0 - tg.y0], loc - r0 * S.W - tg.x0);
         l = st.loss;
         gs = (double)st.gsig;
         go = (double)st.gomg;
@@ -990,6 +998,8 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         red_o[threadIdx.x >> 5] = go;
     }
     __syncthreads();
+    if (a.row_rng && threadIdx.x < a.tile_h)
+        a.row_rng[t * a.tile_h + threadIdx.x] = make_short2((short)rlo[threadIdx.x], (short)rhi[threadIdx.x]);
     if (threadIdx.x == 0) {
         double sum = 0.0, ss = 0.0, so = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
@@ -1012,7 +1022,7 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 // ---------------------------------------------------------------- backward
 // One CTA per work item, thread per record (two records per thread, evaluated
 // side by side in the two lanes of packed f32x2 instructions).  The tile's
-// r_bar values sit densely in shared memory (0 for pixels outside the sample),
+// r_bar values (k_rbar_tiles) sit densely in shared memory (0 for pixels outside the sample),
 // each stored twice so one 64-bit load feeds both lanes, and are read as
 // broadcasts row by row.  Per row the record's row terms are formed once and
 // three row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q)); at the
@@ -1027,7 +1037,7 @@ __device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, flo
     m[5] = fmaf(R0 * dy, dy, m[5]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, 8) k_bwd_items(EvalArgs a) {
     extern __shared__ float2 rb2[];  // tile_h x tile_w, each r_bar duplicated for the packed lanes
     __shared__ int s_item;
     __shared__ int row_lo[32], row_hi[32];  // sampled column range per tile row (lo > hi: none)
@@ -1058,21 +1068,17 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             A = a.rec[refA.x];
             B = a.rec[refB.x];
         }
-        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) rb2[k] = make_float2(0.f, 0.f);
-        if (threadIdx.x < 32) {
-            row_lo[threadIdx.x] = 32;
-            row_hi[threadIdx.x] = -1;
+        // the tile's r_bar (dense, 0 off the sample: k_rbar_tiles) and per-row
+        // sampled column ranges (k_fwd_reduce), coalesced loads
+        const float *rt = a.rbar_tile + (size_t)t * a.tile_px;
+        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) {
+            const float g = __ldg(rt + k);
+            rb2[k] = make_float2(g, g);
         }
-        __syncthreads();
-        for (int s2 = ps + threadIdx.x; s2 < pe; s2 += kThreads) {
-            // r_bar from the per-pixel buffer (a caller may have replaced the
-            // forward's values there); the tile-local position from the forward
-            const int rc = a.tpos_s[s2];
-            const float g = a.rbar[a.sampled[s2]];
-            const int rr = rc >> 8, cc = rc & 255;
-            rb2[rr * tw + cc] = make_float2(g, g);
-            atomicMin(&row_lo[rr], cc);
-            atomicMax(&row_hi[rr], cc);
+        if (threadIdx.x < a.tile_h) {
+            const short2 rr = a.row_rng[t * a.tile_h + threadIdx.x];
+            row_lo[threadIdx.x] = rr.x;
+            row_hi[threadIdx.x] = rr.y;
         }
         __syncthreads();
         if (!v0) continue;
@@ -1117,6 +1123,17 @@ __global__ void __launch_bounds__(kThreads) k_bwd_items(EvalArgs a) {
             a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
         }
     }
+}
+
+// Dense per-tile r_bar for the backward: thread per sample, from the per-pixel
+// buffer (a caller may have replaced the forward's values there); the buffer
+// is zeroed first, so pixels off the sample hold 0.
+__global__ void k_rbar_tiles(EvalArgs a, int cap) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= min(*a.n_sampled, cap)) return;
+    const int p = a.sampled[s];
+    const int rc = a.tpos_s[s];
+    a.rbar_tile[(size_t)a.pix_tile[p] * a.tile_px + (rc >> 8) * a.tile_w + (rc & 255)] = a.rbar[p];
 }
 
 // Per-subject losses: block k sums its subject's tiles in tile order.
@@ -2358,8 +2375,13 @@ void launch_count_pairs(const EvalArgs &a, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
     fwd_items<true>(a, st);
 }
-void launch_backward(const EvalArgs &a, cudaStream_t st) {
+void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st) {
     if (a.n_tiles <= 0 || a.cap_items <= 0) return;
+    cudaMemsetAsync(a.rbar_tile, 0, sizeof(float) * (size_t)a.n_tiles * a.tile_px, st);
+    if (cap_px > 0) {
+        k_rbar_tiles<<<cdiv(cap_px, 256), 256, 0, st>>>(a, cap_px);
+        counted();
+    }
     cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
     k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float2), st>>>(a);
     counted();

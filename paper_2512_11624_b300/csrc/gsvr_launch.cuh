@@ -59,6 +59,9 @@ struct EvalArgs {
     const float *I_obs;        // per global pixel
     float *pred, *rbar;        // per global pixel
     int *tpos_s;               // tile-local (row << 8 | col) per sample position (null: not written)
+    short2 *row_rng;           // per tile row: sampled columns (lo, hi; lo > hi: none), from k_fwd_reduce (null: not written)
+    float *rbar_tile;          // dense r_bar per tile pixel (0 off the sample), built before the backward
+    const int *pix_tile;       // tile of each global pixel
     double *tile_loss;         // per tile
     float4 *mom;               // 2 per key (backward)
     Counters *counters;
@@ -132,7 +135,8 @@ void launch_forward(const EvalArgs &a, cudaStream_t st);
 void launch_count_pairs(const EvalArgs &a, cudaStream_t st);
 long long launch_count();  // kernels launched by this library so far
 void note_launches(int n); // count kernels launched from other translation units
-void launch_backward(const EvalArgs &a, cudaStream_t st);
+// Dense r_bar tiles (from the per-pixel r_bar of the cap_px sample slots), then the tile adjoint.
+void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st);
 // Per-subject losses (subject k owns tiles [tile_first[k], tile_first[k+1]), summed in
 // tile order) and their total; tile_first null = one subject.
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
