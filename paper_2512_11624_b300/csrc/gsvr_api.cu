@@ -91,7 +91,8 @@ struct gsvr_ctx {
     DBuf<Rec> d_rec;
     DBuf<int2> d_tref;
     DBuf<int2> d_rec_tiles, d_cand;
-    DBuf<uint32_t> d_keys, d_keys_sorted, d_vals_sorted, d_keys_alt, d_vals_alt;
+    DBuf<uint32_t> d_keys, d_keys_sorted, d_keys_alt;
+    DBuf<int2> d_vals_alt;
     DBuf<int> d_hist, d_scan_bsum;
     DBuf<float4> d_mom;
     DBuf<int> d_item_cnt, d_item_first, d_item_tile;
@@ -258,7 +259,6 @@ gsvr_status ensure_key_capacity(gsvr_ctx *ctx, int64_t want) {
     CK(ctx->d_keys.ensure(cap));
     CK(ctx->d_key_rec.ensure(cap));
     CK(ctx->d_keys_sorted.ensure(cap));
-    CK(ctx->d_vals_sorted.ensure(cap));
     CK(ctx->d_keys_alt.ensure(cap));
     CK(ctx->d_vals_alt.ensure(cap));
     CK(ctx->d_tref.ensure((size_t)cap + 2));
@@ -1299,10 +1299,10 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     k.status = ctx->d_status.p;
     launch_key_emit(k, n_rec_max, st);
     CK(cudaGetLastError());
-    SortScratch ss{ctx->d_keys_alt.p, ctx->d_vals_alt.p, ctx->d_hist.p, scan_scratch(ctx)};
+    TileSortScratch ss{ctx->d_keys_alt.p, ctx->d_vals_alt.p, ctx->d_hist.p, scan_scratch(ctx)};
     if (n_keys_max > 0)
-        CK(radix_sort_pairs(ctx->d_keys.p, nullptr, ctx->d_keys_sorted.p, ctx->d_vals_sorted.p, &cnt->n_keys,
-                            n_keys_max, ctx->sort_bits, ss, st, ctx->d_key_rec.p, ctx->d_tref.p));
+        CK(sort_tile_keys(ctx->d_keys.p, ctx->d_key_rec.p, ctx->d_keys_sorted.p, ctx->d_tref.p, &cnt->n_keys,
+                          n_keys_max, ctx->sort_bits, ss, ctx->d_status.p, st));
     launch_tile_rec_ranges(ctx->d_keys_sorted.p, &cnt->n_keys, n_keys_max, ctx->n_tiles, ctx->d_tile_rec_start.p,
                            ctx->d_tile_rec_end.p, st);
     {

@@ -18,6 +18,7 @@ constexpr int kSortItems = 16;    // keys per thread per radix pass (4096 per bl
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortDigitMax = 9;    // widest radix digit (bits) of one sort pass
 constexpr int kSortRadixMax = 1 << kSortDigitMax;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s bound on any mbarrier wait
 
 // Device status word bits (latched; read by gsvr_sync_status).
 enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
@@ -168,5 +169,19 @@ size_t sort_hist_size(int n_max);
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
                              uint32_t *vals_out, const int *d_n, int n_max, int bits, const SortScratch &s,
                              cudaStream_t st, const int *key_rec = nullptr, int2 *tref = nullptr);
+
+struct TileSortScratch {
+    uint32_t *keys_alt;  // n_max keys
+    int2 *vals_alt;      // n_max (record, emit index) pairs
+    int *hist;           // sort_hist_size(n_max)
+    ScanScratch scan;
+};
+// Stable LSD radix sort of the n (= *d_n, at most n_max) tile keys in emit
+// order (low `bits` bits, ceil(bits / 9) passes): keys_out[pos] = the sorted
+// tile ids, tref[pos] = (key_rec[e], e) for the key from emit position e.  Every
+// buffer 16-byte aligned (else cudaErrorMisalignedAddress); a bulk copy that
+// does not complete within the wait bound sets ST_TIMEOUT in *status.
+cudaError_t sort_tile_keys(const uint32_t *keys, const int *key_rec, uint32_t *keys_out, int2 *tref, const int *d_n,
+                           int n_max, int bits, const TileSortScratch &s, unsigned *status, cudaStream_t st);
 
 }  // namespace gsvr
