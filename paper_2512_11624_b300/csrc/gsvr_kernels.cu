@@ -39,7 +39,6 @@ namespace gsvr {
 namespace {
 
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -1/2 log2(e)
-constexpr uint64_t kWaitLimitNs = 1000000000ull;            // 1 s bound on any mbarrier wait
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
