@@ -365,13 +365,16 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
     ffma_s, ex2_s, n_sm = gsvr.gsvr_alu_peaks(dev)
     ffma2_s = gsvr.gsvr_ffma2_peak(dev)
     kernels = {}
+    bwd_eval_per_step = kt["bwd_pairs_evaluated"] / max(kt["calls"]["bwd_eval"], 1)
+    evaluated = {"fwd_eval": tile_pairs_per_step, "bwd_eval": bwd_eval_per_step}
     for stg in ("fwd_eval", "bwd_eval"):
         avg_ms = kt["ms"][stg] / max(kt["calls"][stg], 1)
         achieved = useful_per_step / (avg_ms / 1e3) / 1e9
         peak = ffma_s / FP32_PER_PAIR[stg] / 1e9
         kernels[stg] = {"kernel": KERNEL_OF[stg], "pairs_per_launch": useful_per_step, "avg_launch_ms": avg_ms,
                         "fp32_per_pair": FP32_PER_PAIR[stg], "achieved": achieved, "peak": peak,
-                        "frac": achieved / peak}
+                        "frac": achieved / peak, "evaluated_pairs_per_launch": evaluated[stg],
+                        "useful_fraction": useful_per_step / max(evaluated[stg], 1)}
     dom = max(("fwd_eval", "bwd_eval"), key=lambda k: kt["ms"][k])
     traffic = profiled_traffic(KERNEL_OF[dom], "%s-%dx%d" % (name, shape.tile_h, shape.tile_w))
     roofline = dict(kernels[dom], bound="alu", unit="Gpair/s", traffic=traffic, ffma_lane_ops_per_s=ffma_s,

@@ -415,6 +415,8 @@ typedef struct gsvr_kernel_times {
     int64_t calls[GSVR_N_STAGES]; /* executions of each stage */
     int64_t pairs_evaluated;      /* pixel x record pairs the forward visited since the reset */
     int64_t kernel_launches;      /* kernels this library launched since the reset (all contexts) */
+    int64_t bwd_pairs_evaluated;  /* pixel x record pairs the backward evaluated since the reset
+                                     (each record over its in-cut box inside the tile) */
 } gsvr_kernel_times;
 
 /* Clear the stage timers and counters. */

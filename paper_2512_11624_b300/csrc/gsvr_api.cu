@@ -173,7 +173,7 @@ struct gsvr_ctx {
     double ms[GSVR_N_STAGES] = {};
     int64_t calls[GSVR_N_STAGES] = {};
     long long launches_at_reset = 0;
-    DBuf<unsigned long long> d_pairs_total, d_useful;
+    DBuf<unsigned long long> d_pairs_total, d_bwd_pairs_total, d_useful;
 
     ~gsvr_ctx() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -316,6 +316,7 @@ EvalArgs eval_args(gsvr_ctx *ctx, int grid_items) {
     e.mom = ctx->d_mom.p;
     e.counters = ctx->d_counters.p;
     e.pairs_total = ctx->d_pairs_total.p;
+    e.bwd_pairs_total = ctx->d_bwd_pairs_total.p;
     e.item_tile = ctx->d_item_tile.p;
     e.item_first = ctx->d_item_first.p;
     e.n_items = &ctx->d_counters.p->n_items;
@@ -543,8 +544,10 @@ gsvr_status gsvr_create(gsvr_ctx **out, int device, void *cuda_stream, const gsv
     if (e == cudaSuccess) e = ctx->d_counters.ensure(1);
     if (e == cudaSuccess) e = ctx->d_loss.ensure(1);
     if (e == cudaSuccess) e = ctx->d_pairs_total.ensure(1);
+    if (e == cudaSuccess) e = ctx->d_bwd_pairs_total.ensure(1);
     if (e == cudaSuccess) e = ctx->d_useful.ensure(1);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_pairs_total.p, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_bwd_pairs_total.p, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status.p, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters.p, 0, sizeof(Counters));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_loss.p, 0, sizeof(double));
@@ -1561,6 +1564,7 @@ gsvr_status gsvr_timing_reset(gsvr_ctx *ctx) {
         ctx->calls[k] = 0;
     }
     CK(cudaMemset(ctx->d_pairs_total.p, 0, sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->d_bwd_pairs_total.p, 0, sizeof(unsigned long long)));
     ctx->launches_at_reset = launch_count();
     return GSVR_OK;
 }
@@ -1570,13 +1574,15 @@ gsvr_status gsvr_get_kernel_times(gsvr_ctx *ctx, gsvr_kernel_times *out) {
     DeviceGuard g(ctx->device);
     CK(cudaStreamSynchronize(ctx->stream));
     fold_marks(ctx);
-    unsigned long long pt = 0;
+    unsigned long long pt = 0, pb = 0;
     CK(cudaMemcpy(&pt, ctx->d_pairs_total.p, sizeof(pt), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&pb, ctx->d_bwd_pairs_total.p, sizeof(pb), cudaMemcpyDeviceToHost));
     for (int k = 0; k < GSVR_N_STAGES; ++k) {
         out->ms[k] = ctx->ms[k];
         out->calls[k] = ctx->calls[k];
     }
     out->pairs_evaluated = (int64_t)pt;
+    out->bwd_pairs_evaluated = (int64_t)pb;
     out->kernel_launches = launch_count() - ctx->launches_at_reset;
     return GSVR_OK;
 }

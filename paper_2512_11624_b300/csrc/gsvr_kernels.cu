@@ -1019,108 +1019,216 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 }
 
 // ---------------------------------------------------------------- backward
-// One CTA per work item, thread per record (two records per thread, evaluated
-// side by side in the two lanes of packed f32x2 instructions).  The tile's
-// r_bar values (k_rbar_tiles) sit densely in shared memory (0 for pixels outside the sample),
-// each stored twice so one 64-bit load feeds both lanes, and are read as
-// broadcasts row by row.  Per row the record's row terms are formed once and
-// three row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q)); at the
-// end of the row they fold into the 6 moments sum g, g db, g da, g db^2,
-// g db da, g da^2, written to the record's key slot.
-__device__ __forceinline__ void bwd_row_fold(float m[6], float R0, float R1, float R2, float dy) {
-    m[0] += R0;
-    m[1] += R1;
-    m[2] = fmaf(R0, dy, m[2]);
-    m[3] += R2;
-    m[4] = fmaf(R1, dy, m[4]);
-    m[5] = fmaf(R0 * dy, dy, m[5]);
+// One CTA of kBwdThreads threads per work item (up to kItemRecs = 2 x
+// kBwdThreads records of one tile).  A record is evaluated only over its
+// in-cut box inside the tile: the rows and columns whose pixel centres can
+// satisfy the cut q + log2 w_n >= log2 cutoff_rel (the ellipse's axis-aligned
+// half-extents sqrt(4 kappa b / (4ab - c^2)), sqrt(4 kappa a / (4ab - c^2)) of
+// the form -q = a db^2 + c db da + b da^2 <= kappa, widened by a margin),
+// clipped to the rows and columns of the tile that hold sampled pixels.  Pairs
+// outside the box are below the cut, the pairs the method drops.  Rows go two
+// at a time through packed f32x2 instructions (lane x row r, lane y row r + 1;
+// a row past the box reads a tile row or the zero pad row, an exact extra
+// term), so a box is ceil(nr / 2) row pairs x nc columns.
+// The CTA orders its records by nc (a counting sort in shared memory, widest
+// first); thread t evaluates sorted records t and kItemRecs - 1 - t, so the
+// lanes of a warp run column loops of about equal length and every thread gets
+// one wide and one narrow box.  Which thread evaluates a record does not change
+// its moments, so the output does not depend on that order.  The tile's r_bar
+// (k_rbar_tiles; 0 off the sample) sits in shared memory with an odd row stride
+// of tile_w + 1 floats (lanes on different rows spread over the banks) and one
+// zero pad row.  Per row pair the row terms C da and B da^2 are formed once and
+// three packed row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q));
+// they fold into six packed moment sums (sum g, g db, g da, g db^2, g db da,
+// g da^2) whose two lanes are added at the end and written to the record's key
+// slot.
+constexpr int kBwdThreads = kItemRecs / 2;
+constexpr int kBwdClasses = 33;  // box widths 0 .. 32 columns
+
+struct __align__(16) BwdRec {  // a record as its evaluating thread reads it
+    float cb, ca, A, C;
+    float B;
+    int box;  // first row | rows << 8 | first column << 16 | columns << 24
+    int key;  // emit index of the (tile, record) key: the moment slot
+    int pad_;
+};
+
+__device__ __forceinline__ int warp_incl_scan_i(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
 }
 
-__global__ void __launch_bounds__(kThreads, 8) k_bwd_items(EvalArgs a) {
-    extern __shared__ float2 rb2[];  // tile_h x tile_w, each r_bar duplicated for the packed lanes
-    __shared__ int s_item;
-    __shared__ int row_lo[32], row_hi[32];  // sampled column range per tile row (lo > hi: none)
+// In-cut box of record R inside the tile (tile-local rows and columns, clipped
+// to the sampled range packed in sb), packed as BwdRec::box; 0 when empty.
+// Approximate reciprocal and square root suffice: the margin covers them.
+__device__ __forceinline__ int bwd_box(const Rec &R, float qcut, float bx, float by, int sb) {
+    const int rmin = sb & 255, rmax = (sb >> 8) & 255, cmin = (sb >> 16) & 255, cmax = (sb >> 24) & 255;
+    const float kap = R.b.z - qcut;  // -q <= kappa inside the cut
+    const float fa = -R.a.z, fb = -R.b.x, fc = -R.a.w;
+    const float D = 4.f * fa * fb - fc * fc;
+    if (!(kap >= 0.f && D > 0.f)) return 0;
+    const float s = 4.f * kap * __frcp_rn(D);
+    const float hx = __fsqrt_rn(s * fb) * 1.001f + 1e-2f;
+    const float hy = __fsqrt_rn(s * fa) * 1.001f + 1e-2f;
+    const int c0 = max(cmin, __float2int_ru(fminf(fmaxf(bx - hx, -1.f), 64.f)));
+    const int c1 = min(cmax, __float2int_rd(fminf(fmaxf(bx + hx, -1.f), 64.f)));
+    const int r0 = max(rmin, __float2int_ru(fminf(fmaxf(by - hy, -1.f), 64.f)));
+    const int r1 = min(rmax, __float2int_rd(fminf(fmaxf(by + hy, -1.f), 64.f)));
+    if (c0 > c1 || r0 > r1) return 0;
+    return r0 | ((r1 - r0 + 1) << 8) | (c0 << 16) | ((c1 - c0 + 1) << 24);
+}
+
+// Moments of one record over its box (see above); returns the pairs evaluated.
+__device__ __forceinline__ int bwd_eval_rec(const BwdRec &b, const float *rbs, int ts, float x0c, float y0c,
+                                            float4 *mom) {
+    const int r0 = b.box & 255, nr = (b.box >> 8) & 255, c0 = (b.box >> 16) & 255, ncol = (b.box >> 24) & 255;
+    float2 m0 = make_float2(0.f, 0.f), m1 = m0, m2 = m0, m3 = m0, m4 = m0, m5 = m0;
+    const float2 A2 = make_float2(b.A, b.A), C2 = make_float2(b.C, b.C), B2 = make_float2(b.B, b.B);
+    const float2 one = make_float2(1.f, 1.f);
+    const float colc = (x0c + (float)c0) - b.cb;
+    const float rowc = (y0c + (float)r0) - b.ca;
+    const float *rp = rbs + r0 * ts + c0;
+    for (int ri = 0; ri < nr; ri += 2, rp += 2 * ts) {
+        const float2 dy = make_float2(rowc + (float)ri, rowc + (float)(ri + 1));
+        const float2 cc = f2_mul(C2, dy), bb = f2_mul(f2_mul(B2, dy), dy);
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, dx = make_float2(colc, colc);
+#pragma unroll 2
+        for (int j = 0; j < ncol; ++j) {
+            const float2 g = make_float2(rp[j], rp[ts + j]);
+            const float2 q = f2_fma(f2_fma(A2, dx, cc), dx, bb);
+            const float2 e = f2_mul(g, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
+            const float2 ex = f2_mul(e, dx);
+            s0 = f2_add(s0, e);
+            s1 = f2_add(s1, ex);
+            s2 = f2_fma(ex, dx, s2);
+            dx = f2_add(dx, one);
+        }
+        m0 = f2_add(m0, s0);
+        m1 = f2_add(m1, s1);
+        m3 = f2_add(m3, s2);
+        m2 = f2_fma(s0, dy, m2);
+        m4 = f2_fma(s1, dy, m4);
+        m5 = f2_fma(f2_mul(s0, dy), dy, m5);
+    }
+    mom[2 * b.key] = make_float4(m0.x + m0.y, m1.x + m1.y, m2.x + m2.y, m3.x + m3.y);
+    mom[2 * b.key + 1] = make_float4(m4.x + m4.y, m5.x + m5.y, 0.f, 0.f);
+    return ((nr + 1) & ~1) * ncol;
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
+    extern __shared__ float rbs[];  // (tile_h + 1) x (tile_w + 1) r_bar values
+    __shared__ BwdRec srec[kItemRecs];
+    __shared__ int s_item, s_box;
+    __shared__ int cls_cnt[kBwdClasses], cls_start[kBwdClasses];
+    __shared__ unsigned long long s_eval;
+    const int tid = threadIdx.x;
     const int n_items = min(*a.n_items, a.cap_items);
-    const int tw = a.tile_w;
+    const int tw = a.tile_w, th = a.tile_h, ts = tw + 1;
+    unsigned long long evaluated = 0;
+    if (tid == 0) s_eval = 0ull;
+    for (int k = th * ts + tid; k < (th + 1) * ts; k += kBwdThreads) rbs[k] = 0.f;  // the pad row
     for (;;) {
-        __syncthreads();  // previous item's r_bar tile is free
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
+        __syncthreads();  // previous item's shared buffers are free
+        if (tid == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
+        if (tid < kBwdClasses) cls_cnt[tid] = 0;
         __syncthreads();
         if (s_item >= n_items) break;
         const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
         const int t = a.item_tile[i];
-        const int c = i - a.item_first[t];
         const int ps = a.tile_px_start[t], pe = a.tile_px_end[t];
-        const int rs = a.tile_rec_start[t] + c * kItemRecs;
-        const int re = min(rs + kItemRecs, a.tile_rec_end[t]);
-        if (ps >= pe || rs >= re) continue;
+        const int rs = a.tile_rec_start[t] + (i - a.item_first[t]) * kItemRecs;
+        const int nrec = min(kItemRecs, a.tile_rec_end[t] - rs);
+        if (ps >= pe || nrec <= 0) continue;
         const SliceDev &S = a.slices[a.tile_slice[t]];
-        const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
-        // this thread's two records: loads issued before the r_bar tile is built
-        const int r0 = rs + threadIdx.x;
-        const int r1 = r0 + kThreads;
-        const bool v0 = r0 < re, v1 = r1 < re;
-        const int2 refA = v0 ? a.tref[r0] : make_int2(0, 0);
-        const int2 refB = v1 ? a.tref[r1] : refA;
-        Rec A, B;
+        const TileGeom tg = tile_geom(S, t, tw, th);
+        // this thread's records rs + tid and rs + tid + kBwdThreads: loads
+        // issued before the r_bar tile is staged
+        const bool v0 = tid < nrec, v1 = tid + kBwdThreads < nrec;
+        int2 ref0 = make_int2(0, 0), ref1 = ref0;
+        Rec R0, R1;
         if (v0) {
-            A = a.rec[refA.x];
-            B = a.rec[refB.x];
+            ref0 = a.tref[rs + tid];
+            R0 = a.rec[ref0.x];
         }
-        // the tile's r_bar (dense, 0 off the sample: k_rbar_tiles) and per-row
-        // sampled column ranges (k_fwd_reduce), coalesced loads
+        if (v1) {
+            ref1 = a.tref[rs + tid + kBwdThreads];
+            R1 = a.rec[ref1.x];
+        }
         const float *rt = a.rbar_tile + (size_t)t * a.tile_px;
-        for (int k = threadIdx.x; k < a.tile_px; k += kThreads) {
-            const float g = __ldg(rt + k);
-            rb2[k] = make_float2(g, g);
+        for (int k = tid; k < th * tw; k += kBwdThreads) {
+            const int row = k / tw;
+            rbs[row * ts + (k - row * tw)] = __ldg(rt + k);
         }
-        if (threadIdx.x < a.tile_h) {
-            const short2 rr = a.row_rng[t * a.tile_h + threadIdx.x];
-            row_lo[threadIdx.x] = rr.x;
-            row_hi[threadIdx.x] = rr.y;
+        if (tid < 32) {  // the tile's rows and columns that hold samples (k_fwd_reduce)
+            const short2 rr = tid < th ? a.row_rng[t * th + tid] : make_short2(32, -1);
+            const bool has = rr.x <= rr.y;
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            const int lo = __reduce_min_sync(0xffffffffu, has ? (int)rr.x : 255);
+            const int hi = __reduce_max_sync(0xffffffffu, has ? (int)rr.y : 0);
+            if (tid == 0) s_box = (__ffs(m) - 1) | ((31 - __clz(m)) << 8) | (lo << 16) | (hi << 24);
         }
         __syncthreads();
-        if (!v0) continue;
-        float mA[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, mB[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const float colf0 = (float)tg.x0 - S.cx0;
-        // records A and B side by side in the two lanes of packed float32
-        // operations: per column one shared load, 7 packed FP32 and 2 ex2 for
-        // the two (pixel, record) pairs
-        const float2 az = make_float2(A.a.z, B.a.z);
-        const float2 one = make_float2(1.f, 1.f);
-        for (int row = 0; row < tg.rows; ++row) {
-            const int c0 = row_lo[row], c1 = row_hi[row];  // rows and columns without samples are skipped
-            if (c0 > c1) continue;
-            const float rowf = (float)(tg.y0 + row) - S.cy0;
-            const float dyA = rowf - A.a.y, dyB = rowf - B.a.y;
-            const float2 cc = make_float2(A.a.w * dyA, B.a.w * dyB);
-            const float2 bb = make_float2(A.b.x * dyA * dyA, B.b.x * dyB * dyB);
-            float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
-            const float2 *rrow = rb2 + row * tw;
-            const float colc = colf0 + (float)c0;
-            float2 dx = make_float2(colc - A.a.x, colc - B.a.x);  // advance by one pixel per column
-#pragma unroll 4
-            for (int col = c0; col <= c1; ++col) {
-                const float2 gg = rrow[col];
-                const float2 q = f2_fma(f2_fma(az, dx, cc), dx, bb);
-                const float2 e = f2_mul(gg, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
-                const float2 ex = f2_mul(e, dx);
-                s0 = f2_add(s0, e);
-                s1 = f2_add(s1, ex);
-                s2 = f2_fma(ex, dx, s2);
-                dx = f2_add(dx, one);
-            }
-            bwd_row_fold(mA, s0.x, s1.x, s2.x, dyA);
-            bwd_row_fold(mB, s0.y, s1.y, s2.y, dyB);
+        const float x0c = (float)tg.x0 - S.cx0, y0c = (float)tg.y0 - S.cy0;  // tile origin, slice-centred
+        const int sb = s_box;
+        int box0 = 0, box1 = 0, rank0 = 0, rank1 = 0;
+        if (v0) {
+            box0 = bwd_box(R0, a.qcut, R0.a.x - x0c, R0.a.y - y0c, sb);
+            rank0 = atomicAdd(&cls_cnt[box0 >> 24], 1);
         }
-        const int k0 = refA.y;
-        a.mom[2 * k0] = make_float4(mA[0], mA[1], mA[2], mA[3]);
-        a.mom[2 * k0 + 1] = make_float4(mA[4], mA[5], 0.f, 0.f);
         if (v1) {
-            const int k1 = refB.y;
-            a.mom[2 * k1] = make_float4(mB[0], mB[1], mB[2], mB[3]);
-            a.mom[2 * k1 + 1] = make_float4(mB[4], mB[5], 0.f, 0.f);
+            box1 = bwd_box(R1, a.qcut, R1.a.x - x0c, R1.a.y - y0c, sb);
+            rank1 = atomicAdd(&cls_cnt[box1 >> 24], 1);
         }
+        __syncthreads();
+        if (tid < 32) {  // class starts: widths 32 .. 1, then the empty boxes
+            const int ncl = 32 - tid;
+            const int c = cls_cnt[ncl];
+            const int inc = warp_incl_scan_i(c);
+            cls_start[ncl] = inc - c;
+            if (tid == 31) cls_start[0] = inc;
+        }
+        __syncthreads();
+        if (v0) {
+            BwdRec b;
+            b.cb = R0.a.x;
+            b.ca = R0.a.y;
+            b.A = R0.a.z;
+            b.C = R0.a.w;
+            b.B = R0.b.x;
+            b.box = box0;
+            b.key = ref0.y;
+            b.pad_ = 0;
+            srec[cls_start[box0 >> 24] + rank0] = b;
+        }
+        if (v1) {
+            BwdRec b;
+            b.cb = R1.a.x;
+            b.ca = R1.a.y;
+            b.A = R1.a.z;
+            b.C = R1.a.w;
+            b.B = R1.b.x;
+            b.box = box1;
+            b.key = ref1.y;
+            b.pad_ = 0;
+            srec[cls_start[box1 >> 24] + rank1] = b;
+        }
+        __syncthreads();
+        // one wide and one narrow box per thread (sorted positions t and nrec - 1 - t)
+        if (tid < nrec) evaluated += bwd_eval_rec(srec[tid], rbs, ts, x0c, y0c, a.mom);
+        const int u = nrec - 1 - tid;
+        if (u >= kBwdThreads) evaluated += bwd_eval_rec(srec[u], rbs, ts, x0c, y0c, a.mom);
+    }
+    if (a.bwd_pairs_total) {  // pairs this CTA evaluated: one atomic per CTA
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) evaluated += __shfl_down_sync(0xffffffffu, evaluated, o);
+        if ((tid & 31) == 0 && evaluated) atomicAdd(&s_eval, evaluated);
+        __syncthreads();
+        if (tid == 0 && s_eval) atomicAdd(a.bwd_pairs_total, s_eval);
     }
 }
 
@@ -2318,8 +2426,8 @@ int fwd_threads(int tile_w, int tile_h, int pxr) {
 int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
     if (backward) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kThreads,
-                                                      (size_t)tile_w * tile_h * sizeof(float2));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kBwdThreads,
+                                                      (size_t)(tile_h + 1) * (tile_w + 1) * sizeof(float));
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
@@ -2382,7 +2490,7 @@ void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st) {
         counted();
     }
     cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
-    k_bwd_items<<<eval_grid(a, true), kThreads, (size_t)a.tile_px * sizeof(float2), st>>>(a);
+    k_bwd_items<<<eval_grid(a, true), kBwdThreads, (size_t)(a.tile_h + 1) * (a.tile_w + 1) * sizeof(float), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,

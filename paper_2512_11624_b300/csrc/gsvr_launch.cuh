@@ -66,6 +66,7 @@ struct EvalArgs {
     float4 *mom;               // 2 per key (backward)
     Counters *counters;
     unsigned long long *pairs_total;  // running sum of visited pairs (timing)
+    unsigned long long *bwd_pairs_total;  // running sum of pairs the backward evaluated (null: not counted)
     unsigned long long *useful;       // count mode: pairs inside the cut
     float qcut;                       // count mode: log2(cutoff_rel)
     const int *item_tile;             // tile of each work item

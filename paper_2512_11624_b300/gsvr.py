@@ -72,7 +72,7 @@ class AdamCfg(C.Structure):
 
 class KernelTimes(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("calls", C.c_int64 * 8), ("pairs_evaluated", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("bwd_pairs_evaluated", C.c_int64)]
 
 
 class Tiling(C.Structure):
@@ -485,7 +485,8 @@ def gsvr_get_kernel_times(ctx):
     _check(ctx, lib.gsvr_get_kernel_times(ctx, C.byref(t)))
     return {"ms": {STAGES[k]: float(t.ms[k]) for k in range(7)},
             "calls": {STAGES[k]: int(t.calls[k]) for k in range(7)},
-            "pairs_evaluated": int(t.pairs_evaluated), "kernel_launches": int(t.kernel_launches)}
+            "pairs_evaluated": int(t.pairs_evaluated), "kernel_launches": int(t.kernel_launches),
+            "bwd_pairs_evaluated": int(t.bwd_pairs_evaluated)}
 
 
 def gsvr_count_pairs(ctx):
