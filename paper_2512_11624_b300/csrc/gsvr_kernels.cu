@@ -1028,16 +1028,16 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 // clipped to the rows and columns of the tile that hold sampled pixels.  Pairs
 // outside the box are below the cut, the pairs the method drops.  Rows go two
 // at a time through packed f32x2 instructions (lane x row r, lane y row r + 1;
-// a row past the box reads a tile row or the zero pad row, an exact extra
-// term), so a box is ceil(nr / 2) row pairs x nc columns.
+// a row past the box is a tile row, an exact extra term, or past the tile,
+// where r_bar reads 0), so a box is ceil(nr / 2) row pairs x nc columns.
 // The CTA orders its records by nc (a counting sort in shared memory, widest
 // first); thread t evaluates sorted records t and kItemRecs - 1 - t, so the
 // lanes of a warp run column loops of about equal length and every thread gets
 // one wide and one narrow box.  Which thread evaluates a record does not change
 // its moments, so the output does not depend on that order.  The tile's r_bar
-// (k_rbar_tiles; 0 off the sample) sits in shared memory with an odd row stride
-// of tile_w + 1 floats (lanes on different rows spread over the banks) and one
-// zero pad row.  Per row pair the row terms C da and B da^2 are formed once and
+// (k_rbar_tiles; 0 off the sample) sits in shared memory as pairs of
+// vertically adjacent values, one 64-bit load per packed step, with a row
+// stride of tile_w + 1 pairs (lanes on different rows spread over the banks).  Per row pair the row terms C da and B da^2 are formed once and
 // three packed row sums sum g, g db, g db^2 accumulate (g = r_bar exp2(q));
 // they fold into six packed moment sums (sum g, g db, g da, g db^2, g db da,
 // g da^2) whose two lanes are added at the end and written to the record's key
@@ -1084,7 +1084,8 @@ __device__ __forceinline__ int bwd_box(const Rec &R, float qcut, float bx, float
 }
 
 // Moments of one record over its box (see above); returns the pairs evaluated.
-__device__ __forceinline__ int bwd_eval_rec(const BwdRec &b, const float *rbs, int ts, float x0c, float y0c,
+// rb2[row * ts + col] = (r_bar[row][col], r_bar[row + 1][col]).
+__device__ __forceinline__ int bwd_eval_rec(const BwdRec &b, const float2 *rb2, int ts, float x0c, float y0c,
                                             float4 *mom) {
     const int r0 = b.box & 255, nr = (b.box >> 8) & 255, c0 = (b.box >> 16) & 255, ncol = (b.box >> 24) & 255;
     float2 m0 = make_float2(0.f, 0.f), m1 = m0, m2 = m0, m3 = m0, m4 = m0, m5 = m0;
@@ -1092,14 +1093,14 @@ __device__ __forceinline__ int bwd_eval_rec(const BwdRec &b, const float *rbs, i
     const float2 one = make_float2(1.f, 1.f);
     const float colc = (x0c + (float)c0) - b.cb;
     const float rowc = (y0c + (float)r0) - b.ca;
-    const float *rp = rbs + r0 * ts + c0;
+    const float2 *rp = rb2 + r0 * ts + c0;
     for (int ri = 0; ri < nr; ri += 2, rp += 2 * ts) {
         const float2 dy = make_float2(rowc + (float)ri, rowc + (float)(ri + 1));
         const float2 cc = f2_mul(C2, dy), bb = f2_mul(f2_mul(B2, dy), dy);
         float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, dx = make_float2(colc, colc);
 #pragma unroll 2
         for (int j = 0; j < ncol; ++j) {
-            const float2 g = make_float2(rp[j], rp[ts + j]);
+            const float2 g = rp[j];
             const float2 q = f2_fma(f2_fma(A2, dx, cc), dx, bb);
             const float2 e = f2_mul(g, make_float2(ex2_approx(q.x), ex2_approx(q.y)));
             const float2 ex = f2_mul(e, dx);
@@ -1121,7 +1122,7 @@ __device__ __forceinline__ int bwd_eval_rec(const BwdRec &b, const float *rbs, i
 }
 
 __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
-    extern __shared__ float rbs[];  // (tile_h + 1) x (tile_w + 1) r_bar values
+    extern __shared__ float2 rb2[];  // tile_h x (tile_w + 1) pairs (r_bar[row][col], r_bar[row + 1][col])
     __shared__ BwdRec srec[kItemRecs];
     __shared__ int s_item, s_box;
     __shared__ int cls_cnt[kBwdClasses], cls_start[kBwdClasses];
@@ -1131,7 +1132,6 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
     const int tw = a.tile_w, th = a.tile_h, ts = tw + 1;
     unsigned long long evaluated = 0;
     if (tid == 0) s_eval = 0ull;
-    for (int k = th * ts + tid; k < (th + 1) * ts; k += kBwdThreads) rbs[k] = 0.f;  // the pad row
     for (;;) {
         __syncthreads();  // previous item's shared buffers are free
         if (tid == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
@@ -1160,10 +1160,10 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
             R1 = a.rec[ref1.x];
         }
         const float *rt = a.rbar_tile + (size_t)t * a.tile_px;
-        for (int k = tid; k < th * tw; k += kBwdThreads) {
-            const int row = k / tw;
-            rbs[row * ts + (k - row * tw)] = __ldg(rt + k);
-        }
+        for (int row = tid >> 5; row < th; row += kBwdThreads / 32)  // a warp per row, lanes over columns
+            for (int col = tid & 31; col < tw; col += 32)
+                rb2[row * ts + col] =
+                    make_float2(__ldg(rt + row * tw + col), row + 1 < th ? __ldg(rt + (row + 1) * tw + col) : 0.f);
         if (tid < 32) {  // the tile's rows and columns that hold samples (k_fwd_reduce)
             const short2 rr = tid < th ? a.row_rng[t * th + tid] : make_short2(32, -1);
             const bool has = rr.x <= rr.y;
@@ -1219,9 +1219,9 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
         }
         __syncthreads();
         // one wide and one narrow box per thread (sorted positions t and nrec - 1 - t)
-        if (tid < nrec) evaluated += bwd_eval_rec(srec[tid], rbs, ts, x0c, y0c, a.mom);
+        if (tid < nrec) evaluated += bwd_eval_rec(srec[tid], rb2, ts, x0c, y0c, a.mom);
         const int u = nrec - 1 - tid;
-        if (u >= kBwdThreads) evaluated += bwd_eval_rec(srec[u], rbs, ts, x0c, y0c, a.mom);
+        if (u >= kBwdThreads) evaluated += bwd_eval_rec(srec[u], rb2, ts, x0c, y0c, a.mom);
     }
     if (a.bwd_pairs_total) {  // pairs this CTA evaluated: one atomic per CTA
 #pragma unroll
@@ -2427,7 +2427,7 @@ int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
     if (backward) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bwd_items, kBwdThreads,
-                                                      (size_t)(tile_h + 1) * (tile_w + 1) * sizeof(float));
+                                                      (size_t)tile_h * (tile_w + 1) * sizeof(float2));
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
@@ -2490,7 +2490,7 @@ void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st) {
         counted();
     }
     cudaMemsetAsync(&a.counters->work_bwd, 0, sizeof(int), st);
-    k_bwd_items<<<eval_grid(a, true), kBwdThreads, (size_t)(a.tile_h + 1) * (a.tile_w + 1) * sizeof(float), st>>>(a);
+    k_bwd_items<<<eval_grid(a, true), kBwdThreads, (size_t)a.tile_h * (a.tile_w + 1) * sizeof(float2), st>>>(a);
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
