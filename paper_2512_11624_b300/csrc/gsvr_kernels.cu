@@ -122,8 +122,27 @@ __device__ __forceinline__ bool slab_candidate(const float4 g0, const float4 g1,
     return mz * mz <= (rc2 * 1.001f + 1e-3f) * kzz + 1e-3f;
 }
 
-template <bool CENTRE>
-__device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const float mu[3], const SliceDev &S,
+// The slice-frame fields the gradient's record geometry reads (rec_geom
+// without the centre), staged in shared memory by the gradient epilogue; the
+// field names follow SliceDev, so rec_geom<false> takes either.
+struct SliceGeo {
+    float R[9], t[3];
+    float nz_h[3], nz_l[3];
+    float oz_h, oz_l;
+    float var[3];
+    float dx, dy;
+};
+constexpr int kSliceGeoWords = (int)(sizeof(SliceGeo) / 4);  // 25
+// Word offsets in SliceDev of the SliceGeo fields, in SliceGeo order.
+__device__ __forceinline__ int slice_geo_src(int e) {
+    return e < 12 ? e : (e < 18 ? e + 12 : e + 16);  // R, t | nz_h, nz_l | oz_h, oz_l, var, dx, dy
+}
+static_assert(offsetof(SliceDev, nz_h) == 24 * 4 && offsetof(SliceDev, oz_h) == 34 * 4 &&
+                  offsetof(SliceDev, var) == 36 * 4 && offsetof(SliceDev, dy) == 40 * 4,
+              "SliceGeo staging assumes the SliceDev layout");
+
+template <bool CENTRE, typename SL>
+__device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const float mu[3], const SL &S,
                                          float rc2, int norm_mode, RecGeom &G) {
     float zlo;
     const float zhi = ds_dot_sub(S.nz_h, S.nz_l, mu, S.oz_h, S.oz_l, zlo);
@@ -157,7 +176,7 @@ __device__ __forceinline__ bool rec_geom(const float4 g0, const float4 g1, const
         G.w0 = expf(g1.z - 0.5f * G.qz) * rsqrtf(G.Kzz * G.det2);
     else
         G.w0 = expf(-0.5f * G.qz);
-    if (CENTRE) {
+    if constexpr (CENTRE) {
         // centre = m_xy - K_xz,yz m_z / K_zz, in pixels: (u . mu - o) - (K_xz / K_zz) m_z / dx
         float xlo, ylo;
         const float xhi = ds_dot_sub(S.ux_h, S.ux_l, mu, S.ox_h, S.ox_l, xlo);
@@ -1297,9 +1316,10 @@ __global__ void __launch_bounds__(256) k_subject_counts(const int *__restrict__ 
 // a half-warp touch distinct slices when they add their slice-frame terms into
 // the block's shared-memory accumulators; the 11 Gaussian partials are then
 // reduced with half-warp shuffles.
+template <typename SLT>
 __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const float4 g0, const float4 g1,
                                              const float mu[3], const float Sg[9], float gmu[3], float GS[6],
-                                             float &gc, float &glog, float *pacc, int w0) {
+                                             float &gc, float &glog, float *pacc, int w0, const SLT *slices) {
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     const int k_end = min(a.key_off[r + 1], a.cap_keys);
     for (int k = max(a.key_off[r], 0); k < k_end; ++k) {
@@ -1312,8 +1332,8 @@ __device__ __forceinline__ void record_chain(const GradArgs &a, int r, const flo
         Syy += v.y;
     }
     if (S0 == 0.f && Sx == 0.f && Sy == 0.f && Sxx == 0.f && Sxy == 0.f && Syy == 0.f) return;
-    const int i = __float_as_int(a.rec[r].b.w);
-    const SliceDev &SL = a.slices[i];
+    const int i = a.cand[r].y;  // the record's slice
+    const SLT &SL = slices[i - w0];
     RecGeom G;
     if (!rec_geom<false>(g0, g1, mu, SL, a.rc2, a.norm_mode, G)) return;
     const float dx = SL.dx, dy = SL.dy;
@@ -1480,6 +1500,17 @@ __global__ void __launch_bounds__(256, 3) k_gauss_grad(GradArgs a) {
     if (pacc) {
         for (int e = tid; e < (w1 - w0) * 12; e += blockDim.x) pacc[e] = 0.f;
     }
+    // the window's slice geometry in shared memory when it was given room
+    SliceGeo *geo = pacc && a.smem_geo ? reinterpret_cast<SliceGeo *>(pacc_s + 12 * a.smem_slices) : nullptr;
+    if (geo) {
+        const float *src = reinterpret_cast<const float *>(a.slices + w0);
+        float *dst = reinterpret_cast<float *>(geo);
+        constexpr int SW = (int)(sizeof(SliceDev) / 4);
+        for (int e = tid; e < (w1 - w0) * kSliceGeoWords; e += blockDim.x) {
+            const int sl = e / kSliceGeoWords, f = e - sl * kSliceGeoWords;
+            dst[e] = src[sl * SW + slice_geo_src(f)];
+        }
+    }
     __syncthreads();
     auto ro = [&](int j) { return min(a.rec_off[j], a.cap_rec); };
     const int R0 = ro(j0), R1 = ro(j1);
@@ -1506,7 +1537,8 @@ __global__ void __launch_bounds__(256, 3) k_gauss_grad(GradArgs a) {
             const float mu[3] = {a.theta[j], a.theta[N + j], a.theta[2 * N + j]};
             const float4 g0 = a.gpre[2 * j], g1 = a.gpre[2 * j + 1];
             const float Sg[9] = {g0.x, g0.w, g1.x, g0.w, g0.y, g1.y, g1.x, g1.y, g0.z};
-            record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0);
+            if (geo) record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0, geo);
+            else record_chain(a, r, g0, g1, mu, Sg, v, v + 3, v[9], v[10], pacc, w0, a.slices + w0);
         }
         // segmented inclusive scan: lanes of one Gaussian are contiguous
 #pragma unroll
@@ -2533,7 +2565,9 @@ void launch_gauss_grad(const GradArgs &a, cudaStream_t st) {
         }
     }
     g.smem_slices = std::min(widest, a.smem_slices);
-    const size_t smem = (size_t)g.smem_slices * 12 * sizeof(float);
+    // the slice geometry joins the accumulators when both fit in 96 KB
+    g.smem_geo = (size_t)g.smem_slices * (12 + kSliceGeoWords) * sizeof(float) <= 96 * 1024;
+    const size_t smem = (size_t)g.smem_slices * (12 + (g.smem_geo ? kSliceGeoWords : 0)) * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_gauss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // Gaussians without records get no epilogue: their gradient is this zero
     cudaMemsetAsync(g.grad, 0, sizeof(float) * 11 * (size_t)a.N, st);

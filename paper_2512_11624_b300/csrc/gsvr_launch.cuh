@@ -112,6 +112,7 @@ struct GradArgs {
     const int *gauss_subject;  // subject of each Gaussian (null: one subject)
     const int *subj_slice_first;
     int smem_slices;           // slice window that fits the shared accumulators (0: none)
+    int smem_geo;              // the window's slice geometry is staged in shared memory too (set by the launcher)
     // host copies of the subject tables (n_subj + 1 entries each), used by the
     // launcher to size the shared window
     const int64_t *h_gauss_first;
