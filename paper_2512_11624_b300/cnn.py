@@ -186,15 +186,31 @@ def aux_for_stacks(stacks):
     return np.concatenate(rows).astype(np.float32)
 
 
-def pose_target(motion):
-    """Network target of a per-slice motion (r rad, tau mm): (r, tau / 10)."""
+def _frames(aux):
+    """Per-slice nominal rotations R0 [n][3][3] from the auxiliary input rows."""
+    return np.asarray(aux, np.float64)[:, :9].reshape(-1, 3, 3)
+
+
+def pose_target(motion, aux):
+    """Network target of a per-slice motion (r rad, tau mm), expressed in the
+    slice's own frame: r_s = R0^T r and tau_s = R0^T tau (R_i = Rod(r) R0 =
+    R0 Rod(r_s), so r_s is the rotation applied in slice axes: its z part turns
+    the image in plane, its x, y parts tilt it; tau_s is the in-plane shift and
+    the shift along the normal), as (r_s, tau_s / 10)."""
     m = np.asarray(motion, np.float64)
-    return np.concatenate([m[:, :3], m[:, 3:] / 10.0], axis=1).astype(np.float32)
+    R0 = _frames(aux)
+    r_s = np.einsum("nji,nj->ni", R0, m[:, :3])
+    t_s = np.einsum("nji,nj->ni", R0, m[:, 3:])
+    return np.concatenate([r_s, t_s / 10.0], axis=1).astype(np.float32)
 
 
-def pose_from_output(out):
+def pose_from_output(out, aux):
+    """World-frame motion (r, tau) of network outputs (the inverse of pose_target)."""
     o = np.asarray(out, np.float64)
-    return np.concatenate([o[:, :3], o[:, 3:] * 10.0], axis=1)
+    R0 = _frames(aux)
+    r = np.einsum("nij,nj->ni", R0, o[:, :3])
+    t = np.einsum("nij,nj->ni", R0, o[:, 3:] * 10.0)
+    return np.concatenate([r, t], axis=1)
 
 
 def normalise_slices(img):
@@ -321,7 +337,7 @@ def make_training_set(n_phantoms, motions_per_phantom=2, n_slices=20, max_deg=20
                 keep = content_fraction(img) > min_content
                 xs.append(normalise_slices(img[keep]))
                 auxs.append(aux_all[keep])
-                tgts.append(torch.from_numpy(pose_target(motion)).to(img.device)[keep])
+                tgts.append(torch.from_numpy(pose_target(motion, ren.aux)).to(img.device)[keep])
             if log and (p + 1) % max(1, n_phantoms // 10) == 0:
                 log("rendered %d / %d phantoms, %d slices" % (p + 1, n_phantoms, sum(x.shape[0] for x in xs)))
     finally:
@@ -375,3 +391,31 @@ def predict(net, X, A, batch=256):
 def evaluate_loss(net, X, A, Y, batch=256):
     out = predict(net, X, A, batch)
     return float(((out - Y) ** 2).mean().item())
+
+
+def _rod(r):
+    """Rotation matrices of axis-angle vectors r [n][3] (Rodrigues)."""
+    r = np.asarray(r, np.float64)
+    th = np.linalg.norm(r, axis=1)
+    k = np.where(th[:, None] > 1e-12, r / np.maximum(th, 1e-300)[:, None], 0.0)
+    K = np.zeros((r.shape[0], 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -k[:, 2], k[:, 1], -k[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = k[:, 2], -k[:, 1], k[:, 0]
+    s, c = np.sin(th)[:, None, None], np.cos(th)[:, None, None]
+    return np.eye(3)[None] + s * K + (1.0 - c) * (K @ K)
+
+
+def pose_errors_on_set(net, X, A, Y, batch=256):
+    """Per-slice pose errors of the network and of the nominal (zero-motion)
+    start on a rendered set (targets as pose_target): rotation angle of
+    Rod(r_pred)^T Rod(r_true) in degrees and translation error in mm, both
+    frame independent.  Returns a dict of arrays."""
+    out = predict(net, X, A, batch).double().cpu().numpy()
+    y = Y.double().cpu().numpy()
+    Rp, Rt = _rod(out[:, :3]), _rod(y[:, :3])
+    cosang = np.clip((np.einsum("nij,nij->n", Rp, Rt) - 1.0) / 2.0, -1.0, 1.0)
+    return {"net_rot_deg": np.degrees(np.arccos(cosang)),
+            "net_trans_mm": 10.0 * np.linalg.norm(out[:, 3:] - y[:, 3:], axis=1),
+            "nominal_rot_deg": np.degrees(np.linalg.norm(y[:, :3], axis=1)),
+            "nominal_trans_mm": 10.0 * np.linalg.norm(y[:, 3:], axis=1)}
+

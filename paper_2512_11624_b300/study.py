@@ -241,8 +241,9 @@ def run_learned(args):
         lo = (H - cnn.IMAGE) // 2
         crop = I[:, lo:lo + cnn.IMAGE, lo:lo + cnn.IMAGE].contiguous()
         content = cnn.content_fraction(crop) > 0.02
-        aux = torch.from_numpy(cnn.aux_for_stacks(case["stacks"])).cuda()
-        pred = cnn.pose_from_output(cnn.predict(net, cnn.normalise_slices(crop), aux).cpu().numpy())
+        aux_h = cnn.aux_for_stacks(case["stacks"])
+        aux = torch.from_numpy(aux_h).cuda()
+        pred = cnn.pose_from_output(cnn.predict(net, cnn.normalise_slices(crop), aux).cpu().numpy(), aux_h)
         # fallback test against the template
         tc = {"stacks": case["stacks"], "N": tmpl_N,
               "theta": np.concatenate([tmpl_theta, np.zeros(6 * M)]).astype(np.float32), "I": case["I"],
@@ -669,6 +670,37 @@ def run_topk_step(args):
     ctx.close()
 
 
+def run_posefit(args):
+    """Train the pose network and report its pose errors against the nominal
+    start on held-out rendered slices (phantom seeds disjoint from training) at
+    the wide and the fetal motion ranges."""
+    import torch
+    from . import cnn
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, flush=True)  # noqa: E731
+    t0 = time.time()
+    X, A, Y = cnn.make_training_set(args.phantoms, motions_per_phantom=args.motions, seed=args.seed,
+                                    workers=args.workers, log=log)
+    t_data = time.time() - t0
+    net = cnn.PoseNet(max_batch=args.batch, seed=args.seed)
+    hist = cnn.train(net, X, A, Y, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=args.seed, log=log)
+    out = {"training": {"slices": int(X.shape[0]), "phantoms": args.phantoms, "data_s": t_data, "epochs": hist},
+           "held_out": {}}
+    del X, A, Y
+    for deg, mm in ((20.0, 10.0), (5.0, 3.0)):
+        Xv, Av, Yv = cnn.make_training_set(args.eval_phantoms, motions_per_phantom=1, seed=args.seed + 1000,
+                                           max_deg=deg, max_mm=mm, workers=args.workers)
+        e = cnn.pose_errors_on_set(net, Xv, Av, Yv)
+        out["held_out"]["%g deg / %g mm" % (deg, mm)] = {
+            "slices": int(Xv.shape[0]), **{k: [float(np.mean(v)), float(np.median(v))] for k, v in e.items()}}
+        log(json.dumps({k: out["held_out"]["%g deg / %g mm" % (deg, mm)][k] for k in e}))
+    net.close()
+    print(json.dumps(out))
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(out, f, indent=1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -695,6 +727,16 @@ def main():
     lr.add_argument("--eval-every", type=int, default=50)
     lr.add_argument("--workers", type=int, default=8)
     lr.add_argument("--out", default="")
+    pf = sub.add_parser("posefit")
+    pf.add_argument("--phantoms", type=int, default=2000)
+    pf.add_argument("--motions", type=int, default=2)
+    pf.add_argument("--epochs", type=int, default=20)
+    pf.add_argument("--batch", type=int, default=256)
+    pf.add_argument("--lr", type=float, default=1e-3)
+    pf.add_argument("--seed", type=int, default=0)
+    pf.add_argument("--eval-phantoms", type=int, default=40)
+    pf.add_argument("--workers", type=int, default=8)
+    pf.add_argument("--out", default="")
     cb = sub.add_parser("cnnbench")
     cb.add_argument("--batch", type=int, default=256)
     cb.add_argument("--steps", type=int, default=50)
@@ -757,6 +799,8 @@ def main():
         run_batched(args)
     elif args.cmd == "learned":
         run_learned(args)
+    elif args.cmd == "posefit":
+        run_posefit(args)
 
 
 if __name__ == "__main__":
