@@ -163,7 +163,9 @@ gsvr_status gsvr_set_frozen(gsvr_ctx *ctx, const uint8_t *frozen);
 
 /* Sample = the listed global pixels (int32, `mem`, any order; duplicates count
  * once; unmasked pixels are dropped).  n < 0: every masked pixel.
- * w_p = 1 / (number of distinct usable pixels listed). */
+ * w_p = 1 / (number of distinct usable pixels listed).  Indices are checked on
+ * the device (host and device lists alike): an index outside [0, pixels) is
+ * skipped and makes the next gsvr_sync_status return GSVR_ERR_INVALID_ARG. */
 gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, int32_t mem);
 
 /* Sample n masked pixels uniformly without replacement on the device: the

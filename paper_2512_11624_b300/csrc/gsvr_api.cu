@@ -899,9 +899,7 @@ gsvr_status gsvr_set_pixel_sample(gsvr_ctx *ctx, const int32_t *idx, int64_t n, 
     DeviceGuard g(ctx->device);
     cudaStream_t st = ctx->stream;
     const int32_t *didx = idx;
-    if (mem == GSVR_MEM_HOST && n > 0) {
-        for (int64_t k = 0; k < n; ++k)
-            if (idx[k] < 0 || idx[k] >= ctx->P) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range");
+    if (mem == GSVR_MEM_HOST && n > 0) {  // (indices are range-checked on the device, as device lists are)
         CK(ctx->d_idx.ensure((size_t)n));
         CK(cudaMemcpyAsync(ctx->d_idx.p, idx, sizeof(int) * n, cudaMemcpyHostToDevice, st));
         didx = ctx->d_idx.p;
@@ -1530,7 +1528,7 @@ gsvr_status gsvr_sync_status(gsvr_ctx *ctx) {
     if (s & ST_CAPACITY) return fail(ctx, GSVR_ERR_CAPACITY, "record or key capacity exceeded");
     if (s & ST_NONFINITE) return fail(ctx, GSVR_ERR_NONFINITE, "non-finite parameter, pose or loss");
     if (s & ST_TIMEOUT) return fail(ctx, GSVR_ERR_TIMEOUT, "a bounded device wait ran out");
-    if (s & ST_INDEX) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range in a device sample");
+    if (s & ST_INDEX) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range in a sample list");
     return GSVR_OK;
 }
 

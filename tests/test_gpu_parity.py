@@ -253,9 +253,17 @@ def test_nonfinite_and_invalid_arguments(G):
     with pytest.raises(G.GsvrError) as ei:
         G.gsvr_sample_pixels(ctx.ctx, 10 ** 9, 0)
     assert ei.value.status == 1
-    with pytest.raises(G.GsvrError) as ei:
-        G.gsvr_set_pixel_sample(ctx.ctx, np.array([-1, 3], np.int32))
-    assert ei.value.status == 1
+    # out-of-range list entries (host or device list) are skipped on the device
+    # and reported by the next status read; the context stays usable
+    import torch
+    for bad in (np.array([-1, 3], np.int32), torch.tensor([3, 10 ** 6], dtype=torch.int32, device="cuda")):
+        G.gsvr_set_pixel_sample(ctx.ctx, bad)
+        with pytest.raises(G.GsvrError) as ei:
+            G.gsvr_sync_status(ctx.ctx)
+        assert ei.value.status == 1 and "out of range" in str(ei.value)
+    G.gsvr_set_pixel_sample(ctx.ctx, np.array([3, 4], np.int32))
+    ctx.forward()
+    G.gsvr_sync_status(ctx.ctx)
     with pytest.raises(G.GsvrError):
         G.gsvr_set_stacks(ctx.ctx, [dict(case["stacks"][0], n_slices=0)])
     ctx.close()
