@@ -944,8 +944,7 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
 // returns dL/dmodel and the pixel's derivatives in log sigma_i and log omega_i
 // (slw null: sigma = omega = 1 without the log term).
 struct SlwTerms {
-    float pred, dLdm, gsig, gomg;
-    double loss;
+    float pred, dLdm, gsig, gomg, loss;
 };
 __device__ __forceinline__ SlwTerms slw_terms(const float *slw, int M, int i, int l1, float w, float model, float I) {
     const float sig = slw ? expf(slw[i]) : 1.f, lw = slw ? slw[M + i] : 0.f, iw = slw ? expf(-lw) : 1.f;
@@ -954,7 +953,7 @@ __device__ __forceinline__ SlwTerms slw_terms(const float *slw, int M, int i, in
     const float r = t.pred - I;
     const float l = l1 ? w * fabsf(r) : w * r * r;
     const float dl = l1 ? w * (float)((r > 0.f) - (r < 0.f)) : 2.f * w * r;
-    t.loss = (double)l * (double)iw + (slw ? (double)w * (double)lw : 0.0);
+    t.loss = l * iw + (slw ? w * lw : 0.f);
     t.dLdm = sig * dl * iw;
     t.gsig = dl * iw * t.pred;
     t.gomg = w - l * iw;
@@ -980,7 +979,10 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
     }
     __syncthreads();
     const int s = ps + threadIdx.x;
-    double l = 0.0, gs = 0.0, go = 0.0;
+    // per-pixel terms in float32, summed over the warp in float32 (fixed
+    // order) and over the block's warps in float64: this GPU's float64 rate is
+    // a small fraction of its float32 rate
+    float l = 0.f, gs = 0.f, go = 0.f;
     if (s < pe) {
         const SliceDev &S = a.slices[a.tile_slice[t]];
         const TileGeom tg = tile_geom(S, t, a.tile_w, a.tile_h);
@@ -1001,8 +1003,8 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         atomicMin(&rlo[r0 - tg.y0], loc - r0 * S.W - tg.x0);
         atomicMax(&rhi[r0 - tg.y0], loc - r0 * S.W - tg.x0);
         l = st.loss;
-        gs = (double)st.gsig;
-        go = (double)st.gomg;
+        gs = st.gsig;
+        go = st.gomg;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1011,9 +1013,9 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
         go += __shfl_down_sync(0xffffffffu, go, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5] = l;
-        red_s[threadIdx.x >> 5] = gs;
-        red_o[threadIdx.x >> 5] = go;
+        red[threadIdx.x >> 5] = (double)l;
+        red_s[threadIdx.x >> 5] = (double)gs;
+        red_o[threadIdx.x >> 5] = (double)go;
     }
     __syncthreads();
     if (a.row_rng && threadIdx.x < a.tile_h)
@@ -1030,10 +1032,6 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
             a.slw_tile[2 * t] = ss;
             a.slw_tile[2 * t + 1] = so;
         }
-        const unsigned long long np =
-            (unsigned long long)(pe - ps) * (unsigned long long)(a.tile_rec_end[t] - a.tile_rec_start[t]);
-        atomicAdd(&a.counters->pairs, np);
-        if (a.pairs_total) atomicAdd(a.pairs_total, np);
     }
 }
 
@@ -1265,21 +1263,43 @@ __global__ void k_rbar_tiles(EvalArgs a, int cap) {
 }
 
 // Per-subject losses: block k sums its subject's tiles in tile order.
+// Also counts, when pc.pairs is given, the tile pairs of the forward (sampled
+// pixels x records of each tile), one atomic per subject.
 __global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, int n, const int *tile_first,
-                                                      double *subj_loss) {
+                                                      double *subj_loss, PairCount pc) {
     __shared__ double red[32];
+    __shared__ unsigned long long redp[32];
     const int k = blockIdx.x;
     const int t0 = tile_first ? tile_first[k] : 0, t1 = tile_first ? tile_first[k + 1] : n;
     double s = 0.0;
-    for (int t = t0 + threadIdx.x; t < t1; t += 1024) s += tile_loss[t];
+    unsigned long long np = 0ull;
+    for (int t = t0 + threadIdx.x; t < t1; t += 1024) {
+        s += tile_loss[t];
+        if (pc.pairs)
+            np += (unsigned long long)max(pc.tpe[t] - pc.tps[t], 0) * (unsigned long long)max(pc.tre[t] - pc.trs[t], 0);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        np += __shfl_down_sync(0xffffffffu, np, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        redp[threadIdx.x >> 5] = np;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int w = 0; w < 32; ++w) tot += red[w];
+        unsigned long long ptot = 0ull;
+        for (int w = 0; w < 32; ++w) {
+            tot += red[w];
+            ptot += redp[w];
+        }
         subj_loss[k] = tot;
+        if (pc.pairs) {
+            atomicAdd(pc.pairs, ptot);
+            if (pc.pairs_total) atomicAdd(pc.pairs_total, ptot);
+        }
     }
 }
 
@@ -2528,8 +2548,8 @@ void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st) {
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
-                        double *loss, unsigned *status, cudaStream_t st) {
-    k_loss_reduce<<<std::max(n_subj, 1), 1024, 0, st>>>(tile_loss, n_tiles, tile_first, subj_loss);
+                        double *loss, unsigned *status, cudaStream_t st, const PairCount &pc) {
+    k_loss_reduce<<<std::max(n_subj, 1), 1024, 0, st>>>(tile_loss, n_tiles, tile_first, subj_loss, pc);
     k_loss_total<<<1, 1, 0, st>>>(subj_loss, std::max(n_subj, 1), loss, status);
     counted(2);
 }

@@ -139,10 +139,16 @@ long long launch_count();  // kernels launched by this library so far
 void note_launches(int n); // count kernels launched from other translation units
 // Dense r_bar tiles (from the per-pixel r_bar of the cap_px sample slots), then the tile adjoint.
 void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st);
+// Tile pairs of a forward (sampled pixels x records per tile), counted into
+// *pairs and *pairs_total (either may be null) by the loss reduction.
+struct PairCount {
+    const int *tps, *tpe, *trs, *tre;  // tile pixel and record ranges
+    unsigned long long *pairs, *pairs_total;
+};
 // Per-subject losses (subject k owns tiles [tile_first[k], tile_first[k+1]), summed in
 // tile order) and their total; tile_first null = one subject.
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
-                        double *loss, unsigned *status, cudaStream_t st);
+                        double *loss, unsigned *status, cudaStream_t st, const PairCount &pc = PairCount{});
 // Sampled pixels per subject: cnt[k] = sum of the subject's tile pixel counts.
 void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first, int n_subj, int *cnt,
                            cudaStream_t st);
