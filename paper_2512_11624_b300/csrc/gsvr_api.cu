@@ -1280,6 +1280,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     }
     KeyArgs k{};
     k.rec = ctx->d_rec.p;
+    k.cand = ctx->d_cand.p;
     k.rec_tiles = ctx->d_rec_tiles.p;
     k.rec_nkeys = ctx->d_rec_nkeys.p;
     k.rec_mask = ctx->d_rec_mask.p;

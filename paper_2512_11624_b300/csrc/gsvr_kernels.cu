@@ -580,8 +580,7 @@ __global__ void k_key_emit(KeyArgs a) {
     const int k0 = a.key_off[r];
     const int k1 = k0 + a.rec_nkeys[r];
     if (k1 <= k0) return;
-    const Rec R = a.rec[r];
-    const int i = __float_as_int(R.b.w);
+    const int i = a.cand[r].y;  // the record's slice (the full record only when its tiles are tested again)
     const SliceDev &S = a.slices[i];
     const int2 tb = a.rec_tiles[r];
     const int tx0 = tb.x & 0xffff, tx1 = tb.x >> 16, ty0 = tb.y & 0xffff, ty1 = tb.y >> 16;
@@ -602,6 +601,7 @@ __global__ void k_key_emit(KeyArgs a) {
             ++k;
         }
     } else {
+        const Rec R = a.rec[r];
         const float2 iAB = rec_inv_ab(R);
         for (int ty = ty0; ty <= ty1 && k < k1; ++ty)
             for (int tx = tx0; tx <= tx1 && k < k1; ++tx) {

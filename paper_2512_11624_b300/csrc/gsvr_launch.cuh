@@ -31,6 +31,7 @@ struct BinArgs {
 
 struct KeyArgs {
     const Rec *rec;
+    const int2 *cand;          // (Gaussian, slice) per record
     const int2 *rec_tiles;
     const int *rec_nkeys;      // keys per record (from the record pass)
     const unsigned *rec_mask;  // live-tile bits of the record pass (0: test again)

@@ -321,6 +321,7 @@ extern "C" gsvr_status gsvr_forward_noalloc(int device, void *cuda_stream, int32
     NA_CK(scan_exclusive(d_rec_nkeys, d_key_off, &d_cnt->n_rec, 0, cap_rec, &d_cnt->n_keys, scs, st));
     KeyArgs k{};
     k.rec = d_rec;
+    k.cand = d_cand;
     k.rec_tiles = d_rec_tiles;
     k.rec_nkeys = d_rec_nkeys;
     k.rec_mask = d_rec_mask;
