@@ -1312,7 +1312,7 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
         if (si) return si;
     }
     launch_items(ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_tile_rec_start.p, ctx->d_tile_rec_end.p,
-                 ctx->n_tiles, ctx->d_item_cnt.p, nullptr, nullptr, 0, 0, st);
+                 ctx->n_tiles, ctx->d_item_cnt.p, nullptr, nullptr, 0, 0, st, &cnt->pairs, ctx->d_pairs_total.p);
     CK(scan_exclusive(ctx->d_item_cnt.p, ctx->d_item_first.p, nullptr, ctx->n_tiles, ctx->n_tiles, &cnt->n_items,
                       scan_scratch(ctx), st));
     launch_items(nullptr, nullptr, nullptr, nullptr, ctx->n_tiles, nullptr, ctx->d_item_first.p, ctx->d_item_tile.p,
@@ -1334,10 +1334,8 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     launch_forward(e, st);
     stage_end(ctx, GSVR_STAGE_FWD_EVAL);
     if (ctx->slw_on) launch_slw_slices(ctx->d_slw_tile.p, ctx->d_slices.p, M, ctx->d_slw_gacc.p, st);
-    const PairCount pc{ctx->d_tile_px_start.p, ctx->d_tile_px_end.p, ctx->d_tile_rec_start.p, ctx->d_tile_rec_end.p,
-                       &ctx->d_counters.p->pairs, ctx->d_pairs_total.p};
     launch_loss_reduce(ctx->d_tile_loss.p, ctx->n_tiles, ctx->d_subj_tile_first.p, ctx->n_subj, ctx->d_subj_loss.p,
-                       ctx->d_loss.p, ctx->d_status.p, st, pc);
+                       ctx->d_loss.p, ctx->d_status.p, st);
     if (ctx->lambda_reg > 0.f) launch_scale_reg_loss(ctx->d_theta.p, N, ctx->lambda_reg, ctx->s_target, ctx->d_loss.p, st);
     if (ctx->slw_on) launch_slw_grad(ctx->d_slw_gacc.p, 2 * M, ctx->d_slw_grad.p, st);
     CK(cudaGetLastError());

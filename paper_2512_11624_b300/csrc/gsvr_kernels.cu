@@ -650,13 +650,25 @@ __global__ void k_tile_rec_ranges(const uint32_t *__restrict__ keys, const int *
 // The sorted (tile, record) list is cut into work items of at most kItemRecs
 // records of one tile (a tile with pixels and no records gets one empty item),
 // so the evaluation grids are balanced however unevenly records fall on tiles.
+// Also counts the forward's tile pairs (sampled pixels x records of each
+// tile) into *pairs and *pairs_total when given: one atomic per warp.
 __global__ void k_item_count(const int *__restrict__ tps, const int *__restrict__ tpe,
                              const int *__restrict__ trs, const int *__restrict__ tre, int n_tiles,
-                             int *__restrict__ cnt) {
+                             int *__restrict__ cnt, unsigned long long *pairs, unsigned long long *pairs_total) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const int npx = tpe[t] - tps[t], nrec = tre[t] - trs[t];
-    cnt[t] = npx > 0 ? max(1, (nrec + kItemRecs - 1) / kItemRecs) : 0;
+    unsigned long long np = 0ull;
+    if (t < n_tiles) {
+        const int npx = tpe[t] - tps[t], nrec = tre[t] - trs[t];
+        cnt[t] = npx > 0 ? max(1, (nrec + kItemRecs - 1) / kItemRecs) : 0;
+        np = (unsigned long long)max(npx, 0) * (unsigned long long)max(nrec, 0);
+    }
+    if (!pairs) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
+    if ((threadIdx.x & 31) == 0 && np) {
+        atomicAdd(pairs, np);
+        if (pairs_total) atomicAdd(pairs_total, np);
+    }
 }
 
 __global__ void k_item_fill(const int *__restrict__ first, int n_tiles, int *__restrict__ item_tile, int cap) {
@@ -1263,43 +1275,21 @@ __global__ void k_rbar_tiles(EvalArgs a, int cap) {
 }
 
 // Per-subject losses: block k sums its subject's tiles in tile order.
-// Also counts, when pc.pairs is given, the tile pairs of the forward (sampled
-// pixels x records of each tile), one atomic per subject.
 __global__ void __launch_bounds__(1024) k_loss_reduce(const double *tile_loss, int n, const int *tile_first,
-                                                      double *subj_loss, PairCount pc) {
+                                                      double *subj_loss) {
     __shared__ double red[32];
-    __shared__ unsigned long long redp[32];
     const int k = blockIdx.x;
     const int t0 = tile_first ? tile_first[k] : 0, t1 = tile_first ? tile_first[k + 1] : n;
     double s = 0.0;
-    unsigned long long np = 0ull;
-    for (int t = t0 + threadIdx.x; t < t1; t += 1024) {
-        s += tile_loss[t];
-        if (pc.pairs)
-            np += (unsigned long long)max(pc.tpe[t] - pc.tps[t], 0) * (unsigned long long)max(pc.tre[t] - pc.trs[t], 0);
-    }
+    for (int t = t0 + threadIdx.x; t < t1; t += 1024) s += tile_loss[t];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_down_sync(0xffffffffu, s, o);
-        np += __shfl_down_sync(0xffffffffu, np, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5] = s;
-        redp[threadIdx.x >> 5] = np;
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        unsigned long long ptot = 0ull;
-        for (int w = 0; w < 32; ++w) {
-            tot += red[w];
-            ptot += redp[w];
-        }
+        for (int w = 0; w < 32; ++w) tot += red[w];
         subj_loss[k] = tot;
-        if (pc.pairs) {
-            atomicAdd(pc.pairs, ptot);
-            if (pc.pairs_total) atomicAdd(pc.pairs_total, ptot);
-        }
     }
 }
 
@@ -2448,9 +2438,11 @@ void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_key
 }
 static inline int round_warp(int n) { return (n + 31) / 32 * 32; }
 void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre, int n_tiles, int *cnt,
-                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st) {
+                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st,
+                  unsigned long long *pairs, unsigned long long *pairs_total) {
     if (n_tiles <= 0) return;
-    if (phase == 0) k_item_count<<<cdiv(n_tiles, 256), 256, 0, st>>>(tps, tpe, trs, tre, n_tiles, cnt);
+    if (phase == 0)
+        k_item_count<<<cdiv(n_tiles, 256), 256, 0, st>>>(tps, tpe, trs, tre, n_tiles, cnt, pairs, pairs_total);
     else k_item_fill<<<cdiv(n_tiles, 256), 256, 0, st>>>(first, n_tiles, item_tile, cap_items);
     counted();
 }
@@ -2548,8 +2540,8 @@ void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st) {
     counted();
 }
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
-                        double *loss, unsigned *status, cudaStream_t st, const PairCount &pc) {
-    k_loss_reduce<<<std::max(n_subj, 1), 1024, 0, st>>>(tile_loss, n_tiles, tile_first, subj_loss, pc);
+                        double *loss, unsigned *status, cudaStream_t st) {
+    k_loss_reduce<<<std::max(n_subj, 1), 1024, 0, st>>>(tile_loss, n_tiles, tile_first, subj_loss);
     k_loss_total<<<1, 1, 0, st>>>(subj_loss, std::max(n_subj, 1), loss, status);
     counted(2);
 }

@@ -133,23 +133,18 @@ void launch_tile_rec_ranges(const uint32_t *keys, const int *n_keys, int cap_key
                             cudaStream_t st);
 // phase 0: items per tile into cnt; phase 1: item -> tile from the scanned offsets `first`
 void launch_items(const int *tps, const int *tpe, const int *trs, const int *tre, int n_tiles, int *cnt,
-                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st);
+                  const int *first, int *item_tile, int cap_items, int phase, cudaStream_t st,
+                  unsigned long long *pairs = nullptr, unsigned long long *pairs_total = nullptr);
 void launch_forward(const EvalArgs &a, cudaStream_t st);
 void launch_count_pairs(const EvalArgs &a, cudaStream_t st);
 long long launch_count();  // kernels launched by this library so far
 void note_launches(int n); // count kernels launched from other translation units
 // Dense r_bar tiles (from the per-pixel r_bar of the cap_px sample slots), then the tile adjoint.
 void launch_backward(const EvalArgs &a, int cap_px, cudaStream_t st);
-// Tile pairs of a forward (sampled pixels x records per tile), counted into
-// *pairs and *pairs_total (either may be null) by the loss reduction.
-struct PairCount {
-    const int *tps, *tpe, *trs, *tre;  // tile pixel and record ranges
-    unsigned long long *pairs, *pairs_total;
-};
 // Per-subject losses (subject k owns tiles [tile_first[k], tile_first[k+1]), summed in
 // tile order) and their total; tile_first null = one subject.
 void launch_loss_reduce(const double *tile_loss, int n_tiles, const int *tile_first, int n_subj, double *subj_loss,
-                        double *loss, unsigned *status, cudaStream_t st, const PairCount &pc = PairCount{});
+                        double *loss, unsigned *status, cudaStream_t st);
 // Sampled pixels per subject: cnt[k] = sum of the subject's tile pixel counts.
 void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first, int n_subj, int *cnt,
                            cudaStream_t st);
