@@ -94,6 +94,7 @@ struct gsvr_ctx {
     DBuf<uint32_t> d_keys, d_keys_sorted, d_keys_alt;
     DBuf<int2> d_vals_alt;
     DBuf<int> d_hist, d_scan_bsum;
+    DBuf<unsigned> d_cand_mask;  // slab-test bits of the candidate count pass (single subject)
     DBuf<float4> d_mom;
     DBuf<int> d_item_cnt, d_item_first, d_item_tile;
     DBuf<uint32_t> d_item_key, d_item_key_sorted, d_item_order, d_item_key_alt, d_item_val_alt;
@@ -1238,6 +1239,14 @@ gsvr_status gsvr_forward(gsvr_ctx *ctx) {
     b.tile_px_end = ctx->d_tile_px_end.p;
     b.rec_cnt = ctx->d_rec_cnt.p;
     b.status = ctx->d_status.p;
+    {  // candidate masks (single-subject contexts): the emit pass replays the count pass's tests
+        const size_t words = (size_t)((M + 31) / 32) * (size_t)std::max(N, 1);
+        if (!ctx->multi_gauss && ctx->d_cand_mask.n < words) {
+            if (ctx->capturing) return fail(ctx, GSVR_ERR_STATE, "candidate masks must exist before capture");
+            CK(ctx->d_cand_mask.ensure(words));
+        }
+        b.cand_mask = ctx->multi_gauss ? nullptr : ctx->d_cand_mask.p;
+    }
     launch_cand_count(b, st);
     CK(cudaGetLastError());
     CK(scan_exclusive(ctx->d_rec_cnt.p, ctx->d_rec_off.p, nullptr, N, N, &cnt->n_rec, scan_scratch(ctx), st));

@@ -431,7 +431,7 @@ __global__ void k_tile_px_ranges(const int *__restrict__ sampled, const int *n_s
 __global__ void k_set_count(int *dst, int v) { *dst = v; }
 
 // ------------------------------------------------------------------ binning
-constexpr int kSliceChunk = 32;
+constexpr int kSliceChunk = 32;  // slices staged per round (one 32-bit candidate-mask word)
 
 // Candidates: every (slice, Gaussian) pair whose slice-normal offset passes a
 // float32 slab test with a small margin (a superset of the pairs the exact cut
@@ -517,8 +517,10 @@ __global__ void __launch_bounds__(128) k_cand(BinArgs a) {
         }
         __syncthreads();
         if (!live) continue;
+        unsigned bits = 0u;  // (kSliceChunk = 32: chunk i0 / 32 is one mask word)
         for (int ii = 0; ii < nc; ++ii) {
             if (!slab_candidate(g0, g1, mu, ssl[ii], a.rc2)) continue;
+            bits |= 1u << ii;
             if (EMIT && n < room) {
                 const int c = base + n;
                 if (c < a.cap_rec) a.cand[c] = make_int2(j, i0 + ii);
@@ -526,10 +528,57 @@ __global__ void __launch_bounds__(128) k_cand(BinArgs a) {
             }
             ++n;
         }
+        if (!EMIT && a.cand_mask) a.cand_mask[(size_t)(i0 / kSliceChunk) * a.N + j] = bits;
     }
     if (!EMIT && live) a.rec_cnt[j] = n;
     if (EMIT && live)
         for (int k = n; k < room && base + k < a.cap_rec; ++k) a.cand[base + k] = make_int2(j, -1);
+}
+
+// Emit pass from the count pass's slab bits (single subject): the block's
+// Gaussians own the contiguous candidate range [rec_off[j0], rec_off[j1]); each
+// thread places its candidates (slices in order) in shared memory, then the
+// block writes the range with consecutive threads on consecutive candidates.
+// A range larger than the staging buffer is written directly.
+constexpr int kCandThreads = 128;
+constexpr int kCandStage = 6144;  // staged candidates per block (48 KB)
+__global__ void __launch_bounds__(kCandThreads) k_cand_emit_masks(BinArgs a) {
+    extern __shared__ int2 stage[];
+    const int j0 = blockIdx.x * kCandThreads, j1 = min(a.N, j0 + kCandThreads);
+    const int j = j0 + threadIdx.x;
+    const bool live = j < j1;
+    const int c0 = a.rec_off[j0], c1 = a.rec_off[j1];
+    const bool staged = c1 - c0 <= kCandStage;
+    const int base = live ? a.rec_off[j] : 0, room = live ? a.rec_off[j + 1] - base : 0;
+    if (live) {
+        const int W = (a.M + 31) >> 5;
+        int n = 0;
+        for (int w = 0; w < W; ++w) {
+            unsigned m = a.cand_mask[(size_t)w * a.N + j];
+            while (m) {
+                const int i = 32 * w + __ffs(m) - 1;
+                m &= m - 1u;
+                if (n < room) {
+                    if (staged) stage[base - c0 + n] = make_int2(j, i);
+                    else if (base + n < a.cap_rec) a.cand[base + n] = make_int2(j, i);
+                }
+                ++n;
+            }
+        }
+        for (int k = n; k < room; ++k) {  // (a count that moved: padding, as the slab pass pads)
+            if (staged) stage[base - c0 + k] = make_int2(j, -1);
+            else if (base + k < a.cap_rec) a.cand[base + k] = make_int2(j, -1);
+        }
+    }
+    if (!staged) {
+        if (live && base + room > a.cap_rec && room > 0) atomicOr(a.status, ST_CAPACITY);
+        return;
+    }
+    __syncthreads();
+    for (int c = c0 + threadIdx.x; c < c1; c += kCandThreads) {
+        if (c < a.cap_rec) a.cand[c] = stage[c - c0];
+        else atomicOr(a.status, ST_CAPACITY);
+    }
 }
 
 // Thread per candidate: the exact cut, the slice-plane conditioning, the tile
@@ -2416,7 +2465,19 @@ void launch_cand_count(const BinArgs &a, cudaStream_t st) {
 }
 void launch_cand_emit(const BinArgs &a, cudaStream_t st) {
     if (a.N <= 0) return;
-    k_cand<true><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    if (a.cand_mask && !a.gauss_subject) {
+        static int attr_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (attr_dev != dev) {
+            cudaFuncSetAttribute(k_cand_emit_masks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kCandStage * sizeof(int2)));
+            attr_dev = dev;
+        }
+        k_cand_emit_masks<<<cdiv(a.N, kCandThreads), kCandThreads, kCandStage * sizeof(int2), st>>>(a);
+    } else {
+        k_cand<true><<<cdiv(a.N, 128), 128, 0, st>>>(a);
+    }
     counted();
 }
 void launch_records(const BinArgs &a, int n_cand_max, cudaStream_t st) {

@@ -18,6 +18,8 @@ struct BinArgs {
     const int *rec_off;        // first candidate of each Gaussian, N + 1
     const int *n_rec;          // device count of candidates (= records)
     int2 *cand;                // (Gaussian, slice) per candidate; slice -1 = padding
+    unsigned *cand_mask;       // slab-test bits of the count pass, word w of Gaussian j at [w * N + j]
+                               // (ceil(M / 32) words; null or a multi-subject batch: the emit pass tests again)
     const int *gauss_subject;  // subject of each Gaussian (null: one subject)
     const int *subj_slice_first;  // first slice of each subject (n_subj + 1)
     const uint8_t *subj_active;   // per subject, 0 = retired: its Gaussians meet no slice (null: all active)
