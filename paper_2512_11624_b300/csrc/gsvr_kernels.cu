@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(16) int2 sref[3][kItemRecs + 2];
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ __align__(8) uint64_t bar_never;  // initialised, never arrived on (test hook only)
-    __shared__ float red[4 * 256];
+    __shared__ __align__(16) float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
     __shared__ int s_w[3], s_off[3], s_nrec[3], s_pend[3];
     __shared__ int s_fail;
@@ -975,9 +975,16 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
         if (COUNT) continue;
         // groups -> one sum per dense tile pixel
         if (active) {
+            float *dst = red + g * a.tile_px + row * a.tile_w + col0;
+            if (PXR % 4 == 0 && ((a.tile_w | a.tile_px) & 3) == 0 && col0 + PXR <= a.tile_w) {
 #pragma unroll
-            for (int k = 0; k < PXR; ++k)
-                if (col0 + k < a.tile_w) red[g * a.tile_px + row * a.tile_w + col0 + k] = acc[k];
+                for (int k = 0; k < PXR; k += 4)  // 16-byte stores (4-way fewer bank wavefronts)
+                    *reinterpret_cast<float4 *>(dst + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < PXR; ++k)
+                    if (col0 + k < a.tile_w) dst[k] = acc[k];
+            }
         }
         __syncthreads();
         for (int px = tid; px < a.tile_px; px += blockDim.x) {
