@@ -311,8 +311,25 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
         gsvr.gsvr_backward(ctx.ctx)
         gsvr.gsvr_adam_step(ctx.ctx, k + 1)
 
+    # pairs inside the cut per step: counted exactly (count pass over the sampled
+    # pixels) outside the timed region, on the parameters before and after the
+    # timed steps (the optimisation moves the Gaussians, so the count drifts over
+    # a long run; a step's pairs are taken as the mean of the two ends)
+    n_count = 3 if sampled else 1
+
+    def count_pairs(k0):
+        u_sum = t_sum = 0
+        for k in range(n_count):
+            set_sample(ctx, k0 + k)
+            gsvr.gsvr_forward(ctx.ctx)
+            u, e = gsvr.gsvr_count_pairs(ctx.ctx)
+            u_sum += u
+            t_sum += e
+        return u_sum / n_count, t_sum / n_count
+
     for k in range(warmup):
         step(k)
+    useful_start, tile_start = count_pairs(warmup)
     gsvr.gsvr_sync_status(ctx.ctx)
     gsvr.gsvr_timing_reset(ctx.ctx)
     clocks = None
@@ -343,18 +360,9 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
     kt = gsvr.gsvr_get_kernel_times(ctx.ctx)
     ms_max = reduce_max(ms, ws)
 
-    # pairs inside the cut per step: counted exactly (count pass over the sampled pixels)
-    # on the current parameters, outside the timed region (3 more samples when sampling)
-    u_sum = t_sum = 0
-    n_count = 3 if sampled else 1
-    for k in range(n_count):
-        set_sample(ctx, warmup + steps + k)
-        gsvr.gsvr_forward(ctx.ctx)
-        u, e = gsvr.gsvr_count_pairs(ctx.ctx)
-        u_sum += u
-        t_sum += e
-    useful_per_step = u_sum / n_count
-    tile_pairs_per_step = t_sum / n_count
+    useful_end, tile_end = count_pairs(warmup + steps)
+    useful_per_step = 0.5 * (useful_start + useful_end)
+    tile_pairs_per_step = 0.5 * (tile_start + tile_end)
     useful_total = reduce_sum(useful_per_step * steps, ws)
     px_total = reduce_sum(float(n_s) * steps, ws)
     value = useful_total / (ms_max / 1e3)
@@ -481,6 +489,7 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
            "l2": "inputs larger than L2 (records + keys + tile records ~%.0f MB per step)" %
                  ((stats["n_records"] * 44 + stats["n_keys"] * 108) / 1e6),
            "px_per_s": px_total / (ms_max / 1e3), "useful_pairs_per_step": useful_per_step,
+           "useful_pairs_start_end": [useful_start, useful_end],
            "tile_pairs_per_step": tile_pairs_per_step,
            "useful_fraction": useful_per_step / max(tile_pairs_per_step, 1),
            "stage_ms_per_step": {k: v / steps for k, v in kt["ms"].items()},
