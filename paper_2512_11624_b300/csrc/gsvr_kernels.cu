@@ -1115,11 +1115,12 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 // at a time through packed f32x2 instructions (lane x row r, lane y row r + 1;
 // a row past the box is a tile row, an exact extra term, or past the tile,
 // where r_bar reads 0), so a box is ceil(nr / 2) row pairs x nc columns.
-// The CTA orders its records by nc (a counting sort in shared memory, widest
-// first); thread t evaluates sorted records t and kItemRecs - 1 - t, so the
-// lanes of a warp run column loops of about equal length and every thread gets
-// one wide and one narrow box.  Which thread evaluates a record does not change
-// its moments, so the output does not depend on that order.  The tile's r_bar
+// The CTA orders its records by box shape (a counting sort in shared memory:
+// row pairs, then columns, largest first); thread t evaluates sorted records t
+// and nrec - 1 - t, so the lanes of a warp run loops of the same row-pair and
+// column counts and every thread gets one large and one small box.  Which
+// thread evaluates a record does not change its moments, so the output does
+// not depend on that order.  The tile's r_bar
 // (k_rbar_tiles; 0 off the sample) sits in shared memory as pairs of
 // vertically adjacent values, one 64-bit load per packed step, with a row
 // stride of tile_w + 1 pairs (lanes on different rows spread over the banks).  Per row pair the row terms C da and B da^2 are formed once and
@@ -1128,7 +1129,14 @@ __global__ void __launch_bounds__(kMaxTilePx) k_fwd_reduce(EvalArgs a) {
 // g da^2) whose two lanes are added at the end and written to the record's key
 // slot.
 constexpr int kBwdThreads = kItemRecs / 2;
-constexpr int kBwdClasses = 33;  // box widths 0 .. 32 columns
+// Box shape classes: (row pairs 1 .. 16) x (columns 1 .. 32), then the empty box.
+constexpr int kBwdClassesMax = 16 * 33 + 1;
+// Sorted position class of a packed box, for a tile of nrp_max row pairs.
+__device__ __forceinline__ int bwd_class(int box, int nrp_max) {
+    if (box == 0) return nrp_max * 33;
+    const int nrp = (((box >> 8) & 255) + 1) >> 1, ncol = (box >> 24) & 255;
+    return (nrp_max - nrp) * 33 + (32 - ncol);
+}
 
 struct __align__(16) BwdRec {  // a record as its evaluating thread reads it
     float cb, ca, A, C;
@@ -1212,17 +1220,18 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
     extern __shared__ float2 rb2[];  // tile_h x (tile_w + 1) pairs (r_bar[row][col], r_bar[row + 1][col])
     __shared__ BwdRec srec[kItemRecs];
     __shared__ int s_item, s_box;
-    __shared__ int cls_cnt[kBwdClasses], cls_start[kBwdClasses];
+    __shared__ int cls[kBwdClassesMax];  // per class: count, then first sorted position
     __shared__ unsigned long long s_eval;
     const int tid = threadIdx.x;
     const int n_items = min(*a.n_items, a.cap_items);
     const int tw = a.tile_w, th = a.tile_h, ts = tw + 1;
+    const int nrp_max = (th + 1) >> 1, ncls = nrp_max * 33 + 1;
     unsigned long long evaluated = 0;
     if (tid == 0) s_eval = 0ull;
     for (;;) {
         __syncthreads();  // previous item's shared buffers are free
         if (tid == 0) s_item = atomicAdd(&a.counters->work_bwd, 1);
-        if (tid < kBwdClasses) cls_cnt[tid] = 0;
+        for (int c = tid; c < ncls; c += kBwdThreads) cls[c] = 0;
         __syncthreads();
         if (s_item >= n_items) break;
         const int i = a.item_order ? (int)a.item_order[s_item] : s_item;
@@ -1262,22 +1271,29 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
         __syncthreads();
         const float x0c = (float)tg.x0 - S.cx0, y0c = (float)tg.y0 - S.cy0;  // tile origin, slice-centred
         const int sb = s_box;
-        int box0 = 0, box1 = 0, rank0 = 0, rank1 = 0;
+        int box0 = 0, box1 = 0, cl0 = 0, cl1 = 0, rank0 = 0, rank1 = 0;
         if (v0) {
             box0 = bwd_box(R0, a.qcut, R0.a.x - x0c, R0.a.y - y0c, sb);
-            rank0 = atomicAdd(&cls_cnt[box0 >> 24], 1);
+            cl0 = bwd_class(box0, nrp_max);
+            rank0 = atomicAdd(&cls[cl0], 1);
         }
         if (v1) {
             box1 = bwd_box(R1, a.qcut, R1.a.x - x0c, R1.a.y - y0c, sb);
-            rank1 = atomicAdd(&cls_cnt[box1 >> 24], 1);
+            cl1 = bwd_class(box1, nrp_max);
+            rank1 = atomicAdd(&cls[cl1], 1);
         }
         __syncthreads();
-        if (tid < 32) {  // class starts: widths 32 .. 1, then the empty boxes
-            const int ncl = 32 - tid;
-            const int c = cls_cnt[ncl];
-            const int inc = warp_incl_scan_i(c);
-            cls_start[ncl] = inc - c;
-            if (tid == 31) cls_start[0] = inc;
+        if (tid < 32) {  // class counts -> first sorted positions (exclusive scan, class order)
+            const int per = (ncls + 31) >> 5;
+            const int c0 = min(ncls, tid * per), c1 = min(ncls, c0 + per);
+            int sum = 0;
+            for (int c = c0; c < c1; ++c) sum += cls[c];
+            int run = warp_incl_scan_i(sum) - sum;
+            for (int c = c0; c < c1; ++c) {
+                const int n = cls[c];
+                cls[c] = run;
+                run += n;
+            }
         }
         __syncthreads();
         if (v0) {
@@ -1290,7 +1306,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
             b.box = box0;
             b.key = ref0.y;
             b.pad_ = 0;
-            srec[cls_start[box0 >> 24] + rank0] = b;
+            srec[cls[cl0] + rank0] = b;
         }
         if (v1) {
             BwdRec b;
@@ -1302,10 +1318,10 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_bwd_items(EvalArgs a) {
             b.box = box1;
             b.key = ref1.y;
             b.pad_ = 0;
-            srec[cls_start[box1 >> 24] + rank1] = b;
+            srec[cls[cl1] + rank1] = b;
         }
         __syncthreads();
-        // one wide and one narrow box per thread (sorted positions t and nrec - 1 - t)
+        // one large and one small box per thread (sorted positions t and nrec - 1 - t)
         if (tid < nrec) evaluated += bwd_eval_rec(srec[tid], rb2, ts, x0c, y0c, a.mom);
         const int u = nrec - 1 - tid;
         if (u >= kBwdThreads) evaluated += bwd_eval_rec(srec[u], rb2, ts, x0c, y0c, a.mom);
