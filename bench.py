@@ -35,6 +35,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -68,7 +69,8 @@ def parse():
     ap.add_argument("--no-fetal", action="store_true", help="skip the secondary fetal measurement")
     ap.add_argument("--stacks", type=int, default=0, help="keep only the first n stacks (profiling captures)")
     ap.add_argument("--tile", default="auto",
-                    help="HxW tile (no tuning) or 'auto': the library's autotuner picks the launch shape")
+                    help="HxW or HxWpxP tile (no tuning; P forward pixels per thread) or 'auto': the library's "
+                         "autotuner picks the launch shape")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -290,8 +292,10 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
                                                                           r.fwd_blocks_per_sm, r.bwd_blocks_per_sm,
                                                                           r.queue_order, r.ms) for r in res]}
     else:
-        th_, tw_ = (int(v) for v in args.tile.split("x"))
-        shape = gsvr.tiling(th_, tw_)
+        m = re.fullmatch(r"(\d+)x(\d+)(?:px(\d+))?", args.tile)
+        if not m:
+            raise SystemExit("--tile: HxW, HxWpxP or auto")
+        shape = gsvr.tiling(int(m.group(1)), int(m.group(2)), int(m.group(3) or 0))
     shape_d = {k: v for k, v in shape.as_dict().items() if k != "ms"}
     # capacities from one probe forward, then a fixed-capacity context (no host sync per step)
     st0 = probe_counts(shape)

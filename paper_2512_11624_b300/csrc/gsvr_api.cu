@@ -2044,7 +2044,8 @@ gsvr_status gsvr_tune_space_default(gsvr_tiling *out, int32_t cap, int32_t *n) {
         {12, 12, 2, 0, 0, 0},  {12, 12, 0, 4, 4, 0},  {12, 12, 0, 0, -1, 0}, {12, 12, 0, -1, -1, 0},
         {16, 16, 0, 0, 0, 0},  {16, 16, 0, 0, 0, 1},  {16, 16, 2, 0, 0, 0},  {16, 16, 0, 0, -1, 0},
         {8, 16, 0, 0, 0, 0},   {16, 8, 0, 0, 0, 0},   {8, 32, 0, 0, 0, 0},   {32, 8, 0, 0, 0, 0},
-        {12, 16, 0, 0, 0, 0},  {10, 10, 0, 0, 0, 0},  {10, 12, 0, 0, -1, 0}, {12, 8, 0, 0, -1, 0}};
+        {12, 16, 0, 0, 0, 0},  {10, 10, 0, 0, 0, 0},  {10, 12, 0, 0, -1, 0}, {12, 8, 0, 0, -1, 0},
+        {32, 16, 0, 0, 0, 0},  {16, 32, 0, 0, 0, 0},  {32, 32, 0, 0, 0, 0}};
     const int32_t total = (int32_t)(sizeof(space) / sizeof(space[0]));
     *n = total;
     for (int32_t k = 0; k < std::min(cap, total); ++k) {

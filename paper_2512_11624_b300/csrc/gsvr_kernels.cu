@@ -778,6 +778,29 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Row bands of the forward: 16 consecutive threads of a group (a half-warp)
+// own 16 / segs consecutive tile rows.  Bands of a record: those that meet the
+// rows of its in-cut box (the rows whose pixel centres can satisfy the cut
+// q + log2 w_n >= log2 cutoff_rel, the same box and margin as the backward's);
+// its pairs in the other bands are below the cut.  Returns the band bits, 0
+// when the box misses the tile's rows.
+constexpr int kFwdBands = 16, kFwdBandsMin = 4;
+__host__ __device__ __forceinline__ bool fwd_bands_fit(int tpg, int segs, int threads) {
+    return tpg >= 32 && tpg % 16 == 0 && segs <= 16 && 16 % segs == 0 && tpg / 16 <= kFwdBands && threads >= tpg;
+}
+__device__ __forceinline__ unsigned fwd_band_mask(const Rec &R, float qcut, float by, int rows, int rb) {
+    const float kap = R.b.z - qcut;
+    const float fa = -R.a.z, fb = -R.b.x, fc = -R.a.w;
+    const float D = 4.f * fa * fb - fc * fc;
+    if (!(kap >= 0.f && D > 0.f)) return 0u;
+    const float ty = fmaxf(4.f * kap * __fdividef(1.f, D) * fa, 0.f);
+    const float hy = ty * rsqrtf(fmaxf(ty, 1e-30f)) * 1.001f + 1e-2f;
+    const int r0 = max(0, __float2int_ru(fminf(fmaxf(by - hy, -1.f), 64.f)));
+    const int r1 = min(rows - 1, __float2int_rd(fminf(fmaxf(by + hy, -1.f), 64.f)));
+    if (r0 > r1) return 0u;
+    return ((2u << (r1 / rb)) - 1u) & ~((1u << (r0 / rb)) - 1u);
+}
+
 // Work item w (queue position) -> item, tile, first record and record count.
 struct ItemRef {
     int i, t, rs, nrec;
@@ -807,7 +830,12 @@ __device__ __forceinline__ ItemRef item_ref(const EvalArgs &a, int w) {
 // The groups' sums meet in shared memory; part[item][pixel] holds the item's
 // sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
 // (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
-template <bool COUNT, int PXR>
+// BANDS (tall tiles): each half-warp of a group owns a band of rows and walks
+// only the item's records whose in-cut box reaches those rows, from a list per
+// band built for every item by a stable ballot compaction (record order, so
+// a pixel's sum keeps its order and the output stays bitwise reproducible);
+// the lanes of a half-warp still read one record at a time (a broadcast).
+template <bool COUNT, int PXR, bool BANDS = false>
 __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(128) Rec buf[2][kItemRecs];
     __shared__ __align__(16) int2 sref[3][kItemRecs + 2];
@@ -815,6 +843,11 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(8) uint64_t bar_never;  // initialised, never arrived on (test hook only)
     __shared__ __align__(16) float red[4 * 256];
     __shared__ unsigned char present[kMaxTilePx];
+    constexpr int NBS = BANDS ? kFwdBands : 1, NRS = BANDS ? kItemRecs : 1;
+    __shared__ unsigned char blist[NBS][NRS];  // per row band: its records, in record order
+    __shared__ unsigned short bmask[NRS];
+    __shared__ int bcnt[BANDS ? kItemRecs / 32 : 1][NBS];
+    __shared__ int blen[NBS];
     __shared__ int s_w[3], s_off[3], s_nrec[3], s_pend[3];
     __shared__ int s_fail;
     const int n_items = min(*a.n_items, a.cap_items);
@@ -835,6 +868,11 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     const int G = max(1, (int)blockDim.x / tpg);
     const int g = tid / tpg, seg = tid - g * tpg;
     const int row = seg / segs, col0 = (seg - row * segs) * PXR;
+    // row bands (packed path): half-warps of 16 / segs rows, when a group is
+    // at least a warp and splits into whole half-warp bands
+    // (the launcher picks BANDS only for such shapes; NB = 1 otherwise)
+    const int NB = (BANDS && !COUNT && PXR >= 2 && fwd_bands_fit(tpg, segs, blockDim.x)) ? tpg / 16 : 1;
+    const int RB = NB > 1 ? 16 / segs : a.tile_h;
     // thread 0: take the next queue position into ring slot `slot` and start
     // the bulk copy of its references
     auto take = [&](int slot) {
@@ -905,6 +943,40 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
         const bool active = g < G && row < tg.rows;
         const float rowf = (float)(tg.y0 + row) - S.cy0;
         const float colf0 = (float)(tg.x0 + col0) - S.cx0;
+        if (BANDS && NB > 1) {
+            // per band, the item's records that reach it (stable compaction by
+            // ballots over 32-record chunks, so the lists keep record order)
+            const int lane = tid & 31;
+            const unsigned lt = (1u << lane) - 1u;
+            const int nr32 = (nrec + 31) & ~31;
+            const float by0 = S.cy0 - (float)tg.y0;  // + the record centre: its tile-local row
+            for (int r = tid; r < nr32; r += blockDim.x) {
+                const unsigned m = r < nrec ? fwd_band_mask(rb[r], a.qcut, rb[r].a.y + by0, tg.rows, RB) : 0u;
+                bmask[r] = (unsigned short)m;
+                for (int b = 0; b < NB; ++b) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
+                    if (lane == 0) bcnt[r >> 5][b] = __popc(bal);
+                }
+            }
+            __syncthreads();
+            for (int r = tid; r < nr32; r += blockDim.x) {
+                const unsigned m = bmask[r];
+                for (int b = 0; b < NB; ++b) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
+                    if ((m >> b) & 1u) {
+                        int off = 0;
+                        for (int c = 0; c < (r >> 5); ++c) off += bcnt[c][b];
+                        blist[b][off + __popc(bal & lt)] = (unsigned char)r;
+                    }
+                }
+            }
+            if (tid < NB) {
+                int n = 0;
+                for (int c = 0; c < (nr32 >> 5); ++c) n += bcnt[c][tid];
+                blen[tid] = n;
+            }
+            __syncthreads();
+        }
         if (COUNT) {
             const int ps = a.tile_px_start[ir.t], pe = a.tile_px_end[ir.t];
             for (int k = tid; k < a.tile_px; k += blockDim.x) present[k] = 0;
@@ -930,7 +1002,10 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
                     colk[k] = make_float2(colf0 + (float)(2 * k), colf0 + (float)(2 * k + 1));
                     acc2[k] = make_float2(0.f, 0.f);
                 }
-                for (int r = g; r < nrec; r += G) {
+                const int band = BANDS && NB > 1 ? seg >> 4 : 0;
+                const int len = BANDS && NB > 1 ? blen[band] : nrec;
+                for (int i = g; i < len; i += G) {
+                    const int r = BANDS && NB > 1 ? (int)blist[band][i] : i;
                     const float4 r0 = rb[r].a;
                     const float4 r1 = rb[r].b;
                     const float dy = rowf - r0.y;
@@ -2596,7 +2671,16 @@ static void fwd_items(const EvalArgs &a, cudaStream_t st) {
     const int nt = fwd_threads(a.tile_w, a.tile_h, pxr);
     cudaMemsetAsync(&a.counters->work_fwd, 0, sizeof(int), st);
     const int grid = eval_grid(a, false);
-    if (pxr == 8) k_fwd_items<COUNT, 8><<<grid, nt, 0, st>>>(a);
+    // row bands from kFwdBandsMin bands up: on the 1M-Gaussian workload the lists
+    // cut the forward 13.1 -> 8.8 ms at 32 x 32 (8 bands) and 8.5 -> 7.0-7.4 ms
+    // at 32 x 16 / 16 x 32 (4 bands), and cost 7-10 % with 2 bands
+    const int segs = (a.tile_w + pxr - 1) / pxr;
+    const int tpg = a.tile_h * segs;
+    const bool bands = !COUNT && pxr >= 2 && fwd_bands_fit(tpg, segs, nt) && tpg / 16 >= kFwdBandsMin;
+    if (pxr == 8 && bands) k_fwd_items<COUNT, 8, true><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 4 && bands) k_fwd_items<COUNT, 4, true><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 2 && bands) k_fwd_items<COUNT, 2, true><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 8) k_fwd_items<COUNT, 8><<<grid, nt, 0, st>>>(a);
     else if (pxr == 4) k_fwd_items<COUNT, 4><<<grid, nt, 0, st>>>(a);
     else if (pxr == 2) k_fwd_items<COUNT, 2><<<grid, nt, 0, st>>>(a);
     else k_fwd_items<COUNT, 1><<<grid, nt, 0, st>>>(a);

@@ -13,7 +13,10 @@ SHAPES = [dict(tile_h=16, tile_w=16), dict(tile_h=8, tile_w=8, fwd_px_per_thread
           dict(tile_h=8, tile_w=32, fwd_px_per_thread=4, queue_order=1), dict(tile_h=12, tile_w=16, fwd_px_per_thread=2),
           dict(tile_h=5, tile_w=7, fwd_px_per_thread=1, fwd_blocks_per_sm=3),
           dict(tile_h=12, tile_w=12, fwd_blocks_per_sm=-1, bwd_blocks_per_sm=-1, queue_order=1),
-          dict(tile_h=8, tile_w=16, fwd_px_per_thread=8), dict(tile_h=6, tile_w=20, fwd_px_per_thread=8)]
+          dict(tile_h=8, tile_w=16, fwd_px_per_thread=8), dict(tile_h=6, tile_w=20, fwd_px_per_thread=8),
+          # forward row bands: 4 (32 x 16), 6 (24 x 32, 96-thread CTAs), 8 (32 x 32) and 16 (32 x 32, 4 px)
+          dict(tile_h=32, tile_w=16), dict(tile_h=24, tile_w=32), dict(tile_h=32, tile_w=32),
+          dict(tile_h=32, tile_w=32, fwd_px_per_thread=4)]
 
 
 def test_default_space_is_valid_host_logic():
