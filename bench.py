@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--workload", default="large", choices=["large", "fetal", "tiny"])
     ap.add_argument("--no-fetal", action="store_true", help="skip the secondary fetal measurement")
     ap.add_argument("--stacks", type=int, default=0, help="keep only the first n stacks (profiling captures)")
-    ap.add_argument("--tile", default="auto",
+    ap.add_argument("--tile", default="16x16",
                     help="HxW or HxWpxP tile (no tuning; P forward pixels per thread) or 'auto': the library's "
                          "autotuner picks the launch shape")
     ap.add_argument("--no-cpu-baseline", action="store_true")
