@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--tile", default="16x16",
                     help="HxW or HxWpxP tile (no tuning; P forward pixels per thread) or 'auto': the library's "
                          "autotuner picks the launch shape")
+    ap.add_argument("--fetal-tile", default="auto",
+                    help="launch shape of the fetal leg of the default run (as --tile; the autotuner by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -251,7 +253,7 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_e2e, with_cpu, clocks_on):
+def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_e2e, with_cpu, clocks_on, tile):
     """Times `steps` optimisation steps of one workload; returns its JSON fields."""
     case, desc = workload(name, rank, args.stacks)
     sampled = name == "fetal"  # the fetal case draws 2^18 pixels per step; the others use every masked pixel
@@ -277,7 +279,7 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
     # launch shape: fixed, or the autotuner's pick (timed fwd+bwd iterations of
     # every candidate on a fixed-capacity context, before and outside the timed region)
     tuning = None
-    if args.tile == "auto":
+    if tile == "auto":
         st0 = probe_counts(gsvr.tiling(12, 12))
         tune = gsvr.Context(case, device=dev, stream=stream.cuda_stream, tile_h=12, tile_w=12, fixed_capacity=1,
                             cap_records=int(st0["n_records"] * 1.5) + 4096, cap_keys=int(st0["n_keys"] * 4) + 4096)
@@ -292,7 +294,7 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
                                                                           r.fwd_blocks_per_sm, r.bwd_blocks_per_sm,
                                                                           r.queue_order, r.ms) for r in res]}
     else:
-        m = re.fullmatch(r"(\d+)x(\d+)(?:px(\d+))?", args.tile)
+        m = re.fullmatch(r"(\d+)x(\d+)(?:px(\d+))?", tile)
         if not m:
             raise SystemExit("--tile: HxW, HxWpxP or auto")
         shape = gsvr.tiling(int(m.group(1)), int(m.group(2)), int(m.group(3) or 0))
@@ -515,11 +517,12 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream(device=local)
     head = measure(args, gsvr, torch, local, stream, args.workload, rank, ws, args.steps, args.warmup,
-                   not args.no_e2e, not args.no_cpu_baseline, True)
+                   not args.no_e2e, not args.no_cpu_baseline, True, args.tile)
     fetal = None
     if args.workload == "large" and not args.no_fetal:
         fs = max(3, min(args.steps * 5, 1000))
-        f = measure(args, gsvr, torch, local, stream, "fetal", rank, ws, fs, max(args.warmup, 3), False, False, False)
+        f = measure(args, gsvr, torch, local, stream, "fetal", rank, ws, fs, max(args.warmup, 3), False, False, False,
+                    args.fetal_tile)
         fetal = {k: f[k] for k in ("value", "ms_per_step", "desc", "tile", "px_per_s", "useful_pairs_per_step",
                                    "tile_pairs_per_step", "useful_fraction", "stage_ms_per_step", "roofline",
                                    "hbm_stages", "graph", "gpu_launches")}
