@@ -260,8 +260,11 @@ gsvr_status gsvr_set_step(gsvr_ctx *ctx, int64_t step);
  * B300 kernels' knobs.
  *   tile_h, tile_w      pixel tile (each in [4, 32]; 0 -> 16), with
  *                       tile_h * ceil(tile_w / px) <= 256 for the forward's px
- *   fwd_px_per_thread   forward pixels per thread along a tile row: 1, 2, 4 or 8
- *                       (0 -> 8 when tile_w >= 16, 4 when tile_w >= 12, else 2)
+ *   fwd_px_per_thread   forward pixels per thread along a tile row: 1, 2, 4, 8 or 16
+ *                       (0 -> 8 when tile_w > 16, 16 when 12 < tile_w <= 16,
+ *                       4 when tile_w == 12, else 2); the launch is refused when
+ *                       the forward's groups x tile pixels exceed its shared
+ *                       buffer (max(128 x fwd_px_per_thread, 1024) floats)
  *   fwd_blocks_per_sm,
  *   bwd_blocks_per_sm   CTAs per SM of the persistent evaluation kernels
  *                       (0 -> as many as fit; larger requests are clamped;

@@ -1539,6 +1539,7 @@ gsvr_status gsvr_sync_status(gsvr_ctx *ctx) {
     if (s & ST_NONFINITE) return fail(ctx, GSVR_ERR_NONFINITE, "non-finite parameter, pose or loss");
     if (s & ST_TIMEOUT) return fail(ctx, GSVR_ERR_TIMEOUT, "a bounded device wait ran out");
     if (s & ST_INDEX) return fail(ctx, GSVR_ERR_INVALID_ARG, "pixel index out of range in a sample list");
+    if (s & ST_SHAPE) return fail(ctx, GSVR_ERR_INVALID_ARG, "forward launch shape exceeds the kernel's shared buffers");
     return GSVR_OK;
 }
 
@@ -1672,11 +1673,13 @@ gsvr_status check_tiling(gsvr_ctx *ctx, const gsvr_tiling &t) {
     if (th < 4 || th > 32 || tw < 4 || tw > 32)
         return fail(ctx, GSVR_ERR_INVALID_ARG, "tile sides must lie in [4, 32]");
     if (t.fwd_px_per_thread != 0 && t.fwd_px_per_thread != 1 && t.fwd_px_per_thread != 2 &&
-        t.fwd_px_per_thread != 4 && t.fwd_px_per_thread != 8)
-        return fail(ctx, GSVR_ERR_INVALID_ARG, "fwd_px_per_thread must be 0, 1, 2, 4 or 8");
+        t.fwd_px_per_thread != 4 && t.fwd_px_per_thread != 8 && t.fwd_px_per_thread != 16)
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "fwd_px_per_thread must be 0, 1, 2, 4, 8 or 16");
     const int pxr = fwd_pxr(tw, t.fwd_px_per_thread);
     if (th * ((tw + pxr - 1) / pxr) > 256)
         return fail(ctx, GSVR_ERR_INVALID_ARG, "tile_h * ceil(tile_w / px_per_thread) must be <= 256");
+    if (!fwd_shape_fits(tw, th, pxr))
+        return fail(ctx, GSVR_ERR_INVALID_ARG, "forward groups x tile pixels exceed the kernel's shared buffer");
     if (t.fwd_blocks_per_sm < -1 || t.fwd_blocks_per_sm > 64 || t.bwd_blocks_per_sm < -1 || t.bwd_blocks_per_sm > 64)
         return fail(ctx, GSVR_ERR_INVALID_ARG, "blocks per SM must lie in [-1, 64]");
     if (t.queue_order != 0 && t.queue_order != 1) return fail(ctx, GSVR_ERR_INVALID_ARG, "queue_order must be 0 or 1");
@@ -2045,7 +2048,7 @@ gsvr_status gsvr_tune_space_default(gsvr_tiling *out, int32_t cap, int32_t *n) {
         {16, 16, 0, 0, 0, 0},  {16, 16, 0, 0, 0, 1},  {16, 16, 2, 0, 0, 0},  {16, 16, 0, 0, -1, 0},
         {8, 16, 0, 0, 0, 0},   {16, 8, 0, 0, 0, 0},   {8, 32, 0, 0, 0, 0},   {32, 8, 0, 0, 0, 0},
         {12, 16, 0, 0, 0, 0},  {10, 10, 0, 0, 0, 0},  {10, 12, 0, 0, -1, 0}, {12, 8, 0, 0, -1, 0},
-        {32, 16, 0, 0, 0, 0},  {16, 32, 0, 0, 0, 0},  {32, 32, 0, 0, 0, 0}};
+        {32, 16, 0, 0, 0, 0},  {16, 32, 0, 0, 0, 0},  {32, 32, 0, 0, 0, 0},  {16, 16, 8, 0, 0, 0}};
     const int32_t total = (int32_t)(sizeof(space) / sizeof(space[0]));
     *n = total;
     for (int32_t k = 0; k < std::min(cap, total); ++k) {

@@ -21,7 +21,7 @@ constexpr int kSortRadixMax = 1 << kSortDigitMax;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s bound on any mbarrier wait
 
 // Device status word bits (latched; read by gsvr_sync_status).
-enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u };
+enum : unsigned { ST_CAPACITY = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_INDEX = 8u, ST_SHAPE = 16u };
 
 // Per-slice frame and geometry.  The frame fields are rewritten from the pose
 // every forward (Sec. 2.4: R_i = Rod(r) R0_i, t_i = Rod(r) c0_i + tau, computed in

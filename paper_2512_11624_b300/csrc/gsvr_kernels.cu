@@ -785,6 +785,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // its pairs in the other bands are below the cut.  Returns the band bits, 0
 // when the box misses the tile's rows.
 constexpr int kFwdBands = 16, kFwdBandsMin = 4;
+// Floats of the forward's shared per-pixel sums (groups x tile pixels): the
+// groups of a 128-thread CTA hold at most 128 x PXR pixels, and a single group
+// at most a whole tile (kMaxTilePx).
+__host__ __device__ constexpr int fwd_red_floats(int pxr) { return 128 * pxr > kMaxTilePx ? 128 * pxr : kMaxTilePx; }
 __host__ __device__ __forceinline__ bool fwd_bands_fit(int tpg, int segs, int threads) {
     return tpg >= 32 && tpg % 16 == 0 && segs <= 16 && 16 % segs == 0 && tpg / 16 <= kFwdBands && threads >= tpg;
 }
@@ -841,7 +845,7 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     __shared__ __align__(16) int2 sref[3][kItemRecs + 2];
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ __align__(8) uint64_t bar_never;  // initialised, never arrived on (test hook only)
-    __shared__ __align__(16) float red[4 * 256];
+    __shared__ __align__(16) float red[fwd_red_floats(PXR)];  // groups x tile pixels
     __shared__ unsigned char present[kMaxTilePx];
     constexpr int NBS = BANDS ? kFwdBands : 1, NRS = BANDS ? kItemRecs : 1;
     __shared__ unsigned char blist[NBS][NRS];  // per row band: its records, in record order
@@ -866,6 +870,10 @@ __global__ void __launch_bounds__(256) k_fwd_items(EvalArgs a) {
     const int segs = (a.tile_w + PXR - 1) / PXR;
     const int tpg = a.tile_h * segs;
     const int G = max(1, (int)blockDim.x / tpg);
+    if (G * a.tile_px > fwd_red_floats(PXR)) {  // (the launcher never picks such a shape; all threads leave)
+        if (tid == 0) atomicOr(a.status, ST_SHAPE);
+        return;
+    }
     const int g = tid / tpg, seg = tid - g * tpg;
     const int row = seg / segs, col0 = (seg - row * segs) * PXR;
     // row bands (packed path): half-warps of 16 / segs rows, when a group is
@@ -2615,11 +2623,14 @@ void launch_item_order(const int *item_tile, const int *item_first, const int *t
     while ((1 << bits) <= kItemRecs) ++bits;
     radix_sort_pairs(key, nullptr, key_sorted, order, n_items, cap_items, bits, ss, st);
 }
-// Forward pixels per thread: the requested run (1, 2 or 4), else 4 for tiles
-// at least 12 wide and 2 below.
+// Forward pixels per thread: the requested run (1, 2, 4, 8 or 16), else the
+// whole row for tiles 13 to 16 wide (on the 1M-Gaussian workload at 16 x 16 the
+// forward takes 5.23 ms with 16-pixel runs, 5.62 ms with 8), 8 for wider tiles
+// (32 x 32: 8.83 ms against 9.36 with 16, as finer row bands cull more), 4 for
+// tiles 12 wide and 2 below: the row terms amortised over the longest run.
 int fwd_pxr(int tile_w, int req) {
-    if (req == 1 || req == 2 || req == 4 || req == 8) return req;
-    return tile_w >= 16 ? 8 : (tile_w >= 12 ? 4 : 2);  // the row terms amortised over the longest run
+    if (req == 1 || req == 2 || req == 4 || req == 8 || req == 16) return req;
+    return tile_w > 16 ? 8 : (tile_w > 12 ? 16 : (tile_w == 12 ? 4 : 2));
 }
 // Forward CTA shape: groups of tile_h x ceil(tile_w / PXR) threads, as many
 // groups as fit in 128 threads (at least one).
@@ -2627,6 +2638,11 @@ int fwd_threads(int tile_w, int tile_h, int pxr) {
     const int tpg = tile_h * ((tile_w + pxr - 1) / pxr);
     const int G = std::max(1, 128 / tpg);
     return round_warp(G * tpg);
+}
+bool fwd_shape_fits(int tile_w, int tile_h, int pxr) {
+    const int tpg = tile_h * ((tile_w + pxr - 1) / pxr);
+    const int G = std::max(1, fwd_threads(tile_w, tile_h, pxr) / tpg);
+    return G * tile_w * tile_h <= fwd_red_floats(pxr);
 }
 int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     int nb = 0;
@@ -2636,7 +2652,8 @@ int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int pxr_req) {
     } else {
         const int pxr = fwd_pxr(tile_w, pxr_req);
         const int nt = fwd_threads(tile_w, tile_h, pxr);
-        if (pxr == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 8>, nt, 0);
+        if (pxr == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 16>, nt, 0);
+        else if (pxr == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 8>, nt, 0);
         else if (pxr == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 4>, nt, 0);
         else if (pxr == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 2>, nt, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_items<false, 1>, nt, 0);
@@ -2677,7 +2694,9 @@ static void fwd_items(const EvalArgs &a, cudaStream_t st) {
     const int segs = (a.tile_w + pxr - 1) / pxr;
     const int tpg = a.tile_h * segs;
     const bool bands = !COUNT && pxr >= 2 && fwd_bands_fit(tpg, segs, nt) && tpg / 16 >= kFwdBandsMin;
-    if (pxr == 8 && bands) k_fwd_items<COUNT, 8, true><<<grid, nt, 0, st>>>(a);
+    if (pxr == 16 && bands) k_fwd_items<COUNT, 16, true><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 16) k_fwd_items<COUNT, 16><<<grid, nt, 0, st>>>(a);
+    else if (pxr == 8 && bands) k_fwd_items<COUNT, 8, true><<<grid, nt, 0, st>>>(a);
     else if (pxr == 4 && bands) k_fwd_items<COUNT, 4, true><<<grid, nt, 0, st>>>(a);
     else if (pxr == 2 && bands) k_fwd_items<COUNT, 2, true><<<grid, nt, 0, st>>>(a);
     else if (pxr == 8) k_fwd_items<COUNT, 8><<<grid, nt, 0, st>>>(a);

@@ -79,7 +79,7 @@ struct EvalArgs {
     int cap_items;
     const int *subj_cnt;              // sampled pixels per subject (null: *n_sampled)
     const uint32_t *item_order;       // work-queue order of the items (null: item index order)
-    int fwd_pxr;                      // forward pixels per thread, 1, 2 or 4 (0: by tile width)
+    int fwd_pxr;                      // forward pixels per thread, 1, 2, 4, 8 or 16 (0: by tile width)
     int fwd_bps, bwd_bps;             // persistent CTAs per SM (0: as many as fit)
     int tile_px;                      // tile_w * tile_h
     int l1;                           // data term: 0 MSE, 1 L1 (the paper's)
@@ -154,6 +154,7 @@ void launch_subject_counts(const int *tps, const int *tpe, const int *tile_first
 int eval_blocks_per_sm(int tile_w, int tile_h, bool backward, int fwd_pxr_req);
 int fwd_pxr(int tile_w, int req);
 int fwd_threads(int tile_w, int tile_h, int pxr);
+bool fwd_shape_fits(int tile_w, int tile_h, int pxr);  // the groups' per-pixel sums fit the forward's shared buffer
 // Work-queue order: items sorted by descending record count (stable).
 void launch_item_order(const int *item_tile, const int *item_first, const int *trs, const int *tre,
                        const int *n_items, int cap_items, uint32_t *key, uint32_t *key_sorted, uint32_t *order,

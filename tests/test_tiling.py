@@ -16,7 +16,10 @@ SHAPES = [dict(tile_h=16, tile_w=16), dict(tile_h=8, tile_w=8, fwd_px_per_thread
           dict(tile_h=8, tile_w=16, fwd_px_per_thread=8), dict(tile_h=6, tile_w=20, fwd_px_per_thread=8),
           # forward row bands: 4 (32 x 16), 6 (24 x 32, 96-thread CTAs), 8 (32 x 32) and 16 (32 x 32, 4 px)
           dict(tile_h=32, tile_w=16), dict(tile_h=24, tile_w=32), dict(tile_h=32, tile_w=32),
-          dict(tile_h=32, tile_w=32, fwd_px_per_thread=4)]
+          dict(tile_h=32, tile_w=32, fwd_px_per_thread=4),
+          # 16-pixel runs: a whole 16-wide row per thread; ragged 12-wide rows; banded at 32 x 32
+          dict(tile_h=16, tile_w=16, fwd_px_per_thread=16), dict(tile_h=8, tile_w=12, fwd_px_per_thread=16),
+          dict(tile_h=32, tile_w=32, fwd_px_per_thread=16)]
 
 
 def test_default_space_is_valid_host_logic():
@@ -26,8 +29,8 @@ def test_default_space_is_valid_host_logic():
     space = gsvr.gsvr_tune_space_default()
     assert len(space) >= 8
     for t in space:
-        px = t.fwd_px_per_thread or (8 if t.tile_w >= 16 else (4 if t.tile_w >= 12 else 2))
-        assert 4 <= t.tile_h <= 32 and 4 <= t.tile_w <= 32 and px in (1, 2, 4, 8)
+        px = t.fwd_px_per_thread or (8 if t.tile_w > 16 else (16 if t.tile_w > 12 else (4 if t.tile_w == 12 else 2)))
+        assert 4 <= t.tile_h <= 32 and 4 <= t.tile_w <= 32 and px in (1, 2, 4, 8, 16)
         assert t.tile_h * -(-t.tile_w // px) <= 256
         assert t.queue_order in (0, 1)
 
