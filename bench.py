@@ -141,6 +141,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def parse_tile(spec):
+    """'HxW' or 'HxWpxP' -> (tile_h, tile_w, forward pixels per thread, 0 = by width)."""
+    m = re.fullmatch(r"(\d+)x(\d+)(?:px(\d+))?", spec)
+    if not m:
+        raise SystemExit("--tile: HxW, HxWpxP or auto, not %r" % spec)
+    return int(m.group(1)), int(m.group(2)), int(m.group(3) or 0)
+
+
 def kernel_source_sha(kernel):
     """Hash of the source text of one __global__ function (its definition up to the
     matching closing brace) in csrc/gsvr_kernels.cu."""
@@ -294,10 +302,7 @@ def measure(args, gsvr, torch, dev, stream, name, rank, ws, steps, warmup, with_
                                                                           r.fwd_blocks_per_sm, r.bwd_blocks_per_sm,
                                                                           r.queue_order, r.ms) for r in res]}
     else:
-        m = re.fullmatch(r"(\d+)x(\d+)(?:px(\d+))?", tile)
-        if not m:
-            raise SystemExit("--tile: HxW, HxWpxP or auto")
-        shape = gsvr.tiling(int(m.group(1)), int(m.group(2)), int(m.group(3) or 0))
+        shape = gsvr.tiling(*parse_tile(tile))
     shape_d = {k: v for k, v in shape.as_dict().items() if k != "ms"}
     # capacities from one probe forward, then a fixed-capacity context (no host sync per step)
     st0 = probe_counts(shape)

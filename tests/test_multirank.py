@@ -57,3 +57,14 @@ def test_two_gloo_ranks_reduce_and_shard():
     assert res[0]["sum"] == res[1]["sum"] == 30.0
     assert res[0]["theta0"] != res[1]["theta0"]  # each rank its own subject
     assert res[1]["reference_returned"]
+
+
+def test_bench_tile_spec():
+    """Host only: the bench's launch-shape argument."""
+    import bench
+    assert bench.parse_tile("16x16") == (16, 16, 0)
+    assert bench.parse_tile("32x8px4") == (32, 8, 4)
+    assert bench.parse_tile("16x16px16") == (16, 16, 16)
+    for bad in ("16", "16x", "x16", "16x16px", "16*16"):
+        with pytest.raises(SystemExit):
+            bench.parse_tile(bad)
