@@ -758,17 +758,7 @@ __device__ __forceinline__ TileGeom tile_geom(const SliceDev &S, int t, int tw, 
     return g;
 }
 
-// Persistent CTAs take work items from a queue (Counters::work_fwd).  An item's
-// records (at most kItemRecs x 32 bytes) come into shared memory by one 1-D bulk
-// copy (cp.async.bulk, completion on an mbarrier, one phase per item).  The CTA
-// is G groups of threads; in a group each thread owns a run of PXR consecutive
-// pixels of one tile row, and the groups split the records (every lane of a
-// warp reads the same record: a broadcast).  With the row fixed, the record's
-// row terms C2 da and B da^2 are formed once per PXR pixels:
-//   q = (A db + C2 da) db + B da^2,   sum += w exp2(q).
-// The groups' sums meet in shared memory; part[item][pixel] holds the item's
-// sum per dense tile pixel and k_fwd_reduce adds a tile's items in item order
-// (bitwise reproducible).  COUNT: count sampled pairs inside the cut instead.
+// 16-byte asynchronous global -> shared copies (the forward's record gathers).
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
