@@ -540,6 +540,7 @@ def main():
                            "autotune": head["autotune"], "parallelism": "replicas" if ws > 1 else "single",
                            "l2": head["l2"]},
                 "px_per_s": head["px_per_s"], "useful_pairs_per_step": head["useful_pairs_per_step"],
+                "useful_pairs_start_end": head["useful_pairs_start_end"],
                 "tile_pairs_per_step": head["tile_pairs_per_step"], "useful_fraction": head["useful_fraction"],
                 "stage_ms_per_step": head["stage_ms_per_step"], "records_per_step": head["records_per_step"],
                 "keys_per_step": head["keys_per_step"], "roofline": head["roofline"],
